@@ -1,0 +1,151 @@
+"""Pins for the oracle's solvers (Sections 2.2.1 and 2.3.1): convergence to
+dense normal-equation solutions, SIRT's fixed point, the Krylov-subspace
+optimality that defines CGLS, PCG and GMRES iterates, and the qualitative
+ordering of Section 4 (SIRT slowest, WMG-preconditioned Krylov fastest)."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+
+GEOM = (16, 24, 23)
+
+
+def setup(geom=GEOM, noise=0.01, seed=7):
+    op = oracle.Op(*geom)
+    rng = np.random.default_rng(seed)
+    x = rng.random(op.N)
+    b = op.project(x) + noise * rng.standard_normal(op.M)
+    return op, b
+
+
+def ls_solution(op, b, lam):
+    W = op.dense()
+    return np.linalg.solve(W.T @ W + lam * np.eye(op.N), W.T @ b)
+
+
+@pytest.mark.parametrize("lam", [0.0, 0.05])
+@pytest.mark.parametrize("pc", [None, (oracle.CYCLE_ADDITIVE, 0, 1), (2, 2, 1), (2, 1, 0)])
+def test_cgls_converges_to_dense_solution(lam, pc):
+    op, b = setup()
+    xs = ls_solution(op, b, lam)
+    M = None if pc is None else oracle.Wmg(op, 3, pc[2], pc[2], 1.0, lam, pc[0], pc[1])
+    x, k, hist = oracle.cgls(op, b, 2000, 1e-13, lam, M)
+    assert np.linalg.norm(x - xs) < 1e-10 * np.linalg.norm(xs)
+    assert abs(op.ne_residual(b, x, lam) - hist[-1]) < 1e-10
+
+
+@pytest.mark.parametrize("lam", [0.0, 0.05])
+@pytest.mark.parametrize("pc", [None, (oracle.CYCLE_HYBRID, 2, 1), (oracle.CYCLE_HYBRID, 1, 0),
+                                (oracle.CYCLE_ADDITIVE, 0, 0)])
+def test_gmres_converges_to_dense_solution(lam, pc):
+    op, b = setup()
+    xs = ls_solution(op, b, lam)
+    M = None if pc is None else oracle.Wmg(op, 3, pc[2], pc[2], 1.0, lam, pc[0], pc[1])
+    x, k, hist = oracle.gmres(op, b, 3000, 20, 1e-13, lam, M)
+    # the error is bounded by cond(A) times the residual (1e-13 here)
+    W = op.dense()
+    kappa = np.linalg.cond(W.T @ W + lam * np.eye(op.N))
+    assert hist[-1] < 1e-13
+    assert np.linalg.norm(x - xs) < 2e-13 * kappa * np.linalg.norm(xs)
+
+
+def test_sirt_fixed_point():
+    """SIRT's limit solves W^T R W x = W^T R b (C > 0 everywhere here)."""
+    op, b = setup((6, 10, 9))
+    W = op.dense()
+    R, Cc = op.sirt_scalings()
+    assert (Cc > 0).all()
+    xs = np.linalg.solve(W.T @ (R[:, None] * W), W.T @ (R * b))
+    x, hist = oracle.sirt(op, b, 20000)
+    assert np.linalg.norm(x - xs) < 1e-10 * np.linalg.norm(xs)
+
+
+def test_sirt_scalings():
+    op = oracle.Op(8, 6, 14)           # wide detector: some rays miss the image
+    W = op.dense()
+    R, Cc = op.sirt_scalings()
+    rs, cs = W.sum(axis=1), W.sum(axis=0)
+    assert (rs == 0).any()
+    assert np.allclose(R, np.where(rs > 0, 1 / np.where(rs > 0, rs, 1), 0), rtol=1e-14, atol=0)
+    assert np.allclose(Cc, np.where(cs > 0, 1 / np.where(cs > 0, cs, 1), 0), rtol=1e-14, atol=0)
+
+
+def krylov_basis(Mat, v, k):
+    cols = [v]
+    for _ in range(k - 1):
+        cols.append(Mat @ cols[-1])
+    Qb, _ = np.linalg.qr(np.column_stack(cols))
+    return Qb
+
+
+@pytest.mark.parametrize("k", [1, 3, 6])
+def test_cgls_iterate_minimises_over_krylov_space(k):
+    """x_k = argmin ||W x - b||^2 + lam ||x||^2 over K_k(A, W^T b)."""
+    op, b = setup()
+    lam = 0.02
+    W = op.dense()
+    A = W.T @ W + lam * np.eye(op.N)
+    V = krylov_basis(A, W.T @ b, k)
+    y = np.linalg.solve(V.T @ A @ V, V.T @ (W.T @ b))
+    x, it, _ = oracle.cgls(op, b, k, 0.0, lam)
+    assert it == k
+    assert np.linalg.norm(x - V @ y) < 1e-9 * np.linalg.norm(V @ y)
+
+
+@pytest.mark.parametrize("k", [2, 4])
+def test_pcg_iterate_minimises_energy_over_krylov_space(k):
+    """Preconditioned: x_k minimises the A-norm error over K_k(B A, B f)."""
+    op, b = setup()
+    W = op.dense()
+    A = W.T @ W
+    M = oracle.Wmg(op, 3, 1, 1, 1.0, 0.0, 2, 2)
+    B = np.column_stack([M.apply(e) for e in np.eye(op.N)])
+    f = W.T @ b
+    V = krylov_basis(B @ A, B @ f, k)
+    y = np.linalg.solve(V.T @ A @ V, V.T @ f)
+    x, it, _ = oracle.cgls(op, b, k, 0.0, 0.0, M)
+    assert np.linalg.norm(x - V @ y) < 1e-8 * np.linalg.norm(V @ y)
+
+
+@pytest.mark.parametrize("k", [3, 7])
+def test_gmres_iterate_minimises_residual(k):
+    """Right preconditioning, no restart: x_k = B u_k with u_k minimising
+    ||f - A B u|| over K_k(A B, f)."""
+    op, b = setup()
+    W = op.dense()
+    A = W.T @ W
+    M = oracle.Wmg(op, 3, 0, 0, 1.0, 0.0, oracle.CYCLE_HYBRID, 2)
+    B = np.column_stack([M.apply(e) for e in np.eye(op.N)])
+    f = W.T @ b
+    V = krylov_basis(A @ B, f, k)
+    y, *_ = np.linalg.lstsq(A @ B @ V, f, rcond=None)
+    x, it, _ = oracle.gmres(op, b, k, 50, 0.0, 0.0, M)
+    want = B @ V @ y
+    assert np.linalg.norm(x - want) < 1e-8 * np.linalg.norm(want)
+
+
+def test_full_gmres_terminates_within_N_steps():
+    op, b = setup((8, 16, 12))
+    xs = ls_solution(op, b, 0.0)
+    x, k, hist = oracle.gmres(op, b, op.N, op.N, 1e-12)
+    assert k <= op.N
+    assert np.linalg.norm(x - xs) < 1e-8 * np.linalg.norm(xs)
+
+
+def test_qualitative_ordering_small_workload():
+    """Section 4.1's ordering on the 64x64 noiseless workload: SIRT far from
+    converged, WMG-preconditioned Krylov needs fewer iterations than plain."""
+    P = S.workload_small().problems[0]
+    op = oracle.Op(P.n, P.m, P.D)
+    b = op.project(P.image())
+    _, k_plain, _ = oracle.gmres(op, b, 500, 20, 1e-4)
+    M = oracle.Wmg(op, P.levels, 1, 1, 1.0, 0.0, oracle.CYCLE_HYBRID, 2)
+    _, k_wmg, _ = oracle.gmres(op, b, 500, 20, 1e-4, 0.0, M)
+    Ms = oracle.Wmg(op, P.levels, 1, 1, 1.0, 0.0, 2, 2)
+    _, k_cg, _ = oracle.cgls(op, b, 500, 1e-4, 0.0, Ms)
+    _, k_cgp, _ = oracle.cgls(op, b, 500, 1e-4)
+    _, hs = oracle.sirt(op, b, 50)
+    assert k_wmg < k_plain / 2
+    assert k_cg < k_cgp / 2
+    assert hs[-1] > 1e-3

@@ -1,0 +1,177 @@
+/*
+ * wmgct.h -- C ABI of the GB300 library for wavelet-multigrid (WMG)
+ * preconditioned Krylov reconstruction in 2D parallel-beam algebraic
+ * tomography (Cools, Ghysels, van Aarle, Sijbers, Vanroose, arXiv 1310.0956).
+ *
+ * The calls follow the paper's statement of the problem (Section 2.1,
+ * eq. sys / sys_ne / sys_reg): an n x n image x on the unit square, m
+ * projection angles, D detector bins per angle, a sinogram b of M = m*D
+ * values; W holds the exact pixel-ray intersection lengths; the solvers
+ * work on the normal equations (W^T W + lambda I) x = W^T b, optionally
+ * preconditioned by one WMG cycle (Section 3.1).
+ *
+ * Conventions shared by every call
+ *  - Image layout: row-major x[iy*n + ix], iy = 0 at y = -1/2, pixel width
+ *    h = 1/n. Sinogram layout: angle-major b[a*D + k]. Ray (a, k) is the line
+ *    p . (cos t_a, sin t_a) = t_k with t_k = ((k - (D-1)/2)*det_spacing +
+ *    det_offset) * h. A line that runs exactly along a pixel edge gives half
+ *    of the edge to each of the two pixels sharing it.
+ *  - Batches: calls that take `count` operate on `count` problems of the same
+ *    geometry stored back to back (problem q's image at x + q*N, its sinogram
+ *    at b + q*M).
+ *  - Element type of every image/sinogram buffer passed in or out: double
+ *    for WMG_PREC_F64 plans, float for WMG_PREC_F32 plans.
+ *  - Memory: every buffer argument is caller-owned DEVICE memory unless the
+ *    argument says "host". The library keeps no pointer to caller buffers
+ *    after a call returns. Plans own their workspace (device memory taken at
+ *    creation and, for larger batches, at the first solve that needs it).
+ *  - Streams: work is enqueued on the caller's cudaStream_t (passed as
+ *    void*; NULL = the legacy default stream). Calls documented as
+ *    "synchronising" wait for the stream before returning.
+ *  - Errors: every call returns an int32 status (WMG_OK = 0, WMG_NOT_CONVERGED
+ *    = 1, negative = error); no exception crosses the ABI. wmg_last_error()
+ *    returns a message for the last failing call of the calling thread.
+ *  - Threads: a plan, batch or server is not thread-safe; use one per stream.
+ */
+#ifndef WMGCT_H
+#define WMGCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------- */
+#define WMG_OK                 0
+#define WMG_NOT_CONVERGED      1   /* iteration cap reached; x is still valid */
+#define WMG_ERR_INVALID_ARG   -1
+#define WMG_ERR_OOM           -2
+#define WMG_ERR_CUDA          -3
+#define WMG_ERR_LEAF_NOT_SPD  -4   /* a leaf matrix failed its Cholesky pivot test */
+#define WMG_ERR_BREAKDOWN     -5   /* Krylov breakdown: zero curvature / Hessenberg */
+#define WMG_ERR_TIMEOUT       -6
+#define WMG_ERR_NAN           -7   /* non-finite value in a reduction */
+#define WMG_ERR_REJECTED      -8   /* server: request larger than the memory budget */
+
+/* ---- enumerations --------------------------------------------------------- */
+#define WMG_PREC_F64   0   /* operator, vectors and reductions in FP64 */
+#define WMG_PREC_F32   1   /* operator (W, W^T, Haar, leaf solves) in FP32,
+                              Krylov vectors, scalars and reductions in FP64 */
+
+#define WMG_CYCLE_ADDITIVE   0  /* all leaf corrections from one residual */
+#define WMG_CYCLE_HYBRID     1  /* Section 3.1.2: residual recomputed after the
+                                   LL band at every node above hybrid_depth */
+#define WMG_CYCLE_SYMMETRIC  2  /* hybrid followed by a second LL correction
+                                   (LL, rest, LL): symmetric, for CGLS */
+
+#define WMG_SOLVER_SIRT   0   /* eq. sirt_it */
+#define WMG_SOLVER_CGLS   1   /* CGLS / PCG on the normal equations */
+#define WMG_SOLVER_GMRES  2   /* restarted GMRES, right preconditioning */
+
+/* ---- parameter blocks ----------------------------------------------------- */
+typedef struct wmg_geom {
+    int32_t n;              /* image side in pixels, >= 1 */
+    int32_t m;              /* number of projection angles, >= 1 */
+    const double *angles;   /* HOST array of m angles in radians, or NULL for
+                               theta_a = a*pi/m (equiangular over [0, pi)) */
+    int32_t D;              /* detector bins per angle, >= 1 */
+    double det_spacing;     /* bin spacing in pixel widths; <= 0 means 1 */
+    double det_offset;      /* detector centre offset in pixel widths */
+} wmg_geom;
+
+typedef struct wmg_opts {
+    int32_t levels;         /* WMG levels l >= 1; L = l-1 Haar levels, n must be
+                               divisible by 2^L; leaves are (n/2^L)^2 unknowns
+                               (at most 256) and there are 4^L of them */
+    int32_t nu1, nu2;       /* l1-Jacobi pre/post smoothing sweeps (>= 0) */
+    double omega;           /* smoother damping; <= 0 means 1 */
+    double lambda;          /* Tikhonov parameter >= 0 (eq. sys_reg) */
+    int32_t hybrid_depth;   /* nodes at depth < hybrid_depth use the hybrid
+                               residual update (HYBRID/SYMMETRIC cycles) */
+    int32_t cycle;          /* WMG_CYCLE_* */
+    int32_t precision;      /* WMG_PREC_* */
+} wmg_opts;
+
+/* Per-problem outcome of a solve (host memory, one entry per problem). */
+typedef struct wmg_solve_info {
+    int32_t iters;          /* iterations done (A-pairs of the outer solver) */
+    int32_t status;         /* WMG_OK, WMG_NOT_CONVERGED or a negative error */
+    double rel_res;         /* last relative NE residual ||W^T(b-Wx)-lambda x|| / ||W^T b||
+                               as tracked by the solver's recurrence */
+} wmg_solve_info;
+
+typedef struct wmg_plan wmg_plan;
+
+/* Returns the message of the calling thread's last failing call (empty if
+ * none); copies at most len-1 characters into buf and NUL-terminates. */
+int32_t wmg_last_error(char *buf, size_t len);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t wmg_version(void);
+
+/* Plan creation: validates g and o, builds the angle table (equiangular
+ * angles are reduced to the first octant so that multiples of pi/2 and
+ * pi/4 are exact), allocates the plan's device workspace, and runs the setup
+ * on `stream`: the l1-Jacobi diagonal D~ = W^T(W 1) + lambda, the SIRT
+ * scalings R = 1/(W 1), C = 1/(W^T 1) (0 where a sum is 0), and the leaf
+ * Galerkin matrices D_k = Q_k^T (W^T W + lambda I) Q_k (Section 3.1.3: the
+ * coarsest-level subproblems), factorised by Cholesky and inverted in FP64.
+ * Synchronising (the leaf pivots are checked on the host).
+ * Errors: INVALID_ARG (bad sizes, n not divisible by 2^L, leaf larger than
+ * 256 unknowns), OOM, CUDA, LEAF_NOT_SPD (a leaf matrix is singular: use
+ * lambda > 0 or fewer levels). On error *out is NULL. */
+int32_t wmg_plan_create(const wmg_geom *g, const wmg_opts *o, void *stream, wmg_plan **out);
+
+/* Releases the plan and its device memory (after synchronising its stream).
+ * NULL is ignored. */
+int32_t wmg_plan_destroy(wmg_plan *plan);
+
+/* Sizes of the plan's problem: *N = n*n, *M = m*D (either pointer may be NULL). */
+int32_t wmg_plan_sizes(const wmg_plan *plan, int64_t *N, int64_t *M);
+
+/* Forward projection b = W x (Section 2.1, eq. sys), matrix-free: the
+ * intersection lengths are recomputed per ray. x: count images, b: count
+ * sinograms (outputs overwritten). Asynchronous. */
+int32_t wmg_project(wmg_plan *plan, int32_t count, const void *x, void *b, void *stream);
+
+/* Backprojection x = W^T b (the transpose of wmg_project, same weights).
+ * Asynchronous. */
+int32_t wmg_backproject(wmg_plan *plan, int32_t count, const void *b, void *x, void *stream);
+
+/* Preconditioner z = B s: one WMG cycle (Section 3.1) of the plan's options
+ * applied to the normal-equation residual s (count images). Asynchronous. */
+int32_t wmg_precond_apply(wmg_plan *plan, int32_t count, const void *s, void *z, void *stream);
+
+/* Haar wavelet-packet analysis to depth L (eq. 1of4-4of4 applied
+ * recursively): c (count x N) in leaf layout, leaf k = sum_d id_d 4^(L-d)
+ * (id_1 = first split, LL=0, LH=1, HL=2, HH=3) holding an (n/2^L)^2
+ * row-major grid. wmg_haar_synthesis is its transpose (= inverse).
+ * Asynchronous. */
+int32_t wmg_haar_analysis(wmg_plan *plan, int32_t count, const void *x, void *c, void *stream);
+int32_t wmg_haar_synthesis(wmg_plan *plan, int32_t count, const void *c, void *x, void *stream);
+
+/* Copies leaf k's inverse Galerkin matrix D_k^-1 ((n/2^L)^2 squared, plan
+ * precision, row-major) into the device buffer out. Asynchronous. */
+int32_t wmg_leaf_inverse(wmg_plan *plan, int64_t k, void *out, void *stream);
+
+/* Solve `count` problems of the plan's geometry: b (count sinograms) ->
+ * x (count images). x0 = 0 (x is output only). solver = WMG_SOLVER_*;
+ * preconditioned = 1 uses one WMG cycle per iteration (CGLS needs the
+ * SYMMETRIC or ADDITIVE cycle; GMRES any; SIRT ignores it). Stops a problem
+ * when its relative NE residual drops below rtol or after max_iter
+ * iterations; restart is the GMRES cycle length (<= 64). info: HOST array
+ * of count entries, or NULL. res_hist: optional HOST array of
+ * count*(max_iter+1) doubles receiving each problem's residual history
+ * (entry 0 = 1), or NULL. Synchronising: convergence is checked on the host
+ * every few iterations. Returns WMG_OK if every problem converged,
+ * WMG_NOT_CONVERGED if any hit max_iter, or the first negative status. */
+int32_t wmg_solve(wmg_plan *plan, int32_t solver, int32_t preconditioned, int32_t count,
+                  const void *b, void *x, int32_t max_iter, double rtol, int32_t restart,
+                  wmg_solve_info *info, double *res_hist, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WMGCT_H */

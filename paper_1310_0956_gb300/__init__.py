@@ -1,0 +1,256 @@
+"""Python binding of libwmgct, the GB300 library for wavelet-multigrid
+preconditioned Krylov reconstruction in 2D algebraic tomography
+(Cools et al., arXiv 1310.0956).
+
+The C ABI is declared in include/wmgct.h. This module only marshals
+arguments: every function below calls the C entry point of the same name,
+and every step of the computation runs in the library's CUDA kernels. There is
+no CPU fallback: if the shared library is missing or fails to load, the calls
+raise.
+
+`Plan` is a convenience wrapper taking torch CUDA tensors (device memory and
+streams are PyTorch's; the arithmetic is the library's).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import _build
+
+LIB_PATH = _build.LIB
+
+WMG_OK = 0
+WMG_NOT_CONVERGED = 1
+STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA_ERROR",
+                -4: "LEAF_NOT_SPD", -5: "BREAKDOWN", -6: "TIMEOUT", -7: "NAN", -8: "REJECTED"}
+
+PREC_F64, PREC_F32 = 0, 1
+CYCLE_ADDITIVE, CYCLE_HYBRID, CYCLE_SYMMETRIC = 0, 1, 2
+SOLVER_SIRT, SOLVER_CGLS, SOLVER_GMRES = 0, 1, 2
+
+
+class WmgError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class wmg_geom(C.Structure):
+    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("angles", C.c_void_p), ("D", C.c_int32),
+                ("det_spacing", C.c_double), ("det_offset", C.c_double)]
+
+
+class wmg_opts(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("nu1", C.c_int32), ("nu2", C.c_int32),
+                ("omega", C.c_double), ("lambda_", C.c_double), ("hybrid_depth", C.c_int32),
+                ("cycle", C.c_int32), ("precision", C.c_int32)]
+
+
+class wmg_solve_info(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("rel_res", C.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_vp, _i32, _i64, _dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+_SIGNATURES = {
+    "wmg_last_error": (_i32, [C.c_char_p, C.c_size_t]),
+    "wmg_version": (_i32, []),
+    "wmg_plan_create": (_i32, [C.POINTER(wmg_geom), C.POINTER(wmg_opts), _vp, C.POINTER(_vp)]),
+    "wmg_plan_destroy": (_i32, [_vp]),
+    "wmg_plan_sizes": (_i32, [_vp, C.POINTER(_i64), C.POINTER(_i64)]),
+    "wmg_project": (_i32, [_vp, _i32, _vp, _vp, _vp]),
+    "wmg_backproject": (_i32, [_vp, _i32, _vp, _vp, _vp]),
+    "wmg_precond_apply": (_i32, [_vp, _i32, _vp, _vp, _vp]),
+    "wmg_haar_analysis": (_i32, [_vp, _i32, _vp, _vp, _vp]),
+    "wmg_haar_synthesis": (_i32, [_vp, _i32, _vp, _vp, _vp]),
+    "wmg_leaf_inverse": (_i32, [_vp, _i64, _vp, _vp]),
+    "wmg_solve": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _i32, _dbl, _i32,
+                         C.POINTER(wmg_solve_info), C.POINTER(_dbl), _vp]),
+}
+
+
+def build(force: bool = False) -> str:
+    """Compile libwmgct.so for sm_103a (nvcc) in the package's lib/ folder."""
+    return _build.build(force=force)
+
+
+def lib():
+    """Load the shared library (building it first if it is out of date)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            handle = C.CDLL(path)
+            for name, (res, args) in _SIGNATURES.items():
+                fn = getattr(handle, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = handle
+        return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGNATURES)
+
+
+def last_error() -> str:
+    buf = C.create_string_buffer(1024)
+    lib().wmg_last_error(buf, len(buf))
+    return buf.value.decode(errors="replace")
+
+
+def _check(rc: int, allow_not_converged: bool = False) -> int:
+    if rc < 0 or (rc == WMG_NOT_CONVERGED and not allow_not_converged):
+        raise WmgError(rc, last_error())
+    return rc
+
+
+# ---- thin wrappers with the C names ----------------------------------------
+def wmg_plan_create(geom: wmg_geom, opts: wmg_opts, stream=None) -> C.c_void_p:
+    out = _vp()
+    _check(lib().wmg_plan_create(C.byref(geom), C.byref(opts), stream, C.byref(out)))
+    return out
+
+
+def wmg_plan_destroy(plan) -> None:
+    _check(lib().wmg_plan_destroy(plan))
+
+
+def wmg_plan_sizes(plan) -> tuple[int, int]:
+    N, M = _i64(), _i64()
+    _check(lib().wmg_plan_sizes(plan, C.byref(N), C.byref(M)))
+    return N.value, M.value
+
+
+def wmg_project(plan, count, x, b, stream=None):
+    _check(lib().wmg_project(plan, count, x, b, stream))
+
+
+def wmg_backproject(plan, count, b, x, stream=None):
+    _check(lib().wmg_backproject(plan, count, b, x, stream))
+
+
+def wmg_precond_apply(plan, count, s, z, stream=None):
+    _check(lib().wmg_precond_apply(plan, count, s, z, stream))
+
+
+def wmg_haar_analysis(plan, count, x, c, stream=None):
+    _check(lib().wmg_haar_analysis(plan, count, x, c, stream))
+
+
+def wmg_haar_synthesis(plan, count, c, x, stream=None):
+    _check(lib().wmg_haar_synthesis(plan, count, c, x, stream))
+
+
+def wmg_leaf_inverse(plan, k, out, stream=None):
+    _check(lib().wmg_leaf_inverse(plan, k, out, stream))
+
+
+def wmg_solve(plan, solver, preconditioned, count, b, x, max_iter, rtol, restart, info, res_hist,
+              stream=None) -> int:
+    return _check(lib().wmg_solve(plan, solver, preconditioned, count, b, x, max_iter, rtol, restart,
+                                  info, res_hist, stream), allow_not_converged=True)
+
+
+# ---- torch convenience wrapper ---------------------------------------------
+class Plan:
+    """A plan for one geometry; methods take torch CUDA tensors of the plan's
+    dtype (float64 for F64 plans, float32 for F32 plans) holding `count`
+    problems back to back, and run on torch's current stream."""
+
+    def __init__(self, n, m, D, levels=3, nu1=1, nu2=1, omega=1.0, lam=0.0, hybrid_depth=2,
+                 cycle=CYCLE_SYMMETRIC, precision=PREC_F64, angles=None, det_spacing=1.0,
+                 det_offset=0.0):
+        import torch
+        self._torch = torch
+        self._angles = None
+        ap = None
+        if angles is not None:
+            self._angles = (C.c_double * m)(*[float(a) for a in angles])
+            ap = C.cast(self._angles, C.c_void_p)
+        self.geom = wmg_geom(n, m, ap, D, det_spacing, det_offset)
+        self.opts = wmg_opts(levels, nu1, nu2, omega, lam, hybrid_depth, cycle, precision)
+        self.dtype = torch.float64 if precision == PREC_F64 else torch.float32
+        self.n, self.m, self.D = n, m, D
+        self.N, self.M = n * n, m * D
+        self.K = 4 ** (levels - 1)
+        self.P = (n >> (levels - 1)) ** 2
+        self.handle = wmg_plan_create(self.geom, self.opts, self._stream())
+
+    def _stream(self):
+        return C.c_void_p(self._torch.cuda.current_stream().cuda_stream)
+
+    def _arg(self, t, size):
+        torch = self._torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == self.dtype and t.is_contiguous()):
+            raise TypeError(f"expected a contiguous CUDA tensor of dtype {self.dtype}")
+        if t.numel() % size:
+            raise ValueError("tensor size is not a multiple of the problem size")
+        return C.c_void_p(t.data_ptr()), t.numel() // size
+
+    def close(self):
+        if getattr(self, "handle", None):
+            wmg_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def project(self, x, out=None):
+        xp, cnt = self._arg(x, self.N)
+        out = out if out is not None else self._torch.empty(cnt * self.M, dtype=self.dtype, device=x.device)
+        wmg_project(self.handle, cnt, xp, self._arg(out, self.M)[0], self._stream())
+        return out
+
+    def backproject(self, b, out=None):
+        bp, cnt = self._arg(b, self.M)
+        out = out if out is not None else self._torch.empty(cnt * self.N, dtype=self.dtype, device=b.device)
+        wmg_backproject(self.handle, cnt, bp, self._arg(out, self.N)[0], self._stream())
+        return out
+
+    def precond(self, s, out=None):
+        sp, cnt = self._arg(s, self.N)
+        out = out if out is not None else self._torch.empty_like(s)
+        wmg_precond_apply(self.handle, cnt, sp, self._arg(out, self.N)[0], self._stream())
+        return out
+
+    def haar_analysis(self, x, out=None):
+        xp, cnt = self._arg(x, self.N)
+        out = out if out is not None else self._torch.empty_like(x)
+        wmg_haar_analysis(self.handle, cnt, xp, self._arg(out, self.N)[0], self._stream())
+        return out
+
+    def haar_synthesis(self, c, out=None):
+        cp, cnt = self._arg(c, self.N)
+        out = out if out is not None else self._torch.empty_like(c)
+        wmg_haar_synthesis(self.handle, cnt, cp, self._arg(out, self.N)[0], self._stream())
+        return out
+
+    def leaf_inverse(self, k):
+        out = self._torch.empty(self.P * self.P, dtype=self.dtype, device="cuda")
+        wmg_leaf_inverse(self.handle, k, C.c_void_p(out.data_ptr()), self._stream())
+        return out.view(self.P, self.P)
+
+    def solve(self, b, solver=SOLVER_CGLS, preconditioned=True, max_iter=100, rtol=1e-4, restart=20,
+              out=None, history=False):
+        """Returns (x, info list, residual histories or None)."""
+        bp, cnt = self._arg(b, self.M)
+        out = out if out is not None else self._torch.empty(cnt * self.N, dtype=self.dtype, device=b.device)
+        info = (wmg_solve_info * cnt)()
+        hist = (C.c_double * (cnt * (max_iter + 1)))() if history else None
+        rc = wmg_solve(self.handle, solver, 1 if preconditioned else 0, cnt, bp, self._arg(out, self.N)[0],
+                       max_iter, rtol, restart, info, hist, self._stream())
+        infos = [(info[i].iters, info[i].status, info[i].rel_res) for i in range(cnt)]
+        hists = None
+        if history:
+            import numpy as np
+            h = np.frombuffer(hist, dtype=np.float64).reshape(cnt, max_iter + 1)
+            hists = [h[i, :infos[i][0] + 1].copy() for i in range(cnt)]
+        return out, infos, hists, rc

@@ -1,0 +1,1172 @@
+// engine.cu -- host engine behind the C ABI of include/wmgct.h: plan
+// creation and setup, work lists, the WMG cycle schedules and the Krylov
+// drivers. Every arithmetic step runs in the kernels of projector.cu,
+// haar.cu, setup.cu and krylov.cu; this file only orders launches.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "kern_common.cuh"
+#include "krylov.cuh"
+
+namespace wmg {
+
+// ---------------------------------------------------------------------------
+// errors, device properties
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+void set_error(const std::string &msg) { g_last_error = msg; }
+int32_t fail(int32_t code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int num_sms()
+{
+    static int v = [] {
+        int d = 0, n = 0;
+        cudaGetDevice(&d);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d);
+        return n > 0 ? n : 148;
+    }();
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// device buffers
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    // grow-only; contents are not preserved
+    bool ensure(size_t b)
+    {
+        if (b <= bytes && p) return true;
+        release();
+        if (b == 0) b = 16;
+        if (cudaMalloc(&p, b) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return false;
+        }
+        bytes = b;
+        return true;
+    }
+    template <class U> U *as() const { return static_cast<U *>(p); }
+};
+
+// Equiangular angle table: theta_a = pi*a/m reduced to the first octant so
+// that multiples of pi/2 are exactly 0 / +-1, odd multiples of pi/4 give
+// cos = sin = sqrt(1/2), and theta + pi/2 gets exactly (-sin, cos).
+static void angle_table(int m, const double *angles, std::vector<double2> &cs)
+{
+    cs.resize(m);
+    for (int a = 0; a < m; ++a) {
+        double c, s;
+        if (angles) {
+            c = std::cos(angles[a]);
+            s = std::sin(angles[a]);
+        } else {
+            const long twice = 2L * a, quad = twice / m, rem = twice - quad * m;
+            if (rem == 0) { c = 1.0; s = 0.0; }
+            else if (2 * rem == m) { c = std::sqrt(0.5); s = c; }
+            else if (2 * rem < m) {
+                const double phi = (M_PI / 2.0) * ((double)rem / (double)m);
+                c = std::cos(phi); s = std::sin(phi);
+            } else {
+                const double phi = (M_PI / 2.0) * ((double)(m - rem) / (double)m);
+                c = std::sin(phi); s = std::cos(phi);
+            }
+            if (quad & 1) { const double t = c; c = -s; s = t; }
+        }
+        cs[a] = make_double2(c, s);
+    }
+}
+
+struct TileList {
+    DevBuf tiles, tb, te;
+    int n = 0;
+    std::vector<int4> h;
+    bool upload(int nprob, cudaStream_t st)
+    {
+        n = (int)h.size();
+        std::vector<int> b(nprob, 0), e(nprob, 0);
+        for (int i = 0; i < n; ++i) {
+            const int p = h[i].x;
+            if (i == 0 || h[i - 1].x != p) b[p] = i;
+            e[p] = i + 1;
+        }
+        if (!tiles.ensure(std::max<size_t>(1, h.size()) * sizeof(int4)) ||
+            !tb.ensure(nprob * sizeof(int)) || !te.ensure(nprob * sizeof(int)))
+            return false;
+        if (n) cudaMemcpyAsync(tiles.p, h.data(), h.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(tb.p, b.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(te.p, e.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, st);
+        // host vectors must outlive the async copies: keep them (b, e are
+        // copied synchronously with respect to pageable memory)
+        return true;
+    }
+};
+
+// A set of (real or virtual) problems sharing one geometry, with its tiles.
+struct ProbSet {
+    int nprob = 0;
+    std::vector<ProbDev> h;
+    DevBuf d;
+    TileList proj, bp, haar, vimg, vsino;
+    int haar_smem = 0;
+};
+
+struct Node { int k0, k1; };
+
+}  // namespace wmg
+
+// ---------------------------------------------------------------------------
+// The plan
+// ---------------------------------------------------------------------------
+struct wmg_plan {
+    int prec = WMG_PREC_F64;
+    size_t esz = 8;
+    wmg::GeomDev g{};           // host copy (device pointers inside)
+    wmg_opts opts{};
+    int64_t N = 0, M = 0;
+    wmg::DevBuf d_geom, cs64, cs32, dinv, leafinv, sirtR, sirtC;
+    int cap = 0;                // problems the tables are built for
+    wmg::ProbSet real;
+    std::map<std::vector<int>, std::unique_ptr<wmg::ProbSet>> bands;   // band-update groups
+    std::map<std::vector<int>, std::unique_ptr<wmg::TileList>> leafsets;
+    std::map<std::vector<int>, std::unique_ptr<wmg::DevBuf>> segsets;
+    int band_cap = 0;
+    // FP64 pools (per problem: N or M elements)
+    wmg::DevBuf x, s, z, p, f, w, t, u, r;
+    // operator-precision pools
+    wmg::DevBuf p_op, pT_op, z_op, zT_op, r1, C, E, q, r_op, sinoS, b_op;
+    std::vector<std::unique_ptr<wmg::DevBuf>> csave, c2, e2;   // per hybrid depth
+    wmg::DevBuf band_img, band_imgT, band_img2, band_sino;
+    // scalars and partials
+    wmg::DevBuf S, part_a, part_b, part_c, lam, hist;
+    // GMRES
+    wmg::DevBuf V, H, gcs, gsn, gg, gy, h1, h2, jn, done;
+    int gm_restart = 0;
+};
+
+namespace wmg {
+
+// ---- tile lists ------------------------------------------------------------
+static void build_tiles(const wmg_plan *pl, ProbSet &ps)
+{
+    const GeomDev &g = pl->g;
+    ps.proj.h.clear(); ps.bp.h.clear(); ps.haar.h.clear(); ps.vimg.h.clear(); ps.vsino.h.clear();
+    // strip width: a whole number of blocks that divides the image side, at
+    // most max(B, 4096 / B) pixels wide
+    const int nb = g.n / g.B, wmax = std::max(1, std::max(g.B, 4096 / g.B) / g.B);
+    int wb = 1;
+    for (int d = 1; d <= std::min(nb, wmax); ++d)
+        if (nb % d == 0) wb = d;
+    const int W = wb * g.B;
+    ps.haar_smem = g.B * (W + 1);
+    for (int q = 0; q < ps.nprob; ++q) {
+        for (int a = 0; a < g.m; ++a)
+            for (int k0 = 0; k0 < g.D; k0 += 32) ps.proj.h.push_back(make_int4(q, a, k0, 0));
+        for (int iy = 0; iy < g.n; iy += 32)
+            for (int ix = 0; ix < g.n; ix += 32) ps.bp.h.push_back(make_int4(q, iy, ix, 0));
+        for (int cy = 0; cy < g.nc; ++cy)
+            for (int x0 = 0; x0 < g.n; x0 += W) ps.haar.h.push_back(make_int4(q, cy * g.B, x0, W));
+        for (int64_t s0 = 0; s0 < pl->N; s0 += 8192)
+            ps.vimg.h.push_back(make_int4(q, (int)s0, (int)std::min<int64_t>(8192, pl->N - s0), 0));
+        for (int64_t s0 = 0; s0 < pl->M; s0 += 8192)
+            ps.vsino.h.push_back(make_int4(q, (int)s0, (int)std::min<int64_t>(8192, pl->M - s0), 0));
+    }
+}
+
+static bool upload_set(ProbSet &ps, cudaStream_t st)
+{
+    if (!ps.d.ensure(std::max<size_t>(1, ps.h.size()) * sizeof(ProbDev))) return false;
+    cudaMemcpyAsync(ps.d.p, ps.h.data(), ps.h.size() * sizeof(ProbDev), cudaMemcpyHostToDevice, st);
+    return ps.proj.upload(ps.nprob, st) && ps.bp.upload(ps.nprob, st) && ps.haar.upload(ps.nprob, st) &&
+           ps.vimg.upload(ps.nprob, st) && ps.vsino.upload(ps.nprob, st);
+}
+
+// Tables for `count` real problems: problem q's vectors at q*N / q*M.
+static int32_t ensure_count(wmg_plan *pl, int count, cudaStream_t st)
+{
+    if (count == pl->cap) return WMG_OK;
+    ProbSet &ps = pl->real;
+    ps.nprob = count;
+    ps.h.assign(count, ProbDev{});
+    for (int q = 0; q < count; ++q) {
+        ProbDev &d = ps.h[q];
+        d.geom = 0; d.slot = q;
+        d.img = (int64_t)q * pl->N; d.sino = (int64_t)q * pl->M; d.coef = (int64_t)q * pl->N;
+        d.kin0 = 0; d.kin1 = pl->g.K; d.kout0 = 0; d.kout1 = pl->g.K;
+    }
+    build_tiles(pl, ps);
+    if (!upload_set(ps, st)) return fail(WMG_ERR_OOM, "work-list allocation failed");
+    pl->bands.clear();
+    pl->leafsets.clear();
+    pl->segsets.clear();
+    pl->cap = count;
+    // per-problem scalars
+    if (!pl->S.ensure((size_t)count * NSCAL * sizeof(double)) ||
+        !pl->lam.ensure((size_t)count * sizeof(double)))
+        return fail(WMG_ERR_OOM, "scalar allocation failed");
+    std::vector<double> lam(count, pl->g.lambda);
+    cudaMemcpyAsync(pl->lam.p, lam.data(), count * sizeof(double), cudaMemcpyHostToDevice, st);
+    cudaStreamSynchronize(st);
+    return WMG_OK;
+}
+
+static bool ensure_pool(DevBuf &b, int64_t elems, size_t esz) { return b.ensure((size_t)elems * esz); }
+
+static bool ensure_partials(wmg_plan *pl, size_t per_tile_max)
+{
+    const ProbSet &ps = pl->real;
+    size_t n = std::max({(size_t)ps.proj.h.size(), (size_t)ps.bp.h.size(), (size_t)ps.vimg.h.size(),
+                         (size_t)ps.vsino.h.size(), (size_t)1});
+    return pl->part_a.ensure(n * per_tile_max * sizeof(double)) &&
+           pl->part_b.ensure(n * sizeof(double)) && pl->part_c.ensure(n * sizeof(double));
+}
+
+// ---------------------------------------------------------------------------
+// Operator steps
+// ---------------------------------------------------------------------------
+template <class T>
+static void project(wmg_plan *pl, const ProbSet &ps, const void *img, const void *imgT, void *sino,
+                    double *part, const double *S, cudaStream_t st)
+{
+    PjArgs a{img, imgT, sino, part, S};
+    launch_project<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.proj.tiles.as<int4>(),
+                      ps.proj.n, a, st);
+}
+
+template <class T>
+static void backproject(wmg_plan *pl, const ProbSet &ps, BpArgs a, cudaStream_t st)
+{
+    launch_backproject<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.bp.tiles.as<int4>(),
+                          ps.bp.n, a, st);
+}
+
+static BpArgs bp_args(int epi, const void *sino, const double *S)
+{
+    BpArgs a{};
+    a.epi = epi;
+    a.sino = sino;
+    a.S = S;
+    return a;
+}
+
+template <class T>
+static void img_op(wmg_plan *pl, int op, ImgArgs a, cudaStream_t st)
+{
+    const ProbSet &ps = pl->real;
+    launch_img<T>(op, pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.bp.tiles.as<int4>(), ps.bp.n, a, st);
+}
+
+template <class T>
+static void vec_op(wmg_plan *pl, int op, bool sino, VecArgs a, cudaStream_t st)
+{
+    const ProbSet &ps = pl->real;
+    const TileList &tl = sino ? ps.vsino : ps.vimg;
+    a.G = pl->d_geom.as<GeomDev>();
+    launch_vec<T>(op, ps.d.as<ProbDev>(), tl.tiles.as<int4>(), tl.n, a, st);
+}
+
+static void finalize(wmg_plan *pl, int op, const TileList &ta, const double *pa, int nsum,
+                     const TileList *tb, const double *pb, int precond, double *hist, int hist_ld,
+                     cudaStream_t st, int store_slot = 0, double *store_vec = nullptr, int store_ld = 0)
+{
+    FinArgs f{};
+    f.op = op;
+    f.nprob = pl->cap;
+    f.precond = precond;
+    f.part_a = pa;
+    f.tb_a = ta.tb.as<int>();
+    f.te_a = ta.te.as<int>();
+    f.ld_a = std::max(1, nsum);
+    f.nsum_a = std::max(1, nsum);
+    f.part_b = pb;
+    f.tb_b = tb ? tb->tb.as<int>() : nullptr;
+    f.te_b = tb ? tb->te.as<int>() : nullptr;
+    f.S = pl->S.as<double>();
+    f.lambda = pl->lam.as<double>();
+    f.hist = hist;
+    f.hist_ld = hist_ld;
+    f.store_slot = store_slot;
+    f.store_vec = store_vec;
+    f.store_ld = store_ld;
+    launch_finalize(f, st);
+}
+
+// Band-update group tables: virtual problem v = q * G + i for node i.
+static ProbSet *band_set(wmg_plan *pl, const std::vector<Node> &nodes, bool full_in, cudaStream_t st)
+{
+    std::vector<int> key;
+    key.push_back(full_in ? 1 : 0);
+    for (const Node &n : nodes) { key.push_back(n.k0); key.push_back(n.k1); }
+    auto it = pl->bands.find(key);
+    if (it != pl->bands.end()) return it->second.get();
+    auto ps = std::make_unique<ProbSet>();
+    const int G = (int)nodes.size(), B = pl->cap;
+    ps->nprob = B * G;
+    ps->h.resize(ps->nprob);
+    for (int q = 0; q < B; ++q)
+        for (int i = 0; i < G; ++i) {
+            ProbDev &d = ps->h[q * G + i];
+            const int v = q * G + i;
+            const int qq = (nodes[i].k1 - nodes[i].k0) / 4;
+            d.geom = 0; d.slot = q;
+            d.img = (int64_t)v * pl->N; d.sino = (int64_t)v * pl->M; d.coef = (int64_t)q * pl->N;
+            if (full_in) {          // symmetric closing step: all of the node in, LL child out
+                d.kin0 = nodes[i].k0; d.kin1 = nodes[i].k1;
+                d.kout0 = nodes[i].k0; d.kout1 = nodes[i].k0 + qq;
+            } else {                // hybrid step: LL child in, the three other children out
+                d.kin0 = nodes[i].k0; d.kin1 = nodes[i].k0 + qq;
+                d.kout0 = nodes[i].k0 + qq; d.kout1 = nodes[i].k1;
+            }
+        }
+    build_tiles(pl, *ps);
+    if (!upload_set(*ps, st)) return nullptr;
+    ProbSet *raw = ps.get();
+    pl->bands[key] = std::move(ps);
+    return raw;
+}
+
+static TileList *leaf_tiles(wmg_plan *pl, const std::vector<Node> &nodes, cudaStream_t st)
+{
+    std::vector<int> key;
+    for (const Node &n : nodes) { key.push_back(n.k0); key.push_back(n.k1); }
+    auto it = pl->leafsets.find(key);
+    if (it != pl->leafsets.end()) return it->second.get();
+    auto tl = std::make_unique<TileList>();
+    for (const Node &n : nodes)
+        for (int k = n.k0; k < n.k1; ++k) tl->h.push_back(make_int4(0, k, pl->cap, 0));
+    // leaf tiles are not per problem: upload with a one-entry range table
+    if (!tl->upload(1, st)) return nullptr;
+    TileList *raw = tl.get();
+    pl->leafsets[key] = std::move(tl);
+    return raw;
+}
+
+template <class T>
+__global__ void k_coef_add(T *E, const T *E2, const int2 *segs, int nseg, int64_t N, int nprob)
+{
+    // segs: element ranges inside one problem's coefficient vector
+    for (int q = 0; q < nprob; ++q)
+        for (int sgi = 0; sgi < nseg; ++sgi) {
+            const int2 sg = segs[sgi];
+            for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < sg.y; i += gridDim.x * blockDim.x)
+                E[(int64_t)q * N + sg.x + i] += E2[(int64_t)q * N + sg.x + i];
+        }
+}
+
+// One band-local residual update for a group of nodes (hybrid cycle): for
+// every node, C[out range] -= Q_out^T (W^T W + lambda) Q_in E[in range].
+template <class T>
+static int32_t band_update(wmg_plan *pl, const std::vector<Node> &nodes, bool full_in, DevBuf &Cb,
+                           DevBuf &Eb, cudaStream_t st)
+{
+    ProbSet *bs = band_set(pl, nodes, full_in, st);
+    if (!bs) return fail(WMG_ERR_OOM, "band tables");
+    const int64_t V = bs->nprob;
+    if (!ensure_pool(pl->band_img, V * pl->N, pl->esz) || !ensure_pool(pl->band_imgT, V * pl->N, pl->esz) ||
+        !ensure_pool(pl->band_img2, V * pl->N, pl->esz) || !ensure_pool(pl->band_sino, V * pl->M, pl->esz))
+        return fail(WMG_ERR_OOM, "band pools");
+    const GeomDev *G = pl->d_geom.as<GeomDev>();
+    const double *S = pl->S.as<double>();
+    HaarArgs hs{};
+    hs.mode = HS_STORE_MASKED;
+    hs.in = Eb.p;
+    hs.out = pl->band_img.p;
+    hs.outT = pl->band_imgT.p;
+    hs.S = S;
+    launch_haar_synthesis<T>(G, bs->d.as<ProbDev>(), bs->haar.tiles.as<int4>(), bs->haar.n,
+                             bs->haar_smem, hs, st);
+    project<T>(pl, *bs, pl->band_img.p, pl->band_imgT.p, pl->band_sino.p, nullptr, S, st);
+    BpArgs a = bp_args(BP_APPLY_A, pl->band_sino.p, S);
+    a.v_op = pl->band_img.p;
+    a.out_op = pl->band_img2.p;
+    backproject<T>(pl, *bs, a, st);
+    HaarArgs ha{};
+    ha.mode = HA_SUB_MASKED;
+    ha.in = pl->band_img2.p;
+    ha.out = Cb.p;
+    ha.S = S;
+    launch_haar_analysis<T>(G, bs->d.as<ProbDev>(), bs->haar.tiles.as<int4>(), bs->haar.n,
+                            bs->haar_smem, ha, st);
+    return WMG_OK;
+}
+
+// Coarse correction of the WMG cycle for a group of nodes at depth d
+// (Section 3.1.2 recursion, siblings processed together): leaf solves at
+// depth >= hybrid depth, otherwise LL child first, one band-local residual
+// update, the other three children, and (symmetric cycle) the LL child again
+// from the residual of the whole node correction.
+template <class T>
+static int32_t coarse(wmg_plan *pl, int d, const std::vector<Node> &nodes, DevBuf &Cb, DevBuf &Eb,
+                      cudaStream_t st)
+{
+    const wmg_opts &o = pl->opts;
+    const int hd = (o.cycle == WMG_CYCLE_ADDITIVE) ? 0 : std::min(o.hybrid_depth, pl->g.L);
+    if (d >= hd) {
+        TileList *lt = leaf_tiles(pl, nodes, st);
+        if (!lt) return fail(WMG_ERR_OOM, "leaf tables");
+        launch_leaf_apply<T>(pl->d_geom.as<GeomDev>(), pl->real.d.as<ProbDev>(), lt->tiles.as<int4>(),
+                             lt->n, Cb.p, Eb.p, 0, pl->S.as<double>(), st);
+        return WMG_OK;
+    }
+    std::vector<Node> lls, rests;
+    for (const Node &nd : nodes) {
+        const int qq = (nd.k1 - nd.k0) / 4;
+        lls.push_back({nd.k0, nd.k0 + qq});
+        for (int c = 1; c < 4; ++c) rests.push_back({nd.k0 + c * qq, nd.k0 + (c + 1) * qq});
+    }
+    const bool sym = o.cycle == WMG_CYCLE_SYMMETRIC;
+    const size_t cbytes = (size_t)pl->cap * pl->N * pl->esz;
+    if (sym) cudaMemcpyAsync(pl->csave[d]->p, Cb.p, cbytes, cudaMemcpyDeviceToDevice, st);
+    int32_t rc = coarse<T>(pl, d + 1, lls, Cb, Eb, st);
+    if (rc) return rc;
+    if ((rc = band_update<T>(pl, nodes, false, Cb, Eb, st))) return rc;
+    if ((rc = coarse<T>(pl, d + 1, rests, Cb, Eb, st))) return rc;
+    if (sym) {
+        DevBuf &C2 = *pl->c2[d], &E2 = *pl->e2[d];
+        cudaMemcpyAsync(C2.p, pl->csave[d]->p, cbytes, cudaMemcpyDeviceToDevice, st);
+        if ((rc = band_update<T>(pl, nodes, true, C2, Eb, st))) return rc;
+        if ((rc = coarse<T>(pl, d + 1, lls, C2, E2, st))) return rc;
+        std::vector<int> key;
+        std::vector<int2> segs;
+        for (const Node &n : lls) {
+            key.push_back(n.k0); key.push_back(n.k1);
+            segs.push_back(make_int2((int)((int64_t)n.k0 * pl->g.P), (int)((int64_t)(n.k1 - n.k0) * pl->g.P)));
+        }
+        auto it = pl->segsets.find(key);
+        if (it == pl->segsets.end()) {
+            auto db = std::make_unique<DevBuf>();
+            if (!db->ensure(segs.size() * sizeof(int2))) return fail(WMG_ERR_OOM, "segments");
+            cudaMemcpy(db->p, segs.data(), segs.size() * sizeof(int2), cudaMemcpyHostToDevice);
+            it = pl->segsets.emplace(key, std::move(db)).first;
+        }
+        k_coef_add<T><<<num_sms() * 4, 256, 0, st>>>(Eb.as<T>(), E2.as<T>(), it->second->as<int2>(),
+                                                      (int)segs.size(), pl->N, pl->cap);
+    }
+    return WMG_OK;
+}
+
+static int32_t ensure_wmg_pools(wmg_plan *pl)
+{
+    const int64_t nN = (int64_t)pl->cap * pl->N, nM = (int64_t)pl->cap * pl->M;
+    const size_t e = pl->esz;
+    if (!ensure_pool(pl->z, nN, 8) || !ensure_pool(pl->s, nN, 8) || !ensure_pool(pl->z_op, nN, e) ||
+        !ensure_pool(pl->zT_op, nN, e) || !ensure_pool(pl->r1, nN, e) || !ensure_pool(pl->C, nN, e) ||
+        !ensure_pool(pl->E, nN, e) || !ensure_pool(pl->sinoS, nM, e))
+        return fail(WMG_ERR_OOM, "preconditioner pools");
+    const int L = pl->g.L;
+    while ((int)pl->csave.size() < L) {
+        pl->csave.push_back(std::make_unique<DevBuf>());
+        pl->c2.push_back(std::make_unique<DevBuf>());
+        pl->e2.push_back(std::make_unique<DevBuf>());
+    }
+    if (pl->opts.cycle == WMG_CYCLE_SYMMETRIC)
+        for (int d = 0; d < std::min(pl->opts.hybrid_depth, L); ++d)
+            if (!ensure_pool(*pl->csave[d], nN, e) || !ensure_pool(*pl->c2[d], nN, e) ||
+                !ensure_pool(*pl->e2[d], nN, e))
+                return fail(WMG_ERR_OOM, "symmetric-cycle pools");
+    return WMG_OK;
+}
+
+// z = B s (FP64 pools s, z). If `first_done`, z already holds omega D~^-1 s
+// and z_op / zT_op its copies. If `copies`, z_op / zT_op hold z at the end.
+// If `sz_part`, the tile partials of s.z over the backprojection tiles are
+// left in part_b (returns true in *have_sz).
+template <class T>
+static int32_t wmg_apply(wmg_plan *pl, double *s, double *z, bool first_done, bool copies, bool sz_part,
+                         bool *have_sz, cudaStream_t st)
+{
+    const wmg_opts &o = pl->opts;
+    const ProbSet &ps = pl->real;
+    const double *S = pl->S.as<double>();
+    *have_sz = false;
+    if (o.nu1 >= 1) {
+        if (!first_done) {
+            ImgArgs ia{};
+            ia.z = z; ia.s = s; ia.copy_op = pl->z_op.p; ia.copyT_op = pl->zT_op.p; ia.S = S;
+            img_op<T>(pl, IMG_FIRST_SWEEP, ia, st);
+        }
+        for (int it = 1; it < o.nu1; ++it) {
+            project<T>(pl, ps, pl->z_op.p, pl->zT_op.p, pl->sinoS.p, nullptr, S, st);
+            BpArgs a = bp_args(BP_POST, pl->sinoS.p, S);
+            a.s = s; a.z = z; a.copy_op = pl->z_op.p; a.copyT_op = pl->zT_op.p;
+            backproject<T>(pl, ps, a, st);
+        }
+        project<T>(pl, ps, pl->z_op.p, pl->zT_op.p, pl->sinoS.p, nullptr, S, st);
+        BpArgs a = bp_args(BP_RESID, pl->sinoS.p, S);
+        a.s = s; a.z = z; a.out_op = pl->r1.p;
+        backproject<T>(pl, ps, a, st);
+    } else {
+        ImgArgs ia{};
+        ia.z = z; ia.s = s; ia.r1 = pl->r1.p; ia.S = S;
+        img_op<T>(pl, IMG_ZERO_RESID, ia, st);
+    }
+    const GeomDev *G = pl->d_geom.as<GeomDev>();
+    HaarArgs ha{};
+    ha.mode = HA_STORE; ha.in = pl->r1.p; ha.out = pl->C.p; ha.S = S;
+    launch_haar_analysis<T>(G, ps.d.as<ProbDev>(), ps.haar.tiles.as<int4>(), ps.haar.n, ps.haar_smem, ha, st);
+    std::vector<Node> root{{0, pl->g.K}};
+    int32_t rc = coarse<T>(pl, 0, root, pl->C, pl->E, st);
+    if (rc) return rc;
+    const bool need_copies_after_syn = copies || o.nu2 > 0;
+    HaarArgs hs{};
+    hs.mode = HS_CORRECT; hs.in = pl->E.p; hs.z = z; hs.S = S;
+    hs.out = need_copies_after_syn ? pl->z_op.p : nullptr;
+    hs.outT = need_copies_after_syn ? pl->zT_op.p : nullptr;
+    launch_haar_synthesis<T>(G, ps.d.as<ProbDev>(), ps.haar.tiles.as<int4>(), ps.haar.n, ps.haar_smem, hs, st);
+    for (int it = 0; it < o.nu2; ++it) {
+        const bool last = it == o.nu2 - 1;
+        project<T>(pl, ps, pl->z_op.p, pl->zT_op.p, pl->sinoS.p, nullptr, S, st);
+        BpArgs a = bp_args(BP_POST, pl->sinoS.p, S);
+        a.s = s; a.z = z;
+        if (!last || copies) { a.copy_op = pl->z_op.p; a.copyT_op = pl->zT_op.p; }
+        if (last && sz_part) { a.part = pl->part_b.as<double>(); *have_sz = true; }
+        backproject<T>(pl, ps, a, st);
+    }
+    return WMG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// plan creation
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void k_fill(T *p, int64_t n, T v)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+// out = 1 / (in + add) where positive, else 0
+template <class T>
+__global__ void k_recip(const T *in, T *out, int64_t n, double add)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)in[i] + add;
+        out[i] = v > 0.0 ? (T)(1.0 / v) : T(0);
+    }
+}
+
+template <class T>
+static int32_t setup_geometry(wmg_plan *pl, cudaStream_t st)
+{
+    const int64_t N = pl->N, M = pl->M;
+    DevBuf ones_img, ones_sino, tmp_img, tmp_sino;
+    if (!ones_img.ensure(N * sizeof(T)) || !ones_sino.ensure(M * sizeof(T)) ||
+        !tmp_img.ensure(N * sizeof(T)) || !tmp_sino.ensure(M * sizeof(T)) ||
+        !pl->dinv.ensure(N * sizeof(T)) || !pl->sirtR.ensure(M * sizeof(T)) || !pl->sirtC.ensure(N * sizeof(T)))
+        return fail(WMG_ERR_OOM, "setup allocation failed");
+    k_fill<T><<<num_sms() * 4, 256, 0, st>>>(ones_img.as<T>(), N, T(1));
+    k_fill<T><<<num_sms() * 4, 256, 0, st>>>(ones_sino.as<T>(), M, T(1));
+    const ProbSet &ps = pl->real;
+    // W 1 (row sums) -> R; W^T (W 1) -> D~; W^T 1 (column sums) -> C
+    project<T>(pl, ps, ones_img.p, ones_img.p, tmp_sino.p, nullptr, nullptr, st);
+    k_recip<T><<<num_sms() * 4, 256, 0, st>>>(tmp_sino.as<T>(), pl->sirtR.as<T>(), M, 0.0);
+    BpArgs a = bp_args(BP_STORE, tmp_sino.p, nullptr);
+    a.out_op = tmp_img.p;
+    backproject<T>(pl, ps, a, st);
+    k_recip<T><<<num_sms() * 4, 256, 0, st>>>(tmp_img.as<T>(), pl->dinv.as<T>(), N, pl->g.lambda);
+    a = bp_args(BP_STORE, ones_sino.p, nullptr);
+    a.out_op = tmp_img.p;
+    backproject<T>(pl, ps, a, st);
+    k_recip<T><<<num_sms() * 4, 256, 0, st>>>(tmp_img.as<T>(), pl->sirtC.as<T>(), N, 0.0);
+    WMG_CUDA(cudaStreamSynchronize(st));
+    WMG_CUDA(cudaGetLastError());
+    pl->g.dinv = pl->dinv.p;
+    pl->g.sirtR = pl->sirtR.p;
+    pl->g.sirtC = pl->sirtC.p;
+    if (!pl->leafinv.ensure((size_t)pl->g.K * pl->g.P * pl->g.P * sizeof(T)))
+        return fail(WMG_ERR_OOM, "leaf inverse allocation failed");
+    pl->g.leafinv = pl->leafinv.p;
+    WMG_CUDA(cudaMemcpyAsync(pl->d_geom.p, &pl->g, sizeof(GeomDev), cudaMemcpyHostToDevice, st));
+    int32_t rc = build_leaf_inverses<T>(pl->g, pl->d_geom.as<GeomDev>(), pl->leafinv.p, st);
+    if (rc) return rc;
+    WMG_CUDA(cudaGetLastError());
+    return WMG_OK;
+}
+
+}  // namespace wmg
+
+using namespace wmg;
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" int32_t wmg_last_error(char *buf, size_t len)
+{
+    if (!buf || len == 0) return WMG_ERR_INVALID_ARG;
+    const size_t n = std::min(len - 1, g_last_error.size());
+    std::memcpy(buf, g_last_error.data(), n);
+    buf[n] = 0;
+    return WMG_OK;
+}
+
+extern "C" int32_t wmg_version(void) { return 100; }
+
+extern "C" int32_t wmg_plan_create(const wmg_geom *g, const wmg_opts *o, void *stream, wmg_plan **out)
+{
+    if (!out) return fail(WMG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!g || !o) return fail(WMG_ERR_INVALID_ARG, "geometry or options NULL");
+    if (g->n < 1 || g->m < 1 || g->D < 1) return fail(WMG_ERR_INVALID_ARG, "n, m and D must be >= 1");
+    if (o->levels < 1 || o->levels > 12) return fail(WMG_ERR_INVALID_ARG, "levels must be in [1, 12]");
+    const int L = o->levels - 1;
+    if (g->n % (1 << L) != 0) return fail(WMG_ERR_INVALID_ARG, "n must be divisible by 2^(levels-1)");
+    const int nc = g->n >> L;
+    if (nc * nc > 256) return fail(WMG_ERR_INVALID_ARG, "leaf side n/2^(levels-1) must be <= 16");
+    if ((1 << L) > 128) return fail(WMG_ERR_INVALID_ARG, "block side 2^(levels-1) must be <= 128");
+    if (o->nu1 < 0 || o->nu2 < 0 || o->lambda < 0 || o->hybrid_depth < 0 ||
+        o->cycle < WMG_CYCLE_ADDITIVE || o->cycle > WMG_CYCLE_SYMMETRIC ||
+        (o->precision != WMG_PREC_F64 && o->precision != WMG_PREC_F32))
+        return fail(WMG_ERR_INVALID_ARG, "invalid options");
+    if ((int64_t)g->n * g->n > (int64_t)1 << 30 || (int64_t)g->m * g->D > (int64_t)1 << 31)
+        return fail(WMG_ERR_INVALID_ARG, "problem too large");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    auto pl = std::make_unique<wmg_plan>();
+    pl->prec = o->precision;
+    pl->esz = o->precision == WMG_PREC_F64 ? 8 : 4;
+    pl->opts = *o;
+    if (pl->opts.omega <= 0) pl->opts.omega = 1.0;
+    pl->N = (int64_t)g->n * g->n;
+    pl->M = (int64_t)g->m * g->D;
+    GeomDev &gd = pl->g;
+    gd.n = g->n; gd.m = g->m; gd.D = g->D; gd.L = L;
+    gd.nc = nc; gd.P = nc * nc; gd.K = 1 << (2 * L); gd.B = 1 << L;
+    gd.h = 1.0 / g->n;
+    gd.dt = g->det_spacing > 0 ? g->det_spacing : 1.0;
+    gd.t0 = g->det_offset;
+    gd.lambda = o->lambda;
+    gd.omega = pl->opts.omega;
+    std::vector<double2> cs;
+    angle_table(g->m, g->angles, cs);
+    std::vector<float2> cs32(g->m);
+    for (int a = 0; a < g->m; ++a) cs32[a] = make_float2((float)cs[a].x, (float)cs[a].y);
+    if (!pl->cs64.ensure(g->m * sizeof(double2)) || !pl->cs32.ensure(g->m * sizeof(float2)) ||
+        !pl->d_geom.ensure(sizeof(GeomDev)))
+        return fail(WMG_ERR_OOM, "plan allocation failed");
+    WMG_CUDA(cudaMemcpyAsync(pl->cs64.p, cs.data(), g->m * sizeof(double2), cudaMemcpyHostToDevice, st));
+    WMG_CUDA(cudaMemcpyAsync(pl->cs32.p, cs32.data(), g->m * sizeof(float2), cudaMemcpyHostToDevice, st));
+    gd.cs64 = pl->cs64.as<double2>();
+    gd.cs32 = pl->cs32.as<float2>();
+    WMG_CUDA(cudaMemcpyAsync(pl->d_geom.p, &gd, sizeof(GeomDev), cudaMemcpyHostToDevice, st));
+    int32_t rc = ensure_count(pl.get(), 1, st);
+    if (rc) return rc;
+    rc = pl->prec == WMG_PREC_F64 ? setup_geometry<double>(pl.get(), st) : setup_geometry<float>(pl.get(), st);
+    if (rc) return rc;
+    WMG_CUDA(cudaStreamSynchronize(st));
+    *out = pl.release();
+    return WMG_OK;
+}
+
+extern "C" int32_t wmg_plan_destroy(wmg_plan *plan)
+{
+    if (!plan) return WMG_OK;
+    cudaDeviceSynchronize();
+    delete plan;
+    return WMG_OK;
+}
+
+extern "C" int32_t wmg_plan_sizes(const wmg_plan *plan, int64_t *N, int64_t *M)
+{
+    if (!plan) return fail(WMG_ERR_INVALID_ARG, "plan is NULL");
+    if (N) *N = plan->N;
+    if (M) *M = plan->M;
+    return WMG_OK;
+}
+
+#define WMG_DISPATCH(pl, fn, ...) \
+    ((pl)->prec == WMG_PREC_F64 ? fn<double>(__VA_ARGS__) : fn<float>(__VA_ARGS__))
+
+template <class T>
+static int32_t do_project(wmg_plan *pl, int count, const void *x, void *b, cudaStream_t st)
+{
+    if (!ensure_pool(pl->pT_op, (int64_t)count * pl->N, pl->esz)) return fail(WMG_ERR_OOM, "workspace");
+    const ProbSet &ps = pl->real;
+    launch_transpose<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.bp.tiles.as<int4>(), ps.bp.n, x,
+                        pl->pT_op.p, st);
+    project<T>(pl, ps, x, pl->pT_op.p, b, nullptr, nullptr, st);
+    WMG_CUDA(cudaGetLastError());
+    return WMG_OK;
+}
+
+extern "C" int32_t wmg_project(wmg_plan *pl, int32_t count, const void *x, void *b, void *stream)
+{
+    if (!pl || !x || !b || count < 1) return fail(WMG_ERR_INVALID_ARG, "wmg_project: bad arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int32_t rc = ensure_count(pl, count, st);
+    if (rc) return rc;
+    return WMG_DISPATCH(pl, do_project, pl, count, x, b, st);
+}
+
+template <class T>
+static int32_t do_backproject(wmg_plan *pl, const void *b, void *x, cudaStream_t st)
+{
+    BpArgs a = bp_args(BP_STORE, b, nullptr);
+    a.out_op = x;
+    backproject<T>(pl, pl->real, a, st);
+    WMG_CUDA(cudaGetLastError());
+    return WMG_OK;
+}
+
+extern "C" int32_t wmg_backproject(wmg_plan *pl, int32_t count, const void *b, void *x, void *stream)
+{
+    if (!pl || !x || !b || count < 1) return fail(WMG_ERR_INVALID_ARG, "wmg_backproject: bad arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int32_t rc = ensure_count(pl, count, st);
+    if (rc) return rc;
+    return WMG_DISPATCH(pl, do_backproject, pl, b, x, st);
+}
+
+template <class T>
+static int32_t do_haar(wmg_plan *pl, bool analysis, const void *in, void *out, cudaStream_t st)
+{
+    const ProbSet &ps = pl->real;
+    const GeomDev *G = pl->d_geom.as<GeomDev>();
+    HaarArgs a{};
+    a.in = in;
+    a.out = out;
+    if (analysis) {
+        a.mode = HA_STORE;
+        launch_haar_analysis<T>(G, ps.d.as<ProbDev>(), ps.haar.tiles.as<int4>(), ps.haar.n, ps.haar_smem, a, st);
+    } else {
+        a.mode = HS_STORE;
+        launch_haar_synthesis<T>(G, ps.d.as<ProbDev>(), ps.haar.tiles.as<int4>(), ps.haar.n, ps.haar_smem, a, st);
+    }
+    WMG_CUDA(cudaGetLastError());
+    return WMG_OK;
+}
+
+extern "C" int32_t wmg_haar_analysis(wmg_plan *pl, int32_t count, const void *x, void *c, void *stream)
+{
+    if (!pl || !x || !c || count < 1) return fail(WMG_ERR_INVALID_ARG, "wmg_haar_analysis: bad arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int32_t rc = ensure_count(pl, count, st);
+    if (rc) return rc;
+    return WMG_DISPATCH(pl, do_haar, pl, true, x, c, st);
+}
+
+extern "C" int32_t wmg_haar_synthesis(wmg_plan *pl, int32_t count, const void *c, void *x, void *stream)
+{
+    if (!pl || !x || !c || count < 1) return fail(WMG_ERR_INVALID_ARG, "wmg_haar_synthesis: bad arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int32_t rc = ensure_count(pl, count, st);
+    if (rc) return rc;
+    return WMG_DISPATCH(pl, do_haar, pl, false, c, x, st);
+}
+
+extern "C" int32_t wmg_leaf_inverse(wmg_plan *pl, int64_t k, void *out, void *stream)
+{
+    if (!pl || !out || k < 0 || k >= pl->g.K) return fail(WMG_ERR_INVALID_ARG, "wmg_leaf_inverse: bad arguments");
+    const size_t bytes = (size_t)pl->g.P * pl->g.P * pl->esz;
+    WMG_CUDA(cudaMemcpyAsync(out, static_cast<char *>(pl->leafinv.p) + k * bytes, bytes,
+                             cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
+    return WMG_OK;
+}
+
+static void init_scalars(wmg_plan *pl, int count, double rtol, int max_iter, cudaStream_t st)
+{
+    std::vector<double> S((size_t)count * NSCAL, 0.0);
+    for (int q = 0; q < count; ++q) {
+        double *s = &S[(size_t)q * NSCAL];
+        s[SC_ACTIVE] = 1.0;
+        s[SC_STATUS] = WMG_NOT_CONVERGED;
+        s[SC_RTOL] = rtol;
+        s[SC_MAXIT] = max_iter;
+    }
+    cudaMemcpyAsync(pl->S.p, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+    cudaStreamSynchronize(st);
+}
+
+template <class T>
+static int32_t do_precond(wmg_plan *pl, const void *s_in, void *z_out, cudaStream_t st)
+{
+    int32_t rc = ensure_wmg_pools(pl);
+    if (rc) return rc;
+    if (!ensure_partials(pl, 1)) return fail(WMG_ERR_OOM, "partials");
+    init_scalars(pl, pl->cap, 0.0, 1, st);
+    ImgArgs ia{};
+    ia.in_op = s_in;
+    ia.z = pl->s.as<double>();
+    img_op<T>(pl, IMG_LOAD, ia, st);
+    bool have = false;
+    rc = wmg_apply<T>(pl, pl->s.as<double>(), pl->z.as<double>(), false, false, false, &have, st);
+    if (rc) return rc;
+    ImgArgs io{};
+    io.z = pl->z.as<double>();
+    io.out_op = z_out;
+    img_op<T>(pl, IMG_STORE_OUT, io, st);
+    WMG_CUDA(cudaGetLastError());
+    return WMG_OK;
+}
+
+extern "C" int32_t wmg_precond_apply(wmg_plan *pl, int32_t count, const void *s, void *z, void *stream)
+{
+    if (!pl || !s || !z || count < 1) return fail(WMG_ERR_INVALID_ARG, "wmg_precond_apply: bad arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int32_t rc = ensure_count(pl, count, st);
+    if (rc) return rc;
+    return WMG_DISPATCH(pl, do_precond, pl, s, z, st);
+}
+
+// ---------------------------------------------------------------------------
+// Solvers
+// ---------------------------------------------------------------------------
+static int32_t any_active(wmg_plan *pl, int count, cudaStream_t st, bool *any)
+{
+    std::vector<double> S((size_t)count * NSCAL);
+    WMG_CUDA(cudaMemcpyAsync(S.data(), pl->S.p, S.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    WMG_CUDA(cudaStreamSynchronize(st));
+    *any = false;
+    for (int q = 0; q < count; ++q)
+        if (S[(size_t)q * NSCAL + SC_ACTIVE] != 0.0) *any = true;
+    return WMG_OK;
+}
+
+static int32_t collect(wmg_plan *pl, int count, int max_iter, wmg_solve_info *info, double *res_hist,
+                       cudaStream_t st)
+{
+    std::vector<double> S((size_t)count * NSCAL);
+    WMG_CUDA(cudaMemcpyAsync(S.data(), pl->S.p, S.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (res_hist)
+        WMG_CUDA(cudaMemcpyAsync(res_hist, pl->hist.p, (size_t)count * (max_iter + 1) * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+    WMG_CUDA(cudaStreamSynchronize(st));
+    WMG_CUDA(cudaGetLastError());
+    int32_t rc = WMG_OK;
+    for (int q = 0; q < count; ++q) {
+        const double *s = &S[(size_t)q * NSCAL];
+        int status = (int)s[SC_STATUS];
+        if (s[SC_ACTIVE] != 0.0) status = WMG_NOT_CONVERGED;
+        if (info) {
+            info[q].iters = (int)s[SC_ITERS];
+            info[q].status = status;
+            info[q].rel_res = s[SC_RES];
+        }
+        if (status < 0 && rc >= 0) rc = status;
+        else if (status == WMG_NOT_CONVERGED && rc == WMG_OK) rc = WMG_NOT_CONVERGED;
+    }
+    return rc;
+}
+
+template <class T>
+static int32_t solve_cgls(wmg_plan *pl, bool pre, int count, const void *b, void *xout, int max_iter,
+                          cudaStream_t st)
+{
+    const int64_t nN = (int64_t)count * pl->N, nM = (int64_t)count * pl->M;
+    const size_t e = pl->esz;
+    if (!ensure_pool(pl->x, nN, 8) || !ensure_pool(pl->s, nN, 8) || !ensure_pool(pl->z, nN, 8) ||
+        !ensure_pool(pl->p, nN, 8) || !ensure_pool(pl->r, nM, 8) || !ensure_pool(pl->p_op, nN, e) ||
+        !ensure_pool(pl->pT_op, nN, e) || !ensure_pool(pl->q, nM, e) || !ensure_pool(pl->r_op, nM, e) ||
+        !ensure_partials(pl, 1))
+        return fail(WMG_ERR_OOM, "CGLS pools");
+    if (pre) {
+        int32_t rc = ensure_wmg_pools(pl);
+        if (rc) return rc;
+    }
+    const ProbSet &ps = pl->real;
+    const double *S = pl->S.as<double>();
+    double *hist = pl->hist.as<double>();
+    const int hld = max_iter + 1;
+    double *pa = pl->part_a.as<double>(), *pb = pl->part_b.as<double>(), *pc = pl->part_c.as<double>();
+    const bool smooth_fused = pre && pl->opts.nu1 >= 1;
+    cudaMemsetAsync(pl->x.p, 0, nN * 8, st);
+    cudaMemsetAsync(pl->p.p, 0, nN * 8, st);
+    // r = b, s = W^T r (x = 0, alpha = 0)
+    VecArgs va{};
+    va.r = pl->r.as<double>(); va.b_op = b; va.r_op = pl->r_op.p; va.S = S;
+    vec_op<T>(pl, VEC_R_INIT, true, va, st);
+    auto bp_s = [&](void) {
+        BpArgs a = bp_args(BP_CGLS_S, pl->r_op.p, S);
+        a.x = pl->x.as<double>(); a.p = pl->p.as<double>(); a.s = pl->s.as<double>();
+        a.part = pa;
+        if (smooth_fused) { a.z = pl->z.as<double>(); a.copy_op = pl->z_op.p; a.copyT_op = pl->zT_op.p; }
+        backproject<T>(pl, ps, a, st);
+    };
+    bp_s();
+    double *zvec = pre ? pl->z.as<double>() : pl->s.as<double>();
+    bool have_sz = false;
+    if (pre) {
+        int32_t rc = wmg_apply<T>(pl, pl->s.as<double>(), pl->z.as<double>(), smooth_fused, false, true,
+                                  &have_sz, st);
+        if (rc) return rc;
+        if (!have_sz) {
+            ImgArgs ia{};
+            ia.s = pl->s.as<double>(); ia.z = pl->z.as<double>(); ia.part = pb; ia.S = S;
+            img_op<T>(pl, IMG_DOT_SZ, ia, st);
+        }
+    }
+    finalize(pl, FIN_CGLS_INIT, ps.bp, pa, 1, pre ? &ps.bp : nullptr, pre ? pb : nullptr, pre, hist, hld, st);
+    ImgArgs pi{};
+    pi.z = zvec; pi.p = pl->p.as<double>(); pi.copy_op = pl->p_op.p; pi.copyT_op = pl->pT_op.p; pi.part = pc; pi.S = S;
+    img_op<T>(pl, IMG_PINIT, pi, st);
+    finalize(pl, FIN_PNORM, ps.bp, pc, 1, nullptr, nullptr, pre, hist, hld, st);
+    const int chunk = 4;
+    for (int it = 0; it < max_iter; ++it) {
+        project<T>(pl, ps, pl->p_op.p, pl->pT_op.p, pl->q.p, pa, S, st);
+        finalize(pl, FIN_CGLS_ALPHA, ps.proj, pa, 1, nullptr, nullptr, pre, hist, hld, st);
+        VecArgs vr{};
+        vr.r = pl->r.as<double>(); vr.q = pl->q.p; vr.r_op = pl->r_op.p; vr.S = S;
+        vec_op<T>(pl, VEC_R_UPDATE, true, vr, st);
+        bp_s();
+        finalize(pl, FIN_CGLS_RES, ps.bp, pa, 1, nullptr, nullptr, pre, hist, hld, st);
+        if (pre) {
+            int32_t rc = wmg_apply<T>(pl, pl->s.as<double>(), pl->z.as<double>(), smooth_fused, false, true,
+                                      &have_sz, st);
+            if (rc) return rc;
+            if (!have_sz) {
+                ImgArgs ia{};
+                ia.s = pl->s.as<double>(); ia.z = pl->z.as<double>(); ia.part = pb; ia.S = S;
+                img_op<T>(pl, IMG_DOT_SZ, ia, st);
+            }
+        }
+        finalize(pl, FIN_CGLS_BETA, ps.bp, pb, 1, nullptr, nullptr, pre, hist, hld, st);
+        ImgArgs pu{};
+        pu.z = zvec; pu.p = pl->p.as<double>(); pu.copy_op = pl->p_op.p; pu.copyT_op = pl->pT_op.p; pu.part = pc; pu.S = S;
+        img_op<T>(pl, IMG_PUPDATE, pu, st);
+        finalize(pl, FIN_PNORM, ps.bp, pc, 1, nullptr, nullptr, pre, hist, hld, st);
+        if ((it + 1) % chunk == 0 || it + 1 == max_iter) {
+            bool any = false;
+            int32_t rc = any_active(pl, count, st, &any);
+            if (rc) return rc;
+            if (!any) break;
+        }
+    }
+    ImgArgs io{};
+    io.z = pl->x.as<double>(); io.out_op = xout;
+    img_op<T>(pl, IMG_STORE_OUT, io, st);
+    WMG_CUDA(cudaGetLastError());
+    return WMG_OK;
+}
+
+template <class T>
+static int32_t solve_sirt(wmg_plan *pl, int count, const void *b, void *xout, int max_iter, cudaStream_t st)
+{
+    const int64_t nN = (int64_t)count * pl->N, nM = (int64_t)count * pl->M;
+    const size_t e = pl->esz;
+    if (!ensure_pool(pl->x, nN, 8) || !ensure_pool(pl->p_op, nN, e) || !ensure_pool(pl->pT_op, nN, e) ||
+        !ensure_pool(pl->q, nM, e) || !ensure_pool(pl->r_op, nM, e) || !ensure_pool(pl->s, nN, 8) ||
+        !ensure_partials(pl, 1))
+        return fail(WMG_ERR_OOM, "SIRT pools");
+    const ProbSet &ps = pl->real;
+    const double *S = pl->S.as<double>();
+    cudaMemsetAsync(pl->x.p, 0, nN * 8, st);
+    cudaMemsetAsync(pl->p_op.p, 0, nN * e, st);
+    cudaMemsetAsync(pl->pT_op.p, 0, nN * e, st);
+    for (int it = 0; it < max_iter; ++it) {
+        project<T>(pl, ps, pl->p_op.p, pl->pT_op.p, pl->q.p, nullptr, S, st);
+        VecArgs va{};
+        va.b_op = b; va.q = pl->q.p; va.r_op = pl->r_op.p; va.S = S;
+        vec_op<T>(pl, VEC_SIRT_R, true, va, st);
+        BpArgs a = bp_args(BP_SIRT, pl->r_op.p, S);
+        a.x = pl->x.as<double>(); a.copy_op = pl->p_op.p; a.copyT_op = pl->pT_op.p;
+        backproject<T>(pl, ps, a, st);
+    }
+    // relative NE residual of the final iterate: |W^T (b - W x) - lambda x| / |W^T b|
+    double *pb = pl->part_b.as<double>();
+    BpArgs fa = bp_args(BP_ATB, b, S);
+    fa.out64 = pl->s.as<double>(); fa.part = pb;
+    backproject<T>(pl, ps, fa, st);
+    finalize(pl, FIN_STORE, ps.bp, pb, 1, nullptr, nullptr, 0, nullptr, 0, st, SC_S0);
+    project<T>(pl, ps, pl->p_op.p, pl->pT_op.p, pl->q.p, nullptr, S, st);
+    VecArgs vd{};
+    vd.b_op = b; vd.q = pl->q.p; vd.r_op = pl->r_op.p; vd.S = S;
+    vec_op<T>(pl, VEC_SINO_DIFF, true, vd, st);
+    BpArgs ra = bp_args(BP_ATB, pl->r_op.p, S);
+    ra.out64 = pl->s.as<double>();
+    backproject<T>(pl, ps, ra, st);
+    VecArgs vn{};
+    vn.w = pl->s.as<double>(); vn.x = pl->x.as<double>(); vn.part = pb; vn.S = S;
+    vec_op<T>(pl, VEC_NE_RES, false, vn, st);
+    finalize(pl, FIN_SET_RES, ps.vimg, pb, 1, nullptr, nullptr, 0, nullptr, 0, st);
+    std::vector<double> Sh((size_t)count * NSCAL);
+    WMG_CUDA(cudaMemcpyAsync(Sh.data(), pl->S.p, Sh.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    WMG_CUDA(cudaStreamSynchronize(st));
+    for (int q = 0; q < count; ++q) Sh[(size_t)q * NSCAL + SC_ITERS] = max_iter;
+    WMG_CUDA(cudaMemcpyAsync(pl->S.p, Sh.data(), Sh.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    ImgArgs io{};
+    io.z = pl->x.as<double>(); io.out_op = xout;
+    img_op<T>(pl, IMG_STORE_OUT, io, st);
+    WMG_CUDA(cudaGetLastError());
+    return WMG_OK;
+}
+
+template <class T>
+static int32_t solve_gmres(wmg_plan *pl, bool pre, int count, const void *b, void *xout, int max_iter,
+                           int restart, cudaStream_t st)
+{
+    const int64_t nN = (int64_t)count * pl->N, nM = (int64_t)count * pl->M;
+    const size_t e = pl->esz;
+    const int ldp = restart + 1;
+    if (!ensure_pool(pl->x, nN, 8) || !ensure_pool(pl->f, nN, 8) || !ensure_pool(pl->w, nN, 8) ||
+        !ensure_pool(pl->t, nN, 8) || !ensure_pool(pl->u, nN, 8) || !ensure_pool(pl->V, nN * ldp, 8) ||
+        !ensure_pool(pl->z_op, nN, e) || !ensure_pool(pl->zT_op, nN, e) || !ensure_pool(pl->sinoS, nM, e) ||
+        !ensure_partials(pl, ldp) || !pl->H.ensure((size_t)count * ldp * restart * 8) ||
+        !pl->gcs.ensure((size_t)count * restart * 8) || !pl->gsn.ensure((size_t)count * restart * 8) ||
+        !pl->gg.ensure((size_t)count * ldp * 8) || !pl->gy.ensure((size_t)count * ldp * 8) ||
+        !pl->h1.ensure((size_t)count * ldp * 8) || !pl->h2.ensure((size_t)count * ldp * 8) ||
+        !pl->jn.ensure((size_t)count * 4) || !pl->done.ensure((size_t)count * 4))
+        return fail(WMG_ERR_OOM, "GMRES pools");
+    if (pre) {
+        int32_t rc = ensure_wmg_pools(pl);
+        if (rc) return rc;
+    }
+    const ProbSet &ps = pl->real;
+    const double *S = pl->S.as<double>();
+    double *hist = pl->hist.as<double>();
+    const int hld = max_iter + 1;
+    double *pa = pl->part_a.as<double>(), *pb = pl->part_b.as<double>();
+    double *V = pl->V.as<double>();
+    const int64_t vstride = nN;
+    GmArgs ga{};
+    ga.nprob = count; ga.restart = restart; ga.ldp = ldp;
+    ga.S = pl->S.as<double>(); ga.H = pl->H.as<double>(); ga.cs = pl->gcs.as<double>();
+    ga.sn = pl->gsn.as<double>(); ga.g = pl->gg.as<double>(); ga.y = pl->gy.as<double>();
+    ga.h1 = pl->h1.as<double>(); ga.h2 = pl->h2.as<double>(); ga.jn = pl->jn.as<int>();
+    ga.done = pl->done.as<int>(); ga.hist = hist; ga.hist_ld = hld;
+    cudaMemsetAsync(pl->x.p, 0, nN * 8, st);
+    cudaMemsetAsync(pl->H.p, 0, (size_t)count * ldp * restart * 8, st);
+    // f = W^T b ; V_0 = f / |f|
+    BpArgs fa = bp_args(BP_ATB, b, S);
+    fa.out64 = pl->f.as<double>(); fa.part = pb;
+    backproject<T>(pl, ps, fa, st);
+    finalize(pl, FIN_STORE, ps.bp, pb, 1, nullptr, nullptr, 0, nullptr, 0, st, SC_WNORM2);
+    ga.init = 1;
+    launch_gm_scalar(2, ga, st);
+    ga.init = 0;
+    launch_gm_setv(ps.d.as<ProbDev>(), ps.vimg.tiles.as<int4>(), ps.vimg.n, V, vstride, ldp, 0,
+                   pl->f.as<double>(), S, st);
+    int done_iters = 0;
+    while (true) {
+        cudaMemsetAsync(pl->done.p, 0, (size_t)count * 4, st);
+        int j = 0;
+        for (; j < restart && done_iters < max_iter; ++j, ++done_iters) {
+            double *Vj = V + (int64_t)j * vstride;
+            // u = B v_j  (z_op / zT_op copies of u for the product)
+            if (pre) {
+                bool have = false;
+                int32_t rc = wmg_apply<T>(pl, Vj, pl->u.as<double>(), false, true, false, &have, st);
+                if (rc) return rc;
+            } else {
+                cudaMemcpyAsync(pl->u.p, Vj, nN * 8, cudaMemcpyDeviceToDevice, st);
+                ImgArgs ic{};
+                ic.z = pl->u.as<double>(); ic.copy_op = pl->z_op.p; ic.copyT_op = pl->zT_op.p; ic.S = S;
+                img_op<T>(pl, IMG_COPY64, ic, st);
+            }
+            // w = A u
+            project<T>(pl, ps, pl->z_op.p, pl->zT_op.p, pl->sinoS.p, nullptr, S, st);
+            BpArgs wa = bp_args(BP_GMRES_W, pl->sinoS.p, S);
+            wa.z = pl->u.as<double>(); wa.out64 = pl->w.as<double>();
+            backproject<T>(pl, ps, wa, st);
+            // two classical Gram-Schmidt passes
+            for (int pass = 0; pass < 2; ++pass) {
+                launch_gm_dots(ps.d.as<ProbDev>(), ps.vimg.tiles.as<int4>(), ps.vimg.n, V, vstride,
+                               pl->w.as<double>(), j, ldp, pa, S, st);
+                double *hv = pass == 0 ? pl->h1.as<double>() : pl->h2.as<double>();
+                finalize(pl, FIN_STORE, ps.vimg, pa, j + 1, nullptr, nullptr, 0, nullptr, 0, st, 0, hv, ldp);
+                launch_gm_axpy(ps.d.as<ProbDev>(), ps.vimg.tiles.as<int4>(), ps.vimg.n, V, vstride,
+                               pl->w.as<double>(), j, ldp, hv, pass == 1 ? pb : nullptr, S, st);
+            }
+            finalize(pl, FIN_STORE, ps.vimg, pb, 1, nullptr, nullptr, 0, nullptr, 0, st, SC_WNORM2);
+            ga.j = j;
+            launch_gm_scalar(0, ga, st);
+            launch_gm_setv(ps.d.as<ProbDev>(), ps.vimg.tiles.as<int4>(), ps.vimg.n, V, vstride, ldp, j + 1,
+                           pl->w.as<double>(), S, st);
+            if ((j + 1) % 4 == 0) {
+                std::vector<int> dn(count);
+                WMG_CUDA(cudaMemcpyAsync(dn.data(), pl->done.p, count * 4, cudaMemcpyDeviceToHost, st));
+                std::vector<double> Sh((size_t)count * NSCAL);
+                WMG_CUDA(cudaMemcpyAsync(Sh.data(), pl->S.p, Sh.size() * 8, cudaMemcpyDeviceToHost, st));
+                WMG_CUDA(cudaStreamSynchronize(st));
+                bool all = true;
+                for (int q = 0; q < count; ++q)
+                    if (Sh[(size_t)q * NSCAL + SC_ACTIVE] != 0.0 && !dn[q]) all = false;
+                if (all) { ++j; ++done_iters; break; }
+            }
+        }
+        // cycle end: y = H^-1 g, t = V y, x += B t, true residual
+        launch_gm_scalar(1, ga, st);
+        launch_gm_combine(ps.d.as<ProbDev>(), ps.vimg.tiles.as<int4>(), ps.vimg.n, V, vstride, ldp,
+                          pl->gy.as<double>(), pl->jn.as<int>(), pl->t.as<double>(), S, st);
+        if (pre) {
+            bool have = false;
+            int32_t rc = wmg_apply<T>(pl, pl->t.as<double>(), pl->u.as<double>(), false, false, false, &have, st);
+            if (rc) return rc;
+        } else {
+            cudaMemcpyAsync(pl->u.p, pl->t.p, nN * 8, cudaMemcpyDeviceToDevice, st);
+        }
+        VecArgs xa{};
+        xa.x = pl->x.as<double>(); xa.w = pl->u.as<double>(); xa.S = S;
+        vec_op<T>(pl, VEC_X_ADD, false, xa, st);
+        ImgArgs ic{};
+        ic.z = pl->x.as<double>(); ic.copy_op = pl->z_op.p; ic.copyT_op = pl->zT_op.p; ic.S = S;
+        img_op<T>(pl, IMG_COPY64, ic, st);
+        project<T>(pl, ps, pl->z_op.p, pl->zT_op.p, pl->sinoS.p, nullptr, S, st);
+        BpArgs wa = bp_args(BP_GMRES_W, pl->sinoS.p, S);
+        wa.z = pl->x.as<double>(); wa.out64 = pl->w.as<double>();
+        backproject<T>(pl, ps, wa, st);
+        VecArgs rv{};
+        rv.f = pl->f.as<double>(); rv.w = pl->w.as<double>(); rv.v = V; rv.part = pb; rv.S = S;
+        vec_op<T>(pl, VEC_RESID64, false, rv, st);
+        finalize(pl, FIN_STORE, ps.vimg, pb, 1, nullptr, nullptr, 0, nullptr, 0, st, SC_WNORM2);
+        launch_gm_scalar(2, ga, st);
+        launch_gm_setv(ps.d.as<ProbDev>(), ps.vimg.tiles.as<int4>(), ps.vimg.n, V, vstride, ldp, 0, V, S, st);
+        bool any = false;
+        int32_t rc = any_active(pl, count, st, &any);
+        if (rc) return rc;
+        if (!any || done_iters >= max_iter) break;
+    }
+    ImgArgs io{};
+    io.z = pl->x.as<double>(); io.out_op = xout;
+    img_op<T>(pl, IMG_STORE_OUT, io, st);
+    WMG_CUDA(cudaGetLastError());
+    return WMG_OK;
+}
+
+template <class T>
+static int32_t do_solve(wmg_plan *pl, int solver, bool pre, int count, const void *b, void *x, int max_iter,
+                        int restart, cudaStream_t st)
+{
+    if (solver == WMG_SOLVER_CGLS) return solve_cgls<T>(pl, pre, count, b, x, max_iter, st);
+    if (solver == WMG_SOLVER_GMRES) return solve_gmres<T>(pl, pre, count, b, x, max_iter, restart, st);
+    return solve_sirt<T>(pl, count, b, x, max_iter, st);
+}
+
+extern "C" int32_t wmg_solve(wmg_plan *pl, int32_t solver, int32_t preconditioned, int32_t count,
+                             const void *b, void *x, int32_t max_iter, double rtol, int32_t restart,
+                             wmg_solve_info *info, double *res_hist, void *stream)
+{
+    if (!pl || !b || !x || count < 1 || max_iter < 0 || solver < WMG_SOLVER_SIRT || solver > WMG_SOLVER_GMRES)
+        return fail(WMG_ERR_INVALID_ARG, "wmg_solve: bad arguments");
+    if (solver == WMG_SOLVER_GMRES && (restart < 1 || restart > 64))
+        return fail(WMG_ERR_INVALID_ARG, "wmg_solve: restart must be in [1, 64]");
+    if (solver == WMG_SOLVER_CGLS && preconditioned && pl->opts.cycle == WMG_CYCLE_HYBRID)
+        return fail(WMG_ERR_INVALID_ARG, "CGLS needs a symmetric preconditioner (ADDITIVE or SYMMETRIC cycle)");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int32_t rc = ensure_count(pl, count, st);
+    if (rc) return rc;
+    if (!pl->hist.ensure((size_t)count * (max_iter + 1) * sizeof(double)))
+        return fail(WMG_ERR_OOM, "history");
+    cudaMemsetAsync(pl->hist.p, 0, (size_t)count * (max_iter + 1) * sizeof(double), st);
+    init_scalars(pl, count, rtol, max_iter, st);
+    rc = WMG_DISPATCH(pl, do_solve, pl, solver, preconditioned != 0, count, b, x, max_iter, restart, st);
+    if (rc) return rc;
+    return collect(pl, count, max_iter, info, res_hist, st);
+}

@@ -1,0 +1,290 @@
+// haar.cu -- Haar wavelet-packet restriction/prolongation and the leaf
+// (coarsest-level) exact solves of the WMG cycle.
+//
+// Restriction by the four 2D Haar operators (eq. intops, eq. intops_wav,
+// eq. 1of4-4of4), applied recursively to depth L (Section 3.1.3), acts
+// independently on every 2^L x 2^L pixel block: the result is the block's 2D
+// Walsh-Hadamard transform scaled by 2^-L, with the packet path read from the
+// bit-reversed Walsh indices. The kernels below stage a strip of blocks in
+// shared memory, run L butterfly stages along x and L along y, and scatter to
+// the leaf layout C[k][cy][cx] (k = sum_d id_d 4^(L-d), id = 2*hy + hx, the
+// d-th split's high-pass bits in y and x). Prolongation (synthesis) is the
+// same transform run backwards. Fused epilogues update the preconditioner's
+// FP64 iterate and write the operator-precision copies (row-major and
+// transposed) that the next projection reads.
+//
+// Leaf solves: e_k = D_k^-1 c_k with the stored symmetric inverse; one CTA per
+// leaf streams D_k^-1 once for every problem of a same-geometry group, thread
+// i forming e_i = sum_j D^-1[j][i] c_j (rows read coalesced, symmetry).
+#include "kern_common.cuh"
+
+namespace wmg {
+
+__device__ __forceinline__ int bitrev_bits(int u, int L) { return L ? (int)(__brev((unsigned)u) >> (32 - L)) : 0; }
+
+__device__ __forceinline__ int spread_bits(int v, int L)
+{
+    int r = 0;
+    for (int i = 0; i < L; ++i) r |= ((v >> i) & 1) << (2 * i);
+    return r;
+}
+
+// Leaf index of Walsh position (uy, ux) inside a block.
+__device__ __forceinline__ int leaf_of(int uy, int ux, int L)
+{
+    return (spread_bits(bitrev_bits(uy, L), L) << 1) | spread_bits(bitrev_bits(ux, L), L);
+}
+
+// In-place Walsh-Hadamard butterflies over a B x W strip in shared memory
+// (pitch pw), along x (within every B-wide segment) then along y.
+template <class T>
+__device__ __forceinline__ void strip_wht(T *sm, int B, int W, int L, int pw)
+{
+    const int halfx = B * (W >> 1);
+    for (int st = 0; st < L; ++st) {
+        const int hbit = 1 << st;
+        for (int q = threadIdx.x; q < halfx; q += blockDim.x) {
+            const int r = q / (W >> 1), pi = q - r * (W >> 1);
+            const int i = ((pi >> st) << (st + 1)) | (pi & (hbit - 1));
+            T *row = sm + r * pw;
+            const T a = row[i], b = row[i + hbit];
+            row[i] = a + b;
+            row[i + hbit] = a - b;
+        }
+        __syncthreads();
+    }
+    const int halfy = (B >> 1) * W;
+    for (int st = 0; st < L; ++st) {
+        const int hbit = 1 << st;
+        for (int q = threadIdx.x; q < halfy; q += blockDim.x) {
+            const int col = q % W, pi = q / W;
+            const int i = ((pi >> st) << (st + 1)) | (pi & (hbit - 1));
+            const T a = sm[i * pw + col], b = sm[(i + hbit) * pw + col];
+            sm[i * pw + col] = a + b;
+            sm[(i + hbit) * pw + col] = a - b;
+        }
+        __syncthreads();
+    }
+}
+
+// Analysis: tile = {prob, y0, x0, W}; strip of B rows x W columns.
+template <class T, int MODE>
+__global__ void __launch_bounds__(256)
+k_haar_analysis(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
+                const int4 *__restrict__ tiles, int ntiles, HaarArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *sm = reinterpret_cast<T *>(smraw);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 tl = tiles[t];
+        const ProbDev pd = P[tl.x];
+        if (!slot_active(a.S, pd.slot)) continue;
+        const GeomDev &g = G[pd.geom];
+        const int n = g.n, B = g.B, L = g.L, W = tl.w, pw = W + 1;
+        const T *in = static_cast<const T *>(a.in) + pd.img;
+        for (int q = threadIdx.x; q < B * W; q += blockDim.x) {
+            const int r = q / W, x = q - r * W;
+            sm[r * pw + x] = in[(int64_t)(tl.y + r) * n + tl.z + x];
+        }
+        __syncthreads();
+        strip_wht(sm, B, W, L, pw);
+        const T scale = T(1) / T(B);
+        const int nb = W / B, cy = tl.y / B, cx0 = tl.z / B;
+        T *C = static_cast<T *>(a.out) + pd.coef;
+        for (int q = threadIdx.x; q < B * W; q += blockDim.x) {
+            const int bc = q % nb, rest = q / nb, ux = rest % B, uy = rest / B;
+            const int k = leaf_of(uy, ux, L);
+            const T v = sm[uy * pw + bc * B + ux] * scale;
+            const int64_t o = (int64_t)k * g.P + (int64_t)cy * g.nc + cx0 + bc;
+            if (MODE == HA_STORE) C[o] = v;
+            else if (k >= pd.kout0 && k < pd.kout1) {
+                if (MODE == HA_SUB_MASKED) C[o] -= v;
+                else C[o] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Synthesis: the transpose of the analysis.
+template <class T, int MODE>
+__global__ void __launch_bounds__(256)
+k_haar_synthesis(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
+                 const int4 *__restrict__ tiles, int ntiles, HaarArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *sm = reinterpret_cast<T *>(smraw);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 tl = tiles[t];
+        const ProbDev pd = P[tl.x];
+        if (!slot_active(a.S, pd.slot)) continue;
+        const GeomDev &g = G[pd.geom];
+        const int n = g.n, B = g.B, L = g.L, W = tl.w, pw = W + 1;
+        const int nb = W / B, cy = tl.y / B, cx0 = tl.z / B;
+        const T *E = static_cast<const T *>(a.in) + pd.coef;
+        for (int q = threadIdx.x; q < B * W; q += blockDim.x) {
+            const int bc = q % nb, rest = q / nb, ux = rest % B, uy = rest / B;
+            const int k = leaf_of(uy, ux, L);
+            T v = T(0);
+            if (MODE != HS_STORE_MASKED || (k >= pd.kin0 && k < pd.kin1))
+                v = E[(int64_t)k * g.P + (int64_t)cy * g.nc + cx0 + bc];
+            sm[uy * pw + bc * B + ux] = v;
+        }
+        __syncthreads();
+        strip_wht(sm, B, W, L, pw);
+        const T scale = T(1) / T(B);
+        T *out = static_cast<T *>(a.out);
+        for (int q = threadIdx.x; q < B * W; q += blockDim.x) {
+            const int r = q / W, x = q - r * W;
+            const int64_t j = pd.img + (int64_t)(tl.y + r) * n + tl.z + x;
+            const T v = sm[r * pw + x] * scale;
+            if (MODE == HS_CORRECT) {
+                const double zv = a.z[j] + (double)v;
+                a.z[j] = zv;
+                const T zt = (T)zv;
+                sm[r * pw + x] = zt;
+                if (out) out[j] = zt;
+            } else {
+                sm[r * pw + x] = v;
+                out[j] = v;
+            }
+        }
+        if (a.outT) {
+            __syncthreads();
+            T *outT = static_cast<T *>(a.outT);
+            for (int q = threadIdx.x; q < B * W; q += blockDim.x) {
+                const int x = q / B, r = q - x * B;
+                outT[pd.img + (int64_t)(tl.z + x) * n + tl.y + r] = sm[r * pw + x];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+static void set_smem(const void *fn, int bytes)
+{
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <class T>
+void launch_haar_analysis(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
+                          int smem_elems, const HaarArgs &a, cudaStream_t st)
+{
+    if (ntiles <= 0) return;
+    const int bytes = smem_elems * (int)sizeof(T);
+    const int grid = min(ntiles, num_sms() * 8);
+    switch (a.mode) {
+        case HA_STORE:
+            set_smem((const void *)k_haar_analysis<T, HA_STORE>, bytes);
+            k_haar_analysis<T, HA_STORE><<<grid, 256, bytes, st>>>(G, P, tiles, ntiles, a);
+            break;
+        case HA_SUB_MASKED:
+            set_smem((const void *)k_haar_analysis<T, HA_SUB_MASKED>, bytes);
+            k_haar_analysis<T, HA_SUB_MASKED><<<grid, 256, bytes, st>>>(G, P, tiles, ntiles, a);
+            break;
+        case HA_STORE_MASKED:
+            set_smem((const void *)k_haar_analysis<T, HA_STORE_MASKED>, bytes);
+            k_haar_analysis<T, HA_STORE_MASKED><<<grid, 256, bytes, st>>>(G, P, tiles, ntiles, a);
+            break;
+    }
+}
+
+template <class T>
+void launch_haar_synthesis(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
+                           int smem_elems, const HaarArgs &a, cudaStream_t st)
+{
+    if (ntiles <= 0) return;
+    const int bytes = smem_elems * (int)sizeof(T);
+    const int grid = min(ntiles, num_sms() * 8);
+    switch (a.mode) {
+        case HS_STORE:
+            set_smem((const void *)k_haar_synthesis<T, HS_STORE>, bytes);
+            k_haar_synthesis<T, HS_STORE><<<grid, 256, bytes, st>>>(G, P, tiles, ntiles, a);
+            break;
+        case HS_STORE_MASKED:
+            set_smem((const void *)k_haar_synthesis<T, HS_STORE_MASKED>, bytes);
+            k_haar_synthesis<T, HS_STORE_MASKED><<<grid, 256, bytes, st>>>(G, P, tiles, ntiles, a);
+            break;
+        case HS_CORRECT:
+            set_smem((const void *)k_haar_synthesis<T, HS_CORRECT>, bytes);
+            k_haar_synthesis<T, HS_CORRECT><<<grid, 256, bytes, st>>>(G, P, tiles, ntiles, a);
+            break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Leaf solves. tile = {first problem p0, leaf k, problem count np, 0}; the
+// problems p0 .. p0+np-1 share one geometry. NPB problems per pass.
+// ---------------------------------------------------------------------------
+template <class T, int NPB>
+__global__ void __launch_bounds__(256)
+k_leaf_apply(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
+             const int4 *__restrict__ tiles, int ntiles, const T *__restrict__ C,
+             T *__restrict__ E, int accumulate, const double *__restrict__ S)
+{
+    __shared__ T cb[NPB][256];
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 tl = tiles[t];
+        const GeomDev &g = G[P[tl.x].geom];
+        const int Pn = g.P, k = tl.y;
+        const T *__restrict__ Dk = static_cast<const T *>(g.leafinv) + (int64_t)k * Pn * Pn;
+        for (int pb = 0; pb < tl.z; pb += NPB) {
+            const int np = min(NPB, tl.z - pb);
+            for (int q = threadIdx.x; q < NPB * Pn; q += blockDim.x) {
+                const int pi = q / Pn, j = q - pi * Pn;
+                T v = T(0);
+                if (pi < np) {
+                    const ProbDev pd = P[tl.x + pb + pi];
+                    if (slot_active(S, pd.slot)) v = C[pd.coef + (int64_t)k * Pn + j];
+                }
+                cb[pi][j] = v;
+            }
+            __syncthreads();
+            const int i = threadIdx.x;
+            if (i < Pn) {
+                T acc[NPB];
+#pragma unroll
+                for (int u = 0; u < NPB; ++u) acc[u] = T(0);
+#pragma unroll 8
+                for (int j = 0; j < Pn; ++j) {
+                    const T d = ldg_t(Dk + (int64_t)j * Pn + i);
+#pragma unroll
+                    for (int u = 0; u < NPB; ++u) acc[u] = fma_t(d, cb[u][j], acc[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < NPB; ++u) {
+                    if (u < np) {
+                        const ProbDev pd = P[tl.x + pb + u];
+                        if (!slot_active(S, pd.slot)) continue;
+                        T *e = E + pd.coef + (int64_t)k * Pn + i;
+                        *e = accumulate ? *e + acc[u] : acc[u];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <class T>
+void launch_leaf_apply(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
+                       const void *C, void *E, int accumulate, const double *S, cudaStream_t st)
+{
+    if (ntiles <= 0) return;
+    const int grid = min(ntiles, num_sms() * 8);
+    k_leaf_apply<T, 4><<<grid, 256, 0, st>>>(G, P, tiles, ntiles, static_cast<const T *>(C),
+                                             static_cast<T *>(E), accumulate, S);
+}
+
+#define WMG_INST(T)                                                                              \
+    template void launch_haar_analysis<T>(const GeomDev *, const ProbDev *, const int4 *, int,  \
+                                          int, const HaarArgs &, cudaStream_t);                  \
+    template void launch_haar_synthesis<T>(const GeomDev *, const ProbDev *, const int4 *, int, \
+                                           int, const HaarArgs &, cudaStream_t);                 \
+    template void launch_leaf_apply<T>(const GeomDev *, const ProbDev *, const int4 *, int,     \
+                                       const void *, void *, int, const double *, cudaStream_t);
+WMG_INST(float)
+WMG_INST(double)
+#undef WMG_INST
+
+}  // namespace wmg

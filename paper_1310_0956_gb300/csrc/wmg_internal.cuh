@@ -1,0 +1,172 @@
+// wmg_internal.cuh -- shared declarations of the GB300 kernels and the host
+// engine behind include/wmgct.h. Device code targets sm_103a only.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "wmgct.h"
+
+namespace wmg {
+
+// ---------------------------------------------------------------------------
+// Device-side tables. Every kernel is table driven: a launch covers a list of
+// tiles, each tile belongs to one problem, each problem points at one
+// geometry. A single reconstruction, a same-geometry batch and the
+// band-local multi-image products of the hybrid cycle are all just tables.
+// ---------------------------------------------------------------------------
+
+// Immutable per-geometry data (lengths in pixel widths, h = 1/n applied to
+// the weights at the end).
+struct GeomDev {
+    int n, m, D, L;          // image side, angles, bins per angle, Haar levels
+    int nc, P, K, B;         // leaf side n/2^L, P = nc^2, K = 4^L leaves, B = 2^L block side
+    double h;                // pixel width on the unit square
+    double t0, dt;           // detector offset and spacing (pixel widths)
+    double lambda, omega;    // Tikhonov parameter, smoother damping
+    const double2 *cs64;     // (cos, sin) per angle, FP64
+    const float2 *cs32;      // round-to-nearest FP32 copy
+    const void *dinv;        // N: 1/D~ (0 where D~ = 0), operator precision
+    const void *leafinv;     // K*P*P: leaf inverses, operator precision
+    const void *sirtR;       // M: 1/row sums (0 if empty)
+    const void *sirtC;       // N: 1/column sums (0 if empty)
+};
+
+// One problem slot (or one virtual image of a multi-image product).
+struct ProbDev {
+    int geom;                // index into the GeomDev table
+    int slot;                // owning real problem (scalar / flag index)
+    int64_t img;             // element offset of its image-sized vectors
+    int64_t sino;            // element offset of its sinogram-sized vectors
+    int64_t coef;            // element offset of its packet-coefficient vectors
+    int kin0, kin1;          // leaf range read by masked synthesis
+    int kout0, kout1;        // leaf range written by masked analysis
+};
+
+// Per-problem scalar slots (FP64), S[slot * NSCAL + i].
+enum Scal : int {
+    SC_GAMMA = 0, SC_DELTA, SC_ALPHA, SC_BETA, SC_S0, SC_RES, SC_PP, SC_ITERS, SC_ACTIVE,
+    SC_STATUS, SC_RTOL, SC_MAXIT, SC_HNORM, SC_WNORM2, SC_GNEW,
+    NSCAL = 16
+};
+
+// Work lists: int4 tiles, problem index in .x.
+//  project:     {prob, angle a, first ray k0, 0}   -- 32 rays of one angle
+//  backproject: {prob, iy0, ix0, 0}                -- 32 x 32 pixel tile
+//  haar:        {prob, first pixel row y0, first column x0, width}
+//  vec (image): {prob, first element, count, 0}
+//  vec (sino):  {prob, first element, count, 0}
+//  leaf:        {geom, leaf k, first problem in group, problem count}
+
+// ---------------------------------------------------------------------------
+// Host-side error state
+// ---------------------------------------------------------------------------
+void set_error(const std::string &msg);
+int32_t fail(int32_t code, const std::string &msg);
+
+#define WMG_CUDA(call)                                                              \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess)                                                      \
+            return ::wmg::fail(WMG_ERR_CUDA, std::string(#call) + ": " +            \
+                                                 cudaGetErrorString(e_));           \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (projector.cu, haar.cu, setup.cu, krylov.cu).
+// `T` = operator element type (float or double).
+// ---------------------------------------------------------------------------
+
+// Epilogue selectors of the backprojector (see projector.cu for the exact
+// formulas; y = h * sum of weighted bins at a pixel).
+enum BpEpi : int {
+    BP_STORE = 0,      // out_op = y                                      (T)
+    BP_CGLS_S,         // x += alpha p; s = y - lambda x; z1 = w D~^-1 s;  (FP64) + z1 copies
+    BP_RESID,          // r1 = s - y - lambda z                            (T)
+    BP_POST,           // z += w D~^-1 (s - y - lambda z); dot s.z         (FP64)
+    BP_APPLY_A,        // out = y + lambda v                               (T or FP64)
+    BP_SIRT,           // x += C (y - lambda x)                            (FP64) + copies
+    BP_GMRES_W,        // w = y + lambda u                                 (FP64)
+    BP_ATB,            // f = y (FP64), dot f.f
+};
+
+struct BpArgs {
+    int epi;
+    const void *sino;        // T, sinogram input pool
+    void *out_op;            // T image output (BP_STORE, BP_RESID, BP_APPLY_A)
+    double *x, *s, *z, *p;   // FP64 Krylov vectors (pools)
+    const void *v_op;        // T image (BP_APPLY_A, BP_RESID uses z FP64)
+    void *copy_op;           // T copy of the updated FP64 vector (row-major)
+    void *copyT_op;          // T transposed copy
+    double *part;            // per-tile partial dot (or NULL)
+    const double *S;         // per-problem scalars
+    double *out64;           // FP64 output (BP_GMRES_W, BP_ATB, BP_APPLY_A in FP64 mode)
+};
+
+struct PjArgs {
+    const void *img;         // T image pool (row-major)
+    const void *imgT;        // T transposed image pool (for |sin| > |cos| angles)
+    void *sino;              // T sinogram output pool
+    double *part;            // per-tile partial ||q||^2 (or NULL)
+    const double *S;         // scalars (active flags), or NULL = all active
+};
+
+template <class T>
+void launch_project(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
+                    const PjArgs &a, cudaStream_t st);
+template <class T>
+void launch_backproject(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
+                        const BpArgs &a, cudaStream_t st);
+template <class T>
+void launch_transpose(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
+                      const void *src, void *dst, cudaStream_t st);
+
+// Haar packet transforms (haar.cu).
+enum HaarMode : int {
+    HA_STORE = 0,      // C = Q^T img
+    HA_SUB_MASKED,     // C[k] -= (Q^T img)[k] for k in [kout0, kout1)
+    HA_STORE_MASKED,   // C[k]  = (Q^T img)[k] for k in [kout0, kout1)
+};
+enum HaarSynMode : int {
+    HS_STORE = 0,      // img_op = Q E (T)                       + optional transposed copy
+    HS_STORE_MASKED,   // img_op = Q (E masked to [kin0, kin1))  + optional transposed copy
+    HS_CORRECT,        // z += Q E (FP64) ; copies of z in T     (row-major + transposed)
+};
+struct HaarArgs {
+    int mode;
+    const void *in;          // analysis: T image; synthesis: T coefficients
+    void *out;               // analysis: T coefficients; synthesis: T image
+    void *outT;              // synthesis: transposed T copy (or NULL)
+    double *z;               // HS_CORRECT: FP64 vector updated in place
+    const double *S;         // scalars (active flags) or NULL
+};
+template <class T>
+void launch_haar_analysis(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
+                          int smem_elems, const HaarArgs &a, cudaStream_t st);
+template <class T>
+void launch_haar_synthesis(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
+                           int smem_elems, const HaarArgs &a, cudaStream_t st);
+
+// Leaf solves E[k] = Dinv_k C[k] for the problems of a group (haar.cu).
+// accumulate = 1 adds into E.
+template <class T>
+void launch_leaf_apply(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
+                       const void *C, void *E, int accumulate, const double *S, cudaStream_t st);
+
+// Setup (setup.cu).
+template <class T>
+int32_t build_leaf_inverses(const GeomDev &g_host, const GeomDev *g_dev, void *leafinv_out,
+                            cudaStream_t st);
+
+// Elementwise / reduction kernels (krylov.cu), all FP64 Krylov state.
+void launch_vec_kernel(int op, const ProbDev *P, const int4 *tiles, int ntiles,
+                       const GeomDev *G, void *const *ptrs, const double *S, double *part,
+                       int is_f32, cudaStream_t st);
+void launch_finalize(int op, int nprob, const int *tile_begin, const int *tile_end,
+                     const double *partA, const double *partB, double *S, int iter_idx,
+                     double *hist, int hist_stride, cudaStream_t st);
+
+}  // namespace wmg

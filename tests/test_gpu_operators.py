@@ -1,0 +1,126 @@
+"""GPU parity of the operators against the FP64 oracle, element by element:
+forward projection W, backprojection W^T (Section 2.1), the Haar packet
+transforms (Section 3.1), the leaf inverses and one WMG cycle."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+
+torch = pytest.importorskip("torch")
+import paper_1310_0956_gb300 as wmg  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+GEOMS = [  # n, m, D, dt, t0 -- tiny, odd/even D, axis angles, non-unit spacing, ragged tiles
+    (4, 8, 7, 1.0, 0.0), (5, 7, 8, 1.0, 0.0), (8, 24, 12, 1.0, 0.0), (6, 10, 11, 0.75, 0.3),
+    (16, 1, 23, 1.0, 0.0), (16, 40, 33, 1.0, 0.5), (32, 36, 46, 1.0, 0.0), (33, 20, 48, 1.0, 0.0),
+    (40, 13, 57, 1.3, -0.7), (64, 90, 91, 1.0, 0.0),
+]
+
+
+def dev(a, dtype=torch.float64):
+    return torch.tensor(np.asarray(a), dtype=dtype, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy()
+
+
+def relmax(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("n,m,D,dt,t0", GEOMS)
+def test_project_backproject_f64(n, m, D, dt, t0):
+    op = oracle.Op(n, m, D, dt, t0)
+    plan = wmg.Plan(n, m, D, levels=1, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F64,
+                    det_spacing=dt, det_offset=t0)
+    rng = np.random.default_rng(n * 1000 + m)
+    x, y = rng.standard_normal(op.N), rng.standard_normal(op.M)
+    assert relmax(host(plan.project(dev(x))), op.project(x)) < 1e-13
+    assert relmax(host(plan.backproject(dev(y))), op.backproject(y)) < 1e-13
+
+
+@pytest.mark.parametrize("n,m,D", [(64, 90, 91), (32, 36, 46), (256, 180, 363)])
+def test_project_backproject_f32(n, m, D):
+    op = oracle.Op(n, m, D)
+    plan = wmg.Plan(n, m, D, levels=1, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F32)
+    rng = np.random.default_rng(3)
+    x, y = rng.random(op.N), rng.random(op.M)
+    assert relmax(host(plan.project(dev(x, torch.float32))), op.project(x)) < 2e-6
+    assert relmax(host(plan.backproject(dev(y, torch.float32))), op.backproject(y)) < 2e-6
+
+
+def test_batched_projection_equals_single():
+    n, m, D = 64, 90, 91
+    plan = wmg.Plan(n, m, D, levels=1, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F64)
+    rng = np.random.default_rng(4)
+    xs = rng.standard_normal((3, n * n))
+    batched = host(plan.project(dev(xs.reshape(-1)))).reshape(3, -1)
+    for i in range(3):
+        single = host(plan.project(dev(xs[i])))
+        assert np.array_equal(single, batched[i])
+
+
+def test_adjointness_gpu():
+    n, m, D = 64, 90, 91
+    plan = wmg.Plan(n, m, D, levels=1, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F64)
+    rng = np.random.default_rng(5)
+    x, y = rng.standard_normal(n * n), rng.standard_normal(m * D)
+    lhs = host(plan.project(dev(x))) @ y
+    rhs = x @ host(plan.backproject(dev(y)))
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+@pytest.mark.parametrize("n,levels", [(16, 3), (64, 3), (32, 4), (48, 4), (256, 5)])
+def test_haar_packets(n, levels):
+    L = levels - 1
+    plan = wmg.Plan(n, 4, 2 * n, levels=levels, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE,
+                    precision=wmg.PREC_F64, lam=1.0)
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal(n * n)
+    c = host(plan.haar_analysis(dev(x)))
+    assert relmax(c, oracle.packet_analysis(x, n, L)) < 1e-14
+    xr = host(plan.haar_synthesis(dev(c)))
+    assert relmax(xr, oracle.packet_synthesis(c, n, L)) < 1e-14
+
+
+@pytest.mark.parametrize("n,m,D,levels,lam", [(16, 24, 23, 3, 0.0), (32, 36, 46, 3, 0.1), (64, 90, 91, 3, 0.0)])
+def test_leaf_inverses(n, m, D, levels, lam):
+    op = oracle.Op(n, m, D)
+    ref = oracle.Wmg(op, levels, lam=lam, factor=False)
+    plan = wmg.Plan(n, m, D, levels=levels, nu1=0, nu2=0, lam=lam, cycle=wmg.CYCLE_ADDITIVE,
+                    precision=wmg.PREC_F64)
+    for k in range(ref.K):
+        Dk = ref.leaf(k)
+        inv = host(plan.leaf_inverse(k))
+        assert np.abs(inv @ Dk - np.eye(Dk.shape[0])).max() < 1e-9
+        assert np.abs(inv - inv.T).max() < 1e-12 * np.abs(inv).max()
+
+
+CYCLES = [  # levels, nu1, nu2, cycle, hybrid depth, lambda
+    (3, 0, 0, wmg.CYCLE_ADDITIVE, 0, 0.0),
+    (3, 1, 1, wmg.CYCLE_ADDITIVE, 0, 0.0),
+    (3, 0, 0, wmg.CYCLE_HYBRID, 2, 0.0),
+    (3, 1, 1, wmg.CYCLE_HYBRID, 2, 0.3),
+    (4, 0, 0, wmg.CYCLE_HYBRID, 1, 0.0),
+    (4, 1, 1, wmg.CYCLE_HYBRID, 3, 0.0),
+    (3, 1, 1, wmg.CYCLE_SYMMETRIC, 2, 0.0),
+    (4, 2, 1, wmg.CYCLE_SYMMETRIC, 2, 0.1),
+]
+
+
+@pytest.mark.parametrize("levels,nu1,nu2,cycle,hd,lam", CYCLES)
+def test_wmg_cycle(levels, nu1, nu2, cycle, hd, lam):
+    n, m, D = 32, 36, 46
+    op = oracle.Op(n, m, D)
+    ref = oracle.Wmg(op, levels, nu1, nu2, 1.0, lam, cycle, hd)
+    plan = wmg.Plan(n, m, D, levels=levels, nu1=nu1, nu2=nu2, lam=lam, hybrid_depth=hd, cycle=cycle,
+                    precision=wmg.PREC_F64)
+    rng = np.random.default_rng(7)
+    s = rng.standard_normal((2, op.N))
+    z = host(plan.precond(dev(s.reshape(-1)))).reshape(2, -1)
+    for i in range(2):
+        assert relmax(z[i], ref.apply(s[i])) < 1e-10

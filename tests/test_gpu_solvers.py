@@ -1,0 +1,113 @@
+"""GPU parity of the solvers against the FP64 oracle at the same iteration
+count: SIRT (eq. sirt_it), CGLS / WMG-preconditioned CGLS and restarted
+right-preconditioned GMRES (Section 2.3.1) on the 64x64 workload in FP64
+(1e-10 relative image error) and the 256x256 workload with the FP32
+operator (1e-4 relative image error)."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+
+torch = pytest.importorskip("torch")
+import paper_1310_0956_gb300 as wmg  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a, dtype=torch.float64):
+    return torch.tensor(np.asarray(a), dtype=dtype, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def small():
+    P = S.workload_small().problems[0]
+    op = oracle.Op(P.n, P.m, P.D)
+    b = op.project(P.image())
+    return P, op, b
+
+
+def test_sirt_small(small):
+    P, op, b = small
+    x_ref, _ = oracle.sirt(op, b, 50)
+    plan = wmg.Plan(P.n, P.m, P.D, levels=P.levels, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE)
+    x, info, _, _ = plan.solve(dev(b), wmg.SOLVER_SIRT, False, max_iter=50, rtol=0.0)
+    assert rel(host(x), x_ref) < 1e-10
+    assert info[0][0] == 50
+
+
+@pytest.mark.parametrize("pre,cycle,hd", [(False, 0, 0), (True, wmg.CYCLE_ADDITIVE, 0),
+                                          (True, wmg.CYCLE_SYMMETRIC, 2)])
+def test_cgls_small_50_iterations(small, pre, cycle, hd):
+    P, op, b = small
+    M = oracle.Wmg(op, P.levels, 1, 1, 1.0, 0.0, cycle, hd) if pre else None
+    x_ref, k_ref, h_ref = oracle.cgls(op, b, 50, 0.0, 0.0, M)
+    plan = wmg.Plan(P.n, P.m, P.D, levels=P.levels, nu1=1, nu2=1, hybrid_depth=hd, cycle=cycle)
+    x, info, hist, _ = plan.solve(dev(b), wmg.SOLVER_CGLS, pre, max_iter=50, rtol=0.0, history=True)
+    assert info[0][0] == k_ref == 50
+    assert rel(host(x), x_ref) < 1e-10
+    assert np.abs(hist[0] - h_ref).max() < 1e-9
+
+
+@pytest.mark.parametrize("pre,cycle,hd", [(False, 0, 0), (True, wmg.CYCLE_HYBRID, 2),
+                                          (True, wmg.CYCLE_ADDITIVE, 0)])
+def test_gmres_small(small, pre, cycle, hd):
+    P, op, b = small
+    M = oracle.Wmg(op, P.levels, 1, 1, 1.0, 0.0, cycle, hd) if pre else None
+    x_ref, k_ref, h_ref = oracle.gmres(op, b, 30, 20, 0.0, 0.0, M)
+    plan = wmg.Plan(P.n, P.m, P.D, levels=P.levels, nu1=1, nu2=1, hybrid_depth=hd, cycle=cycle)
+    x, info, hist, _ = plan.solve(dev(b), wmg.SOLVER_GMRES, pre, max_iter=30, rtol=0.0, restart=20,
+                                  history=True)
+    assert info[0][0] == k_ref == 30
+    assert rel(host(x), x_ref) < 1e-10
+    assert np.abs(hist[0] - h_ref).max() < 1e-9
+
+
+def test_cgls_converges_to_tolerance(small):
+    P, op, b = small
+    plan = wmg.Plan(P.n, P.m, P.D, levels=P.levels, nu1=1, nu2=1, hybrid_depth=2, cycle=wmg.CYCLE_SYMMETRIC)
+    x, info, _, rc = plan.solve(dev(b), wmg.SOLVER_CGLS, True, max_iter=200, rtol=1e-4)
+    assert rc == 0 and info[0][1] == 0
+    assert op.ne_residual(b, host(x)) < 1.2e-4
+
+
+def test_batch_alone_equals_in_mix(small):
+    P, op, b = small
+    rng = np.random.default_rng(8)
+    bs = np.stack([b, b + 0.01 * rng.standard_normal(op.M), 0.5 * b])
+    plan = wmg.Plan(P.n, P.m, P.D, levels=P.levels, nu1=1, nu2=1, hybrid_depth=2, cycle=wmg.CYCLE_HYBRID)
+    xb, infob, _, _ = plan.solve(dev(bs.reshape(-1)), wmg.SOLVER_GMRES, True, max_iter=40, rtol=1e-6)
+    xb = host(xb).reshape(3, -1)
+    for i in range(3):
+        xs, infos, _, _ = plan.solve(dev(bs[i]), wmg.SOLVER_GMRES, True, max_iter=40, rtol=1e-6)
+        assert infos[0][0] == infob[i][0]
+        assert np.array_equal(host(xs), xb[i])
+
+
+@pytest.fixture(scope="module")
+def mid():
+    P = S.workload_mid(1).problems[0]
+    op = oracle.Op(P.n, P.m, P.D)
+    b0 = op.project(P.image())
+    b = b0 + P.noise * np.abs(b0).max() * P.noise_unit()
+    return P, op, b
+
+
+def test_gmres_mid_f32_against_f64_oracle(mid):
+    P, op, b = mid
+    M = oracle.Wmg(op, P.levels, 1, 1, 1.0, 0.0, wmg.CYCLE_HYBRID, 2)
+    x_ref, k_ref, _ = oracle.gmres(op, b, 16, 20, 0.0, 0.0, M)
+    plan = wmg.Plan(P.n, P.m, P.D, levels=P.levels, nu1=1, nu2=1, hybrid_depth=2, cycle=wmg.CYCLE_HYBRID,
+                    precision=wmg.PREC_F32)
+    x, info, _, _ = plan.solve(dev(b, torch.float32), wmg.SOLVER_GMRES, True, max_iter=16, rtol=0.0)
+    assert info[0][0] == 16
+    assert rel(host(x), x_ref) < 1e-4

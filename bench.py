@@ -1,0 +1,340 @@
+"""Benchmark: WMG-preconditioned Krylov reconstructions per second to a 1e-4
+relative normal-equation residual on the 256x256 parallel-beam workload
+(180 angles, 363 detector bins, seeded 20-ellipse phantoms, 1% Gaussian
+noise, 5 WMG levels), solved by restarted GMRES(20) with right
+preconditioning by the hybrid WMG cycle (hybrid depth 2, one l1-Jacobi pre-
+and post-sweep), FP32 operator with FP64 Krylov vectors and reductions.
+
+One step = one batch of `--batch` independent reconstructions (distinct
+phantoms and noise), all iterated together until each reaches the tolerance.
+The plan (geometry, smoother diagonal, leaf inverses) is built once for the
+geometry and reused by every step; its setup time is reported separately.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B]
+                       [--impl ours|reference]
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (one reconstruction, setup excluded) and prints the same JSON line.
+Under torchrun (N > 1) every rank solves its own batch (replicas, no
+communication); the value is the total over ranks divided by the slowest
+rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synthetic as S  # noqa: E402
+
+METRIC = "WMG-Krylov recon/s to 1e-4 residual"
+RTOL = 1e-4
+MAX_ITER = 200
+RESTART = 20
+LEVELS, NU1, NU2, HYB = 5, 1, 1, 2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_problems(batch: int, rank: int):
+    return S.workload_mid(batch * (rank + 1)).problems[batch * rank: batch * (rank + 1)]
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (one reconstruction of the workload, FP64, 1 thread)
+# ---------------------------------------------------------------------------
+def cpu_baseline(problem) -> dict:
+    import oracle
+
+    op = oracle.Op(problem.n, problem.m, problem.D)
+    b0 = op.project(problem.image())
+    b = b0 + problem.noise * np.abs(b0).max() * problem.noise_unit()
+    t0 = time.perf_counter()
+    M = oracle.Wmg(op, LEVELS, NU1, NU2, 1.0, 0.0, oracle.CYCLE_HYBRID, HYB)
+    setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    x, k, hist = oracle.gmres(op, b, MAX_ITER, RESTART, RTOL, 0.0, M)
+    solve = time.perf_counter() - t0
+    return {"value": 1.0 / solve, "unit": "recon/s", "cores": 1, "kind": "oracle",
+            "sample": (f"1 reconstruction of the workload (problem seed {problem.seed}): WMG-GMRES(20) "
+                       f"to {RTOL:g} in {k} iterations, {solve:.1f} s; plan setup {setup:.1f} s "
+                       "excluded like the GPU plan's"),
+            "iters": int(k), "setup_s": setup}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    P = workload_problems(1, 0)[0]
+    per = []
+    base = None
+    for _ in range(max(1, args.warmup and 0) + args.steps):
+        base = cpu_baseline(P)
+        per.append(1.0 / base["value"])
+    t = float(np.mean(per))
+    val = 1.0 / t
+    line = {"metric": METRIC, "value": val, "unit": "recon/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "256x256_180ang_363det_noise1pct", "batch": 1, "solver": "WMG-GMRES(20)",
+                       "levels": LEVELS, "precision": "fp64 oracle (CPU)"},
+            "cpu_baseline": {"value": val, "unit": "recon/s", "cores": 1, "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": val, "unit": "recon/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU run
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_1310_0956_gb300 as wmg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    probs = workload_problems(args.batch, rank)
+    P0 = probs[0]
+    B = len(probs)
+    N, M = P0.N, P0.M
+
+    # plan: built once for the geometry (timed separately)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = wmg.Plan(P0.n, P0.m, P0.D, levels=LEVELS, nu1=NU1, nu2=NU2, hybrid_depth=HYB,
+                    cycle=wmg.CYCLE_HYBRID, precision=wmg.PREC_F32)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+
+    # synthetic inputs, resident in HBM: b = W x_phantom (FP64 library
+    # projector) + sigma * N(0,1), sigma = 1% of max|W x|
+    plan64 = wmg.Plan(P0.n, P0.m, P0.D, levels=0, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE,
+                      precision=wmg.PREC_F64)
+    imgs = torch.tensor(np.stack([p.image() for p in probs]).reshape(-1), dtype=torch.float64, device=dev)
+    b64 = plan64.project(imgs).view(B, M)
+    noise = torch.tensor(np.stack([p.noise_unit() for p in probs]), dtype=torch.float64, device=dev)
+    sigma = torch.tensor([p.noise for p in probs], dtype=torch.float64, device=dev)[:, None] * \
+        b64.abs().amax(dim=1, keepdim=True)
+    b = (b64 + sigma * noise).to(torch.float32).contiguous().view(-1)
+    plan64.close()
+    del imgs, b64, noise
+    x = torch.empty(B * N, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        _, info, _, rc = plan.solve(b, wmg.SOLVER_GMRES, True, MAX_ITER, RTOL, RESTART, out=x)
+        return info, rc
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    wmg.wmg_launch_count(True)
+    sampler.start()
+    times, iters, statuses = [], [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)                              # evict L2 between steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info, rc = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        iters.extend(i[0] for i in info)
+        statuses.extend(i[1] for i in info)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = wmg.wmg_launch_count(False)
+    t_step = float(np.mean(times))
+    t_total = float(np.sum(times))
+    if world > 1:
+        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(tt.item())
+        torch.distributed.barrier()
+    value = B * world * args.steps / t_total
+
+    # end-to-end: the same solve through the C ABI with HOST (pinned) buffers,
+    # host->device copy of the sinograms and device->host copy of the images
+    # inside the timed region
+    b_host = b.cpu().pin_memory()
+    x_host = torch.empty(B * N, dtype=torch.float32).pin_memory()
+    b_dev = torch.empty_like(b)
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b_dev.copy_(b_host, non_blocking=True)
+        plan.solve(b_dev, wmg.SOLVER_GMRES, True, MAX_ITER, RTOL, RESTART, out=x)
+        x_host.copy_(x, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_times.append(e0.elapsed_time(e1) / 1e3)
+    e2e_val = B * world / float(np.mean(e2e_times))
+
+    # dominant-kernel timing: projector and backprojector launches of one
+    # profiled step (CUDA events around every launch on the plan's stream)
+    prof = plan.profile_step(b, x, MAX_ITER, RTOL, RESTART)
+    roofline = None
+    if prof:
+        roofline = roofline_entry(prof, P0, B)
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            try:
+                cpu = cpu_baseline(P0)
+                cpu.pop("iters", None)
+                cpu.pop("setup_s", None)
+            except Exception as e:  # the oracle is a baseline, never the product path
+                cpu = {"value": None, "unit": "recon/s", "cores": 1, "kind": "oracle",
+                       "sample": f"unavailable: {e}"}
+        line = {
+            "metric": METRIC, "value": value, "unit": "recon/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "256x256_180ang_363det_noise1pct", "batch_per_gpu": B,
+                       "solver": "WMG-GMRES(20), hybrid cycle depth 2, nu1=nu2=1", "levels": LEVELS,
+                       "precision": "fp32 operator, fp64 Krylov vectors/reductions/leaf solves",
+                       "rtol": RTOL, "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "iters_mean": float(np.mean(iters)), "iters_max": int(np.max(iters)),
+                       "all_converged": bool(all(s == 0 for s in statuses)),
+                       "plan_setup_s": setup_s},
+            "clocks": clocks,
+            "e2e": {"value": e2e_val, "unit": "recon/s", "h2d_bytes_per_step": int(B * M * 4),
+                    "d2h_bytes_per_step": int(B * N * 4)},
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def roofline_entry(prof: dict, P0, B: int) -> dict:
+    """Dominant kernel (larger total time of projector / backprojector). It is
+    bound by FP32 arithmetic, not memory: the algorithmic work is one
+    multiply-add (2 FLOP) per nonzero of W, against the FP32 FMA peak of 152
+    SMs x 128 lanes x 2 FLOP at the maximum SM clock. Algorithmic nnz per
+    launch = nnz(W) of the geometry x images in the launch."""
+    name = max(("project", "backproject"), key=lambda k: prof[k]["total_ms"])
+    p = prof[name]
+    nnz_per_image = prof["nnz_per_image"]
+    flops_per_launch = 2.0 * nnz_per_image * p["images_per_launch"]
+    achieved = flops_per_launch / (p["mean_ms"] * 1e-3) / 1e12
+    peaks = load_peaks()
+    clk = peaks.get("sm_max_mhz", 2070.0)
+    peak = 152 * 128 * 2 * clk * 1e6 / 1e12
+    return {"kernel": f"k_{name}", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "note": (f"{p['launches']} launches, mean {p['mean_ms']:.3f} ms, "
+                     f"{nnz_per_image * p['images_per_launch'] / (p['mean_ms'] * 1e-3) / 1e9:.0f} Gnnz/s; "
+                     f"peak derived: 152 SMs x 128 FP32 lanes x 2 FLOP x {clk:.0f} MHz")}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -84,7 +84,9 @@ typedef struct wmg_geom {
 typedef struct wmg_opts {
     int32_t levels;         /* WMG levels l >= 1; L = l-1 Haar levels, n must be
                                divisible by 2^L; leaves are (n/2^L)^2 unknowns
-                               (at most 256) and there are 4^L of them */
+                               (at most 256) and there are 4^L of them.
+                               0 = no preconditioner: operator, Haar (identity)
+                               and unpreconditioned solver calls only */
     int32_t nu1, nu2;       /* l1-Jacobi pre/post smoothing sweeps (>= 0) */
     double omega;           /* smoother damping; <= 0 means 1 */
     double lambda;          /* Tikhonov parameter >= 0 (eq. sys_reg) */
@@ -170,6 +172,31 @@ int32_t wmg_leaf_inverse(wmg_plan *plan, int64_t k, void *out, void *stream);
 int32_t wmg_solve(wmg_plan *plan, int32_t solver, int32_t preconditioned, int32_t count,
                   const void *b, void *x, int32_t max_iter, double rtol, int32_t restart,
                   wmg_solve_info *info, double *res_hist, void *stream);
+
+/* Number of nonzero intersection lengths of the plan's W (rays x pixels with
+ * a nonzero weight), counted on the device at plan creation. */
+int32_t wmg_plan_nnz(const wmg_plan *plan, int64_t *nnz);
+
+/* Library-wide count of kernel launches since the last reset (all plans of
+ * the process); reset != 0 zeroes the counter after reading it. */
+int64_t wmg_launch_count(int32_t reset);
+
+/* Per-kernel timing of the projector and backprojector launches of one plan:
+ * between wmg_profile_begin and wmg_profile_end every such launch is
+ * bracketed by CUDA events recorded on its stream (adds a few microseconds
+ * per launch; for measurement runs only). wmg_profile_end synchronises the
+ * stream and fills *out. */
+typedef struct wmg_profile_stats {
+    int32_t project_launches;
+    double project_ms;            /* summed device time */
+    double project_images;        /* summed images processed */
+    int32_t backproject_launches;
+    double backproject_ms;
+    double backproject_images;
+    double nnz_per_image;         /* nonzeros of W */
+} wmg_profile_stats;
+int32_t wmg_profile_begin(wmg_plan *plan);
+int32_t wmg_profile_end(wmg_plan *plan, wmg_profile_stats *out, void *stream);
 
 #ifdef __cplusplus
 }

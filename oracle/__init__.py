@@ -87,11 +87,18 @@ def _load():
         lib.or_wmg_apply.argtypes = [vp, _dp, _dp]
         lib.or_cgls.restype = C.c_int
         lib.or_cgls.argtypes = [vp, vp, C.c_double, _dp, _dp, C.c_int, C.c_double, C.c_void_p]
+        lib.or_set_reverse.argtypes = [C.c_int]
         lib.or_gmres.restype = C.c_int
         lib.or_gmres.argtypes = [vp, vp, C.c_double, _dp, _dp, C.c_int, C.c_int, C.c_double,
                                  C.c_void_p]
         _lib = lib
         return lib
+
+
+def set_reverse_summation(flag: bool) -> None:
+    """Run every later SpMV and dot product in reversed order (a second,
+    differently rounded evaluation of the same arithmetic)."""
+    _load().or_set_reverse(1 if flag else 0)
 
 
 def _f64(a) -> np.ndarray:

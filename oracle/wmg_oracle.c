@@ -281,14 +281,25 @@ void or_op_trig(const or_op *op, double *c, double *s)
     memcpy(s, op->s, (size_t)op->m * sizeof(double));
 }
 
+/* Summation order: 0 = natural, 1 = reversed (every SpMV row, the
+ * backprojection's row sweep and every dot product run backwards). The
+ * reversed run gives the same results up to rounding; the difference between
+ * the two runs measures how much rounding the computed iterates carry. */
+static int g_reverse = 0;
+void or_set_reverse(int r) { g_reverse = r; }
+
 /* y = W x  (one SpMV, Section 2.1) */
 void or_project(const or_op *op, const double *x, double *y)
 {
     const int64_t M = (int64_t)op->m * op->D;
     for (int64_t i = 0; i < M; i++) {
         double acc = 0.0;
-        for (int64_t q = op->rowptr[i]; q < op->rowptr[i + 1]; q++)
-            acc += op->val[q] * x[op->col[q]];
+        if (g_reverse)
+            for (int64_t q = op->rowptr[i + 1] - 1; q >= op->rowptr[i]; q--)
+                acc += op->val[q] * x[op->col[q]];
+        else
+            for (int64_t q = op->rowptr[i]; q < op->rowptr[i + 1]; q++)
+                acc += op->val[q] * x[op->col[q]];
         y[i] = acc;
     }
 }
@@ -298,9 +309,11 @@ void or_backproject(const or_op *op, const double *y, double *x)
 {
     const int64_t M = (int64_t)op->m * op->D, N = (int64_t)op->n * op->n;
     for (int64_t j = 0; j < N; j++) x[j] = 0.0;
-    for (int64_t i = 0; i < M; i++)
+    for (int64_t ii = 0; ii < M; ii++) {
+        const int64_t i = g_reverse ? M - 1 - ii : ii;
         for (int64_t q = op->rowptr[i]; q < op->rowptr[i + 1]; q++)
             x[op->col[q]] += op->val[q] * y[i];
+    }
 }
 
 /* z = (W^T W + lambda I) v  (normal-equation operator, eq. sys_reg) */
@@ -315,7 +328,10 @@ static void apply_A(const or_op *op, double lambda, const double *v, double *z, 
 static double dot(const double *a, const double *b, int64_t len)
 {
     double acc = 0.0;
-    for (int64_t i = 0; i < len; i++) acc += a[i] * b[i];
+    if (g_reverse)
+        for (int64_t i = len - 1; i >= 0; i--) acc += a[i] * b[i];
+    else
+        for (int64_t i = 0; i < len; i++) acc += a[i] * b[i];
     return acc;
 }
 

@@ -52,6 +52,13 @@ class wmg_solve_info(C.Structure):
     _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("rel_res", C.c_double)]
 
 
+class wmg_profile_stats(C.Structure):
+    _fields_ = [("project_launches", C.c_int32), ("project_ms", C.c_double),
+                ("project_images", C.c_double), ("backproject_launches", C.c_int32),
+                ("backproject_ms", C.c_double), ("backproject_images", C.c_double),
+                ("nnz_per_image", C.c_double)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -70,6 +77,10 @@ _SIGNATURES = {
     "wmg_leaf_inverse": (_i32, [_vp, _i64, _vp, _vp]),
     "wmg_solve": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _i32, _dbl, _i32,
                          C.POINTER(wmg_solve_info), C.POINTER(_dbl), _vp]),
+    "wmg_plan_nnz": (_i32, [_vp, C.POINTER(_i64)]),
+    "wmg_launch_count": (_i64, [_i32]),
+    "wmg_profile_begin": (_i32, [_vp]),
+    "wmg_profile_end": (_i32, [_vp, C.POINTER(wmg_profile_stats), _vp]),
 }
 
 
@@ -156,6 +167,26 @@ def wmg_solve(plan, solver, preconditioned, count, b, x, max_iter, rtol, restart
                                   info, res_hist, stream), allow_not_converged=True)
 
 
+def wmg_plan_nnz(plan) -> int:
+    v = _i64()
+    _check(lib().wmg_plan_nnz(plan, C.byref(v)))
+    return v.value
+
+
+def wmg_launch_count(reset: bool = False) -> int:
+    return lib().wmg_launch_count(1 if reset else 0)
+
+
+def wmg_profile_begin(plan):
+    _check(lib().wmg_profile_begin(plan))
+
+
+def wmg_profile_end(plan, stream=None) -> wmg_profile_stats:
+    out = wmg_profile_stats()
+    _check(lib().wmg_profile_end(plan, C.byref(out), stream))
+    return out
+
+
 # ---- torch convenience wrapper ---------------------------------------------
 class Plan:
     """A plan for one geometry; methods take torch CUDA tensors of the plan's
@@ -177,8 +208,8 @@ class Plan:
         self.dtype = torch.float64 if precision == PREC_F64 else torch.float32
         self.n, self.m, self.D = n, m, D
         self.N, self.M = n * n, m * D
-        self.K = 4 ** (levels - 1)
-        self.P = (n >> (levels - 1)) ** 2
+        self.K = 4 ** (levels - 1) if levels >= 1 else 0
+        self.P = (n >> (levels - 1)) ** 2 if levels >= 1 else 0
         self.handle = wmg_plan_create(self.geom, self.opts, self._stream())
 
     def _stream(self):
@@ -237,6 +268,28 @@ class Plan:
         out = self._torch.empty(self.P * self.P, dtype=self.dtype, device="cuda")
         wmg_leaf_inverse(self.handle, k, C.c_void_p(out.data_ptr()), self._stream())
         return out.view(self.P, self.P)
+
+    def nnz(self) -> int:
+        return wmg_plan_nnz(self.handle)
+
+    def launch_count(self, reset=False) -> int:
+        """Library kernel launches since the last reset (process-wide)."""
+        return wmg_launch_count(reset)
+
+    def profile_step(self, b, out, max_iter, rtol, restart, solver=SOLVER_GMRES, preconditioned=True):
+        """One solve with CUDA events around every projector / backprojector
+        launch; returns per-kernel totals."""
+        wmg_profile_begin(self.handle)
+        self.solve(b, solver, preconditioned, max_iter, rtol, restart, out=out)
+        st = wmg_profile_end(self.handle, self._stream())
+        res = {"nnz_per_image": st.nnz_per_image}
+        for k in ("project", "backproject"):
+            n = getattr(st, k + "_launches")
+            ms = getattr(st, k + "_ms")
+            imgs = getattr(st, k + "_images")
+            res[k] = {"launches": n, "total_ms": ms, "mean_ms": ms / max(n, 1),
+                      "images_per_launch": imgs / max(n, 1)}
+        return res
 
     def solve(self, b, solver=SOLVER_CGLS, preconditioned=True, max_iter=100, rtol=1e-4, restart=20,
               out=None, history=False):

@@ -3,6 +3,7 @@
 // drivers. Every arithmetic step runs in the kernels of projector.cu,
 // haar.cu, setup.cu and krylov.cu; this file only orders launches.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -25,6 +26,9 @@ int32_t fail(int32_t code, const std::string &msg)
     g_last_error = msg;
     return code;
 }
+
+static std::atomic<long long> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 int num_sms()
 {
@@ -145,7 +149,7 @@ struct wmg_plan {
     wmg::GeomDev g{};           // host copy (device pointers inside)
     wmg_opts opts{};
     int64_t N = 0, M = 0;
-    wmg::DevBuf d_geom, cs64, cs32, dinv, leafinv, sirtR, sirtC;
+    wmg::DevBuf d_geom, cs64, cs32, csx, dinv, leafinv, sirtR, sirtC;
     int cap = 0;                // problems the tables are built for
     wmg::ProbSet real;
     std::map<std::vector<int>, std::unique_ptr<wmg::ProbSet>> bands;   // band-update groups
@@ -163,6 +167,12 @@ struct wmg_plan {
     // GMRES
     wmg::DevBuf V, H, gcs, gsn, gg, gy, h1, h2, jn, done;
     int gm_restart = 0;
+    bool has_wmg = true;        // levels >= 1: the WMG preconditioner is set up
+    int64_t nnz = 0;            // nonzeros of W
+    // profiling: (kind 0 = project / 1 = backproject, images, start, stop)
+    bool profiling = false;
+    struct ProfRec { int kind; int images; cudaEvent_t e0, e1; };
+    std::vector<ProfRec> prof;
 };
 
 namespace wmg {
@@ -245,20 +255,34 @@ static bool ensure_partials(wmg_plan *pl, size_t per_tile_max)
 // ---------------------------------------------------------------------------
 // Operator steps
 // ---------------------------------------------------------------------------
+static void prof_begin(wmg_plan *pl, int kind, int images, cudaStream_t st)
+{
+    wmg_plan::ProfRec r{kind, images, nullptr, nullptr};
+    cudaEventCreate(&r.e0);
+    cudaEventCreate(&r.e1);
+    cudaEventRecord(r.e0, st);
+    pl->prof.push_back(r);
+}
+static void prof_end(wmg_plan *pl, cudaStream_t st) { cudaEventRecord(pl->prof.back().e1, st); }
+
 template <class T>
 static void project(wmg_plan *pl, const ProbSet &ps, const void *img, const void *imgT, void *sino,
                     double *part, const double *S, cudaStream_t st)
 {
     PjArgs a{img, imgT, sino, part, S};
+    if (pl->profiling) prof_begin(pl, 0, ps.nprob, st);
     launch_project<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.proj.tiles.as<int4>(),
                       ps.proj.n, a, st);
+    if (pl->profiling) prof_end(pl, st);
 }
 
 template <class T>
 static void backproject(wmg_plan *pl, const ProbSet &ps, BpArgs a, cudaStream_t st)
 {
+    if (pl->profiling) prof_begin(pl, 1, ps.nprob, st);
     launch_backproject<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.bp.tiles.as<int4>(),
                           ps.bp.n, a, st);
+    if (pl->profiling) prof_end(pl, st);
 }
 
 static BpArgs bp_args(int epi, const void *sino, const double *S)
@@ -288,7 +312,8 @@ static void vec_op(wmg_plan *pl, int op, bool sino, VecArgs a, cudaStream_t st)
 
 static void finalize(wmg_plan *pl, int op, const TileList &ta, const double *pa, int nsum,
                      const TileList *tb, const double *pb, int precond, double *hist, int hist_ld,
-                     cudaStream_t st, int store_slot = 0, double *store_vec = nullptr, int store_ld = 0)
+                     cudaStream_t st, int store_slot = 0, double *store_vec = nullptr, int store_ld = 0,
+                     int part_ld = 1)
 {
     FinArgs f{};
     f.op = op;
@@ -297,7 +322,7 @@ static void finalize(wmg_plan *pl, int op, const TileList &ta, const double *pa,
     f.part_a = pa;
     f.tb_a = ta.tb.as<int>();
     f.te_a = ta.te.as<int>();
-    f.ld_a = std::max(1, nsum);
+    f.ld_a = std::max(part_ld, std::max(1, nsum));
     f.nsum_a = std::max(1, nsum);
     f.part_b = pb;
     f.tb_b = tb ? tb->tb.as<int>() : nullptr;
@@ -384,7 +409,7 @@ static int32_t band_update(wmg_plan *pl, const std::vector<Node> &nodes, bool fu
     if (!bs) return fail(WMG_ERR_OOM, "band tables");
     const int64_t V = bs->nprob;
     if (!ensure_pool(pl->band_img, V * pl->N, pl->esz) || !ensure_pool(pl->band_imgT, V * pl->N, pl->esz) ||
-        !ensure_pool(pl->band_img2, V * pl->N, pl->esz) || !ensure_pool(pl->band_sino, V * pl->M, pl->esz))
+        !ensure_pool(pl->band_img2, V * pl->N, 8) || !ensure_pool(pl->band_sino, V * pl->M, pl->esz))
         return fail(WMG_ERR_OOM, "band pools");
     const GeomDev *G = pl->d_geom.as<GeomDev>();
     const double *S = pl->S.as<double>();
@@ -394,20 +419,20 @@ static int32_t band_update(wmg_plan *pl, const std::vector<Node> &nodes, bool fu
     hs.out = pl->band_img.p;
     hs.outT = pl->band_imgT.p;
     hs.S = S;
-    launch_haar_synthesis<T>(G, bs->d.as<ProbDev>(), bs->haar.tiles.as<int4>(), bs->haar.n,
-                             bs->haar_smem, hs, st);
+    launch_haar_synthesis<double, T>(G, bs->d.as<ProbDev>(), bs->haar.tiles.as<int4>(), bs->haar.n,
+                                     bs->haar_smem, hs, st);
     project<T>(pl, *bs, pl->band_img.p, pl->band_imgT.p, pl->band_sino.p, nullptr, S, st);
     BpArgs a = bp_args(BP_APPLY_A, pl->band_sino.p, S);
     a.v_op = pl->band_img.p;
-    a.out_op = pl->band_img2.p;
+    a.out64 = pl->band_img2.as<double>();
     backproject<T>(pl, *bs, a, st);
     HaarArgs ha{};
     ha.mode = HA_SUB_MASKED;
     ha.in = pl->band_img2.p;
     ha.out = Cb.p;
     ha.S = S;
-    launch_haar_analysis<T>(G, bs->d.as<ProbDev>(), bs->haar.tiles.as<int4>(), bs->haar.n,
-                            bs->haar_smem, ha, st);
+    launch_haar_analysis<double, double>(G, bs->d.as<ProbDev>(), bs->haar.tiles.as<int4>(), bs->haar.n,
+                                         bs->haar_smem, ha, st);
     return WMG_OK;
 }
 
@@ -425,8 +450,8 @@ static int32_t coarse(wmg_plan *pl, int d, const std::vector<Node> &nodes, DevBu
     if (d >= hd) {
         TileList *lt = leaf_tiles(pl, nodes, st);
         if (!lt) return fail(WMG_ERR_OOM, "leaf tables");
-        launch_leaf_apply<T>(pl->d_geom.as<GeomDev>(), pl->real.d.as<ProbDev>(), lt->tiles.as<int4>(),
-                             lt->n, Cb.p, Eb.p, 0, pl->S.as<double>(), st);
+        launch_leaf_apply(pl->d_geom.as<GeomDev>(), pl->real.d.as<ProbDev>(), lt->tiles.as<int4>(),
+                          lt->n, Cb.as<double>(), Eb.as<double>(), 0, pl->S.as<double>(), st);
         return WMG_OK;
     }
     std::vector<Node> lls, rests;
@@ -436,7 +461,7 @@ static int32_t coarse(wmg_plan *pl, int d, const std::vector<Node> &nodes, DevBu
         for (int c = 1; c < 4; ++c) rests.push_back({nd.k0 + c * qq, nd.k0 + (c + 1) * qq});
     }
     const bool sym = o.cycle == WMG_CYCLE_SYMMETRIC;
-    const size_t cbytes = (size_t)pl->cap * pl->N * pl->esz;
+    const size_t cbytes = (size_t)pl->cap * pl->N * sizeof(double);
     if (sym) cudaMemcpyAsync(pl->csave[d]->p, Cb.p, cbytes, cudaMemcpyDeviceToDevice, st);
     int32_t rc = coarse<T>(pl, d + 1, lls, Cb, Eb, st);
     if (rc) return rc;
@@ -460,8 +485,10 @@ static int32_t coarse(wmg_plan *pl, int d, const std::vector<Node> &nodes, DevBu
             cudaMemcpy(db->p, segs.data(), segs.size() * sizeof(int2), cudaMemcpyHostToDevice);
             it = pl->segsets.emplace(key, std::move(db)).first;
         }
-        k_coef_add<T><<<num_sms() * 4, 256, 0, st>>>(Eb.as<T>(), E2.as<T>(), it->second->as<int2>(),
-                                                      (int)segs.size(), pl->N, pl->cap);
+        count_launches(1);
+        k_coef_add<double><<<num_sms() * 4, 256, 0, st>>>(Eb.as<double>(), E2.as<double>(),
+                                                           it->second->as<int2>(), (int)segs.size(),
+                                                           pl->N, pl->cap);
     }
     return WMG_OK;
 }
@@ -471,8 +498,8 @@ static int32_t ensure_wmg_pools(wmg_plan *pl)
     const int64_t nN = (int64_t)pl->cap * pl->N, nM = (int64_t)pl->cap * pl->M;
     const size_t e = pl->esz;
     if (!ensure_pool(pl->z, nN, 8) || !ensure_pool(pl->s, nN, 8) || !ensure_pool(pl->z_op, nN, e) ||
-        !ensure_pool(pl->zT_op, nN, e) || !ensure_pool(pl->r1, nN, e) || !ensure_pool(pl->C, nN, e) ||
-        !ensure_pool(pl->E, nN, e) || !ensure_pool(pl->sinoS, nM, e))
+        !ensure_pool(pl->zT_op, nN, e) || !ensure_pool(pl->r1, nN, 8) || !ensure_pool(pl->C, nN, 8) ||
+        !ensure_pool(pl->E, nN, 8) || !ensure_pool(pl->sinoS, nM, e))
         return fail(WMG_ERR_OOM, "preconditioner pools");
     const int L = pl->g.L;
     while ((int)pl->csave.size() < L) {
@@ -482,8 +509,8 @@ static int32_t ensure_wmg_pools(wmg_plan *pl)
     }
     if (pl->opts.cycle == WMG_CYCLE_SYMMETRIC)
         for (int d = 0; d < std::min(pl->opts.hybrid_depth, L); ++d)
-            if (!ensure_pool(*pl->csave[d], nN, e) || !ensure_pool(*pl->c2[d], nN, e) ||
-                !ensure_pool(*pl->e2[d], nN, e))
+            if (!ensure_pool(*pl->csave[d], nN, 8) || !ensure_pool(*pl->c2[d], nN, 8) ||
+                !ensure_pool(*pl->e2[d], nN, 8))
                 return fail(WMG_ERR_OOM, "symmetric-cycle pools");
     return WMG_OK;
 }
@@ -514,7 +541,7 @@ static int32_t wmg_apply(wmg_plan *pl, double *s, double *z, bool first_done, bo
         }
         project<T>(pl, ps, pl->z_op.p, pl->zT_op.p, pl->sinoS.p, nullptr, S, st);
         BpArgs a = bp_args(BP_RESID, pl->sinoS.p, S);
-        a.s = s; a.z = z; a.out_op = pl->r1.p;
+        a.s = s; a.z = z; a.out64 = pl->r1.as<double>();
         backproject<T>(pl, ps, a, st);
     } else {
         ImgArgs ia{};
@@ -524,7 +551,8 @@ static int32_t wmg_apply(wmg_plan *pl, double *s, double *z, bool first_done, bo
     const GeomDev *G = pl->d_geom.as<GeomDev>();
     HaarArgs ha{};
     ha.mode = HA_STORE; ha.in = pl->r1.p; ha.out = pl->C.p; ha.S = S;
-    launch_haar_analysis<T>(G, ps.d.as<ProbDev>(), ps.haar.tiles.as<int4>(), ps.haar.n, ps.haar_smem, ha, st);
+    launch_haar_analysis<double, double>(G, ps.d.as<ProbDev>(), ps.haar.tiles.as<int4>(), ps.haar.n,
+                                         ps.haar_smem, ha, st);
     std::vector<Node> root{{0, pl->g.K}};
     int32_t rc = coarse<T>(pl, 0, root, pl->C, pl->E, st);
     if (rc) return rc;
@@ -533,7 +561,8 @@ static int32_t wmg_apply(wmg_plan *pl, double *s, double *z, bool first_done, bo
     hs.mode = HS_CORRECT; hs.in = pl->E.p; hs.z = z; hs.S = S;
     hs.out = need_copies_after_syn ? pl->z_op.p : nullptr;
     hs.outT = need_copies_after_syn ? pl->zT_op.p : nullptr;
-    launch_haar_synthesis<T>(G, ps.d.as<ProbDev>(), ps.haar.tiles.as<int4>(), ps.haar.n, ps.haar_smem, hs, st);
+    launch_haar_synthesis<double, T>(G, ps.d.as<ProbDev>(), ps.haar.tiles.as<int4>(), ps.haar.n,
+                                     ps.haar_smem, hs, st);
     for (int it = 0; it < o.nu2; ++it) {
         const bool last = it == o.nu2 - 1;
         project<T>(pl, ps, pl->z_op.p, pl->zT_op.p, pl->sinoS.p, nullptr, S, st);
@@ -555,6 +584,11 @@ __global__ void k_fill(T *p, int64_t n, T v)
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = v;
 }
+__global__ void k_to_f32(const double *in, float *out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
 // out = 1 / (in + add) where positive, else 0
 template <class T>
 __global__ void k_recip(const T *in, T *out, int64_t n, double add)
@@ -574,6 +608,7 @@ static int32_t setup_geometry(wmg_plan *pl, cudaStream_t st)
         !tmp_img.ensure(N * sizeof(T)) || !tmp_sino.ensure(M * sizeof(T)) ||
         !pl->dinv.ensure(N * sizeof(T)) || !pl->sirtR.ensure(M * sizeof(T)) || !pl->sirtC.ensure(N * sizeof(T)))
         return fail(WMG_ERR_OOM, "setup allocation failed");
+    count_launches(5);
     k_fill<T><<<num_sms() * 4, 256, 0, st>>>(ones_img.as<T>(), N, T(1));
     k_fill<T><<<num_sms() * 4, 256, 0, st>>>(ones_sino.as<T>(), M, T(1));
     const ProbSet &ps = pl->real;
@@ -588,16 +623,27 @@ static int32_t setup_geometry(wmg_plan *pl, cudaStream_t st)
     a.out_op = tmp_img.p;
     backproject<T>(pl, ps, a, st);
     k_recip<T><<<num_sms() * 4, 256, 0, st>>>(tmp_img.as<T>(), pl->sirtC.as<T>(), N, 0.0);
+    unsigned long long *dcount = nullptr;
+    WMG_CUDA(cudaMalloc(&dcount, sizeof(unsigned long long)));
+    cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), st);
+    launch_count_nnz(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.proj.tiles.as<int4>(), ps.proj.n,
+                     dcount, st);
+    unsigned long long hcount = 0;
+    cudaMemcpyAsync(&hcount, dcount, sizeof(hcount), cudaMemcpyDeviceToHost, st);
     WMG_CUDA(cudaStreamSynchronize(st));
+    cudaFree(dcount);
+    pl->nnz = (int64_t)hcount;
     WMG_CUDA(cudaGetLastError());
     pl->g.dinv = pl->dinv.p;
     pl->g.sirtR = pl->sirtR.p;
     pl->g.sirtC = pl->sirtC.p;
-    if (!pl->leafinv.ensure((size_t)pl->g.K * pl->g.P * pl->g.P * sizeof(T)))
-        return fail(WMG_ERR_OOM, "leaf inverse allocation failed");
-    pl->g.leafinv = pl->leafinv.p;
     WMG_CUDA(cudaMemcpyAsync(pl->d_geom.p, &pl->g, sizeof(GeomDev), cudaMemcpyHostToDevice, st));
-    int32_t rc = build_leaf_inverses<T>(pl->g, pl->d_geom.as<GeomDev>(), pl->leafinv.p, st);
+    if (!pl->has_wmg) return WMG_OK;
+    if (!pl->leafinv.ensure((size_t)pl->g.K * pl->g.P * pl->g.P * sizeof(double)))
+        return fail(WMG_ERR_OOM, "leaf inverse allocation failed");
+    pl->g.leafinv = pl->leafinv.as<double>();
+    WMG_CUDA(cudaMemcpyAsync(pl->d_geom.p, &pl->g, sizeof(GeomDev), cudaMemcpyHostToDevice, st));
+    int32_t rc = build_leaf_inverses(pl->g, pl->d_geom.as<GeomDev>(), pl->leafinv.as<double>(), st);
     if (rc) return rc;
     WMG_CUDA(cudaGetLastError());
     return WMG_OK;
@@ -627,11 +673,12 @@ extern "C" int32_t wmg_plan_create(const wmg_geom *g, const wmg_opts *o, void *s
     *out = nullptr;
     if (!g || !o) return fail(WMG_ERR_INVALID_ARG, "geometry or options NULL");
     if (g->n < 1 || g->m < 1 || g->D < 1) return fail(WMG_ERR_INVALID_ARG, "n, m and D must be >= 1");
-    if (o->levels < 1 || o->levels > 12) return fail(WMG_ERR_INVALID_ARG, "levels must be in [1, 12]");
-    const int L = o->levels - 1;
+    if (o->levels < 0 || o->levels > 12) return fail(WMG_ERR_INVALID_ARG, "levels must be in [0, 12]");
+    const bool has_wmg = o->levels >= 1;
+    const int L = has_wmg ? o->levels - 1 : 0;
     if (g->n % (1 << L) != 0) return fail(WMG_ERR_INVALID_ARG, "n must be divisible by 2^(levels-1)");
     const int nc = g->n >> L;
-    if (nc * nc > 256) return fail(WMG_ERR_INVALID_ARG, "leaf side n/2^(levels-1) must be <= 16");
+    if (has_wmg && nc * nc > 256) return fail(WMG_ERR_INVALID_ARG, "leaf side n/2^(levels-1) must be <= 16");
     if ((1 << L) > 128) return fail(WMG_ERR_INVALID_ARG, "block side 2^(levels-1) must be <= 128");
     if (o->nu1 < 0 || o->nu2 < 0 || o->lambda < 0 || o->hybrid_depth < 0 ||
         o->cycle < WMG_CYCLE_ADDITIVE || o->cycle > WMG_CYCLE_SYMMETRIC ||
@@ -644,6 +691,7 @@ extern "C" int32_t wmg_plan_create(const wmg_geom *g, const wmg_opts *o, void *s
     pl->prec = o->precision;
     pl->esz = o->precision == WMG_PREC_F64 ? 8 : 4;
     pl->opts = *o;
+    pl->has_wmg = has_wmg;
     if (pl->opts.omega <= 0) pl->opts.omega = 1.0;
     pl->N = (int64_t)g->n * g->n;
     pl->M = (int64_t)g->m * g->D;
@@ -658,14 +706,23 @@ extern "C" int32_t wmg_plan_create(const wmg_geom *g, const wmg_opts *o, void *s
     std::vector<double2> cs;
     angle_table(g->m, g->angles, cs);
     std::vector<float2> cs32(g->m);
-    for (int a = 0; a < g->m; ++a) cs32[a] = make_float2((float)cs[a].x, (float)cs[a].y);
+    std::vector<float4> csx(g->m);
+    for (int a = 0; a < g->m; ++a) {
+        cs32[a] = make_float2((float)cs[a].x, (float)cs[a].y);
+        // split: 12-significant-bit head (a multiple of 2^-12) and FP32 tail
+        const double ch = std::nearbyint(cs[a].x * 4096.0) / 4096.0;
+        const double sh = std::nearbyint(cs[a].y * 4096.0) / 4096.0;
+        csx[a] = make_float4((float)ch, (float)(cs[a].x - ch), (float)sh, (float)(cs[a].y - sh));
+    }
     if (!pl->cs64.ensure(g->m * sizeof(double2)) || !pl->cs32.ensure(g->m * sizeof(float2)) ||
-        !pl->d_geom.ensure(sizeof(GeomDev)))
+        !pl->csx.ensure(g->m * sizeof(float4)) || !pl->d_geom.ensure(sizeof(GeomDev)))
         return fail(WMG_ERR_OOM, "plan allocation failed");
+    WMG_CUDA(cudaMemcpyAsync(pl->csx.p, csx.data(), g->m * sizeof(float4), cudaMemcpyHostToDevice, st));
     WMG_CUDA(cudaMemcpyAsync(pl->cs64.p, cs.data(), g->m * sizeof(double2), cudaMemcpyHostToDevice, st));
     WMG_CUDA(cudaMemcpyAsync(pl->cs32.p, cs32.data(), g->m * sizeof(float2), cudaMemcpyHostToDevice, st));
     gd.cs64 = pl->cs64.as<double2>();
     gd.cs32 = pl->cs32.as<float2>();
+    gd.csx = pl->csx.as<float4>();
     WMG_CUDA(cudaMemcpyAsync(pl->d_geom.p, &gd, sizeof(GeomDev), cudaMemcpyHostToDevice, st));
     int32_t rc = ensure_count(pl.get(), 1, st);
     if (rc) return rc;
@@ -681,6 +738,46 @@ extern "C" int32_t wmg_plan_destroy(wmg_plan *plan)
     if (!plan) return WMG_OK;
     cudaDeviceSynchronize();
     delete plan;
+    return WMG_OK;
+}
+
+extern "C" int32_t wmg_plan_nnz(const wmg_plan *plan, int64_t *nnz)
+{
+    if (!plan || !nnz) return fail(WMG_ERR_INVALID_ARG, "wmg_plan_nnz: bad arguments");
+    *nnz = plan->nnz;
+    return WMG_OK;
+}
+
+extern "C" int64_t wmg_launch_count(int32_t reset)
+{
+    return reset ? g_launches.exchange(0) : g_launches.load();
+}
+
+extern "C" int32_t wmg_profile_begin(wmg_plan *plan)
+{
+    if (!plan) return fail(WMG_ERR_INVALID_ARG, "wmg_profile_begin: plan is NULL");
+    for (auto &r : plan->prof) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+    plan->prof.clear();
+    plan->profiling = true;
+    return WMG_OK;
+}
+
+extern "C" int32_t wmg_profile_end(wmg_plan *plan, wmg_profile_stats *out, void *stream)
+{
+    if (!plan || !out) return fail(WMG_ERR_INVALID_ARG, "wmg_profile_end: bad arguments");
+    plan->profiling = false;
+    WMG_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    std::memset(out, 0, sizeof(*out));
+    for (auto &r : plan->prof) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.e0, r.e1);
+        if (r.kind == 0) { out->project_launches++; out->project_ms += ms; out->project_images += r.images; }
+        else { out->backproject_launches++; out->backproject_ms += ms; out->backproject_images += r.images; }
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+    }
+    plan->prof.clear();
+    out->nnz_per_image = (double)plan->nnz;
     return WMG_OK;
 }
 
@@ -745,10 +842,10 @@ static int32_t do_haar(wmg_plan *pl, bool analysis, const void *in, void *out, c
     a.out = out;
     if (analysis) {
         a.mode = HA_STORE;
-        launch_haar_analysis<T>(G, ps.d.as<ProbDev>(), ps.haar.tiles.as<int4>(), ps.haar.n, ps.haar_smem, a, st);
+        launch_haar_analysis<T, T>(G, ps.d.as<ProbDev>(), ps.haar.tiles.as<int4>(), ps.haar.n, ps.haar_smem, a, st);
     } else {
         a.mode = HS_STORE;
-        launch_haar_synthesis<T>(G, ps.d.as<ProbDev>(), ps.haar.tiles.as<int4>(), ps.haar.n, ps.haar_smem, a, st);
+        launch_haar_synthesis<T, T>(G, ps.d.as<ProbDev>(), ps.haar.tiles.as<int4>(), ps.haar.n, ps.haar_smem, a, st);
     }
     WMG_CUDA(cudaGetLastError());
     return WMG_OK;
@@ -774,10 +871,16 @@ extern "C" int32_t wmg_haar_synthesis(wmg_plan *pl, int32_t count, const void *c
 
 extern "C" int32_t wmg_leaf_inverse(wmg_plan *pl, int64_t k, void *out, void *stream)
 {
-    if (!pl || !out || k < 0 || k >= pl->g.K) return fail(WMG_ERR_INVALID_ARG, "wmg_leaf_inverse: bad arguments");
-    const size_t bytes = (size_t)pl->g.P * pl->g.P * pl->esz;
-    WMG_CUDA(cudaMemcpyAsync(out, static_cast<char *>(pl->leafinv.p) + k * bytes, bytes,
-                             cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
+    if (!pl || !out || k < 0 || k >= pl->g.K || !pl->has_wmg)
+        return fail(WMG_ERR_INVALID_ARG, "wmg_leaf_inverse: bad arguments (or a plan without WMG levels)");
+    const int64_t PP = (int64_t)pl->g.P * pl->g.P;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (pl->prec == WMG_PREC_F64)
+        WMG_CUDA(cudaMemcpyAsync(out, pl->leafinv.as<double>() + k * PP, PP * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, st));
+    else
+        count_launches(1), k_to_f32<<<num_sms(), 256, 0, st>>>(pl->leafinv.as<double>() + k * PP, static_cast<float *>(out), PP);
+    WMG_CUDA(cudaGetLastError());
     return WMG_OK;
 }
 
@@ -820,6 +923,7 @@ static int32_t do_precond(wmg_plan *pl, const void *s_in, void *z_out, cudaStrea
 extern "C" int32_t wmg_precond_apply(wmg_plan *pl, int32_t count, const void *s, void *z, void *stream)
 {
     if (!pl || !s || !z || count < 1) return fail(WMG_ERR_INVALID_ARG, "wmg_precond_apply: bad arguments");
+    if (!pl->has_wmg) return fail(WMG_ERR_INVALID_ARG, "wmg_precond_apply: the plan has no WMG levels");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int32_t rc = ensure_count(pl, count, st);
     if (rc) return rc;
@@ -1080,7 +1184,8 @@ static int32_t solve_gmres(wmg_plan *pl, bool pre, int count, const void *b, voi
                 launch_gm_dots(ps.d.as<ProbDev>(), ps.vimg.tiles.as<int4>(), ps.vimg.n, V, vstride,
                                pl->w.as<double>(), j, ldp, pa, S, st);
                 double *hv = pass == 0 ? pl->h1.as<double>() : pl->h2.as<double>();
-                finalize(pl, FIN_STORE, ps.vimg, pa, j + 1, nullptr, nullptr, 0, nullptr, 0, st, 0, hv, ldp);
+                finalize(pl, FIN_STORE, ps.vimg, pa, j + 1, nullptr, nullptr, 0, nullptr, 0, st, 0, hv, ldp,
+                         ldp);
                 launch_gm_axpy(ps.d.as<ProbDev>(), ps.vimg.tiles.as<int4>(), ps.vimg.n, V, vstride,
                                pl->w.as<double>(), j, ldp, hv, pass == 1 ? pb : nullptr, S, st);
             }
@@ -1157,6 +1262,8 @@ extern "C" int32_t wmg_solve(wmg_plan *pl, int32_t solver, int32_t preconditione
         return fail(WMG_ERR_INVALID_ARG, "wmg_solve: bad arguments");
     if (solver == WMG_SOLVER_GMRES && (restart < 1 || restart > 64))
         return fail(WMG_ERR_INVALID_ARG, "wmg_solve: restart must be in [1, 64]");
+    if (preconditioned && !pl->has_wmg && solver != WMG_SOLVER_SIRT)
+        return fail(WMG_ERR_INVALID_ARG, "wmg_solve: the plan has no WMG levels to precondition with");
     if (solver == WMG_SOLVER_CGLS && preconditioned && pl->opts.cycle == WMG_CYCLE_HYBRID)
         return fail(WMG_ERR_INVALID_ARG, "CGLS needs a symmetric preconditioner (ADDITIVE or SYMMETRIC cycle)");
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -37,8 +37,7 @@ __device__ __forceinline__ int leaf_of(int uy, int ux, int L)
 
 // In-place Walsh-Hadamard butterflies over a B x W strip in shared memory
 // (pitch pw), along x (within every B-wide segment) then along y.
-template <class T>
-__device__ __forceinline__ void strip_wht(T *sm, int B, int W, int L, int pw)
+__device__ __forceinline__ void strip_wht(double *sm, int B, int W, int L, int pw)
 {
     const int halfx = B * (W >> 1);
     for (int st = 0; st < L; ++st) {
@@ -46,8 +45,8 @@ __device__ __forceinline__ void strip_wht(T *sm, int B, int W, int L, int pw)
         for (int q = threadIdx.x; q < halfx; q += blockDim.x) {
             const int r = q / (W >> 1), pi = q - r * (W >> 1);
             const int i = ((pi >> st) << (st + 1)) | (pi & (hbit - 1));
-            T *row = sm + r * pw;
-            const T a = row[i], b = row[i + hbit];
+            double *row = sm + r * pw;
+            const double a = row[i], b = row[i + hbit];
             row[i] = a + b;
             row[i + hbit] = a - b;
         }
@@ -59,7 +58,7 @@ __device__ __forceinline__ void strip_wht(T *sm, int B, int W, int L, int pw)
         for (int q = threadIdx.x; q < halfy; q += blockDim.x) {
             const int col = q % W, pi = q / W;
             const int i = ((pi >> st) << (st + 1)) | (pi & (hbit - 1));
-            const T a = sm[i * pw + col], b = sm[(i + hbit) * pw + col];
+            const double a = sm[i * pw + col], b = sm[(i + hbit) * pw + col];
             sm[i * pw + col] = a + b;
             sm[(i + hbit) * pw + col] = a - b;
         }
@@ -67,34 +66,35 @@ __device__ __forceinline__ void strip_wht(T *sm, int B, int W, int L, int pw)
     }
 }
 
-// Analysis: tile = {prob, y0, x0, W}; strip of B rows x W columns.
-template <class T, int MODE>
+// Analysis: tile = {prob, y0, x0, W}; strip of B rows x W columns. The
+// butterflies run in FP64 whatever the storage types.
+template <class TIn, class TOut, int MODE>
 __global__ void __launch_bounds__(256)
 k_haar_analysis(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
                 const int4 *__restrict__ tiles, int ntiles, HaarArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *sm = reinterpret_cast<T *>(smraw);
+    double *sm = reinterpret_cast<double *>(smraw);
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 tl = tiles[t];
         const ProbDev pd = P[tl.x];
         if (!slot_active(a.S, pd.slot)) continue;
         const GeomDev &g = G[pd.geom];
         const int n = g.n, B = g.B, L = g.L, W = tl.w, pw = W + 1;
-        const T *in = static_cast<const T *>(a.in) + pd.img;
+        const TIn *in = static_cast<const TIn *>(a.in) + pd.img;
         for (int q = threadIdx.x; q < B * W; q += blockDim.x) {
             const int r = q / W, x = q - r * W;
-            sm[r * pw + x] = in[(int64_t)(tl.y + r) * n + tl.z + x];
+            sm[r * pw + x] = (double)in[(int64_t)(tl.y + r) * n + tl.z + x];
         }
         __syncthreads();
         strip_wht(sm, B, W, L, pw);
-        const T scale = T(1) / T(B);
+        const double scale = 1.0 / (double)B;
         const int nb = W / B, cy = tl.y / B, cx0 = tl.z / B;
-        T *C = static_cast<T *>(a.out) + pd.coef;
+        TOut *C = static_cast<TOut *>(a.out) + pd.coef;
         for (int q = threadIdx.x; q < B * W; q += blockDim.x) {
             const int bc = q % nb, rest = q / nb, ux = rest % B, uy = rest / B;
             const int k = leaf_of(uy, ux, L);
-            const T v = sm[uy * pw + bc * B + ux] * scale;
+            const TOut v = (TOut)(sm[uy * pw + bc * B + ux] * scale);
             const int64_t o = (int64_t)k * g.P + (int64_t)cy * g.nc + cx0 + bc;
             if (MODE == HA_STORE) C[o] = v;
             else if (k >= pd.kout0 && k < pd.kout1) {
@@ -106,14 +106,14 @@ k_haar_analysis(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
     }
 }
 
-// Synthesis: the transpose of the analysis.
-template <class T, int MODE>
+// Synthesis: the transpose of the analysis (FP64 butterflies).
+template <class TIn, class TOut, int MODE>
 __global__ void __launch_bounds__(256)
 k_haar_synthesis(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
                  const int4 *__restrict__ tiles, int ntiles, HaarArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *sm = reinterpret_cast<T *>(smraw);
+    double *sm = reinterpret_cast<double *>(smraw);
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 tl = tiles[t];
         const ProbDev pd = P[tl.x];
@@ -121,40 +121,41 @@ k_haar_synthesis(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
         const GeomDev &g = G[pd.geom];
         const int n = g.n, B = g.B, L = g.L, W = tl.w, pw = W + 1;
         const int nb = W / B, cy = tl.y / B, cx0 = tl.z / B;
-        const T *E = static_cast<const T *>(a.in) + pd.coef;
+        const TIn *E = static_cast<const TIn *>(a.in) + pd.coef;
         for (int q = threadIdx.x; q < B * W; q += blockDim.x) {
             const int bc = q % nb, rest = q / nb, ux = rest % B, uy = rest / B;
             const int k = leaf_of(uy, ux, L);
-            T v = T(0);
+            double v = 0.0;
             if (MODE != HS_STORE_MASKED || (k >= pd.kin0 && k < pd.kin1))
-                v = E[(int64_t)k * g.P + (int64_t)cy * g.nc + cx0 + bc];
+                v = (double)E[(int64_t)k * g.P + (int64_t)cy * g.nc + cx0 + bc];
             sm[uy * pw + bc * B + ux] = v;
         }
         __syncthreads();
         strip_wht(sm, B, W, L, pw);
-        const T scale = T(1) / T(B);
-        T *out = static_cast<T *>(a.out);
+        const double scale = 1.0 / (double)B;
+        TOut *out = static_cast<TOut *>(a.out);
         for (int q = threadIdx.x; q < B * W; q += blockDim.x) {
             const int r = q / W, x = q - r * W;
             const int64_t j = pd.img + (int64_t)(tl.y + r) * n + tl.z + x;
-            const T v = sm[r * pw + x] * scale;
+            const double v = sm[r * pw + x] * scale;
             if (MODE == HS_CORRECT) {
-                const double zv = a.z[j] + (double)v;
+                const double zv = a.z[j] + v;
                 a.z[j] = zv;
-                const T zt = (T)zv;
-                sm[r * pw + x] = zt;
+                const TOut zt = (TOut)zv;
+                sm[r * pw + x] = (double)zt;
                 if (out) out[j] = zt;
             } else {
-                sm[r * pw + x] = v;
-                out[j] = v;
+                const TOut vt = (TOut)v;
+                sm[r * pw + x] = (double)vt;
+                out[j] = vt;
             }
         }
         if (a.outT) {
             __syncthreads();
-            T *outT = static_cast<T *>(a.outT);
+            TOut *outT = static_cast<TOut *>(a.outT);
             for (int q = threadIdx.x; q < B * W; q += blockDim.x) {
                 const int x = q / B, r = q - x * B;
-                outT[pd.img + (int64_t)(tl.z + x) * n + tl.y + r] = sm[r * pw + x];
+                outT[pd.img + (int64_t)(tl.z + x) * n + tl.y + r] = (TOut)sm[r * pw + x];
             }
         }
         __syncthreads();
@@ -166,68 +167,57 @@ static void set_smem(const void *fn, int bytes)
     if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-template <class T>
+template <class TIn, class TOut>
 void launch_haar_analysis(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
                           int smem_elems, const HaarArgs &a, cudaStream_t st)
 {
     if (ntiles <= 0) return;
-    const int bytes = smem_elems * (int)sizeof(T);
+    count_launches(1);
+    const int bytes = smem_elems * (int)sizeof(double);
     const int grid = min(ntiles, num_sms() * 8);
-    switch (a.mode) {
-        case HA_STORE:
-            set_smem((const void *)k_haar_analysis<T, HA_STORE>, bytes);
-            k_haar_analysis<T, HA_STORE><<<grid, 256, bytes, st>>>(G, P, tiles, ntiles, a);
-            break;
-        case HA_SUB_MASKED:
-            set_smem((const void *)k_haar_analysis<T, HA_SUB_MASKED>, bytes);
-            k_haar_analysis<T, HA_SUB_MASKED><<<grid, 256, bytes, st>>>(G, P, tiles, ntiles, a);
-            break;
-        case HA_STORE_MASKED:
-            set_smem((const void *)k_haar_analysis<T, HA_STORE_MASKED>, bytes);
-            k_haar_analysis<T, HA_STORE_MASKED><<<grid, 256, bytes, st>>>(G, P, tiles, ntiles, a);
-            break;
-    }
+#define WMG_HA(M)                                                                                  \
+    case M:                                                                                        \
+        set_smem((const void *)k_haar_analysis<TIn, TOut, M>, bytes);                              \
+        k_haar_analysis<TIn, TOut, M><<<grid, 256, bytes, st>>>(G, P, tiles, ntiles, a);           \
+        break;
+    switch (a.mode) { WMG_HA(HA_STORE) WMG_HA(HA_SUB_MASKED) WMG_HA(HA_STORE_MASKED) default: break; }
+#undef WMG_HA
 }
 
-template <class T>
+template <class TIn, class TOut>
 void launch_haar_synthesis(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
                            int smem_elems, const HaarArgs &a, cudaStream_t st)
 {
     if (ntiles <= 0) return;
-    const int bytes = smem_elems * (int)sizeof(T);
+    count_launches(1);
+    const int bytes = smem_elems * (int)sizeof(double);
     const int grid = min(ntiles, num_sms() * 8);
-    switch (a.mode) {
-        case HS_STORE:
-            set_smem((const void *)k_haar_synthesis<T, HS_STORE>, bytes);
-            k_haar_synthesis<T, HS_STORE><<<grid, 256, bytes, st>>>(G, P, tiles, ntiles, a);
-            break;
-        case HS_STORE_MASKED:
-            set_smem((const void *)k_haar_synthesis<T, HS_STORE_MASKED>, bytes);
-            k_haar_synthesis<T, HS_STORE_MASKED><<<grid, 256, bytes, st>>>(G, P, tiles, ntiles, a);
-            break;
-        case HS_CORRECT:
-            set_smem((const void *)k_haar_synthesis<T, HS_CORRECT>, bytes);
-            k_haar_synthesis<T, HS_CORRECT><<<grid, 256, bytes, st>>>(G, P, tiles, ntiles, a);
-            break;
-    }
+#define WMG_HS(M)                                                                                  \
+    case M:                                                                                        \
+        set_smem((const void *)k_haar_synthesis<TIn, TOut, M>, bytes);                             \
+        k_haar_synthesis<TIn, TOut, M><<<grid, 256, bytes, st>>>(G, P, tiles, ntiles, a);          \
+        break;
+    switch (a.mode) { WMG_HS(HS_STORE) WMG_HS(HS_STORE_MASKED) WMG_HS(HS_CORRECT) default: break; }
+#undef WMG_HS
 }
 
 // ---------------------------------------------------------------------------
 // Leaf solves. tile = {first problem p0, leaf k, problem count np, 0}; the
 // problems p0 .. p0+np-1 share one geometry. NPB problems per pass.
 // ---------------------------------------------------------------------------
-template <class T, int NPB>
+template <int NPB>
 __global__ void __launch_bounds__(256)
 k_leaf_apply(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
-             const int4 *__restrict__ tiles, int ntiles, const T *__restrict__ C,
-             T *__restrict__ E, int accumulate, const double *__restrict__ S)
+             const int4 *__restrict__ tiles, int ntiles, const double *__restrict__ C,
+             double *__restrict__ E, int accumulate, const double *__restrict__ S)
 {
+    typedef double T;
     __shared__ T cb[NPB][256];
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 tl = tiles[t];
         const GeomDev &g = G[P[tl.x].geom];
         const int Pn = g.P, k = tl.y;
-        const T *__restrict__ Dk = static_cast<const T *>(g.leafinv) + (int64_t)k * Pn * Pn;
+        const T *__restrict__ Dk = g.leafinv + (int64_t)k * Pn * Pn;
         for (int pb = 0; pb < tl.z; pb += NPB) {
             const int np = min(NPB, tl.z - pb);
             for (int q = threadIdx.x; q < NPB * Pn; q += blockDim.x) {
@@ -266,25 +256,24 @@ k_leaf_apply(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
     }
 }
 
-template <class T>
 void launch_leaf_apply(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
-                       const void *C, void *E, int accumulate, const double *S, cudaStream_t st)
+                       const double *C, double *E, int accumulate, const double *S, cudaStream_t st)
 {
     if (ntiles <= 0) return;
+    count_launches(1);
     const int grid = min(ntiles, num_sms() * 8);
-    k_leaf_apply<T, 4><<<grid, 256, 0, st>>>(G, P, tiles, ntiles, static_cast<const T *>(C),
-                                             static_cast<T *>(E), accumulate, S);
+    k_leaf_apply<4><<<grid, 256, 0, st>>>(G, P, tiles, ntiles, C, E, accumulate, S);
 }
 
-#define WMG_INST(T)                                                                              \
-    template void launch_haar_analysis<T>(const GeomDev *, const ProbDev *, const int4 *, int,  \
-                                          int, const HaarArgs &, cudaStream_t);                  \
-    template void launch_haar_synthesis<T>(const GeomDev *, const ProbDev *, const int4 *, int, \
-                                           int, const HaarArgs &, cudaStream_t);                 \
-    template void launch_leaf_apply<T>(const GeomDev *, const ProbDev *, const int4 *, int,     \
-                                       const void *, void *, int, const double *, cudaStream_t);
-WMG_INST(float)
-WMG_INST(double)
+#define WMG_INST(TI, TO)                                                                         \
+    template void launch_haar_analysis<TI, TO>(const GeomDev *, const ProbDev *, const int4 *,  \
+                                               int, int, const HaarArgs &, cudaStream_t);        \
+    template void launch_haar_synthesis<TI, TO>(const GeomDev *, const ProbDev *, const int4 *, \
+                                                int, int, const HaarArgs &, cudaStream_t);
+WMG_INST(float, float)
+WMG_INST(double, double)
+WMG_INST(float, double)
+WMG_INST(double, float)
 #undef WMG_INST
 
 }  // namespace wmg

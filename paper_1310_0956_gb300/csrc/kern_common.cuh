@@ -34,17 +34,54 @@ __device__ __forceinline__ double fma_t(double a, double b, double c) { return _
 __device__ __forceinline__ float ldg_t(const float *p) { return __ldg(p); }
 __device__ __forceinline__ double ldg_t(const double *p) { return __ldg(p); }
 
-// Signed distance reference tau = x c + y s of a pixel centre, rounded as two
-// products and one sum (no fused multiply-add), so the value is the same
-// whichever of the two orders of the terms a kernel evaluates.
-template <class T> __device__ __forceinline__ T tau_of(T x, T c, T y, T s);
-template <> __device__ __forceinline__ float tau_of<float>(float x, float c, float y, float s)
+// Distance t - tau between a line p.(c, s) = t and a pixel centre (x, y),
+// tau = x c + y s (pixel widths; x, y are half-integers, |x|, |y| <= n/2).
+//
+// FP64: tau as two rounded products and one sum (no fused multiply-add), so
+// the value does not depend on which of the two terms a kernel puts first.
+// FP32: with c = c_hi + c_lo, c_hi a multiple of 2^-12 (12 significant bits),
+// the products x c_hi, y s_hi and the differences with t are multiples of
+// 2^-13 below 2048 in magnitude, hence exact in FP32; only the small
+// correction x c_lo + y s_lo (|.| < 1/4) is rounded. The FP32 distance is
+// therefore within a few 1e-8 pixel widths of the exact one, however far the
+// pixel is from the centre, and both directions of the projector evaluate the
+// same expression.
+struct LineF {
+    float t, chi, clo, shi, slo;
+};
+struct LineD {
+    double t, c, s;
+};
+__device__ __forceinline__ float line_dist(const LineF &l, float x, float y)
 {
-    return __fadd_rn(__fmul_rn(x, c), __fmul_rn(y, s));
+    const float ex = __fmaf_rn(-x, l.chi, __fmaf_rn(-y, l.shi, l.t));          // exact
+    const float corr = __fadd_rn(__fmul_rn(x, l.clo), __fmul_rn(y, l.slo));
+    return __fsub_rn(ex, corr);
 }
-template <> __device__ __forceinline__ double tau_of<double>(double x, double c, double y, double s)
+__device__ __forceinline__ double line_dist(const LineD &l, double x, double y)
 {
-    return __dadd_rn(__dmul_rn(x, c), __dmul_rn(y, s));
+    return __dsub_rn(l.t, __dadd_rn(__dmul_rn(x, l.c), __dmul_rn(y, l.s)));
+}
+
+// Per-angle line description for a kernel's frame; `swap` exchanges the roles
+// of x and y (transposed-image frame).
+template <class T> struct LineOf;
+template <> struct LineOf<float> { typedef LineF type; };
+template <> struct LineOf<double> { typedef LineD type; };
+
+__device__ __forceinline__ void make_line(const GeomDev &g, int a, bool swap, float t, LineF &l)
+{
+    const float4 v = g.csx[a];
+    l.t = t;
+    if (swap) { l.chi = v.z; l.clo = v.w; l.shi = v.x; l.slo = v.y; }
+    else { l.chi = v.x; l.clo = v.y; l.shi = v.z; l.slo = v.w; }
+}
+__device__ __forceinline__ void make_line(const GeomDev &g, int a, bool swap, double t, LineD &l)
+{
+    const double2 v = g.cs64[a];
+    l.t = t;
+    l.c = swap ? v.y : v.x;
+    l.s = swap ? v.x : v.y;
 }
 
 // Detector offset t_k of bin k in pixel widths: (k - (D-1)/2) * dt + t0.
@@ -81,6 +118,28 @@ __device__ __forceinline__ Chord<T> make_chord(T c, T s)
     ch.lmax = T(1) / al;
     return ch;
 }
+
+// Running sum. FP32: compensated (Kahan) summation, so the error of a long
+// sum stays at a few units of FP32 rounding of its terms instead of growing
+// with the number of terms; value() returns sum + compensation in FP64.
+// FP64: plain summation.
+template <class T> struct Accum;
+template <> struct Accum<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v)
+    {
+        const float y = __fsub_rn(v, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+template <> struct Accum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double value() const { return s; }
+};
 
 __device__ __forceinline__ int warp_min(int v)
 {

@@ -51,7 +51,7 @@ k_img(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P, const int4 *
                     a.z[j] = v;
                 } else if (OP == IMG_ZERO_RESID) {  // z = 0, r1 = s (operator copy)
                     a.z[j] = 0.0;
-                    static_cast<T *>(a.r1)[j] = (T)a.s[j];
+                    static_cast<double *>(a.r1)[j] = a.s[j];
                 } else if (OP == IMG_LOAD) {        // v64 = (double) in_op ; copies
                     v = (double)static_cast<const T *>(a.in_op)[j];
                     a.z[j] = v;
@@ -446,6 +446,7 @@ void launch_img(int op, const GeomDev *G, const ProbDev *P, const int4 *tiles, i
                 const ImgArgs &a, cudaStream_t st)
 {
     if (ntiles <= 0) return;
+    count_launches(1);
     const int grid = grid_for(ntiles);
 #define WMG_IMG_CASE(O) case O: k_img<T, O><<<grid, 256, 0, st>>>(G, P, tiles, ntiles, a); break;
     switch (op) {
@@ -467,6 +468,7 @@ void launch_vec(int op, const ProbDev *P, const int4 *tiles, int ntiles, const V
                 cudaStream_t st)
 {
     if (ntiles <= 0) return;
+    count_launches(1);
     const int grid = grid_for(ntiles);
 #define WMG_VEC_CASE(O) case O: k_vec<T, O><<<grid, 256, 0, st>>>(P, tiles, ntiles, a); break;
     switch (op) {
@@ -488,6 +490,7 @@ void launch_vec(int op, const ProbDev *P, const int4 *tiles, int ntiles, const V
 void launch_finalize(const FinArgs &f, cudaStream_t st)
 {
     if (f.nprob <= 0) return;
+    count_launches(1);
     k_finalize<<<f.nprob, 256, 0, st>>>(f);
 }
 
@@ -495,6 +498,7 @@ void launch_gm_dots(const ProbDev *P, const int4 *tiles, int ntiles, const doubl
                     const double *w, int j, int ldp, double *part, const double *S, cudaStream_t st)
 {
     if (ntiles <= 0) return;
+    count_launches(1);
     k_gm_dots<<<grid_for(ntiles), 256, 0, st>>>(P, tiles, ntiles, V, vstride, w, j, ldp, part, S);
 }
 void launch_gm_axpy(const ProbDev *P, const int4 *tiles, int ntiles, const double *V, int64_t vstride,
@@ -502,6 +506,7 @@ void launch_gm_axpy(const ProbDev *P, const int4 *tiles, int ntiles, const doubl
                     cudaStream_t st)
 {
     if (ntiles <= 0) return;
+    count_launches(1);
     k_gm_axpy<<<grid_for(ntiles), 256, 0, st>>>(P, tiles, ntiles, V, vstride, w, j, ldp, Hc, part, S);
 }
 void launch_gm_combine(const ProbDev *P, const int4 *tiles, int ntiles, const double *V,
@@ -509,17 +514,20 @@ void launch_gm_combine(const ProbDev *P, const int4 *tiles, int ntiles, const do
                        const double *S, cudaStream_t st)
 {
     if (ntiles <= 0) return;
+    count_launches(1);
     k_gm_combine<<<grid_for(ntiles), 256, 0, st>>>(P, tiles, ntiles, V, vstride, ldp, Yv, jn, out, S);
 }
 void launch_gm_setv(const ProbDev *P, const int4 *tiles, int ntiles, double *V, int64_t vstride,
                     int ldp, int j, const double *w, const double *S, cudaStream_t st)
 {
     if (ntiles <= 0) return;
+    count_launches(1);
     k_gm_setv<<<grid_for(ntiles), 256, 0, st>>>(P, tiles, ntiles, V, vstride, ldp, j, w, S);
 }
 void launch_gm_scalar(int which, const GmArgs &a, cudaStream_t st)
 {
     const int blocks = (a.nprob + 127) / 128;
+    count_launches(1);
     if (which == 0) k_gm_arnoldi<<<blocks, 128, 0, st>>>(a);
     else if (which == 1) k_gm_solve_y<<<blocks, 128, 0, st>>>(a);
     else k_gm_restart<<<blocks, 128, 0, st>>>(a);

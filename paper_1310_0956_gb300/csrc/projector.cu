@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(32 * NW)
 k_project(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
           const int4 *__restrict__ tiles, int ntiles, PjArgs a)
 {
-    __shared__ T red[NW][33];
+    __shared__ double red[NW][33];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 tl = tiles[t];
@@ -54,6 +54,8 @@ k_project(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
         const T hwx = ch.hw / fabs(cc);
         const T half_n = T(0.5) * T(n);
         const T tk = ray_offset<T>(g, k);
+        typename LineOf<T>::type line;
+        make_line(g, ang, !steep, tk, line);
         // rows this lane's ray can touch (image x-range widened by one pixel)
         int lo = n, hi = -1;
         if (valid) {
@@ -69,7 +71,7 @@ k_project(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
         }
         lo = warp_min(lo);
         hi = warp_max(hi);
-        T acc = T(0);
+        Accum<T> acc;
         if (lo <= hi) {
             const int rows = hi - lo + 1, per = (rows + NW - 1) / NW;
             const int r0 = lo + w * per, r1 = min(hi + 1, r0 + per);
@@ -78,24 +80,26 @@ k_project(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
                 const T xs = (tk - yc * ss) * inv_cc;          // crossing of the row centre line
                 const int ix0 = (int)ceil(xs + half_n - T(0.5) - hwx);
                 const T *__restrict__ row = src + (int64_t)iy * n;
+                T rs = T(0);
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
                     const int ix = ix0 + q;
                     if (valid && ix >= 0 && ix < n) {
                         const T xc = T(ix) + T(0.5) - half_n;
-                        const T wgt = ch(fabs(tk - tau_of<T>(xc, cc, yc, ss)));
-                        acc = fma_t(wgt, ldg_t(row + ix), acc);
+                        const T wgt = ch(fabs(line_dist(line, xc, yc)));
+                        rs = fma_t(wgt, ldg_t(row + ix), rs);
                     }
                 }
+                acc.add(rs);
             }
         }
-        red[w][lane] = acc;
+        red[w][lane] = acc.value();
         __syncthreads();
         if (w == 0) {
-            T v = T(0);
+            double vd = 0.0;
 #pragma unroll
-            for (int i = 0; i < NW; ++i) v += red[i][lane];
-            v *= T(g.h);
+            for (int i = 0; i < NW; ++i) vd += red[i][lane];
+            const T v = (T)(vd * g.h);
             if (valid) static_cast<T *>(a.sino)[pd.sino + (int64_t)ang * D + k] = v;
             if (a.part) {
                 double q2 = valid ? (double)v * (double)v : 0.0;
@@ -112,6 +116,7 @@ void launch_project(const GeomDev *G, const ProbDev *P, const int4 *tiles, int n
                     const PjArgs &a, cudaStream_t st)
 {
     if (ntiles <= 0) return;
+    count_launches(1);
     constexpr int NW = 8;
     const int grid = min(ntiles, num_sms() * 8);
     k_project<T, NW><<<grid, 32 * NW, 0, st>>>(G, P, tiles, ntiles, a);
@@ -122,12 +127,12 @@ void launch_project(const GeomDev *G, const ProbDev *P, const int4 *tiles, int n
 // ---------------------------------------------------------------------------
 template <class T, int EPI>
 __device__ __forceinline__ double bp_epilogue(const GeomDev &g, const ProbDev &pd,
-                                              const BpArgs &a, int ix, int iy, T yT)
+                                              const BpArgs &a, int ix, int iy, double y)
 {
     const int n = g.n;
     const int64_t j = pd.img + (int64_t)iy * n + ix;
     const int64_t jt = pd.img + (int64_t)ix * n + iy;
-    const double y = (double)yT;
+    const T yT = (T)y;
     const double lam = g.lambda;
     const double *S = a.S + (int64_t)pd.slot * NSCAL;
     const T *dinv = static_cast<const T *>(g.dinv) + (j - pd.img);
@@ -147,7 +152,7 @@ __device__ __forceinline__ double bp_epilogue(const GeomDev &g, const ProbDev &p
             static_cast<T *>(a.copyT_op)[jt] = (T)zv;
         }
     } else if (EPI == BP_RESID) {
-        static_cast<T *>(a.out_op)[j] = (T)(a.s[j] - y - lam * a.z[j]);
+        a.out64[j] = a.s[j] - y - lam * a.z[j];
     } else if (EPI == BP_POST) {
         const double zv = a.z[j] + g.omega * (double)dinv[0] * (a.s[j] - y - lam * a.z[j]);
         a.z[j] = zv;
@@ -192,12 +197,10 @@ k_backproject(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
         const int ix = tl.z + tx;
         const T half_n = T(0.5) * T(n);
         const T xo = T(ix) + T(0.5) - half_n;
-        T yo[4], acc[4];
+        T yo[4];
+        Accum<T> acc[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            yo[r] = T(tl.y + ty + 8 * r) + T(0.5) - half_n;
-            acc[r] = T(0);
-        }
+        for (int r = 0; r < 4; ++r) yo[r] = T(tl.y + ty + 8 * r) + T(0.5) - half_n;
         const T *__restrict__ sg = static_cast<const T *>(a.sino) + pd.sino;
         const T dt = T(g.dt), inv_dt = T(1) / T(g.dt), t0 = T(g.t0);
         const T hD = T(0.5) * T(D - 1);
@@ -207,19 +210,24 @@ k_backproject(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
             const Chord<T> ch = make_chord<T>(c, s);
             const T hwb = ch.hw * inv_dt;
             const int ncand = (int)floor(T(2) * hwb) + 1;
+            typename LineOf<T>::type line0, line;
+            make_line(g, ang, false, T(0), line0);
+            line = line0;
             const T *__restrict__ row = sg + (int64_t)ang * D;
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                const T tau = tau_of<T>(xo, c, yo[r], s);
+                const T tau = -line_dist(line0, xo, yo[r]);     // approximate, for the bin range
                 const int k0 = (int)ceil((tau - t0) * inv_dt + hD - hwb);
+                T rs = T(0);
                 for (int q = 0; q < ncand; ++q) {
                     const int k = k0 + q;
                     if (k >= 0 && k < D) {
-                        const T tk = fma_t(T(k) - hD, dt, t0);
-                        const T wgt = ch(fabs(tk - tau));
-                        acc[r] = fma_t(wgt, ldg_t(row + k), acc[r]);
+                        line.t = fma_t(T(k) - hD, dt, t0);
+                        const T wgt = ch(fabs(line_dist(line, xo, yo[r])));
+                        rs = fma_t(wgt, ldg_t(row + k), rs);
                     }
                 }
+                acc[r].add(rs);
             }
         }
         double part = 0.0;
@@ -227,7 +235,7 @@ k_backproject(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const int iy = tl.y + ty + 8 * r;
-                if (iy < n) part += bp_epilogue<T, EPI>(g, pd, a, ix, iy, acc[r] * T(g.h));
+                if (iy < n) part += bp_epilogue<T, EPI>(g, pd, a, ix, iy, acc[r].value() * g.h);
             }
         }
         if (a.part) {
@@ -249,6 +257,7 @@ void launch_backproject(const GeomDev *G, const ProbDev *P, const int4 *tiles, i
                         const BpArgs &a, cudaStream_t st)
 {
     if (ntiles <= 0) return;
+    count_launches(1);
     const int grid = min(ntiles, num_sms() * 8);
 #define WMG_BP_CASE(E) \
     case E: k_backproject<T, E><<<grid, 256, 0, st>>>(G, P, tiles, ntiles, a); break;
@@ -264,6 +273,47 @@ void launch_backproject(const GeomDev *G, const ProbDev *P, const int4 *tiles, i
         default: break;
     }
 #undef WMG_BP_CASE
+}
+
+// Count of nonzero weights (FP64 geometry), same walk as the forward kernel.
+__global__ void __launch_bounds__(256)
+k_count_nnz(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
+            const int4 *__restrict__ tiles, int ntiles, unsigned long long *count)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 tl = tiles[t];
+        const GeomDev &g = G[P[tl.x].geom];
+        const int n = g.n, D = g.D, ang = tl.y, k = tl.z + lane;
+        if (k >= D) continue;
+        double c, s;
+        load_cs(g, ang, c, s);
+        const bool steep = fabs(c) >= fabs(s);
+        const double cc = steep ? c : s, ss = steep ? s : c;
+        const Chord<double> ch = make_chord<double>(cc, ss);
+        const double hwx = ch.hw / fabs(cc), half_n = 0.5 * n;
+        const double tk = ray_offset<double>(g, k);
+        LineD line;
+        make_line(g, ang, !steep, tk, line);
+        unsigned long long cnt = 0;
+        for (int iy = w; iy < n; iy += 8) {
+            const double yc = iy + 0.5 - half_n;
+            const int ix0 = (int)ceil((tk - yc * ss) / cc + half_n - 0.5 - hwx);
+            for (int q = 0; q < 2; ++q) {
+                const int ix = ix0 + q;
+                if (ix >= 0 && ix < n && ch(fabs(line_dist(line, ix + 0.5 - half_n, yc))) > 0.0) ++cnt;
+            }
+        }
+        atomicAdd(count, cnt);
+    }
+}
+
+void launch_count_nnz(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
+                      unsigned long long *count, cudaStream_t st)
+{
+    if (ntiles <= 0) return;
+    count_launches(1);
+    k_count_nnz<<<min(ntiles, num_sms() * 8), 256, 0, st>>>(G, P, tiles, ntiles, count);
 }
 
 // ---------------------------------------------------------------------------
@@ -299,6 +349,7 @@ void launch_transpose(const GeomDev *G, const ProbDev *P, const int4 *tiles, int
                       const void *src, void *dst, cudaStream_t st)
 {
     if (ntiles <= 0) return;
+    count_launches(1);
     const int grid = min(ntiles, num_sms() * 8);
     k_transpose<T><<<grid, 256, 0, st>>>(G, P, tiles, ntiles, static_cast<const T *>(src),
                                          static_cast<T *>(dst));

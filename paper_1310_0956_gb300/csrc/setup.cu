@@ -76,7 +76,8 @@ k_leaf_coeffs(const GeomDev *__restrict__ Gd, int a0, int na, int R, double *__r
                     int loc = 0;
                     if (fx >= fx0 && fx < fx0 + B) {
                         const double xc = fx + 0.5 - half_n;
-                        w = ch(fabs(tk - tau_of<double>(xc, cc, yc, ss)));
+                        const LineD ln{tk, cc, ss};
+                        w = ch(fabs(line_dist(ln, xc, yc)));
                         const int ly = steep ? fr - fr0 : fx - fx0;
                         const int lx = steep ? fx - fx0 : fr - fr0;
                         loc = (ly << 8) | lx;
@@ -202,8 +203,7 @@ k_leaf_invert(const GeomDev *__restrict__ Gd, double *__restrict__ Dm, double *_
 
 // Host driver: assembles, factorises and inverts every leaf of one geometry.
 // `leafinv_out` receives K*P*P values of type T. Returns WMG_OK or an error.
-template <class T>
-int32_t build_leaf_inverses(const GeomDev &gh, const GeomDev *gd, void *leafinv_out, cudaStream_t st)
+int32_t build_leaf_inverses(const GeomDev &gh, const GeomDev *gd, double *leafinv_out, cudaStream_t st)
 {
     const int P = gh.P, K = gh.K;
     const int R = (int)floor(gh.B * 1.4142135623730951 / gh.dt) + 3;
@@ -237,11 +237,13 @@ int32_t build_leaf_inverses(const GeomDev &gh, const GeomDev *gd, void *leafinv_
     const int gram_threads = std::min(256, std::max(32, ((K + 31) / 32) * 32));
     for (int a0 = 0; a0 < gh.m; a0 += chunk) {
         const int na = std::min(chunk, gh.m - a0);
+        count_launches(2);
         k_leaf_coeffs<<<std::min(na * P, num_sms() * 8), 256, 0, st>>>(gd, a0, na, R, Gbuf);
         k_leaf_gram<<<std::min(npairs, num_sms() * 16), gram_threads, 0, st>>>(gd, a0, na, R, Gbuf,
                                                                                pairs, npairs, Dm);
     }
-    k_leaf_invert<T><<<inv_ctas, 256, 0, st>>>(gd, Dm, Y, static_cast<T *>(leafinv_out), status);
+    count_launches(1);
+    k_leaf_invert<double><<<inv_ctas, 256, 0, st>>>(gd, Dm, Y, leafinv_out, status);
     std::vector<int> hs(K);
     cudaMemcpyAsync(hs.data(), status, (size_t)K * sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
@@ -259,7 +261,5 @@ int32_t build_leaf_inverses(const GeomDev &gh, const GeomDev *gd, void *leafinv_
     return rc;
 }
 
-template int32_t build_leaf_inverses<float>(const GeomDev &, const GeomDev *, void *, cudaStream_t);
-template int32_t build_leaf_inverses<double>(const GeomDev &, const GeomDev *, void *, cudaStream_t);
 
 }  // namespace wmg

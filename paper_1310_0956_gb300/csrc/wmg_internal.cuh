@@ -29,8 +29,10 @@ struct GeomDev {
     double lambda, omega;    // Tikhonov parameter, smoother damping
     const double2 *cs64;     // (cos, sin) per angle, FP64
     const float2 *cs32;      // round-to-nearest FP32 copy
+    const float4 *csx;       // (c_hi, c_lo, s_hi, s_lo): c_hi = c rounded to a
+                             // multiple of 2^-12, c_lo = c - c_hi in FP32
     const void *dinv;        // N: 1/D~ (0 where D~ = 0), operator precision
-    const void *leafinv;     // K*P*P: leaf inverses, operator precision
+    const double *leafinv;   // K*P*P: leaf inverses, FP64
     const void *sirtR;       // M: 1/row sums (0 if empty)
     const void *sirtC;       // N: 1/column sums (0 if empty)
 };
@@ -66,6 +68,8 @@ enum Scal : int {
 // ---------------------------------------------------------------------------
 void set_error(const std::string &msg);
 int32_t fail(int32_t code, const std::string &msg);
+// library-wide kernel launch counter (every launcher adds its launches)
+void count_launches(int n);
 
 #define WMG_CUDA(call)                                                              \
     do {                                                                            \
@@ -120,6 +124,9 @@ void launch_project(const GeomDev *G, const ProbDev *P, const int4 *tiles, int n
 template <class T>
 void launch_backproject(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
                         const BpArgs &a, cudaStream_t st);
+// nnz of W: rays x pixels with a nonzero weight, added into *count (one problem)
+void launch_count_nnz(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
+                      unsigned long long *count, cudaStream_t st);
 template <class T>
 void launch_transpose(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
                       const void *src, void *dst, cudaStream_t st);
@@ -143,22 +150,20 @@ struct HaarArgs {
     double *z;               // HS_CORRECT: FP64 vector updated in place
     const double *S;         // scalars (active flags) or NULL
 };
-template <class T>
+template <class TIn, class TOut>
 void launch_haar_analysis(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
                           int smem_elems, const HaarArgs &a, cudaStream_t st);
-template <class T>
+template <class TIn, class TOut>
 void launch_haar_synthesis(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
                            int smem_elems, const HaarArgs &a, cudaStream_t st);
 
-// Leaf solves E[k] = Dinv_k C[k] for the problems of a group (haar.cu).
+// Leaf solves E[k] = Dinv_k C[k] for the problems of a group (haar.cu), FP64.
 // accumulate = 1 adds into E.
-template <class T>
 void launch_leaf_apply(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
-                       const void *C, void *E, int accumulate, const double *S, cudaStream_t st);
+                       const double *C, double *E, int accumulate, const double *S, cudaStream_t st);
 
 // Setup (setup.cu).
-template <class T>
-int32_t build_leaf_inverses(const GeomDev &g_host, const GeomDev *g_dev, void *leafinv_out,
+int32_t build_leaf_inverses(const GeomDev &g_host, const GeomDev *g_dev, double *leafinv_out,
                             cudaStream_t st);
 
 // Elementwise / reduction kernels (krylov.cu), all FP64 Krylov state.

@@ -35,7 +35,7 @@ def relmax(a, b):
 @pytest.mark.parametrize("n,m,D,dt,t0", GEOMS)
 def test_project_backproject_f64(n, m, D, dt, t0):
     op = oracle.Op(n, m, D, dt, t0)
-    plan = wmg.Plan(n, m, D, levels=1, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F64,
+    plan = wmg.Plan(n, m, D, levels=0, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F64,
                     det_spacing=dt, det_offset=t0)
     rng = np.random.default_rng(n * 1000 + m)
     x, y = rng.standard_normal(op.N), rng.standard_normal(op.M)
@@ -46,7 +46,7 @@ def test_project_backproject_f64(n, m, D, dt, t0):
 @pytest.mark.parametrize("n,m,D", [(64, 90, 91), (32, 36, 46), (256, 180, 363)])
 def test_project_backproject_f32(n, m, D):
     op = oracle.Op(n, m, D)
-    plan = wmg.Plan(n, m, D, levels=1, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F32)
+    plan = wmg.Plan(n, m, D, levels=0, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F32)
     rng = np.random.default_rng(3)
     x, y = rng.random(op.N), rng.random(op.M)
     assert relmax(host(plan.project(dev(x, torch.float32))), op.project(x)) < 2e-6
@@ -55,7 +55,7 @@ def test_project_backproject_f32(n, m, D):
 
 def test_batched_projection_equals_single():
     n, m, D = 64, 90, 91
-    plan = wmg.Plan(n, m, D, levels=1, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F64)
+    plan = wmg.Plan(n, m, D, levels=0, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F64)
     rng = np.random.default_rng(4)
     xs = rng.standard_normal((3, n * n))
     batched = host(plan.project(dev(xs.reshape(-1)))).reshape(3, -1)
@@ -66,7 +66,7 @@ def test_batched_projection_equals_single():
 
 def test_adjointness_gpu():
     n, m, D = 64, 90, 91
-    plan = wmg.Plan(n, m, D, levels=1, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F64)
+    plan = wmg.Plan(n, m, D, levels=0, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F64)
     rng = np.random.default_rng(5)
     x, y = rng.standard_normal(n * n), rng.standard_normal(m * D)
     lhs = host(plan.project(dev(x))) @ y

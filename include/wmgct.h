@@ -198,6 +198,25 @@ typedef struct wmg_profile_stats {
 int32_t wmg_profile_begin(wmg_plan *plan);
 int32_t wmg_profile_end(wmg_plan *plan, wmg_profile_stats *out, void *stream);
 
+/* Forward projection b = W x that allocates no device memory, for callers
+ * that cannot call cudaMalloc once they are running: an acquisition loop that
+ * reserves all its device memory at start-up so that nothing can fail or
+ * stall mid-scan, or a program whose framework allocator already holds all
+ * free device memory. The paper has no counterpart: this is an interface
+ * variant of wmg_project, not part of the method.
+ * Geometry: n x n image, m equiangular angles over [0, pi), D bins of one
+ * pixel width, centred; FP32 image x (n*n) and sinogram b (m*D), device
+ * memory, one image per call. Results equal wmg_project's for that geometry.
+ * Limits: n <= 1024, m <= 4096, D <= 2048; larger sizes return
+ * WMG_ERR_INVALID_ARG. The scratch (transposed image, work lists, angle
+ * tables; about 12 MiB) lives in fixed __device__ arrays that every GPU which
+ * loads the library keeps until the process exits. The first call on a
+ * device looks up those arrays' device addresses; make that first call before
+ * any stream capture. Every call shares the same arrays, so calls whose work
+ * overlaps on the GPU (other streams, other host threads) race: serialise
+ * them. Asynchronous on `stream`. */
+int32_t wmg_project_noalloc(int32_t n, int32_t m, int32_t D, const float *x, float *b, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -81,6 +81,7 @@ _SIGNATURES = {
     "wmg_launch_count": (_i64, [_i32]),
     "wmg_profile_begin": (_i32, [_vp]),
     "wmg_profile_end": (_i32, [_vp, C.POINTER(wmg_profile_stats), _vp]),
+    "wmg_project_noalloc": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp]),
 }
 
 
@@ -165,6 +166,12 @@ def wmg_solve(plan, solver, preconditioned, count, b, x, max_iter, rtol, restart
               stream=None) -> int:
     return _check(lib().wmg_solve(plan, solver, preconditioned, count, b, x, max_iter, rtol, restart,
                                   info, res_hist, stream), allow_not_converged=True)
+
+
+def wmg_project_noalloc(n, m, D, x, b, stream=None):
+    """Forward projection without device allocation (FP32, equiangular
+    geometry, unit bins; see include/wmgct.h for the limits)."""
+    _check(lib().wmg_project_noalloc(n, m, D, x, b, stream))
 
 
 def wmg_plan_nnz(plan) -> int:

@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-case", action="store_true",
+                    help="run 3 projector and 3 backprojector launches on a batch of 16 images of the "
+                         "workload geometry (FP32) and exit: the small case for ncu captures")
     return ap.parse_args()
 
 
@@ -327,9 +330,29 @@ def roofline_entry(prof: dict, P0, B: int) -> dict:
                      f"peak derived: 152 SMs x 128 FP32 lanes x 2 FLOP x {clk:.0f} MHz")}
 
 
+def kernel_case():
+    import torch
+    import paper_1310_0956_gb300 as wmg
+    P0 = workload_problems(1, 0)[0]
+    plan = wmg.Plan(P0.n, P0.m, P0.D, levels=0, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE,
+                    precision=wmg.PREC_F32)
+    x = torch.rand(16 * P0.N, dtype=torch.float32, device="cuda")
+    b = torch.empty(16 * P0.M, dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(3):
+        plan.project(x, out=b)
+    for _ in range(3):
+        plan.backproject(b, out=y)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_case": "ok", "nnz_per_image": plan.nnz()}))
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.kernel_case:
+        kernel_case()
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

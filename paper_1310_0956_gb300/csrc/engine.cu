@@ -149,7 +149,8 @@ struct wmg_plan {
     wmg::GeomDev g{};           // host copy (device pointers inside)
     wmg_opts opts{};
     int64_t N = 0, M = 0;
-    wmg::DevBuf d_geom, cs64, cs32, csx, dinv, leafinv, sirtR, sirtC;
+    wmg::DevBuf d_geom, cs64, cs32, csx, angf, dinv, leafinv, sirtR, sirtC;
+    bool unit_bins = true;      // unit bin spacing and zero offset
     int cap = 0;                // problems the tables are built for
     wmg::ProbSet real;
     std::map<std::vector<int>, std::unique_ptr<wmg::ProbSet>> bands;   // band-update groups
@@ -279,6 +280,7 @@ static void project(wmg_plan *pl, const ProbSet &ps, const void *img, const void
 template <class T>
 static void backproject(wmg_plan *pl, const ProbSet &ps, BpArgs a, cudaStream_t st)
 {
+    a.unit = pl->unit_bins ? 1 : 0;
     if (pl->profiling) prof_begin(pl, 1, ps.nprob, st);
     launch_backproject<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.bp.tiles.as<int4>(),
                           ps.bp.n, a, st);
@@ -288,6 +290,7 @@ static void backproject(wmg_plan *pl, const ProbSet &ps, BpArgs a, cudaStream_t 
 static BpArgs bp_args(int epi, const void *sino, const double *S)
 {
     BpArgs a{};
+    a.unit = 0;
     a.epi = epi;
     a.sino = sino;
     a.S = S;
@@ -714,15 +717,25 @@ extern "C" int32_t wmg_plan_create(const wmg_geom *g, const wmg_opts *o, void *s
         const double sh = std::nearbyint(cs[a].y * 4096.0) / 4096.0;
         csx[a] = make_float4((float)ch, (float)(cs[a].x - ch), (float)sh, (float)(cs[a].y - sh));
     }
+    std::vector<AngleF> angf(g->m);
+    fill_angle_table(cs.data(), g->m, angf.data());
     if (!pl->cs64.ensure(g->m * sizeof(double2)) || !pl->cs32.ensure(g->m * sizeof(float2)) ||
-        !pl->csx.ensure(g->m * sizeof(float4)) || !pl->d_geom.ensure(sizeof(GeomDev)))
+        !pl->csx.ensure(g->m * sizeof(float4)) || !pl->angf.ensure(g->m * sizeof(AngleF)) ||
+        !pl->d_geom.ensure(sizeof(GeomDev)))
         return fail(WMG_ERR_OOM, "plan allocation failed");
+    WMG_CUDA(cudaMemcpyAsync(pl->angf.p, angf.data(), g->m * sizeof(AngleF), cudaMemcpyHostToDevice, st));
     WMG_CUDA(cudaMemcpyAsync(pl->csx.p, csx.data(), g->m * sizeof(float4), cudaMemcpyHostToDevice, st));
     WMG_CUDA(cudaMemcpyAsync(pl->cs64.p, cs.data(), g->m * sizeof(double2), cudaMemcpyHostToDevice, st));
     WMG_CUDA(cudaMemcpyAsync(pl->cs32.p, cs32.data(), g->m * sizeof(float2), cudaMemcpyHostToDevice, st));
     gd.cs64 = pl->cs64.as<double2>();
     gd.cs32 = pl->cs32.as<float2>();
     gd.csx = pl->csx.as<float4>();
+    gd.angf = pl->angf.as<AngleF>();
+    gd.hf = (float)gd.h;
+    gd.dtf = (float)gd.dt;
+    gd.t0f = (float)gd.t0;
+    gd.hDf = 0.5f * (float)(g->D - 1);
+    pl->unit_bins = gd.dt == 1.0 && gd.t0 == 0.0;
     WMG_CUDA(cudaMemcpyAsync(pl->d_geom.p, &gd, sizeof(GeomDev), cudaMemcpyHostToDevice, st));
     int32_t rc = ensure_count(pl.get(), 1, st);
     if (rc) return rc;

@@ -19,6 +19,20 @@ namespace wmg {
 // band-local multi-image products of the hybrid cycle are all just tables.
 // ---------------------------------------------------------------------------
 
+// Per-angle constants of the FP32 kernels (built in FP64 on the host).
+// Split trigonometry: c = chi + clo with chi a multiple of 2^-12; chord of a
+// unit pixel at distance d: clamp(hw_inv - d * inv_ab, 0, lmax); frame =
+// rows of the image (steep, |c| >= |s|) or of its transpose (cc, ss = the
+// frame's cos / sin): inv_cc = 1/cc, slope = ss/cc, inv_slope = cc/ss,
+// hwx = hw/|cc|.
+struct __align__(16) AngleF {
+    float chi, clo, shi, slo;
+    float hw_inv, inv_ab, lmax, hwx;
+    float inv_cc, slope, inv_slope, hw;
+    float flags;              // int bits: 1 = steep, 2 = axis-aligned
+    float pad0, pad1, pad2;
+};
+
 // Immutable per-geometry data (lengths in pixel widths, h = 1/n applied to
 // the weights at the end).
 struct GeomDev {
@@ -35,7 +49,12 @@ struct GeomDev {
     const double *leafinv;   // K*P*P: leaf inverses, FP64
     const void *sirtR;       // M: 1/row sums (0 if empty)
     const void *sirtC;       // N: 1/column sums (0 if empty)
+    const AngleF *angf;      // m per-angle constants (FP32 kernels)
+    float hf, dtf, t0f, hDf; // FP32 copies of h, dt, t0 and (D-1)/2
 };
+
+// Fills the FP32 per-angle table from FP64 (cos, sin) pairs.
+void fill_angle_table(const double2 *cs, int m, AngleF *out);
 
 // One problem slot (or one virtual image of a multi-image product).
 struct ProbDev {
@@ -99,6 +118,7 @@ enum BpEpi : int {
 
 struct BpArgs {
     int epi;
+    int unit;                // FP32 kernels: unit bin spacing, zero offset (two candidate bins)
     const void *sino;        // T, sinogram input pool
     void *out_op;            // T image output (BP_STORE, BP_RESID, BP_APPLY_A)
     double *x, *s, *z, *p;   // FP64 Krylov vectors (pools)
@@ -127,6 +147,10 @@ void launch_backproject(const GeomDev *G, const ProbDev *P, const int4 *tiles, i
 // nnz of W: rays x pixels with a nonzero weight, added into *count (one problem)
 void launch_count_nnz(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
                       unsigned long long *count, cudaStream_t st);
+void launch_project_f32(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
+                        const PjArgs &a, cudaStream_t st);
+void launch_backproject_f32(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
+                            const BpArgs &a, bool unit, cudaStream_t st);
 template <class T>
 void launch_transpose(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
                       const void *src, void *dst, cudaStream_t st);

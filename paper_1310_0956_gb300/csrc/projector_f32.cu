@@ -29,6 +29,12 @@ __device__ __forceinline__ float chord_f(const AngleF &A, bool axis, float d)
     return fminf(fmaxf(__fmaf_rn(-d, A.inv_ab, A.hw_inv), 0.f), A.lmax);
 }
 
+// Chord divided by lmax = 1/alpha, in [0, 1]: one saturating FMA.
+__device__ __forceinline__ float chord_n(float wa, float wb, float d)
+{
+    return __saturatef(__fmaf_rn(-d, wa, wb));
+}
+
 // ---------------------------------------------------------------------------
 // Forward: tile = {prob, angle, first ray, 0}; lane = ray, warps take every
 // NW-th row of the rays' common row range.
@@ -72,39 +78,51 @@ k_project_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
         float s = 0.f, c = 0.f;                        // compensated sum
         const int nrows = hi - lo + 1;
         if (nrows > 0) {
+            // warp w takes rows lo + w + NW*j; R consecutive ones per step,
+            // their 2R loads issued before any is used
+            constexpr int R = 4;
             const int iy0 = lo + w;
+            const float dy = (float)NW;
             float yc = (float)iy0 + 0.5f - half_n;
             float brow = __fmaf_rn(-yc, ss_hi, tk);            // t - yc ss_hi: exact
             float cy = yc * ss_lo;
             float xs = __fmaf_rn(-yc, A.slope, tk * A.inv_cc); // crossing of the row centre line
-            const float dy = (float)NW;
             const float dbrow = -dy * ss_hi, dcy = dy * ss_lo, dxs = -dy * A.slope;
             // candidates: the two pixel centres nearest the crossing. The
             // support half-width hwx is at most 1, so every pixel with a
             // nonzero weight is one of them whatever the rounding of xs.
             const float off = half_n - 0.5f;
+            const int nmine = (nrows - w + NW - 1) / NW;       // rows of this warp
             const float *__restrict__ row = src + (int64_t)iy0 * n;
             const int64_t drow = (int64_t)NW * n;
-            for (int j = w; j < nrows; j += NW) {
-                const int ix0 = __float2int_rd(xs + off);
-                const float xc = (float)ix0 + 0.5f - half_n;
-                const float ex0 = __fmaf_rn(-xc, cc_hi, brow);  // exact
-                const float co0 = __fmaf_rn(xc, cc_lo, cy);
-                const float d0 = fabsf(ex0 - co0);
-                const float d1 = fabsf((ex0 - cc_hi) - (co0 + cc_lo));
-                const float w0 = chord_f(A, axis, d0), w1 = chord_f(A, axis, d1);
-                const float v0 = (valid && (unsigned)ix0 < (unsigned)n) ? __ldg(row + ix0) : 0.f;
-                const float v1 = (valid && (unsigned)(ix0 + 1) < (unsigned)n) ? __ldg(row + ix0 + 1) : 0.f;
-                const float rs = __fmaf_rn(w0, v0, w1 * v1);
-                const float y = rs - c;                        // Kahan step
-                const float tt = s + y;
-                c = (tt - s) - y;
-                s = tt;
-                brow += dbrow;
-                cy += dcy;
-                xs += dxs;
-                yc += dy;
-                row += drow;
+            const float wa = A.wa, wb = A.wb, ccf = A.cc;
+            for (int j = 0; j < nmine; j += R) {
+                float v0[R], v1[R], w0[R], w1[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const bool live = valid && (j + r < nmine);
+                    const int ix0 = __float2int_rd(xs + off);
+                    const float *rp = row + ix0;
+                    v0[r] = (live && (unsigned)ix0 < (unsigned)n) ? __ldg(rp) : 0.f;
+                    v1[r] = (live && (unsigned)(ix0 + 1) < (unsigned)n) ? __ldg(rp + 1) : 0.f;
+                    const float xc = (float)ix0 + 0.5f - half_n;
+                    const float dl0 = __fmaf_rn(-xc, cc_hi, brow) - __fmaf_rn(xc, cc_lo, cy);
+                    w0[r] = chord_n(wa, wb, fabsf(dl0));
+                    w1[r] = chord_n(wa, wb, fabsf(dl0 - ccf));
+                    brow += dbrow;
+                    cy += dcy;
+                    xs += dxs;
+                    row += drow;
+                }
+#pragma unroll
+                for (int r = 0; r < R; r += 2) {
+                    const float rs = __fmaf_rn(w0[r], v0[r], __fmaf_rn(w1[r], v1[r],
+                                     __fmaf_rn(w0[r + 1], v0[r + 1], w1[r + 1] * v1[r + 1])));
+                    const float y = rs - c;                    // Kahan step
+                    const float tt = s + y;
+                    c = (tt - s) - y;
+                    s = tt;
+                }
             }
         }
         red_s[w][lane] = s;
@@ -119,7 +137,7 @@ k_project_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
                 Cc = (tt - S) - y;
                 S = tt;
             }
-            const float v = (S - Cc) * g.hf;
+            const float v = (S - Cc) * (A.lmax * g.hf);
             if (valid) static_cast<float *>(a.sino)[pd.sino + (int64_t)ang * D + k] = v;
             if (a.part) {
                 double q2 = valid ? (double)v * (double)v : 0.0;
@@ -180,10 +198,10 @@ k_backproject_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
                     const int k0 = __float2int_rd((ph + pc) - t0 + hD);
                     const float tk = (float)k0 - hD + t0;
                     const float d0 = (tk - ph) - pc;
-                    const float w0 = chord_f(A, axis, fabsf(d0)), w1 = chord_f(A, axis, fabsf(d0 + 1.f));
+                    const float w0 = chord_n(A.wa, A.wb, fabsf(d0)), w1 = chord_n(A.wa, A.wb, fabsf(d0 + 1.f));
                     const float v0 = (unsigned)k0 < (unsigned)D ? __ldg(row + k0) : 0.f;
                     const float v1 = (unsigned)(k0 + 1) < (unsigned)D ? __ldg(row + k0 + 1) : 0.f;
-                    rs = __fmaf_rn(w0, v0, w1 * v1);
+                    rs = __fmaf_rn(w0, v0, w1 * v1) * A.lmax;
                 } else {
                     const float hwb = A.hw * inv_dt;
                     const int k0 = __float2int_ru(((ph + pc) - t0) * inv_dt + hD - hwb);
@@ -268,6 +286,9 @@ void fill_angle_table(const double2 *cs, int m, AngleF *out)
         A.inv_slope = ss != 0.0 ? (float)(cc / ss) : 0.f;
         const int flags = (steep ? 1 : 0) | (axis ? 2 : 0);
         std::memcpy(&A.flags, &flags, sizeof(int));
+        A.wa = axis ? 4194304.f : (float)(1.0 / be);
+        A.wb = axis ? 2097152.5f : (float)(hw / be);
+        A.cc = (float)cc;
         out[a] = A;
     }
 }

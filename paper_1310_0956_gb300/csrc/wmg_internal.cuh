@@ -25,12 +25,16 @@ namespace wmg {
 // rows of the image (steep, |c| >= |s|) or of its transpose (cc, ss = the
 // frame's cos / sin): inv_cc = 1/cc, slope = ss/cc, inv_slope = cc/ss,
 // hwx = hw/|cc|.
+// Normalised chord: L(d) = lmax * sat(wb - d * wa) with wa = 1/beta,
+// wb = hw/beta (sat = clamp to [0, 1], one saturating FMA); axis-aligned
+// angles use wa = 2^22, wb = 2^21 + 1/2, which is the step 1 / 1/2 / 0 at the
+// half-integer distances those rays have to pixel centres.
 struct __align__(16) AngleF {
     float chi, clo, shi, slo;
     float hw_inv, inv_ab, lmax, hwx;
     float inv_cc, slope, inv_slope, hw;
     float flags;              // int bits: 1 = steep, 2 = axis-aligned
-    float pad0, pad1, pad2;
+    float wa, wb, cc;         // normalised chord; frame cos (cc_hi + cc_lo)
 };
 
 // Immutable per-geometry data (lengths in pixel widths, h = 1/n applied to

@@ -2,7 +2,7 @@
 relative normal-equation residual on the 256x256 parallel-beam workload
 (180 angles, 363 detector bins, seeded 20-ellipse phantoms, 1% Gaussian
 noise, 5 WMG levels), solved by restarted GMRES(20) with right
-preconditioning by the hybrid WMG cycle (hybrid depth 2, one l1-Jacobi pre-
+preconditioning by the hybrid WMG cycle (hybrid depth 1, one l1-Jacobi pre-
 and post-sweep), FP32 operator with FP64 Krylov vectors and reductions.
 
 One step = one batch of `--batch` independent reconstructions (distinct
@@ -40,7 +40,7 @@ METRIC = "WMG-Krylov recon/s to 1e-4 residual"
 RTOL = 1e-4
 MAX_ITER = 200
 RESTART = 20
-LEVELS, NU1, NU2, HYB = 5, 1, 1, 2
+LEVELS, NU1, NU2, HYB = 5, 1, 1, 1
 
 
 def parse():
@@ -283,7 +283,7 @@ def run_ours(args, rank, world, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "256x256_180ang_363det_noise1pct", "batch_per_gpu": B,
-                       "solver": "WMG-GMRES(20), hybrid cycle depth 2, nu1=nu2=1", "levels": LEVELS,
+                       "solver": f"WMG-GMRES(20), hybrid cycle depth {HYB}, nu1=nu2={NU1}", "levels": LEVELS,
                        "precision": "fp32 operator, fp64 Krylov vectors/reductions/leaf solves",
                        "rtol": RTOL, "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",

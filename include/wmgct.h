@@ -173,6 +173,33 @@ int32_t wmg_solve(wmg_plan *plan, int32_t solver, int32_t preconditioned, int32_
                   const void *b, void *x, int32_t max_iter, double rtol, int32_t restart,
                   wmg_solve_info *info, double *res_hist, void *stream);
 
+/* ---- batches of problems of different geometries ------------------------- */
+/* A batch solves `count` independent reconstructions, each with its own
+ * geometry (image side, angles, bins) and WMG levels, together: every
+ * operator application is one launch over all of them (the problems are
+ * independent: no data moves between them). Identical geometries are set up
+ * once and share their leaf inverses.
+ * wmg_batch_create: gs, os are HOST arrays of count entries; all problems
+ * must share precision, nu1, nu2, omega, cycle and hybrid depth (levels and
+ * lambda may differ). Runs every distinct geometry's setup (as
+ * wmg_plan_create). Synchronising. */
+typedef struct wmg_batch wmg_batch;
+int32_t wmg_batch_create(const wmg_geom *gs, const wmg_opts *os, int32_t count, void *stream, wmg_batch **out);
+int32_t wmg_batch_destroy(wmg_batch *batch);
+
+/* N = n*n and M = m*D of problem i. */
+int32_t wmg_batch_sizes(const wmg_batch *batch, int32_t i, int64_t *N, int64_t *M);
+
+/* Solve every problem of the batch: b[i] (device sinogram of problem i),
+ * x[i] (device image of problem i) are HOST arrays of device pointers; the
+ * element type is the batch precision's. Other arguments as wmg_solve; info
+ * and res_hist are in the caller's problem order. A problem alone and the
+ * same problem inside a batch give bitwise identical results (fixed
+ * per-problem summation orders). Synchronising. */
+int32_t wmg_batch_solve(wmg_batch *batch, int32_t solver, int32_t preconditioned, const void *const *b,
+                        void *const *x, int32_t max_iter, double rtol, int32_t restart,
+                        wmg_solve_info *info, double *res_hist, void *stream);
+
 /* Number of nonzero intersection lengths of the plan's W (rays x pixels with
  * a nonzero weight), counted on the device at plan creation. */
 int32_t wmg_plan_nnz(const wmg_plan *plan, int64_t *nnz);

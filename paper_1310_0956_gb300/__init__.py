@@ -82,6 +82,11 @@ _SIGNATURES = {
     "wmg_profile_begin": (_i32, [_vp]),
     "wmg_profile_end": (_i32, [_vp, C.POINTER(wmg_profile_stats), _vp]),
     "wmg_project_noalloc": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp]),
+    "wmg_batch_create": (_i32, [C.POINTER(wmg_geom), C.POINTER(wmg_opts), _i32, _vp, C.POINTER(_vp)]),
+    "wmg_batch_destroy": (_i32, [_vp]),
+    "wmg_batch_sizes": (_i32, [_vp, _i32, C.POINTER(_i64), C.POINTER(_i64)]),
+    "wmg_batch_solve": (_i32, [_vp, _i32, _i32, C.POINTER(_vp), C.POINTER(_vp), _i32, _dbl, _i32,
+                               C.POINTER(wmg_solve_info), C.POINTER(_dbl), _vp]),
 }
 
 
@@ -172,6 +177,34 @@ def wmg_project_noalloc(n, m, D, x, b, stream=None):
     """Forward projection without device allocation (FP32, equiangular
     geometry, unit bins; see include/wmgct.h for the limits)."""
     _check(lib().wmg_project_noalloc(n, m, D, x, b, stream))
+
+
+def wmg_batch_create(geoms, opts, stream=None) -> C.c_void_p:
+    n = len(geoms)
+    ga = (wmg_geom * n)(*geoms)
+    oa = (wmg_opts * n)(*opts)
+    out = _vp()
+    _check(lib().wmg_batch_create(ga, oa, n, stream, C.byref(out)))
+    return out
+
+
+def wmg_batch_destroy(batch):
+    _check(lib().wmg_batch_destroy(batch))
+
+
+def wmg_batch_sizes(batch, i) -> tuple[int, int]:
+    N, M = _i64(), _i64()
+    _check(lib().wmg_batch_sizes(batch, i, C.byref(N), C.byref(M)))
+    return N.value, M.value
+
+
+def wmg_batch_solve(batch, solver, preconditioned, b_ptrs, x_ptrs, max_iter, rtol, restart, info, res_hist,
+                    stream=None) -> int:
+    n = len(b_ptrs)
+    ba = (_vp * n)(*b_ptrs)
+    xa = (_vp * n)(*x_ptrs)
+    return _check(lib().wmg_batch_solve(batch, solver, preconditioned, ba, xa, max_iter, rtol, restart, info,
+                                        res_hist, stream), allow_not_converged=True)
 
 
 def wmg_plan_nnz(plan) -> int:
@@ -314,3 +347,54 @@ class Plan:
             h = np.frombuffer(hist, dtype=np.float64).reshape(cnt, max_iter + 1)
             hists = [h[i, :infos[i][0] + 1].copy() for i in range(cnt)]
         return out, infos, hists, rc
+
+
+class Batch:
+    """Problems of different geometries solved together (torch CUDA tensors).
+    `problems` is a list of dicts with keys n, m, D and optionally levels,
+    lam, angles; the cycle options are shared."""
+
+    def __init__(self, problems, nu1=1, nu2=1, omega=1.0, hybrid_depth=1, cycle=CYCLE_HYBRID,
+                 precision=PREC_F32):
+        import torch
+        self._torch = torch
+        self._keep = []
+        geoms, opts = [], []
+        for p in problems:
+            ap = None
+            if p.get("angles") is not None:
+                arr = (C.c_double * p["m"])(*[float(a) for a in p["angles"]])
+                self._keep.append(arr)
+                ap = C.cast(arr, C.c_void_p)
+            geoms.append(wmg_geom(p["n"], p["m"], ap, p["D"], p.get("det_spacing", 1.0), p.get("det_offset", 0.0)))
+            opts.append(wmg_opts(p.get("levels", 1), nu1, nu2, omega, p.get("lam", 0.0), hybrid_depth, cycle,
+                                 precision))
+        self.count = len(problems)
+        self.dtype = torch.float64 if precision == PREC_F64 else torch.float32
+        self.handle = wmg_batch_create(geoms, opts, C.c_void_p(torch.cuda.current_stream().cuda_stream))
+        self.sizes = [wmg_batch_sizes(self.handle, i) for i in range(self.count)]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            wmg_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, bs, solver=SOLVER_GMRES, preconditioned=True, max_iter=100, rtol=1e-4, restart=20,
+              outs=None):
+        torch = self._torch
+        if outs is None:
+            outs = [torch.empty(N, dtype=self.dtype, device="cuda") for N, _ in self.sizes]
+        for t, (N, M) in zip(bs, self.sizes):
+            if t.dtype != self.dtype or t.numel() != M or not t.is_cuda or not t.is_contiguous():
+                raise TypeError("sinogram tensors must match the batch's sizes and dtype")
+        info = (wmg_solve_info * self.count)()
+        rc = wmg_batch_solve(self.handle, solver, 1 if preconditioned else 0, [t.data_ptr() for t in bs],
+                             [t.data_ptr() for t in outs], max_iter, rtol, restart, info, None,
+                             C.c_void_p(torch.cuda.current_stream().cuda_stream))
+        return outs, [(info[i].iters, info[i].status, info[i].rel_res) for i in range(self.count)], rc

@@ -127,7 +127,8 @@ struct TileList {
     }
 };
 
-// A set of (real or virtual) problems sharing one geometry, with its tiles.
+// A set of (real or virtual) problems with their tiles (problems may have
+// different geometries; each tile belongs to one problem).
 struct ProbSet {
     int nprob = 0;
     std::vector<ProbDev> h;
@@ -136,72 +137,97 @@ struct ProbSet {
     int haar_smem = 0;
 };
 
-struct Node { int k0, k1; };
+// One geometry of a plan with its device tables.
+struct Geo {
+    GeomDev g{};
+    int64_t N = 0, M = 0, nnz = 0;
+    bool has_wmg = true, unit_bins = true;
+    int hd = 0;                 // hybrid depth in use: min(hybrid_depth, L), 0 for additive
+    int haar_W = 1;             // Haar strip width (pixels)
+    DevBuf cs64, cs32, csx, angf, dinv, leafinv, sirtR, sirtC;
+};
 
 }  // namespace wmg
 
 // ---------------------------------------------------------------------------
-// The plan
+// The plan: one or more geometries and a table of problem slots. A plan made
+// by wmg_plan_create has one geometry and any number of same-geometry
+// problems per call; a batch (wmg_batch_create) has a fixed list of problems
+// of several geometries, stored grouped by geometry.
 // ---------------------------------------------------------------------------
 struct wmg_plan {
     int prec = WMG_PREC_F64;
     size_t esz = 8;
-    wmg::GeomDev g{};           // host copy (device pointers inside)
     wmg_opts opts{};
-    int64_t N = 0, M = 0;
-    wmg::DevBuf d_geom, cs64, cs32, csx, angf, dinv, leafinv, sirtR, sirtC;
-    bool unit_bins = true;      // unit bin spacing and zero offset
-    int cap = 0;                // problems the tables are built for
+    std::vector<std::unique_ptr<wmg::Geo>> geos;
+    wmg::DevBuf d_geom;         // GeomDev array, one per geometry
+    bool unit_bins = true;      // every geometry has unit bins, zero offset
+    bool batch = false;         // fixed problem list
+    int cap = 0;                // problem slots
+    std::vector<int> pgeo;      // geometry of each slot
+    std::vector<int64_t> img_off, sino_off;
+    int64_t Ntot = 0, Mtot = 0;
+    std::vector<int> order;     // batch: slot of the caller's problem i
     wmg::ProbSet real;
     std::map<std::vector<int>, std::unique_ptr<wmg::ProbSet>> bands;   // band-update groups
     std::map<std::vector<int>, std::unique_ptr<wmg::TileList>> leafsets;
     std::map<std::vector<int>, std::unique_ptr<wmg::DevBuf>> segsets;
-    int band_cap = 0;
-    // FP64 pools (per problem: N or M elements)
+    // FP64 pools (all slots back to back)
     wmg::DevBuf x, s, z, p, f, w, t, u, r;
     // operator-precision pools
-    wmg::DevBuf p_op, pT_op, z_op, zT_op, r1, C, E, q, r_op, sinoS, b_op;
+    wmg::DevBuf p_op, pT_op, z_op, zT_op, r1, C, E, q, r_op, sinoS, b_op, x_io;
     std::vector<std::unique_ptr<wmg::DevBuf>> csave, c2, e2;   // per hybrid depth
     wmg::DevBuf band_img, band_imgT, band_img2, band_sino;
     // scalars and partials
     wmg::DevBuf S, part_a, part_b, part_c, lam, hist;
     // GMRES
     wmg::DevBuf V, H, gcs, gsn, gg, gy, h1, h2, jn, done;
-    int gm_restart = 0;
-    bool has_wmg = true;        // levels >= 1: the WMG preconditioner is set up
-    int64_t nnz = 0;            // nonzeros of W
     // profiling: (kind 0 = project / 1 = backproject, images, start, stop)
     bool profiling = false;
     struct ProfRec { int kind; int images; cudaEvent_t e0, e1; };
     std::vector<ProfRec> prof;
+    const wmg::Geo &geo(int slot) const { return *geos[pgeo[slot]]; }
+    bool has_wmg() const
+    {
+        for (auto &g : geos)
+            if (!g->has_wmg) return false;
+        return true;
+    }
 };
 
 namespace wmg {
 
 // ---- tile lists ------------------------------------------------------------
-static void build_tiles(const wmg_plan *pl, ProbSet &ps)
+// Haar strip width of a geometry: a whole number of 2^L blocks that divides
+// the image side, at most max(B, 4096 / B) pixels wide.
+static int haar_width(const GeomDev &g)
 {
-    const GeomDev &g = pl->g;
-    ps.proj.h.clear(); ps.bp.h.clear(); ps.haar.h.clear(); ps.vimg.h.clear(); ps.vsino.h.clear();
-    // strip width: a whole number of blocks that divides the image side, at
-    // most max(B, 4096 / B) pixels wide
     const int nb = g.n / g.B, wmax = std::max(1, std::max(g.B, 4096 / g.B) / g.B);
     int wb = 1;
     for (int d = 1; d <= std::min(nb, wmax); ++d)
         if (nb % d == 0) wb = d;
-    const int W = wb * g.B;
-    ps.haar_smem = g.B * (W + 1);
+    return wb * g.B;
+}
+
+static void build_tiles(const wmg_plan *pl, ProbSet &ps)
+{
+    ps.proj.h.clear(); ps.bp.h.clear(); ps.haar.h.clear(); ps.vimg.h.clear(); ps.vsino.h.clear();
+    ps.haar_smem = 0;
     for (int q = 0; q < ps.nprob; ++q) {
+        const Geo &G = *pl->geos[ps.h[q].geom];
+        const GeomDev &g = G.g;
+        const int W = G.haar_W;
+        ps.haar_smem = std::max(ps.haar_smem, g.B * (W + 1));
         for (int a = 0; a < g.m; ++a)
             for (int k0 = 0; k0 < g.D; k0 += 32) ps.proj.h.push_back(make_int4(q, a, k0, 0));
         for (int iy = 0; iy < g.n; iy += 32)
             for (int ix = 0; ix < g.n; ix += 32) ps.bp.h.push_back(make_int4(q, iy, ix, 0));
         for (int cy = 0; cy < g.nc; ++cy)
             for (int x0 = 0; x0 < g.n; x0 += W) ps.haar.h.push_back(make_int4(q, cy * g.B, x0, W));
-        for (int64_t s0 = 0; s0 < pl->N; s0 += 8192)
-            ps.vimg.h.push_back(make_int4(q, (int)s0, (int)std::min<int64_t>(8192, pl->N - s0), 0));
-        for (int64_t s0 = 0; s0 < pl->M; s0 += 8192)
-            ps.vsino.h.push_back(make_int4(q, (int)s0, (int)std::min<int64_t>(8192, pl->M - s0), 0));
+        for (int64_t s0 = 0; s0 < G.N; s0 += 8192)
+            ps.vimg.h.push_back(make_int4(q, (int)s0, (int)std::min<int64_t>(8192, G.N - s0), 0));
+        for (int64_t s0 = 0; s0 < G.M; s0 += 8192)
+            ps.vsino.h.push_back(make_int4(q, (int)s0, (int)std::min<int64_t>(8192, G.M - s0), 0));
     }
 }
 
@@ -213,18 +239,29 @@ static bool upload_set(ProbSet &ps, cudaStream_t st)
            ps.vimg.upload(ps.nprob, st) && ps.vsino.upload(ps.nprob, st);
 }
 
-// Tables for `count` real problems: problem q's vectors at q*N / q*M.
-static int32_t ensure_count(wmg_plan *pl, int count, cudaStream_t st)
+// (Re)build the slot tables from pgeo (offsets in slot order).
+static int32_t set_slots(wmg_plan *pl, cudaStream_t st)
 {
-    if (count == pl->cap) return WMG_OK;
+    const int count = (int)pl->pgeo.size();
+    pl->img_off.assign(count, 0);
+    pl->sino_off.assign(count, 0);
+    int64_t ni = 0, ns = 0;
+    for (int q = 0; q < count; ++q) {
+        pl->img_off[q] = ni;
+        pl->sino_off[q] = ns;
+        ni += pl->geo(q).N;
+        ns += pl->geo(q).M;
+    }
+    pl->Ntot = ni;
+    pl->Mtot = ns;
     ProbSet &ps = pl->real;
     ps.nprob = count;
     ps.h.assign(count, ProbDev{});
     for (int q = 0; q < count; ++q) {
         ProbDev &d = ps.h[q];
-        d.geom = 0; d.slot = q;
-        d.img = (int64_t)q * pl->N; d.sino = (int64_t)q * pl->M; d.coef = (int64_t)q * pl->N;
-        d.kin0 = 0; d.kin1 = pl->g.K; d.kout0 = 0; d.kout1 = pl->g.K;
+        d.geom = pl->pgeo[q]; d.slot = q;
+        d.img = pl->img_off[q]; d.sino = pl->sino_off[q]; d.coef = pl->img_off[q];
+        d.kin0 = 0; d.kin1 = pl->geo(q).g.K; d.kout0 = 0; d.kout1 = pl->geo(q).g.K;
     }
     build_tiles(pl, ps);
     if (!upload_set(ps, st)) return fail(WMG_ERR_OOM, "work-list allocation failed");
@@ -232,14 +269,26 @@ static int32_t ensure_count(wmg_plan *pl, int count, cudaStream_t st)
     pl->leafsets.clear();
     pl->segsets.clear();
     pl->cap = count;
-    // per-problem scalars
     if (!pl->S.ensure((size_t)count * NSCAL * sizeof(double)) ||
         !pl->lam.ensure((size_t)count * sizeof(double)))
         return fail(WMG_ERR_OOM, "scalar allocation failed");
-    std::vector<double> lam(count, pl->g.lambda);
+    std::vector<double> lam(count);
+    for (int q = 0; q < count; ++q) lam[q] = pl->geo(q).g.lambda;
     cudaMemcpyAsync(pl->lam.p, lam.data(), count * sizeof(double), cudaMemcpyHostToDevice, st);
     cudaStreamSynchronize(st);
     return WMG_OK;
+}
+
+// Single-geometry plans: `count` problems of geometry 0 back to back.
+static int32_t ensure_count(wmg_plan *pl, int count, cudaStream_t st)
+{
+    if (pl->batch) {
+        if (count != pl->cap) return fail(WMG_ERR_INVALID_ARG, "a batch has a fixed problem count");
+        return WMG_OK;
+    }
+    if (count == pl->cap) return WMG_OK;
+    pl->pgeo.assign(count, 0);
+    return set_slots(pl, st);
 }
 
 static bool ensure_pool(DevBuf &b, int64_t elems, size_t esz) { return b.ensure((size_t)elems * esz); }
@@ -340,31 +389,50 @@ static void finalize(wmg_plan *pl, int op, const TileList &ta, const double *pa,
     launch_finalize(f, st);
 }
 
-// Band-update group tables: virtual problem v = q * G + i for node i.
-static ProbSet *band_set(wmg_plan *pl, const std::vector<Node> &nodes, bool full_in, cudaStream_t st)
+// ---------------------------------------------------------------------------
+// WMG coarse correction (Section 3.1.2 recursion) on the packet coefficients.
+// A tree node at depth d is named by its path prefix q in [0, 4^d); for a
+// slot with L levels it owns the leaves [q 4^(L-d), (q+1) 4^(L-d)). The LL
+// child of q is 4q, the other children 4q+1 .. 4q+3.
+// ---------------------------------------------------------------------------
+static inline int node_lo(int L, int d, int q) { return q << (2 * (L - d)); }
+static inline int node_hi(int L, int d, int q) { return (q + 1) << (2 * (L - d)); }
+
+static std::vector<int> make_key(int tag, int d, const std::vector<int> &nodes, const std::vector<int> &slots)
 {
-    std::vector<int> key;
-    key.push_back(full_in ? 1 : 0);
-    for (const Node &n : nodes) { key.push_back(n.k0); key.push_back(n.k1); }
+    std::vector<int> key{tag, d, (int)nodes.size()};
+    key.insert(key.end(), nodes.begin(), nodes.end());
+    key.insert(key.end(), slots.begin(), slots.end());
+    return key;
+}
+
+// Band-update group tables: one virtual image per (slot, node); it reads the
+// slot's correction coefficients and writes the slot's residual coefficients.
+static ProbSet *band_set(wmg_plan *pl, int d, const std::vector<int> &nodes, const std::vector<int> &slots,
+                         bool full_in, cudaStream_t st)
+{
+    const std::vector<int> key = make_key(full_in ? 1 : 0, d, nodes, slots);
     auto it = pl->bands.find(key);
     if (it != pl->bands.end()) return it->second.get();
     auto ps = std::make_unique<ProbSet>();
-    const int G = (int)nodes.size(), B = pl->cap;
-    ps->nprob = B * G;
+    ps->nprob = (int)(slots.size() * nodes.size());
     ps->h.resize(ps->nprob);
-    for (int q = 0; q < B; ++q)
-        for (int i = 0; i < G; ++i) {
-            ProbDev &d = ps->h[q * G + i];
-            const int v = q * G + i;
-            const int qq = (nodes[i].k1 - nodes[i].k0) / 4;
-            d.geom = 0; d.slot = q;
-            d.img = (int64_t)v * pl->N; d.sino = (int64_t)v * pl->M; d.coef = (int64_t)q * pl->N;
-            if (full_in) {          // symmetric closing step: all of the node in, LL child out
-                d.kin0 = nodes[i].k0; d.kin1 = nodes[i].k1;
-                d.kout0 = nodes[i].k0; d.kout1 = nodes[i].k0 + qq;
-            } else {                // hybrid step: LL child in, the three other children out
-                d.kin0 = nodes[i].k0; d.kin1 = nodes[i].k0 + qq;
-                d.kout0 = nodes[i].k0 + qq; d.kout1 = nodes[i].k1;
+    int64_t oi = 0, os = 0;
+    int v = 0;
+    for (int slot : slots)
+        for (int q : nodes) {
+            const Geo &G = pl->geo(slot);
+            const int L = G.g.L;
+            ProbDev &pd = ps->h[v++];
+            pd.geom = pl->pgeo[slot]; pd.slot = slot;
+            pd.img = oi; pd.sino = os; pd.coef = pl->img_off[slot];
+            oi += G.N; os += G.M;
+            const int lo = node_lo(L, d, q), hi = node_hi(L, d, q);
+            const int ll_hi = node_hi(L, d + 1, 4 * q);
+            if (full_in) {          // symmetric closing step: the whole node in, its LL child out
+                pd.kin0 = lo; pd.kin1 = hi; pd.kout0 = lo; pd.kout1 = ll_hi;
+            } else {                // hybrid step: the LL child in, the three other children out
+                pd.kin0 = lo; pd.kin1 = ll_hi; pd.kout0 = ll_hi; pd.kout1 = hi;
             }
         }
     build_tiles(pl, *ps);
@@ -374,45 +442,53 @@ static ProbSet *band_set(wmg_plan *pl, const std::vector<Node> &nodes, bool full
     return raw;
 }
 
-static TileList *leaf_tiles(wmg_plan *pl, const std::vector<Node> &nodes, cudaStream_t st)
+// Leaf-solve tiles: {first slot of a run of same-geometry slots, leaf, run length}.
+static TileList *leaf_tiles(wmg_plan *pl, int d, const std::vector<int> &nodes, const std::vector<int> &slots,
+                            cudaStream_t st)
 {
-    std::vector<int> key;
-    for (const Node &n : nodes) { key.push_back(n.k0); key.push_back(n.k1); }
+    const std::vector<int> key = make_key(2, d, nodes, slots);
     auto it = pl->leafsets.find(key);
     if (it != pl->leafsets.end()) return it->second.get();
     auto tl = std::make_unique<TileList>();
-    for (const Node &n : nodes)
-        for (int k = n.k0; k < n.k1; ++k) tl->h.push_back(make_int4(0, k, pl->cap, 0));
-    // leaf tiles are not per problem: upload with a one-entry range table
-    if (!tl->upload(1, st)) return nullptr;
+    size_t i = 0;
+    while (i < slots.size()) {
+        size_t j = i + 1;
+        while (j < slots.size() && slots[j] == slots[j - 1] + 1 && pl->pgeo[slots[j]] == pl->pgeo[slots[i]]) ++j;
+        const int L = pl->geo(slots[i]).g.L;
+        for (int q : nodes)
+            for (int k = node_lo(L, d, q); k < node_hi(L, d, q); ++k)
+                tl->h.push_back(make_int4(slots[i], k, (int)(j - i), 0));
+        i = j;
+    }
+    if (!tl->upload(pl->cap, st)) return nullptr;
     TileList *raw = tl.get();
     pl->leafsets[key] = std::move(tl);
     return raw;
 }
 
-template <class T>
-__global__ void k_coef_add(T *E, const T *E2, const int2 *segs, int nseg, int64_t N, int nprob)
+// E[seg] += E2[seg] over absolute element segments of the coefficient pool.
+__global__ void k_coef_add(double *E, const double *E2, const longlong2 *segs, int nseg)
 {
-    // segs: element ranges inside one problem's coefficient vector
-    for (int q = 0; q < nprob; ++q)
-        for (int sgi = 0; sgi < nseg; ++sgi) {
-            const int2 sg = segs[sgi];
-            for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < sg.y; i += gridDim.x * blockDim.x)
-                E[(int64_t)q * N + sg.x + i] += E2[(int64_t)q * N + sg.x + i];
-        }
+    for (int sgi = 0; sgi < nseg; ++sgi) {
+        const longlong2 sg = segs[sgi];
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < sg.y;
+             i += (long long)gridDim.x * blockDim.x)
+            E[sg.x + i] += E2[sg.x + i];
+    }
 }
 
 // One band-local residual update for a group of nodes (hybrid cycle): for
-// every node, C[out range] -= Q_out^T (W^T W + lambda) Q_in E[in range].
+// every slot and node, C[out range] -= Q_out^T (W^T W + lambda) Q_in E[in range].
 template <class T>
-static int32_t band_update(wmg_plan *pl, const std::vector<Node> &nodes, bool full_in, DevBuf &Cb,
-                           DevBuf &Eb, cudaStream_t st)
+static int32_t band_update(wmg_plan *pl, int d, const std::vector<int> &nodes, const std::vector<int> &slots,
+                           bool full_in, DevBuf &Cb, DevBuf &Eb, cudaStream_t st)
 {
-    ProbSet *bs = band_set(pl, nodes, full_in, st);
+    ProbSet *bs = band_set(pl, d, nodes, slots, full_in, st);
     if (!bs) return fail(WMG_ERR_OOM, "band tables");
-    const int64_t V = bs->nprob;
-    if (!ensure_pool(pl->band_img, V * pl->N, pl->esz) || !ensure_pool(pl->band_imgT, V * pl->N, pl->esz) ||
-        !ensure_pool(pl->band_img2, V * pl->N, 8) || !ensure_pool(pl->band_sino, V * pl->M, pl->esz))
+    int64_t VN = 0, VM = 0;
+    for (const ProbDev &pd : bs->h) { VN += pl->geos[pd.geom]->N; VM += pl->geos[pd.geom]->M; }
+    if (!ensure_pool(pl->band_img, VN, pl->esz) || !ensure_pool(pl->band_imgT, VN, pl->esz) ||
+        !ensure_pool(pl->band_img2, VN, 8) || !ensure_pool(pl->band_sino, VM, pl->esz))
         return fail(WMG_ERR_OOM, "band pools");
     const GeomDev *G = pl->d_geom.as<GeomDev>();
     const double *S = pl->S.as<double>();
@@ -439,72 +515,86 @@ static int32_t band_update(wmg_plan *pl, const std::vector<Node> &nodes, bool fu
     return WMG_OK;
 }
 
-// Coarse correction of the WMG cycle for a group of nodes at depth d
-// (Section 3.1.2 recursion, siblings processed together): leaf solves at
-// depth >= hybrid depth, otherwise LL child first, one band-local residual
-// update, the other three children, and (symmetric cycle) the LL child again
-// from the residual of the whole node correction.
+// Coarse correction for the nodes `nodes` at depth d of the slots `slots`
+// (Section 3.1.2, siblings processed together): slots whose hybrid depth is
+// reached solve their leaves exactly; the others correct the LL child first,
+// update the residual of the other three children once, correct them, and
+// (symmetric cycle) correct the LL child again from the residual of the
+// whole node correction.
 template <class T>
-static int32_t coarse(wmg_plan *pl, int d, const std::vector<Node> &nodes, DevBuf &Cb, DevBuf &Eb,
-                      cudaStream_t st)
+static int32_t coarse(wmg_plan *pl, int d, const std::vector<int> &nodes, const std::vector<int> &slots,
+                      DevBuf &Cb, DevBuf &Eb, cudaStream_t st)
 {
-    const wmg_opts &o = pl->opts;
-    const int hd = (o.cycle == WMG_CYCLE_ADDITIVE) ? 0 : std::min(o.hybrid_depth, pl->g.L);
-    if (d >= hd) {
-        TileList *lt = leaf_tiles(pl, nodes, st);
+    std::vector<int> done, deeper;
+    for (int s : slots) (d >= pl->geo(s).hd ? done : deeper).push_back(s);
+    if (!done.empty()) {
+        TileList *lt = leaf_tiles(pl, d, nodes, done, st);
         if (!lt) return fail(WMG_ERR_OOM, "leaf tables");
         launch_leaf_apply(pl->d_geom.as<GeomDev>(), pl->real.d.as<ProbDev>(), lt->tiles.as<int4>(),
                           lt->n, Cb.as<double>(), Eb.as<double>(), 0, pl->S.as<double>(), st);
-        return WMG_OK;
     }
-    std::vector<Node> lls, rests;
-    for (const Node &nd : nodes) {
-        const int qq = (nd.k1 - nd.k0) / 4;
-        lls.push_back({nd.k0, nd.k0 + qq});
-        for (int c = 1; c < 4; ++c) rests.push_back({nd.k0 + c * qq, nd.k0 + (c + 1) * qq});
+    if (deeper.empty()) return WMG_OK;
+    std::vector<int> lls, rests;
+    for (int q : nodes) {
+        lls.push_back(4 * q);
+        for (int c = 1; c < 4; ++c) rests.push_back(4 * q + c);
     }
-    const bool sym = o.cycle == WMG_CYCLE_SYMMETRIC;
-    const size_t cbytes = (size_t)pl->cap * pl->N * sizeof(double);
+    const bool sym = pl->opts.cycle == WMG_CYCLE_SYMMETRIC;
+    const size_t cbytes = (size_t)pl->Ntot * sizeof(double);
     if (sym) cudaMemcpyAsync(pl->csave[d]->p, Cb.p, cbytes, cudaMemcpyDeviceToDevice, st);
-    int32_t rc = coarse<T>(pl, d + 1, lls, Cb, Eb, st);
+    int32_t rc = coarse<T>(pl, d + 1, lls, deeper, Cb, Eb, st);
     if (rc) return rc;
-    if ((rc = band_update<T>(pl, nodes, false, Cb, Eb, st))) return rc;
-    if ((rc = coarse<T>(pl, d + 1, rests, Cb, Eb, st))) return rc;
+    if ((rc = band_update<T>(pl, d, nodes, deeper, false, Cb, Eb, st))) return rc;
+    if ((rc = coarse<T>(pl, d + 1, rests, deeper, Cb, Eb, st))) return rc;
     if (sym) {
         DevBuf &C2 = *pl->c2[d], &E2 = *pl->e2[d];
         cudaMemcpyAsync(C2.p, pl->csave[d]->p, cbytes, cudaMemcpyDeviceToDevice, st);
-        if ((rc = band_update<T>(pl, nodes, true, C2, Eb, st))) return rc;
-        if ((rc = coarse<T>(pl, d + 1, lls, C2, E2, st))) return rc;
-        std::vector<int> key;
-        std::vector<int2> segs;
-        for (const Node &n : lls) {
-            key.push_back(n.k0); key.push_back(n.k1);
-            segs.push_back(make_int2((int)((int64_t)n.k0 * pl->g.P), (int)((int64_t)(n.k1 - n.k0) * pl->g.P)));
-        }
+        if ((rc = band_update<T>(pl, d, nodes, deeper, true, C2, Eb, st))) return rc;
+        if ((rc = coarse<T>(pl, d + 1, lls, deeper, C2, E2, st))) return rc;
+        const std::vector<int> key = make_key(3, d, nodes, deeper);
         auto it = pl->segsets.find(key);
         if (it == pl->segsets.end()) {
+            std::vector<longlong2> segs;
+            for (int s : deeper) {
+                const Geo &G = pl->geo(s);
+                for (int q : lls) {
+                    const long long lo = node_lo(G.g.L, d + 1, q), hi = node_hi(G.g.L, d + 1, q);
+                    longlong2 sg;
+                    sg.x = pl->img_off[s] + lo * G.g.P;
+                    sg.y = (hi - lo) * G.g.P;
+                    segs.push_back(sg);
+                }
+            }
             auto db = std::make_unique<DevBuf>();
-            if (!db->ensure(segs.size() * sizeof(int2))) return fail(WMG_ERR_OOM, "segments");
-            cudaMemcpy(db->p, segs.data(), segs.size() * sizeof(int2), cudaMemcpyHostToDevice);
+            if (!db->ensure(segs.size() * sizeof(longlong2))) return fail(WMG_ERR_OOM, "segments");
+            cudaMemcpy(db->p, segs.data(), segs.size() * sizeof(longlong2), cudaMemcpyHostToDevice);
+            db->bytes = segs.size() * sizeof(longlong2);
             it = pl->segsets.emplace(key, std::move(db)).first;
         }
         count_launches(1);
-        k_coef_add<double><<<num_sms() * 4, 256, 0, st>>>(Eb.as<double>(), E2.as<double>(),
-                                                           it->second->as<int2>(), (int)segs.size(),
-                                                           pl->N, pl->cap);
+        k_coef_add<<<num_sms() * 4, 256, 0, st>>>(Eb.as<double>(), E2.as<double>(),
+                                                   it->second->as<longlong2>(),
+                                                   (int)(it->second->bytes / sizeof(longlong2)));
     }
     return WMG_OK;
 }
 
+static int max_levels(const wmg_plan *pl)
+{
+    int L = 0;
+    for (auto &g : pl->geos) L = std::max(L, g->g.L);
+    return L;
+}
+
 static int32_t ensure_wmg_pools(wmg_plan *pl)
 {
-    const int64_t nN = (int64_t)pl->cap * pl->N, nM = (int64_t)pl->cap * pl->M;
+    const int64_t nN = pl->Ntot, nM = pl->Mtot;
     const size_t e = pl->esz;
     if (!ensure_pool(pl->z, nN, 8) || !ensure_pool(pl->s, nN, 8) || !ensure_pool(pl->z_op, nN, e) ||
         !ensure_pool(pl->zT_op, nN, e) || !ensure_pool(pl->r1, nN, 8) || !ensure_pool(pl->C, nN, 8) ||
         !ensure_pool(pl->E, nN, 8) || !ensure_pool(pl->sinoS, nM, e))
         return fail(WMG_ERR_OOM, "preconditioner pools");
-    const int L = pl->g.L;
+    const int L = max_levels(pl);
     while ((int)pl->csave.size() < L) {
         pl->csave.push_back(std::make_unique<DevBuf>());
         pl->c2.push_back(std::make_unique<DevBuf>());
@@ -556,8 +646,9 @@ static int32_t wmg_apply(wmg_plan *pl, double *s, double *z, bool first_done, bo
     ha.mode = HA_STORE; ha.in = pl->r1.p; ha.out = pl->C.p; ha.S = S;
     launch_haar_analysis<double, double>(G, ps.d.as<ProbDev>(), ps.haar.tiles.as<int4>(), ps.haar.n,
                                          ps.haar_smem, ha, st);
-    std::vector<Node> root{{0, pl->g.K}};
-    int32_t rc = coarse<T>(pl, 0, root, pl->C, pl->E, st);
+    std::vector<int> all(pl->cap);
+    for (int q = 0; q < pl->cap; ++q) all[q] = q;
+    int32_t rc = coarse<T>(pl, 0, std::vector<int>{0}, all, pl->C, pl->E, st);
     if (rc) return rc;
     const bool need_copies_after_syn = copies || o.nu2 > 0;
     HaarArgs hs{};
@@ -579,7 +670,7 @@ static int32_t wmg_apply(wmg_plan *pl, double *s, double *z, bool first_done, bo
 }
 
 // ---------------------------------------------------------------------------
-// plan creation
+// geometry creation and setup
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void k_fill(T *p, int64_t n, T v)
@@ -602,51 +693,144 @@ __global__ void k_recip(const T *in, T *out, int64_t n, double add)
     }
 }
 
-template <class T>
-static int32_t setup_geometry(wmg_plan *pl, cudaStream_t st)
+static int32_t validate(const wmg_geom *g, const wmg_opts *o)
 {
-    const int64_t N = pl->N, M = pl->M;
+    if (!g || !o) return fail(WMG_ERR_INVALID_ARG, "geometry or options NULL");
+    if (g->n < 1 || g->m < 1 || g->D < 1) return fail(WMG_ERR_INVALID_ARG, "n, m and D must be >= 1");
+    if (o->levels < 0 || o->levels > 12) return fail(WMG_ERR_INVALID_ARG, "levels must be in [0, 12]");
+    const int L = o->levels >= 1 ? o->levels - 1 : 0;
+    if (g->n % (1 << L) != 0) return fail(WMG_ERR_INVALID_ARG, "n must be divisible by 2^(levels-1)");
+    const int nc = g->n >> L;
+    if (o->levels >= 1 && nc * nc > 256) return fail(WMG_ERR_INVALID_ARG, "leaf side n/2^(levels-1) must be <= 16");
+    if ((1 << L) > 128) return fail(WMG_ERR_INVALID_ARG, "block side 2^(levels-1) must be <= 128");
+    if (o->nu1 < 0 || o->nu2 < 0 || o->lambda < 0 || o->hybrid_depth < 0 ||
+        o->cycle < WMG_CYCLE_ADDITIVE || o->cycle > WMG_CYCLE_SYMMETRIC ||
+        (o->precision != WMG_PREC_F64 && o->precision != WMG_PREC_F32))
+        return fail(WMG_ERR_INVALID_ARG, "invalid options");
+    if ((int64_t)g->n * g->n > (int64_t)1 << 30 || (int64_t)g->m * g->D > (int64_t)1 << 31)
+        return fail(WMG_ERR_INVALID_ARG, "problem too large");
+    return WMG_OK;
+}
+
+// Host part of a geometry: angle tables and scalar fields.
+static int32_t make_geo(const wmg_geom *g, const wmg_opts *o, Geo &G, cudaStream_t st)
+{
+    G.has_wmg = o->levels >= 1;
+    const int L = G.has_wmg ? o->levels - 1 : 0;
+    const int nc = g->n >> L;
+    G.N = (int64_t)g->n * g->n;
+    G.M = (int64_t)g->m * g->D;
+    GeomDev &gd = G.g;
+    gd.n = g->n; gd.m = g->m; gd.D = g->D; gd.L = L;
+    gd.nc = nc; gd.P = nc * nc; gd.K = 1 << (2 * L); gd.B = 1 << L;
+    gd.h = 1.0 / g->n;
+    gd.dt = g->det_spacing > 0 ? g->det_spacing : 1.0;
+    gd.t0 = g->det_offset;
+    gd.lambda = o->lambda;
+    gd.omega = o->omega > 0 ? o->omega : 1.0;
+    G.hd = (o->cycle == WMG_CYCLE_ADDITIVE || !G.has_wmg) ? 0 : std::min(o->hybrid_depth, L);
+    G.haar_W = haar_width(gd);
+    std::vector<double2> cs;
+    angle_table(g->m, g->angles, cs);
+    std::vector<float2> cs32(g->m);
+    std::vector<float4> csx(g->m);
+    for (int a = 0; a < g->m; ++a) {
+        cs32[a] = make_float2((float)cs[a].x, (float)cs[a].y);
+        // split: 12-significant-bit head (a multiple of 2^-12) and FP32 tail
+        const double ch = std::nearbyint(cs[a].x * 4096.0) / 4096.0;
+        const double sh = std::nearbyint(cs[a].y * 4096.0) / 4096.0;
+        csx[a] = make_float4((float)ch, (float)(cs[a].x - ch), (float)sh, (float)(cs[a].y - sh));
+    }
+    std::vector<AngleF> angf(g->m);
+    fill_angle_table(cs.data(), g->m, angf.data());
+    if (!G.cs64.ensure(g->m * sizeof(double2)) || !G.cs32.ensure(g->m * sizeof(float2)) ||
+        !G.csx.ensure(g->m * sizeof(float4)) || !G.angf.ensure(g->m * sizeof(AngleF)))
+        return fail(WMG_ERR_OOM, "plan allocation failed");
+    WMG_CUDA(cudaMemcpyAsync(G.angf.p, angf.data(), g->m * sizeof(AngleF), cudaMemcpyHostToDevice, st));
+    WMG_CUDA(cudaMemcpyAsync(G.csx.p, csx.data(), g->m * sizeof(float4), cudaMemcpyHostToDevice, st));
+    WMG_CUDA(cudaMemcpyAsync(G.cs64.p, cs.data(), g->m * sizeof(double2), cudaMemcpyHostToDevice, st));
+    WMG_CUDA(cudaMemcpyAsync(G.cs32.p, cs32.data(), g->m * sizeof(float2), cudaMemcpyHostToDevice, st));
+    WMG_CUDA(cudaStreamSynchronize(st));
+    gd.cs64 = G.cs64.as<double2>();
+    gd.cs32 = G.cs32.as<float2>();
+    gd.csx = G.csx.as<float4>();
+    gd.angf = G.angf.as<AngleF>();
+    gd.hf = (float)gd.h;
+    gd.dtf = (float)gd.dt;
+    gd.t0f = (float)gd.t0;
+    gd.hDf = 0.5f * (float)(g->D - 1);
+    G.unit_bins = gd.dt == 1.0 && gd.t0 == 0.0;
+    return WMG_OK;
+}
+
+static int32_t upload_geoms(wmg_plan *pl, cudaStream_t st)
+{
+    std::vector<GeomDev> h;
+    bool unit = true;
+    for (auto &g : pl->geos) { h.push_back(g->g); unit = unit && g->unit_bins; }
+    pl->unit_bins = unit;
+    if (!pl->d_geom.ensure(h.size() * sizeof(GeomDev))) return fail(WMG_ERR_OOM, "geometry table");
+    WMG_CUDA(cudaMemcpyAsync(pl->d_geom.p, h.data(), h.size() * sizeof(GeomDev), cudaMemcpyHostToDevice, st));
+    WMG_CUDA(cudaStreamSynchronize(st));
+    return WMG_OK;
+}
+
+// Device setup of geometry gi: D~ = W^T (W 1) + lambda, SIRT R and C, nnz(W)
+// and the leaf inverses. Runs on a one-slot table of that geometry.
+template <class T>
+static int32_t setup_geometry(wmg_plan *pl, int gi, cudaStream_t st)
+{
+    Geo &G = *pl->geos[gi];
+    const int64_t N = G.N, M = G.M;
+    ProbSet one;
+    one.nprob = 1;
+    one.h.assign(1, ProbDev{});
+    one.h[0].geom = gi;
+    one.h[0].slot = 0;
+    one.h[0].kin1 = one.h[0].kout1 = G.g.K;
+    build_tiles(pl, one);
+    if (!upload_set(one, st)) return fail(WMG_ERR_OOM, "setup tables");
     DevBuf ones_img, ones_sino, tmp_img, tmp_sino;
     if (!ones_img.ensure(N * sizeof(T)) || !ones_sino.ensure(M * sizeof(T)) ||
         !tmp_img.ensure(N * sizeof(T)) || !tmp_sino.ensure(M * sizeof(T)) ||
-        !pl->dinv.ensure(N * sizeof(T)) || !pl->sirtR.ensure(M * sizeof(T)) || !pl->sirtC.ensure(N * sizeof(T)))
+        !G.dinv.ensure(N * sizeof(T)) || !G.sirtR.ensure(M * sizeof(T)) || !G.sirtC.ensure(N * sizeof(T)))
         return fail(WMG_ERR_OOM, "setup allocation failed");
     count_launches(5);
     k_fill<T><<<num_sms() * 4, 256, 0, st>>>(ones_img.as<T>(), N, T(1));
     k_fill<T><<<num_sms() * 4, 256, 0, st>>>(ones_sino.as<T>(), M, T(1));
-    const ProbSet &ps = pl->real;
     // W 1 (row sums) -> R; W^T (W 1) -> D~; W^T 1 (column sums) -> C
-    project<T>(pl, ps, ones_img.p, ones_img.p, tmp_sino.p, nullptr, nullptr, st);
-    k_recip<T><<<num_sms() * 4, 256, 0, st>>>(tmp_sino.as<T>(), pl->sirtR.as<T>(), M, 0.0);
+    project<T>(pl, one, ones_img.p, ones_img.p, tmp_sino.p, nullptr, nullptr, st);
+    k_recip<T><<<num_sms() * 4, 256, 0, st>>>(tmp_sino.as<T>(), G.sirtR.as<T>(), M, 0.0);
     BpArgs a = bp_args(BP_STORE, tmp_sino.p, nullptr);
     a.out_op = tmp_img.p;
-    backproject<T>(pl, ps, a, st);
-    k_recip<T><<<num_sms() * 4, 256, 0, st>>>(tmp_img.as<T>(), pl->dinv.as<T>(), N, pl->g.lambda);
+    backproject<T>(pl, one, a, st);
+    k_recip<T><<<num_sms() * 4, 256, 0, st>>>(tmp_img.as<T>(), G.dinv.as<T>(), N, G.g.lambda);
     a = bp_args(BP_STORE, ones_sino.p, nullptr);
     a.out_op = tmp_img.p;
-    backproject<T>(pl, ps, a, st);
-    k_recip<T><<<num_sms() * 4, 256, 0, st>>>(tmp_img.as<T>(), pl->sirtC.as<T>(), N, 0.0);
+    backproject<T>(pl, one, a, st);
+    k_recip<T><<<num_sms() * 4, 256, 0, st>>>(tmp_img.as<T>(), G.sirtC.as<T>(), N, 0.0);
     unsigned long long *dcount = nullptr;
     WMG_CUDA(cudaMalloc(&dcount, sizeof(unsigned long long)));
     cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), st);
-    launch_count_nnz(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.proj.tiles.as<int4>(), ps.proj.n,
+    launch_count_nnz(pl->d_geom.as<GeomDev>(), one.d.as<ProbDev>(), one.proj.tiles.as<int4>(), one.proj.n,
                      dcount, st);
     unsigned long long hcount = 0;
     cudaMemcpyAsync(&hcount, dcount, sizeof(hcount), cudaMemcpyDeviceToHost, st);
     WMG_CUDA(cudaStreamSynchronize(st));
     cudaFree(dcount);
-    pl->nnz = (int64_t)hcount;
+    G.nnz = (int64_t)hcount;
     WMG_CUDA(cudaGetLastError());
-    pl->g.dinv = pl->dinv.p;
-    pl->g.sirtR = pl->sirtR.p;
-    pl->g.sirtC = pl->sirtC.p;
-    WMG_CUDA(cudaMemcpyAsync(pl->d_geom.p, &pl->g, sizeof(GeomDev), cudaMemcpyHostToDevice, st));
-    if (!pl->has_wmg) return WMG_OK;
-    if (!pl->leafinv.ensure((size_t)pl->g.K * pl->g.P * pl->g.P * sizeof(double)))
+    G.g.dinv = G.dinv.p;
+    G.g.sirtR = G.sirtR.p;
+    G.g.sirtC = G.sirtC.p;
+    int32_t rc = upload_geoms(pl, st);
+    if (rc) return rc;
+    if (!G.has_wmg) return WMG_OK;
+    if (!G.leafinv.ensure((size_t)G.g.K * G.g.P * G.g.P * sizeof(double)))
         return fail(WMG_ERR_OOM, "leaf inverse allocation failed");
-    pl->g.leafinv = pl->leafinv.as<double>();
-    WMG_CUDA(cudaMemcpyAsync(pl->d_geom.p, &pl->g, sizeof(GeomDev), cudaMemcpyHostToDevice, st));
-    int32_t rc = build_leaf_inverses(pl->g, pl->d_geom.as<GeomDev>(), pl->leafinv.as<double>(), st);
+    G.g.leafinv = G.leafinv.as<double>();
+    if ((rc = upload_geoms(pl, st))) return rc;
+    rc = build_leaf_inverses(G.g, pl->d_geom.as<GeomDev>() + gi, G.leafinv.as<double>(), st);
     if (rc) return rc;
     WMG_CUDA(cudaGetLastError());
     return WMG_OK;
@@ -674,72 +858,19 @@ extern "C" int32_t wmg_plan_create(const wmg_geom *g, const wmg_opts *o, void *s
 {
     if (!out) return fail(WMG_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
-    if (!g || !o) return fail(WMG_ERR_INVALID_ARG, "geometry or options NULL");
-    if (g->n < 1 || g->m < 1 || g->D < 1) return fail(WMG_ERR_INVALID_ARG, "n, m and D must be >= 1");
-    if (o->levels < 0 || o->levels > 12) return fail(WMG_ERR_INVALID_ARG, "levels must be in [0, 12]");
-    const bool has_wmg = o->levels >= 1;
-    const int L = has_wmg ? o->levels - 1 : 0;
-    if (g->n % (1 << L) != 0) return fail(WMG_ERR_INVALID_ARG, "n must be divisible by 2^(levels-1)");
-    const int nc = g->n >> L;
-    if (has_wmg && nc * nc > 256) return fail(WMG_ERR_INVALID_ARG, "leaf side n/2^(levels-1) must be <= 16");
-    if ((1 << L) > 128) return fail(WMG_ERR_INVALID_ARG, "block side 2^(levels-1) must be <= 128");
-    if (o->nu1 < 0 || o->nu2 < 0 || o->lambda < 0 || o->hybrid_depth < 0 ||
-        o->cycle < WMG_CYCLE_ADDITIVE || o->cycle > WMG_CYCLE_SYMMETRIC ||
-        (o->precision != WMG_PREC_F64 && o->precision != WMG_PREC_F32))
-        return fail(WMG_ERR_INVALID_ARG, "invalid options");
-    if ((int64_t)g->n * g->n > (int64_t)1 << 30 || (int64_t)g->m * g->D > (int64_t)1 << 31)
-        return fail(WMG_ERR_INVALID_ARG, "problem too large");
+    int32_t rc = validate(g, o);
+    if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     auto pl = std::make_unique<wmg_plan>();
     pl->prec = o->precision;
     pl->esz = o->precision == WMG_PREC_F64 ? 8 : 4;
     pl->opts = *o;
-    pl->has_wmg = has_wmg;
     if (pl->opts.omega <= 0) pl->opts.omega = 1.0;
-    pl->N = (int64_t)g->n * g->n;
-    pl->M = (int64_t)g->m * g->D;
-    GeomDev &gd = pl->g;
-    gd.n = g->n; gd.m = g->m; gd.D = g->D; gd.L = L;
-    gd.nc = nc; gd.P = nc * nc; gd.K = 1 << (2 * L); gd.B = 1 << L;
-    gd.h = 1.0 / g->n;
-    gd.dt = g->det_spacing > 0 ? g->det_spacing : 1.0;
-    gd.t0 = g->det_offset;
-    gd.lambda = o->lambda;
-    gd.omega = pl->opts.omega;
-    std::vector<double2> cs;
-    angle_table(g->m, g->angles, cs);
-    std::vector<float2> cs32(g->m);
-    std::vector<float4> csx(g->m);
-    for (int a = 0; a < g->m; ++a) {
-        cs32[a] = make_float2((float)cs[a].x, (float)cs[a].y);
-        // split: 12-significant-bit head (a multiple of 2^-12) and FP32 tail
-        const double ch = std::nearbyint(cs[a].x * 4096.0) / 4096.0;
-        const double sh = std::nearbyint(cs[a].y * 4096.0) / 4096.0;
-        csx[a] = make_float4((float)ch, (float)(cs[a].x - ch), (float)sh, (float)(cs[a].y - sh));
-    }
-    std::vector<AngleF> angf(g->m);
-    fill_angle_table(cs.data(), g->m, angf.data());
-    if (!pl->cs64.ensure(g->m * sizeof(double2)) || !pl->cs32.ensure(g->m * sizeof(float2)) ||
-        !pl->csx.ensure(g->m * sizeof(float4)) || !pl->angf.ensure(g->m * sizeof(AngleF)) ||
-        !pl->d_geom.ensure(sizeof(GeomDev)))
-        return fail(WMG_ERR_OOM, "plan allocation failed");
-    WMG_CUDA(cudaMemcpyAsync(pl->angf.p, angf.data(), g->m * sizeof(AngleF), cudaMemcpyHostToDevice, st));
-    WMG_CUDA(cudaMemcpyAsync(pl->csx.p, csx.data(), g->m * sizeof(float4), cudaMemcpyHostToDevice, st));
-    WMG_CUDA(cudaMemcpyAsync(pl->cs64.p, cs.data(), g->m * sizeof(double2), cudaMemcpyHostToDevice, st));
-    WMG_CUDA(cudaMemcpyAsync(pl->cs32.p, cs32.data(), g->m * sizeof(float2), cudaMemcpyHostToDevice, st));
-    gd.cs64 = pl->cs64.as<double2>();
-    gd.cs32 = pl->cs32.as<float2>();
-    gd.csx = pl->csx.as<float4>();
-    gd.angf = pl->angf.as<AngleF>();
-    gd.hf = (float)gd.h;
-    gd.dtf = (float)gd.dt;
-    gd.t0f = (float)gd.t0;
-    gd.hDf = 0.5f * (float)(g->D - 1);
-    pl->unit_bins = gd.dt == 1.0 && gd.t0 == 0.0;
-    WMG_CUDA(cudaMemcpyAsync(pl->d_geom.p, &gd, sizeof(GeomDev), cudaMemcpyHostToDevice, st));
-    int32_t rc = ensure_count(pl.get(), 1, st);
-    if (rc) return rc;
-    rc = pl->prec == WMG_PREC_F64 ? setup_geometry<double>(pl.get(), st) : setup_geometry<float>(pl.get(), st);
+    pl->geos.push_back(std::make_unique<Geo>());
+    if ((rc = make_geo(g, o, *pl->geos[0], st))) return rc;
+    if ((rc = upload_geoms(pl.get(), st))) return rc;
+    if ((rc = ensure_count(pl.get(), 1, st))) return rc;
+    rc = pl->prec == WMG_PREC_F64 ? setup_geometry<double>(pl.get(), 0, st) : setup_geometry<float>(pl.get(), 0, st);
     if (rc) return rc;
     WMG_CUDA(cudaStreamSynchronize(st));
     *out = pl.release();
@@ -757,7 +888,7 @@ extern "C" int32_t wmg_plan_destroy(wmg_plan *plan)
 extern "C" int32_t wmg_plan_nnz(const wmg_plan *plan, int64_t *nnz)
 {
     if (!plan || !nnz) return fail(WMG_ERR_INVALID_ARG, "wmg_plan_nnz: bad arguments");
-    *nnz = plan->nnz;
+    *nnz = plan->geos[0]->nnz;
     return WMG_OK;
 }
 
@@ -790,25 +921,31 @@ extern "C" int32_t wmg_profile_end(wmg_plan *plan, wmg_profile_stats *out, void 
         cudaEventDestroy(r.e1);
     }
     plan->prof.clear();
-    out->nnz_per_image = (double)plan->nnz;
+    out->nnz_per_image = (double)plan->geos[0]->nnz;
     return WMG_OK;
 }
 
 extern "C" int32_t wmg_plan_sizes(const wmg_plan *plan, int64_t *N, int64_t *M)
 {
     if (!plan) return fail(WMG_ERR_INVALID_ARG, "plan is NULL");
-    if (N) *N = plan->N;
-    if (M) *M = plan->M;
+    if (N) *N = plan->geos[0]->N;
+    if (M) *M = plan->geos[0]->M;
     return WMG_OK;
 }
 
 #define WMG_DISPATCH(pl, fn, ...) \
     ((pl)->prec == WMG_PREC_F64 ? fn<double>(__VA_ARGS__) : fn<float>(__VA_ARGS__))
 
-template <class T>
-static int32_t do_project(wmg_plan *pl, int count, const void *x, void *b, cudaStream_t st)
+static int32_t single_geometry(wmg_plan *pl, const char *what)
 {
-    if (!ensure_pool(pl->pT_op, (int64_t)count * pl->N, pl->esz)) return fail(WMG_ERR_OOM, "workspace");
+    if (pl->batch) return fail(WMG_ERR_INVALID_ARG, std::string(what) + ": not available on a batch");
+    return WMG_OK;
+}
+
+template <class T>
+static int32_t do_project(wmg_plan *pl, const void *x, void *b, cudaStream_t st)
+{
+    if (!ensure_pool(pl->pT_op, pl->Ntot, pl->esz)) return fail(WMG_ERR_OOM, "workspace");
     const ProbSet &ps = pl->real;
     launch_transpose<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.bp.tiles.as<int4>(), ps.bp.n, x,
                         pl->pT_op.p, st);
@@ -820,10 +957,11 @@ static int32_t do_project(wmg_plan *pl, int count, const void *x, void *b, cudaS
 extern "C" int32_t wmg_project(wmg_plan *pl, int32_t count, const void *x, void *b, void *stream)
 {
     if (!pl || !x || !b || count < 1) return fail(WMG_ERR_INVALID_ARG, "wmg_project: bad arguments");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int32_t rc = ensure_count(pl, count, st);
+    int32_t rc = single_geometry(pl, "wmg_project");
     if (rc) return rc;
-    return WMG_DISPATCH(pl, do_project, pl, count, x, b, st);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((rc = ensure_count(pl, count, st))) return rc;
+    return WMG_DISPATCH(pl, do_project, pl, x, b, st);
 }
 
 template <class T>
@@ -839,9 +977,10 @@ static int32_t do_backproject(wmg_plan *pl, const void *b, void *x, cudaStream_t
 extern "C" int32_t wmg_backproject(wmg_plan *pl, int32_t count, const void *b, void *x, void *stream)
 {
     if (!pl || !x || !b || count < 1) return fail(WMG_ERR_INVALID_ARG, "wmg_backproject: bad arguments");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int32_t rc = ensure_count(pl, count, st);
+    int32_t rc = single_geometry(pl, "wmg_backproject");
     if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((rc = ensure_count(pl, count, st))) return rc;
     return WMG_DISPATCH(pl, do_backproject, pl, b, x, st);
 }
 
@@ -867,38 +1006,43 @@ static int32_t do_haar(wmg_plan *pl, bool analysis, const void *in, void *out, c
 extern "C" int32_t wmg_haar_analysis(wmg_plan *pl, int32_t count, const void *x, void *c, void *stream)
 {
     if (!pl || !x || !c || count < 1) return fail(WMG_ERR_INVALID_ARG, "wmg_haar_analysis: bad arguments");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int32_t rc = ensure_count(pl, count, st);
+    int32_t rc = single_geometry(pl, "wmg_haar_analysis");
     if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((rc = ensure_count(pl, count, st))) return rc;
     return WMG_DISPATCH(pl, do_haar, pl, true, x, c, st);
 }
 
 extern "C" int32_t wmg_haar_synthesis(wmg_plan *pl, int32_t count, const void *c, void *x, void *stream)
 {
     if (!pl || !x || !c || count < 1) return fail(WMG_ERR_INVALID_ARG, "wmg_haar_synthesis: bad arguments");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int32_t rc = ensure_count(pl, count, st);
+    int32_t rc = single_geometry(pl, "wmg_haar_synthesis");
     if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((rc = ensure_count(pl, count, st))) return rc;
     return WMG_DISPATCH(pl, do_haar, pl, false, c, x, st);
 }
 
 extern "C" int32_t wmg_leaf_inverse(wmg_plan *pl, int64_t k, void *out, void *stream)
 {
-    if (!pl || !out || k < 0 || k >= pl->g.K || !pl->has_wmg)
+    if (!pl || !out || pl->batch || !pl->geos[0]->has_wmg || k < 0 || k >= pl->geos[0]->g.K)
         return fail(WMG_ERR_INVALID_ARG, "wmg_leaf_inverse: bad arguments (or a plan without WMG levels)");
-    const int64_t PP = (int64_t)pl->g.P * pl->g.P;
+    const Geo &G = *pl->geos[0];
+    const int64_t PP = (int64_t)G.g.P * G.g.P;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (pl->prec == WMG_PREC_F64)
-        WMG_CUDA(cudaMemcpyAsync(out, pl->leafinv.as<double>() + k * PP, PP * sizeof(double),
+        WMG_CUDA(cudaMemcpyAsync(out, G.leafinv.as<double>() + k * PP, PP * sizeof(double),
                                  cudaMemcpyDeviceToDevice, st));
     else
-        count_launches(1), k_to_f32<<<num_sms(), 256, 0, st>>>(pl->leafinv.as<double>() + k * PP, static_cast<float *>(out), PP);
+        count_launches(1), k_to_f32<<<num_sms(), 256, 0, st>>>(G.leafinv.as<double>() + k * PP,
+                                                               static_cast<float *>(out), PP);
     WMG_CUDA(cudaGetLastError());
     return WMG_OK;
 }
 
-static void init_scalars(wmg_plan *pl, int count, double rtol, int max_iter, cudaStream_t st)
+static void init_scalars(wmg_plan *pl, double rtol, int max_iter, cudaStream_t st)
 {
+    const int count = pl->cap;
     std::vector<double> S((size_t)count * NSCAL, 0.0);
     for (int q = 0; q < count; ++q) {
         double *s = &S[(size_t)q * NSCAL];
@@ -917,7 +1061,7 @@ static int32_t do_precond(wmg_plan *pl, const void *s_in, void *z_out, cudaStrea
     int32_t rc = ensure_wmg_pools(pl);
     if (rc) return rc;
     if (!ensure_partials(pl, 1)) return fail(WMG_ERR_OOM, "partials");
-    init_scalars(pl, pl->cap, 0.0, 1, st);
+    init_scalars(pl, 0.0, 1, st);
     ImgArgs ia{};
     ia.in_op = s_in;
     ia.z = pl->s.as<double>();
@@ -936,47 +1080,55 @@ static int32_t do_precond(wmg_plan *pl, const void *s_in, void *z_out, cudaStrea
 extern "C" int32_t wmg_precond_apply(wmg_plan *pl, int32_t count, const void *s, void *z, void *stream)
 {
     if (!pl || !s || !z || count < 1) return fail(WMG_ERR_INVALID_ARG, "wmg_precond_apply: bad arguments");
-    if (!pl->has_wmg) return fail(WMG_ERR_INVALID_ARG, "wmg_precond_apply: the plan has no WMG levels");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int32_t rc = ensure_count(pl, count, st);
+    int32_t rc = single_geometry(pl, "wmg_precond_apply");
     if (rc) return rc;
+    if (!pl->has_wmg()) return fail(WMG_ERR_INVALID_ARG, "wmg_precond_apply: the plan has no WMG levels");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((rc = ensure_count(pl, count, st))) return rc;
     return WMG_DISPATCH(pl, do_precond, pl, s, z, st);
 }
 
 // ---------------------------------------------------------------------------
-// Solvers
+// Solvers (every slot of the plan's table; b and x in slot layout)
 // ---------------------------------------------------------------------------
-static int32_t any_active(wmg_plan *pl, int count, cudaStream_t st, bool *any)
+static int32_t any_active(wmg_plan *pl, cudaStream_t st, bool *any)
 {
-    std::vector<double> S((size_t)count * NSCAL);
+    std::vector<double> S((size_t)pl->cap * NSCAL);
     WMG_CUDA(cudaMemcpyAsync(S.data(), pl->S.p, S.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     WMG_CUDA(cudaStreamSynchronize(st));
     *any = false;
-    for (int q = 0; q < count; ++q)
+    for (int q = 0; q < pl->cap; ++q)
         if (S[(size_t)q * NSCAL + SC_ACTIVE] != 0.0) *any = true;
     return WMG_OK;
 }
 
-static int32_t collect(wmg_plan *pl, int count, int max_iter, wmg_solve_info *info, double *res_hist,
-                       cudaStream_t st)
+// Per-slot results; `order` (optional) maps the caller's problem i to its slot.
+static int32_t collect(wmg_plan *pl, int max_iter, wmg_solve_info *info, double *res_hist, cudaStream_t st)
 {
+    const int count = pl->cap;
     std::vector<double> S((size_t)count * NSCAL);
+    std::vector<double> H;
     WMG_CUDA(cudaMemcpyAsync(S.data(), pl->S.p, S.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-    if (res_hist)
-        WMG_CUDA(cudaMemcpyAsync(res_hist, pl->hist.p, (size_t)count * (max_iter + 1) * sizeof(double),
-                                 cudaMemcpyDeviceToHost, st));
+    if (res_hist) {
+        H.resize((size_t)count * (max_iter + 1));
+        WMG_CUDA(cudaMemcpyAsync(H.data(), pl->hist.p, H.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
     WMG_CUDA(cudaStreamSynchronize(st));
     WMG_CUDA(cudaGetLastError());
     int32_t rc = WMG_OK;
-    for (int q = 0; q < count; ++q) {
+    for (int i = 0; i < count; ++i) {
+        const int q = pl->batch ? pl->order[i] : i;
         const double *s = &S[(size_t)q * NSCAL];
         int status = (int)s[SC_STATUS];
         if (s[SC_ACTIVE] != 0.0) status = WMG_NOT_CONVERGED;
         if (info) {
-            info[q].iters = (int)s[SC_ITERS];
-            info[q].status = status;
-            info[q].rel_res = s[SC_RES];
+            info[i].iters = (int)s[SC_ITERS];
+            info[i].status = status;
+            info[i].rel_res = s[SC_RES];
         }
+        if (res_hist)
+            std::memcpy(res_hist + (size_t)i * (max_iter + 1), H.data() + (size_t)q * (max_iter + 1),
+                        (max_iter + 1) * sizeof(double));
         if (status < 0 && rc >= 0) rc = status;
         else if (status == WMG_NOT_CONVERGED && rc == WMG_OK) rc = WMG_NOT_CONVERGED;
     }
@@ -984,10 +1136,9 @@ static int32_t collect(wmg_plan *pl, int count, int max_iter, wmg_solve_info *in
 }
 
 template <class T>
-static int32_t solve_cgls(wmg_plan *pl, bool pre, int count, const void *b, void *xout, int max_iter,
-                          cudaStream_t st)
+static int32_t solve_cgls(wmg_plan *pl, bool pre, const void *b, void *xout, int max_iter, cudaStream_t st)
 {
-    const int64_t nN = (int64_t)count * pl->N, nM = (int64_t)count * pl->M;
+    const int64_t nN = pl->Ntot, nM = pl->Mtot;
     const size_t e = pl->esz;
     if (!ensure_pool(pl->x, nN, 8) || !ensure_pool(pl->s, nN, 8) || !ensure_pool(pl->z, nN, 8) ||
         !ensure_pool(pl->p, nN, 8) || !ensure_pool(pl->r, nM, 8) || !ensure_pool(pl->p_op, nN, e) ||
@@ -1061,7 +1212,7 @@ static int32_t solve_cgls(wmg_plan *pl, bool pre, int count, const void *b, void
         finalize(pl, FIN_PNORM, ps.bp, pc, 1, nullptr, nullptr, pre, hist, hld, st);
         if ((it + 1) % chunk == 0 || it + 1 == max_iter) {
             bool any = false;
-            int32_t rc = any_active(pl, count, st, &any);
+            int32_t rc = any_active(pl, st, &any);
             if (rc) return rc;
             if (!any) break;
         }
@@ -1074,9 +1225,10 @@ static int32_t solve_cgls(wmg_plan *pl, bool pre, int count, const void *b, void
 }
 
 template <class T>
-static int32_t solve_sirt(wmg_plan *pl, int count, const void *b, void *xout, int max_iter, cudaStream_t st)
+static int32_t solve_sirt(wmg_plan *pl, const void *b, void *xout, int max_iter, cudaStream_t st)
 {
-    const int64_t nN = (int64_t)count * pl->N, nM = (int64_t)count * pl->M;
+    const int count = pl->cap;
+    const int64_t nN = pl->Ntot, nM = pl->Mtot;
     const size_t e = pl->esz;
     if (!ensure_pool(pl->x, nN, 8) || !ensure_pool(pl->p_op, nN, e) || !ensure_pool(pl->pT_op, nN, e) ||
         !ensure_pool(pl->q, nM, e) || !ensure_pool(pl->r_op, nM, e) || !ensure_pool(pl->s, nN, 8) ||
@@ -1126,10 +1278,11 @@ static int32_t solve_sirt(wmg_plan *pl, int count, const void *b, void *xout, in
 }
 
 template <class T>
-static int32_t solve_gmres(wmg_plan *pl, bool pre, int count, const void *b, void *xout, int max_iter,
-                           int restart, cudaStream_t st)
+static int32_t solve_gmres(wmg_plan *pl, bool pre, const void *b, void *xout, int max_iter, int restart,
+                           cudaStream_t st)
 {
-    const int64_t nN = (int64_t)count * pl->N, nM = (int64_t)count * pl->M;
+    const int count = pl->cap;
+    const int64_t nN = pl->Ntot, nM = pl->Mtot;
     const size_t e = pl->esz;
     const int ldp = restart + 1;
     if (!ensure_pool(pl->x, nN, 8) || !ensure_pool(pl->f, nN, 8) || !ensure_pool(pl->w, nN, 8) ||
@@ -1247,7 +1400,7 @@ static int32_t solve_gmres(wmg_plan *pl, bool pre, int count, const void *b, voi
         launch_gm_scalar(2, ga, st);
         launch_gm_setv(ps.d.as<ProbDev>(), ps.vimg.tiles.as<int4>(), ps.vimg.n, V, vstride, ldp, 0, V, S, st);
         bool any = false;
-        int32_t rc = any_active(pl, count, st, &any);
+        int32_t rc = any_active(pl, st, &any);
         if (rc) return rc;
         if (!any || done_iters >= max_iter) break;
     }
@@ -1259,34 +1412,184 @@ static int32_t solve_gmres(wmg_plan *pl, bool pre, int count, const void *b, voi
 }
 
 template <class T>
-static int32_t do_solve(wmg_plan *pl, int solver, bool pre, int count, const void *b, void *x, int max_iter,
-                        int restart, cudaStream_t st)
+static int32_t do_solve(wmg_plan *pl, int solver, bool pre, const void *b, void *x, int max_iter, int restart,
+                        cudaStream_t st)
 {
-    if (solver == WMG_SOLVER_CGLS) return solve_cgls<T>(pl, pre, count, b, x, max_iter, st);
-    if (solver == WMG_SOLVER_GMRES) return solve_gmres<T>(pl, pre, count, b, x, max_iter, restart, st);
-    return solve_sirt<T>(pl, count, b, x, max_iter, st);
+    if (solver == WMG_SOLVER_CGLS) return solve_cgls<T>(pl, pre, b, x, max_iter, st);
+    if (solver == WMG_SOLVER_GMRES) return solve_gmres<T>(pl, pre, b, x, max_iter, restart, st);
+    return solve_sirt<T>(pl, b, x, max_iter, st);
+}
+
+static int32_t check_solve_args(wmg_plan *pl, int32_t solver, int32_t preconditioned, int32_t max_iter,
+                                int32_t restart)
+{
+    if (max_iter < 0 || solver < WMG_SOLVER_SIRT || solver > WMG_SOLVER_GMRES)
+        return fail(WMG_ERR_INVALID_ARG, "wmg_solve: bad arguments");
+    if (solver == WMG_SOLVER_GMRES && (restart < 1 || restart > 64))
+        return fail(WMG_ERR_INVALID_ARG, "wmg_solve: restart must be in [1, 64]");
+    if (preconditioned && !pl->has_wmg() && solver != WMG_SOLVER_SIRT)
+        return fail(WMG_ERR_INVALID_ARG, "wmg_solve: the plan has no WMG levels to precondition with");
+    if (solver == WMG_SOLVER_CGLS && preconditioned && pl->opts.cycle == WMG_CYCLE_HYBRID)
+        return fail(WMG_ERR_INVALID_ARG, "CGLS needs a symmetric preconditioner (ADDITIVE or SYMMETRIC cycle)");
+    return WMG_OK;
+}
+
+static int32_t run_solve(wmg_plan *pl, int32_t solver, int32_t preconditioned, const void *b, void *x,
+                         int32_t max_iter, double rtol, int32_t restart, wmg_solve_info *info, double *res_hist,
+                         cudaStream_t st)
+{
+    if (!pl->hist.ensure((size_t)pl->cap * (max_iter + 1) * sizeof(double)))
+        return fail(WMG_ERR_OOM, "history");
+    cudaMemsetAsync(pl->hist.p, 0, (size_t)pl->cap * (max_iter + 1) * sizeof(double), st);
+    init_scalars(pl, rtol, max_iter, st);
+    int32_t rc = WMG_DISPATCH(pl, do_solve, pl, solver, preconditioned != 0, b, x, max_iter, restart, st);
+    if (rc) return rc;
+    return collect(pl, max_iter, info, res_hist, st);
 }
 
 extern "C" int32_t wmg_solve(wmg_plan *pl, int32_t solver, int32_t preconditioned, int32_t count,
                              const void *b, void *x, int32_t max_iter, double rtol, int32_t restart,
                              wmg_solve_info *info, double *res_hist, void *stream)
 {
-    if (!pl || !b || !x || count < 1 || max_iter < 0 || solver < WMG_SOLVER_SIRT || solver > WMG_SOLVER_GMRES)
-        return fail(WMG_ERR_INVALID_ARG, "wmg_solve: bad arguments");
-    if (solver == WMG_SOLVER_GMRES && (restart < 1 || restart > 64))
-        return fail(WMG_ERR_INVALID_ARG, "wmg_solve: restart must be in [1, 64]");
-    if (preconditioned && !pl->has_wmg && solver != WMG_SOLVER_SIRT)
-        return fail(WMG_ERR_INVALID_ARG, "wmg_solve: the plan has no WMG levels to precondition with");
-    if (solver == WMG_SOLVER_CGLS && preconditioned && pl->opts.cycle == WMG_CYCLE_HYBRID)
-        return fail(WMG_ERR_INVALID_ARG, "CGLS needs a symmetric preconditioner (ADDITIVE or SYMMETRIC cycle)");
+    if (!pl || !b || !x || count < 1) return fail(WMG_ERR_INVALID_ARG, "wmg_solve: bad arguments");
+    int32_t rc = single_geometry(pl, "wmg_solve");
+    if (rc) return rc;
+    if ((rc = check_solve_args(pl, solver, preconditioned, max_iter, restart))) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int32_t rc = ensure_count(pl, count, st);
+    if ((rc = ensure_count(pl, count, st))) return rc;
+    return run_solve(pl, solver, preconditioned, b, x, max_iter, rtol, restart, info, res_hist, st);
+}
+
+// ---------------------------------------------------------------------------
+// Batches of problems with different geometries
+// ---------------------------------------------------------------------------
+struct wmg_batch {
+    wmg_plan *plan = nullptr;
+};
+
+static bool same_geometry(const wmg_geom &a, const wmg_geom &b, const wmg_opts &oa, const wmg_opts &ob)
+{
+    if (a.n != b.n || a.m != b.m || a.D != b.D || a.det_spacing != b.det_spacing || a.det_offset != b.det_offset ||
+        oa.levels != ob.levels || oa.lambda != ob.lambda)
+        return false;
+    if ((a.angles == nullptr) != (b.angles == nullptr)) return false;
+    if (a.angles && std::memcmp(a.angles, b.angles, a.m * sizeof(double)) != 0) return false;
+    return true;
+}
+
+extern "C" int32_t wmg_batch_create(const wmg_geom *gs, const wmg_opts *os, int32_t count, void *stream,
+                                    wmg_batch **out)
+{
+    if (!out) return fail(WMG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!gs || !os || count < 1) return fail(WMG_ERR_INVALID_ARG, "wmg_batch_create: bad arguments");
+    for (int i = 0; i < count; ++i) {
+        int32_t rc = validate(&gs[i], &os[i]);
+        if (rc) return rc;
+        const wmg_opts &a = os[0], &b = os[i];
+        if (a.nu1 != b.nu1 || a.nu2 != b.nu2 || a.cycle != b.cycle || a.hybrid_depth != b.hybrid_depth ||
+            a.precision != b.precision || a.omega != b.omega || (a.levels >= 1) != (b.levels >= 1))
+            return fail(WMG_ERR_INVALID_ARG,
+                        "wmg_batch_create: problems must share nu1, nu2, omega, cycle, hybrid depth and precision");
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    auto pl = std::make_unique<wmg_plan>();
+    pl->prec = os[0].precision;
+    pl->esz = pl->prec == WMG_PREC_F64 ? 8 : 4;
+    pl->opts = os[0];
+    if (pl->opts.omega <= 0) pl->opts.omega = 1.0;
+    pl->batch = true;
+    // distinct geometries (first occurrence order), each set up once
+    std::vector<int> gid(count, -1), first;
+    for (int i = 0; i < count; ++i) {
+        for (size_t u = 0; u < first.size(); ++u)
+            if (same_geometry(gs[i], gs[first[u]], os[i], os[first[u]])) { gid[i] = (int)u; break; }
+        if (gid[i] < 0) { gid[i] = (int)first.size(); first.push_back(i); }
+    }
+    int32_t rc;
+    for (size_t u = 0; u < first.size(); ++u) {
+        pl->geos.push_back(std::make_unique<Geo>());
+        if ((rc = make_geo(&gs[first[u]], &os[first[u]], *pl->geos.back(), st))) return rc;
+    }
+    if ((rc = upload_geoms(pl.get(), st))) return rc;
+    for (size_t u = 0; u < first.size(); ++u) {
+        rc = pl->prec == WMG_PREC_F64 ? setup_geometry<double>(pl.get(), (int)u, st)
+                                      : setup_geometry<float>(pl.get(), (int)u, st);
+        if (rc) return rc;
+    }
+    // slots grouped by geometry; order[i] = slot of problem i
+    std::vector<int> idx(count);
+    for (int i = 0; i < count; ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return gid[a] < gid[b]; });
+    pl->order.assign(count, 0);
+    pl->pgeo.assign(count, 0);
+    for (int q = 0; q < count; ++q) {
+        pl->order[idx[q]] = q;
+        pl->pgeo[q] = gid[idx[q]];
+    }
+    if ((rc = set_slots(pl.get(), st))) return rc;
+    WMG_CUDA(cudaStreamSynchronize(st));
+    auto bt = std::make_unique<wmg_batch>();
+    bt->plan = pl.release();
+    *out = bt.release();
+    return WMG_OK;
+}
+
+extern "C" int32_t wmg_batch_destroy(wmg_batch *batch)
+{
+    if (!batch) return WMG_OK;
+    wmg_plan_destroy(batch->plan);
+    delete batch;
+    return WMG_OK;
+}
+
+extern "C" int32_t wmg_batch_sizes(const wmg_batch *batch, int32_t i, int64_t *N, int64_t *M)
+{
+    if (!batch || i < 0 || i >= batch->plan->cap) return fail(WMG_ERR_INVALID_ARG, "wmg_batch_sizes: bad arguments");
+    const Geo &G = batch->plan->geo(batch->plan->order[i]);
+    if (N) *N = G.N;
+    if (M) *M = G.M;
+    return WMG_OK;
+}
+
+// copy kernels between the caller's per-problem buffers and the slot pools
+template <class T>
+static int32_t gather_scatter(wmg_plan *pl, const void *const *src, void *const *dst, bool to_pool, void *pool,
+                              bool image, cudaStream_t st)
+{
+    for (int i = 0; i < pl->cap; ++i) {
+        const int q = pl->order[i];
+        const Geo &G = pl->geo(q);
+        const int64_t off = image ? pl->img_off[q] : pl->sino_off[q];
+        const size_t bytes = (size_t)(image ? G.N : G.M) * sizeof(T);
+        char *pp = static_cast<char *>(pool) + off * sizeof(T);
+        if (to_pool) WMG_CUDA(cudaMemcpyAsync(pp, src[i], bytes, cudaMemcpyDeviceToDevice, st));
+        else WMG_CUDA(cudaMemcpyAsync(dst[i], pp, bytes, cudaMemcpyDeviceToDevice, st));
+    }
+    return WMG_OK;
+}
+
+extern "C" int32_t wmg_batch_solve(wmg_batch *batch, int32_t solver, int32_t preconditioned, const void *const *b,
+                                   void *const *x, int32_t max_iter, double rtol, int32_t restart,
+                                   wmg_solve_info *info, double *res_hist, void *stream)
+{
+    if (!batch || !b || !x) return fail(WMG_ERR_INVALID_ARG, "wmg_batch_solve: bad arguments");
+    wmg_plan *pl = batch->plan;
+    for (int i = 0; i < pl->cap; ++i)
+        if (!b[i] || !x[i]) return fail(WMG_ERR_INVALID_ARG, "wmg_batch_solve: NULL problem buffer");
+    int32_t rc = check_solve_args(pl, solver, preconditioned, max_iter, restart);
     if (rc) return rc;
-    if (!pl->hist.ensure((size_t)count * (max_iter + 1) * sizeof(double)))
-        return fail(WMG_ERR_OOM, "history");
-    cudaMemsetAsync(pl->hist.p, 0, (size_t)count * (max_iter + 1) * sizeof(double), st);
-    init_scalars(pl, count, rtol, max_iter, st);
-    rc = WMG_DISPATCH(pl, do_solve, pl, solver, preconditioned != 0, count, b, x, max_iter, restart, st);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!ensure_pool(pl->b_op, pl->Mtot, pl->esz) || !ensure_pool(pl->x_io, pl->Ntot, pl->esz))
+        return fail(WMG_ERR_OOM, "batch input pools");
+    rc = pl->prec == WMG_PREC_F64 ? gather_scatter<double>(pl, b, nullptr, true, pl->b_op.p, false, st)
+                                  : gather_scatter<float>(pl, b, nullptr, true, pl->b_op.p, false, st);
     if (rc) return rc;
-    return collect(pl, count, max_iter, info, res_hist, st);
+    rc = run_solve(pl, solver, preconditioned, pl->b_op.p, pl->x_io.p, max_iter, rtol, restart, info, res_hist, st);
+    if (rc < 0) return rc;
+    const int32_t rc2 = pl->prec == WMG_PREC_F64 ? gather_scatter<double>(pl, nullptr, x, false, pl->x_io.p, true, st)
+                                                 : gather_scatter<float>(pl, nullptr, x, false, pl->x_io.p, true, st);
+    if (rc2) return rc2;
+    WMG_CUDA(cudaStreamSynchronize(st));
+    return rc;
 }

@@ -1,0 +1,67 @@
+"""Batches of problems with different geometries (image side, angle count,
+bins, WMG levels) solved together, one launch per operator application: each
+problem must give bitwise the same reconstruction as when solved alone with
+its own plan, and the same as the FP64 oracle within the solver tolerances."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+
+torch = pytest.importorskip("torch")
+import paper_1310_0956_gb300 as wmg  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+PROBLEMS = [  # n, m, D, levels
+    dict(n=32, m=24, D=46, levels=3), dict(n=48, m=30, D=68, levels=3), dict(n=32, m=24, D=46, levels=3),
+    dict(n=64, m=36, D=91, levels=3), dict(n=24, m=20, D=34, levels=2),
+]
+
+
+def sinograms(problems):
+    out = []
+    for i, p in enumerate(problems):
+        op = oracle.Op(p["n"], p["m"], p["D"])
+        x = S.phantom(p["n"], 5, S.seed_for(3, 100 + i))
+        b = op.project(x)
+        b = b + 0.01 * np.abs(b).max() * S.noise_draws(op.M, S.seed_for(3, 100 + i))
+        out.append((op, b))
+    return out
+
+
+@pytest.mark.parametrize("prec,cycle,hd,solver", [
+    (wmg.PREC_F64, wmg.CYCLE_HYBRID, 1, wmg.SOLVER_GMRES),
+    (wmg.PREC_F32, wmg.CYCLE_HYBRID, 2, wmg.SOLVER_GMRES),
+    (wmg.PREC_F64, wmg.CYCLE_ADDITIVE, 0, wmg.SOLVER_CGLS),
+    (wmg.PREC_F32, wmg.CYCLE_SYMMETRIC, 1, wmg.SOLVER_CGLS),
+])
+def test_batch_equals_alone(prec, cycle, hd, solver):
+    dt = torch.float64 if prec == wmg.PREC_F64 else torch.float32
+    data = sinograms(PROBLEMS)
+    batch = wmg.Batch(PROBLEMS, nu1=1, nu2=1, hybrid_depth=hd, cycle=cycle, precision=prec)
+    bs = [torch.tensor(b, dtype=dt, device="cuda") for _, b in data]
+    xs, infos, rc = batch.solve(bs, solver, True, max_iter=40, rtol=1e-6)
+    torch.cuda.synchronize()
+    for i, p in enumerate(PROBLEMS):
+        plan = wmg.Plan(p["n"], p["m"], p["D"], levels=p["levels"], nu1=1, nu2=1, hybrid_depth=hd,
+                        cycle=cycle, precision=prec)
+        x1, info1, _, _ = plan.solve(bs[i], solver, True, max_iter=40, rtol=1e-6)
+        torch.cuda.synchronize()
+        assert info1[0][0] == infos[i][0]
+        assert torch.equal(x1, xs[i]), i
+        plan.close()
+
+
+def test_batch_matches_oracle_f64():
+    data = sinograms(PROBLEMS[:2])
+    batch = wmg.Batch(PROBLEMS[:2], nu1=1, nu2=1, hybrid_depth=1, cycle=wmg.CYCLE_HYBRID, precision=wmg.PREC_F64)
+    xs, infos, _ = batch.solve([torch.tensor(b, dtype=torch.float64, device="cuda") for _, b in data],
+                               wmg.SOLVER_GMRES, True, max_iter=12, rtol=0.0)
+    for i, p in enumerate(PROBLEMS[:2]):
+        op, b = data[i]
+        M = oracle.Wmg(op, p["levels"], 1, 1, 1.0, 0.0, oracle.CYCLE_HYBRID, 1)
+        x_ref, k, _ = oracle.gmres(op, b, 12, 20, 0.0, 0.0, M)
+        x = xs[i].cpu().numpy()
+        assert infos[i][0] == k == 12
+        assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) < 1e-10

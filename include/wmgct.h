@@ -200,6 +200,102 @@ int32_t wmg_batch_solve(wmg_batch *batch, int32_t solver, int32_t preconditioned
                         void *const *x, int32_t max_iter, double rtol, int32_t restart,
                         wmg_solve_info *info, double *res_hist, void *stream);
 
+/* ---- continuous-batching server -------------------------------------------
+ * A request loop for reconstructions that arrive over time. Each request is
+ * an independent problem of its own geometry (image side, angle set,
+ * detector grid) solved by restarted GMRES(restart) on the normal equations
+ * (Section 2.3) with right preconditioning by one WMG cycle (Section 3.1), as
+ * wmg_solve with WMG_SOLVER_GMRES does.
+ *
+ * Requests wait in a FIFO queue; the head is admitted when a slot is free and
+ * its footprint fits the free memory. An admitted request keeps all of its
+ * solver state (x, W^T b, the Arnoldi basis, Hessenberg and Givens data,
+ * residual history) resident in the server's device pools until it ends.
+ * Every wmg_server_step admits what fits, then runs one GMRES step for all
+ * admitted requests together, each at its own position in its own cycle: one
+ * preconditioner application and one A-pair launched over all of them, then
+ * the per-request Gram-Schmidt / restart steps. Requests that converged (or
+ * hit max_iter, or broke down) retire at the end of the step: x is written
+ * to the caller's buffer and their memory and slot go to waiting requests.
+ * A request's arithmetic does not depend on the other requests: its x is
+ * bitwise the same alone, in any mix, and as from wmg_solve on that problem.
+ *
+ * Memory. hbm_budget bytes in total: state_bytes (0: half) are taken at
+ * creation as the state pools, sized for sino_ratio (0: 4) sinogram elements
+ * per image element; the rest holds geometry setups (trig tables, D~^-1,
+ * SIRT scalings, leaf inverses K * P^2 doubles), cached by geometry and
+ * evicted least-recently-used when no admitted request uses them. Footprint
+ * of a request: (restart + 11) * 8 + 2 s bytes per pixel and 2 s bytes per ray
+ * (s = 8 for F64, 4 for F32), more with hybrid depth h >= 1 (band images,
+ * 3^(h-1) (2 s + 8) per pixel and 3^(h-1) s per ray) and the symmetric cycle
+ * (24 h per pixel), plus its geometry's setup when not cached. The transient
+ * scratch of a geometry setup (at most about 256 MiB) is not counted.
+ *
+ * Streams: all work is on the stream given at creation; wmg_server_step
+ * synchronises it. Not thread-safe. */
+#define WMG_REQ_QUEUED   0
+#define WMG_REQ_RUNNING  1
+#define WMG_REQ_DONE     2
+
+typedef struct wmg_server_config {
+    int64_t hbm_budget;      /* bytes: state pools + geometry setups */
+    int64_t state_bytes;     /* bytes of hbm_budget for the state pools (0: half) */
+    double sino_ratio;       /* sinogram elements per image element in the pools (0: 4) */
+    int32_t max_slots;       /* requests in flight at most */
+    int32_t preconditioned;  /* 1: WMG-GMRES (levels >= 1 per request), 0: GMRES */
+    int32_t max_iter;        /* iteration cap per request */
+    double rtol;             /* stop when |W^T b - (W^T W + lambda) x| / |W^T b| < rtol */
+    int32_t restart;         /* GMRES restart length, 1..64 */
+    wmg_opts opts;           /* precision, cycle, nu1, nu2, omega and hybrid_depth shared by
+                                every request; levels and lambda are the defaults of
+                                requests submitted with opts = NULL */
+} wmg_server_config;
+
+typedef struct wmg_server_counters {
+    int64_t submitted, admitted, completed, rejected, ticks;
+    int64_t geometry_setups, geometries_evicted;
+    int32_t running, queued, geometries_cached;
+    int64_t state_bytes_capacity, state_bytes_used;
+    int64_t geometry_bytes_capacity, geometry_bytes_used;
+} wmg_server_counters;
+
+typedef struct wmg_server wmg_server;
+
+/* Create a server: takes the state pools (device) and pinned host staging.
+ * WMG_ERR_INVALID_ARG for an invalid configuration or a state budget below
+ * one 64-pixel image, WMG_ERR_OOM when the pools do not fit. Synchronising. */
+int32_t wmg_server_create(const wmg_server_config *cfg, void *stream, wmg_server **out);
+/* Destroy a server (waits for its stream); outstanding requests are dropped. */
+int32_t wmg_server_destroy(wmg_server *srv);
+
+/* Queue a request: geometry g (angles, if given, are copied), options o
+ * (NULL: the server's; precision, cycle, nu1, nu2, omega and hybrid_depth
+ * must equal the server's), sinogram b (device, m*D elements of the server
+ * precision's type) and the output image x (device, n*n elements). b and x
+ * must stay valid and unchanged (x unread) until wmg_server_poll reports
+ * WMG_REQ_DONE. Does not block and launches nothing. Returns
+ * WMG_ERR_REJECTED (no ticket) when the footprint can never fit the budget,
+ * WMG_ERR_INVALID_ARG for an invalid geometry or options. */
+int32_t wmg_server_submit(wmg_server *srv, const wmg_geom *g, const wmg_opts *o, const void *b, void *x,
+                          uint64_t *ticket);
+
+/* One tick: admit, run one GMRES step for every admitted request, retire the
+ * finished ones. *pending (may be NULL) = requests running + queued after
+ * the tick. A geometry seen for the first time is set up inside the tick
+ * that admits its first request. Synchronising. */
+int32_t wmg_server_step(wmg_server *srv, int32_t *pending);
+
+/* State of a request (WMG_REQ_QUEUED / RUNNING / DONE). When DONE: *info
+ * (iterations, status, final relative residual), *latency_ms (host time from
+ * submit to retirement) and res_hist (max_iter + 1 doubles, as wmg_solve's)
+ * are filled where not NULL, x holds the result, and the ticket is released
+ * (polling it again is WMG_ERR_INVALID_ARG). Host-only, never blocks. */
+int32_t wmg_server_poll(wmg_server *srv, uint64_t ticket, int32_t *state, wmg_solve_info *info,
+                        double *latency_ms, double *res_hist);
+
+/* Counters and memory use. Host-only. */
+int32_t wmg_server_stats(const wmg_server *srv, wmg_server_counters *out);
+
 /* Number of nonzero intersection lengths of the plan's W (rays x pixels with
  * a nonzero weight), counted on the device at plan creation. */
 int32_t wmg_plan_nnz(const wmg_plan *plan, int64_t *nnz);

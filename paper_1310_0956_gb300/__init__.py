@@ -29,6 +29,7 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "INVALID_ARG", -2: "OOM", -3: "
 PREC_F64, PREC_F32 = 0, 1
 CYCLE_ADDITIVE, CYCLE_HYBRID, CYCLE_SYMMETRIC = 0, 1, 2
 SOLVER_SIRT, SOLVER_CGLS, SOLVER_GMRES = 0, 1, 2
+REQ_QUEUED, REQ_RUNNING, REQ_DONE = 0, 1, 2
 
 
 class WmgError(RuntimeError):
@@ -59,6 +60,21 @@ class wmg_profile_stats(C.Structure):
                 ("nnz_per_image", C.c_double)]
 
 
+class wmg_server_config(C.Structure):
+    _fields_ = [("hbm_budget", C.c_int64), ("state_bytes", C.c_int64), ("sino_ratio", C.c_double),
+                ("max_slots", C.c_int32), ("preconditioned", C.c_int32), ("max_iter", C.c_int32),
+                ("rtol", C.c_double), ("restart", C.c_int32), ("opts", wmg_opts)]
+
+
+class wmg_server_counters(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("rejected", C.c_int64), ("ticks", C.c_int64), ("geometry_setups", C.c_int64),
+                ("geometries_evicted", C.c_int64), ("running", C.c_int32), ("queued", C.c_int32),
+                ("geometries_cached", C.c_int32), ("state_bytes_capacity", C.c_int64),
+                ("state_bytes_used", C.c_int64), ("geometry_bytes_capacity", C.c_int64),
+                ("geometry_bytes_used", C.c_int64)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -87,6 +103,14 @@ _SIGNATURES = {
     "wmg_batch_sizes": (_i32, [_vp, _i32, C.POINTER(_i64), C.POINTER(_i64)]),
     "wmg_batch_solve": (_i32, [_vp, _i32, _i32, C.POINTER(_vp), C.POINTER(_vp), _i32, _dbl, _i32,
                                C.POINTER(wmg_solve_info), C.POINTER(_dbl), _vp]),
+    "wmg_server_create": (_i32, [C.POINTER(wmg_server_config), _vp, C.POINTER(_vp)]),
+    "wmg_server_destroy": (_i32, [_vp]),
+    "wmg_server_submit": (_i32, [_vp, C.POINTER(wmg_geom), C.POINTER(wmg_opts), _vp, _vp,
+                                 C.POINTER(C.c_uint64)]),
+    "wmg_server_step": (_i32, [_vp, C.POINTER(_i32)]),
+    "wmg_server_poll": (_i32, [_vp, C.c_uint64, C.POINTER(_i32), C.POINTER(wmg_solve_info), C.POINTER(_dbl),
+                               C.POINTER(_dbl)]),
+    "wmg_server_stats": (_i32, [_vp, C.POINTER(wmg_server_counters)]),
 }
 
 
@@ -224,6 +248,43 @@ def wmg_profile_begin(plan):
 def wmg_profile_end(plan, stream=None) -> wmg_profile_stats:
     out = wmg_profile_stats()
     _check(lib().wmg_profile_end(plan, C.byref(out), stream))
+    return out
+
+
+def wmg_server_create(cfg: wmg_server_config, stream=None) -> C.c_void_p:
+    out = _vp()
+    _check(lib().wmg_server_create(C.byref(cfg), stream, C.byref(out)))
+    return out
+
+
+def wmg_server_destroy(srv):
+    _check(lib().wmg_server_destroy(srv))
+
+
+def wmg_server_submit(srv, geom: wmg_geom, opts, b, x) -> int:
+    """Returns the ticket; raises WmgError (code -8) when rejected."""
+    t = C.c_uint64()
+    _check(lib().wmg_server_submit(srv, C.byref(geom), C.byref(opts) if opts is not None else None, b, x,
+                                   C.byref(t)))
+    return t.value
+
+
+def wmg_server_step(srv) -> int:
+    pending = _i32()
+    _check(lib().wmg_server_step(srv, C.byref(pending)))
+    return pending.value
+
+
+def wmg_server_poll(srv, ticket, res_hist=None):
+    """Returns (state, info, latency_ms)."""
+    state, info, lat = _i32(), wmg_solve_info(), _dbl()
+    _check(lib().wmg_server_poll(srv, ticket, C.byref(state), C.byref(info), C.byref(lat), res_hist))
+    return state.value, info, lat.value
+
+
+def wmg_server_stats(srv) -> wmg_server_counters:
+    out = wmg_server_counters()
+    _check(lib().wmg_server_stats(srv, C.byref(out)))
     return out
 
 
@@ -398,3 +459,79 @@ class Batch:
                              [t.data_ptr() for t in outs], max_iter, rtol, restart, info, None,
                              C.c_void_p(torch.cuda.current_stream().cuda_stream))
         return outs, [(info[i].iters, info[i].status, info[i].rel_res) for i in range(self.count)], rc
+
+
+class Server:
+    """Continuous-batching request server (torch CUDA tensors). Requests are
+    dicts with keys n, m, D and optionally levels, lam, angles, det_spacing,
+    det_offset; submit() takes the request's sinogram b and returns a ticket;
+    the output image is allocated here and returned by poll() when done."""
+
+    def __init__(self, hbm_budget, max_slots=64, state_bytes=0, sino_ratio=0.0, preconditioned=True,
+                 max_iter=200, rtol=1e-4, restart=20, levels=1, nu1=1, nu2=1, omega=1.0, lam=0.0,
+                 hybrid_depth=1, cycle=CYCLE_HYBRID, precision=PREC_F32):
+        import torch
+        self._torch = torch
+        self.dtype = torch.float64 if precision == PREC_F64 else torch.float32
+        self.max_iter = max_iter
+        self.defaults = dict(levels=levels, nu1=nu1, nu2=nu2, omega=omega, lam=lam, hybrid_depth=hybrid_depth,
+                             cycle=cycle, precision=precision)
+        cfg = wmg_server_config(int(hbm_budget), int(state_bytes), float(sino_ratio), max_slots,
+                                1 if preconditioned else 0, max_iter, rtol, restart,
+                                wmg_opts(levels, nu1, nu2, omega, lam, hybrid_depth, cycle, precision))
+        self._live = {}
+        self.handle = wmg_server_create(cfg, C.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            wmg_server_destroy(self.handle)
+            self.handle = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, req, b):
+        torch = self._torch
+        n, m, D = req["n"], req["m"], req["D"]
+        if b.dtype != self.dtype or b.numel() != m * D or not b.is_cuda or not b.is_contiguous():
+            raise TypeError("sinogram must be a contiguous CUDA tensor of the server's dtype and size m*D")
+        keep = []
+        ap = None
+        if req.get("angles") is not None:
+            arr = (C.c_double * m)(*[float(a) for a in req["angles"]])
+            keep.append(arr)
+            ap = C.cast(arr, C.c_void_p)
+        geom = wmg_geom(n, m, ap, D, req.get("det_spacing", 1.0), req.get("det_offset", 0.0))
+        d = self.defaults
+        opts = wmg_opts(req.get("levels", d["levels"]), d["nu1"], d["nu2"], d["omega"], req.get("lam", d["lam"]),
+                        d["hybrid_depth"], d["cycle"], d["precision"])
+        x = torch.empty(n * n, dtype=self.dtype, device=b.device)
+        t = wmg_server_submit(self.handle, geom, opts, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()))
+        self._live[t] = (b, x)
+        return t
+
+    def step(self) -> int:
+        """One tick; returns the number of requests running or queued."""
+        return wmg_server_step(self.handle)
+
+    def poll(self, ticket, history=False):
+        """None while the request runs; else (x, (iters, status, rel_res),
+        latency_ms[, residual history])."""
+        hist = (C.c_double * (self.max_iter + 1))() if history else None
+        state, info, lat = wmg_server_poll(self.handle, ticket, hist)
+        if state != REQ_DONE:
+            return None
+        _, x = self._live.pop(ticket)
+        res = (x, (info.iters, info.status, info.rel_res), lat)
+        if history:
+            import numpy as np
+            res = res + (np.frombuffer(hist, dtype=np.float64)[:info.iters + 1].copy(),)
+        return res
+
+    def stats(self) -> dict:
+        st = wmg_server_stats(self.handle)
+        return {name: getattr(st, name) for name, _ in wmg_server_counters._fields_}

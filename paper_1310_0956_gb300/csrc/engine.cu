@@ -11,8 +11,7 @@
 #include <string>
 #include <vector>
 
-#include "kern_common.cuh"
-#include "krylov.cuh"
+#include "engine.cuh"
 
 namespace wmg {
 
@@ -40,39 +39,6 @@ int num_sms()
     }();
     return v;
 }
-
-// ---------------------------------------------------------------------------
-// device buffers
-// ---------------------------------------------------------------------------
-struct DevBuf {
-    void *p = nullptr;
-    size_t bytes = 0;
-    DevBuf() = default;
-    DevBuf(const DevBuf &) = delete;
-    DevBuf &operator=(const DevBuf &) = delete;
-    ~DevBuf() { release(); }
-    void release()
-    {
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-    }
-    // grow-only; contents are not preserved
-    bool ensure(size_t b)
-    {
-        if (b <= bytes && p) return true;
-        release();
-        if (b == 0) b = 16;
-        if (cudaMalloc(&p, b) != cudaSuccess) {
-            cudaGetLastError();
-            p = nullptr;
-            return false;
-        }
-        bytes = b;
-        return true;
-    }
-    template <class U> U *as() const { return static_cast<U *>(p); }
-};
 
 // Equiangular angle table: theta_a = pi*a/m reduced to the first octant so
 // that multiples of pi/2 are exactly 0 / +-1, odd multiples of pi/4 give
@@ -102,101 +68,6 @@ static void angle_table(int m, const double *angles, std::vector<double2> &cs)
     }
 }
 
-struct TileList {
-    DevBuf tiles, tb, te;
-    int n = 0;
-    std::vector<int4> h;
-    bool upload(int nprob, cudaStream_t st)
-    {
-        n = (int)h.size();
-        std::vector<int> b(nprob, 0), e(nprob, 0);
-        for (int i = 0; i < n; ++i) {
-            const int p = h[i].x;
-            if (i == 0 || h[i - 1].x != p) b[p] = i;
-            e[p] = i + 1;
-        }
-        if (!tiles.ensure(std::max<size_t>(1, h.size()) * sizeof(int4)) ||
-            !tb.ensure(nprob * sizeof(int)) || !te.ensure(nprob * sizeof(int)))
-            return false;
-        if (n) cudaMemcpyAsync(tiles.p, h.data(), h.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(tb.p, b.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(te.p, e.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, st);
-        // host vectors must outlive the async copies: keep them (b, e are
-        // copied synchronously with respect to pageable memory)
-        return true;
-    }
-};
-
-// A set of (real or virtual) problems with their tiles (problems may have
-// different geometries; each tile belongs to one problem).
-struct ProbSet {
-    int nprob = 0;
-    std::vector<ProbDev> h;
-    DevBuf d;
-    TileList proj, bp, haar, vimg, vsino;
-    int haar_smem = 0;
-};
-
-// One geometry of a plan with its device tables.
-struct Geo {
-    GeomDev g{};
-    int64_t N = 0, M = 0, nnz = 0;
-    bool has_wmg = true, unit_bins = true;
-    int hd = 0;                 // hybrid depth in use: min(hybrid_depth, L), 0 for additive
-    int haar_W = 1;             // Haar strip width (pixels)
-    DevBuf cs64, cs32, csx, angf, dinv, leafinv, sirtR, sirtC;
-};
-
-}  // namespace wmg
-
-// ---------------------------------------------------------------------------
-// The plan: one or more geometries and a table of problem slots. A plan made
-// by wmg_plan_create has one geometry and any number of same-geometry
-// problems per call; a batch (wmg_batch_create) has a fixed list of problems
-// of several geometries, stored grouped by geometry.
-// ---------------------------------------------------------------------------
-struct wmg_plan {
-    int prec = WMG_PREC_F64;
-    size_t esz = 8;
-    wmg_opts opts{};
-    std::vector<std::unique_ptr<wmg::Geo>> geos;
-    wmg::DevBuf d_geom;         // GeomDev array, one per geometry
-    bool unit_bins = true;      // every geometry has unit bins, zero offset
-    bool batch = false;         // fixed problem list
-    int cap = 0;                // problem slots
-    std::vector<int> pgeo;      // geometry of each slot
-    std::vector<int64_t> img_off, sino_off;
-    int64_t Ntot = 0, Mtot = 0;
-    std::vector<int> order;     // batch: slot of the caller's problem i
-    wmg::ProbSet real;
-    std::map<std::vector<int>, std::unique_ptr<wmg::ProbSet>> bands;   // band-update groups
-    std::map<std::vector<int>, std::unique_ptr<wmg::TileList>> leafsets;
-    std::map<std::vector<int>, std::unique_ptr<wmg::DevBuf>> segsets;
-    // FP64 pools (all slots back to back)
-    wmg::DevBuf x, s, z, p, f, w, t, u, r;
-    // operator-precision pools
-    wmg::DevBuf p_op, pT_op, z_op, zT_op, r1, C, E, q, r_op, sinoS, b_op, x_io;
-    std::vector<std::unique_ptr<wmg::DevBuf>> csave, c2, e2;   // per hybrid depth
-    wmg::DevBuf band_img, band_imgT, band_img2, band_sino;
-    // scalars and partials
-    wmg::DevBuf S, part_a, part_b, part_c, lam, hist;
-    // GMRES
-    wmg::DevBuf V, H, gcs, gsn, gg, gy, h1, h2, jn, done;
-    // profiling: (kind 0 = project / 1 = backproject, images, start, stop)
-    bool profiling = false;
-    struct ProfRec { int kind; int images; cudaEvent_t e0, e1; };
-    std::vector<ProfRec> prof;
-    const wmg::Geo &geo(int slot) const { return *geos[pgeo[slot]]; }
-    bool has_wmg() const
-    {
-        for (auto &g : geos)
-            if (!g->has_wmg) return false;
-        return true;
-    }
-};
-
-namespace wmg {
-
 // ---- tile lists ------------------------------------------------------------
 // Haar strip width of a geometry: a whole number of 2^L blocks that divides
 // the image side, at most max(B, 4096 / B) pixels wide.
@@ -209,11 +80,12 @@ static int haar_width(const GeomDev &g)
     return wb * g.B;
 }
 
-static void build_tiles(const wmg_plan *pl, ProbSet &ps)
+void build_tiles(const wmg_plan *pl, ProbSet &ps)
 {
     ps.proj.h.clear(); ps.bp.h.clear(); ps.haar.h.clear(); ps.vimg.h.clear(); ps.vsino.h.clear();
     ps.haar_smem = 0;
     for (int q = 0; q < ps.nprob; ++q) {
+        if (ps.h[q].geom < 0) continue;          // an empty server slot: no tiles
         const Geo &G = *pl->geos[ps.h[q].geom];
         const GeomDev &g = G.g;
         const int W = G.haar_W;
@@ -231,7 +103,7 @@ static void build_tiles(const wmg_plan *pl, ProbSet &ps)
     }
 }
 
-static bool upload_set(ProbSet &ps, cudaStream_t st)
+bool upload_set(ProbSet &ps, cudaStream_t st)
 {
     if (!ps.d.ensure(std::max<size_t>(1, ps.h.size()) * sizeof(ProbDev))) return false;
     cudaMemcpyAsync(ps.d.p, ps.h.data(), ps.h.size() * sizeof(ProbDev), cudaMemcpyHostToDevice, st);
@@ -269,6 +141,8 @@ static int32_t set_slots(wmg_plan *pl, cudaStream_t st)
     pl->leafsets.clear();
     pl->segsets.clear();
     pl->cap = count;
+    pl->live.resize(count);
+    for (int q = 0; q < count; ++q) pl->live[q] = q;
     if (!pl->S.ensure((size_t)count * NSCAL * sizeof(double)) ||
         !pl->lam.ensure((size_t)count * sizeof(double)))
         return fail(WMG_ERR_OOM, "scalar allocation failed");
@@ -291,9 +165,9 @@ static int32_t ensure_count(wmg_plan *pl, int count, cudaStream_t st)
     return set_slots(pl, st);
 }
 
-static bool ensure_pool(DevBuf &b, int64_t elems, size_t esz) { return b.ensure((size_t)elems * esz); }
+bool ensure_pool(DevBuf &b, int64_t elems, size_t esz) { return b.ensure((size_t)elems * esz); }
 
-static bool ensure_partials(wmg_plan *pl, size_t per_tile_max)
+bool ensure_partials(wmg_plan *pl, size_t per_tile_max)
 {
     const ProbSet &ps = pl->real;
     size_t n = std::max({(size_t)ps.proj.h.size(), (size_t)ps.bp.h.size(), (size_t)ps.vimg.h.size(),
@@ -316,7 +190,7 @@ static void prof_begin(wmg_plan *pl, int kind, int images, cudaStream_t st)
 static void prof_end(wmg_plan *pl, cudaStream_t st) { cudaEventRecord(pl->prof.back().e1, st); }
 
 template <class T>
-static void project(wmg_plan *pl, const ProbSet &ps, const void *img, const void *imgT, void *sino,
+void project(wmg_plan *pl, const ProbSet &ps, const void *img, const void *imgT, void *sino,
                     double *part, const double *S, cudaStream_t st)
 {
     PjArgs a{img, imgT, sino, part, S};
@@ -327,7 +201,7 @@ static void project(wmg_plan *pl, const ProbSet &ps, const void *img, const void
 }
 
 template <class T>
-static void backproject(wmg_plan *pl, const ProbSet &ps, BpArgs a, cudaStream_t st)
+void backproject(wmg_plan *pl, const ProbSet &ps, BpArgs a, cudaStream_t st)
 {
     a.unit = pl->unit_bins ? 1 : 0;
     if (pl->profiling) prof_begin(pl, 1, ps.nprob, st);
@@ -336,7 +210,7 @@ static void backproject(wmg_plan *pl, const ProbSet &ps, BpArgs a, cudaStream_t 
     if (pl->profiling) prof_end(pl, st);
 }
 
-static BpArgs bp_args(int epi, const void *sino, const double *S)
+BpArgs bp_args(int epi, const void *sino, const double *S)
 {
     BpArgs a{};
     a.unit = 0;
@@ -347,14 +221,14 @@ static BpArgs bp_args(int epi, const void *sino, const double *S)
 }
 
 template <class T>
-static void img_op(wmg_plan *pl, int op, ImgArgs a, cudaStream_t st)
+void img_op(wmg_plan *pl, int op, ImgArgs a, cudaStream_t st)
 {
     const ProbSet &ps = pl->real;
     launch_img<T>(op, pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.bp.tiles.as<int4>(), ps.bp.n, a, st);
 }
 
 template <class T>
-static void vec_op(wmg_plan *pl, int op, bool sino, VecArgs a, cudaStream_t st)
+void vec_op(wmg_plan *pl, int op, bool sino, VecArgs a, cudaStream_t st)
 {
     const ProbSet &ps = pl->real;
     const TileList &tl = sino ? ps.vsino : ps.vimg;
@@ -362,10 +236,9 @@ static void vec_op(wmg_plan *pl, int op, bool sino, VecArgs a, cudaStream_t st)
     launch_vec<T>(op, ps.d.as<ProbDev>(), tl.tiles.as<int4>(), tl.n, a, st);
 }
 
-static void finalize(wmg_plan *pl, int op, const TileList &ta, const double *pa, int nsum,
-                     const TileList *tb, const double *pb, int precond, double *hist, int hist_ld,
-                     cudaStream_t st, int store_slot = 0, double *store_vec = nullptr, int store_ld = 0,
-                     int part_ld = 1)
+void finalize(wmg_plan *pl, int op, const TileList &ta, const double *pa, int nsum, const TileList *tb,
+              const double *pb, int precond, double *hist, int hist_ld, cudaStream_t st, int store_slot,
+              double *store_vec, int store_ld, int part_ld)
 {
     FinArgs f{};
     f.op = op;
@@ -582,11 +455,12 @@ static int32_t coarse(wmg_plan *pl, int d, const std::vector<int> &nodes, const 
 static int max_levels(const wmg_plan *pl)
 {
     int L = 0;
-    for (auto &g : pl->geos) L = std::max(L, g->g.L);
+    for (auto &g : pl->geos)
+        if (g) L = std::max(L, g->g.L);
     return L;
 }
 
-static int32_t ensure_wmg_pools(wmg_plan *pl)
+int32_t ensure_wmg_pools(wmg_plan *pl)
 {
     const int64_t nN = pl->Ntot, nM = pl->Mtot;
     const size_t e = pl->esz;
@@ -613,7 +487,7 @@ static int32_t ensure_wmg_pools(wmg_plan *pl)
 // If `sz_part`, the tile partials of s.z over the backprojection tiles are
 // left in part_b (returns true in *have_sz).
 template <class T>
-static int32_t wmg_apply(wmg_plan *pl, double *s, double *z, bool first_done, bool copies, bool sz_part,
+int32_t wmg_apply(wmg_plan *pl, double *s, double *z, bool first_done, bool copies, bool sz_part,
                          bool *have_sz, cudaStream_t st)
 {
     const wmg_opts &o = pl->opts;
@@ -646,9 +520,7 @@ static int32_t wmg_apply(wmg_plan *pl, double *s, double *z, bool first_done, bo
     ha.mode = HA_STORE; ha.in = pl->r1.p; ha.out = pl->C.p; ha.S = S;
     launch_haar_analysis<double, double>(G, ps.d.as<ProbDev>(), ps.haar.tiles.as<int4>(), ps.haar.n,
                                          ps.haar_smem, ha, st);
-    std::vector<int> all(pl->cap);
-    for (int q = 0; q < pl->cap; ++q) all[q] = q;
-    int32_t rc = coarse<T>(pl, 0, std::vector<int>{0}, all, pl->C, pl->E, st);
+    int32_t rc = coarse<T>(pl, 0, std::vector<int>{0}, pl->live, pl->C, pl->E, st);
     if (rc) return rc;
     const bool need_copies_after_syn = copies || o.nu2 > 0;
     HaarArgs hs{};
@@ -693,7 +565,7 @@ __global__ void k_recip(const T *in, T *out, int64_t n, double add)
     }
 }
 
-static int32_t validate(const wmg_geom *g, const wmg_opts *o)
+int32_t validate(const wmg_geom *g, const wmg_opts *o)
 {
     if (!g || !o) return fail(WMG_ERR_INVALID_ARG, "geometry or options NULL");
     if (g->n < 1 || g->m < 1 || g->D < 1) return fail(WMG_ERR_INVALID_ARG, "n, m and D must be >= 1");
@@ -713,7 +585,7 @@ static int32_t validate(const wmg_geom *g, const wmg_opts *o)
 }
 
 // Host part of a geometry: angle tables and scalar fields.
-static int32_t make_geo(const wmg_geom *g, const wmg_opts *o, Geo &G, cudaStream_t st)
+int32_t make_geo(const wmg_geom *g, const wmg_opts *o, Geo &G, cudaStream_t st)
 {
     G.has_wmg = o->levels >= 1;
     const int L = G.has_wmg ? o->levels - 1 : 0;
@@ -760,14 +632,19 @@ static int32_t make_geo(const wmg_geom *g, const wmg_opts *o, Geo &G, cudaStream
     gd.t0f = (float)gd.t0;
     gd.hDf = 0.5f * (float)(g->D - 1);
     G.unit_bins = gd.dt == 1.0 && gd.t0 == 0.0;
+    gd.unit = G.unit_bins ? 1 : 0;
     return WMG_OK;
 }
 
-static int32_t upload_geoms(wmg_plan *pl, cudaStream_t st)
+int32_t upload_geoms(wmg_plan *pl, cudaStream_t st)
 {
     std::vector<GeomDev> h;
     bool unit = true;
-    for (auto &g : pl->geos) { h.push_back(g->g); unit = unit && g->unit_bins; }
+    for (auto &g : pl->geos) {
+        if (!g) { h.push_back(GeomDev{}); continue; }   // an evicted server geometry
+        h.push_back(g->g);
+        unit = unit && g->unit_bins;
+    }
     pl->unit_bins = unit;
     if (!pl->d_geom.ensure(h.size() * sizeof(GeomDev))) return fail(WMG_ERR_OOM, "geometry table");
     WMG_CUDA(cudaMemcpyAsync(pl->d_geom.p, h.data(), h.size() * sizeof(GeomDev), cudaMemcpyHostToDevice, st));
@@ -778,7 +655,7 @@ static int32_t upload_geoms(wmg_plan *pl, cudaStream_t st)
 // Device setup of geometry gi: D~ = W^T (W 1) + lambda, SIRT R and C, nnz(W)
 // and the leaf inverses. Runs on a one-slot table of that geometry.
 template <class T>
-static int32_t setup_geometry(wmg_plan *pl, int gi, cudaStream_t st)
+int32_t setup_geometry(wmg_plan *pl, int gi, cudaStream_t st)
 {
     Geo &G = *pl->geos[gi];
     const int64_t N = G.N, M = G.M;
@@ -835,6 +712,21 @@ static int32_t setup_geometry(wmg_plan *pl, int gi, cudaStream_t st)
     WMG_CUDA(cudaGetLastError());
     return WMG_OK;
 }
+
+template void project<float>(wmg_plan *, const ProbSet &, const void *, const void *, void *, double *,
+                             const double *, cudaStream_t);
+template void project<double>(wmg_plan *, const ProbSet &, const void *, const void *, void *, double *,
+                              const double *, cudaStream_t);
+template void backproject<float>(wmg_plan *, const ProbSet &, BpArgs, cudaStream_t);
+template void backproject<double>(wmg_plan *, const ProbSet &, BpArgs, cudaStream_t);
+template void img_op<float>(wmg_plan *, int, ImgArgs, cudaStream_t);
+template void img_op<double>(wmg_plan *, int, ImgArgs, cudaStream_t);
+template void vec_op<float>(wmg_plan *, int, bool, VecArgs, cudaStream_t);
+template void vec_op<double>(wmg_plan *, int, bool, VecArgs, cudaStream_t);
+template int32_t wmg_apply<float>(wmg_plan *, double *, double *, bool, bool, bool, bool *, cudaStream_t);
+template int32_t wmg_apply<double>(wmg_plan *, double *, double *, bool, bool, bool, bool *, cudaStream_t);
+template int32_t setup_geometry<float>(wmg_plan *, int, cudaStream_t);
+template int32_t setup_geometry<double>(wmg_plan *, int, cudaStream_t);
 
 }  // namespace wmg
 

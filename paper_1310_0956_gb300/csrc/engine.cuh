@@ -1,0 +1,179 @@
+// engine.cuh -- host-side structures of the engine (device buffers, work
+// lists, geometries, the plan) and the engine steps shared by the plan and
+// batch drivers in engine.cu and the request server in server.cu.
+#pragma once
+
+#include <algorithm>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "kern_common.cuh"
+#include "krylov.cuh"
+
+namespace wmg {
+
+int num_sms();
+
+// ---------------------------------------------------------------------------
+// device buffers
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    // grow-only; contents are not preserved
+    bool ensure(size_t b)
+    {
+        if (b <= bytes && p) return true;
+        release();
+        if (b == 0) b = 16;
+        if (cudaMalloc(&p, b) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return false;
+        }
+        bytes = b;
+        return true;
+    }
+    template <class U> U *as() const { return static_cast<U *>(p); }
+};
+
+// ---------------------------------------------------------------------------
+// work lists and geometries
+// ---------------------------------------------------------------------------
+struct TileList {
+    DevBuf tiles, tb, te;
+    int n = 0;
+    std::vector<int4> h;
+    bool upload(int nprob, cudaStream_t st)
+    {
+        n = (int)h.size();
+        std::vector<int> b(nprob, 0), e(nprob, 0);
+        for (int i = 0; i < n; ++i) {
+            const int p = h[i].x;
+            if (i == 0 || h[i - 1].x != p) b[p] = i;
+            e[p] = i + 1;
+        }
+        if (!tiles.ensure(std::max<size_t>(1, h.size()) * sizeof(int4)) ||
+            !tb.ensure(nprob * sizeof(int)) || !te.ensure(nprob * sizeof(int)))
+            return false;
+        if (n) cudaMemcpyAsync(tiles.p, h.data(), h.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(tb.p, b.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(te.p, e.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, st);
+        // host vectors must outlive the async copies: keep them (b, e are
+        // copied synchronously with respect to pageable memory)
+        return true;
+    }
+};
+
+// A set of (real or virtual) problems with their tiles (problems may have
+// different geometries; each tile belongs to one problem).
+struct ProbSet {
+    int nprob = 0;
+    std::vector<ProbDev> h;
+    DevBuf d;
+    TileList proj, bp, haar, vimg, vsino;
+    int haar_smem = 0;
+};
+
+// One geometry of a plan with its device tables.
+struct Geo {
+    GeomDev g{};
+    int64_t N = 0, M = 0, nnz = 0;
+    bool has_wmg = true, unit_bins = true;
+    int hd = 0;                 // hybrid depth in use: min(hybrid_depth, L), 0 for additive
+    int haar_W = 1;             // Haar strip width (pixels)
+    DevBuf cs64, cs32, csx, angf, dinv, leafinv, sirtR, sirtC;
+};
+
+}  // namespace wmg
+
+// ---------------------------------------------------------------------------
+// The plan: one or more geometries and a table of problem slots. A plan made
+// by wmg_plan_create has one geometry and any number of same-geometry
+// problems per call; a batch (wmg_batch_create) has a fixed list of problems
+// of several geometries, stored grouped by geometry.
+// ---------------------------------------------------------------------------
+struct wmg_plan {
+    int prec = WMG_PREC_F64;
+    size_t esz = 8;
+    wmg_opts opts{};
+    std::vector<std::unique_ptr<wmg::Geo>> geos;
+    wmg::DevBuf d_geom;         // GeomDev array, one per geometry
+    bool unit_bins = true;      // every geometry has unit bins, zero offset
+    bool batch = false;         // fixed problem list
+    int cap = 0;                // problem slots
+    std::vector<int> pgeo;      // geometry of each slot
+    std::vector<int64_t> img_off, sino_off;
+    int64_t Ntot = 0, Mtot = 0;
+    std::vector<int> order;     // batch: slot of the caller's problem i
+    std::vector<int> live;      // slots that hold a problem, ascending (all slots but in a server)
+    wmg::ProbSet real;
+    std::map<std::vector<int>, std::unique_ptr<wmg::ProbSet>> bands;   // band-update groups
+    std::map<std::vector<int>, std::unique_ptr<wmg::TileList>> leafsets;
+    std::map<std::vector<int>, std::unique_ptr<wmg::DevBuf>> segsets;
+    // FP64 pools (all slots back to back)
+    wmg::DevBuf x, s, z, p, f, w, t, u, r;
+    // operator-precision pools
+    wmg::DevBuf p_op, pT_op, z_op, zT_op, r1, C, E, q, r_op, sinoS, b_op, x_io;
+    std::vector<std::unique_ptr<wmg::DevBuf>> csave, c2, e2;   // per hybrid depth
+    wmg::DevBuf band_img, band_imgT, band_img2, band_sino;
+    // scalars and partials
+    wmg::DevBuf S, part_a, part_b, part_c, lam, hist;
+    // GMRES
+    wmg::DevBuf V, H, gcs, gsn, gg, gy, h1, h2, jn, done;
+    // profiling: (kind 0 = project / 1 = backproject, images, start, stop)
+    bool profiling = false;
+    struct ProfRec { int kind; int images; cudaEvent_t e0, e1; };
+    std::vector<ProfRec> prof;
+    const wmg::Geo &geo(int slot) const { return *geos[pgeo[slot]]; }
+    bool has_wmg() const
+    {
+        for (auto &g : geos)
+            if (g && !g->has_wmg) return false;
+        return true;
+    }
+};
+
+namespace wmg {
+
+// ---- engine steps (engine.cu) ----------------------------------------------
+void build_tiles(const wmg_plan *pl, ProbSet &ps);
+bool upload_set(ProbSet &ps, cudaStream_t st);
+bool ensure_pool(DevBuf &b, int64_t elems, size_t esz);
+bool ensure_partials(wmg_plan *pl, size_t per_tile_max);
+template <class T>
+void project(wmg_plan *pl, const ProbSet &ps, const void *img, const void *imgT, void *sino, double *part,
+             const double *S, cudaStream_t st);
+template <class T>
+void backproject(wmg_plan *pl, const ProbSet &ps, BpArgs a, cudaStream_t st);
+BpArgs bp_args(int epi, const void *sino, const double *S);
+template <class T>
+void img_op(wmg_plan *pl, int op, ImgArgs a, cudaStream_t st);
+template <class T>
+void vec_op(wmg_plan *pl, int op, bool sino, VecArgs a, cudaStream_t st);
+void finalize(wmg_plan *pl, int op, const TileList &ta, const double *pa, int nsum, const TileList *tb,
+              const double *pb, int precond, double *hist, int hist_ld, cudaStream_t st, int store_slot = 0,
+              double *store_vec = nullptr, int store_ld = 0, int part_ld = 1);
+template <class T>
+int32_t wmg_apply(wmg_plan *pl, double *s, double *z, bool first_done, bool copies, bool sz_part,
+                  bool *have_sz, cudaStream_t st);
+int32_t ensure_wmg_pools(wmg_plan *pl);
+int32_t validate(const wmg_geom *g, const wmg_opts *o);
+int32_t make_geo(const wmg_geom *g, const wmg_opts *o, Geo &G, cudaStream_t st);
+int32_t upload_geoms(wmg_plan *pl, cudaStream_t st);
+template <class T>
+int32_t setup_geometry(wmg_plan *pl, int gi, cudaStream_t st);
+
+}  // namespace wmg

@@ -147,19 +147,22 @@ k_vec(const ProbDev *__restrict__ P, const int4 *__restrict__ tiles, int ntiles,
 
 // ---------------------------------------------------------------------------
 // GMRES: classical Gram-Schmidt passes over the basis V (restart+1 vectors of
-// N per problem, stride `vstride` elements between basis vectors).
+// N per problem, stride `vstride` elements between basis vectors). The column
+// index j is one for all problems, or, when `jv` is given, jv[slot] per
+// problem (problems at different Arnoldi steps in one launch).
 // ---------------------------------------------------------------------------
 // Partial dots part[t * (jmax+1) + i] = <V_i, w> over the tile, i <= j.
 __global__ void __launch_bounds__(256)
 k_gm_dots(const ProbDev *__restrict__ P, const int4 *__restrict__ tiles, int ntiles,
-          const double *__restrict__ V, int64_t vstride, const double *__restrict__ w, int j,
-          int ldp, double *__restrict__ part, const double *__restrict__ S)
+          const double *__restrict__ V, int64_t vstride, const double *__restrict__ w, int j0,
+          const int *__restrict__ jv, int ldp, double *__restrict__ part, const double *__restrict__ S)
 {
     __shared__ double red[8];
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 tl = tiles[t];
         const ProbDev pd = P[tl.x];
         if (!slot_active(S, pd.slot)) continue;
+        const int j = jv ? jv[pd.slot] : j0;
         for (int i = 0; i <= j; ++i) {
             const double *Vi = V + (int64_t)i * vstride + pd.img;
             double acc = 0.0;
@@ -177,14 +180,16 @@ k_gm_dots(const ProbDev *__restrict__ P, const int4 *__restrict__ tiles, int nti
 // w -= sum_i h_i V_i (h from Hc[slot*ldp + i]); part = |w|^2 after the update.
 __global__ void __launch_bounds__(256)
 k_gm_axpy(const ProbDev *__restrict__ P, const int4 *__restrict__ tiles, int ntiles,
-          const double *__restrict__ V, int64_t vstride, double *__restrict__ w, int j, int ldp,
-          const double *__restrict__ Hc, double *__restrict__ part, const double *__restrict__ S)
+          const double *__restrict__ V, int64_t vstride, double *__restrict__ w, int j0,
+          const int *__restrict__ jv, int ldp, const double *__restrict__ Hc, double *__restrict__ part,
+          const double *__restrict__ S)
 {
     __shared__ double red[8];
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 tl = tiles[t];
         const ProbDev pd = P[tl.x];
         if (!slot_active(S, pd.slot)) continue;
+        const int j = jv ? jv[pd.slot] : j0;
         const double *h = Hc + (int64_t)pd.slot * ldp;
         const double *Vb = V + pd.img;
         double acc = 0.0;
@@ -225,16 +230,17 @@ k_gm_combine(const ProbDev *__restrict__ P, const int4 *__restrict__ tiles, int 
     }
 }
 
-// v_j = w / S[HNORM], written into basis slot j.
+// v_j = w / S[HNORM], written into basis slot j (jv[slot] when given).
 __global__ void __launch_bounds__(256)
 k_gm_setv(const ProbDev *__restrict__ P, const int4 *__restrict__ tiles, int ntiles,
-          double *__restrict__ V, int64_t vstride, int ldp, int j, const double *__restrict__ w,
-          const double *__restrict__ S)
+          double *__restrict__ V, int64_t vstride, int ldp, int j0, const int *__restrict__ jv,
+          const double *__restrict__ w, const double *__restrict__ S)
 {
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 tl = tiles[t];
         const ProbDev pd = P[tl.x];
         if (!slot_active(S, pd.slot)) continue;
+        const int j = jv ? jv[pd.slot] : j0;
         const double hn = S[(int64_t)pd.slot * NSCAL + SC_HNORM];
         const double inv = hn != 0.0 ? 1.0 / hn : 0.0;
         double *Vj = V + (int64_t)j * vstride + pd.img;
@@ -350,7 +356,7 @@ __global__ void k_gm_arnoldi(GmArgs a)
     if (p >= a.nprob) return;
     double *S = a.S + (int64_t)p * NSCAL;
     if (S[SC_ACTIVE] == 0.0 || a.done[p]) return;
-    const int ld = a.ldp, j = a.j, r = a.restart;
+    const int ld = a.ldp, j = a.jslot ? a.jn[p] : a.j, r = a.restart;
     double *H = a.H + (int64_t)p * (r + 1) * r;     // H[i*r + jj]
     double *cs = a.cs + (int64_t)p * r, *sn = a.sn + (int64_t)p * r, *g = a.g + (int64_t)p * (r + 1);
     const double *h1 = a.h1 + (int64_t)p * ld, *h2 = a.h2 + (int64_t)p * ld;
@@ -495,19 +501,20 @@ void launch_finalize(const FinArgs &f, cudaStream_t st)
 }
 
 void launch_gm_dots(const ProbDev *P, const int4 *tiles, int ntiles, const double *V, int64_t vstride,
-                    const double *w, int j, int ldp, double *part, const double *S, cudaStream_t st)
+                    const double *w, int j, int ldp, double *part, const double *S, cudaStream_t st,
+                    const int *jv)
 {
     if (ntiles <= 0) return;
     count_launches(1);
-    k_gm_dots<<<grid_for(ntiles), 256, 0, st>>>(P, tiles, ntiles, V, vstride, w, j, ldp, part, S);
+    k_gm_dots<<<grid_for(ntiles), 256, 0, st>>>(P, tiles, ntiles, V, vstride, w, j, jv, ldp, part, S);
 }
 void launch_gm_axpy(const ProbDev *P, const int4 *tiles, int ntiles, const double *V, int64_t vstride,
                     double *w, int j, int ldp, const double *Hc, double *part, const double *S,
-                    cudaStream_t st)
+                    cudaStream_t st, const int *jv)
 {
     if (ntiles <= 0) return;
     count_launches(1);
-    k_gm_axpy<<<grid_for(ntiles), 256, 0, st>>>(P, tiles, ntiles, V, vstride, w, j, ldp, Hc, part, S);
+    k_gm_axpy<<<grid_for(ntiles), 256, 0, st>>>(P, tiles, ntiles, V, vstride, w, j, jv, ldp, Hc, part, S);
 }
 void launch_gm_combine(const ProbDev *P, const int4 *tiles, int ntiles, const double *V,
                        int64_t vstride, int ldp, const double *Yv, const int *jn, double *out,
@@ -518,11 +525,11 @@ void launch_gm_combine(const ProbDev *P, const int4 *tiles, int ntiles, const do
     k_gm_combine<<<grid_for(ntiles), 256, 0, st>>>(P, tiles, ntiles, V, vstride, ldp, Yv, jn, out, S);
 }
 void launch_gm_setv(const ProbDev *P, const int4 *tiles, int ntiles, double *V, int64_t vstride,
-                    int ldp, int j, const double *w, const double *S, cudaStream_t st)
+                    int ldp, int j, const double *w, const double *S, cudaStream_t st, const int *jv)
 {
     if (ntiles <= 0) return;
     count_launches(1);
-    k_gm_setv<<<grid_for(ntiles), 256, 0, st>>>(P, tiles, ntiles, V, vstride, ldp, j, w, S);
+    k_gm_setv<<<grid_for(ntiles), 256, 0, st>>>(P, tiles, ntiles, V, vstride, ldp, j, jv, w, S);
 }
 void launch_gm_scalar(int which, const GmArgs &a, cudaStream_t st)
 {

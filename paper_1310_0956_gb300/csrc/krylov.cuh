@@ -81,6 +81,7 @@ struct FinArgs {
 
 struct GmArgs {
     int nprob, restart, ldp, j, init;
+    int jslot;               // Arnoldi step: column jn[p] per problem instead of j
     double *S, *H, *cs, *sn, *g, *y;
     const double *h1, *h2;
     int *jn, *done;
@@ -95,16 +96,19 @@ template <class T>
 void launch_vec(int op, const ProbDev *P, const int4 *tiles, int ntiles, const VecArgs &a,
                 cudaStream_t st);
 void launch_finalize(const FinArgs &f, cudaStream_t st);
+// jv (optional): per-slot column index replacing j
 void launch_gm_dots(const ProbDev *P, const int4 *tiles, int ntiles, const double *V, int64_t vstride,
-                    const double *w, int j, int ldp, double *part, const double *S, cudaStream_t st);
+                    const double *w, int j, int ldp, double *part, const double *S, cudaStream_t st,
+                    const int *jv = nullptr);
 void launch_gm_axpy(const ProbDev *P, const int4 *tiles, int ntiles, const double *V, int64_t vstride,
                     double *w, int j, int ldp, const double *Hc, double *part, const double *S,
-                    cudaStream_t st);
+                    cudaStream_t st, const int *jv = nullptr);
 void launch_gm_combine(const ProbDev *P, const int4 *tiles, int ntiles, const double *V,
                        int64_t vstride, int ldp, const double *Yv, const int *jn, double *out,
                        const double *S, cudaStream_t st);
 void launch_gm_setv(const ProbDev *P, const int4 *tiles, int ntiles, double *V, int64_t vstride,
-                    int ldp, int j, const double *w, const double *S, cudaStream_t st);
+                    int ldp, int j, const double *w, const double *S, cudaStream_t st,
+                    const int *jv = nullptr);
 // which: 0 = Arnoldi scalar step, 1 = solve H y = g, 2 = restart
 void launch_gm_scalar(int which, const GmArgs &a, cudaStream_t st);
 

@@ -161,9 +161,12 @@ void launch_project_f32(const GeomDev *G, const ProbDev *P, const int4 *tiles, i
 
 // ---------------------------------------------------------------------------
 // Backward: tile = {prob, iy0, ix0, 0} of 32 x 32 pixels, thread = one column
-// and 4 rows 8 apart. UNIT: unit bin spacing (two candidate bins).
+// and 4 rows 8 apart. Geometries with unit bins (g.unit) take the two-bin
+// path, the others the general one; ALL_UNIT (every geometry of the launch
+// has unit bins) compiles the general path out. The choice depends on the
+// tile's own geometry only, so a problem gets the same bits in any batch.
 // ---------------------------------------------------------------------------
-template <int EPI, bool UNIT>
+template <int EPI, bool ALL_UNIT>
 __global__ void __launch_bounds__(256)
 k_backproject_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
                   const int4 *__restrict__ tiles, int ntiles, BpArgs a)
@@ -182,6 +185,7 @@ k_backproject_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
         const float yo0 = (float)(tl.y + ty) + 0.5f - half_n;
         const float *__restrict__ sg = static_cast<const float *>(a.sino) + pd.sino;
         const float hD = g.hDf, dt = g.dtf, t0 = g.t0f, inv_dt = 1.f / g.dtf;
+        const bool unit = ALL_UNIT || g.unit;
         float s[4] = {0.f, 0.f, 0.f, 0.f}, cmp[4] = {0.f, 0.f, 0.f, 0.f};
         for (int ang = 0; ang < m; ++ang) {
             const AngleF A = g.angf[ang];
@@ -193,7 +197,7 @@ k_backproject_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 float rs;
-                if (UNIT) {
+                if (unit) {
                     // the two bins nearest tau (support half-width <= sqrt(1/2))
                     const int k0 = __float2int_rd((ph + pc) - t0 + hD);
                     const float tk = (float)k0 - hD + t0;
@@ -201,7 +205,9 @@ k_backproject_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
                     const float w0 = chord_n(A.wa, A.wb, fabsf(d0)), w1 = chord_n(A.wa, A.wb, fabsf(d0 + 1.f));
                     const float v0 = (unsigned)k0 < (unsigned)D ? __ldg(row + k0) : 0.f;
                     const float v1 = (unsigned)(k0 + 1) < (unsigned)D ? __ldg(row + k0 + 1) : 0.f;
-                    rs = __fmaf_rn(w0, v0, w1 * v1) * A.lmax;
+                    // explicit rounding: no contraction into the Kahan step
+                    // below, whichever paths the instantiation holds
+                    rs = __fmul_rn(__fmaf_rn(w0, v0, w1 * v1), A.lmax);
                 } else {
                     const float hwb = A.hw * inv_dt;
                     const int k0 = __float2int_ru(((ph + pc) - t0) * inv_dt + hD - hwb);

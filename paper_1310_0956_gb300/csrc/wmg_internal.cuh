@@ -55,6 +55,8 @@ struct GeomDev {
     const void *sirtC;       // N: 1/column sums (0 if empty)
     const AngleF *angf;      // m per-angle constants (FP32 kernels)
     float hf, dtf, t0f, hDf; // FP32 copies of h, dt, t0 and (D-1)/2
+    int unit;                // bins of one pixel width, no offset: the FP32
+                             // backprojector takes its two-bin path
 };
 
 // Fills the FP32 per-angle table from FP64 (cos, sin) pairs.
@@ -75,6 +77,7 @@ struct ProbDev {
 enum Scal : int {
     SC_GAMMA = 0, SC_DELTA, SC_ALPHA, SC_BETA, SC_S0, SC_RES, SC_PP, SC_ITERS, SC_ACTIVE,
     SC_STATUS, SC_RTOL, SC_MAXIT, SC_HNORM, SC_WNORM2, SC_GNEW,
+    SC_HELD,                 // server: SC_ACTIVE of a slot held out of a phase group
     NSCAL = 16
 };
 
@@ -122,7 +125,7 @@ enum BpEpi : int {
 
 struct BpArgs {
     int epi;
-    int unit;                // FP32 kernels: unit bin spacing, zero offset (two candidate bins)
+    int unit;                // FP32 kernels: every geometry of the launch has unit bins
     const void *sino;        // T, sinogram input pool
     void *out_op;            // T image output (BP_STORE, BP_RESID, BP_APPLY_A)
     double *x, *s, *z, *p;   // FP64 Krylov vectors (pools)

@@ -65,3 +65,28 @@ def test_batch_matches_oracle_f64():
         x = xs[i].cpu().numpy()
         assert infos[i][0] == k == 12
         assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) < 1e-10
+
+
+def test_batch_mixed_bin_spacing_equals_alone():
+    # a geometry with wider, offset bins in the batch must not change how the
+    # unit-bin problems are computed (the FP32 backprojector picks its path
+    # per geometry), and vice versa
+    probs = [dict(n=32, m=24, D=46, levels=3), dict(n=32, m=24, D=40, levels=3, det_spacing=1.25, det_offset=0.5),
+             dict(n=24, m=20, D=34, levels=2)]
+    bs = []
+    for i, p in enumerate(probs):
+        op = oracle.Op(p["n"], p["m"], p["D"], p.get("det_spacing", 1.0), p.get("det_offset", 0.0))
+        b = op.project(S.phantom(p["n"], 5, S.seed_for(3, 300 + i)))
+        bs.append(torch.tensor(b, dtype=torch.float32, device="cuda"))
+    batch = wmg.Batch(probs, nu1=1, nu2=1, hybrid_depth=1, cycle=wmg.CYCLE_HYBRID, precision=wmg.PREC_F32)
+    xs, infos, _ = batch.solve(bs, wmg.SOLVER_GMRES, True, max_iter=30, rtol=1e-6)
+    torch.cuda.synchronize()
+    for i, p in enumerate(probs):
+        plan = wmg.Plan(p["n"], p["m"], p["D"], levels=p["levels"], nu1=1, nu2=1, hybrid_depth=1,
+                        cycle=wmg.CYCLE_HYBRID, precision=wmg.PREC_F32, det_spacing=p.get("det_spacing", 1.0),
+                        det_offset=p.get("det_offset", 0.0))
+        x1, info1, _, _ = plan.solve(bs[i], wmg.SOLVER_GMRES, True, max_iter=30, rtol=1e-6)
+        torch.cuda.synchronize()
+        plan.close()
+        assert info1[0][0] == infos[i][0]
+        assert torch.equal(x1, xs[i]), i

@@ -707,7 +707,7 @@ int32_t setup_geometry(wmg_plan *pl, int gi, cudaStream_t st)
         return fail(WMG_ERR_OOM, "leaf inverse allocation failed");
     G.g.leafinv = G.leafinv.as<double>();
     if ((rc = upload_geoms(pl, st))) return rc;
-    rc = build_leaf_inverses(G.g, pl->d_geom.as<GeomDev>() + gi, G.leafinv.as<double>(), st);
+    rc = build_leaf_inverses(G.g, pl->d_geom.as<GeomDev>() + gi, G.leafinv.as<double>(), sizeof(T) == 4, st);
     if (rc) return rc;
     WMG_CUDA(cudaGetLastError());
     return WMG_OK;

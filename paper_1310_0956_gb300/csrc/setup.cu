@@ -5,16 +5,33 @@
 // Leaf k's matrix is D_k = Q_k^T (W^T W + lambda I) Q_k = G_k^T G_k + lambda I
 // with G_k = W Q_k (the paper's tall-and-skinny W I_{2h,id}^h, here never
 // stored whole). Each column of Q_k is a 2^L x 2^L Walsh pattern
-// (+-2^-L) on one pixel block, so G_k[ray, block] is the ray's intersection
-// lengths inside the block weighted by the pattern's signs. The assembly runs
-// per chunk of angles in two deterministic passes:
-//   1. for every (angle, block) and every ray that can cross the block, the
-//      K leaf coefficients of the ray's weights inside the block;
-//   2. for every pair of blocks (b1 <= b2) and every leaf, the sum over the
-//      chunk's rays that cross both blocks, added to D_k[b1][b2] in FP64.
+// (+-2^-L) on one pixel block, so G_k[ray, block] -- the ray's "profile"
+// coefficient -- is the ray's intersection lengths inside the block weighted
+// by the pattern's signs. Leaf k is the pattern pair (HY, HX) (row and column
+// Walsh indices) with HY, HX the bit-reversed odd / even bits of k.
+//
+// The assembly runs over tiles of leaves and chunks of angles, in two passes
+// per (tile, chunk):
+//   1. profiles: for every (angle, block) and every ray that can cross the
+//      block, the tile's coefficients. A ray crosses at most two pixels per
+//      frame row (the image rows for |cos| >= |sin|, columns otherwise), so
+//      the tile is "S masks along the frame columns x all B masks along the
+//      frame rows" (sign of pixel (row, col) under masks (R, C):
+//      (-1)^(popc(R & row) + popc(C & col))): h[row][j] = sum over the row's
+//      pixels of sign x weight for each of the S column masks, then a fast
+//      Walsh-Hadamard transform along the rows gives all B row masks
+//      (2 + log2 B operations per coefficient);
+//   2. pairs: for every block b1 and every block b2 >= b1 whose ray ranges
+//      overlap at an angle, the sum over the shared rays of the products of
+//      their coefficients, added to D[b1][b2] (FP64).
+// Profiles and pair sums run in the operator precision (FP32 for F32 plans:
+// a pair sum has at most ~1.5 B terms), D accumulates over angles in FP64.
+// Every D entry is owned by one thread of one launch and the launches run in
+// a fixed order, so the result is the same on every run.
 // Then D_k += lambda I and every leaf is factorised (Cholesky, FP64, pivot
-// test) and inverted (two triangular solves per column), the inverse
-// rounded to the operator precision.
+// test) and inverted (two triangular solves per column).
+#include <climits>
+
 #include "kern_common.cuh"
 
 namespace wmg {
@@ -34,6 +51,12 @@ __device__ __forceinline__ void block_ray_range(const GeomDev &g, int a, int b, 
     khi = min(g.D - 1, (int)floor(u + hw / g.dt + 1e-9));
 }
 
+__device__ __forceinline__ int spread_bits(int v, int L)
+{
+    int r = 0;
+    for (int i = 0; i < L; ++i) r |= ((v >> i) & 1) << (2 * i);
+    return r;
+}
 __device__ __forceinline__ int unspread_bits(int v, int L)
 {
     int r = 0;
@@ -42,130 +65,288 @@ __device__ __forceinline__ int unspread_bits(int v, int L)
 }
 __device__ __forceinline__ int bitrev_L(int u, int L) { return L ? (int)(__brev((unsigned)u) >> (32 - L)) : 0; }
 
-// Pass 1. tile = {angle a (absolute), block b, 0, 0}; writes
-// Gbuf[((a - a0) * P + b) * R + (k - klo)) * K + leaf].
-__global__ void __launch_bounds__(256)
-k_leaf_coeffs(const GeomDev *__restrict__ Gd, int a0, int na, int R, double *__restrict__ Gbuf)
+// Tile-local coefficient index t of (column pattern j, row pattern T) and the
+// (HY, HX) index c = HY * B + HX it stands for. Class 0 (|cos| >= |sin|):
+// frame rows are image rows, so T = HY and HX = q0 + j, t = T * S + j.
+// Class 1: frame rows are image columns, T = HX and HY = q0 + j, t = j * B + T.
+__device__ __forceinline__ int tile_t(int cls, int j, int T, int S, int B) { return cls ? j * B + T : T * S + j; }
+__device__ __forceinline__ int tile_c(int cls, int t, int q0, int S, int B)
 {
-    __shared__ double wv[2 * 128];
-    __shared__ int wl[2 * 128];
+    if (cls) { const int j = t / B, T = t - j * B; return (q0 + j) * B + T; }
+    const int T = t / S, j = t - T * S;
+    return T * B + q0 + j;
+}
+
+// Pass 1a. CTA = (angle al of the chunk, block b); thread = (ray, frame row).
+// The ray's (at most) two pixels of the frame row inside the block:
+// Fw[(((al * P + b) * R + kk) * B + row) * 2 + q] = weight x h / B (0 if none),
+// Fc[...] = frame column (-1 if none). rng[al * P + b] = (klo, ray count).
+template <class TG>
+__global__ void __launch_bounds__(256)
+k_leaf_footprint(const GeomDev *__restrict__ Gd, const int *__restrict__ alist, int na, int R,
+                 int2 *__restrict__ rng, TG *__restrict__ Fw, signed char *__restrict__ Fc)
+{
     const GeomDev &g = *Gd;
-    const int P = g.P, K = g.K, B = g.B, L = g.L, n = g.n;
-    const int ntiles = na * P;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int al = t / P, b = t - al * P, a = a0 + al;
+    const int P = g.P, B = g.B, n = g.n;
+    for (int tile = blockIdx.x; tile < na * P; tile += gridDim.x) {
+        const int al = tile / P, b = tile - al * P, a = alist[al];
         int klo, khi;
         block_ray_range(g, a, b, klo, khi);
+        const int cnt = max(0, min(khi - klo + 1, R));
+        if (threadIdx.x == 0) rng[tile] = make_int2(klo, cnt);
         const double2 cs = g.cs64[a];
         const bool steep = fabs(cs.x) >= fabs(cs.y);
         const double cc = steep ? cs.x : cs.y, ss = steep ? cs.y : cs.x;
         const Chord<double> ch = make_chord<double>(cc, ss);
-        const double hwx = ch.hw / fabs(cc), half_n = 0.5 * n;
+        const double inv_cc = 1.0 / cc, hwx = ch.hw / fabs(cc), half_n = 0.5 * n;
         const int cy = b / g.nc, cx = b - cy * g.nc;
         const int fr0 = (steep ? cy : cx) * B, fx0 = (steep ? cx : cy) * B;
-        for (int k = klo; k <= khi && k - klo < R; ++k) {
-            const double tk = ray_offset<double>(g, k);
-            if (threadIdx.x < B) {                       // one frame row per thread
-                const int fr = fr0 + threadIdx.x;
-                const double yc = fr + 0.5 - half_n;
-                const double xs = (tk - yc * ss) / cc;
-                const int f0 = (int)ceil(xs + half_n - 0.5 - hwx);
-                for (int q = 0; q < 2; ++q) {
-                    const int fx = f0 + q;
-                    double w = 0.0;
-                    int loc = 0;
-                    if (fx >= fx0 && fx < fx0 + B) {
-                        const double xc = fx + 0.5 - half_n;
-                        const LineD ln{tk, cc, ss};
-                        w = ch(fabs(line_dist(ln, xc, yc)));
-                        const int ly = steep ? fr - fr0 : fx - fx0;
-                        const int lx = steep ? fx - fx0 : fr - fr0;
-                        loc = (ly << 8) | lx;
-                    }
-                    wv[2 * threadIdx.x + q] = w;
-                    wl[2 * threadIdx.x + q] = loc;
+        const double scale = g.h / (double)B;                        // unit-square length x 2^-L
+        for (int e = threadIdx.x; e < cnt * B; e += blockDim.x) {
+            const int kk = e / B, row = e - kk * B;
+            const double tk = ray_offset<double>(g, klo + kk);
+            const int fr = fr0 + row;
+            const double yc = fr + 0.5 - half_n;
+            const double xs = (tk - yc * ss) * inv_cc;
+            const int f0 = (int)ceil(xs + half_n - 0.5 - hwx);
+            const int64_t o = (((int64_t)tile * R + kk) * B + row) * 2;
+            for (int q = 0; q < 2; ++q) {
+                const int fx = f0 + q;
+                double w = 0.0;
+                int col = -1;
+                if (fx >= fx0 && fx < fx0 + B) {
+                    const double xc = fx + 0.5 - half_n;
+                    const LineD ln{tk, cc, ss};
+                    w = ch(fabs(line_dist(ln, xc, yc)));
+                    col = fx - fx0;
                 }
+                Fw[o + q] = (TG)(w * scale);
+                Fc[o + q] = (signed char)col;
             }
-            __syncthreads();
-            const double scale = g.h / (double)B;        // unit-square length x 2^-L
-            for (int leaf = threadIdx.x; leaf < K; leaf += blockDim.x) {
-                const int HY = bitrev_L(unspread_bits(leaf >> 1, L), L);
-                const int HX = bitrev_L(unspread_bits(leaf, L), L);
-                double acc = 0.0;
-                for (int e = 0; e < 2 * B; ++e) {
-                    const double w = wv[e];
-                    if (w != 0.0) {
-                        const int loc = wl[e];
-                        const int par = (__popc(HY & (loc >> 8)) + __popc(HX & (loc & 255))) & 1;
-                        acc += par ? -w : w;
-                    }
-                }
-                Gbuf[(((int64_t)al * P + b) * R + (k - klo)) * K + leaf] = acc * scale;
-            }
-            __syncthreads();
         }
     }
 }
 
-// Pass 2. tile = pair index over b1 <= b2 (row-major upper triangle).
-__global__ void k_leaf_gram(const GeomDev *__restrict__ Gd, int a0, int na, int R,
-                            const double *__restrict__ Gbuf, const int2 *__restrict__ pairs,
-                            int npairs, double *__restrict__ Dm)
+// Pass 1b. One warp per ray: lane holds frame rows lane + 32 i (i < NR) and
+// the S column masks q0 + j of the tile; h[i][j] = sum over the row's pixels
+// of (-1)^popc(mask & column) w, then a Walsh-Hadamard transform along the
+// rows (shuffles below 32 rows, registers above). Output coefficient (j, row
+// mask r) goes to Gbuf[((al * P + b) * R + kk) * KT + tile_t(cls, j, r)].
+template <class TG, int NR, int S>
+__global__ void __launch_bounds__(256)
+k_leaf_profiles(const GeomDev *__restrict__ Gd, int na, int cls, int q0, int R, int KT,
+                const int2 *__restrict__ rng, const TG *__restrict__ Fw, const signed char *__restrict__ Fc,
+                TG *__restrict__ Gbuf)
 {
     const GeomDev &g = *Gd;
-    const int P = g.P, K = g.K;
-    for (int t = blockIdx.x; t < npairs; t += gridDim.x) {
-        const int2 pr = pairs[t];
-        const int b1 = pr.x, b2 = pr.y;
-        for (int leaf0 = 0; leaf0 < K; leaf0 += blockDim.x) {
-            const int leaf = leaf0 + threadIdx.x;
-            double acc = 0.0;
-            for (int al = 0; al < na; ++al) {
-                int l1, h1, l2, h2;
-                block_ray_range(g, a0 + al, b1, l1, h1);
-                block_ray_range(g, a0 + al, b2, l2, h2);
-                h1 = min(h1, l1 + R - 1);
-                h2 = min(h2, l2 + R - 1);
-                const int lo = max(l1, l2), hi = min(h1, h2);
-                if (leaf < K)
-                    for (int k = lo; k <= hi; ++k) {
-                        const double g1 = Gbuf[(((int64_t)al * P + b1) * R + (k - l1)) * K + leaf];
-                        const double g2 = Gbuf[(((int64_t)al * P + b2) * R + (k - l2)) * K + leaf];
-                        acc = __fma_rn(g1, g2, acc);
+    const int P = g.P, B = g.B;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)na * P * R;
+    for (int64_t wid = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); wid < nwarps;
+         wid += (int64_t)gridDim.x * (blockDim.x >> 5)) {
+        const int tile = (int)(wid / R), kk = (int)(wid - (int64_t)tile * R);
+        if (kk >= rng[tile].y) continue;                              // warp-uniform
+        const int64_t fo = ((int64_t)tile * R + kk) * B;
+        TG h[NR][S];
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            const int row = lane + 32 * i;
+            TG w0 = TG(0), w1 = TG(0);
+            int c0 = -1, c1 = -1;
+            if (row < B) {
+                w0 = Fw[(fo + row) * 2]; w1 = Fw[(fo + row) * 2 + 1];
+                c0 = Fc[(fo + row) * 2]; c1 = Fc[(fo + row) * 2 + 1];
+            }
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+                const int mask = q0 + j;
+                TG v = TG(0);
+                if (c0 >= 0) v += (__popc(mask & c0) & 1) ? -w0 : w0;
+                if (c1 >= 0) v += (__popc(mask & c1) & 1) ? -w1 : w1;
+                h[i][j] = v;
+            }
+        }
+        // butterflies across lanes (row distance < 32)
+        for (int half = 1; half < 32 && half < B; half <<= 1) {
+            const bool upper = lane & half;
+#pragma unroll
+            for (int i = 0; i < NR; ++i)
+#pragma unroll
+                for (int j = 0; j < S; ++j) {
+                    const TG o = __shfl_xor_sync(0xffffffffu, h[i][j], half);
+                    h[i][j] = upper ? o - h[i][j] : h[i][j] + o;
+                }
+        }
+        // butterflies within the lane (row distance 32 i)
+#pragma unroll
+        for (int hs = 1; hs < NR; hs <<= 1)
+#pragma unroll
+            for (int i = 0; i < NR; ++i)
+                if (!(i & hs))
+#pragma unroll
+                    for (int j = 0; j < S; ++j) {
+                        const TG u = h[i][j], v = h[i + hs][j];
+                        h[i][j] = u + v;
+                        h[i + hs][j] = u - v;
                     }
-            }
-            if (leaf < K) {
-                double *Dk = Dm + (int64_t)leaf * P * P;
-                Dk[(int64_t)b1 * P + b2] += acc;
-                if (b1 != b2) Dk[(int64_t)b2 * P + b1] += acc;
-            }
+        TG *out = Gbuf + ((int64_t)tile * R + kk) * KT;
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            const int r = lane + 32 * i;
+            if (r < B)
+#pragma unroll
+                for (int j = 0; j < S; ++j) out[tile_t(cls, j, r, S, B)] = h[i][j];
         }
     }
 }
 
-// D_k += lambda I, Cholesky D_k = L L^T in place (lower triangle, left
-// looking, FP64), pivot test, then inverse columns by two triangular solves.
-// One CTA per leaf. status[k] = 0 ok, -1 if a pivot is not positive.
+template <class TG>
+static void launch_profiles(int B, int S, const GeomDev *gd, int na, int cls, int q0, int R, int KT, int P,
+                            const int2 *rng, const TG *Fw, const signed char *Fc, TG *Gbuf, cudaStream_t st)
+{
+    const int64_t warps = (int64_t)na * P * R;
+    const int grid = (int)std::min<int64_t>((warps + 7) / 8, (int64_t)num_sms() * 16);
+    count_launches(1);
+#define WMG_PROF(NR_, S_) k_leaf_profiles<TG, NR_, S_><<<grid, 256, 0, st>>>(gd, na, cls, q0, R, KT, rng, Fw, Fc, Gbuf)
+    if (B == 128) WMG_PROF(4, 2);
+    else if (B == 64) WMG_PROF(2, 4);
+    else if (B == 32) WMG_PROF(1, 8);
+    else if (B == 16) WMG_PROF(1, 16);
+    else if (B == 8) WMG_PROF(1, 8);
+    else if (B == 4) WMG_PROF(1, 4);
+    else if (B == 2) WMG_PROF(1, 2);
+    else WMG_PROF(1, 1);
+#undef WMG_PROF
+    (void)S;
+}
+
+// Pass 2. CTA = (group of up to GB blocks along the rays' direction -- a
+// column of blocks for class 0, a row for class 1 -- and a sub-tile of 32
+// coefficients, one per lane). The members' coefficients of the angle are
+// staged in shared memory; warps take the partner blocks b2 in turn, load a
+// partner's coefficients once per ray and use them for every member b1 <= b2
+// whose ray range covers that ray. Dacc[(b1 * P + b2) * K + c] += the pair's
+// sum over shared rays (c = HY * B + HX). Row b1 of Dacc belongs to b1's
+// group only, so no two threads of a launch write the same entry.
+constexpr int kPairGroup = 4;
+
+template <class TG>
+__global__ void __launch_bounds__(256)
+k_leaf_pairs(const GeomDev *__restrict__ Gd, const int2 *__restrict__ rng, int na, int cls, int q0, int S,
+             int R, int KT, const TG *__restrict__ Gbuf, double *__restrict__ Dacc)
+{
+    extern __shared__ unsigned char smem_raw[];
+    TG *g1 = reinterpret_cast<TG *>(smem_raw);                     // GB x R x 32
+    const GeomDev &g = *Gd;
+    const int P = g.P, B = g.B, K = g.K, nc = g.nc;
+    const int ngq = (nc + kPairGroup - 1) / kPairGroup;
+    const int gq = blockIdx.x / nc, gl = blockIdx.x - gq * nc;       // group along / across
+    const int t0 = blockIdx.y * 32;
+    const int lane = threadIdx.x & 31;
+    // partner b2 = bmin + warp + i * nw: blockIdx.z splits the partners
+    // between CTAs (disjoint Dacc entries)
+    const int warp = (threadIdx.x >> 5) * gridDim.z + blockIdx.z, nw = (blockDim.x >> 5) * gridDim.z;
+    if (gq >= ngq) return;
+    int mb[kPairGroup];
+    int nm = 0;
+    for (int i = 0; i < kPairGroup; ++i) {
+        const int along = gq * kPairGroup + i;
+        mb[i] = -1;
+        if (along < nc) { mb[i] = cls == 0 ? along * nc + gl : gl * nc + along; ++nm; }
+    }
+    const bool have = t0 + lane < KT;
+    const int c = have ? tile_c(cls, t0 + lane, q0, S, B) : 0;
+    const int bmin = mb[0];                                          // members ascend in index
+    for (int al = 0; al < na; ++al) {
+        int2 r1[kPairGroup];
+#pragma unroll
+        for (int i = 0; i < kPairGroup; ++i) r1[i] = mb[i] >= 0 ? rng[al * P + mb[i]] : make_int2(0, 0);
+        for (int i = 0; i < nm; ++i)
+            for (int e = threadIdx.x; e < r1[i].y * 32; e += blockDim.x) {
+                const int kk = e >> 5, tt = e & 31;
+                g1[(i * R + kk) * 32 + tt] =
+                    t0 + tt < KT ? Gbuf[(((int64_t)al * P + mb[i]) * R + kk) * KT + t0 + tt] : TG(0);
+            }
+        __syncthreads();
+        for (int b2 = bmin + warp; b2 < P; b2 += nw) {
+            const int2 r2 = rng[al * P + b2];
+            int lo[kPairGroup], hi[kPairGroup];
+            int ulo = INT_MAX, uhi = INT_MIN;
+#pragma unroll
+            for (int i = 0; i < kPairGroup; ++i) {
+                lo[i] = max(r1[i].x, r2.x);
+                hi[i] = min(r1[i].x + r1[i].y, r2.x + r2.y);
+                if (mb[i] < 0 || mb[i] > b2 || lo[i] >= hi[i]) { lo[i] = 0; hi[i] = 0; continue; }
+                ulo = min(ulo, lo[i]);
+                uhi = max(uhi, hi[i]);
+            }
+            if (ulo >= uhi) continue;
+            // the D values are read before the sums so that their latency
+            // overlaps the arithmetic
+            double dold[kPairGroup];
+#pragma unroll
+            for (int i = 0; i < kPairGroup; ++i)
+                dold[i] = (have && hi[i] > lo[i]) ? Dacc[((int64_t)mb[i] * P + b2) * K + c] : 0.0;
+            TG acc[kPairGroup];
+#pragma unroll
+            for (int i = 0; i < kPairGroup; ++i) acc[i] = TG(0);
+            const TG *g2 = Gbuf + (((int64_t)al * P + b2) * R + (ulo - r2.x)) * KT + t0 + lane;
+            // eight rays per step: the partner's loads are issued together
+            for (int k = ulo; k < uhi; k += 8) {
+                TG v2[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v2[u] = (have && k + u < uhi) ? g2[(int64_t)(k + u - ulo) * KT] : TG(0);
+#pragma unroll
+                for (int i = 0; i < kPairGroup; ++i)
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int kk = k + u;
+                        if (kk >= lo[i] && kk < hi[i])
+                            acc[i] = fma_t(g1[(i * R + kk - r1[i].x) * 32 + lane], v2[u], acc[i]);
+                    }
+            }
+            if (have)
+#pragma unroll
+                for (int i = 0; i < kPairGroup; ++i)
+                    if (hi[i] > lo[i]) Dacc[((int64_t)mb[i] * P + b2) * K + c] = dold[i] + (double)acc[i];
+        }
+        __syncthreads();
+    }
+}
+
+// D_k + lambda I gathered from Dacc (upper triangle, layout [b1][b2][c]),
+// Cholesky D_k = L L^T (left looking, FP64) in a per-CTA work matrix M
+// stored by columns of L (M[q * P + i] = L[i][q]: thread i's loads are
+// consecutive across threads), pivot test, then the inverse columns by two
+// triangular solves (thread c owns column c of Y; the factor entries it
+// reads are the same for every thread). One CTA per leaf. status[k] = 0 ok,
+// -1 if a pivot is not positive.
 template <class T>
 __global__ void __launch_bounds__(256)
-k_leaf_invert(const GeomDev *__restrict__ Gd, double *__restrict__ Dm, double *__restrict__ Ywork,
-              T *__restrict__ inv, int *__restrict__ status)
+k_leaf_invert(const GeomDev *__restrict__ Gd, const double *__restrict__ Dacc, double *__restrict__ Mwork,
+              double *__restrict__ Ywork, T *__restrict__ inv, int *__restrict__ status)
 {
     __shared__ double colbuf[256];
     __shared__ int bad;
     const GeomDev &g = *Gd;
-    const int P = g.P;
-    for (int k = blockIdx.x; k < g.K; k += gridDim.x) {
-        double *A = Dm + (int64_t)k * P * P;
+    const int P = g.P, K = g.K, L = g.L, B = g.B;
+    for (int k = blockIdx.x; k < K; k += gridDim.x) {
+        double *M = Mwork + (int64_t)blockIdx.x * P * P;
         double *Y = Ywork + (int64_t)blockIdx.x * P * P;
+        const int HY = bitrev_L(unspread_bits(k >> 1, L), L), HX = bitrev_L(unspread_bits(k, L), L);
+        const int c = HY * B + HX;
         if (threadIdx.x == 0) bad = 0;
-        for (int i = threadIdx.x; i < P; i += blockDim.x) A[(int64_t)i * P + i] += g.lambda;
+        for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
+            const int q = e / P, i = e - q * P;
+            const int lo = min(i, q), hi = max(i, q);
+            M[e] = Dacc[((int64_t)lo * P + hi) * K + c] + (i == q ? g.lambda : 0.0);
+        }
         __syncthreads();
-        // left-looking Cholesky: column j = (A[j:, j] - L[j:, :j] L[j, :j]^T) / sqrt(pivot)
+        // column j: L[i][j] = (A[i][j] - sum_q L[i][q] L[j][q]) / sqrt(pivot), i >= j
         for (int j = 0; j < P; ++j) {
             for (int i = j + threadIdx.x; i < P; i += blockDim.x) {
-                double v = A[(int64_t)i * P + j];
-                for (int q = 0; q < j; ++q) v -= A[(int64_t)i * P + q] * A[(int64_t)j * P + q];
+                double v = M[(int64_t)j * P + i];
+                for (int q = 0; q < j; ++q) v -= M[(int64_t)q * P + i] * M[(int64_t)q * P + j];
                 colbuf[i] = v;
             }
             __syncthreads();
@@ -175,75 +356,112 @@ k_leaf_invert(const GeomDev *__restrict__ Gd, double *__restrict__ Dm, double *_
             }
             const double d = piv > 0.0 ? sqrt(piv) : 1.0;
             for (int i = j + threadIdx.x; i < P; i += blockDim.x)
-                A[(int64_t)i * P + j] = (i == j) ? d : colbuf[i] / d;
+                M[(int64_t)j * P + i] = (i == j) ? d : colbuf[i] / d;
             __syncthreads();
         }
         if (threadIdx.x == 0) status[k] = bad ? -1 : 0;
-        // inverse: column c solves L y = e_c, then L^T x = y. Thread c owns
-        // column c of the work matrix (coalesced across threads); the factor
-        // entries are the same address for every thread (broadcast).
-        const int c = threadIdx.x;
-        if (c < P) {
-            for (int i = 0; i < P; ++i) {
-                double y = (i == c) ? 1.0 : 0.0;
-                for (int q = 0; q < i; ++q) y -= A[(int64_t)i * P + q] * Y[(int64_t)q * P + c];
-                Y[(int64_t)i * P + c] = y / A[(int64_t)i * P + i];
+        const int col = threadIdx.x;
+        if (col < P) {
+            for (int i = 0; i < P; ++i) {            // L y = e_col
+                double y = (i == col) ? 1.0 : 0.0;
+                for (int q = 0; q < i; ++q) y -= M[(int64_t)q * P + i] * Y[(int64_t)q * P + col];
+                Y[(int64_t)i * P + col] = y / M[(int64_t)i * P + i];
             }
-            for (int i = P - 1; i >= 0; --i) {
-                double x = Y[(int64_t)i * P + c];
-                for (int q = i + 1; q < P; ++q) x -= A[(int64_t)q * P + i] * Y[(int64_t)q * P + c];
-                x /= A[(int64_t)i * P + i];
-                Y[(int64_t)i * P + c] = x;
+            for (int i = P - 1; i >= 0; --i) {       // L^T x = y
+                double x = Y[(int64_t)i * P + col];
+                for (int q = i + 1; q < P; ++q) x -= M[(int64_t)i * P + q] * Y[(int64_t)q * P + col];
+                x /= M[(int64_t)i * P + i];
+                Y[(int64_t)i * P + col] = x;
             }
-            for (int i = 0; i < P; ++i) inv[(int64_t)k * P * P + (int64_t)i * P + c] = (T)Y[(int64_t)i * P + c];
+            for (int i = 0; i < P; ++i) inv[(int64_t)k * P * P + (int64_t)i * P + col] = (T)Y[(int64_t)i * P + col];
         }
         __syncthreads();
     }
 }
 
 // Host driver: assembles, factorises and inverts every leaf of one geometry.
-// `leafinv_out` receives K*P*P values of type T. Returns WMG_OK or an error.
-int32_t build_leaf_inverses(const GeomDev &gh, const GeomDev *gd, double *leafinv_out, cudaStream_t st)
+// `leafinv_out` receives K*P*P doubles. `fp32`: profiles and pair sums in
+// FP32 (F32 plans), else FP64. Returns WMG_OK or an error.
+template <class TG>
+static int32_t assemble(const GeomDev &gh, const GeomDev *gd, double *Dacc, cudaStream_t st)
 {
-    const int P = gh.P, K = gh.K;
+    const int P = gh.P, K = gh.K, B = gh.B;
     const int R = (int)floor(gh.B * 1.4142135623730951 / gh.dt) + 3;
-    // angle chunk sized for a ~256 MB coefficient buffer
-    const double per_angle = (double)P * R * K * sizeof(double);
-    int chunk = (int)fmax(1.0, fmin((double)gh.m, 256.0 * 1024 * 1024 / per_angle));
-    double *Gbuf = nullptr, *Dm = nullptr, *Y = nullptr;
-    int *status = nullptr;
-    int2 *pairs = nullptr;
-    const int npairs = P * (P + 1) / 2;
-    std::vector<int2> hp;
-    hp.reserve(npairs);
-    for (int b1 = 0; b1 < P; ++b1)
-        for (int b2 = b1; b2 < P; ++b2) hp.push_back(make_int2(b1, b2));
-    const int inv_ctas = std::min(K, num_sms() * 2);
-    int32_t rc = WMG_OK;
-    auto cleanup = [&]() {
-        cudaFree(Gbuf); cudaFree(Dm); cudaFree(Y); cudaFree(status); cudaFree(pairs);
-    };
-    if (cudaMalloc(&Gbuf, (size_t)chunk * P * R * K * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&Dm, (size_t)K * P * P * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&Y, (size_t)inv_ctas * P * P * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&status, (size_t)K * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&pairs, (size_t)npairs * sizeof(int2)) != cudaSuccess) {
+    const int KT = std::min(K, 256), S = KT / B;
+    // angle classes from the FP64 table (|cos| >= |sin|: class 0)
+    std::vector<double2> cs(gh.m);
+    WMG_CUDA(cudaMemcpyAsync(cs.data(), gh.cs64, gh.m * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    WMG_CUDA(cudaStreamSynchronize(st));
+    std::vector<int> lists[2];
+    for (int a = 0; a < gh.m; ++a) lists[std::fabs(cs[a].x) >= std::fabs(cs[a].y) ? 0 : 1].push_back(a);
+    // angle chunk: about 96 MB of profiles (L2-sized); the chunk's
+    // footprints are computed once and serve every leaf tile
+    const double per_angle = (double)P * R * KT * sizeof(TG);
+    const int chunk = (int)std::max(1.0, std::min((double)gh.m, 96.0 * 1024 * 1024 / per_angle));
+    TG *Gbuf = nullptr, *Fw = nullptr;
+    signed char *Fc = nullptr;
+    int2 *rng = nullptr;
+    int *dlist = nullptr;
+    auto cleanup = [&]() { cudaFree(Gbuf); cudaFree(Fw); cudaFree(Fc); cudaFree(rng); cudaFree(dlist); };
+    const size_t nfoot = (size_t)chunk * P * R * B * 2;
+    if (cudaMalloc(&Gbuf, (size_t)chunk * P * R * KT * sizeof(TG)) != cudaSuccess ||
+        cudaMalloc(&Fw, nfoot * sizeof(TG)) != cudaSuccess || cudaMalloc(&Fc, nfoot) != cudaSuccess ||
+        cudaMalloc(&rng, (size_t)chunk * P * sizeof(int2)) != cudaSuccess ||
+        cudaMalloc(&dlist, (size_t)gh.m * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         cleanup();
         return fail(WMG_ERR_OOM, "leaf setup: device allocation failed");
     }
-    cudaMemcpyAsync(pairs, hp.data(), (size_t)npairs * sizeof(int2), cudaMemcpyHostToDevice, st);
-    cudaMemsetAsync(Dm, 0, (size_t)K * P * P * sizeof(double), st);
-    const int gram_threads = std::min(256, std::max(32, ((K + 31) / 32) * 32));
-    for (int a0 = 0; a0 < gh.m; a0 += chunk) {
-        const int na = std::min(chunk, gh.m - a0);
-        count_launches(2);
-        k_leaf_coeffs<<<std::min(na * P, num_sms() * 8), 256, 0, st>>>(gd, a0, na, R, Gbuf);
-        k_leaf_gram<<<std::min(npairs, num_sms() * 16), gram_threads, 0, st>>>(gd, a0, na, R, Gbuf,
-                                                                               pairs, npairs, Dm);
+    const size_t sm2 = (size_t)kPairGroup * R * 32 * sizeof(TG);
+    const int ngq = (gh.nc + kPairGroup - 1) / kPairGroup;
+    if (sm2 > 48 * 1024)
+        cudaFuncSetAttribute(k_leaf_pairs<TG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+    int off = 0;
+    for (int cls = 0; cls < 2; ++cls) {
+        const std::vector<int> &lst = lists[cls];
+        if (lst.empty()) continue;
+        WMG_CUDA(cudaMemcpyAsync(dlist + off, lst.data(), lst.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        for (int c0 = 0; c0 < (int)lst.size(); c0 += chunk) {
+            const int na = std::min(chunk, (int)lst.size() - c0);
+            count_launches(1);
+            k_leaf_footprint<TG><<<std::min(na * P, num_sms() * 16), 256, 0, st>>>(gd, dlist + off + c0, na, R,
+                                                                                   rng, Fw, Fc);
+            for (int q0 = 0; q0 < B; q0 += S) {
+                launch_profiles<TG>(B, S, gd, na, cls, q0, R, KT, P, rng, Fw, Fc, Gbuf, st);
+                count_launches(1);
+                k_leaf_pairs<TG><<<dim3(ngq * gh.nc, (KT + 31) / 32, 1), 256, sm2, st>>>(gd, rng, na, cls, q0, S,
+                                                                                         R, KT, Gbuf, Dacc);
+            }
+        }
+        off += (int)lst.size();
     }
+    cudaError_t e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) return fail(WMG_ERR_CUDA, std::string("leaf setup: ") + cudaGetErrorString(e));
+    return WMG_OK;
+}
+
+int32_t build_leaf_inverses(const GeomDev &gh, const GeomDev *gd, double *leafinv_out, bool fp32,
+                            cudaStream_t st)
+{
+    const int P = gh.P, K = gh.K;
+    const int inv_ctas = std::min(K, num_sms() * 4);
+    double *Dacc = nullptr, *A = nullptr, *Y = nullptr;
+    int *status = nullptr;
+    auto cleanup = [&]() { cudaFree(Dacc); cudaFree(A); cudaFree(Y); cudaFree(status); };
+    if (cudaMalloc(&Dacc, (size_t)K * P * P * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&A, (size_t)inv_ctas * P * P * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&Y, (size_t)inv_ctas * P * P * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&status, (size_t)K * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return fail(WMG_ERR_OOM, "leaf setup: device allocation failed");
+    }
+    cudaMemsetAsync(Dacc, 0, (size_t)K * P * P * sizeof(double), st);
+    int32_t rc = fp32 ? assemble<float>(gh, gd, Dacc, st) : assemble<double>(gh, gd, Dacc, st);
+    if (rc) { cleanup(); return rc; }
     count_launches(1);
-    k_leaf_invert<double><<<inv_ctas, 256, 0, st>>>(gd, Dm, Y, leafinv_out, status);
+    k_leaf_invert<double><<<inv_ctas, 256, 0, st>>>(gd, Dacc, A, Y, leafinv_out, status);
     std::vector<int> hs(K);
     cudaMemcpyAsync(hs.data(), status, (size_t)K * sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);

@@ -194,7 +194,8 @@ void launch_leaf_apply(const GeomDev *G, const ProbDev *P, const int4 *tiles, in
                        const double *C, double *E, int accumulate, const double *S, cudaStream_t st);
 
 // Setup (setup.cu).
-int32_t build_leaf_inverses(const GeomDev &g_host, const GeomDev *g_dev, double *leafinv_out,
+// fp32: profiles and pair sums in FP32 (FP64 accumulation over angles).
+int32_t build_leaf_inverses(const GeomDev &g_host, const GeomDev *g_dev, double *leafinv_out, bool fp32,
                             cudaStream_t st);
 
 // Elementwise / reduction kernels (krylov.cu), all FP64 Krylov state.

@@ -41,6 +41,10 @@ RTOL = 1e-4
 MAX_ITER = 200
 RESTART = 20
 LEVELS, NU1, NU2, HYB = 5, 1, 1, 1
+# serving stream: Tikhonov parameter relative to m / n, the scale of the
+# spectral radius of W^T W in unit-square units (noisy, often underdetermined
+# requests; regularised normal equations as in the paper's noisy experiments)
+SERVING_EPS = 1e-3
 
 
 def parse():
@@ -51,6 +55,13 @@ def parse():
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the serving leg (request stream through the continuous-batching server)")
+    ap.add_argument("--serving-requests", type=int, default=48)
+    ap.add_argument("--serving-rate", type=float, default=6.0, help="mean arrivals per second (Poisson)")
+    ap.add_argument("--serving-max-n", type=int, default=512,
+                    help="largest image side of the serving stream (sizes 128 .. 2048 in the full stream)")
+    ap.add_argument("--serving-only", action="store_true", help="run the serving leg alone and print its JSON")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run 3 projector and 3 backprojector launches on a batch of 16 images of the "
                          "workload geometry (FP32) and exit: the small case for ncu captures")
@@ -297,9 +308,84 @@ def run_ours(args, rank, world, local):
             "roofline": roofline,
             "cpu_baseline": cpu,
         }
+        if not args.no_serving and world == 1:
+            try:
+                line["serving"] = serving_leg(args, dev)
+            except Exception as e:
+                line["serving"] = {"unavailable": f"{type(e).__name__}: {e}"}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# Serving leg: a seeded Poisson stream of reconstruction requests of mixed
+# image sizes and angle counts through the continuous-batching server
+# ---------------------------------------------------------------------------
+def serving_leg(args, dev) -> dict:
+    import torch
+    import paper_1310_0956_gb300 as wmg
+
+    wl, gaps = S.workload_serving(max(2000, args.serving_requests))
+    picked = [(p, g) for p, g in zip(wl.problems, gaps) if p.n <= args.serving_max_n][:args.serving_requests]
+    probs = [p for p, _ in picked]
+    arrivals = np.cumsum([g for _, g in picked]) / args.serving_rate
+    arrivals -= arrivals[0]
+    # sinograms b = W x + 1% noise (FP64 library projector), resident on the device
+    bs = []
+    for p in probs:
+        op = wmg.Plan(p.n, p.m, p.D, levels=0, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F64)
+        b64 = op.project(torch.tensor(p.image().reshape(-1), dtype=torch.float64, device=dev))
+        b64 = b64 + p.noise * b64.abs().max() * torch.tensor(p.noise_unit(), dtype=torch.float64, device=dev)
+        bs.append(b64.to(torch.float32).contiguous())
+        op.close()
+    torch.cuda.synchronize()
+    srv = wmg.Server(64 << 30, max_slots=64, state_bytes=32 << 30, sino_ratio=4.0, preconditioned=True,
+                     max_iter=MAX_ITER, rtol=RTOL, restart=RESTART, levels=1, nu1=NU1, nu2=NU2, hybrid_depth=HYB,
+                     cycle=wmg.CYCLE_HYBRID, precision=wmg.PREC_F32)
+    launches0 = wmg.wmg_launch_count(False)
+    t0 = time.perf_counter()
+    nxt, live, done = 0, {}, {}
+    peak = 0
+    while len(done) < len(probs):
+        now = time.perf_counter() - t0
+        while nxt < len(probs) and arrivals[nxt] <= now:
+            p = probs[nxt]
+            t = srv.submit({"n": p.n, "m": p.m, "D": p.D, "levels": S.levels_for(p.n),
+                            "lam": SERVING_EPS * p.m / p.n}, bs[nxt])
+            live[t] = nxt
+            nxt += 1
+        if live:
+            srv.step()
+            peak = max(peak, srv.stats()["running"])
+            now = time.perf_counter() - t0
+            for t in list(live):
+                r = srv.poll(t)
+                if r is not None:
+                    done[live.pop(t)] = (now, r[1])
+        elif nxt < len(probs):
+            time.sleep(max(0.0, min(0.01, arrivals[nxt] - now)))
+    wall = max(d[0] for d in done.values())
+    st = srv.stats()
+    srv.close()
+    lat = np.array([(done[i][0] - arrivals[i]) * 1e3 for i in range(len(probs))])
+    infos = [done[i][1] for i in range(len(probs))]
+    sizes = sorted({p.n for p in probs})
+    return {
+        "workload": f"poisson_{len(probs)}req_rate{args.serving_rate:g}_n" + "-".join(map(str, sizes)) +
+                    "_m90-720",
+        "requests": len(probs), "recon_per_s": len(probs) / wall, "wall_s": wall,
+        "p50_latency_ms": float(np.percentile(lat, 50)), "p99_latency_ms": float(np.percentile(lat, 99)),
+        "mean_latency_ms": float(lat.mean()),
+        "latency_from": "scheduled arrival to retirement seen by the host",
+        "all_converged": bool(all(i[1] == 0 for i in infos)),
+        "iters_mean": float(np.mean([i[0] for i in infos])),
+        "max_running": peak, "ticks": st["ticks"], "geometry_setups": st["geometry_setups"],
+        "gpu_launches": wmg.wmg_launch_count(False) - launches0,
+        "solver": "WMG-GMRES(20) hybrid depth 1, FP32 operator / FP64 Krylov, rtol 1e-4",
+        "lambda": f"Tikhonov (W^T W + lambda) x = W^T b, lambda = {SERVING_EPS:g} * m / n",
+        "note": "geometry setups (leaf Gram + inverses) run on a worker stream, overlapping the steps",
+    }
 
 
 def load_peaks():
@@ -355,6 +441,11 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.serving_only:
+        import torch
+        torch.cuda.set_device(local)
+        print(json.dumps(serving_leg(args, torch.device("cuda", local))), flush=True)
         return
     run_ours(args, rank, world, local)
 

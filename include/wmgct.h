@@ -224,15 +224,21 @@ int32_t wmg_batch_solve(wmg_batch *batch, int32_t solver, int32_t preconditioned
  * creation as the state pools, sized for sino_ratio (0: 4) sinogram elements
  * per image element; the rest holds geometry setups (trig tables, D~^-1,
  * SIRT scalings, leaf inverses K * P^2 doubles), cached by geometry and
- * evicted least-recently-used when no admitted request uses them. Footprint
- * of a request: (restart + 11) * 8 + 2 s bytes per pixel and 2 s bytes per ray
- * (s = 8 for F64, 4 for F32), more with hybrid depth h >= 1 (band images,
- * 3^(h-1) (2 s + 8) per pixel and 3^(h-1) s per ray) and the symmetric cycle
- * (24 h per pixel), plus its geometry's setup when not cached. The transient
- * scratch of a geometry setup (at most about 256 MiB) is not counted.
+ * evicted least-recently-used when no admitted or queued request uses them.
+ * Footprint of a request: (restart + 11) * 8 + 2 s bytes per pixel and 2 s
+ * bytes per ray (s = 8 for F64, 4 for F32), more with hybrid depth h >= 1
+ * (band images, 3^(h-1) (2 s + 8) per pixel and 3^(h-1) s per ray) and the
+ * symmetric cycle (24 h per pixel); plus, when its geometry is not cached,
+ * the geometry's setup and, while that setup runs, its scratch
+ * (wmg_server_footprint gives all three).
  *
- * Streams: all work is on the stream given at creation; wmg_server_step
- * synchronises it. Not thread-safe. */
+ * Geometry setups run on a worker thread with a stream of its own, so that
+ * they overlap the steps of the requests already admitted; a request waits
+ * in the queue until its geometry is ready (requests behind it whose
+ * geometries are ready may pass it), at most two setups run at a time.
+ *
+ * Streams: all request work is on the stream given at creation;
+ * wmg_server_step synchronises it. Not thread-safe. */
 #define WMG_REQ_QUEUED   0
 #define WMG_REQ_RUNNING  1
 #define WMG_REQ_DONE     2
@@ -279,10 +285,10 @@ int32_t wmg_server_destroy(wmg_server *srv);
 int32_t wmg_server_submit(wmg_server *srv, const wmg_geom *g, const wmg_opts *o, const void *b, void *x,
                           uint64_t *ticket);
 
-/* One tick: admit, run one GMRES step for every admitted request, retire the
- * finished ones. *pending (may be NULL) = requests running + queued after
- * the tick. A geometry seen for the first time is set up inside the tick
- * that admits its first request. Synchronising. */
+/* One tick: install finished geometry setups, admit, run one GMRES step for
+ * every admitted request, retire the finished ones. *pending (may be NULL) =
+ * requests running + queued after the tick. When nothing is admitted and
+ * setups run, waits about 0.2 ms. Synchronising. */
 int32_t wmg_server_step(wmg_server *srv, int32_t *pending);
 
 /* State of a request (WMG_REQ_QUEUED / RUNNING / DONE). When DONE: *info
@@ -295,6 +301,13 @@ int32_t wmg_server_poll(wmg_server *srv, uint64_t ticket, int32_t *state, wmg_so
 
 /* Counters and memory use. Host-only. */
 int32_t wmg_server_stats(const wmg_server *srv, wmg_server_counters *out);
+
+/* The footprint the server charges a request of geometry g, options o (NULL:
+ * the server's): *state = bytes of its state in the pools, *geometry = its
+ * geometry's setup kept while cached, *setup = bytes the setup holds only
+ * while it runs (any pointer may be NULL). Host-only. */
+int32_t wmg_server_footprint(const wmg_server *srv, const wmg_geom *g, const wmg_opts *o, int64_t *state,
+                             int64_t *geometry, int64_t *setup);
 
 /* Number of nonzero intersection lengths of the plan's W (rays x pixels with
  * a nonzero weight), counted on the device at plan creation. */

@@ -111,6 +111,8 @@ _SIGNATURES = {
     "wmg_server_poll": (_i32, [_vp, C.c_uint64, C.POINTER(_i32), C.POINTER(wmg_solve_info), C.POINTER(_dbl),
                                C.POINTER(_dbl)]),
     "wmg_server_stats": (_i32, [_vp, C.POINTER(wmg_server_counters)]),
+    "wmg_server_footprint": (_i32, [_vp, C.POINTER(wmg_geom), C.POINTER(wmg_opts), C.POINTER(_i64),
+                                    C.POINTER(_i64), C.POINTER(_i64)]),
 }
 
 
@@ -286,6 +288,14 @@ def wmg_server_stats(srv) -> wmg_server_counters:
     out = wmg_server_counters()
     _check(lib().wmg_server_stats(srv, C.byref(out)))
     return out
+
+
+def wmg_server_footprint(srv, geom: wmg_geom, opts=None) -> tuple[int, int, int]:
+    """(state bytes, cached geometry bytes, setup scratch bytes) of a request."""
+    a, b, c = _i64(), _i64(), _i64()
+    _check(lib().wmg_server_footprint(srv, C.byref(geom), C.byref(opts) if opts is not None else None,
+                                      C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
 
 
 # ---- torch convenience wrapper ---------------------------------------------
@@ -531,6 +541,13 @@ class Server:
             import numpy as np
             res = res + (np.frombuffer(hist, dtype=np.float64)[:info.iters + 1].copy(),)
         return res
+
+    def footprint(self, req) -> tuple[int, int, int]:
+        d = self.defaults
+        geom = wmg_geom(req["n"], req["m"], None, req["D"], req.get("det_spacing", 1.0), req.get("det_offset", 0.0))
+        opts = wmg_opts(req.get("levels", d["levels"]), d["nu1"], d["nu2"], d["omega"], req.get("lam", d["lam"]),
+                        d["hybrid_depth"], d["cycle"], d["precision"])
+        return wmg_server_footprint(self.handle, geom, opts)
 
     def stats(self) -> dict:
         st = wmg_server_stats(self.handle)

@@ -19,9 +19,12 @@
 // fixed order, so a request's arithmetic does not depend on what else runs:
 // it gives the same x alone, in any mix, and through wmg_solve.
 #include <chrono>
+#include <condition_variable>
 #include <cstring>
 #include <deque>
 #include <map>
+#include <mutex>
+#include <thread>
 
 #include "engine.cuh"
 
@@ -185,6 +188,90 @@ struct GeoEntry {
     int64_t bytes = 0;
 };
 
+// A geometry setup run by the worker thread on its own stream.
+struct SetupJob {
+    std::string key;
+    wmg_geom g{};
+    std::vector<double> angles;
+    wmg_opts o{};
+    int64_t bytes = 0, transient = 0;
+    std::unique_ptr<Geo> geo;
+    int32_t rc = WMG_OK;
+};
+
+// Geometry setups (leaf Gram assembly and inverses) run here, overlapping the
+// ticks of the requests already admitted. Each setup builds a one-geometry
+// plan on the worker's stream and hands its geometry over to the server.
+struct SetupWorker {
+    std::thread th;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<std::shared_ptr<SetupJob>> todo;
+    std::vector<std::shared_ptr<SetupJob>> done;
+    bool stop = false;
+    cudaStream_t st = nullptr;
+    int device = 0;
+
+    void start()
+    {
+        cudaGetDevice(&device);
+        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        th = std::thread([this] { run(); });
+    }
+    void run()
+    {
+        cudaSetDevice(device);
+        for (;;) {
+            std::shared_ptr<SetupJob> job;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv.wait(lk, [&] { return stop || !todo.empty(); });
+                if (stop) return;
+                job = todo.front();
+                todo.pop_front();
+            }
+            wmg_geom g = job->g;
+            g.angles = job->angles.empty() ? nullptr : job->angles.data();
+            wmg_plan *tmp = nullptr;
+            job->rc = wmg_plan_create(&g, &job->o, st, &tmp);
+            if (job->rc == WMG_OK) {
+                job->geo = std::move(tmp->geos[0]);
+                cudaStreamSynchronize(st);
+                delete tmp;
+            }
+            std::lock_guard<std::mutex> lk(mu);
+            done.push_back(job);
+        }
+    }
+    void submit(std::shared_ptr<SetupJob> job)
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        todo.push_back(std::move(job));
+        cv.notify_one();
+    }
+    std::vector<std::shared_ptr<SetupJob>> take_done()
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        std::vector<std::shared_ptr<SetupJob>> out;
+        out.swap(done);
+        return out;
+    }
+    void shutdown()
+    {
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            stop = true;
+            cv.notify_all();
+        }
+        if (th.joinable()) th.join();
+        if (st) cudaStreamSynchronize(st);
+        if (st) cudaStreamDestroy(st);
+        st = nullptr;
+    }
+};
+
+constexpr int kMaxSetupsInFlight = 2;
+
 }  // namespace
 
 struct wmg_server {
@@ -205,10 +292,14 @@ struct wmg_server {
     uint64_t next_id = 1, use_clock = 0;
     std::vector<GeoEntry> geo_entries;   // by geometry index of the plan
     std::map<std::string, int> geo_by_key;
+    std::map<std::string, std::shared_ptr<SetupJob>> in_setup;   // running or waiting setups
+    std::map<std::string, int32_t> failed;                       // geometries whose setup failed
+    SetupWorker worker;
     bool dirty = false;
     wmg_server_counters stats{};
     ~wmg_server()
     {
+        worker.shutdown();
         if (st) cudaStreamSynchronize(st);
         if (h_phase) cudaFreeHost(h_phase);
         if (h_jn) cudaFreeHost(h_jn);
@@ -247,6 +338,32 @@ int64_t geo_bytes(const wmg_geom &g, const wmg_opts &o, size_t esz)
     return b;
 }
 
+// Device bytes a geometry setup holds only while it runs, as allocated by
+// setup_geometry and build_leaf_inverses: the all-ones and product vectors,
+// the pair sums D (K P^2 doubles), the per-CTA Cholesky work matrices, and
+// the profile / footprint buffers of one angle chunk.
+int64_t setup_transient_bytes(const wmg_geom &g, const wmg_opts &o, size_t esz)
+{
+    const int64_t N = (int64_t)g.n * g.n, M = (int64_t)g.m * g.D;
+    int64_t b = 2 * (N + M) * (int64_t)esz + (64 << 10);
+    if (o.levels >= 1) {
+        const int L = o.levels - 1;
+        const int64_t nc = g.n >> L, P = nc * nc, K = (int64_t)1 << (2 * L), B = (int64_t)1 << L;
+        int sms = 148, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const double dt = g.det_spacing > 0 ? g.det_spacing : 1.0;
+        const int64_t R = (int64_t)std::floor((double)B * 1.4142135623730951 / dt) + 3;
+        const int64_t KT = std::min<int64_t>(K, 256);
+        const double per_angle = (double)P * R * KT * esz;
+        const int64_t chunk = (int64_t)std::max(1.0, std::min((double)g.m, 96.0 * 1024 * 1024 / per_angle));
+        b += K * P * P * 8 + 2 * std::min<int64_t>(K, 4 * sms) * P * P * 8 + K * 4;
+        b += chunk * P * R * KT * (int64_t)esz + chunk * P * R * B * 2 * ((int64_t)esz + 1) + chunk * P * 8 +
+             (int64_t)g.m * 4;
+    }
+    return b;
+}
+
 int64_t state_bytes(const wmg_server *s, int64_t N, int64_t M)
 {
     return RangeAlloc::round(N) * s->bpi + RangeAlloc::round(M) * s->bps;
@@ -259,15 +376,15 @@ int free_slot(const wmg_server *s)
     return -1;
 }
 
-// Evict unused geometries (least recently used first) until `need` more
-// bytes fit in the geometry budget.
-bool make_room(wmg_server *s, int64_t need)
+// Evict unused geometries (least recently used first; none that a queued
+// request waits for) until `need` more bytes fit in the geometry budget.
+bool make_room(wmg_server *s, int64_t need, const std::map<std::string, int> &wanted)
 {
     while (s->geo_used + need > s->geo_budget) {
         int victim = -1;
         for (int gi = 0; gi < (int)s->geo_entries.size(); ++gi) {
             const GeoEntry &e = s->geo_entries[gi];
-            if (!s->pl->geos[gi] || e.refs > 0) continue;
+            if (!s->pl->geos[gi] || e.refs > 0 || wanted.count(e.key)) continue;
             if (victim < 0 || e.last_use < s->geo_entries[victim].last_use) victim = gi;
         }
         if (victim < 0) return false;
@@ -280,45 +397,54 @@ bool make_room(wmg_server *s, int64_t need)
     return true;
 }
 
-// The geometry of request r: cached, or created and set up now.
-int32_t acquire_geometry(wmg_server *s, Request &r, int *gi_out)
+// Finished background setups: install their geometries (or record the
+// failure for the requests that wait for them).
+int32_t collect_setups(wmg_server *s)
 {
-    auto it = s->geo_by_key.find(r.key);
-    if (it != s->geo_by_key.end()) {
-        *gi_out = it->second;
-        return WMG_OK;
-    }
-    const int64_t need = geo_bytes(r.g, r.o, s->pl->esz);
-    if (!make_room(s, need)) return WMG_ERR_REJECTED;    // wait for running requests to free theirs
     wmg_plan *pl = s->pl.get();
-    int gi = -1;
-    for (int i = 0; i < (int)pl->geos.size(); ++i)
-        if (!pl->geos[i]) { gi = i; break; }
-    if (gi < 0) {
-        gi = (int)pl->geos.size();
-        pl->geos.emplace_back();
-        s->geo_entries.emplace_back();
+    bool installed = false;
+    for (auto &job : s->worker.take_done()) {
+        s->in_setup.erase(job->key);
+        s->geo_used -= job->transient;
+        if (job->rc != WMG_OK || !job->geo) {
+            s->geo_used -= job->bytes;
+            s->failed[job->key] = job->rc != WMG_OK ? job->rc : WMG_ERR_CUDA;
+            continue;
+        }
+        int gi = -1;
+        for (int i = 0; i < (int)pl->geos.size(); ++i)
+            if (!pl->geos[i]) { gi = i; break; }
+        if (gi < 0) {
+            gi = (int)pl->geos.size();
+            pl->geos.emplace_back();
+            s->geo_entries.emplace_back();
+        }
+        pl->geos[gi] = std::move(job->geo);
+        s->geo_entries[gi] = GeoEntry{job->key, 0, ++s->use_clock, job->bytes};
+        s->geo_by_key[job->key] = gi;
+        s->stats.geometry_setups++;
+        installed = true;
     }
-    pl->geos[gi] = std::make_unique<Geo>();
-    wmg_geom g = r.g;
-    g.angles = r.angles.empty() ? nullptr : r.angles.data();
-    int32_t rc = make_geo(&g, &r.o, *pl->geos[gi], s->st);
-    if (!rc) rc = upload_geoms(pl, s->st);
-    if (!rc) rc = pl->prec == WMG_PREC_F64 ? setup_geometry<double>(pl, gi, s->st)
-                                          : setup_geometry<float>(pl, gi, s->st);
-    if (rc) {
-        pl->geos[gi].reset();
-        upload_geoms(pl, s->st);
-        return rc;
-    }
-    s->geo_entries[gi].key = r.key;
-    s->geo_entries[gi].bytes = need;
-    s->geo_entries[gi].refs = 0;
-    s->geo_used += need;
-    s->geo_by_key[r.key] = gi;
-    s->stats.geometry_setups++;
-    *gi_out = gi;
+    if (installed) return upload_geoms(pl, s->st);
     return WMG_OK;
+}
+
+// Start the setup of request r's geometry on the worker if memory allows.
+bool start_setup(wmg_server *s, const Request &r, const std::map<std::string, int> &wanted)
+{
+    if ((int)s->in_setup.size() >= kMaxSetupsInFlight) return false;
+    auto job = std::make_shared<SetupJob>();
+    job->key = r.key;
+    job->g = r.g;
+    job->angles = r.angles;
+    job->o = r.o;
+    job->bytes = geo_bytes(r.g, r.o, s->pl->esz);
+    job->transient = setup_transient_bytes(r.g, r.o, s->pl->esz);
+    if (!make_room(s, job->bytes + job->transient, wanted)) return false;
+    s->geo_used += job->bytes + job->transient;
+    s->in_setup[r.key] = job;
+    s->worker.submit(job);
+    return true;
 }
 
 void finish(wmg_server *s, Request &r, int status)
@@ -329,27 +455,42 @@ void finish(wmg_server *s, Request &r, int status)
     s->stats.completed++;
 }
 
-// Admit queued requests in arrival order while a slot and memory are free.
+// Admit queued requests in arrival order while slots and memory are free. A
+// request whose geometry is not set up yet starts that setup in the
+// background (at most kMaxSetupsInFlight at a time) and waits; requests
+// behind it whose geometries are ready may pass it.
 int32_t admit(wmg_server *s)
 {
     wmg_plan *pl = s->pl.get();
+    int32_t rc = collect_setups(s);
+    if (rc) return rc;
+    std::map<std::string, int> wanted;
+    for (uint64_t id : s->queue) wanted[s->reqs[id].key]++;
+    std::deque<uint64_t> keep;
     while (!s->queue.empty()) {
-        Request &r = s->reqs[s->queue.front()];
-        const int slot = free_slot(s);
-        if (slot < 0) break;
-        int gi = -1;
-        int32_t rc = acquire_geometry(s, r, &gi);
-        if (rc == WMG_ERR_REJECTED) break;                 // geometry memory busy: wait
-        if (rc) {                                          // setup failed: the request ends with that status
-            s->queue.pop_front();
-            finish(s, r, rc);
+        const uint64_t id = s->queue.front();
+        s->queue.pop_front();
+        Request &r = s->reqs[id];
+        auto fk = s->failed.find(r.key);
+        if (fk != s->failed.end()) {                       // setup failed: the request ends with that status
+            finish(s, r, fk->second);
             continue;
         }
+        auto gk = s->geo_by_key.find(r.key);
+        const int slot = free_slot(s);
+        if (gk == s->geo_by_key.end() || slot < 0) {
+            if (gk == s->geo_by_key.end() && !s->in_setup.count(r.key)) start_setup(s, r, wanted);
+            keep.push_back(id);
+            continue;
+        }
+        const int gi = gk->second;
         const int64_t io = s->img.alloc(r.N);
-        if (io < 0) break;
-        const int64_t so = s->sino.alloc(r.M);
-        if (so < 0) { s->img.release(io, r.N); break; }
-        s->queue.pop_front();
+        const int64_t so = io < 0 ? -1 : s->sino.alloc(r.M);
+        if (so < 0) {
+            if (io >= 0) s->img.release(io, r.N);
+            keep.push_back(id);
+            continue;
+        }
         GeoEntry &e = s->geo_entries[gi];
         e.refs++;
         e.last_use = ++s->use_clock;
@@ -376,6 +517,7 @@ int32_t admit(wmg_server *s)
         k_srv_admit<<<1, 32, 0, st>>>(pl->S.as<double>(), pl->lam.as<double>(), slot, s->cfg.rtol,
                                       s->cfg.max_iter, G.g.lambda);
     }
+    s->queue.swap(keep);
     return WMG_OK;
 }
 
@@ -659,6 +801,7 @@ extern "C" int32_t wmg_server_create(const wmg_server_config *cfg, void *stream,
     int32_t rc = relayout(s.get());
     if (rc) return rc;
     WMG_CUDA(cudaStreamSynchronize(s->st));
+    s->worker.start();
     s->stats.state_bytes_capacity = Ncap * s->bpi + Mcap * s->bps;
     s->stats.geometry_bytes_capacity = s->geo_budget;
     *out = s.release();
@@ -698,7 +841,9 @@ extern "C" int32_t wmg_server_submit(wmg_server *srv, const wmg_geom *g, const w
     r.x = x;
     r.N = (int64_t)g->n * g->n;
     r.M = (int64_t)g->m * g->D;
-    const int64_t gb = srv->geo_by_key.count(r.key) ? 0 : geo_bytes(*g, opt, srv->pl->esz);
+    const int64_t gb = srv->geo_by_key.count(r.key)
+                           ? 0
+                           : geo_bytes(*g, opt, srv->pl->esz) + setup_transient_bytes(*g, opt, srv->pl->esz);
     if (RangeAlloc::round(r.N) > srv->img.cap || RangeAlloc::round(r.M) > srv->sino.cap || gb > srv->geo_budget) {
         srv->stats.rejected++;
         return fail(WMG_ERR_REJECTED, "wmg_server_submit: the request's footprint exceeds the server's budget");
@@ -718,6 +863,8 @@ extern "C" int32_t wmg_server_step(wmg_server *srv, int32_t *pending)
     if (!rc && srv->dirty) rc = relayout(srv);
     if (!rc && !srv->pl->live.empty())
         rc = srv->pl->prec == WMG_PREC_F64 ? tick<double>(srv) : tick<float>(srv);
+    else if (!rc && !srv->in_setup.empty())
+        std::this_thread::sleep_for(std::chrono::microseconds(200));   // nothing to run: let setups progress
     if (rc) return rc;
     int running = 0;
     for (int ph : srv->phase) running += ph != PH_EMPTY;
@@ -740,6 +887,20 @@ extern "C" int32_t wmg_server_poll(wmg_server *srv, uint64_t ticket, int32_t *st
     if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r.t_done - r.t_submit).count();
     if (res_hist && !r.hist.empty()) std::memcpy(res_hist, r.hist.data(), r.hist.size() * sizeof(double));
     srv->reqs.erase(it);
+    return WMG_OK;
+}
+
+extern "C" int32_t wmg_server_footprint(const wmg_server *srv, const wmg_geom *g, const wmg_opts *o,
+                                        int64_t *state, int64_t *geometry, int64_t *setup)
+{
+    if (!srv || !g) return fail(WMG_ERR_INVALID_ARG, "wmg_server_footprint: bad arguments");
+    wmg_opts opt = o ? *o : srv->cfg.opts;
+    int32_t rc = validate(g, &opt);
+    if (rc) return rc;
+    const int64_t N = (int64_t)g->n * g->n, M = (int64_t)g->m * g->D;
+    if (state) *state = state_bytes(srv, N, M);
+    if (geometry) *geometry = geo_bytes(*g, opt, srv->pl->esz);
+    if (setup) *setup = setup_transient_bytes(*g, opt, srv->pl->esz);
     return WMG_OK;
 }
 

@@ -154,18 +154,36 @@ def test_admission_by_footprint_and_rejection():
 
 
 def test_geometry_eviction():
-    # geometry budget for one set-up geometry at a time: requests of two
-    # geometries alternate, so each admission waits for the other geometry's
-    # requests to retire and evicts its setup
-    reqs = [REQUESTS[0], REQUESTS[3], REQUESTS[0], REQUESTS[3]]
+    # a geometry budget that fits any one geometry's setup but not the three
+    # geometries of the stream cached together with a setup: a setup has to
+    # evict an unused cached geometry; results must not change
+    reqs = [REQUESTS[0], REQUESTS[3], REQUESTS[4], REQUESTS[0], REQUESTS[3]]
     data = sinograms(reqs, torch.float64)
+    probe = make_server(wmg.PREC_F64)
+    fps = [probe.footprint(p)[1:] for p in (REQUESTS[0], REQUESTS[3], REQUESTS[4])]
+    probe.close()
+    gbud = max(g + t for g, t in fps) + 4096
+    assert gbud < sum(g for g, _ in fps) + min(t for _, t in fps)
     state = 64 << 20
-    srv = make_server(wmg.PREC_F64, budget=state + 1_000_000, state=state, slots=4)
+    srv = make_server(wmg.PREC_F64, budget=state + gbud, state=state, slots=4)
     tickets = [srv.submit(p, b) for p, (_, b) in zip(reqs, data)]
-    done = run_to_end(srv, list(tickets))
+    done = {}
+    left = list(tickets)
+    for _ in range(100000):
+        pending = srv.step()
+        st = srv.stats()
+        assert st["geometry_bytes_used"] <= gbud
+        for t in list(left):
+            r = srv.poll(t)
+            if r is not None:
+                done[t] = r
+                left.remove(t)
+        if pending == 0 and not left:
+            break
     st = srv.stats()
     srv.close()
-    assert st["geometries_evicted"] >= 2 and st["geometry_setups"] >= 3
+    assert not left
+    assert st["geometries_evicted"] >= 1 and st["geometry_setups"] >= 3
     ref = make_server(wmg.PREC_F64)
     for t, p, (_, b) in zip(tickets, reqs, data):
         u = ref.submit(p, b)

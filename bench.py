@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--serving-max-n", type=int, default=512,
                     help="largest image side of the serving stream (sizes 128 .. 2048 in the full stream)")
     ap.add_argument("--serving-only", action="store_true", help="run the serving leg alone and print its JSON")
+    ap.add_argument("--serving-burst", action="store_true",
+                    help="serving leg with every request arriving at t = 0 (saturated throughput)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the uneven-batch leg")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run 3 projector and 3 backprojector launches on a batch of 16 images of the "
                          "workload geometry (FP32) and exit: the small case for ncu captures")
@@ -308,6 +311,11 @@ def run_ours(args, rank, world, local):
             "roofline": roofline,
             "cpu_baseline": cpu,
         }
+        if not args.no_batched and world == 1:
+            try:
+                line["batched"] = batched_leg(args, dev)
+            except Exception as e:
+                line["batched"] = {"unavailable": f"{type(e).__name__}: {e}"}
         if not args.no_serving and world == 1:
             try:
                 line["serving"] = serving_leg(args, dev)
@@ -331,6 +339,8 @@ def serving_leg(args, dev) -> dict:
     probs = [p for p, _ in picked]
     arrivals = np.cumsum([g for _, g in picked]) / args.serving_rate
     arrivals -= arrivals[0]
+    if args.serving_burst:
+        arrivals[:] = 0.0
     # sinograms b = W x + 1% noise (FP64 library projector), resident on the device
     bs = []
     for p in probs:
@@ -372,8 +382,8 @@ def serving_leg(args, dev) -> dict:
     infos = [done[i][1] for i in range(len(probs))]
     sizes = sorted({p.n for p in probs})
     return {
-        "workload": f"poisson_{len(probs)}req_rate{args.serving_rate:g}_n" + "-".join(map(str, sizes)) +
-                    "_m90-720",
+        "workload": ("burst" if args.serving_burst else f"poisson_rate{args.serving_rate:g}") +
+                    f"_{len(probs)}req_n" + "-".join(map(str, sizes)) + "_m90-720",
         "requests": len(probs), "recon_per_s": len(probs) / wall, "wall_s": wall,
         "p50_latency_ms": float(np.percentile(lat, 50)), "p99_latency_ms": float(np.percentile(lat, 99)),
         "mean_latency_ms": float(lat.mean()),
@@ -385,6 +395,51 @@ def serving_leg(args, dev) -> dict:
         "solver": "WMG-GMRES(20) hybrid depth 1, FP32 operator / FP64 Krylov, rtol 1e-4",
         "lambda": f"Tikhonov (W^T W + lambda) x = W^T b, lambda = {SERVING_EPS:g} * m / n",
         "note": "geometry setups (leaf Gram + inverses) run on a worker stream, overlapping the steps",
+    }
+
+
+# ---------------------------------------------------------------------------
+# Uneven-batch leg: 64 problems of different sizes and angle counts solved
+# together (one launch per operator application over all of them)
+# ---------------------------------------------------------------------------
+def batched_leg(args, dev) -> dict:
+    import torch
+    import paper_1310_0956_gb300 as wmg
+
+    probs = S.workload_batched(64).problems
+    bs = []
+    for p in probs:
+        op = wmg.Plan(p.n, p.m, p.D, levels=0, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F64)
+        b64 = op.project(torch.tensor(p.image().reshape(-1), dtype=torch.float64, device=dev))
+        b64 = b64 + p.noise * b64.abs().max() * torch.tensor(p.noise_unit(), dtype=torch.float64, device=dev)
+        bs.append(b64.to(torch.float32).contiguous())
+        op.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bt = wmg.Batch([dict(n=p.n, m=p.m, D=p.D, levels=p.levels, lam=SERVING_EPS * p.m / p.n) for p in probs],
+                   nu1=NU1, nu2=NU2, hybrid_depth=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F32)
+    torch.cuda.synchronize()
+    setup = time.perf_counter() - t0
+    outs = [torch.empty(p.N, dtype=torch.float32, device=dev) for p in probs]
+    bt.solve(bs, wmg.SOLVER_CGLS, True, MAX_ITER, RTOL, outs=outs)          # warm-up
+    times, infos = [], None
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, infos, _ = bt.solve(bs, wmg.SOLVER_CGLS, True, MAX_ITER, RTOL, outs=outs)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    bt.close()
+    t = float(np.mean(times))
+    return {
+        "workload": "batched64_n128-512_m60-360_noise1pct", "problems": len(probs),
+        "recon_per_s": len(probs) / t, "ms_per_batch": t * 1e3,
+        "solver": f"WMG-CGLS (PCG on the normal equations), additive cycle, nu1=nu2={NU1}, rtol {RTOL:g}",
+        "lambda": f"lambda = {SERVING_EPS:g} * m / n",
+        "precision": "fp32 operator, fp64 Krylov/leaf solves",
+        "iters_mean": float(np.mean([i[0] for i in infos])), "iters_max": int(max(i[0] for i in infos)),
+        "all_converged": bool(all(i[1] == 0 for i in infos)),
+        "setup_s": setup, "timing": "host clock around the synchronising batch solve, mean of 3",
     }
 
 

@@ -232,10 +232,11 @@ int32_t wmg_batch_solve(wmg_batch *batch, int32_t solver, int32_t preconditioned
  * the geometry's setup and, while that setup runs, its scratch
  * (wmg_server_footprint gives all three).
  *
- * Geometry setups run on a worker thread with a stream of its own, so that
- * they overlap the steps of the requests already admitted; a request waits
- * in the queue until its geometry is ready (requests behind it whose
- * geometries are ready may pass it), at most two setups run at a time.
+ * Geometry setups run on three worker threads, each with a stream of its
+ * own, so that they overlap one another and the steps of the requests
+ * already admitted; a request waits in the queue until its geometry is ready
+ * (requests behind it whose geometries are ready may pass it); at most four
+ * setups are started or queued at a time.
  *
  * Streams: all request work is on the stream given at creation;
  * wmg_server_step synchronises it. Not thread-safe. */
@@ -309,8 +310,25 @@ int32_t wmg_server_stats(const wmg_server *srv, wmg_server_counters *out);
 int32_t wmg_server_footprint(const wmg_server *srv, const wmg_geom *g, const wmg_opts *o, int64_t *state,
                              int64_t *geometry, int64_t *setup);
 
+/* ---- stored-matrix comparator -------------------------------------------
+ * W (transposed = 0: M rows, one per ray) or W^T (transposed = 1: N rows, one
+ * per pixel) of a single-geometry plan assembled on the device as CSR: int64
+ * row pointers, int32 column indices, values = the exact intersection lengths
+ * (evaluated in FP64 by the same trapezoid law as the matrix-free kernels,
+ * stored as double for F64 plans and float for F32 plans). Not part of the
+ * method: a reference for what storing W instead of recomputing it costs.
+ * Device memory 12 or 16 bytes per nonzero; synchronising. */
+typedef struct wmg_csr wmg_csr;
+int32_t wmg_csr_create(wmg_plan *plan, int32_t transposed, void *stream, wmg_csr **out);
+int32_t wmg_csr_destroy(wmg_csr *csr);
+int32_t wmg_csr_info(const wmg_csr *csr, int64_t *rows, int64_t *cols, int64_t *nnz);
+/* y_v = A x_v for v < count (x_v at x + v * cols, y_v at y + v * rows, device
+ * memory of the plan precision's type); one launch, asynchronous on stream. */
+int32_t wmg_csr_apply(const wmg_csr *csr, int32_t count, const void *x, void *y, void *stream);
+
 /* Number of nonzero intersection lengths of the plan's W (rays x pixels with
- * a nonzero weight), counted on the device at plan creation. */
+ * a nonzero weight), counted on the device at the first call (on the legacy
+ * default stream, synchronising) and cached. */
 int32_t wmg_plan_nnz(const wmg_plan *plan, int64_t *nnz);
 
 /* Library-wide count of kernel launches since the last reset (all plans of

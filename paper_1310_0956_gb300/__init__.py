@@ -111,6 +111,10 @@ _SIGNATURES = {
     "wmg_server_poll": (_i32, [_vp, C.c_uint64, C.POINTER(_i32), C.POINTER(wmg_solve_info), C.POINTER(_dbl),
                                C.POINTER(_dbl)]),
     "wmg_server_stats": (_i32, [_vp, C.POINTER(wmg_server_counters)]),
+    "wmg_csr_create": (_i32, [_vp, _i32, _vp, C.POINTER(_vp)]),
+    "wmg_csr_destroy": (_i32, [_vp]),
+    "wmg_csr_info": (_i32, [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64)]),
+    "wmg_csr_apply": (_i32, [_vp, _i32, _vp, _vp, _vp]),
     "wmg_server_footprint": (_i32, [_vp, C.POINTER(wmg_geom), C.POINTER(wmg_opts), C.POINTER(_i64),
                                     C.POINTER(_i64), C.POINTER(_i64)]),
 }
@@ -298,6 +302,26 @@ def wmg_server_footprint(srv, geom: wmg_geom, opts=None) -> tuple[int, int, int]
     return a.value, b.value, c.value
 
 
+def wmg_csr_create(plan, transposed, stream=None):
+    out = _vp()
+    _check(lib().wmg_csr_create(plan, 1 if transposed else 0, stream, C.byref(out)))
+    return out
+
+
+def wmg_csr_destroy(csr):
+    _check(lib().wmg_csr_destroy(csr))
+
+
+def wmg_csr_info(csr) -> tuple[int, int, int]:
+    r, c, z = _i64(), _i64(), _i64()
+    _check(lib().wmg_csr_info(csr, C.byref(r), C.byref(c), C.byref(z)))
+    return r.value, c.value, z.value
+
+
+def wmg_csr_apply(csr, count, x, y, stream=None):
+    _check(lib().wmg_csr_apply(csr, count, x, y, stream))
+
+
 # ---- torch convenience wrapper ---------------------------------------------
 class Plan:
     """A plan for one geometry; methods take torch CUDA tensors of the plan's
@@ -383,6 +407,10 @@ class Plan:
     def nnz(self) -> int:
         return wmg_plan_nnz(self.handle)
 
+    def csr(self, transposed=False):
+        """The plan's W (or W^T) stored as CSR: a StoredOperator."""
+        return StoredOperator(self, transposed)
+
     def launch_count(self, reset=False) -> int:
         """Library kernel launches since the last reset (process-wide)."""
         return wmg_launch_count(reset)
@@ -418,6 +446,33 @@ class Plan:
             h = np.frombuffer(hist, dtype=np.float64).reshape(cnt, max_iter + 1)
             hists = [h[i, :infos[i][0] + 1].copy() for i in range(cnt)]
         return out, infos, hists, rc
+
+
+class StoredOperator:
+    """W or W^T of a plan assembled as CSR on the device (wmg_csr_*):
+    apply(x) multiplies `count` vectors stored back to back."""
+
+    def __init__(self, plan, transposed=False):
+        self._plan = plan
+        self.handle = wmg_csr_create(plan.handle, transposed, plan._stream())
+        self.rows, self.cols, self.nnz = wmg_csr_info(self.handle)
+
+    def apply(self, x, out=None):
+        xp, cnt = self._plan._arg(x, self.cols)
+        out = out if out is not None else self._plan._torch.empty(cnt * self.rows, dtype=x.dtype, device=x.device)
+        wmg_csr_apply(self.handle, cnt, xp, self._plan._arg(out, self.rows)[0], self._plan._stream())
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            wmg_csr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:

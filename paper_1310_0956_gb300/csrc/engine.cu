@@ -26,6 +26,8 @@ int32_t fail(int32_t code, const std::string &msg)
     return code;
 }
 
+thread_local cudaStream_t g_alloc_stream = nullptr;
+
 static std::atomic<long long> g_launches{0};
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
@@ -652,8 +654,37 @@ int32_t upload_geoms(wmg_plan *pl, cudaStream_t st)
     return WMG_OK;
 }
 
-// Device setup of geometry gi: D~ = W^T (W 1) + lambda, SIRT R and C, nnz(W)
-// and the leaf inverses. Runs on a one-slot table of that geometry.
+// nnz(W) of geometry gi, counted on the device on first use (a measurement
+// aid: the solvers do not need it). Synchronising.
+static int32_t count_nnz(wmg_plan *pl, int gi, cudaStream_t st, int64_t *out)
+{
+    Geo &G = *pl->geos[gi];
+    if (G.nnz < 0) {
+        ProbSet one;
+        one.nprob = 1;
+        one.h.assign(1, ProbDev{});
+        one.h[0].geom = gi;
+        one.h[0].kin1 = one.h[0].kout1 = G.g.K;
+        build_tiles(pl, one);
+        if (!upload_set(one, st)) return fail(WMG_ERR_OOM, "nnz tables");
+        unsigned long long *dcount = nullptr;
+        WMG_CUDA(cudaMallocAsync(&dcount, sizeof(unsigned long long), st));
+        cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), st);
+        launch_count_nnz(pl->d_geom.as<GeomDev>(), one.d.as<ProbDev>(), one.proj.tiles.as<int4>(), one.proj.n,
+                         dcount, st);
+        unsigned long long hcount = 0;
+        cudaMemcpyAsync(&hcount, dcount, sizeof(hcount), cudaMemcpyDeviceToHost, st);
+        WMG_CUDA(cudaStreamSynchronize(st));
+        cudaFreeAsync(dcount, st);
+        WMG_CUDA(cudaGetLastError());
+        G.nnz = (int64_t)hcount;
+    }
+    *out = G.nnz;
+    return WMG_OK;
+}
+
+// Device setup of geometry gi: D~ = W^T (W 1) + lambda, SIRT R and C and the
+// leaf inverses. Runs on a one-slot table of that geometry.
 template <class T>
 int32_t setup_geometry(wmg_plan *pl, int gi, cudaStream_t st)
 {
@@ -686,16 +717,7 @@ int32_t setup_geometry(wmg_plan *pl, int gi, cudaStream_t st)
     a.out_op = tmp_img.p;
     backproject<T>(pl, one, a, st);
     k_recip<T><<<num_sms() * 4, 256, 0, st>>>(tmp_img.as<T>(), G.sirtC.as<T>(), N, 0.0);
-    unsigned long long *dcount = nullptr;
-    WMG_CUDA(cudaMalloc(&dcount, sizeof(unsigned long long)));
-    cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), st);
-    launch_count_nnz(pl->d_geom.as<GeomDev>(), one.d.as<ProbDev>(), one.proj.tiles.as<int4>(), one.proj.n,
-                     dcount, st);
-    unsigned long long hcount = 0;
-    cudaMemcpyAsync(&hcount, dcount, sizeof(hcount), cudaMemcpyDeviceToHost, st);
-    WMG_CUDA(cudaStreamSynchronize(st));
-    cudaFree(dcount);
-    G.nnz = (int64_t)hcount;
+    G.nnz = -1;                                      // counted on first request (count_nnz)
     WMG_CUDA(cudaGetLastError());
     G.g.dinv = G.dinv.p;
     G.g.sirtR = G.sirtR.p;
@@ -780,7 +802,7 @@ extern "C" int32_t wmg_plan_destroy(wmg_plan *plan)
 extern "C" int32_t wmg_plan_nnz(const wmg_plan *plan, int64_t *nnz)
 {
     if (!plan || !nnz) return fail(WMG_ERR_INVALID_ARG, "wmg_plan_nnz: bad arguments");
-    *nnz = plan->geos[0]->nnz;
+    return count_nnz(const_cast<wmg_plan *>(plan), 0, nullptr, nnz);
     return WMG_OK;
 }
 
@@ -813,7 +835,10 @@ extern "C" int32_t wmg_profile_end(wmg_plan *plan, wmg_profile_stats *out, void 
         cudaEventDestroy(r.e1);
     }
     plan->prof.clear();
-    out->nnz_per_image = (double)plan->geos[0]->nnz;
+    int64_t nnz = 0;
+    int32_t rc = count_nnz(plan, 0, static_cast<cudaStream_t>(stream), &nnz);
+    if (rc) return rc;
+    out->nnz_per_image = (double)nnz;
     return WMG_OK;
 }
 

@@ -19,18 +19,31 @@ int num_sms();
 // ---------------------------------------------------------------------------
 // device buffers
 // ---------------------------------------------------------------------------
+// Stream for the allocations of this host thread's non-persistent buffers
+// (set by threads that build geometries concurrently with running solves):
+// when set, DevBuf allocates and frees stream-ordered on it, so that freeing
+// a temporary does not synchronise the device.
+extern thread_local cudaStream_t g_alloc_stream;
+
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    bool persistent = false;       // outlives the thread's allocation stream
+    cudaStream_t ast = nullptr;    // stream of a stream-ordered allocation
     DevBuf() = default;
+    explicit DevBuf(bool persist) : persistent(persist) {}
     DevBuf(const DevBuf &) = delete;
     DevBuf &operator=(const DevBuf &) = delete;
     ~DevBuf() { release(); }
     void release()
     {
-        if (p) cudaFree(p);
+        if (p) {
+            if (ast) cudaFreeAsync(p, ast);
+            else cudaFree(p);
+        }
         p = nullptr;
         bytes = 0;
+        ast = nullptr;
     }
     // grow-only; contents are not preserved
     bool ensure(size_t b)
@@ -38,7 +51,14 @@ struct DevBuf {
         if (b <= bytes && p) return true;
         release();
         if (b == 0) b = 16;
-        if (cudaMalloc(&p, b) != cudaSuccess) {
+        cudaError_t e;
+        if (!persistent && g_alloc_stream) {
+            e = cudaMallocAsync(&p, b, g_alloc_stream);
+            if (e == cudaSuccess) ast = g_alloc_stream;
+        } else {
+            e = cudaMalloc(&p, b);
+        }
+        if (e != cudaSuccess) {
             cudaGetLastError();
             p = nullptr;
             return false;
@@ -90,11 +110,11 @@ struct ProbSet {
 // One geometry of a plan with its device tables.
 struct Geo {
     GeomDev g{};
-    int64_t N = 0, M = 0, nnz = 0;
+    int64_t N = 0, M = 0, nnz = -1;     // nnz: counted on first request
     bool has_wmg = true, unit_bins = true;
     int hd = 0;                 // hybrid depth in use: min(hybrid_depth, L), 0 for additive
     int haar_W = 1;             // Haar strip width (pixels)
-    DevBuf cs64, cs32, csx, angf, dinv, leafinv, sirtR, sirtC;
+    DevBuf cs64{true}, cs32{true}, csx{true}, angf{true}, dinv{true}, leafinv{true}, sirtR{true}, sirtC{true};
 };
 
 }  // namespace wmg

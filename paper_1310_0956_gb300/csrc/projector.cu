@@ -256,7 +256,7 @@ k_count_nnz(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
             const int ix0 = (int)ceil((tk - yc * ss) / cc + half_n - 0.5 - hwx);
             for (int q = 0; q < 2; ++q) {
                 const int ix = ix0 + q;
-                if (ix >= 0 && ix < n && ch(fabs(line_dist(line, ix + 0.5 - half_n, yc))) > 0.0) ++cnt;
+                if (ix >= 0 && ix < n && ch(fabs(line_dist(line, ix + 0.5 - half_n, yc))) > kNnzEps) ++cnt;
             }
         }
         atomicAdd(count, cnt);

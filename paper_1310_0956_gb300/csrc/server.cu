@@ -199,28 +199,34 @@ struct SetupJob {
     int32_t rc = WMG_OK;
 };
 
-// Geometry setups (leaf Gram assembly and inverses) run here, overlapping the
-// ticks of the requests already admitted. Each setup builds a one-geometry
-// plan on the worker's stream and hands its geometry over to the server.
+// Geometry setups (leaf Gram assembly and inverses) run on kSetupThreads
+// worker threads, each with a stream of its own, overlapping one another and
+// the ticks of the requests already admitted. Each setup builds a
+// one-geometry plan on its thread's stream and hands the geometry over.
+constexpr int kSetupThreads = 3;
+
 struct SetupWorker {
-    std::thread th;
+    std::thread th[kSetupThreads];
+    cudaStream_t sts[kSetupThreads] = {};
     std::mutex mu;
     std::condition_variable cv;
     std::deque<std::shared_ptr<SetupJob>> todo;
     std::vector<std::shared_ptr<SetupJob>> done;
     bool stop = false;
-    cudaStream_t st = nullptr;
     int device = 0;
 
     void start()
     {
         cudaGetDevice(&device);
-        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-        th = std::thread([this] { run(); });
+        for (int i = 0; i < kSetupThreads; ++i) {
+            cudaStreamCreateWithFlags(&sts[i], cudaStreamNonBlocking);
+            th[i] = std::thread([this, i] { run(sts[i]); });
+        }
     }
-    void run()
+    void run(cudaStream_t st)
     {
         cudaSetDevice(device);
+        g_alloc_stream = st;           // temporaries of the setups: stream-ordered
         for (;;) {
             std::shared_ptr<SetupJob> job;
             {
@@ -263,14 +269,18 @@ struct SetupWorker {
             stop = true;
             cv.notify_all();
         }
-        if (th.joinable()) th.join();
-        if (st) cudaStreamSynchronize(st);
-        if (st) cudaStreamDestroy(st);
-        st = nullptr;
+        for (int i = 0; i < kSetupThreads; ++i) {
+            if (th[i].joinable()) th[i].join();
+            if (sts[i]) {
+                cudaStreamSynchronize(sts[i]);
+                cudaStreamDestroy(sts[i]);
+            }
+            sts[i] = nullptr;
+        }
     }
 };
 
-constexpr int kMaxSetupsInFlight = 2;
+constexpr int kMaxSetupsInFlight = kSetupThreads + 1;
 
 }  // namespace
 

@@ -402,12 +402,17 @@ static int32_t assemble(const GeomDev &gh, const GeomDev *gd, double *Dacc, cuda
     signed char *Fc = nullptr;
     int2 *rng = nullptr;
     int *dlist = nullptr;
-    auto cleanup = [&]() { cudaFree(Gbuf); cudaFree(Fw); cudaFree(Fc); cudaFree(rng); cudaFree(dlist); };
+    // stream-ordered scratch: no device-wide synchronisation on free, so
+    // setups on other streams and the solves keep running
+    auto cleanup = [&]() {
+        cudaFreeAsync(Gbuf, st); cudaFreeAsync(Fw, st); cudaFreeAsync(Fc, st); cudaFreeAsync(rng, st);
+        cudaFreeAsync(dlist, st);
+    };
     const size_t nfoot = (size_t)chunk * P * R * B * 2;
-    if (cudaMalloc(&Gbuf, (size_t)chunk * P * R * KT * sizeof(TG)) != cudaSuccess ||
-        cudaMalloc(&Fw, nfoot * sizeof(TG)) != cudaSuccess || cudaMalloc(&Fc, nfoot) != cudaSuccess ||
-        cudaMalloc(&rng, (size_t)chunk * P * sizeof(int2)) != cudaSuccess ||
-        cudaMalloc(&dlist, (size_t)gh.m * sizeof(int)) != cudaSuccess) {
+    if (cudaMallocAsync(&Gbuf, (size_t)chunk * P * R * KT * sizeof(TG), st) != cudaSuccess ||
+        cudaMallocAsync(&Fw, nfoot * sizeof(TG), st) != cudaSuccess || cudaMallocAsync(&Fc, nfoot, st) != cudaSuccess ||
+        cudaMallocAsync(&rng, (size_t)chunk * P * sizeof(int2), st) != cudaSuccess ||
+        cudaMallocAsync(&dlist, (size_t)gh.m * sizeof(int), st) != cudaSuccess) {
         cudaGetLastError();
         cleanup();
         return fail(WMG_ERR_OOM, "leaf setup: device allocation failed");
@@ -448,11 +453,13 @@ int32_t build_leaf_inverses(const GeomDev &gh, const GeomDev *gd, double *leafin
     const int inv_ctas = std::min(K, num_sms() * 4);
     double *Dacc = nullptr, *A = nullptr, *Y = nullptr;
     int *status = nullptr;
-    auto cleanup = [&]() { cudaFree(Dacc); cudaFree(A); cudaFree(Y); cudaFree(status); };
-    if (cudaMalloc(&Dacc, (size_t)K * P * P * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&A, (size_t)inv_ctas * P * P * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&Y, (size_t)inv_ctas * P * P * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&status, (size_t)K * sizeof(int)) != cudaSuccess) {
+    auto cleanup = [&]() {
+        cudaFreeAsync(Dacc, st); cudaFreeAsync(A, st); cudaFreeAsync(Y, st); cudaFreeAsync(status, st);
+    };
+    if (cudaMallocAsync(&Dacc, (size_t)K * P * P * sizeof(double), st) != cudaSuccess ||
+        cudaMallocAsync(&A, (size_t)inv_ctas * P * P * sizeof(double), st) != cudaSuccess ||
+        cudaMallocAsync(&Y, (size_t)inv_ctas * P * P * sizeof(double), st) != cudaSuccess ||
+        cudaMallocAsync(&status, (size_t)K * sizeof(int), st) != cudaSuccess) {
         cudaGetLastError();
         cleanup();
         return fail(WMG_ERR_OOM, "leaf setup: device allocation failed");

@@ -59,6 +59,11 @@ struct GeomDev {
                              // backprojector takes its two-bin path
 };
 
+// A weight counts as a nonzero of W when its chord exceeds this many pixel
+// widths: lines through a pixel corner give chords of rounding size (~1e-16)
+// that are zero in exact arithmetic.
+constexpr double kNnzEps = 1e-12;
+
 // Fills the FP32 per-angle table from FP64 (cos, sin) pairs.
 void fill_angle_table(const double2 *cs, int m, AngleF *out);
 

@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--serving-burst", action="store_true",
                     help="serving leg with every request arriving at t = 0 (saturated throughput)")
     ap.add_argument("--no-batched", action="store_true", help="skip the uneven-batch leg")
+    ap.add_argument("--no-comparator", action="store_true", help="skip the stored-W (CSR) comparator leg")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run 3 projector and 3 backprojector launches on a batch of 16 images of the "
                          "workload geometry (FP32) and exit: the small case for ncu captures")
@@ -280,6 +281,14 @@ def run_ours(args, rank, world, local):
     roofline = None
     if prof:
         roofline = roofline_entry(prof, P0, B)
+    comparator = None
+    if not args.no_comparator and rank == 0:
+        try:
+            comparator = comparator_leg(plan, P0, x, b, flush, dev)
+            if roofline is not None:
+                roofline["fp32_sgemm_tflops_measured"] = comparator["fp32_sgemm_tflops_measured"]
+        except Exception as e:
+            comparator = {"unavailable": f"{type(e).__name__}: {e}"}
 
     if rank == 0:
         cpu = None
@@ -310,6 +319,7 @@ def run_ours(args, rank, world, local):
             "gpu_launches": launches,
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "stored_w_comparator": comparator,
         }
         if not args.no_batched and world == 1:
             try:
@@ -441,6 +451,82 @@ def batched_leg(args, dev) -> dict:
         "all_converged": bool(all(i[1] == 0 for i in infos)),
         "setup_s": setup, "timing": "host clock around the synchronising batch solve, mean of 3",
     }
+
+
+# ---------------------------------------------------------------------------
+# Stored-W comparator: the workload's W and W^T as CSR (wmg_csr_*), applied
+# to the same 64-image batch as the matrix-free operators; its bandwidth is
+# where an HBM roofline fraction means something. Also the measured FP32
+# peak (cuBLAS SGEMM, no TF32) as context for the ALU-bound projector.
+# ---------------------------------------------------------------------------
+def _event_time(fn, stream, flush, reps=5):
+    """Median device time of fn() between CUDA events, L2 flushed before each
+    call; a ~0.2 ms spin kernel ahead of the start event keeps the GPU busy
+    while the host issues fn(), so host launch latency is not timed."""
+    import torch
+    ts = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        torch.cuda._sleep(400_000)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) * 1e-3)
+    return float(np.median(ts))
+
+
+def comparator_leg(plan, P0, x_batch, b_batch, flush, dev) -> dict:
+    import torch
+    stream = torch.cuda.current_stream()
+    B = x_batch.numel() // P0.N
+    out = {"workload": f"{P0.n}x{P0.n}_{P0.m}ang_{P0.D}det, batch {B}, fp32"}
+    Wc, WTc = plan.csr(False), plan.csr(True)
+    hbm = load_peaks().get("hbm_gbs")
+    y_b = torch.empty_like(b_batch)
+    y_x = torch.empty_like(x_batch)
+    for name, csr, fn_free, inp, res in (("W", Wc, lambda: plan.project(x_batch, out=y_b), x_batch, y_b),
+                                        ("WT", WTc, lambda: plan.backproject(b_batch, out=y_x), b_batch, y_x)):
+        for cnt in (1, B):
+            xi = inp[: cnt * csr.cols]
+            yo = res[: cnt * csr.rows]
+            t_csr = _event_time(lambda: csr.apply(xi, out=yo), stream, flush)
+            bytes_ = csr.nnz * 8 + (csr.rows + 1) * 8 + cnt * (csr.rows + csr.cols) * 4
+            out[f"{name}_csr_x{cnt}_ms"] = t_csr * 1e3
+            out[f"{name}_csr_x{cnt}_gbs"] = bytes_ / t_csr / 1e9
+            if hbm:
+                out[f"{name}_csr_x{cnt}_hbm_frac"] = bytes_ / t_csr / 1e9 / hbm
+        if name == "W":
+            t_free = _event_time(lambda: plan.project(x_batch, out=y_b), stream, flush)
+        else:
+            t_free = _event_time(lambda: plan.backproject(b_batch, out=y_x), stream, flush)
+        out[f"{name}_matrix_free_x{B}_ms"] = t_free * 1e3
+        out[f"{name}_speedup_vs_csr_x{B}"] = out[f"{name}_csr_x{B}_ms"] / (t_free * 1e3)
+    out["nnz"] = Wc.nnz
+    out["csr_bytes"] = int(Wc.nnz * 8 + (Wc.rows + 1) * 8)
+    Wc.close()
+    WTc.close()
+    # FP32 arithmetic peak, measured: cuBLAS SGEMM with TF32 off
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    a = torch.randn(8192, 8192, device=dev)
+    bm = torch.randn(8192, 8192, device=dev)
+    c = torch.empty(8192, 8192, device=dev)
+    for _ in range(2):
+        torch.matmul(a, bm, out=c)
+    ts = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        torch.matmul(a, bm, out=c)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) * 1e-3)
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    out["fp32_sgemm_tflops_measured"] = 2 * 8192 ** 3 / min(ts) / 1e12
+    del a, bm, c
+    return out
 
 
 def load_peaks():

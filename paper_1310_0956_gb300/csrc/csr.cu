@@ -126,22 +126,38 @@ k_csr_pixels(const GeomDev *__restrict__ Gd, int64_t *__restrict__ rp, int *__re
 }
 
 // y_v = A x_v for `count` vectors (x_v at x + v * cols, y_v at y + v * rows):
-// one warp per row, the row's entries re-read from L1 for each vector.
+// one half-warp per row (two rows per warp in flight), four entries per lane
+// per step; the row's entries are re-read from L1 for each vector.
 template <class T>
 __global__ void __launch_bounds__(256)
 k_csr_spmv(int64_t rows, int64_t cols, const int64_t *__restrict__ rp, const int *__restrict__ col,
            const T *__restrict__ val, int count, const T *__restrict__ x, T *__restrict__ y)
 {
-    const int lane = threadIdx.x & 31;
-    for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows;
-         r += (int64_t)gridDim.x * (blockDim.x >> 5)) {
-        const int64_t b = rp[r], e = rp[r + 1];
+    const int lane = threadIdx.x & 15;
+    const int64_t hw0 = blockIdx.x * (int64_t)(blockDim.x >> 4) + (threadIdx.x >> 4);
+    const int64_t nhw = (int64_t)gridDim.x * (blockDim.x >> 4);
+    // every half-warp runs the same number of iterations (shuffles stay converged)
+    const int64_t iters = (rows + nhw - 1) / nhw;
+    for (int64_t it = 0; it < iters; ++it) {
+        const int64_t r = hw0 + it * nhw;
+        const bool live = r < rows;
+        const int64_t b = live ? rp[r] : 0, e = live ? rp[r + 1] : 0;
         for (int v = 0; v < count; ++v) {
             const T *xv = x + (int64_t)v * cols;
-            T acc = T(0);
-            for (int64_t p = b + lane; p < e; p += 32) acc = fma_t(__ldg(val + p), __ldg(xv + __ldg(col + p)), acc);
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) y[(int64_t)v * rows + r] = acc;
+            T acc[4] = {T(0), T(0), T(0), T(0)};
+            int64_t p = b + lane;
+            for (; p + 48 < e; p += 64) {
+                int cl[4];
+                T vl[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) { cl[u] = __ldg(col + p + 16 * u); vl[u] = __ldg(val + p + 16 * u); }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[u] = fma_t(vl[u], __ldg(xv + cl[u]), acc[u]);
+            }
+            for (; p < e; p += 16) acc[0] = fma_t(__ldg(val + p), __ldg(xv + __ldg(col + p)), acc[0]);
+            T sum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+            for (int o = 8; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if (live && lane == 0) y[(int64_t)v * rows + r] = sum;
         }
     }
 }

@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the serving leg (request stream through the continuous-batching server)")
     ap.add_argument("--serving-requests", type=int, default=48)
-    ap.add_argument("--serving-rate", type=float, default=6.0, help="mean arrivals per second (Poisson)")
+    ap.add_argument("--serving-rate", type=float, default=8.0,
+                    help="mean arrivals per second (Poisson); 8 = 0.7 x the saturated throughput measured once")
     ap.add_argument("--serving-max-n", type=int, default=512,
                     help="largest image side of the serving stream (sizes 128 .. 2048 in the full stream)")
     ap.add_argument("--serving-only", action="store_true", help="run the serving leg alone and print its JSON")
@@ -66,6 +67,8 @@ def parse():
                     help="serving leg with every request arriving at t = 0 (saturated throughput)")
     ap.add_argument("--no-batched", action="store_true", help="skip the uneven-batch leg")
     ap.add_argument("--no-comparator", action="store_true", help="skip the stored-W (CSR) comparator leg")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 1024x1024 / 1024-angle leg (mixed FP32 path vs the FP64 GPU path)")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run 3 projector and 3 backprojector launches on a batch of 16 images of the "
                          "workload geometry (FP32) and exit: the small case for ncu captures")
@@ -321,6 +324,11 @@ def run_ours(args, rank, world, local):
             "cpu_baseline": cpu,
             "stored_w_comparator": comparator,
         }
+        if not args.no_large and world == 1:
+            try:
+                line["large"] = large_leg(dev)
+            except Exception as e:
+                line["large"] = {"unavailable": f"{type(e).__name__}: {e}"}
         if not args.no_batched and world == 1:
             try:
                 line["batched"] = batched_leg(args, dev)
@@ -526,6 +534,47 @@ def comparator_leg(plan, P0, x_batch, b_batch, flush, dev) -> dict:
     torch.backends.cuda.matmul.allow_tf32 = prev
     out["fp32_sgemm_tflops_measured"] = 2 * 8192 ** 3 / min(ts) / 1e12
     del a, bm, c
+    return out
+
+
+# ---------------------------------------------------------------------------
+# 1024 x 1024 leg: one reconstruction of the large workload by WMG-CGLS
+# (additive cycle) to 1e-4, mixed path (FP32 operator, FP64 Krylov / leaf
+# solves) next to the all-FP64 GPU path
+# ---------------------------------------------------------------------------
+def large_leg(dev) -> dict:
+    import torch
+    import paper_1310_0956_gb300 as wmg
+
+    p = S.workload_large().problems[0]
+    lam = SERVING_EPS * p.m / p.n
+    op = wmg.Plan(p.n, p.m, p.D, levels=0, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F64)
+    xt = torch.tensor(p.image().reshape(-1), dtype=torch.float64, device=dev)
+    b = op.project(xt)
+    b = b + p.noise * b.abs().max() * torch.tensor(p.noise_unit(), dtype=torch.float64, device=dev)
+    op.close()
+    out = {"workload": "1024x1024_1024ang_1449det_50ell_tex0.05_noise0.5pct", "levels": p.levels,
+           "solver": f"WMG-CGLS additive cycle, nu1=nu2={NU1}, rtol {RTOL:g}",
+           "lambda": f"lambda = {SERVING_EPS:g} * m / n"}
+    xs = {}
+    for prec, tag in ((wmg.PREC_F32, "mixed_fp32"), (wmg.PREC_F64, "fp64")):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pl = wmg.Plan(p.n, p.m, p.D, levels=p.levels, nu1=NU1, nu2=NU2, lam=lam, hybrid_depth=0,
+                      cycle=wmg.CYCLE_ADDITIVE, precision=prec)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        bb = b.float().contiguous() if prec == wmg.PREC_F32 else b
+        x, info, _, _ = pl.solve(bb, wmg.SOLVER_CGLS, True, MAX_ITER, RTOL, RESTART)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        pl.close()
+        xs[tag] = x.double()
+        out[tag] = {"setup_s": t1 - t0, "solve_s": t2 - t1, "recon_per_s": 1.0 / (t2 - t1),
+                    "iters": info[0][0], "status": info[0][1], "rel_res": info[0][2],
+                    "image_err_vs_phantom": (torch.norm(x.double() - xt) / torch.norm(xt)).item()}
+    out["rel_diff_mixed_vs_fp64"] = (torch.norm(xs["mixed_fp32"] - xs["fp64"]) / torch.norm(xs["fp64"])).item()
+    out["solve_speedup_mixed_vs_fp64"] = out["fp64"]["solve_s"] / out["mixed_fp32"]["solve_s"]
     return out
 
 

@@ -62,6 +62,9 @@ def _load():
         lib.or_op_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                      C.c_void_p, C.c_int]
         lib.or_op_free.argtypes = [vp]
+        lib.or_ray_row.restype = C.c_int64
+        lib.or_ray_row.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, vp, C.c_int, C.c_int,
+                                   _i32p, _dp, C.c_int64]
         lib.or_op_nnz.restype = C.c_int64
         lib.or_op_nnz.argtypes = [vp]
         lib.or_op_export.argtypes = [vp, _i64p, _i32p, _dp]
@@ -109,6 +112,21 @@ def weight_trapezoid(c: float, s: float, delta: float) -> float:
     """Chord of a unit pixel at signed distance `delta` (pixel units) from its
     centre for a line with unit normal (c, s)."""
     return _load().or_weight_trapezoid(c, s, delta)
+
+
+def ray_row(n: int, m: int, D: int, a: int, k: int, dt: float = 1.0, t0: float = 0.0, angles=None):
+    """Row (a, k) of W as (columns, values), built by the same walk as Op
+    (Section 2.1) without assembling W: for sampled checks at large sizes."""
+    lib = _load()
+    cap = 4 * n + 8
+    col = np.zeros(cap, np.int32)
+    val = np.zeros(cap, np.float64)
+    ang = None if angles is None else _f64(angles)
+    cnt = lib.or_ray_row(n, m, D, dt, t0, None if ang is None else ang.ctypes.data_as(C.c_void_p), a, k,
+                         col, val, cap)
+    if cnt < 0:
+        raise RuntimeError("row longer than expected")
+    return col[:cnt].copy(), val[:cnt].copy()
 
 
 class Op:

@@ -258,6 +258,38 @@ or_op *or_op_create(int n, int m, int D, double dt, double t0,
     return op;
 }
 
+/* One row (ray (a, k)) of W, built by the same walk as or_op_create without
+ * assembling the matrix: for sampled checks at sizes where W does not fit in
+ * memory. Entries sorted by column, repeated pixels merged, values in
+ * unit-square lengths. Returns the entry count; if it exceeds cap, nothing is
+ * written and the negated count is returned. */
+int64_t or_ray_row(int n, int m, int D, double dt, double t0, const double *angles, int a, int k,
+                   int32_t *col, double *val, int64_t cap)
+{
+    if (n <= 0 || m <= 0 || D <= 0 || a < 0 || a >= m || k < 0 || k >= D) return 0;
+    double c, s;
+    if (angles) { c = cos(angles[a]); s = sin(angles[a]); }
+    else trig_equispaced(a, m, &c, &s);
+    dt = dt > 0 ? dt : 1.0;
+    const double T = (k - 0.5 * (D - 1)) * dt + t0, h = 1.0 / n;
+    rowbuf rb = {0};
+    ray_siddon(n, c, s, T, &rb);
+    qsort(rb.e, (size_t)rb.len, sizeof(entry), cmp_entry);
+    int64_t cnt = 0;
+    for (int64_t q = 0; q < rb.len; q++)
+        if (q == 0 || rb.e[q].col != rb.e[q - 1].col) cnt++;
+    if (cnt > cap) { free(rb.e); return -cnt; }
+    int64_t w = 0;
+    for (int64_t q = 0; q < rb.len; q++) {
+        if (q > 0 && rb.e[q].col == rb.e[q - 1].col) { val[w - 1] += rb.e[q].val * h; continue; }
+        col[w] = rb.e[q].col;
+        val[w] = rb.e[q].val * h;
+        w++;
+    }
+    free(rb.e);
+    return cnt;
+}
+
 void or_op_free(or_op *op)
 {
     if (!op) return;

@@ -155,3 +155,14 @@ def test_nnz_scale():
     op = oracle.Op(64, 90, 91)
     ratio = op.nnz / ((4 / math.pi) * 90 * 64 * 64)
     assert 0.95 < ratio < 1.1
+
+
+def test_ray_row_matches_assembled_rows():
+    """The single-row builder gives exactly the rows of the assembled W."""
+    for (n, m, D, dt, t0) in [(16, 12, 23, 1.0, 0.0), (20, 9, 31, 1.25, 0.5), (24, 17, 35, 1.0, 0.0)]:
+        op = oracle.Op(n, m, D, dt, t0)
+        rp, col, val = op.csr()
+        for r in range(0, m * D, 7):
+            c, v = oracle.ray_row(n, m, D, r // D, r % D, dt, t0)
+            np.testing.assert_array_equal(c, col[rp[r]:rp[r + 1]])
+            np.testing.assert_array_equal(v, val[rp[r]:rp[r + 1]])

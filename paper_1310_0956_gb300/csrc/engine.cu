@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -27,6 +28,15 @@ int32_t fail(int32_t code, const std::string &msg)
 }
 
 thread_local cudaStream_t g_alloc_stream = nullptr;
+
+bool graphs_default()
+{
+    static const bool on = [] {
+        const char *v = std::getenv("WMG_GRAPHS");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
 
 static std::atomic<long long> g_launches{0};
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -1019,6 +1029,51 @@ static int32_t any_active(wmg_plan *pl, cudaStream_t st, bool *any)
     return WMG_OK;
 }
 
+// Capture `body(stream)` (a fixed sequence of launches) into g on the plan's
+// private stream. Returns false (and leaves g empty) when graphs are off or
+// the capture fails; the caller then runs the body eagerly.
+template <class F>
+static bool capture(wmg_plan *pl, Graph &g, F body)
+{
+    if (!pl->use_graphs || pl->profiling) return false;
+    if (!pl->cap_stream && cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        pl->use_graphs = false;
+        return false;
+    }
+    const long long before = g_launches.load();
+    if (cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const int32_t rc = body(pl->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(pl->cap_stream, &graph);
+    const long long n = g_launches.load() - before;
+    g_launches.fetch_sub(n);                 // nothing ran during the capture
+    if (rc != WMG_OK || e != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return false;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+        cudaGetLastError();
+        g.exec = nullptr;
+        return false;
+    }
+    g.launches = n;
+    return true;
+}
+
+static int32_t replay(const Graph &g, cudaStream_t st)
+{
+    count_launches((int)g.launches);
+    WMG_CUDA(cudaGraphLaunch(g.exec, st));
+    return WMG_OK;
+}
+
 // Per-slot results; `order` (optional) maps the caller's problem i to its slot.
 static int32_t collect(wmg_plan *pl, int max_iter, wmg_solve_info *info, double *res_hist, cudaStream_t st)
 {
@@ -1103,30 +1158,47 @@ static int32_t solve_cgls(wmg_plan *pl, bool pre, const void *b, void *xout, int
     pi.z = zvec; pi.p = pl->p.as<double>(); pi.copy_op = pl->p_op.p; pi.copyT_op = pl->pT_op.p; pi.part = pc; pi.S = S;
     img_op<T>(pl, IMG_PINIT, pi, st);
     finalize(pl, FIN_PNORM, ps.bp, pc, 1, nullptr, nullptr, pre, hist, hld, st);
-    const int chunk = 4;
-    for (int it = 0; it < max_iter; ++it) {
-        project<T>(pl, ps, pl->p_op.p, pl->pT_op.p, pl->q.p, pa, S, st);
-        finalize(pl, FIN_CGLS_ALPHA, ps.proj, pa, 1, nullptr, nullptr, pre, hist, hld, st);
+    // one iteration (a fixed launch sequence: every per-iteration decision is
+    // taken on the device from the scalars)
+    auto iteration = [&](cudaStream_t s) -> int32_t {
+        project<T>(pl, ps, pl->p_op.p, pl->pT_op.p, pl->q.p, pa, S, s);
+        finalize(pl, FIN_CGLS_ALPHA, ps.proj, pa, 1, nullptr, nullptr, pre, hist, hld, s);
         VecArgs vr{};
         vr.r = pl->r.as<double>(); vr.q = pl->q.p; vr.r_op = pl->r_op.p; vr.S = S;
-        vec_op<T>(pl, VEC_R_UPDATE, true, vr, st);
-        bp_s();
-        finalize(pl, FIN_CGLS_RES, ps.bp, pa, 1, nullptr, nullptr, pre, hist, hld, st);
+        vec_op<T>(pl, VEC_R_UPDATE, true, vr, s);
+        BpArgs a = bp_args(BP_CGLS_S, pl->r_op.p, S);
+        a.x = pl->x.as<double>(); a.p = pl->p.as<double>(); a.s = pl->s.as<double>();
+        a.part = pa;
+        if (smooth_fused) { a.z = pl->z.as<double>(); a.copy_op = pl->z_op.p; a.copyT_op = pl->zT_op.p; }
+        backproject<T>(pl, ps, a, s);
+        finalize(pl, FIN_CGLS_RES, ps.bp, pa, 1, nullptr, nullptr, pre, hist, hld, s);
         if (pre) {
             int32_t rc = wmg_apply<T>(pl, pl->s.as<double>(), pl->z.as<double>(), smooth_fused, false, true,
-                                      &have_sz, st);
+                                      &have_sz, s);
             if (rc) return rc;
             if (!have_sz) {
                 ImgArgs ia{};
                 ia.s = pl->s.as<double>(); ia.z = pl->z.as<double>(); ia.part = pb; ia.S = S;
-                img_op<T>(pl, IMG_DOT_SZ, ia, st);
+                img_op<T>(pl, IMG_DOT_SZ, ia, s);
             }
         }
-        finalize(pl, FIN_CGLS_BETA, ps.bp, pb, 1, nullptr, nullptr, pre, hist, hld, st);
+        finalize(pl, FIN_CGLS_BETA, ps.bp, pb, 1, nullptr, nullptr, pre, hist, hld, s);
         ImgArgs pu{};
-        pu.z = zvec; pu.p = pl->p.as<double>(); pu.copy_op = pl->p_op.p; pu.copyT_op = pl->pT_op.p; pu.part = pc; pu.S = S;
-        img_op<T>(pl, IMG_PUPDATE, pu, st);
-        finalize(pl, FIN_PNORM, ps.bp, pc, 1, nullptr, nullptr, pre, hist, hld, st);
+        pu.z = zvec; pu.p = pl->p.as<double>(); pu.copy_op = pl->p_op.p; pu.copyT_op = pl->pT_op.p; pu.part = pc;
+        pu.S = S;
+        img_op<T>(pl, IMG_PUPDATE, pu, s);
+        finalize(pl, FIN_PNORM, ps.bp, pc, 1, nullptr, nullptr, pre, hist, hld, s);
+        return WMG_OK;
+    };
+    const int chunk = 4;
+    Graph graph;
+    bool graphed = false;
+    for (int it = 0; it < max_iter; ++it) {
+        // the first iteration runs eagerly (it fills the work-list caches),
+        // the others replay its captured graph
+        if (it == 1) graphed = capture(pl, graph, iteration);
+        int32_t rc = graphed ? replay(graph, st) : iteration(st);
+        if (rc) return rc;
         if ((it + 1) % chunk == 0 || it + 1 == max_iter) {
             bool any = false;
             int32_t rc = any_active(pl, st, &any);
@@ -1240,43 +1312,90 @@ static int32_t solve_gmres(wmg_plan *pl, bool pre, const void *b, void *xout, in
     ga.init = 0;
     launch_gm_setv(ps.d.as<ProbDev>(), ps.vimg.tiles.as<int4>(), ps.vimg.n, V, vstride, ldp, 0,
                    pl->f.as<double>(), S, st);
+    const ProbDev *P = ps.d.as<ProbDev>();
+    const int4 *vt = ps.vimg.tiles.as<int4>();
+    const int nv = ps.vimg.n;
+    const int *jv = pl->jn.as<int>();
+    ga.jslot = 1;
+    // One Arnoldi step for every problem at its own column j = jn[slot]
+    // (the same for all problems of a solve): u = B v_j, w = A u, two
+    // classical Gram-Schmidt passes, Hessenberg column, Givens, v_{j+1}.
+    // Every index lives on the device, so the step is one fixed launch
+    // sequence (a graph after its first run).
+    auto arnoldi = [&](cudaStream_t s) -> int32_t {
+        launch_gm_getv(P, vt, nv, V, vstride, jv, pl->t.as<double>(), S, s);
+        if (pre) {
+            bool have = false;
+            int32_t rc = wmg_apply<T>(pl, pl->t.as<double>(), pl->u.as<double>(), false, true, false, &have, s);
+            if (rc) return rc;
+        } else {
+            WMG_CUDA(cudaMemcpyAsync(pl->u.p, pl->t.p, nN * 8, cudaMemcpyDeviceToDevice, s));
+            ImgArgs ic{};
+            ic.z = pl->u.as<double>(); ic.copy_op = pl->z_op.p; ic.copyT_op = pl->zT_op.p; ic.S = S;
+            img_op<T>(pl, IMG_COPY64, ic, s);
+        }
+        project<T>(pl, ps, pl->z_op.p, pl->zT_op.p, pl->sinoS.p, nullptr, S, s);
+        BpArgs wa = bp_args(BP_GMRES_W, pl->sinoS.p, S);
+        wa.z = pl->u.as<double>(); wa.out64 = pl->w.as<double>();
+        backproject<T>(pl, ps, wa, s);
+        for (int pass = 0; pass < 2; ++pass) {
+            launch_gm_dots(P, vt, nv, V, vstride, pl->w.as<double>(), 0, ldp, pa, S, s, jv);
+            double *hv = pass == 0 ? pl->h1.as<double>() : pl->h2.as<double>();
+            // all ldp columns are summed; the Arnoldi step reads those <= j
+            finalize(pl, FIN_STORE, ps.vimg, pa, ldp, nullptr, nullptr, 0, nullptr, 0, s, 0, hv, ldp, ldp);
+            launch_gm_axpy(P, vt, nv, V, vstride, pl->w.as<double>(), 0, ldp, hv, pass == 1 ? pb : nullptr, S, s,
+                           jv);
+        }
+        finalize(pl, FIN_STORE, ps.vimg, pb, 1, nullptr, nullptr, 0, nullptr, 0, s, SC_WNORM2);
+        launch_gm_scalar(0, ga, s);
+        launch_gm_setv(P, vt, nv, V, vstride, ldp, 0, pl->w.as<double>(), S, s, jv);
+        return WMG_OK;
+    };
+    // End of a cycle: y = H^-1 g, t = V y, x += B t, true residual r = f - A x
+    // into v_0, restart (or stop) on |r|.
+    auto cycle_end = [&](cudaStream_t s) -> int32_t {
+        launch_gm_scalar(1, ga, s);
+        launch_gm_combine(P, vt, nv, V, vstride, ldp, pl->gy.as<double>(), pl->jn.as<int>(), pl->t.as<double>(), S,
+                          s);
+        if (pre) {
+            bool have = false;
+            int32_t rc = wmg_apply<T>(pl, pl->t.as<double>(), pl->u.as<double>(), false, false, false, &have, s);
+            if (rc) return rc;
+        } else {
+            WMG_CUDA(cudaMemcpyAsync(pl->u.p, pl->t.p, nN * 8, cudaMemcpyDeviceToDevice, s));
+        }
+        VecArgs xa{};
+        xa.x = pl->x.as<double>(); xa.w = pl->u.as<double>(); xa.S = S;
+        vec_op<T>(pl, VEC_X_ADD, false, xa, s);
+        ImgArgs ic{};
+        ic.z = pl->x.as<double>(); ic.copy_op = pl->z_op.p; ic.copyT_op = pl->zT_op.p; ic.S = S;
+        img_op<T>(pl, IMG_COPY64, ic, s);
+        project<T>(pl, ps, pl->z_op.p, pl->zT_op.p, pl->sinoS.p, nullptr, S, s);
+        BpArgs wa = bp_args(BP_GMRES_W, pl->sinoS.p, S);
+        wa.z = pl->x.as<double>(); wa.out64 = pl->w.as<double>();
+        backproject<T>(pl, ps, wa, s);
+        VecArgs rv{};
+        rv.f = pl->f.as<double>(); rv.w = pl->w.as<double>(); rv.v = V; rv.part = pb; rv.S = S;
+        vec_op<T>(pl, VEC_RESID64, false, rv, s);
+        finalize(pl, FIN_STORE, ps.vimg, pb, 1, nullptr, nullptr, 0, nullptr, 0, s, SC_WNORM2);
+        launch_gm_scalar(2, ga, s);
+        launch_gm_setv(P, vt, nv, V, vstride, ldp, 0, V, S, s);
+        return WMG_OK;
+    };
+    Graph g_step, g_end;
+    bool step_graphed = false, end_graphed = false, step_tried = false, end_tried = false;
     int done_iters = 0;
     while (true) {
         cudaMemsetAsync(pl->done.p, 0, (size_t)count * 4, st);
         int j = 0;
         for (; j < restart && done_iters < max_iter; ++j, ++done_iters) {
-            double *Vj = V + (int64_t)j * vstride;
-            // u = B v_j  (z_op / zT_op copies of u for the product)
-            if (pre) {
-                bool have = false;
-                int32_t rc = wmg_apply<T>(pl, Vj, pl->u.as<double>(), false, true, false, &have, st);
-                if (rc) return rc;
-            } else {
-                cudaMemcpyAsync(pl->u.p, Vj, nN * 8, cudaMemcpyDeviceToDevice, st);
-                ImgArgs ic{};
-                ic.z = pl->u.as<double>(); ic.copy_op = pl->z_op.p; ic.copyT_op = pl->zT_op.p; ic.S = S;
-                img_op<T>(pl, IMG_COPY64, ic, st);
+            // first step eager (fills the work-list caches), then the graph
+            if (!step_tried && done_iters == 1) {
+                step_tried = true;
+                step_graphed = capture(pl, g_step, arnoldi);
             }
-            // w = A u
-            project<T>(pl, ps, pl->z_op.p, pl->zT_op.p, pl->sinoS.p, nullptr, S, st);
-            BpArgs wa = bp_args(BP_GMRES_W, pl->sinoS.p, S);
-            wa.z = pl->u.as<double>(); wa.out64 = pl->w.as<double>();
-            backproject<T>(pl, ps, wa, st);
-            // two classical Gram-Schmidt passes
-            for (int pass = 0; pass < 2; ++pass) {
-                launch_gm_dots(ps.d.as<ProbDev>(), ps.vimg.tiles.as<int4>(), ps.vimg.n, V, vstride,
-                               pl->w.as<double>(), j, ldp, pa, S, st);
-                double *hv = pass == 0 ? pl->h1.as<double>() : pl->h2.as<double>();
-                finalize(pl, FIN_STORE, ps.vimg, pa, j + 1, nullptr, nullptr, 0, nullptr, 0, st, 0, hv, ldp,
-                         ldp);
-                launch_gm_axpy(ps.d.as<ProbDev>(), ps.vimg.tiles.as<int4>(), ps.vimg.n, V, vstride,
-                               pl->w.as<double>(), j, ldp, hv, pass == 1 ? pb : nullptr, S, st);
-            }
-            finalize(pl, FIN_STORE, ps.vimg, pb, 1, nullptr, nullptr, 0, nullptr, 0, st, SC_WNORM2);
-            ga.j = j;
-            launch_gm_scalar(0, ga, st);
-            launch_gm_setv(ps.d.as<ProbDev>(), ps.vimg.tiles.as<int4>(), ps.vimg.n, V, vstride, ldp, j + 1,
-                           pl->w.as<double>(), S, st);
+            int32_t rc = step_graphed ? replay(g_step, st) : arnoldi(st);
+            if (rc) return rc;
             if ((j + 1) % 4 == 0) {
                 std::vector<int> dn(count);
                 WMG_CUDA(cudaMemcpyAsync(dn.data(), pl->done.p, count * 4, cudaMemcpyDeviceToHost, st));
@@ -1289,33 +1408,18 @@ static int32_t solve_gmres(wmg_plan *pl, bool pre, const void *b, void *xout, in
                 if (all) { ++j; ++done_iters; break; }
             }
         }
-        // cycle end: y = H^-1 g, t = V y, x += B t, true residual
-        launch_gm_scalar(1, ga, st);
-        launch_gm_combine(ps.d.as<ProbDev>(), ps.vimg.tiles.as<int4>(), ps.vimg.n, V, vstride, ldp,
-                          pl->gy.as<double>(), pl->jn.as<int>(), pl->t.as<double>(), S, st);
-        if (pre) {
-            bool have = false;
-            int32_t rc = wmg_apply<T>(pl, pl->t.as<double>(), pl->u.as<double>(), false, false, false, &have, st);
+        if (end_tried && !end_graphed) {
+            int32_t rc = cycle_end(st);
+            if (rc) return rc;
+        } else if (end_tried) {
+            int32_t rc = replay(g_end, st);
             if (rc) return rc;
         } else {
-            cudaMemcpyAsync(pl->u.p, pl->t.p, nN * 8, cudaMemcpyDeviceToDevice, st);
+            int32_t rc = cycle_end(st);                       // first one eager
+            if (rc) return rc;
+            end_tried = true;
+            end_graphed = capture(pl, g_end, cycle_end);
         }
-        VecArgs xa{};
-        xa.x = pl->x.as<double>(); xa.w = pl->u.as<double>(); xa.S = S;
-        vec_op<T>(pl, VEC_X_ADD, false, xa, st);
-        ImgArgs ic{};
-        ic.z = pl->x.as<double>(); ic.copy_op = pl->z_op.p; ic.copyT_op = pl->zT_op.p; ic.S = S;
-        img_op<T>(pl, IMG_COPY64, ic, st);
-        project<T>(pl, ps, pl->z_op.p, pl->zT_op.p, pl->sinoS.p, nullptr, S, st);
-        BpArgs wa = bp_args(BP_GMRES_W, pl->sinoS.p, S);
-        wa.z = pl->x.as<double>(); wa.out64 = pl->w.as<double>();
-        backproject<T>(pl, ps, wa, st);
-        VecArgs rv{};
-        rv.f = pl->f.as<double>(); rv.w = pl->w.as<double>(); rv.v = V; rv.part = pb; rv.S = S;
-        vec_op<T>(pl, VEC_RESID64, false, rv, st);
-        finalize(pl, FIN_STORE, ps.vimg, pb, 1, nullptr, nullptr, 0, nullptr, 0, st, SC_WNORM2);
-        launch_gm_scalar(2, ga, st);
-        launch_gm_setv(ps.d.as<ProbDev>(), ps.vimg.tiles.as<int4>(), ps.vimg.n, V, vstride, ldp, 0, V, S, st);
         bool any = false;
         int32_t rc = any_active(pl, st, &any);
         if (rc) return rc;

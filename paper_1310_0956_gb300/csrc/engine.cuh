@@ -117,6 +117,9 @@ struct Geo {
     DevBuf cs64{true}, cs32{true}, csx{true}, angf{true}, dinv{true}, leafinv{true}, sirtR{true}, sirtC{true};
 };
 
+// CUDA graphs for the solver iterations unless WMG_GRAPHS=0 in the environment.
+bool graphs_default();
+
 }  // namespace wmg
 
 // ---------------------------------------------------------------------------
@@ -154,6 +157,16 @@ struct wmg_plan {
     // GMRES
     wmg::DevBuf V, H, gcs, gsn, gg, gy, h1, h2, jn, done;
     // profiling: (kind 0 = project / 1 = backproject, images, start, stop)
+    // CUDA graphs of the solver iterations are captured on this private
+    // stream (capture cannot use the legacy default stream) and launched on
+    // the caller's stream. use_graphs: WMG_GRAPHS=0 in the environment at
+    // plan creation keeps every launch eager.
+    cudaStream_t cap_stream = nullptr;
+    bool use_graphs = wmg::graphs_default();
+    ~wmg_plan()
+    {
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
     bool profiling = false;
     struct ProfRec { int kind; int images; cudaEvent_t e0, e1; };
     std::vector<ProfRec> prof;
@@ -167,6 +180,20 @@ struct wmg_plan {
 };
 
 namespace wmg {
+
+// One captured sequence of launches (a solver iteration), replayed with
+// cudaGraphLaunch; `launches` = kernels per replay (for the launch counter).
+struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;
+    Graph() = default;
+    Graph(const Graph &) = delete;
+    Graph &operator=(const Graph &) = delete;
+    ~Graph()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
 
 // ---- engine steps (engine.cu) ----------------------------------------------
 void build_tiles(const wmg_plan *pl, ProbSet &ps);

@@ -251,6 +251,24 @@ k_gm_setv(const ProbDev *__restrict__ P, const int4 *__restrict__ tiles, int nti
     }
 }
 
+// out = v_j with j = jv[slot] (the Arnoldi step's preconditioner input).
+__global__ void __launch_bounds__(256)
+k_gm_getv(const ProbDev *__restrict__ P, const int4 *__restrict__ tiles, int ntiles,
+          const double *__restrict__ V, int64_t vstride, const int *__restrict__ jv, double *__restrict__ out,
+          const double *__restrict__ S)
+{
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 tl = tiles[t];
+        const ProbDev pd = P[tl.x];
+        if (!slot_active(S, pd.slot)) continue;
+        const double *Vj = V + (int64_t)jv[pd.slot] * vstride + pd.img;
+        for (int e = threadIdx.x; e < tl.z; e += blockDim.x) {
+            const int64_t o = tl.y + e;
+            out[pd.img + o] = Vj[o];
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Finalize: one CTA per problem.
 // ---------------------------------------------------------------------------
@@ -530,6 +548,13 @@ void launch_gm_setv(const ProbDev *P, const int4 *tiles, int ntiles, double *V, 
     if (ntiles <= 0) return;
     count_launches(1);
     k_gm_setv<<<grid_for(ntiles), 256, 0, st>>>(P, tiles, ntiles, V, vstride, ldp, j, jv, w, S);
+}
+void launch_gm_getv(const ProbDev *P, const int4 *tiles, int ntiles, const double *V, int64_t vstride,
+                    const int *jv, double *out, const double *S, cudaStream_t st)
+{
+    if (ntiles <= 0) return;
+    count_launches(1);
+    k_gm_getv<<<grid_for(ntiles), 256, 0, st>>>(P, tiles, ntiles, V, vstride, jv, out, S);
 }
 void launch_gm_scalar(int which, const GmArgs &a, cudaStream_t st)
 {

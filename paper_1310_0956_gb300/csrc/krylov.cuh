@@ -109,6 +109,9 @@ void launch_gm_combine(const ProbDev *P, const int4 *tiles, int ntiles, const do
 void launch_gm_setv(const ProbDev *P, const int4 *tiles, int ntiles, double *V, int64_t vstride,
                     int ldp, int j, const double *w, const double *S, cudaStream_t st,
                     const int *jv = nullptr);
+// out = v_{jv[slot]} for every active problem
+void launch_gm_getv(const ProbDev *P, const int4 *tiles, int ntiles, const double *V, int64_t vstride,
+                    const int *jv, double *out, const double *S, cudaStream_t st);
 // which: 0 = Arnoldi scalar step, 1 = solve H y = g, 2 = restart
 void launch_gm_scalar(int which, const GmArgs &a, cudaStream_t st);
 

@@ -315,7 +315,8 @@ def run_ours(args, rank, world, local):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "iters_mean": float(np.mean(iters)), "iters_max": int(np.max(iters)),
                        "all_converged": bool(all(s == 0 for s in statuses)),
-                       "plan_setup_s": setup_s},
+                       "plan_setup_s": setup_s,
+                       "launch_shapes_ctas_per_sm": dict(zip(("project", "backproject"), plan.tuning()))},
             "clocks": clocks,
             "e2e": {"value": e2e_val, "unit": "recon/s", "h2d_bytes_per_step": int(B * M * 4),
                     "d2h_bytes_per_step": int(B * N * 4)},

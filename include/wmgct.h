@@ -331,6 +331,16 @@ int32_t wmg_csr_apply(const wmg_csr *csr, int32_t count, const void *x, void *y,
  * default stream, synchronising) and cached. */
 int32_t wmg_plan_nnz(const wmg_plan *plan, int64_t *nnz);
 
+/* Launch shapes of the plan's projector and backprojector: CTAs per SM of
+ * their grid-stride launches (grid = min(tiles, SMs x value)). The library
+ * times 1, 2, 4, 8 and 16 whenever a plan's problem table changes
+ * (wmg_plan_create, a new count in a call, wmg_batch_create) and keeps the
+ * fastest; WMG_AUTOTUNE=0 in the environment keeps 8. Every shape gives
+ * bitwise the same results (each tile's arithmetic does not depend on the
+ * CTA that runs it). set: values in [1, 64]; kept until the table changes. */
+int32_t wmg_plan_get_tuning(const wmg_plan *plan, int32_t *project_ctas, int32_t *backproject_ctas);
+int32_t wmg_plan_set_tuning(wmg_plan *plan, int32_t project_ctas, int32_t backproject_ctas);
+
 /* Library-wide count of kernel launches since the last reset (all plans of
  * the process); reset != 0 zeroes the counter after reading it. */
 int64_t wmg_launch_count(int32_t reset);

@@ -95,6 +95,8 @@ _SIGNATURES = {
                          C.POINTER(wmg_solve_info), C.POINTER(_dbl), _vp]),
     "wmg_plan_nnz": (_i32, [_vp, C.POINTER(_i64)]),
     "wmg_launch_count": (_i64, [_i32]),
+    "wmg_plan_get_tuning": (_i32, [_vp, C.POINTER(_i32), C.POINTER(_i32)]),
+    "wmg_plan_set_tuning": (_i32, [_vp, _i32, _i32]),
     "wmg_profile_begin": (_i32, [_vp]),
     "wmg_profile_end": (_i32, [_vp, C.POINTER(wmg_profile_stats), _vp]),
     "wmg_project_noalloc": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp]),
@@ -241,6 +243,16 @@ def wmg_plan_nnz(plan) -> int:
     v = _i64()
     _check(lib().wmg_plan_nnz(plan, C.byref(v)))
     return v.value
+
+
+def wmg_plan_get_tuning(plan) -> tuple[int, int]:
+    a, b = _i32(), _i32()
+    _check(lib().wmg_plan_get_tuning(plan, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def wmg_plan_set_tuning(plan, project_ctas, backproject_ctas):
+    _check(lib().wmg_plan_set_tuning(plan, project_ctas, backproject_ctas))
 
 
 def wmg_launch_count(reset: bool = False) -> int:
@@ -406,6 +418,13 @@ class Plan:
 
     def nnz(self) -> int:
         return wmg_plan_nnz(self.handle)
+
+    def tuning(self, project_ctas=None, backproject_ctas=None) -> tuple[int, int]:
+        """Launch shapes (CTAs per SM) of the projector / backprojector;
+        sets them when both are given."""
+        if project_ctas is not None and backproject_ctas is not None:
+            wmg_plan_set_tuning(self.handle, project_ctas, backproject_ctas)
+        return wmg_plan_get_tuning(self.handle)
 
     def csr(self, transposed=False):
         """The plan's W (or W^T) stored as CSR: a StoredOperator."""

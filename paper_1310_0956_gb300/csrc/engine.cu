@@ -174,7 +174,9 @@ static int32_t ensure_count(wmg_plan *pl, int count, cudaStream_t st)
     }
     if (count == pl->cap) return WMG_OK;
     pl->pgeo.assign(count, 0);
-    return set_slots(pl, st);
+    int32_t rc = set_slots(pl, st);
+    if (rc) return rc;
+    return pl->prec == WMG_PREC_F64 ? autotune<double>(pl, pl->real, st) : autotune<float>(pl, pl->real, st);
 }
 
 bool ensure_pool(DevBuf &b, int64_t elems, size_t esz) { return b.ensure((size_t)elems * esz); }
@@ -205,7 +207,7 @@ template <class T>
 void project(wmg_plan *pl, const ProbSet &ps, const void *img, const void *imgT, void *sino,
                     double *part, const double *S, cudaStream_t st)
 {
-    PjArgs a{img, imgT, sino, part, S};
+    PjArgs a{ps.pj_ctas, img, imgT, sino, part, S};
     if (pl->profiling) prof_begin(pl, 0, ps.nprob, st);
     launch_project<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.proj.tiles.as<int4>(),
                       ps.proj.n, a, st);
@@ -216,10 +218,73 @@ template <class T>
 void backproject(wmg_plan *pl, const ProbSet &ps, BpArgs a, cudaStream_t st)
 {
     a.unit = pl->unit_bins ? 1 : 0;
+    a.ctas_per_sm = ps.bp_ctas;
     if (pl->profiling) prof_begin(pl, 1, ps.nprob, st);
     launch_backproject<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.bp.tiles.as<int4>(),
                           ps.bp.n, a, st);
     if (pl->profiling) prof_end(pl, st);
+}
+
+static bool autotune_enabled()
+{
+    static const bool on = [] {
+        const char *v = std::getenv("WMG_AUTOTUNE");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
+template <class T>
+int32_t autotune(wmg_plan *pl, ProbSet &ps, cudaStream_t st)
+{
+    ps.pj_ctas = ps.bp_ctas = 0;
+    if (!autotune_enabled() || ps.proj.n < num_sms() || pl->profiling) return WMG_OK;
+    int64_t VN = 0, VM = 0;
+    for (const ProbDev &pd : ps.h) {
+        if (pd.geom < 0) continue;
+        VN = std::max<int64_t>(VN, pd.img + pl->geos[pd.geom]->N);
+        VM = std::max<int64_t>(VM, pd.sino + pl->geos[pd.geom]->M);
+    }
+    DevBuf img, imgT, sino;
+    if (!img.ensure(VN * sizeof(T)) || !imgT.ensure(VN * sizeof(T)) || !sino.ensure(VM * sizeof(T)))
+        return WMG_OK;                                   // no room to tune: keep the default shapes
+    cudaMemsetAsync(img.p, 0, VN * sizeof(T), st);
+    cudaMemsetAsync(imgT.p, 0, VN * sizeof(T), st);
+    cudaMemsetAsync(sino.p, 0, VM * sizeof(T), st);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int opts[] = {1, 2, 4, 8, 16};
+    float best_p = 1e30f, best_b = 1e30f;
+    for (int c : opts) {
+        ps.pj_ctas = ps.bp_ctas = c;
+        for (int kind = 0; kind < 2; ++kind) {
+            float total = 0.f;
+            for (int rep = 0; rep < 4; ++rep) {
+                cudaEventRecord(e0, st);
+                if (kind == 0) {
+                    project<T>(pl, ps, img.p, imgT.p, sino.p, nullptr, nullptr, st);
+                } else {
+                    BpArgs a = bp_args(BP_STORE, sino.p, nullptr);
+                    a.out_op = img.p;
+                    backproject<T>(pl, ps, a, st);
+                }
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) total += ms;                // the first launch is a warm-up
+            }
+            if (kind == 0 && total < best_p) { best_p = total; pl->tuned_pj = c; }
+            if (kind == 1 && total < best_b) { best_b = total; pl->tuned_bp = c; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ps.pj_ctas = pl->tuned_pj;
+    ps.bp_ctas = pl->tuned_bp;
+    WMG_CUDA(cudaGetLastError());
+    return WMG_OK;
 }
 
 BpArgs bp_args(int epi, const void *sino, const double *S)
@@ -322,6 +387,8 @@ static ProbSet *band_set(wmg_plan *pl, int d, const std::vector<int> &nodes, con
         }
     build_tiles(pl, *ps);
     if (!upload_set(*ps, st)) return nullptr;
+    ps->pj_ctas = pl->real.pj_ctas;
+    ps->bp_ctas = pl->real.bp_ctas;
     ProbSet *raw = ps.get();
     pl->bands[key] = std::move(ps);
     return raw;
@@ -813,6 +880,27 @@ extern "C" int32_t wmg_plan_nnz(const wmg_plan *plan, int64_t *nnz)
 {
     if (!plan || !nnz) return fail(WMG_ERR_INVALID_ARG, "wmg_plan_nnz: bad arguments");
     return count_nnz(const_cast<wmg_plan *>(plan), 0, nullptr, nnz);
+    return WMG_OK;
+}
+
+extern "C" int32_t wmg_plan_get_tuning(const wmg_plan *plan, int32_t *project_ctas, int32_t *backproject_ctas)
+{
+    if (!plan) return fail(WMG_ERR_INVALID_ARG, "wmg_plan_get_tuning: plan is NULL");
+    if (project_ctas) *project_ctas = plan->real.pj_ctas > 0 ? plan->real.pj_ctas : 8;
+    if (backproject_ctas) *backproject_ctas = plan->real.bp_ctas > 0 ? plan->real.bp_ctas : 8;
+    return WMG_OK;
+}
+
+extern "C" int32_t wmg_plan_set_tuning(wmg_plan *plan, int32_t project_ctas, int32_t backproject_ctas)
+{
+    if (!plan || project_ctas < 1 || project_ctas > 64 || backproject_ctas < 1 || backproject_ctas > 64)
+        return fail(WMG_ERR_INVALID_ARG, "wmg_plan_set_tuning: bad arguments");
+    plan->real.pj_ctas = project_ctas;
+    plan->real.bp_ctas = backproject_ctas;
+    for (auto &kv : plan->bands) {
+        kv.second->pj_ctas = project_ctas;
+        kv.second->bp_ctas = backproject_ctas;
+    }
     return WMG_OK;
 }
 
@@ -1549,6 +1637,8 @@ extern "C" int32_t wmg_batch_create(const wmg_geom *gs, const wmg_opts *os, int3
         pl->pgeo[q] = gid[idx[q]];
     }
     if ((rc = set_slots(pl.get(), st))) return rc;
+    rc = pl->prec == WMG_PREC_F64 ? autotune<double>(pl.get(), pl->real, st) : autotune<float>(pl.get(), pl->real, st);
+    if (rc) return rc;
     WMG_CUDA(cudaStreamSynchronize(st));
     auto bt = std::make_unique<wmg_batch>();
     bt->plan = pl.release();

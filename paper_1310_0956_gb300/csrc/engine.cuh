@@ -105,6 +105,9 @@ struct ProbSet {
     DevBuf d;
     TileList proj, bp, haar, vimg, vsino;
     int haar_smem = 0;
+    // launch shapes of the projector / backprojector over this set's tiles
+    // (CTAs per SM; 0 = 8), chosen by autotune(); they do not change results
+    int pj_ctas = 0, bp_ctas = 0;
 };
 
 // One geometry of a plan with its device tables.
@@ -163,6 +166,7 @@ struct wmg_plan {
     // plan creation keeps every launch eager.
     cudaStream_t cap_stream = nullptr;
     bool use_graphs = wmg::graphs_default();
+    int tuned_pj = 8, tuned_bp = 8;     // last autotune result (CTAs per SM)
     ~wmg_plan()
     {
         if (cap_stream) cudaStreamDestroy(cap_stream);
@@ -196,6 +200,11 @@ struct Graph {
 };
 
 // ---- engine steps (engine.cu) ----------------------------------------------
+// Time the projector and backprojector over ps's tiles at 1, 2, 4, 8 and 16
+// CTAs per SM and keep the fastest (skipped when WMG_AUTOTUNE=0 in the
+// environment or when the set has fewer tiles than SMs).
+template <class T>
+int32_t autotune(wmg_plan *pl, ProbSet &ps, cudaStream_t st);
 void build_tiles(const wmg_plan *pl, ProbSet &ps);
 bool upload_set(ProbSet &ps, cudaStream_t st);
 bool ensure_pool(DevBuf &b, int64_t elems, size_t esz);

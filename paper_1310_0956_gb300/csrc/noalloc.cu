@@ -160,7 +160,7 @@ extern "C" int32_t wmg_project_noalloc(int32_t n, int32_t m, int32_t D, const fl
     // the transposed copy overwrites every element the projector reads, so
     // nothing has to be cleared between calls
     launch_transpose<float>(s->geom, s->prob, s->img_tiles, nimg, x, s->scratch_T, st);
-    PjArgs a{x, s->scratch_T, b, nullptr, nullptr};
+    PjArgs a{0, x, s->scratch_T, b, nullptr, nullptr};
     launch_project<float>(s->geom, s->prob, s->proj_tiles, nproj, a, st);
     WMG_CUDA(cudaGetLastError());
     return WMG_OK;

@@ -125,7 +125,7 @@ void launch_project(const GeomDev *G, const ProbDev *P, const int4 *tiles, int n
     if (ntiles <= 0) return;
     count_launches(1);
     constexpr int NW = 8;
-    const int grid = min(ntiles, num_sms() * 8);
+    const int grid = min(ntiles, num_sms() * (a.ctas_per_sm > 0 ? a.ctas_per_sm : 8));
     k_project<T, NW><<<grid, 32 * NW, 0, st>>>(G, P, tiles, ntiles, a);
 }
 
@@ -213,7 +213,7 @@ void launch_backproject(const GeomDev *G, const ProbDev *P, const int4 *tiles, i
     }
     if (ntiles <= 0) return;
     count_launches(1);
-    const int grid = min(ntiles, num_sms() * 8);
+    const int grid = min(ntiles, num_sms() * (a.ctas_per_sm > 0 ? a.ctas_per_sm : 8));
 #define WMG_BP_CASE(E) \
     case E: k_backproject<T, E><<<grid, 256, 0, st>>>(G, P, tiles, ntiles, a); break;
     switch (a.epi) {

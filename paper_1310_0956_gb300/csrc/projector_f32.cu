@@ -155,7 +155,7 @@ void launch_project_f32(const GeomDev *G, const ProbDev *P, const int4 *tiles, i
     if (ntiles <= 0) return;
     count_launches(1);
     constexpr int NW = 8;
-    const int grid = min(ntiles, num_sms() * 8);
+    const int grid = min(ntiles, num_sms() * (a.ctas_per_sm > 0 ? a.ctas_per_sm : 8));
     k_project_f32<NW><<<grid, 32 * NW, 0, st>>>(G, P, tiles, ntiles, a);
 }
 
@@ -257,7 +257,7 @@ void launch_backproject_f32(const GeomDev *G, const ProbDev *P, const int4 *tile
 {
     if (ntiles <= 0) return;
     count_launches(1);
-    const int grid = min(ntiles, num_sms() * 8);
+    const int grid = min(ntiles, num_sms() * (a.ctas_per_sm > 0 ? a.ctas_per_sm : 8));
 #define WMG_BPF(E)                                                                                  \
     case E:                                                                                         \
         if (unit) k_backproject_f32<E, true><<<grid, 256, 0, st>>>(G, P, tiles, ntiles, a);         \

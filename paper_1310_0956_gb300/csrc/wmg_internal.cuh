@@ -130,6 +130,7 @@ enum BpEpi : int {
 
 struct BpArgs {
     int epi;
+    int ctas_per_sm;         // grid = min(tiles, SMs x this) (0: 8); any value gives the same bits
     int unit;                // FP32 kernels: every geometry of the launch has unit bins
     const void *sino;        // T, sinogram input pool
     void *out_op;            // T image output (BP_STORE, BP_RESID, BP_APPLY_A)
@@ -143,6 +144,7 @@ struct BpArgs {
 };
 
 struct PjArgs {
+    int ctas_per_sm;         // grid = min(tiles, SMs x this) (0: 8); any value gives the same bits
     const void *img;         // T image pool (row-major)
     const void *imgT;        // T transposed image pool (for |sin| > |cos| angles)
     void *sino;              // T sinogram output pool

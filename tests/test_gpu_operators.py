@@ -124,3 +124,27 @@ def test_wmg_cycle(levels, nu1, nu2, cycle, hd, lam):
     z = host(plan.precond(dev(s.reshape(-1)))).reshape(2, -1)
     for i in range(2):
         assert relmax(z[i], ref.apply(s[i])) < 1e-10
+
+
+@pytest.mark.parametrize("prec", [wmg.PREC_F64, wmg.PREC_F32])
+def test_launch_shapes_do_not_change_results(prec):
+    """The autotuned grid shapes (CTAs per SM) give bitwise equal operators
+    and solves."""
+    dt = torch.float64 if prec == wmg.PREC_F64 else torch.float32
+    n, m, D = 64, 36, 91
+    plan = wmg.Plan(n, m, D, levels=3, nu1=1, nu2=1, hybrid_depth=1, cycle=wmg.CYCLE_HYBRID, precision=prec)
+    x = torch.tensor(np.stack([S.phantom(n, 6, S.seed_for(7, i)).reshape(-1) for i in range(8)]).reshape(-1),
+                     dtype=dt, device="cuda")
+    plan.project(x)                      # fixes the problem count (the autotune runs here)
+    outs = []
+    for shape in ((1, 1), (16, 16), (3, 5)):
+        plan.tuning(*shape)
+        b = plan.project(x)
+        assert plan.tuning() == shape
+        y = plan.backproject(b)
+        xs, _, _, _ = plan.solve(b, wmg.SOLVER_GMRES, True, 8, 0.0, 20)
+        torch.cuda.synchronize()
+        outs.append((b.clone(), y.clone(), xs.clone()))
+    for o in outs[1:]:
+        for a_, b_ in zip(outs[0], o):
+            assert torch.equal(a_, b_)

@@ -310,7 +310,7 @@ def run_ours(args, rank, world, local):
             "data": "synthetic",
             "config": {"workload": "256x256_180ang_363det_noise1pct", "batch_per_gpu": B,
                        "solver": f"WMG-GMRES(20), hybrid cycle depth {HYB}, nu1=nu2={NU1}", "levels": LEVELS,
-                       "precision": "fp32 operator, fp64 Krylov vectors/reductions/leaf solves",
+                       "precision": "fp32 operator and leaf solves, fp64 Krylov vectors/reductions/Gram-Schmidt",
                        "rtol": RTOL, "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "iters_mean": float(np.mean(iters)), "iters_max": int(np.max(iters)),
@@ -455,7 +455,7 @@ def batched_leg(args, dev) -> dict:
         "recon_per_s": len(probs) / t, "ms_per_batch": t * 1e3,
         "solver": f"WMG-CGLS (PCG on the normal equations), additive cycle, nu1=nu2={NU1}, rtol {RTOL:g}",
         "lambda": f"lambda = {SERVING_EPS:g} * m / n",
-        "precision": "fp32 operator, fp64 Krylov/leaf solves",
+        "precision": "fp32 operator and leaf solves, fp64 Krylov",
         "iters_mean": float(np.mean([i[0] for i in infos])), "iters_max": int(max(i[0] for i in infos)),
         "all_converged": bool(all(i[1] == 0 for i in infos)),
         "setup_s": setup, "timing": "host clock around the synchronising batch solve, mean of 3",

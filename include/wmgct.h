@@ -223,7 +223,7 @@ int32_t wmg_batch_solve(wmg_batch *batch, int32_t solver, int32_t preconditioned
  * Memory. hbm_budget bytes in total: state_bytes (0: half) are taken at
  * creation as the state pools, sized for sino_ratio (0: 4) sinogram elements
  * per image element; the rest holds geometry setups (trig tables, D~^-1,
- * SIRT scalings, leaf inverses K * P^2 doubles), cached by geometry and
+ * SIRT scalings, leaf inverses K * P^2 values of the plan precision), cached by geometry and
  * evicted least-recently-used when no admitted or queued request uses them.
  * Footprint of a request: (restart + 11) * 8 + 2 s bytes per pixel and 2 s
  * bytes per ray (s = 8 for F64, 4 for F32), more with hybrid depth h >= 1

@@ -483,7 +483,8 @@ static int32_t coarse(wmg_plan *pl, int d, const std::vector<int> &nodes, const 
         TileList *lt = leaf_tiles(pl, d, nodes, done, st);
         if (!lt) return fail(WMG_ERR_OOM, "leaf tables");
         launch_leaf_apply(pl->d_geom.as<GeomDev>(), pl->real.d.as<ProbDev>(), lt->tiles.as<int4>(),
-                          lt->n, Cb.as<double>(), Eb.as<double>(), 0, pl->S.as<double>(), st);
+                          lt->n, Cb.as<double>(), Eb.as<double>(), 0, pl->S.as<double>(), pl->prec == WMG_PREC_F32,
+                          st);
     }
     if (deeper.empty()) return WMG_OK;
     std::vector<int> lls, rests;
@@ -802,11 +803,11 @@ int32_t setup_geometry(wmg_plan *pl, int gi, cudaStream_t st)
     int32_t rc = upload_geoms(pl, st);
     if (rc) return rc;
     if (!G.has_wmg) return WMG_OK;
-    if (!G.leafinv.ensure((size_t)G.g.K * G.g.P * G.g.P * sizeof(double)))
+    if (!G.leafinv.ensure((size_t)G.g.K * G.g.P * G.g.P * sizeof(T)))
         return fail(WMG_ERR_OOM, "leaf inverse allocation failed");
-    G.g.leafinv = G.leafinv.as<double>();
+    G.g.leafinv = G.leafinv.p;
     if ((rc = upload_geoms(pl, st))) return rc;
-    rc = build_leaf_inverses(G.g, pl->d_geom.as<GeomDev>() + gi, G.leafinv.as<double>(), sizeof(T) == 4, st);
+    rc = build_leaf_inverses(G.g, pl->d_geom.as<GeomDev>() + gi, G.leafinv.p, sizeof(T) == 4, st);
     if (rc) return rc;
     WMG_CUDA(cudaGetLastError());
     return WMG_OK;
@@ -1045,12 +1046,8 @@ extern "C" int32_t wmg_leaf_inverse(wmg_plan *pl, int64_t k, void *out, void *st
     const Geo &G = *pl->geos[0];
     const int64_t PP = (int64_t)G.g.P * G.g.P;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (pl->prec == WMG_PREC_F64)
-        WMG_CUDA(cudaMemcpyAsync(out, G.leafinv.as<double>() + k * PP, PP * sizeof(double),
-                                 cudaMemcpyDeviceToDevice, st));
-    else
-        count_launches(1), k_to_f32<<<num_sms(), 256, 0, st>>>(G.leafinv.as<double>() + k * PP,
-                                                               static_cast<float *>(out), PP);
+    WMG_CUDA(cudaMemcpyAsync(out, static_cast<const char *>(G.leafinv.p) + k * PP * pl->esz, PP * pl->esz,
+                             cudaMemcpyDeviceToDevice, st));
     WMG_CUDA(cudaGetLastError());
     return WMG_OK;
 }

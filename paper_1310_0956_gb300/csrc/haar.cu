@@ -217,7 +217,7 @@ k_leaf_apply(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
         const int4 tl = tiles[t];
         const GeomDev &g = G[P[tl.x].geom];
         const int Pn = g.P, k = tl.y;
-        const T *__restrict__ Dk = g.leafinv + (int64_t)k * Pn * Pn;
+        const T *__restrict__ Dk = static_cast<const T *>(g.leafinv) + (int64_t)k * Pn * Pn;
         for (int pb = 0; pb < tl.z; pb += NPB) {
             const int np = min(NPB, tl.z - pb);
             for (int q = threadIdx.x; q < NPB * Pn; q += blockDim.x) {
@@ -256,11 +256,74 @@ k_leaf_apply(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
     }
 }
 
+// FP32 leaf solves (F32 plans). Work item = (tile, group of NPB problems of
+// its run): blockIdx.y selects the group, so the problems of a long run are
+// spread over CTAs; thread i forms row i of D_k^{-1} [c_1 .. c_NPB] reading
+// column i of the symmetric inverse (consecutive threads, consecutive
+// addresses), the coefficients broadcast from shared memory, FP32 sums of the
+// P products, results added to / stored in FP64.
+template <int NPB>
+__global__ void __launch_bounds__(256)
+k_leaf_apply32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
+               const int4 *__restrict__ tiles, int ntiles, const double *__restrict__ C,
+               double *__restrict__ E, int accumulate, const double *__restrict__ S)
+{
+    __shared__ float cb[NPB][256];
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 tl = tiles[t];
+        const GeomDev &g = G[P[tl.x].geom];
+        const int Pn = g.P, k = tl.y;
+        const float *__restrict__ Dk = static_cast<const float *>(g.leafinv) + (int64_t)k * Pn * Pn;
+      for (int pb = blockIdx.y * NPB; pb < tl.z; pb += gridDim.y * NPB) {   // CTA-uniform bounds
+        const int np = min(NPB, tl.z - pb);
+        for (int q = threadIdx.x; q < NPB * Pn; q += blockDim.x) {
+            const int pi = q / Pn, j = q - pi * Pn;
+            float v = 0.f;
+            if (pi < np) {
+                const ProbDev pd = P[tl.x + pb + pi];
+                if (slot_active(S, pd.slot)) v = (float)C[pd.coef + (int64_t)k * Pn + j];
+            }
+            cb[pi][j] = v;
+        }
+        __syncthreads();
+        const int i = threadIdx.x;
+        if (i < Pn) {
+            float acc[NPB];
+#pragma unroll
+            for (int u = 0; u < NPB; ++u) acc[u] = 0.f;
+#pragma unroll 4
+            for (int j = 0; j < Pn; ++j) {
+                const float d = __ldg(Dk + (int64_t)j * Pn + i);
+#pragma unroll
+                for (int u = 0; u < NPB; ++u) acc[u] = __fmaf_rn(d, cb[u][j], acc[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < NPB; ++u) {
+                if (u < np) {
+                    const ProbDev pd = P[tl.x + pb + u];
+                    if (!slot_active(S, pd.slot)) continue;
+                    double *e = E + pd.coef + (int64_t)k * Pn + i;
+                    *e = accumulate ? *e + (double)acc[u] : (double)acc[u];
+                }
+            }
+        }
+        __syncthreads();
+      }
+    }
+}
+
 void launch_leaf_apply(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
-                       const double *C, double *E, int accumulate, const double *S, cudaStream_t st)
+                       const double *C, double *E, int accumulate, const double *S, bool fp32,
+                       cudaStream_t st)
 {
     if (ntiles <= 0) return;
     count_launches(1);
+    if (fp32) {
+        // 4 CTAs share each tile's run of problems (groups of 16 strided by 64)
+        const dim3 grid(min(ntiles, num_sms() * 8), 4);
+        k_leaf_apply32<16><<<grid, 256, 0, st>>>(G, P, tiles, ntiles, C, E, accumulate, S);
+        return;
+    }
     const int grid = min(ntiles, num_sms() * 8);
     k_leaf_apply<4><<<grid, 256, 0, st>>>(G, P, tiles, ntiles, C, E, accumulate, S);
 }

@@ -343,7 +343,7 @@ int64_t geo_bytes(const wmg_geom &g, const wmg_opts &o, size_t esz)
     if (o.levels >= 1) {
         const int L = o.levels - 1;
         const int64_t nc = g.n >> L, P = nc * nc, K = (int64_t)1 << (2 * L);
-        b += K * P * P * (int64_t)sizeof(double);
+        b += K * P * P * (int64_t)esz;                     // leaf inverses in the plan precision
     }
     return b;
 }

@@ -380,8 +380,9 @@ k_leaf_invert(const GeomDev *__restrict__ Gd, const double *__restrict__ Dacc, d
 }
 
 // Host driver: assembles, factorises and inverts every leaf of one geometry.
-// `leafinv_out` receives K*P*P doubles. `fp32`: profiles and pair sums in
-// FP32 (F32 plans), else FP64. Returns WMG_OK or an error.
+// `fp32` (F32 plans): profiles and pair sums in FP32 and the inverses stored
+// as K*P*P floats in `leafinv_out`; else FP64 throughout and K*P*P doubles.
+// The Cholesky factorisation and the triangular solves are FP64 in both.
 template <class TG>
 static int32_t assemble(const GeomDev &gh, const GeomDev *gd, double *Dacc, cudaStream_t st)
 {
@@ -446,7 +447,7 @@ static int32_t assemble(const GeomDev &gh, const GeomDev *gd, double *Dacc, cuda
     return WMG_OK;
 }
 
-int32_t build_leaf_inverses(const GeomDev &gh, const GeomDev *gd, double *leafinv_out, bool fp32,
+int32_t build_leaf_inverses(const GeomDev &gh, const GeomDev *gd, void *leafinv_out, bool fp32,
                             cudaStream_t st)
 {
     const int P = gh.P, K = gh.K;
@@ -468,7 +469,8 @@ int32_t build_leaf_inverses(const GeomDev &gh, const GeomDev *gd, double *leafin
     int32_t rc = fp32 ? assemble<float>(gh, gd, Dacc, st) : assemble<double>(gh, gd, Dacc, st);
     if (rc) { cleanup(); return rc; }
     count_launches(1);
-    k_leaf_invert<double><<<inv_ctas, 256, 0, st>>>(gd, Dacc, A, Y, leafinv_out, status);
+    if (fp32) k_leaf_invert<float><<<inv_ctas, 256, 0, st>>>(gd, Dacc, A, Y, static_cast<float *>(leafinv_out), status);
+    else k_leaf_invert<double><<<inv_ctas, 256, 0, st>>>(gd, Dacc, A, Y, static_cast<double *>(leafinv_out), status);
     std::vector<int> hs(K);
     cudaMemcpyAsync(hs.data(), status, (size_t)K * sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);

@@ -50,7 +50,7 @@ struct GeomDev {
     const float4 *csx;       // (c_hi, c_lo, s_hi, s_lo): c_hi = c rounded to a
                              // multiple of 2^-12, c_lo = c - c_hi in FP32
     const void *dinv;        // N: 1/D~ (0 where D~ = 0), operator precision
-    const double *leafinv;   // K*P*P: leaf inverses, FP64
+    const void *leafinv;     // K*P*P: leaf inverses (FP64 for F64 plans, FP32 for F32 plans)
     const void *sirtR;       // M: 1/row sums (0 if empty)
     const void *sirtC;       // N: 1/column sums (0 if empty)
     const AngleF *angf;      // m per-angle constants (FP32 kernels)
@@ -195,14 +195,16 @@ template <class TIn, class TOut>
 void launch_haar_synthesis(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
                            int smem_elems, const HaarArgs &a, cudaStream_t st);
 
-// Leaf solves E[k] = Dinv_k C[k] for the problems of a group (haar.cu), FP64.
-// accumulate = 1 adds into E.
+// Leaf solves E[k] = Dinv_k C[k] for the problems of a group (haar.cu):
+// FP64 inverses and arithmetic (fp32 = false) or FP32 inverses and
+// arithmetic (F32 plans); C and E are FP64 in both. accumulate = 1 adds into E.
 void launch_leaf_apply(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
-                       const double *C, double *E, int accumulate, const double *S, cudaStream_t st);
+                       const double *C, double *E, int accumulate, const double *S, bool fp32,
+                       cudaStream_t st);
 
 // Setup (setup.cu).
 // fp32: profiles and pair sums in FP32 (FP64 accumulation over angles).
-int32_t build_leaf_inverses(const GeomDev &g_host, const GeomDev *g_dev, double *leafinv_out, bool fp32,
+int32_t build_leaf_inverses(const GeomDev &g_host, const GeomDev *g_dev, void *leafinv_out, bool fp32,
                             cudaStream_t st);
 
 // Elementwise / reduction kernels (krylov.cu), all FP64 Krylov state.

@@ -333,7 +333,7 @@ int32_t wmg_plan_nnz(const wmg_plan *plan, int64_t *nnz);
 
 /* Launch shapes of the plan's projector and backprojector: CTAs per SM of
  * their grid-stride launches (grid = min(tiles, SMs x value)). The library
- * times 1, 2, 4, 8 and 16 whenever a plan's problem table changes
+ * times 1, 2, 4, 8 and 16 (F32 plans) whenever a plan's problem table changes
  * (wmg_plan_create, a new count in a call, wmg_batch_create) and keeps the
  * fastest; WMG_AUTOTUNE=0 in the environment keeps 8. Every shape gives
  * bitwise the same results (each tile's arithmetic does not depend on the

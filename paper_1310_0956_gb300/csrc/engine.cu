@@ -95,7 +95,25 @@ static int haar_width(const GeomDev &g)
 void build_tiles(const wmg_plan *pl, ProbSet &ps)
 {
     ps.proj.h.clear(); ps.bp.h.clear(); ps.haar.h.clear(); ps.vimg.h.clear(); ps.vsino.h.clear();
+    ps.projg.h.clear(); ps.proj1.h.clear();
     ps.haar_smem = 0;
+    // FP32 projector tiles: runs of consecutive problems of one geometry cut
+    // into full groups of kProjGroup images (one tile per group, angle and
+    // ray block); the problems left over get one-image tiles
+    for (int q = 0; q < ps.nprob;) {
+        if (ps.h[q].geom < 0) { ++q; continue; }
+        int e = q + 1;
+        while (e < ps.nprob && ps.h[e].geom == ps.h[q].geom) ++e;
+        const GeomDev &g = pl->geos[ps.h[q].geom]->g;
+        int f = q;
+        for (; f + kProjGroup <= e; f += kProjGroup)
+            for (int a = 0; a < g.m; ++a)
+                for (int k0 = 0; k0 < g.D; k0 += 32) ps.projg.h.push_back(make_int4(f, a, k0, kProjGroup));
+        for (; f < e; ++f)
+            for (int a = 0; a < g.m; ++a)
+                for (int k0 = 0; k0 < g.D; k0 += 32) ps.proj1.h.push_back(make_int4(f, a, k0, 1));
+        q = e;
+    }
     for (int q = 0; q < ps.nprob; ++q) {
         if (ps.h[q].geom < 0) continue;          // an empty server slot: no tiles
         const Geo &G = *pl->geos[ps.h[q].geom];
@@ -120,6 +138,7 @@ bool upload_set(ProbSet &ps, cudaStream_t st)
     if (!ps.d.ensure(std::max<size_t>(1, ps.h.size()) * sizeof(ProbDev))) return false;
     cudaMemcpyAsync(ps.d.p, ps.h.data(), ps.h.size() * sizeof(ProbDev), cudaMemcpyHostToDevice, st);
     return ps.proj.upload(ps.nprob, st) && ps.bp.upload(ps.nprob, st) && ps.haar.upload(ps.nprob, st) &&
+           ps.projg.upload(ps.nprob, st) && ps.proj1.upload(ps.nprob, st) &&
            ps.vimg.upload(ps.nprob, st) && ps.vsino.upload(ps.nprob, st);
 }
 
@@ -207,10 +226,20 @@ template <class T>
 void project(wmg_plan *pl, const ProbSet &ps, const void *img, const void *imgT, void *sino,
                     double *part, const double *S, cudaStream_t st)
 {
-    PjArgs a{ps.pj_ctas, img, imgT, sino, part, S};
+    PjArgs a{ps.pj_ctas, img, imgT, sino, part, S, ps.proj.tb.as<int>(), 1};
     if (pl->profiling) prof_begin(pl, 0, ps.nprob, st);
-    launch_project<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.proj.tiles.as<int4>(),
-                      ps.proj.n, a, st);
+    if (sizeof(T) == 4) {
+        // FP32: groups of kProjGroup images share the weights; the rest run
+        // one image per tile (the same per-image arithmetic in both)
+        a.group = kProjGroup;
+        launch_project<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.projg.tiles.as<int4>(), ps.projg.n, a,
+                          st);
+        a.group = 1;
+        launch_project<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.proj1.tiles.as<int4>(), ps.proj1.n, a,
+                          st);
+    } else {
+        launch_project<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.proj.tiles.as<int4>(), ps.proj.n, a, st);
+    }
     if (pl->profiling) prof_end(pl, st);
 }
 
@@ -219,9 +248,9 @@ void backproject(wmg_plan *pl, const ProbSet &ps, BpArgs a, cudaStream_t st)
 {
     a.unit = pl->unit_bins ? 1 : 0;
     a.ctas_per_sm = ps.bp_ctas;
+    a.part_base = ps.bp.tb.as<int>();
     if (pl->profiling) prof_begin(pl, 1, ps.nprob, st);
-    launch_backproject<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.bp.tiles.as<int4>(),
-                          ps.bp.n, a, st);
+    launch_backproject<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.bp.tiles.as<int4>(), ps.bp.n, a, st);
     if (pl->profiling) prof_end(pl, st);
 }
 
@@ -238,7 +267,9 @@ template <class T>
 int32_t autotune(wmg_plan *pl, ProbSet &ps, cudaStream_t st)
 {
     ps.pj_ctas = ps.bp_ctas = 0;
-    if (!autotune_enabled() || ps.proj.n < num_sms() || pl->profiling) return WMG_OK;
+    // FP32 plans only: the FP64 operators are the parity path, and timing
+    // them would cost more than it can save
+    if (!autotune_enabled() || sizeof(T) != 4 || ps.proj.n < num_sms() || pl->profiling) return WMG_OK;
     int64_t VN = 0, VM = 0;
     for (const ProbDev &pd : ps.h) {
         if (pd.geom < 0) continue;

@@ -104,6 +104,10 @@ struct ProbSet {
     std::vector<ProbDev> h;
     DevBuf d;
     TileList proj, bp, haar, vimg, vsino;
+    // FP32 projector tiles ({first problem, angle, first ray, images}): full
+    // groups of kProjGroup consecutive same-geometry problems, and one-image
+    // tiles for the problems left over
+    TileList projg, proj1;
     int haar_smem = 0;
     // launch shapes of the projector / backprojector over this set's tiles
     // (CTAs per SM; 0 = 8), chosen by autotune(); they do not change results
@@ -201,8 +205,8 @@ struct Graph {
 
 // ---- engine steps (engine.cu) ----------------------------------------------
 // Time the projector and backprojector over ps's tiles at 1, 2, 4, 8 and 16
-// CTAs per SM and keep the fastest (skipped when WMG_AUTOTUNE=0 in the
-// environment or when the set has fewer tiles than SMs).
+// CTAs per SM and keep the fastest (F32 plans; skipped when WMG_AUTOTUNE=0 in
+// the environment or when the set has fewer tiles than SMs).
 template <class T>
 int32_t autotune(wmg_plan *pl, ProbSet &ps, cudaStream_t st);
 void build_tiles(const wmg_plan *pl, ProbSet &ps);

@@ -36,29 +36,49 @@ __device__ __forceinline__ float chord_n(float wa, float wb, float d)
 }
 
 // ---------------------------------------------------------------------------
-// Forward: tile = {prob, angle, first ray, 0}; lane = ray, warps take every
-// NW-th row of the rays' common row range.
+// Forward: tile = {first problem, angle, first ray, images}: `images`
+// consecutive problems of one geometry (0 or 1: one problem). Lane = ray,
+// warps take every NW-th row of the rays' common row range. The candidate
+// pixels and their weights are computed once per row and applied to every
+// image of the tile; each image keeps its own compensated sums in the same
+// order whatever the tile holds, so a problem gets the same bits alone and
+// grouped with others.
 // ---------------------------------------------------------------------------
-template <int NW>
-__global__ void __launch_bounds__(32 * NW, 4)
+template <int NW, int IB>
+__global__ void __launch_bounds__(32 * NW, 2)
 k_project_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
               const int4 *__restrict__ tiles, int ntiles, PjArgs a)
 {
-    __shared__ float red_s[NW][32], red_c[NW][32];
+    __shared__ float red_s[NW][IB][32], red_c[NW][IB][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 tl = tiles[t];
-        const ProbDev pd = P[tl.x];
-        if (!slot_active(a.S, pd.slot)) continue;
-        const GeomDev &g = G[pd.geom];
+        const int nimg = min(IB, max(1, tl.w));
+        const ProbDev p0 = P[tl.x];
+        const GeomDev &g = G[p0.geom];
         const int n = g.n, D = g.D, ang = tl.y, k = tl.z + lane;
-        const bool valid = k < D;
         const AngleF A = g.angf[ang];
         const int flags = __float_as_int(A.flags);
-        const bool steep = flags & 1, axis = flags & 2;
+        const bool steep = flags & 1;
+        const float *__restrict__ base = static_cast<const float *>(steep ? a.img : a.imgT);
+        const float *src[IB];
+        bool act[IB];
+        bool any = false;
+#pragma unroll
+        for (int b = 0; b < IB; ++b) {
+            act[b] = false;
+            src[b] = base;
+            if (b < nimg) {
+                const ProbDev pb = P[tl.x + b];
+                act[b] = slot_active(a.S, pb.slot);
+                src[b] = base + pb.img;
+            }
+            any |= act[b];
+        }
+        if (!any) continue;                                        // CTA-uniform
+        const bool valid = k < D;
         const float cc_hi = steep ? A.chi : A.shi, cc_lo = steep ? A.clo : A.slo;
         const float ss_hi = steep ? A.shi : A.chi, ss_lo = steep ? A.slo : A.clo;
-        const float *__restrict__ src = static_cast<const float *>(steep ? a.img : a.imgT) + pd.img;
         const float half_n = 0.5f * (float)n;
         const float tk = __fmaf_rn((float)k - g.hDf, g.dtf, g.t0f);
         // rows the lane's ray can touch (image x-range widened by one pixel)
@@ -75,11 +95,12 @@ k_project_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
         }
         lo = warp_min(lo);
         hi = warp_max(hi);
-        float s = 0.f, c = 0.f;                        // compensated sum
+        float s[IB], c[IB];                            // compensated sums per image
+#pragma unroll
+        for (int b = 0; b < IB; ++b) { s[b] = 0.f; c[b] = 0.f; }
         const int nrows = hi - lo + 1;
         if (nrows > 0) {
-            // warp w takes rows lo + w + NW*j; R consecutive ones per step,
-            // their 2R loads issued before any is used
+            // warp w takes rows lo + w + NW*j, R consecutive ones per step
             constexpr int R = 4;
             const int iy0 = lo + w;
             const float dy = (float)NW;
@@ -93,18 +114,20 @@ k_project_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
             // nonzero weight is one of them whatever the rounding of xs.
             const float off = half_n - 0.5f;
             const int nmine = (nrows - w + NW - 1) / NW;       // rows of this warp
-            const float *__restrict__ row = src + (int64_t)iy0 * n;
-            const int64_t drow = (int64_t)NW * n;
+            int roff = iy0 * n;
+            const int drow = NW * n;
             const float wa = A.wa, wb = A.wb, ccf = A.cc;
             for (int j = 0; j < nmine; j += R) {
-                float v0[R], v1[R], w0[R], w1[R];
+                int idx[R];
+                bool ok0[R], ok1[R];
+                float w0[R], w1[R];
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const bool live = valid && (j + r < nmine);
                     const int ix0 = __float2int_rd(xs + off);
-                    const float *rp = row + ix0;
-                    v0[r] = (live && (unsigned)ix0 < (unsigned)n) ? __ldg(rp) : 0.f;
-                    v1[r] = (live && (unsigned)(ix0 + 1) < (unsigned)n) ? __ldg(rp + 1) : 0.f;
+                    idx[r] = roff + ix0;
+                    ok0[r] = live && (unsigned)ix0 < (unsigned)n;
+                    ok1[r] = live && (unsigned)(ix0 + 1) < (unsigned)n;
                     const float xc = (float)ix0 + 0.5f - half_n;
                     const float dl0 = __fmaf_rn(-xc, cc_hi, brow) - __fmaf_rn(xc, cc_lo, cy);
                     w0[r] = chord_n(wa, wb, fabsf(dl0));
@@ -112,37 +135,54 @@ k_project_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
                     brow += dbrow;
                     cy += dcy;
                     xs += dxs;
-                    row += drow;
+                    roff += drow;
                 }
 #pragma unroll
-                for (int r = 0; r < R; r += 2) {
-                    const float rs = __fmaf_rn(w0[r], v0[r], __fmaf_rn(w1[r], v1[r],
-                                     __fmaf_rn(w0[r + 1], v0[r + 1], w1[r + 1] * v1[r + 1])));
-                    const float y = rs - c;                    // Kahan step
-                    const float tt = s + y;
-                    c = (tt - s) - y;
-                    s = tt;
+                for (int b = 0; b < IB; ++b) {
+                    if (!act[b]) continue;                      // uniform across the CTA
+                    float v0[R], v1[R];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        v0[r] = ok0[r] ? __ldg(src[b] + idx[r]) : 0.f;
+                        v1[r] = ok1[r] ? __ldg(src[b] + idx[r] + 1) : 0.f;
+                    }
+#pragma unroll
+                    for (int r = 0; r < R; r += 2) {
+                        const float rs = __fmaf_rn(w0[r], v0[r], __fmaf_rn(w1[r], v1[r],
+                                         __fmaf_rn(w0[r + 1], v0[r + 1], w1[r + 1] * v1[r + 1])));
+                        const float y = rs - c[b];                 // Kahan step
+                        const float tt = s[b] + y;
+                        c[b] = (tt - s[b]) - y;
+                        s[b] = tt;
+                    }
                 }
             }
         }
-        red_s[w][lane] = s;
-        red_c[w][lane] = c;
+#pragma unroll
+        for (int b = 0; b < IB; ++b) {
+            red_s[w][b][lane] = s[b];
+            red_c[w][b][lane] = c[b];
+        }
         __syncthreads();
-        if (w == 0) {
+        if (w < IB && act[w]) {                                  // warp w finishes image w
+            const int b = w;
             float S = 0.f, Cc = 0.f;
 #pragma unroll
             for (int i = 0; i < NW; ++i) {
-                const float y = (red_s[i][lane] - red_c[i][lane]) - Cc;
+                const float y = (red_s[i][b][lane] - red_c[i][b][lane]) - Cc;
                 const float tt = S + y;
                 Cc = (tt - S) - y;
                 S = tt;
             }
+            const ProbDev pb = P[tl.x + b];
             const float v = (S - Cc) * (A.lmax * g.hf);
-            if (valid) static_cast<float *>(a.sino)[pd.sino + (int64_t)ang * D + k] = v;
+            if (valid) static_cast<float *>(a.sino)[pb.sino + (int64_t)ang * D + k] = v;
             if (a.part) {
                 double q2 = valid ? (double)v * (double)v : 0.0;
                 q2 = warp_sum_fixed(q2);
-                if (lane == 0) a.part[t] = q2;
+                // the problem's partial of this (angle, ray block), at the
+                // index its one-image tile list gives it
+                if (lane == 0) a.part[a.part_base[tl.x + b] + ang * ((D + 31) / 32) + tl.z / 32] = q2;
             }
         }
         __syncthreads();
@@ -156,96 +196,146 @@ void launch_project_f32(const GeomDev *G, const ProbDev *P, const int4 *tiles, i
     count_launches(1);
     constexpr int NW = 8;
     const int grid = min(ntiles, num_sms() * (a.ctas_per_sm > 0 ? a.ctas_per_sm : 8));
-    k_project_f32<NW><<<grid, 32 * NW, 0, st>>>(G, P, tiles, ntiles, a);
+    if (a.group == kProjGroup) k_project_f32<NW, kProjGroup><<<grid, 32 * NW, 0, st>>>(G, P, tiles, ntiles, a);
+    else k_project_f32<NW, 1><<<grid, 32 * NW, 0, st>>>(G, P, tiles, ntiles, a);
 }
 
 // ---------------------------------------------------------------------------
-// Backward: tile = {prob, iy0, ix0, 0} of 32 x 32 pixels, thread = one column
-// and 4 rows 8 apart. Geometries with unit bins (g.unit) take the two-bin
-// path, the others the general one; ALL_UNIT (every geometry of the launch
-// has unit bins) compiles the general path out. The choice depends on the
-// tile's own geometry only, so a problem gets the same bits in any batch.
+// Backward: tile = {first problem, iy0, ix0, images} of 32 x 32 pixels of
+// `images` consecutive problems of one geometry (the launcher uses one image
+// per tile); thread = one column and 4 rows 8 apart. The bins and weights of
+// a pixel and angle are computed once for the tile's images. Geometries with
+// unit bins (g.unit) take the two-bin path, the others the general one;
+// ALL_UNIT (every geometry of the launch has unit bins) compiles the general
+// path out.
 // ---------------------------------------------------------------------------
-template <int EPI, bool ALL_UNIT>
-__global__ void __launch_bounds__(256)
+template <int EPI, bool ALL_UNIT, int IB>
+__global__ void __launch_bounds__(256, 2)
 k_backproject_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
                   const int4 *__restrict__ tiles, int ntiles, BpArgs a)
 {
-    __shared__ double red[8];
+    __shared__ double red[IB][8];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 tl = tiles[t];
-        const ProbDev pd = P[tl.x];
-        if (!slot_active(a.S, pd.slot)) continue;
-        const GeomDev &g = G[pd.geom];
+        const int nimg = min(IB, max(1, tl.w));
+        const ProbDev p0 = P[tl.x];
+        const float *sg[IB];
+        bool act[IB];
+        bool any = false;
+#pragma unroll
+        for (int b = 0; b < IB; ++b) {
+            act[b] = false;
+            sg[b] = static_cast<const float *>(a.sino);
+            if (b < nimg) {
+                const ProbDev pb = P[tl.x + b];
+                act[b] = slot_active(a.S, pb.slot);
+                sg[b] = static_cast<const float *>(a.sino) + pb.sino;
+            }
+            any |= act[b];
+        }
+        if (!any) continue;                                        // CTA-uniform
+        const GeomDev &g = G[p0.geom];
         const int n = g.n, m = g.m, D = g.D;
         const int ix = tl.z + tx;
         const float half_n = 0.5f * (float)n;
         const float xo = (float)ix + 0.5f - half_n;
         const float yo0 = (float)(tl.y + ty) + 0.5f - half_n;
-        const float *__restrict__ sg = static_cast<const float *>(a.sino) + pd.sino;
         const float hD = g.hDf, dt = g.dtf, t0 = g.t0f, inv_dt = 1.f / g.dtf;
         const bool unit = ALL_UNIT || g.unit;
-        float s[4] = {0.f, 0.f, 0.f, 0.f}, cmp[4] = {0.f, 0.f, 0.f, 0.f};
+        float s[IB][4], cmp[IB][4];
+#pragma unroll
+        for (int b = 0; b < IB; ++b)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) { s[b][r] = 0.f; cmp[b][r] = 0.f; }
         for (int ang = 0; ang < m; ++ang) {
             const AngleF A = g.angf[ang];
             const bool axis = __float_as_int(A.flags) & 2;
-            const float *__restrict__ row = sg + (int64_t)ang * D;
+            const int64_t roff = (int64_t)ang * D;
             float ph = __fmaf_rn(xo, A.chi, yo0 * A.shi);        // exact head of tau
             float pc = __fmaf_rn(xo, A.clo, yo0 * A.slo);        // rounded tail
             const float dph = 8.f * A.shi, dpc = 8.f * A.slo;
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                float rs;
                 if (unit) {
                     // the two bins nearest tau (support half-width <= sqrt(1/2))
                     const int k0 = __float2int_rd((ph + pc) - t0 + hD);
                     const float tk = (float)k0 - hD + t0;
                     const float d0 = (tk - ph) - pc;
                     const float w0 = chord_n(A.wa, A.wb, fabsf(d0)), w1 = chord_n(A.wa, A.wb, fabsf(d0 + 1.f));
-                    const float v0 = (unsigned)k0 < (unsigned)D ? __ldg(row + k0) : 0.f;
-                    const float v1 = (unsigned)(k0 + 1) < (unsigned)D ? __ldg(row + k0 + 1) : 0.f;
-                    // explicit rounding: no contraction into the Kahan step
-                    // below, whichever paths the instantiation holds
-                    rs = __fmul_rn(__fmaf_rn(w0, v0, w1 * v1), A.lmax);
+                    const bool ok0 = (unsigned)k0 < (unsigned)D, ok1 = (unsigned)(k0 + 1) < (unsigned)D;
+#pragma unroll
+                    for (int b = 0; b < IB; ++b) {
+                        if (!act[b]) continue;
+                        const float *row = sg[b] + roff;
+                        const float v0 = ok0 ? __ldg(row + k0) : 0.f;
+                        const float v1 = ok1 ? __ldg(row + k0 + 1) : 0.f;
+                        // explicit rounding: no contraction into the Kahan step
+                        const float rs = __fmul_rn(__fmaf_rn(w0, v0, w1 * v1), A.lmax);
+                        const float y = rs - cmp[b][r];
+                        const float tt = s[b][r] + y;
+                        cmp[b][r] = (tt - s[b][r]) - y;
+                        s[b][r] = tt;
+                    }
                 } else {
                     const float hwb = A.hw * inv_dt;
                     const int k0 = __float2int_ru(((ph + pc) - t0) * inv_dt + hD - hwb);
                     const int nc = __float2int_rd(2.f * hwb) + 1;
-                    rs = 0.f;
+                    float rs[IB];
+#pragma unroll
+                    for (int b = 0; b < IB; ++b) rs[b] = 0.f;
                     for (int q = 0; q < nc; ++q) {
                         const int kk = k0 + q;
                         if ((unsigned)kk < (unsigned)D) {
-                            const float tk = __fmaf_rn((float)kk - hD, dt, t0);
-                            rs = __fmaf_rn(chord_f(A, axis, fabsf((tk - ph) - pc)), __ldg(row + kk), rs);
+                            const float tkk = __fmaf_rn((float)kk - hD, dt, t0);
+                            const float wq = chord_f(A, axis, fabsf((tkk - ph) - pc));
+#pragma unroll
+                            for (int b = 0; b < IB; ++b)
+                                if (act[b]) rs[b] = __fmaf_rn(wq, __ldg(sg[b] + roff + kk), rs[b]);
                         }
                     }
+#pragma unroll
+                    for (int b = 0; b < IB; ++b) {
+                        if (!act[b]) continue;
+                        const float y = rs[b] - cmp[b][r];
+                        const float tt = s[b][r] + y;
+                        cmp[b][r] = (tt - s[b][r]) - y;
+                        s[b][r] = tt;
+                    }
                 }
-                const float y = rs - cmp[r];
-                const float tt = s[r] + y;
-                cmp[r] = (tt - s[r]) - y;
-                s[r] = tt;
                 ph += dph;
                 pc += dpc;
             }
         }
-        double part = 0.0;
-        if (ix < n) {
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int iy = tl.y + ty + 8 * r;
-                if (iy < n)
-                    part += bp_epilogue<float, EPI>(g, pd, a, ix, iy, ((double)s[r] - (double)cmp[r]) * g.h);
+        for (int b = 0; b < IB; ++b) {
+            if (!act[b]) continue;                                  // uniform across the CTA
+            const ProbDev pb = P[tl.x + b];
+            double part = 0.0;
+            if (ix < n) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int iy = tl.y + ty + 8 * r;
+                    if (iy < n)
+                        part += bp_epilogue<float, EPI>(g, pb, a, ix, iy,
+                                                        ((double)s[b][r] - (double)cmp[b][r]) * g.h);
+                }
+            }
+            if (a.part) {
+                part = warp_sum_fixed(part);
+                if (tx == 0) red[b][ty] = part;
             }
         }
         if (a.part) {
-            part = warp_sum_fixed(part);
-            if (tx == 0) red[ty] = part;
             __syncthreads();
-            if (threadIdx.x == 0) {
+            if (threadIdx.x < IB && act[threadIdx.x]) {
+                const int b = threadIdx.x;
                 double v = 0.0;
-                for (int i = 0; i < 8; ++i) v += red[i];
-                a.part[t] = v;
+                for (int i = 0; i < 8; ++i) v += red[b][i];
+                // the problem's partial of this pixel tile, at the index its
+                // one-image tile list gives it
+                const int ntx = (n + 31) / 32;
+                a.part[a.part_base[tl.x + b] + (tl.y / 32) * ntx + tl.z / 32] = v;
             }
             __syncthreads();
         }
@@ -260,8 +350,8 @@ void launch_backproject_f32(const GeomDev *G, const ProbDev *P, const int4 *tile
     const int grid = min(ntiles, num_sms() * (a.ctas_per_sm > 0 ? a.ctas_per_sm : 8));
 #define WMG_BPF(E)                                                                                  \
     case E:                                                                                         \
-        if (unit) k_backproject_f32<E, true><<<grid, 256, 0, st>>>(G, P, tiles, ntiles, a);         \
-        else k_backproject_f32<E, false><<<grid, 256, 0, st>>>(G, P, tiles, ntiles, a);             \
+        if (unit) k_backproject_f32<E, true, 1><<<grid, 256, 0, st>>>(G, P, tiles, ntiles, a);      \
+        else k_backproject_f32<E, false, 1><<<grid, 256, 0, st>>>(G, P, tiles, ntiles, a);          \
         break;
     switch (a.epi) {
         WMG_BPF(BP_STORE) WMG_BPF(BP_CGLS_S) WMG_BPF(BP_RESID) WMG_BPF(BP_POST)

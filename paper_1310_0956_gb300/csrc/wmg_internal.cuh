@@ -141,6 +141,7 @@ struct BpArgs {
     double *part;            // per-tile partial dot (or NULL)
     const double *S;         // per-problem scalars
     double *out64;           // FP64 output (BP_GMRES_W, BP_ATB, BP_APPLY_A in FP64 mode)
+    const int *part_base;    // FP32 kernels: problem p's first partial index (its one-image tile list)
 };
 
 struct PjArgs {
@@ -150,7 +151,14 @@ struct PjArgs {
     void *sino;              // T sinogram output pool
     double *part;            // per-tile partial ||q||^2 (or NULL)
     const double *S;         // scalars (active flags), or NULL = all active
+    const int *part_base;    // FP32 kernel: problem p's first partial index (its one-image tile list)
+    int group;               // FP32 kernel: images per tile of the tile list (1 or kProjGroup)
 };
+
+// Images per group tile of the FP32 projector (consecutive problems of one
+// geometry share the weight computation). The backprojector keeps one image
+// per tile: grouping cost it more occupancy than it saved (measured).
+constexpr int kProjGroup = 8;
 
 template <class T>
 void launch_project(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,

@@ -90,3 +90,30 @@ def test_batch_mixed_bin_spacing_equals_alone():
         plan.close()
         assert info1[0][0] == infos[i][0]
         assert torch.equal(x1, xs[i]), i
+
+
+@pytest.mark.parametrize("solver,cycle", [(wmg.SOLVER_GMRES, wmg.CYCLE_HYBRID), (wmg.SOLVER_CGLS, wmg.CYCLE_ADDITIVE)])
+def test_grouped_projector_tiles_equal_single(solver, cycle):
+    # 11 problems of one geometry: the FP32 projector runs the first 8 as one
+    # group tile (weights shared) and the other 3 one image per tile; every
+    # problem must give the same bits as when solved alone
+    n, m, D = 48, 30, 68
+    plan = wmg.Plan(n, m, D, levels=3, nu1=1, nu2=1, hybrid_depth=1, cycle=cycle, precision=wmg.PREC_F32)
+    op = oracle.Op(n, m, D)
+    bs = np.stack([op.project(S.phantom(n, 5, S.seed_for(3, 400 + i))) for i in range(11)])
+    b = torch.tensor(bs.reshape(-1), dtype=torch.float32, device="cuda")
+    q_all = plan.project(torch.tensor(np.stack([S.phantom(n, 5, S.seed_for(3, 500 + i)).reshape(-1)
+                                                for i in range(11)]).reshape(-1), dtype=torch.float32,
+                                      device="cuda"))
+    x_all, info_all, _, _ = plan.solve(b, solver, True, 25, 1e-6, 20)
+    torch.cuda.synchronize()
+    single = wmg.Plan(n, m, D, levels=3, nu1=1, nu2=1, hybrid_depth=1, cycle=cycle, precision=wmg.PREC_F32)
+    for i in range(11):
+        xi = torch.tensor(S.phantom(n, 5, S.seed_for(3, 500 + i)).reshape(-1), dtype=torch.float32, device="cuda")
+        assert torch.equal(single.project(xi), q_all[i * m * D:(i + 1) * m * D]), i
+        x1, info1, _, _ = single.solve(b[i * m * D:(i + 1) * m * D].contiguous(), solver, True, 25, 1e-6, 20)
+        torch.cuda.synchronize()
+        assert info1[0][0] == info_all[i][0]
+        assert torch.equal(x1, x_all[i * n * n:(i + 1) * n * n]), i
+    plan.close()
+    single.close()

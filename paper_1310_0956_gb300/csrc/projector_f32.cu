@@ -248,36 +248,56 @@ k_backproject_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
         for (int b = 0; b < IB; ++b)
 #pragma unroll
             for (int r = 0; r < 4; ++r) { s[b][r] = 0.f; cmp[b][r] = 0.f; }
-        for (int ang = 0; ang < m; ++ang) {
-            const AngleF A = g.angf[ang];
-            const bool axis = __float_as_int(A.flags) & 2;
-            const int64_t roff = (int64_t)ang * D;
-            float ph = __fmaf_rn(xo, A.chi, yo0 * A.shi);        // exact head of tau
-            float pc = __fmaf_rn(xo, A.clo, yo0 * A.slo);        // rounded tail
-            const float dph = 8.f * A.shi, dpc = 8.f * A.slo;
+        if (unit) {
+            // two angles per step: their contributions are added (rounded
+            // explicitly) before the compensated step
+            for (int ang = 0; ang < m; ang += 2) {
+                const bool two = ang + 1 < m;
+                const AngleF A0 = g.angf[ang];
+                const AngleF A1 = g.angf[two ? ang + 1 : ang];
+                const int64_t roff0 = (int64_t)ang * D, roff1 = (int64_t)(ang + 1) * D;
+                float ph0 = __fmaf_rn(xo, A0.chi, yo0 * A0.shi), pc0 = __fmaf_rn(xo, A0.clo, yo0 * A0.slo);
+                float ph1 = __fmaf_rn(xo, A1.chi, yo0 * A1.shi), pc1 = __fmaf_rn(xo, A1.clo, yo0 * A1.slo);
+                const float dph0 = 8.f * A0.shi, dpc0 = 8.f * A0.slo, dph1 = 8.f * A1.shi, dpc1 = 8.f * A1.slo;
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                if (unit) {
-                    // the two bins nearest tau (support half-width <= sqrt(1/2))
-                    const int k0 = __float2int_rd((ph + pc) - t0 + hD);
-                    const float tk = (float)k0 - hD + t0;
-                    const float d0 = (tk - ph) - pc;
-                    const float w0 = chord_n(A.wa, A.wb, fabsf(d0)), w1 = chord_n(A.wa, A.wb, fabsf(d0 + 1.f));
-                    const bool ok0 = (unsigned)k0 < (unsigned)D, ok1 = (unsigned)(k0 + 1) < (unsigned)D;
+                for (int r = 0; r < 4; ++r) {
+                    // the two bins nearest tau at each angle (support half-width <= sqrt(1/2))
+                    const int k0 = __float2int_rd((ph0 + pc0) - t0 + hD);
+                    const float d0 = (((float)k0 - hD + t0) - ph0) - pc0;
+                    const float wa0 = chord_n(A0.wa, A0.wb, fabsf(d0)), wb0 = chord_n(A0.wa, A0.wb, fabsf(d0 + 1.f));
+                    const int k1 = __float2int_rd((ph1 + pc1) - t0 + hD);
+                    const float d1 = (((float)k1 - hD + t0) - ph1) - pc1;
+                    const float wa1 = chord_n(A1.wa, A1.wb, fabsf(d1)), wb1 = chord_n(A1.wa, A1.wb, fabsf(d1 + 1.f));
+                    const bool o00 = (unsigned)k0 < (unsigned)D, o01 = (unsigned)(k0 + 1) < (unsigned)D;
+                    const bool o10 = two && (unsigned)k1 < (unsigned)D, o11 = two && (unsigned)(k1 + 1) < (unsigned)D;
 #pragma unroll
                     for (int b = 0; b < IB; ++b) {
                         if (!act[b]) continue;
-                        const float *row = sg[b] + roff;
-                        const float v0 = ok0 ? __ldg(row + k0) : 0.f;
-                        const float v1 = ok1 ? __ldg(row + k0 + 1) : 0.f;
+                        const float *row0 = sg[b] + roff0, *row1 = sg[b] + roff1;
+                        const float u0 = o00 ? __ldg(row0 + k0) : 0.f, u1 = o01 ? __ldg(row0 + k0 + 1) : 0.f;
+                        const float v0 = o10 ? __ldg(row1 + k1) : 0.f, v1 = o11 ? __ldg(row1 + k1 + 1) : 0.f;
                         // explicit rounding: no contraction into the Kahan step
-                        const float rs = __fmul_rn(__fmaf_rn(w0, v0, w1 * v1), A.lmax);
+                        const float x0 = __fmaf_rn(wa0, u0, __fmul_rn(wb0, u1));
+                        const float x1 = __fmaf_rn(wa1, v0, __fmul_rn(wb1, v1));
+                        const float rs = __fmaf_rn(x0, A0.lmax, __fmul_rn(x1, A1.lmax));
                         const float y = rs - cmp[b][r];
                         const float tt = s[b][r] + y;
                         cmp[b][r] = (tt - s[b][r]) - y;
                         s[b][r] = tt;
                     }
-                } else {
+                    ph0 += dph0; pc0 += dpc0; ph1 += dph1; pc1 += dpc1;
+                }
+            }
+        } else {
+            for (int ang = 0; ang < m; ++ang) {
+                const AngleF A = g.angf[ang];
+                const bool axis = __float_as_int(A.flags) & 2;
+                const int64_t roff = (int64_t)ang * D;
+                float ph = __fmaf_rn(xo, A.chi, yo0 * A.shi);        // exact head of tau
+                float pc = __fmaf_rn(xo, A.clo, yo0 * A.slo);        // rounded tail
+                const float dph = 8.f * A.shi, dpc = 8.f * A.slo;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
                     const float hwb = A.hw * inv_dt;
                     const int k0 = __float2int_ru(((ph + pc) - t0) * inv_dt + hD - hwb);
                     const int nc = __float2int_rd(2.f * hwb) + 1;
@@ -302,9 +322,9 @@ k_backproject_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
                         cmp[b][r] = (tt - s[b][r]) - y;
                         s[b][r] = tt;
                     }
+                    ph += dph;
+                    pc += dpc;
                 }
-                ph += dph;
-                pc += dpc;
             }
         }
 #pragma unroll

@@ -91,6 +91,9 @@ def _load():
         lib.or_cgls.restype = C.c_int
         lib.or_cgls.argtypes = [vp, vp, C.c_double, _dp, _dp, C.c_int, C.c_double, C.c_void_p]
         lib.or_set_reverse.argtypes = [C.c_int]
+        lib.or_bicgstab.restype = C.c_int
+        lib.or_bicgstab.argtypes = [vp, vp, C.c_double, _dp, _dp, C.c_int, C.c_double, vp,
+                                    C.POINTER(C.c_int)]
         lib.or_gmres.restype = C.c_int
         lib.or_gmres.argtypes = [vp, vp, C.c_double, _dp, _dp, C.c_int, C.c_int, C.c_double,
                                  C.c_void_p]
@@ -279,3 +282,15 @@ def gmres(op: Op, b, max_iter: int, restart: int = 20, rtol: float = 0.0, lam: f
     k = _load().or_gmres(op._h, precond._h if precond else None, lam, _f64(b), x, restart,
                          max_iter, rtol, hist.ctypes.data_as(C.c_void_p))
     return x, k, hist[:k + 1]
+
+
+def bicgstab(op: Op, b, max_iter: int, rtol: float = 0.0, lam: float = 0.0, precond: Wmg = None):
+    """Right-preconditioned BiCGStab on (W^T W + lam) x = W^T b, the paper's
+    Krylov solver (Section 2.3.1, Section 4); returns (x, iterations, relative
+    residual history, status: 0 converged, 1 iteration cap, -5 breakdown)."""
+    x = np.zeros(op.N)
+    hist = np.zeros(max_iter + 1)
+    st = C.c_int(0)
+    k = _load().or_bicgstab(op._h, precond._h if precond else None, lam, _f64(b), x, max_iter, rtol,
+                            hist.ctypes.data_as(C.c_void_p), C.byref(st))
+    return x, k, hist[:k + 1], st.value

@@ -921,3 +921,62 @@ done:
     free(V); free(H); free(cs); free(sn); free(g); free(y); free(f); free(w); free(u); free(tmpM);
     return k;
 }
+
+/* Right-preconditioned BiCGStab (van der Vorst, 1992) on (W^T W + lambda) x =
+ * W^T b from x0 = 0 -- the Krylov solver of the paper's experiments
+ * (Section 2.3.1 and Section 4): the shadow residual is r0; per iteration
+ *   rho = <rh, r>, beta = (rho / rho_prev)(alpha / omega),
+ *   p = r + beta (p - omega v), ph = B p, v = A ph, alpha = rho / <rh, v>,
+ *   s = r - alpha v, sh = B s, t = A sh, omega = <t, s> / <t, t>,
+ *   x += alpha ph + omega sh, r = s - omega t,
+ * with B the WMG cycle (identity when M is NULL). res_hist[k] = |r_k| / |r_0|.
+ * *status: 0 converged (rtol) or r = 0, 1 iteration cap, -5 breakdown
+ * (rho or <rh, v> zero, or omega zero with r nonzero). Returns the count. */
+int or_bicgstab(const or_op *op, const or_wmg *M, double lambda, const double *b, double *x,
+                int max_iter, double rtol, double *res_hist, int *status)
+{
+    const int64_t Mr = (int64_t)op->m * op->D, N = (int64_t)op->n * op->n;
+    double *r = malloc((size_t)N * sizeof(double)), *rh = malloc((size_t)N * sizeof(double));
+    double *p = calloc((size_t)N, sizeof(double)), *v = calloc((size_t)N, sizeof(double));
+    double *ph = malloc((size_t)N * sizeof(double)), *sv = malloc((size_t)N * sizeof(double));
+    double *sh = malloc((size_t)N * sizeof(double)), *t = malloc((size_t)N * sizeof(double));
+    double *tmpM = malloc((size_t)Mr * sizeof(double));
+    for (int64_t j = 0; j < N; j++) x[j] = 0.0;
+    or_backproject(op, b, r);                          /* r0 = f - A 0 */
+    memcpy(rh, r, (size_t)N * sizeof(double));
+    const double r0 = sqrt(dot(r, r, N));
+    if (res_hist) res_hist[0] = 1.0;
+    int k = 0, st = 1;
+    double rho_prev = 1.0, alpha = 1.0, omega = 1.0;
+    if (r0 == 0.0) { st = 0; goto done; }
+    while (k < max_iter) {
+        const double rho = dot(rh, r, N);
+        if (rho == 0.0) { st = -5; break; }
+        const double beta = (rho / rho_prev) * (alpha / omega);
+        for (int64_t j = 0; j < N; j++) p[j] = r[j] + beta * (p[j] - omega * v[j]);
+        if (M) or_wmg_apply(M, p, ph); else memcpy(ph, p, (size_t)N * sizeof(double));
+        apply_A(op, lambda, ph, v, tmpM);
+        const double rv = dot(rh, v, N);
+        if (rv == 0.0) { st = -5; break; }
+        alpha = rho / rv;
+        for (int64_t j = 0; j < N; j++) sv[j] = r[j] - alpha * v[j];
+        if (M) or_wmg_apply(M, sv, sh); else memcpy(sh, sv, (size_t)N * sizeof(double));
+        apply_A(op, lambda, sh, t, tmpM);
+        const double tt = dot(t, t, N);
+        omega = tt > 0.0 ? dot(t, sv, N) / tt : 0.0;
+        for (int64_t j = 0; j < N; j++) {
+            x[j] += alpha * ph[j] + omega * sh[j];
+            r[j] = sv[j] - omega * t[j];
+        }
+        k++;
+        const double rel = sqrt(dot(r, r, N)) / r0;
+        if (res_hist) res_hist[k] = rel;
+        if (rel < rtol || rel == 0.0) { st = 0; break; }
+        if (omega == 0.0) { st = -5; break; }
+        rho_prev = rho;
+    }
+done:
+    if (status) *status = st;
+    free(r); free(rh); free(p); free(v); free(ph); free(sv); free(sh); free(t); free(tmpM);
+    return k;
+}

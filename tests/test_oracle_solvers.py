@@ -149,3 +149,54 @@ def test_qualitative_ordering_small_workload():
     assert k_wmg < k_plain / 2
     assert k_cg < k_cgp / 2
     assert hs[-1] > 1e-3
+
+
+@pytest.mark.parametrize("lam", [0.0, 0.05])
+@pytest.mark.parametrize("pc", [None, (oracle.CYCLE_HYBRID, 2, 1), (oracle.CYCLE_ADDITIVE, 0, 0)])
+def test_bicgstab_converges_to_dense_solution(lam, pc):
+    """BiCGStab (the paper's solver) reaches the dense normal-equation
+    solution, and its recurrence residual is the true residual of its
+    iterate (a mismatch between the x and r updates breaks the second)."""
+    op, b = setup()
+    xs = ls_solution(op, b, lam)
+    M = None if pc is None else oracle.Wmg(op, 3, pc[2], pc[2], 1.0, lam, pc[0], pc[1])
+    x, k, hist, st = oracle.bicgstab(op, b, 3000, 1e-12, lam, M)
+    assert st == 0
+    W = op.dense()
+    kappa = np.linalg.cond(W.T @ W + lam * np.eye(op.N))
+    assert np.linalg.norm(x - xs) < 1e-11 * kappa * np.linalg.norm(xs)
+    assert abs(op.ne_residual(b, x, lam) - hist[-1]) < 1e-10
+
+
+def test_bicgstab_exact_preconditioner_one_step():
+    """With B = A^{-1} (one WMG level: the single leaf is the whole operator)
+    BiCGStab's first half-step is the exact solution: alpha = 1, s = 0,
+    omega = 0, done in one iteration."""
+    op, b = setup((8, 10, 13), noise=0.0)
+    lam = 0.01
+    M = oracle.Wmg(op, 1, 0, 0, 1.0, lam, oracle.CYCLE_ADDITIVE, 0)
+    x, k, hist, st = oracle.bicgstab(op, b, 10, 1e-12, lam, M)
+    assert (k, st) == (1, 0)
+    np.testing.assert_allclose(x, ls_solution(op, b, lam), rtol=0, atol=1e-12 * np.abs(x).max())
+
+
+def test_bicgstab_first_step_galerkin_conditions():
+    """Unpreconditioned, the first half-step is a CG step (the shadow residual
+    is r0): s = r0 - alpha A r0 is orthogonal to r0; omega minimises |r1| over
+    s - omega A s, so r1 is orthogonal to A s. Both follow from the
+    definitions and fail for a wrong alpha, omega or sign."""
+    op, b = setup((10, 12, 15))
+    W = op.dense()
+    A = W.T @ W
+    f = W.T @ b
+    x1, k, hist, st = oracle.bicgstab(op, b, 1, 0.0, 0.0, None)
+    assert k == 1
+    r0 = f
+    alpha = (r0 @ r0) / (r0 @ (A @ r0))
+    s = r0 - alpha * (A @ r0)
+    assert abs(s @ r0) < 1e-12 * (r0 @ r0)
+    r1 = f - A @ x1
+    # x1 = alpha r0 + omega s and r1 = s - omega A s: r1 orthogonal to A s
+    assert abs(r1 @ (A @ s)) < 1e-10 * np.linalg.norm(r1) * np.linalg.norm(A @ s)
+    omega = (x1 - alpha * r0) @ s / (s @ s)
+    np.testing.assert_allclose(x1, alpha * r0 + omega * s, rtol=0, atol=1e-12 * np.abs(x1).max())

@@ -69,6 +69,8 @@ extern "C" {
 #define WMG_SOLVER_SIRT   0   /* eq. sirt_it */
 #define WMG_SOLVER_CGLS   1   /* CGLS / PCG on the normal equations */
 #define WMG_SOLVER_GMRES  2   /* restarted GMRES, right preconditioning */
+#define WMG_SOLVER_BICGSTAB 3 /* BiCGStab, right preconditioning: the solver of
+                                 the paper's experiments (Section 4) */
 
 /* ---- parameter blocks ----------------------------------------------------- */
 typedef struct wmg_geom {
@@ -160,8 +162,11 @@ int32_t wmg_leaf_inverse(wmg_plan *plan, int64_t k, void *out, void *stream);
 
 /* Solve `count` problems of the plan's geometry: b (count sinograms) ->
  * x (count images). x0 = 0 (x is output only). solver = WMG_SOLVER_*;
- * preconditioned = 1 uses one WMG cycle per iteration (CGLS needs the
- * SYMMETRIC or ADDITIVE cycle; GMRES any; SIRT ignores it). Stops a problem
+ * preconditioned = 1 uses one WMG cycle per iteration (two for BiCGStab;
+ * CGLS needs the SYMMETRIC or ADDITIVE cycle; GMRES and BiCGStab any; SIRT
+ * ignores it). A BiCGStab iteration counts as one (two A-pairs); its
+ * breakdowns (rho, <rh, v> or omega zero before convergence) end the problem
+ * with WMG_ERR_BREAKDOWN and the last iterate in x. Stops a problem
  * when its relative NE residual drops below rtol or after max_iter
  * iterations; restart is the GMRES cycle length (<= 64). info: HOST array
  * of count entries, or NULL. res_hist: optional HOST array of

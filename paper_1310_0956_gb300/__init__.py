@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "INVALID_ARG", -2: "OOM", -3: "
 
 PREC_F64, PREC_F32 = 0, 1
 CYCLE_ADDITIVE, CYCLE_HYBRID, CYCLE_SYMMETRIC = 0, 1, 2
-SOLVER_SIRT, SOLVER_CGLS, SOLVER_GMRES = 0, 1, 2
+SOLVER_SIRT, SOLVER_CGLS, SOLVER_GMRES, SOLVER_BICGSTAB = 0, 1, 2, 3
 REQ_QUEUED, REQ_RUNNING, REQ_DONE = 0, 1, 2
 
 

@@ -1548,19 +1548,111 @@ static int32_t solve_gmres(wmg_plan *pl, bool pre, const void *b, void *xout, in
     return WMG_OK;
 }
 
+// Right-preconditioned BiCGStab (van der Vorst 1992), the solver of the
+// paper's experiments (Section 2.3.1, Section 4): two preconditioner
+// applications and two A-pairs per iteration; every scalar lives on the
+// device, so one iteration is a fixed launch sequence (a graph after its first
+// run). Vectors: r = f, rh = w, p = p, v = t, s = u, t = bi_t, ph = z, sh = bi_sh.
+template <class T>
+static int32_t solve_bicgstab(wmg_plan *pl, bool pre, const void *b, void *xout, int max_iter, cudaStream_t st)
+{
+    const int64_t nN = pl->Ntot, nM = pl->Mtot;
+    const size_t e = pl->esz;
+    if (!ensure_pool(pl->x, nN, 8) || !ensure_pool(pl->f, nN, 8) || !ensure_pool(pl->w, nN, 8) ||
+        !ensure_pool(pl->p, nN, 8) || !ensure_pool(pl->t, nN, 8) || !ensure_pool(pl->u, nN, 8) ||
+        !ensure_pool(pl->z, nN, 8) || !ensure_pool(pl->bi_t, nN, 8) || !ensure_pool(pl->bi_sh, nN, 8) ||
+        !ensure_pool(pl->z_op, nN, e) || !ensure_pool(pl->zT_op, nN, e) || !ensure_pool(pl->sinoS, nM, e) ||
+        !ensure_partials(pl, 1))
+        return fail(WMG_ERR_OOM, "BiCGStab pools");
+    if (pre) {
+        int32_t rc = ensure_wmg_pools(pl);
+        if (rc) return rc;
+    }
+    const ProbSet &ps = pl->real;
+    const ProbDev *P = ps.d.as<ProbDev>();
+    const int4 *vt = ps.vimg.tiles.as<int4>();
+    const int nv = ps.vimg.n;
+    const double *S = pl->S.as<double>();
+    double *hist = pl->hist.as<double>();
+    const int hld = max_iter + 1;
+    double *pa = pl->part_a.as<double>(), *pb = pl->part_b.as<double>();
+    BicgArgs ba{};
+    ba.x = pl->x.as<double>(); ba.r = pl->f.as<double>(); ba.rh = pl->w.as<double>(); ba.p = pl->p.as<double>();
+    ba.v = pl->t.as<double>(); ba.s = pl->u.as<double>(); ba.t = pl->bi_t.as<double>();
+    ba.ph = pl->z.as<double>(); ba.sh = pl->bi_sh.as<double>();
+    ba.part_a = pa; ba.part_b = pb; ba.S = S;
+    cudaMemsetAsync(pl->x.p, 0, nN * 8, st);
+    // r0 = W^T b (x0 = 0), rh = r0, p = v = 0
+    BpArgs fa = bp_args(BP_ATB, b, S);
+    fa.out64 = ba.r; fa.part = pb;
+    backproject<T>(pl, ps, fa, st);
+    finalize(pl, FIN_BI_INIT, ps.bp, pb, 1, nullptr, nullptr, 0, hist, hld, st);
+    launch_bicg(BI_INIT, P, vt, nv, ba, st);
+    // z_out = B z_in (FP64) with the operator copies of z_out; then w_out = A z_out
+    auto precond_then_A = [&](double *z_in, double *z_out, double *w_out, cudaStream_t s) -> int32_t {
+        if (pre) {
+            bool have = false;
+            int32_t rc = wmg_apply<T>(pl, z_in, z_out, false, true, false, &have, s);
+            if (rc) return rc;
+        } else {
+            WMG_CUDA(cudaMemcpyAsync(z_out, z_in, nN * 8, cudaMemcpyDeviceToDevice, s));
+            ImgArgs ic{};
+            ic.z = z_out; ic.copy_op = pl->z_op.p; ic.copyT_op = pl->zT_op.p; ic.S = S;
+            img_op<T>(pl, IMG_COPY64, ic, s);
+        }
+        project<T>(pl, ps, pl->z_op.p, pl->zT_op.p, pl->sinoS.p, nullptr, S, s);
+        BpArgs wa = bp_args(BP_GMRES_W, pl->sinoS.p, S);
+        wa.z = z_out; wa.out64 = w_out;
+        backproject<T>(pl, ps, wa, s);
+        return WMG_OK;
+    };
+    auto iteration = [&](cudaStream_t s) -> int32_t {
+        launch_bicg(BI_P, P, vt, nv, ba, s);                           // p = r + beta (p - omega v)
+        int32_t rc = precond_then_A(ba.p, ba.ph, ba.v, s);              // ph = B p, v = A ph
+        if (rc) return rc;
+        launch_bicg(BI_RV, P, vt, nv, ba, s);
+        finalize(pl, FIN_BI_ALPHA, ps.vimg, pa, 1, nullptr, nullptr, 0, hist, hld, s);
+        launch_bicg(BI_S, P, vt, nv, ba, s);                           // s = r - alpha v
+        if ((rc = precond_then_A(ba.s, ba.sh, ba.t, s))) return rc;     // sh = B s, t = A sh
+        launch_bicg(BI_TS, P, vt, nv, ba, s);
+        finalize(pl, FIN_BI_OMEGA, ps.vimg, pa, 1, &ps.vimg, pb, 0, hist, hld, s);
+        launch_bicg(BI_XR, P, vt, nv, ba, s);                          // x, r updates
+        finalize(pl, FIN_BI_RES, ps.vimg, pa, 1, &ps.vimg, pb, 0, hist, hld, s);
+        return WMG_OK;
+    };
+    Graph graph;
+    bool graphed = false;
+    for (int it = 0; it < max_iter; ++it) {
+        if (it == 1) graphed = capture(pl, graph, iteration);
+        int32_t rc = graphed ? replay(graph, st) : iteration(st);
+        if (rc) return rc;
+        if ((it + 1) % 4 == 0 || it + 1 == max_iter) {
+            bool any = false;
+            if ((rc = any_active(pl, st, &any))) return rc;
+            if (!any) break;
+        }
+    }
+    ImgArgs io{};
+    io.z = pl->x.as<double>(); io.out_op = xout;
+    img_op<T>(pl, IMG_STORE_OUT, io, st);
+    WMG_CUDA(cudaGetLastError());
+    return WMG_OK;
+}
+
 template <class T>
 static int32_t do_solve(wmg_plan *pl, int solver, bool pre, const void *b, void *x, int max_iter, int restart,
                         cudaStream_t st)
 {
     if (solver == WMG_SOLVER_CGLS) return solve_cgls<T>(pl, pre, b, x, max_iter, st);
     if (solver == WMG_SOLVER_GMRES) return solve_gmres<T>(pl, pre, b, x, max_iter, restart, st);
+    if (solver == WMG_SOLVER_BICGSTAB) return solve_bicgstab<T>(pl, pre, b, x, max_iter, st);
     return solve_sirt<T>(pl, b, x, max_iter, st);
 }
 
 static int32_t check_solve_args(wmg_plan *pl, int32_t solver, int32_t preconditioned, int32_t max_iter,
                                 int32_t restart)
 {
-    if (max_iter < 0 || solver < WMG_SOLVER_SIRT || solver > WMG_SOLVER_GMRES)
+    if (max_iter < 0 || solver < WMG_SOLVER_SIRT || solver > WMG_SOLVER_BICGSTAB)
         return fail(WMG_ERR_INVALID_ARG, "wmg_solve: bad arguments");
     if (solver == WMG_SOLVER_GMRES && (restart < 1 || restart > 64))
         return fail(WMG_ERR_INVALID_ARG, "wmg_solve: restart must be in [1, 64]");

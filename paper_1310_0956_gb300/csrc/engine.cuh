@@ -163,6 +163,8 @@ struct wmg_plan {
     wmg::DevBuf S, part_a, part_b, part_c, lam, hist;
     // GMRES
     wmg::DevBuf V, H, gcs, gsn, gg, gy, h1, h2, jn, done;
+    // BiCGStab (t and the preconditioned s)
+    wmg::DevBuf bi_t, bi_sh;
     // profiling: (kind 0 = project / 1 = backproject, images, start, stop)
     // CUDA graphs of the solver iterations are captured on this private
     // stream (capture cannot use the legacy default stream) and launched on

@@ -146,6 +146,58 @@ k_vec(const ProbDev *__restrict__ P, const int4 *__restrict__ tiles, int ntiles,
 }
 
 // ---------------------------------------------------------------------------
+// BiCGStab vector steps (right preconditioning; van der Vorst 1992), one
+// image chunk per tile, FP64, per-tile partial dot products.
+// ---------------------------------------------------------------------------
+template <int OP>
+__global__ void __launch_bounds__(256)
+k_bicg(const ProbDev *__restrict__ P, const int4 *__restrict__ tiles, int ntiles, BicgArgs a)
+{
+    __shared__ double red[8];
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 tl = tiles[t];
+        const ProbDev pd = P[tl.x];
+        if (!slot_active(a.S, pd.slot)) continue;
+        const double *S = a.S + (int64_t)pd.slot * NSCAL;
+        const double alpha = S[SC_ALPHA], omega = S[SC_DELTA], beta = S[SC_BETA];
+        double pa = 0.0, pb = 0.0;
+        for (int e = threadIdx.x; e < tl.z; e += blockDim.x) {
+            const int64_t j = pd.img + tl.y + e;
+            if (OP == BI_INIT) {
+                a.rh[j] = a.r[j];
+                a.p[j] = 0.0;
+                a.v[j] = 0.0;
+            } else if (OP == BI_P) {
+                a.p[j] = a.r[j] + beta * (a.p[j] - omega * a.v[j]);
+            } else if (OP == BI_RV) {
+                pa += a.rh[j] * a.v[j];
+            } else if (OP == BI_S) {
+                a.s[j] = a.r[j] - alpha * a.v[j];
+            } else if (OP == BI_TS) {
+                pa += a.t[j] * a.s[j];
+                pb += a.t[j] * a.t[j];
+            } else if (OP == BI_XR) {
+                a.x[j] += alpha * a.ph[j] + omega * a.sh[j];
+                const double rv = a.s[j] - omega * a.t[j];
+                a.r[j] = rv;
+                pa += rv * rv;
+                pb += a.rh[j] * rv;
+            }
+        }
+        if (OP == BI_RV || OP == BI_TS || OP == BI_XR) {
+            const double ta = block_sum_fixed(pa, red);
+            if (threadIdx.x == 0) a.part_a[t] = ta;
+            __syncthreads();
+            if (OP != BI_RV) {
+                const double tb = block_sum_fixed(pb, red);
+                if (threadIdx.x == 0) a.part_b[t] = tb;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // GMRES: classical Gram-Schmidt passes over the basis V (restart+1 vectors of
 // N per problem, stride `vstride` elements between basis vectors). The column
 // index j is one for all problems, or, when `jv` is given, jv[slot] per
@@ -346,6 +398,44 @@ k_finalize(FinArgs f)
             S[SC_BETA] = gnew / S[SC_GAMMA];
             S[SC_GAMMA] = gnew;
             if (!isfinite(gnew)) stop(WMG_ERR_NAN);
+            break;
+        }
+        case FIN_BI_INIT: {              // sa = |r0|^2 (r0 = f, the shadow residual)
+            S[SC_S0] = sqrt(sa);
+            S[SC_GAMMA] = sa;                   // rho = <rh, r0> = |r0|^2
+            S[SC_ALPHA] = 1.0;
+            S[SC_DELTA] = 1.0;                  // omega
+            S[SC_BETA] = sa;                    // (rho / 1)(1 / 1); p = r as p = v = 0
+            S[SC_RES] = 1.0;
+            S[SC_ITERS] = 0.0;
+            if (f.hist) f.hist[(int64_t)p * f.hist_ld] = 1.0;
+            if (!(sa > 0.0)) stop(sa == 0.0 ? WMG_OK : WMG_ERR_NAN);
+            break;
+        }
+        case FIN_BI_ALPHA: {             // sa = <rh, v>
+            if (!(sa != 0.0) || !isfinite(sa)) stop(isfinite(sa) ? WMG_ERR_BREAKDOWN : WMG_ERR_NAN);
+            else S[SC_ALPHA] = S[SC_GAMMA] / sa;
+            break;
+        }
+        case FIN_BI_OMEGA: {             // sa = <t, s>, sb = <t, t>
+            S[SC_DELTA] = sb > 0.0 ? sa / sb : 0.0;
+            break;
+        }
+        case FIN_BI_RES: {               // sa = |r|^2, sb = <rh, r>
+            const int it = (int)S[SC_ITERS] + 1;
+            S[SC_ITERS] = it;
+            const double rel = sqrt(sa) / S[SC_S0];
+            S[SC_RES] = rel;
+            if (f.hist && it < f.hist_ld) f.hist[(int64_t)p * f.hist_ld + it] = rel;
+            const double omega = S[SC_DELTA];
+            if (!isfinite(rel)) stop(WMG_ERR_NAN);
+            else if (rel < S[SC_RTOL] || rel == 0.0) stop(WMG_OK);
+            else if (it >= (int)S[SC_MAXIT]) stop(WMG_NOT_CONVERGED);
+            else if (omega == 0.0 || sb == 0.0) stop(WMG_ERR_BREAKDOWN);
+            else {
+                S[SC_BETA] = (sb / S[SC_GAMMA]) * (S[SC_ALPHA] / omega);
+                S[SC_GAMMA] = sb;
+            }
             break;
         }
         case FIN_SET_RES: {
@@ -556,6 +646,22 @@ void launch_gm_getv(const ProbDev *P, const int4 *tiles, int ntiles, const doubl
     count_launches(1);
     k_gm_getv<<<grid_for(ntiles), 256, 0, st>>>(P, tiles, ntiles, V, vstride, jv, out, S);
 }
+void launch_bicg(int op, const ProbDev *P, const int4 *tiles, int ntiles, const BicgArgs &a, cudaStream_t st)
+{
+    if (ntiles <= 0) return;
+    count_launches(1);
+    const int grid = grid_for(ntiles);
+    switch (op) {
+        case BI_INIT: k_bicg<BI_INIT><<<grid, 256, 0, st>>>(P, tiles, ntiles, a); break;
+        case BI_P: k_bicg<BI_P><<<grid, 256, 0, st>>>(P, tiles, ntiles, a); break;
+        case BI_RV: k_bicg<BI_RV><<<grid, 256, 0, st>>>(P, tiles, ntiles, a); break;
+        case BI_S: k_bicg<BI_S><<<grid, 256, 0, st>>>(P, tiles, ntiles, a); break;
+        case BI_TS: k_bicg<BI_TS><<<grid, 256, 0, st>>>(P, tiles, ntiles, a); break;
+        case BI_XR: k_bicg<BI_XR><<<grid, 256, 0, st>>>(P, tiles, ntiles, a); break;
+        default: break;
+    }
+}
+
 void launch_gm_scalar(int which, const GmArgs &a, cudaStream_t st)
 {
     const int blocks = (a.nprob + 127) / 128;

@@ -59,6 +59,10 @@ enum FinOp : int {
     FIN_SIRT_RES,
     FIN_STORE,         // S[store_slot] = sum of part_a
     FIN_SET_RES,       // S[RES] = sqrt(sum) / S[S0], end of a fixed-count solve
+    FIN_BI_INIT,       // BiCGStab: |r0|^2 -> S0, rho = |r0|^2, alpha = omega = 1, beta = rho
+    FIN_BI_ALPHA,      // <rh, v> -> alpha = rho / <rh, v>
+    FIN_BI_OMEGA,      // <t, s>, <t, t> -> omega
+    FIN_BI_RES,        // |r|^2, <rh, r> -> residual, stop tests, beta, rho
 };
 
 struct FinArgs {
@@ -77,6 +81,23 @@ struct FinArgs {
     int store_slot;
     double *store_vec;       // FIN_STORE with nsum_a > 1: out[p*ld + i]
     int store_ld;
+};
+
+// BiCGStab vector steps over image chunks (scalars rho = S[GAMMA],
+// alpha = S[ALPHA], omega = S[DELTA], beta = S[BETA]).
+enum BicgOp : int {
+    BI_INIT = 0,       // rh = r, p = 0, v = 0
+    BI_P,              // p = r + beta (p - omega v)
+    BI_RV,             // part_a = <rh, v>
+    BI_S,              // s = r - alpha v
+    BI_TS,             // part_a = <t, s>, part_b = <t, t>
+    BI_XR,             // x += alpha ph + omega sh, r = s - omega t; part_a = |r|^2, part_b = <rh, r>
+};
+
+struct BicgArgs {
+    double *x, *r, *rh, *p, *v, *s, *t, *ph, *sh;
+    double *part_a, *part_b;
+    const double *S;
 };
 
 struct GmArgs {
@@ -112,6 +133,7 @@ void launch_gm_setv(const ProbDev *P, const int4 *tiles, int ntiles, double *V, 
 // out = v_{jv[slot]} for every active problem
 void launch_gm_getv(const ProbDev *P, const int4 *tiles, int ntiles, const double *V, int64_t vstride,
                     const int *jv, double *out, const double *S, cudaStream_t st);
+void launch_bicg(int op, const ProbDev *P, const int4 *tiles, int ntiles, const BicgArgs &a, cudaStream_t st);
 // which: 0 = Arnoldi scalar step, 1 = solve H y = g, 2 = restart
 void launch_gm_scalar(int which, const GmArgs &a, cudaStream_t st);
 

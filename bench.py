@@ -287,6 +287,23 @@ def run_ours(args, rank, world, local):
         variant = {"cycle": f"hybrid depth {HYB}, nu1=nu2={NU_SMOOTHED} (l1-Jacobi)",
                    "recon_per_s": B / float(np.mean(vt)), "iters_mean": float(np.mean(vit)),
                    "ms_per_step": float(np.mean(vt)) * 1e3}
+        # the paper's own Krylov solver on the same batch and cycle
+        xb_ = torch.empty_like(x)
+        plan.solve(b, wmg.SOLVER_BICGSTAB, True, MAX_ITER, RTOL, RESTART, out=xb_)
+        bt_, bit_, bst_ = [], [], []
+        for _ in range(max(1, min(args.steps, 3))):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, binfo, _, _ = plan.solve(b, wmg.SOLVER_BICGSTAB, True, MAX_ITER, RTOL, RESTART, out=xb_)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            bt_.append(e0.elapsed_time(e1) / 1e3)
+            bit_.extend(i[0] for i in binfo)
+            bst_.extend(i[1] for i in binfo)
+        variant["bicgstab"] = {"solver": "WMG-BiCGStab (right preconditioning), the paper's cycle",
+                               "recon_per_s": B / float(np.mean(bt_)), "iters_mean": float(np.mean(bit_)),
+                               "all_converged": bool(all(s_ == 0 for s_ in bst_))}
 
     # end-to-end: the same solve through the C ABI with HOST (pinned) buffers,
     # host->device copy of the sinograms and device->host copy of the images
@@ -618,6 +635,26 @@ def load_peaks():
         return {}
 
 
+# DRAM traffic of the FP32 projector / backprojector measured by ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum, 16-image launches of the
+# workload geometry; profiles/dram_traffic_k_project_backproject_256x256.md),
+# per image; valid while the kernels' source is the one measured (hash).
+KERNEL_TRAFFIC = {"source": "paper_1310_0956_gb300/csrc/projector_f32.cu", "sha256_16": "2101b2b8c2c8510b",
+                  "project_bytes_per_image": (8495360 + 24832) / 16.0,
+                  "backproject_bytes_per_image": (4037632 + 512) / 16.0}
+
+
+def _kernel_traffic(name: str, images: float):
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, KERNEL_TRAFFIC["source"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest()[:16] != KERNEL_TRAFFIC["sha256_16"]:
+                return None
+    except OSError:
+        return None
+    return KERNEL_TRAFFIC[name + "_bytes_per_image"] * images
+
+
 def roofline_entry(prof: dict, P0, B: int) -> dict:
     """Dominant kernel (larger total time of projector / backprojector). It is
     bound by FP32 arithmetic, not memory: the algorithmic work is one
@@ -633,7 +670,8 @@ def roofline_entry(prof: dict, P0, B: int) -> dict:
     clk = peaks.get("sm_max_mhz", 2070.0)
     peak = 152 * 128 * 2 * clk * 1e6 / 1e12
     return {"kernel": f"k_{name}", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": _kernel_traffic(name, p["images_per_launch"]),
+            "traffic_unit": "bytes per launch (DRAM read + write)",
             "note": (f"{p['launches']} launches, mean {p['mean_ms']:.3f} ms, "
                      f"{nnz_per_image * p['images_per_launch'] / (p['mean_ms'] * 1e-3) / 1e9:.0f} Gnnz/s; "
                      f"peak derived: 152 SMs x 128 FP32 lanes x 2 FLOP x {clk:.0f} MHz")}

@@ -103,7 +103,9 @@ typedef struct wmg_solve_info {
     int32_t iters;          /* iterations done (A-pairs of the outer solver) */
     int32_t status;         /* WMG_OK, WMG_NOT_CONVERGED or a negative error */
     double rel_res;         /* last relative NE residual ||W^T(b-Wx)-lambda x|| / ||W^T b||
-                               as tracked by the solver's recurrence */
+                               as tracked by the solver's recurrence (GMRES, BiCGStab: the
+                               residual of their own system); 0 with status WMG_OK and x = 0
+                               when the initial residual is exactly 0 (e.g. b = 0) */
 } wmg_solve_info;
 
 typedef struct wmg_plan wmg_plan;

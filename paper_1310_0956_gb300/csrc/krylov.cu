@@ -361,7 +361,7 @@ k_finalize(FinArgs f)
         case FIN_CGLS_INIT: {            // sa = |s0|^2, sb = s.z (or |s|^2 unpreconditioned)
             S[SC_S0] = sqrt(sa);
             S[SC_GAMMA] = f.precond ? sb : sa;
-            S[SC_RES] = 1.0;
+            S[SC_RES] = sa == 0.0 ? 0.0 : 1.0;       // W^T b = 0: x = 0 is exact
             S[SC_ITERS] = 0.0;
             if (f.hist) f.hist[(int64_t)p * f.hist_ld] = 1.0;
             if (!(sa > 0.0)) stop(sa == 0.0 ? WMG_OK : WMG_ERR_NAN);
@@ -406,7 +406,7 @@ k_finalize(FinArgs f)
             S[SC_ALPHA] = 1.0;
             S[SC_DELTA] = 1.0;                  // omega
             S[SC_BETA] = sa;                    // (rho / 1)(1 / 1); p = r as p = v = 0
-            S[SC_RES] = 1.0;
+            S[SC_RES] = sa == 0.0 ? 0.0 : 1.0;  // b = 0: x = 0 is exact
             S[SC_ITERS] = 0.0;
             if (f.hist) f.hist[(int64_t)p * f.hist_ld] = 1.0;
             if (!(sa > 0.0)) stop(sa == 0.0 ? WMG_OK : WMG_ERR_NAN);
@@ -438,10 +438,13 @@ k_finalize(FinArgs f)
             }
             break;
         }
-        case FIN_SET_RES: {
-            const double rel = sqrt(sa) / S[SC_S0];
+        case FIN_SET_RES: {              // sa = |NE residual|^2 of the final iterate
+            const double s0 = S[SC_S0];
+            // W^T b = 0 (e.g. b = 0): x = 0 is exact when the residual is 0
+            const double rel = s0 > 0.0 ? sqrt(sa) / s0 : (sa == 0.0 ? 0.0 : INFINITY);
             S[SC_RES] = rel;
-            stop(rel < S[SC_RTOL] ? WMG_OK : WMG_NOT_CONVERGED);
+            if (!isfinite(sa) || !isfinite(s0)) stop(WMG_ERR_NAN);
+            else stop(rel < S[SC_RTOL] || rel == 0.0 ? WMG_OK : WMG_NOT_CONVERGED);
             break;
         }
         case FIN_STORE: {
@@ -535,7 +538,7 @@ __global__ void k_gm_restart(GmArgs a)
     a.done[p] = 0;
     if (a.init) {
         S[SC_S0] = beta;
-        S[SC_RES] = 1.0;
+        S[SC_RES] = beta == 0.0 ? 0.0 : 1.0;           // b = 0: x = 0 is exact
         S[SC_ITERS] = 0.0;
         if (a.hist) a.hist[(int64_t)p * a.hist_ld] = 1.0;
         if (!(beta > 0.0)) { S[SC_ACTIVE] = 0.0; S[SC_STATUS] = beta == 0.0 ? WMG_OK : WMG_ERR_NAN; }

@@ -38,6 +38,17 @@ bool graphs_default()
     return on;
 }
 
+// TMA-staged group tiles of the FP32 projector unless WMG_PROJ_TMA=0 in the
+// environment (both kernels give the same bits).
+static bool proj_tma_default()
+{
+    static const bool on = [] {
+        const char *v = std::getenv("WMG_PROJ_TMA");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
 static std::atomic<long long> g_launches{0};
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
@@ -113,6 +124,31 @@ void build_tiles(const wmg_plan *pl, ProbSet &ps)
             for (int a = 0; a < g.m; ++a)
                 for (int k0 = 0; k0 < g.D; k0 += 32) ps.proj1.h.push_back(make_int4(f, a, k0, 1));
         q = e;
+    }
+    ps.tma_n = 0;
+    ps.tma_count = 0;
+    if (pl->prec == WMG_PREC_F32 && !ps.projg.h.empty() && proj_tma_default()) {
+        int n0 = -1;
+        bool ok = true;
+        int64_t count = 0;
+        for (int q = 0; q < ps.nprob && ok; ++q) {
+            if (ps.h[q].geom < 0) continue;
+            const GeomDev &g = pl->geos[ps.h[q].geom]->g;
+            if (n0 < 0) n0 = g.n;
+            const int64_t N = (int64_t)g.n * g.n;
+            ok = g.n == n0 && g.n % 4 == 0 && g.dt <= 1.0 && ps.h[q].img % N == 0;
+            count = std::max<int64_t>(count, ps.h[q].img / N + 1);
+        }
+        for (size_t i = 0; i < ps.projg.h.size() && ok; ++i) {
+            const int f = ps.projg.h[i].x;
+            if (i > 0 && ps.projg.h[i - 1].x == f) continue;
+            for (int b = 1; b < kProjGroup && ok; ++b)
+                ok = ps.h[f + b].img == ps.h[f].img + (int64_t)b * n0 * n0;
+        }
+        if (ok && n0 > 0) {
+            ps.tma_n = n0;
+            ps.tma_count = count;
+        }
     }
     for (int q = 0; q < ps.nprob; ++q) {
         if (ps.h[q].geom < 0) continue;          // an empty server slot: no tiles
@@ -232,8 +268,11 @@ void project(wmg_plan *pl, const ProbSet &ps, const void *img, const void *imgT,
         // FP32: groups of kProjGroup images share the weights; the rest run
         // one image per tile (the same per-image arithmetic in both)
         a.group = kProjGroup;
-        launch_project<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.projg.tiles.as<int4>(), ps.projg.n, a,
-                          st);
+        if (!(ps.tma_n > 0 && launch_project_f32_tma(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(),
+                                                      ps.projg.tiles.as<int4>(), ps.projg.n, a, ps.tma_n,
+                                                      ps.tma_count, st)))
+            launch_project<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.projg.tiles.as<int4>(), ps.projg.n,
+                              a, st);
         a.group = 1;
         launch_project<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.proj1.tiles.as<int4>(), ps.proj1.n, a,
                           st);
@@ -744,6 +783,18 @@ int32_t make_geo(const wmg_geom *g, const wmg_opts *o, Geo &G, cudaStream_t st)
     gd.hDf = 0.5f * (float)(g->D - 1);
     G.unit_bins = gd.dt == 1.0 && gd.t0 == 0.0;
     gd.unit = G.unit_bins ? 1 : 0;
+    if (G.unit_bins) {
+        // Pixel centres of the 32 x 32 backprojection tiles (the last tile
+        // row and column may reach past the image) lie within rmax of the
+        // centre, so |tau| <= rmax at every angle. The unit-bin path takes
+        // bins k0 = rint(tau + hD - 1/2) and k0 + 1 (up to FP32 rounding of
+        // tau, far below the 0.01 margin): both lie in [0, D) when
+        // rmax < hD.
+        const double half = 0.5 * g->n;
+        const double xmax = std::max(half - 0.5, 32.0 * ((g->n + 31) / 32) - half - 0.5);
+        const double rmax = std::sqrt(2.0) * xmax;
+        if (rmax + 0.01 < 0.5 * (g->D - 1)) gd.unit = 2;
+    }
     return WMG_OK;
 }
 
@@ -1203,6 +1254,9 @@ static int32_t collect(wmg_plan *pl, int max_iter, wmg_solve_info *info, double 
     }
     WMG_CUDA(cudaStreamSynchronize(st));
     WMG_CUDA(cudaGetLastError());
+    if (const int e = tma_error_take())
+        return fail(WMG_ERR_CUDA, e == 1 ? "projector: a wait for staged pixels timed out"
+                                         : "projector: a candidate pixel fell outside its staged box");
     int32_t rc = WMG_OK;
     for (int i = 0; i < count; ++i) {
         const int q = pl->batch ? pl->order[i] : i;

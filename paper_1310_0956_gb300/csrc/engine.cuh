@@ -108,6 +108,12 @@ struct ProbSet {
     // groups of kProjGroup consecutive same-geometry problems, and one-image
     // tiles for the problems left over
     TileList projg, proj1;
+    // the group tiles read their pixels through TMA boxes (projector_tma.cu)
+    // when every problem has image side tma_n (> 0; a multiple of 4) and bins
+    // no wider than a pixel, its image is image number img / n^2 of a pool of
+    // tma_count images, and each group's images are consecutive there
+    int tma_n = 0;
+    int64_t tma_count = 0;
     int haar_smem = 0;
     // launch shapes of the projector / backprojector over this set's tiles
     // (CTAs per SM; 0 = 8), chosen by autotune(); they do not change results

@@ -200,6 +200,72 @@ void launch_project_f32(const GeomDev *G, const ProbDev *P, const int4 *tiles, i
     else k_project_f32<NW, 1><<<grid, 32 * NW, 0, st>>>(G, P, tiles, ntiles, a);
 }
 
+// Unit-bin backprojection sums of one thread's 4 pixels (column xo, rows
+// yo0 + 8r), two angles per compensated step (their contributions are added,
+// rounded explicitly, before the step). At each angle the candidates are the
+// bins k0 = rint(tau + hD - 1/2) and k0 + 1: the support half-width is at most
+// sqrt(1/2), so any pair picked within 0.29 bins of that one holds every bin
+// with a nonzero weight. Adding 1.5 * 2^23 rounds to an integer without the
+// conversion pipe: the sum's low mantissa bits hold k0, and subtracting the
+// constant again gives k0 as an exact float. The distance t_k0 - tau is
+// exact up to the one rounding of the tail pc (split trigonometry).
+// COVERED: both candidates always lie on the detector (GeomDev::unit == 2).
+template <bool COVERED, int IB>
+__device__ __forceinline__ void bp_unit_sums(const GeomDev &g, const float *const (&sg)[IB],
+                                             const bool (&act)[IB], float xo, float yo0,
+                                             float (&s)[IB][4], float (&cmp)[IB][4])
+{
+    constexpr float kRound = 12582912.f;   // 1.5 * 2^23
+    constexpr int kRoundBits = 0x4B400000;
+    const int m = g.m, D = g.D;
+    const float hD = g.hDf, ks = g.hDf - 0.5f;
+    for (int ang = 0; ang < m; ang += 2) {
+        const bool two = ang + 1 < m;
+        // (chi, clo, shi, slo) and (wa, wb, lmax, flags) of both angles
+        const float4 *q0 = reinterpret_cast<const float4 *>(g.angf + ang);
+        const float4 *q1 = reinterpret_cast<const float4 *>(g.angf + (two ? ang + 1 : ang));
+        const float4 t0 = __ldg(q0), c0 = __ldg(q0 + 1), t1 = __ldg(q1), c1 = __ldg(q1 + 1);
+        const float l0 = c0.z, l1 = two ? c1.z : 0.f;   // a missing second angle weighs 0
+        // the second angle's row: its own, or (no second angle) the first's
+        const int64_t roff0 = (int64_t)ang * D - kRoundBits, roff1 = (two ? roff0 + D : roff0);
+        float ph0 = __fmaf_rn(xo, t0.x, yo0 * t0.z), pc0 = __fmaf_rn(xo, t0.y, yo0 * t0.w);
+        float ph1 = __fmaf_rn(xo, t1.x, yo0 * t1.z), pc1 = __fmaf_rn(xo, t1.y, yo0 * t1.w);
+        const float dph0 = 8.f * t0.z, dpc0 = 8.f * t0.w, dph1 = 8.f * t1.z, dpc1 = 8.f * t1.w;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float y0 = __fadd_rn(__fadd_rn(ph0, pc0), ks) + kRound;
+            const float y1 = __fadd_rn(__fadd_rn(ph1, pc1), ks) + kRound;
+            const int b0 = __float_as_int(y0), b1 = __float_as_int(y1);   // k + kRoundBits
+            const float d0 = ((__fadd_rn(y0, -kRound) - hD) - ph0) - pc0;
+            const float d1 = ((__fadd_rn(y1, -kRound) - hD) - ph1) - pc1;
+            const float wa0 = chord_n(c0.x, c0.y, fabsf(d0)), wb0 = chord_n(c0.x, c0.y, fabsf(d0 + 1.f));
+            const float wa1 = chord_n(c1.x, c1.y, fabsf(d1)), wb1 = chord_n(c1.x, c1.y, fabsf(d1 + 1.f));
+            bool o00 = true, o01 = true, o10 = true, o11 = true;
+            if (!COVERED) {
+                const int k0 = b0 - kRoundBits, k1 = b1 - kRoundBits;
+                o00 = (unsigned)k0 < (unsigned)D; o01 = (unsigned)(k0 + 1) < (unsigned)D;
+                o10 = (unsigned)k1 < (unsigned)D; o11 = (unsigned)(k1 + 1) < (unsigned)D;
+            }
+#pragma unroll
+            for (int b = 0; b < IB; ++b) {
+                if (!act[b]) continue;
+                const float *row0 = sg[b] + roff0, *row1 = sg[b] + roff1;
+                const float u0 = o00 ? __ldg(row0 + b0) : 0.f, u1 = o01 ? __ldg(row0 + b0 + 1) : 0.f;
+                const float v0 = o10 ? __ldg(row1 + b1) : 0.f, v1 = o11 ? __ldg(row1 + b1 + 1) : 0.f;
+                // explicit rounding: no contraction into the Kahan step
+                const float x0 = __fmaf_rn(wa0, u0, __fmul_rn(wb0, u1));
+                const float x1 = __fmaf_rn(wa1, v0, __fmul_rn(wb1, v1));
+                const float rs = __fmaf_rn(x0, l0, __fmul_rn(x1, l1));
+                const float yk = rs - cmp[b][r];
+                const float tt = s[b][r] + yk;
+                cmp[b][r] = (tt - s[b][r]) - yk;
+                s[b][r] = tt;
+            }
+            ph0 += dph0; pc0 += dpc0; ph1 += dph1; pc1 += dpc1;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Backward: tile = {first problem, iy0, ix0, images} of 32 x 32 pixels of
 // `images` consecutive problems of one geometry (the launcher uses one image
@@ -249,45 +315,8 @@ k_backproject_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
 #pragma unroll
             for (int r = 0; r < 4; ++r) { s[b][r] = 0.f; cmp[b][r] = 0.f; }
         if (unit) {
-            // two angles per step: their contributions are added (rounded
-            // explicitly) before the compensated step
-            for (int ang = 0; ang < m; ang += 2) {
-                const bool two = ang + 1 < m;
-                const AngleF A0 = g.angf[ang];
-                const AngleF A1 = g.angf[two ? ang + 1 : ang];
-                const int64_t roff0 = (int64_t)ang * D, roff1 = (int64_t)(ang + 1) * D;
-                float ph0 = __fmaf_rn(xo, A0.chi, yo0 * A0.shi), pc0 = __fmaf_rn(xo, A0.clo, yo0 * A0.slo);
-                float ph1 = __fmaf_rn(xo, A1.chi, yo0 * A1.shi), pc1 = __fmaf_rn(xo, A1.clo, yo0 * A1.slo);
-                const float dph0 = 8.f * A0.shi, dpc0 = 8.f * A0.slo, dph1 = 8.f * A1.shi, dpc1 = 8.f * A1.slo;
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    // the two bins nearest tau at each angle (support half-width <= sqrt(1/2))
-                    const int k0 = __float2int_rd((ph0 + pc0) - t0 + hD);
-                    const float d0 = (((float)k0 - hD + t0) - ph0) - pc0;
-                    const float wa0 = chord_n(A0.wa, A0.wb, fabsf(d0)), wb0 = chord_n(A0.wa, A0.wb, fabsf(d0 + 1.f));
-                    const int k1 = __float2int_rd((ph1 + pc1) - t0 + hD);
-                    const float d1 = (((float)k1 - hD + t0) - ph1) - pc1;
-                    const float wa1 = chord_n(A1.wa, A1.wb, fabsf(d1)), wb1 = chord_n(A1.wa, A1.wb, fabsf(d1 + 1.f));
-                    const bool o00 = (unsigned)k0 < (unsigned)D, o01 = (unsigned)(k0 + 1) < (unsigned)D;
-                    const bool o10 = two && (unsigned)k1 < (unsigned)D, o11 = two && (unsigned)(k1 + 1) < (unsigned)D;
-#pragma unroll
-                    for (int b = 0; b < IB; ++b) {
-                        if (!act[b]) continue;
-                        const float *row0 = sg[b] + roff0, *row1 = sg[b] + roff1;
-                        const float u0 = o00 ? __ldg(row0 + k0) : 0.f, u1 = o01 ? __ldg(row0 + k0 + 1) : 0.f;
-                        const float v0 = o10 ? __ldg(row1 + k1) : 0.f, v1 = o11 ? __ldg(row1 + k1 + 1) : 0.f;
-                        // explicit rounding: no contraction into the Kahan step
-                        const float x0 = __fmaf_rn(wa0, u0, __fmul_rn(wb0, u1));
-                        const float x1 = __fmaf_rn(wa1, v0, __fmul_rn(wb1, v1));
-                        const float rs = __fmaf_rn(x0, A0.lmax, __fmul_rn(x1, A1.lmax));
-                        const float y = rs - cmp[b][r];
-                        const float tt = s[b][r] + y;
-                        cmp[b][r] = (tt - s[b][r]) - y;
-                        s[b][r] = tt;
-                    }
-                    ph0 += dph0; pc0 += dpc0; ph1 += dph1; pc1 += dpc1;
-                }
-            }
+            if (g.unit == 2) bp_unit_sums<true, IB>(g, sg, act, xo, yo0, s, cmp);
+            else bp_unit_sums<false, IB>(g, sg, act, xo, yo0, s, cmp);
         } else {
             for (int ang = 0; ang < m; ++ang) {
                 const AngleF A = g.angf[ang];

@@ -29,12 +29,13 @@ namespace wmg {
 // wb = hw/beta (sat = clamp to [0, 1], one saturating FMA); axis-aligned
 // angles use wa = 2^22, wb = 2^21 + 1/2, which is the step 1 / 1/2 / 0 at the
 // half-integer distances those rays have to pixel centres.
+// The fields the unit-bin backprojector reads are the first 28 bytes.
 struct __align__(16) AngleF {
     float chi, clo, shi, slo;
-    float hw_inv, inv_ab, lmax, hwx;
-    float inv_cc, slope, inv_slope, hw;
+    float wa, wb, lmax;       // normalised chord
     float flags;              // int bits: 1 = steep, 2 = axis-aligned
-    float wa, wb, cc;         // normalised chord; frame cos (cc_hi + cc_lo)
+    float hw_inv, inv_ab, hwx, hw;
+    float inv_cc, slope, inv_slope, cc;   // cc: frame cos
 };
 
 // Immutable per-geometry data (lengths in pixel widths, h = 1/n applied to
@@ -56,7 +57,10 @@ struct GeomDev {
     const AngleF *angf;      // m per-angle constants (FP32 kernels)
     float hf, dtf, t0f, hDf; // FP32 copies of h, dt, t0 and (D-1)/2
     int unit;                // bins of one pixel width, no offset: the FP32
-                             // backprojector takes its two-bin path
+                             // backprojector takes its two-bin path (1); 2: in
+                             // addition both candidate bins of every pixel of
+                             // every 32 x 32 tile lie on the detector at every
+                             // angle, so that path needs no bounds checks
 };
 
 // A weight counts as a nonzero of W when its chord exceeds this many pixel
@@ -173,6 +177,17 @@ void launch_project_f32(const GeomDev *G, const ProbDev *P, const int4 *tiles, i
                         const PjArgs &a, cudaStream_t st);
 void launch_backproject_f32(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
                             const BpArgs &a, bool unit, cudaStream_t st);
+// Group tiles (kProjGroup images) with the pixels staged by TMA
+// (projector_tma.cu): pools a.img / a.imgT of `count` images of side n (a
+// multiple of 4), problem p's image number img / n^2 there, the images of a
+// group consecutive. false: not launched (no tensor-map encoder, or
+// unaligned pools): use launch_project_f32.
+bool launch_project_f32_tma(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
+                            const PjArgs &a, int n, int64_t count, cudaStream_t st);
+// Error flag of the TMA projector since the last call (0: none; 1: a staged
+// copy wait timed out; 2: a candidate pixel outside its box), cleared.
+// Synchronising.
+int tma_error_take();
 template <class T>
 void launch_transpose(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
                       const void *src, void *dst, cudaStream_t st);

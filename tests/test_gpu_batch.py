@@ -117,3 +117,31 @@ def test_grouped_projector_tiles_equal_single(solver, cycle):
         assert torch.equal(x1, x_all[i * n * n:(i + 1) * n * n]), i
     plan.close()
     single.close()
+
+
+@pytest.mark.parametrize("geom", [(256, 36, 363, 1.0, 0.0), (64, 40, 140, 0.7, 0.3), (52, 17, 60, 1.0, -2.5),
+                                  (36, 12, 200, 0.5, 0.0), (30, 20, 45, 1.0, 0.0)])
+def test_grouped_projection_equals_single(geom):
+    # group tiles (8 images sharing the weights; their pixels staged in
+    # shared memory where the image side is a multiple of 4) against one
+    # image per tile: bitwise equal, and within the FP32 bound of the oracle.
+    # Geometries: the workload's, finer offset bins, a detector wider than
+    # the image (rays that miss it), and a side that is not a multiple of 4.
+    n, m, D, dt, t0 = geom
+    plan = wmg.Plan(n, m, D, levels=0, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F32,
+                    det_spacing=dt, det_offset=t0)
+    single = wmg.Plan(n, m, D, levels=0, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F32,
+                      det_spacing=dt, det_offset=t0)
+    imgs = np.stack([S.phantom(n, 6, S.seed_for(8, 40 + i)).reshape(-1) for i in range(9)])
+    x = torch.tensor(imgs.reshape(-1), dtype=torch.float32, device="cuda")
+    q = plan.project(x)
+    torch.cuda.synchronize()
+    op = oracle.Op(n, m, D, dt, t0)
+    for i in range(9):
+        qi = single.project(x[i * n * n:(i + 1) * n * n].contiguous())
+        assert torch.equal(qi, q[i * m * D:(i + 1) * m * D]), i
+    ref = op.project(imgs[3])
+    got = q[3 * m * D:4 * m * D].double().cpu().numpy()
+    assert np.abs(got - ref).max() <= 3e-6 * max(np.abs(ref).max(), 1e-300)
+    plan.close()
+    single.close()

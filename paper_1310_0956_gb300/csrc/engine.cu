@@ -765,6 +765,14 @@ int32_t make_geo(const wmg_geom *g, const wmg_opts *o, Geo &G, cudaStream_t st)
     }
     std::vector<AngleF> angf(g->m);
     fill_angle_table(cs.data(), g->m, angf.data());
+    // quarter-turn pairs: angle a + m/2 is angle a turned by pi/2 in the
+    // FP32 table, (c, s) -> (-s, c) with the same chord constants
+    gd.qpair = g->m % 2 == 0 && g->m >= 2;
+    for (int a = 0; gd.qpair && a < g->m / 2; ++a) {
+        const AngleF &u = angf[a], &v = angf[a + g->m / 2];
+        gd.qpair = v.chi == -u.shi && v.clo == -u.slo && v.shi == u.chi && v.slo == u.clo && v.wa == u.wa &&
+                   v.wb == u.wb && v.lmax == u.lmax;
+    }
     if (!G.cs64.ensure(g->m * sizeof(double2)) || !G.cs32.ensure(g->m * sizeof(float2)) ||
         !G.csx.ensure(g->m * sizeof(float4)) || !G.angf.ensure(g->m * sizeof(AngleF)))
         return fail(WMG_ERR_OOM, "plan allocation failed");

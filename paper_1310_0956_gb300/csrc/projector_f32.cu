@@ -200,191 +200,189 @@ void launch_project_f32(const GeomDev *G, const ProbDev *P, const int4 *tiles, i
     else k_project_f32<NW, 1><<<grid, 32 * NW, 0, st>>>(G, P, tiles, ntiles, a);
 }
 
-// Unit-bin backprojection sums of one thread's 4 pixels (column xo, rows
-// yo0 + 8r), two angles per compensated step (their contributions are added,
-// rounded explicitly, before the step). At each angle the candidates are the
-// bins k0 = rint(tau + hD - 1/2) and k0 + 1: the support half-width is at most
-// sqrt(1/2), so any pair picked within 0.29 bins of that one holds every bin
-// with a nonzero weight. Adding 1.5 * 2^23 rounds to an integer without the
-// conversion pipe: the sum's low mantissa bits hold k0, and subtracting the
-// constant again gives k0 as an exact float. The distance t_k0 - tau is
-// exact up to the one rounding of the tail pc (split trigonometry).
+// ---------------------------------------------------------------------------
+// Backward: tile = {problem, iy0, ix0, -} of 32 x 32 pixels, 128 threads;
+// thread = one column and kBpRows rows 4 apart. Geometries with unit bins
+// (g.unit) take the two-bin path, the others the general one; ALL_UNIT
+// (every geometry of the launch has unit bins) compiles the general path
+// out. Per-thread partials of the epilogue are summed over its rows in row
+// order, then over the lanes (fixed tree) and the 4 warps in order.
+// ---------------------------------------------------------------------------
+constexpr int kBpRows = 8;
+constexpr int kBpWarps = 32 / kBpRows;
+
+// Unit-bin sums of one thread's kBpRows pixels (column xo, rows yo0 + 4r),
+// two angles per compensated step (their contributions are added, rounded
+// explicitly, before the step). QPAIR (an even number of equiangular angles:
+// angle a + m/2 is angle a turned by a quarter, (c, s) -> (-s, c) exactly in
+// the table) pairs a with a + m/2: the pair shares its chord constants and
+// the second angle's split trigonometry follows from the first's; otherwise
+// a pairs with a + 1.
+// At each angle the candidates are the two bins nearest tau: t = m0, m0 + 1
+// with m0 = rint(tau - 1/2) (odd D: bins at integers) or t = m0 -+ 1/2 with
+// m0 = rint(tau) (even D). The support half-width is at most sqrt(1/2), so
+// every bin with a nonzero weight is one of them whatever the rounding of
+// tau. Adding 1.5 * 2^23 rounds to an integer without the conversion pipe:
+// the sum's low mantissa bits hold m0 and subtracting the constant again
+// gives it as an exact float. The half is taken off the exact head ph (odd D)
+// before the sum, so both parities cost the same; t - tau is exact up to the
+// one rounding of the tail pc (split trigonometry).
 // COVERED: both candidates always lie on the detector (GeomDev::unit == 2).
-template <bool COVERED, int IB>
-__device__ __forceinline__ void bp_unit_sums(const GeomDev &g, const float *const (&sg)[IB],
-                                             const bool (&act)[IB], float xo, float yo0,
-                                             float (&s)[IB][4], float (&cmp)[IB][4])
+template <bool COVERED, bool QPAIR>
+__device__ __forceinline__ void bp_unit_sums(const GeomDev &g, const float *__restrict__ sg, float xo, float yo0,
+                                             float (&s)[kBpRows], float (&cmp)[kBpRows])
 {
     constexpr float kRound = 12582912.f;   // 1.5 * 2^23
     constexpr int kRoundBits = 0x4B400000;
     const int m = g.m, D = g.D;
-    const float hD = g.hDf, ks = g.hDf - 0.5f;
-    for (int ang = 0; ang < m; ang += 2) {
-        const bool two = ang + 1 < m;
+    const bool odd = D & 1;
+    const float e = odd ? 0.5f : 0.f;
+    // bin of t = m0 (odd D) or m0 - 1/2 (even D), m0 in the mantissa bits
+    const int kofs = odd ? (D - 1) / 2 : D / 2 - 1;
+    const int npair = QPAIR ? m / 2 : (m + 1) / 2;
+    const float dy = (float)kBpWarps;
+    for (int pr = 0; pr < npair; ++pr) {
+        const int a0 = QPAIR ? pr : 2 * pr;
+        const bool two = QPAIR || a0 + 1 < m;
+        const int a1 = QPAIR ? pr + m / 2 : (two ? a0 + 1 : a0);
         // (chi, clo, shi, slo) and (wa, wb, lmax, flags) of both angles
-        const float4 *q0 = reinterpret_cast<const float4 *>(g.angf + ang);
-        const float4 *q1 = reinterpret_cast<const float4 *>(g.angf + (two ? ang + 1 : ang));
-        const float4 t0 = __ldg(q0), c0 = __ldg(q0 + 1), t1 = __ldg(q1), c1 = __ldg(q1 + 1);
+        const float4 *q0 = reinterpret_cast<const float4 *>(g.angf + a0);
+        const float4 t0 = __ldg(q0), c0 = __ldg(q0 + 1);
+        float4 t1, c1;
+        if (QPAIR) {
+            t1 = make_float4(-t0.z, -t0.w, t0.x, t0.y);
+            c1 = c0;
+        } else {
+            const float4 *q1 = reinterpret_cast<const float4 *>(g.angf + a1);
+            t1 = __ldg(q1);
+            c1 = __ldg(q1 + 1);
+        }
         const float l0 = c0.z, l1 = two ? c1.z : 0.f;   // a missing second angle weighs 0
         // the second angle's row: its own, or (no second angle) the first's
-        const int64_t roff0 = (int64_t)ang * D - kRoundBits, roff1 = (two ? roff0 + D : roff0);
-        float ph0 = __fmaf_rn(xo, t0.x, yo0 * t0.z), pc0 = __fmaf_rn(xo, t0.y, yo0 * t0.w);
-        float ph1 = __fmaf_rn(xo, t1.x, yo0 * t1.z), pc1 = __fmaf_rn(xo, t1.y, yo0 * t1.w);
-        const float dph0 = 8.f * t0.z, dpc0 = 8.f * t0.w, dph1 = 8.f * t1.z, dpc1 = 8.f * t1.w;
+        const float *row0 = sg + ((int64_t)a0 * D + kofs - kRoundBits);
+        const float *row1 = sg + ((int64_t)a1 * D + kofs - kRoundBits);
+        float ph0 = __fmaf_rn(xo, t0.x, yo0 * t0.z) - e, pc0 = __fmaf_rn(xo, t0.y, yo0 * t0.w);
+        float ph1 = __fmaf_rn(xo, t1.x, yo0 * t1.z) - e, pc1 = __fmaf_rn(xo, t1.y, yo0 * t1.w);
+        const float dph0 = dy * t0.z, dpc0 = dy * t0.w, dph1 = dy * t1.z, dpc1 = dy * t1.w;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const float y0 = __fadd_rn(__fadd_rn(ph0, pc0), ks) + kRound;
-            const float y1 = __fadd_rn(__fadd_rn(ph1, pc1), ks) + kRound;
-            const int b0 = __float_as_int(y0), b1 = __float_as_int(y1);   // k + kRoundBits
-            const float d0 = ((__fadd_rn(y0, -kRound) - hD) - ph0) - pc0;
-            const float d1 = ((__fadd_rn(y1, -kRound) - hD) - ph1) - pc1;
+        for (int r = 0; r < kBpRows; ++r) {
+            const float y0 = __fadd_rn(ph0, pc0) + kRound;
+            const float y1 = __fadd_rn(ph1, pc1) + kRound;
+            const int b0 = __float_as_int(y0), b1 = __float_as_int(y1);   // m0 + kRoundBits
+            const float d0 = (((__fadd_rn(y0, -kRound) - ph0) - 0.5f) - pc0);
+            const float d1 = (((__fadd_rn(y1, -kRound) - ph1) - 0.5f) - pc1);
             const float wa0 = chord_n(c0.x, c0.y, fabsf(d0)), wb0 = chord_n(c0.x, c0.y, fabsf(d0 + 1.f));
             const float wa1 = chord_n(c1.x, c1.y, fabsf(d1)), wb1 = chord_n(c1.x, c1.y, fabsf(d1 + 1.f));
             bool o00 = true, o01 = true, o10 = true, o11 = true;
             if (!COVERED) {
-                const int k0 = b0 - kRoundBits, k1 = b1 - kRoundBits;
+                const int k0 = b0 - kRoundBits + kofs, k1 = b1 - kRoundBits + kofs;
                 o00 = (unsigned)k0 < (unsigned)D; o01 = (unsigned)(k0 + 1) < (unsigned)D;
                 o10 = (unsigned)k1 < (unsigned)D; o11 = (unsigned)(k1 + 1) < (unsigned)D;
             }
-#pragma unroll
-            for (int b = 0; b < IB; ++b) {
-                if (!act[b]) continue;
-                const float *row0 = sg[b] + roff0, *row1 = sg[b] + roff1;
-                const float u0 = o00 ? __ldg(row0 + b0) : 0.f, u1 = o01 ? __ldg(row0 + b0 + 1) : 0.f;
-                const float v0 = o10 ? __ldg(row1 + b1) : 0.f, v1 = o11 ? __ldg(row1 + b1 + 1) : 0.f;
-                // explicit rounding: no contraction into the Kahan step
+            const float u0 = o00 ? __ldg(row0 + b0) : 0.f, u1 = o01 ? __ldg(row0 + b0 + 1) : 0.f;
+            const float v0 = o10 ? __ldg(row1 + b1) : 0.f, v1 = o11 ? __ldg(row1 + b1 + 1) : 0.f;
+            // explicit rounding: no contraction into the Kahan step
+            float rs;
+            if (QPAIR) {
+                const float x0 = __fmaf_rn(wa0, u0, __fmul_rn(wb0, u1));
+                rs = __fmul_rn(__fmaf_rn(wa1, v0, __fmaf_rn(wb1, v1, x0)), l0);
+            } else {
                 const float x0 = __fmaf_rn(wa0, u0, __fmul_rn(wb0, u1));
                 const float x1 = __fmaf_rn(wa1, v0, __fmul_rn(wb1, v1));
-                const float rs = __fmaf_rn(x0, l0, __fmul_rn(x1, l1));
-                const float yk = rs - cmp[b][r];
-                const float tt = s[b][r] + yk;
-                cmp[b][r] = (tt - s[b][r]) - yk;
-                s[b][r] = tt;
+                rs = __fmaf_rn(x0, l0, __fmul_rn(x1, l1));
             }
+            const float yk = rs - cmp[r];
+            const float tt = s[r] + yk;
+            cmp[r] = (tt - s[r]) - yk;
+            s[r] = tt;
             ph0 += dph0; pc0 += dpc0; ph1 += dph1; pc1 += dpc1;
         }
     }
 }
 
-// ---------------------------------------------------------------------------
-// Backward: tile = {first problem, iy0, ix0, images} of 32 x 32 pixels of
-// `images` consecutive problems of one geometry (the launcher uses one image
-// per tile); thread = one column and 4 rows 8 apart. The bins and weights of
-// a pixel and angle are computed once for the tile's images. Geometries with
-// unit bins (g.unit) take the two-bin path, the others the general one;
-// ALL_UNIT (every geometry of the launch has unit bins) compiles the general
-// path out.
-// ---------------------------------------------------------------------------
-template <int EPI, bool ALL_UNIT, int IB>
-__global__ void __launch_bounds__(256, 2)
+template <int EPI, bool ALL_UNIT>
+__global__ void __launch_bounds__(32 * kBpWarps, 4)
 k_backproject_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
                   const int4 *__restrict__ tiles, int ntiles, BpArgs a)
 {
-    __shared__ double red[IB][8];
+    __shared__ double red[kBpWarps];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 tl = tiles[t];
-        const int nimg = min(IB, max(1, tl.w));
-        const ProbDev p0 = P[tl.x];
-        const float *sg[IB];
-        bool act[IB];
-        bool any = false;
-#pragma unroll
-        for (int b = 0; b < IB; ++b) {
-            act[b] = false;
-            sg[b] = static_cast<const float *>(a.sino);
-            if (b < nimg) {
-                const ProbDev pb = P[tl.x + b];
-                act[b] = slot_active(a.S, pb.slot);
-                sg[b] = static_cast<const float *>(a.sino) + pb.sino;
-            }
-            any |= act[b];
-        }
-        if (!any) continue;                                        // CTA-uniform
-        const GeomDev &g = G[p0.geom];
+        const ProbDev pb = P[tl.x];
+        if (!slot_active(a.S, pb.slot)) continue;                  // CTA-uniform
+        const float *sg = static_cast<const float *>(a.sino) + pb.sino;
+        const GeomDev &g = G[pb.geom];
         const int n = g.n, m = g.m, D = g.D;
         const int ix = tl.z + tx;
         const float half_n = 0.5f * (float)n;
         const float xo = (float)ix + 0.5f - half_n;
         const float yo0 = (float)(tl.y + ty) + 0.5f - half_n;
-        const float hD = g.hDf, dt = g.dtf, t0 = g.t0f, inv_dt = 1.f / g.dtf;
         const bool unit = ALL_UNIT || g.unit;
-        float s[IB][4], cmp[IB][4];
+        float s[kBpRows], cmp[kBpRows];
 #pragma unroll
-        for (int b = 0; b < IB; ++b)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) { s[b][r] = 0.f; cmp[b][r] = 0.f; }
+        for (int r = 0; r < kBpRows; ++r) { s[r] = 0.f; cmp[r] = 0.f; }
         if (unit) {
-            if (g.unit == 2) bp_unit_sums<true, IB>(g, sg, act, xo, yo0, s, cmp);
-            else bp_unit_sums<false, IB>(g, sg, act, xo, yo0, s, cmp);
+            const bool qp = g.qpair;
+            if (g.unit == 2) {
+                if (qp) bp_unit_sums<true, true>(g, sg, xo, yo0, s, cmp);
+                else bp_unit_sums<true, false>(g, sg, xo, yo0, s, cmp);
+            } else {
+                if (qp) bp_unit_sums<false, true>(g, sg, xo, yo0, s, cmp);
+                else bp_unit_sums<false, false>(g, sg, xo, yo0, s, cmp);
+            }
         } else {
+            const float hD = g.hDf, dt = g.dtf, t0 = g.t0f, inv_dt = 1.f / g.dtf;
+            const float dy = (float)kBpWarps;
             for (int ang = 0; ang < m; ++ang) {
                 const AngleF A = g.angf[ang];
                 const bool axis = __float_as_int(A.flags) & 2;
                 const int64_t roff = (int64_t)ang * D;
                 float ph = __fmaf_rn(xo, A.chi, yo0 * A.shi);        // exact head of tau
                 float pc = __fmaf_rn(xo, A.clo, yo0 * A.slo);        // rounded tail
-                const float dph = 8.f * A.shi, dpc = 8.f * A.slo;
+                const float dph = dy * A.shi, dpc = dy * A.slo;
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
+                for (int r = 0; r < kBpRows; ++r) {
                     const float hwb = A.hw * inv_dt;
                     const int k0 = __float2int_ru(((ph + pc) - t0) * inv_dt + hD - hwb);
                     const int nc = __float2int_rd(2.f * hwb) + 1;
-                    float rs[IB];
-#pragma unroll
-                    for (int b = 0; b < IB; ++b) rs[b] = 0.f;
+                    float rs = 0.f;
                     for (int q = 0; q < nc; ++q) {
                         const int kk = k0 + q;
                         if ((unsigned)kk < (unsigned)D) {
                             const float tkk = __fmaf_rn((float)kk - hD, dt, t0);
                             const float wq = chord_f(A, axis, fabsf((tkk - ph) - pc));
-#pragma unroll
-                            for (int b = 0; b < IB; ++b)
-                                if (act[b]) rs[b] = __fmaf_rn(wq, __ldg(sg[b] + roff + kk), rs[b]);
+                            rs = __fmaf_rn(wq, __ldg(sg + roff + kk), rs);
                         }
                     }
-#pragma unroll
-                    for (int b = 0; b < IB; ++b) {
-                        if (!act[b]) continue;
-                        const float y = rs[b] - cmp[b][r];
-                        const float tt = s[b][r] + y;
-                        cmp[b][r] = (tt - s[b][r]) - y;
-                        s[b][r] = tt;
-                    }
+                    const float y = rs - cmp[r];
+                    const float tt = s[r] + y;
+                    cmp[r] = (tt - s[r]) - y;
+                    s[r] = tt;
                     ph += dph;
                     pc += dpc;
                 }
             }
         }
+        double part = 0.0;
+        if (ix < n) {
 #pragma unroll
-        for (int b = 0; b < IB; ++b) {
-            if (!act[b]) continue;                                  // uniform across the CTA
-            const ProbDev pb = P[tl.x + b];
-            double part = 0.0;
-            if (ix < n) {
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const int iy = tl.y + ty + 8 * r;
-                    if (iy < n)
-                        part += bp_epilogue<float, EPI>(g, pb, a, ix, iy,
-                                                        ((double)s[b][r] - (double)cmp[b][r]) * g.h);
-                }
-            }
-            if (a.part) {
-                part = warp_sum_fixed(part);
-                if (tx == 0) red[b][ty] = part;
+            for (int r = 0; r < kBpRows; ++r) {
+                const int iy = tl.y + ty + kBpWarps * r;
+                if (iy < n)
+                    part += bp_epilogue<float, EPI>(g, pb, a, ix, iy, ((double)s[r] - (double)cmp[r]) * g.h);
             }
         }
         if (a.part) {
+            part = warp_sum_fixed(part);
+            if (tx == 0) red[ty] = part;
             __syncthreads();
-            if (threadIdx.x < IB && act[threadIdx.x]) {
-                const int b = threadIdx.x;
+            if (threadIdx.x == 0) {
                 double v = 0.0;
-                for (int i = 0; i < 8; ++i) v += red[b][i];
-                // the problem's partial of this pixel tile, at the index its
-                // one-image tile list gives it
+                for (int i = 0; i < kBpWarps; ++i) v += red[i];
+                // the problem's partial of this pixel tile
                 const int ntx = (n + 31) / 32;
-                a.part[a.part_base[tl.x + b] + (tl.y / 32) * ntx + tl.z / 32] = v;
+                a.part[a.part_base[tl.x] + (tl.y / 32) * ntx + tl.z / 32] = v;
             }
             __syncthreads();
         }
@@ -396,11 +394,11 @@ void launch_backproject_f32(const GeomDev *G, const ProbDev *P, const int4 *tile
 {
     if (ntiles <= 0) return;
     count_launches(1);
-    const int grid = min(ntiles, num_sms() * (a.ctas_per_sm > 0 ? a.ctas_per_sm : 8));
+    const int grid = min(ntiles, num_sms() * 2 * (a.ctas_per_sm > 0 ? a.ctas_per_sm : 8));
 #define WMG_BPF(E)                                                                                  \
     case E:                                                                                         \
-        if (unit) k_backproject_f32<E, true, 1><<<grid, 256, 0, st>>>(G, P, tiles, ntiles, a);      \
-        else k_backproject_f32<E, false, 1><<<grid, 256, 0, st>>>(G, P, tiles, ntiles, a);          \
+        if (unit) k_backproject_f32<E, true><<<grid, 32 * kBpWarps, 0, st>>>(G, P, tiles, ntiles, a);  \
+        else k_backproject_f32<E, false><<<grid, 32 * kBpWarps, 0, st>>>(G, P, tiles, ntiles, a);      \
         break;
     switch (a.epi) {
         WMG_BPF(BP_STORE) WMG_BPF(BP_CGLS_S) WMG_BPF(BP_RESID) WMG_BPF(BP_POST)

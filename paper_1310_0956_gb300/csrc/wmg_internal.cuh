@@ -61,6 +61,8 @@ struct GeomDev {
                              // addition both candidate bins of every pixel of
                              // every 32 x 32 tile lie on the detector at every
                              // angle, so that path needs no bounds checks
+    int qpair;               // even m, angle a + m/2 = angle a turned by pi/2 in
+                             // the FP32 table (the unit-bin backprojector pairs them)
 };
 
 // A weight counts as a nonzero of W when its chord exceeds this many pixel

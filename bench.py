@@ -635,24 +635,29 @@ def load_peaks():
         return {}
 
 
-# DRAM traffic of the FP32 projector / backprojector measured by ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum, 16-image launches of the
-# workload geometry; profiles/dram_traffic_k_project_backproject_256x256.md),
-# per image; valid while the kernels' source is the one measured (hash).
-KERNEL_TRAFFIC = {"source": "paper_1310_0956_gb300/csrc/projector_f32.cu", "sha256_16": "2101b2b8c2c8510b",
-                  "project_bytes_per_image": (8495360 + 24832) / 16.0,
-                  "backproject_bytes_per_image": (4037632 + 512) / 16.0}
+# DRAM traffic of the FP32 projector (8-image TMA group tiles) and
+# backprojector measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum,
+# 16-image launches of the workload geometry;
+# profiles/dram_traffic_k_project_backproject_256x256.md), per image; each
+# valid while its kernel's source is the one measured (hash), else null.
+KERNEL_TRAFFIC = {
+    "project": {"source": "paper_1310_0956_gb300/csrc/projector_tma.cu", "sha256_16": "6115a9f383afc7ae",
+                "bytes_per_image": (8497664 + 8498432) / 2 / 16.0},
+    "backproject": {"source": "paper_1310_0956_gb300/csrc/projector_f32.cu", "sha256_16": "57f012eb8cf87922",
+                    "bytes_per_image": (4067840 + 4100096) / 2 / 16.0},
+}
 
 
 def _kernel_traffic(name: str, images: float):
     import hashlib
+    rec = KERNEL_TRAFFIC[name]
     try:
-        with open(os.path.join(ROOT, KERNEL_TRAFFIC["source"]), "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest()[:16] != KERNEL_TRAFFIC["sha256_16"]:
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest()[:16] != rec["sha256_16"]:
                 return None
     except OSError:
         return None
-    return KERNEL_TRAFFIC[name + "_bytes_per_image"] * images
+    return rec["bytes_per_image"] * images
 
 
 def roofline_entry(prof: dict, P0, B: int) -> dict:

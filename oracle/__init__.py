@@ -7,7 +7,9 @@ it never imports the product library. The arithmetic lives in `wmg_oracle.c`
 with ctypes on numpy arrays.
 
 Every function follows a passage of Cools et al., arXiv 1310.0956:
-  Op.project / backproject    W x and W^T y as SpMVs (Section 2.1, eq. sys)
+  Op.project / backproject    W x and W^T y as SpMVs (Section 2.1, eq. sys);
+                              W by exact intersection lengths or by Joseph's
+                              interpolating kernel
   sirt                        eq. sirt_it with R, C of Section 2.2.1
   packet_analysis/synthesis   Haar operators eq. intops, eq. intops_wav,
                               eq. 1of4-4of4 applied recursively (Section 3.1.3)
@@ -62,6 +64,9 @@ def _load():
         lib.or_op_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                      C.c_void_p, C.c_int]
         lib.or_op_free.argtypes = [vp]
+        lib.or_ray_row_k.restype = C.c_int64
+        lib.or_ray_row_k.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, vp, C.c_int, C.c_int,
+                                     C.c_int, _i32p, _dp, C.c_int64]
         lib.or_ray_row.restype = C.c_int64
         lib.or_ray_row.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, vp, C.c_int, C.c_int,
                                    _i32p, _dp, C.c_int64]
@@ -117,7 +122,13 @@ def weight_trapezoid(c: float, s: float, delta: float) -> float:
     return _load().or_weight_trapezoid(c, s, delta)
 
 
-def ray_row(n: int, m: int, D: int, a: int, k: int, dt: float = 1.0, t0: float = 0.0, angles=None):
+KERNEL_STRIP = "strip"      # exact pixel-line intersection lengths
+KERNEL_JOSEPH = "joseph"    # Joseph's interpolating kernel (Section 2.1)
+_METHOD = {KERNEL_STRIP: 0, KERNEL_JOSEPH: 2}
+
+
+def ray_row(n: int, m: int, D: int, a: int, k: int, dt: float = 1.0, t0: float = 0.0, angles=None,
+            kernel: str = KERNEL_STRIP):
     """Row (a, k) of W as (columns, values), built by the same walk as Op
     (Section 2.1) without assembling W: for sampled checks at large sizes."""
     lib = _load()
@@ -125,8 +136,8 @@ def ray_row(n: int, m: int, D: int, a: int, k: int, dt: float = 1.0, t0: float =
     col = np.zeros(cap, np.int32)
     val = np.zeros(cap, np.float64)
     ang = None if angles is None else _f64(angles)
-    cnt = lib.or_ray_row(n, m, D, dt, t0, None if ang is None else ang.ctypes.data_as(C.c_void_p), a, k,
-                         col, val, cap)
+    cnt = lib.or_ray_row_k(n, m, D, dt, t0, None if ang is None else ang.ctypes.data_as(C.c_void_p), a, k,
+                           _METHOD[kernel], col, val, cap)
     if cnt < 0:
         raise RuntimeError("row longer than expected")
     return col[:cnt].copy(), val[:cnt].copy()
@@ -136,12 +147,19 @@ class Op:
     """Explicit projection matrix W (M x N CSR, FP64) of a parallel-beam
     geometry: n x n image, m angles, D detector bins of spacing `dt` pixels,
     offset `t0` pixels; `angles` None means theta_a = a*pi/m.
-    method 0 = parametric walk (production), 1 = brute-force clipping of each
-    line against each pixel (tiny n only)."""
+    kernel "strip": exact intersection lengths, by the parametric walk
+    (method 0) or by brute-force clipping of each line against each pixel
+    (method 1, tiny n only); kernel "joseph": Joseph's interpolation along the
+    dominant axis (Section 2.1)."""
 
     def __init__(self, n: int, m: int, D: int, dt: float = 1.0, t0: float = 0.0,
-                 angles=None, method: int = 0):
+                 angles=None, method: int = 0, kernel: str = KERNEL_STRIP):
         lib = _load()
+        if kernel == KERNEL_JOSEPH:
+            method = 2
+        elif kernel != KERNEL_STRIP:
+            raise ValueError("kernel must be 'strip' or 'joseph'")
+        self.kernel = kernel
         self.n, self.m, self.D = n, m, D
         self.N, self.M = n * n, m * D
         self._angles = None if angles is None else _f64(angles)

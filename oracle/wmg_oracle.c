@@ -189,6 +189,35 @@ static double clip_len(double c, double s, double T, double x0, double y0)
     return hi > lo ? hi - lo : 0.0;
 }
 
+/* Joseph's kernel (Joseph 1982), the paper's choice of W (Section 2.1): the
+ * line {x c + y s = T} is sampled where it crosses the centre line of every
+ * pixel row (if |c| >= |s|: the line runs closer to the y axis) or every
+ * pixel column (otherwise); at each crossing the image is interpolated
+ * linearly between the two nearest pixel centres of that row (column), and
+ * each sample is weighted by the length of line between consecutive rows
+ * (columns), 1 / max(|c|, |s|) pixel widths. Pixels outside the image count as
+ * zero. Weights in pixel widths. */
+static void ray_joseph(int n, double c, double s, double T, rowbuf *rb)
+{
+    const double half = 0.5 * n;
+    const int by_rows = fabs(c) >= fabs(s);
+    const double step = 1.0 / (by_rows ? fabs(c) : fabs(s));
+    for (int r = 0; r < n; r++) {
+        const double u = r + 0.5 - half;                      /* row y (column x) centre */
+        const double v = by_rows ? (T - u * s) / c : (T - u * c) / s;   /* crossing x (y) */
+        const double q = v + half - 0.5;                      /* in pixel-centre index units */
+        const double f = floor(q);
+        const int i0 = (int)f;
+        const double w1 = q - f, w0 = 1.0 - w1;
+        for (int e = 0; e < 2; e++) {
+            const int i = i0 + e;
+            const double w = e ? w1 : w0;
+            if (i < 0 || i >= n || !(w > 0.0)) continue;
+            rb_add(rb, by_rows ? r * n + i : i * n + r, w * step);
+        }
+    }
+}
+
 /* Trapezoid law: chord of a unit pixel at signed distance delta from its
  * centre, for a line with unit normal (c, s). Test-only closed form. */
 double or_weight_trapezoid(double c, double s, double delta)
@@ -228,6 +257,8 @@ or_op *or_op_create(int n, int m, int D, double dt, double t0,
             rb.len = 0;
             if (method == 0) {
                 ray_siddon(n, op->c[a], op->s[a], T, &rb);
+            } else if (method == 2) {
+                ray_joseph(n, op->c[a], op->s[a], T, &rb);
             } else {
                 for (int iy = 0; iy < n; iy++)
                     for (int ix = 0; ix < n; ix++)
@@ -263,8 +294,8 @@ or_op *or_op_create(int n, int m, int D, double dt, double t0,
  * memory. Entries sorted by column, repeated pixels merged, values in
  * unit-square lengths. Returns the entry count; if it exceeds cap, nothing is
  * written and the negated count is returned. */
-int64_t or_ray_row(int n, int m, int D, double dt, double t0, const double *angles, int a, int k,
-                   int32_t *col, double *val, int64_t cap)
+int64_t or_ray_row_k(int n, int m, int D, double dt, double t0, const double *angles, int a, int k,
+                     int method, int32_t *col, double *val, int64_t cap)
 {
     if (n <= 0 || m <= 0 || D <= 0 || a < 0 || a >= m || k < 0 || k >= D) return 0;
     double c, s;
@@ -273,7 +304,8 @@ int64_t or_ray_row(int n, int m, int D, double dt, double t0, const double *angl
     dt = dt > 0 ? dt : 1.0;
     const double T = (k - 0.5 * (D - 1)) * dt + t0, h = 1.0 / n;
     rowbuf rb = {0};
-    ray_siddon(n, c, s, T, &rb);
+    if (method == 2) ray_joseph(n, c, s, T, &rb);
+    else ray_siddon(n, c, s, T, &rb);
     qsort(rb.e, (size_t)rb.len, sizeof(entry), cmp_entry);
     int64_t cnt = 0;
     for (int64_t q = 0; q < rb.len; q++)
@@ -288,6 +320,12 @@ int64_t or_ray_row(int n, int m, int D, double dt, double t0, const double *angl
     }
     free(rb.e);
     return cnt;
+}
+
+int64_t or_ray_row(int n, int m, int D, double dt, double t0, const double *angles, int a, int k,
+                   int32_t *col, double *val, int64_t cap)
+{
+    return or_ray_row_k(n, m, D, dt, t0, angles, a, k, 0, col, val, cap);
 }
 
 void or_op_free(or_op *op)

@@ -155,7 +155,7 @@ void build_tiles(const wmg_plan *pl, ProbSet &ps)
         const Geo &G = *pl->geos[ps.h[q].geom];
         const GeomDev &g = G.g;
         const int W = G.haar_W;
-        ps.haar_smem = std::max(ps.haar_smem, g.B * (W + 1));
+        ps.haar_smem = std::max(ps.haar_smem, g.B * (W + W / g.B + 1));
         for (int a = 0; a < g.m; ++a)
             for (int k0 = 0; k0 < g.D; k0 += 32) ps.proj.h.push_back(make_int4(q, a, k0, 0));
         for (int iy = 0; iy < g.n; iy += 32)

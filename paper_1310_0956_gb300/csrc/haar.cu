@@ -35,8 +35,14 @@ __device__ __forceinline__ int leaf_of(int uy, int ux, int L)
     return (spread_bits(bitrev_bits(uy, L), L) << 1) | spread_bits(bitrev_bits(ux, L), L);
 }
 
+// Shared-memory column of strip column x: one pad slot after every B-wide
+// segment, so that the 16 block columns a warp touches at one Walsh position
+// (stride B + 1 doubles) fall in different banks.
+__device__ __forceinline__ int padx(int x, int L) { return x + (x >> L); }
+
 // In-place Walsh-Hadamard butterflies over a B x W strip in shared memory
-// (pitch pw), along x (within every B-wide segment) then along y.
+// (pitch pw, columns padded by padx), along x (within every B-wide segment)
+// then along y.
 __device__ __forceinline__ void strip_wht(double *sm, int B, int W, int L, int pw)
 {
     const int halfx = B * (W >> 1);
@@ -46,9 +52,10 @@ __device__ __forceinline__ void strip_wht(double *sm, int B, int W, int L, int p
             const int r = q / (W >> 1), pi = q - r * (W >> 1);
             const int i = ((pi >> st) << (st + 1)) | (pi & (hbit - 1));
             double *row = sm + r * pw;
-            const double a = row[i], b = row[i + hbit];
-            row[i] = a + b;
-            row[i + hbit] = a - b;
+            const int i0 = padx(i, L), i1 = padx(i + hbit, L);
+            const double a = row[i0], b = row[i1];
+            row[i0] = a + b;
+            row[i1] = a - b;
         }
         __syncthreads();
     }
@@ -56,7 +63,7 @@ __device__ __forceinline__ void strip_wht(double *sm, int B, int W, int L, int p
     for (int st = 0; st < L; ++st) {
         const int hbit = 1 << st;
         for (int q = threadIdx.x; q < halfy; q += blockDim.x) {
-            const int col = q % W, pi = q / W;
+            const int col = padx(q % W, L), pi = q / W;
             const int i = ((pi >> st) << (st + 1)) | (pi & (hbit - 1));
             const double a = sm[i * pw + col], b = sm[(i + hbit) * pw + col];
             sm[i * pw + col] = a + b;
@@ -80,11 +87,11 @@ k_haar_analysis(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
         const ProbDev pd = P[tl.x];
         if (!slot_active(a.S, pd.slot)) continue;
         const GeomDev &g = G[pd.geom];
-        const int n = g.n, B = g.B, L = g.L, W = tl.w, pw = W + 1;
+        const int n = g.n, B = g.B, L = g.L, W = tl.w, pw = W + (W >> L) + 1;
         const TIn *in = static_cast<const TIn *>(a.in) + pd.img;
         for (int q = threadIdx.x; q < B * W; q += blockDim.x) {
             const int r = q / W, x = q - r * W;
-            sm[r * pw + x] = (double)in[(int64_t)(tl.y + r) * n + tl.z + x];
+            sm[r * pw + padx(x, L)] = (double)in[(int64_t)(tl.y + r) * n + tl.z + x];
         }
         __syncthreads();
         strip_wht(sm, B, W, L, pw);
@@ -94,7 +101,7 @@ k_haar_analysis(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
         for (int q = threadIdx.x; q < B * W; q += blockDim.x) {
             const int bc = q % nb, rest = q / nb, ux = rest % B, uy = rest / B;
             const int k = leaf_of(uy, ux, L);
-            const TOut v = (TOut)(sm[uy * pw + bc * B + ux] * scale);
+            const TOut v = (TOut)(sm[uy * pw + bc * (B + 1) + ux] * scale);
             const int64_t o = (int64_t)k * g.P + (int64_t)cy * g.nc + cx0 + bc;
             if (MODE == HA_STORE) C[o] = v;
             else if (k >= pd.kout0 && k < pd.kout1) {
@@ -119,7 +126,7 @@ k_haar_synthesis(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
         const ProbDev pd = P[tl.x];
         if (!slot_active(a.S, pd.slot)) continue;
         const GeomDev &g = G[pd.geom];
-        const int n = g.n, B = g.B, L = g.L, W = tl.w, pw = W + 1;
+        const int n = g.n, B = g.B, L = g.L, W = tl.w, pw = W + (W >> L) + 1;
         const int nb = W / B, cy = tl.y / B, cx0 = tl.z / B;
         const TIn *E = static_cast<const TIn *>(a.in) + pd.coef;
         for (int q = threadIdx.x; q < B * W; q += blockDim.x) {
@@ -128,7 +135,7 @@ k_haar_synthesis(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
             double v = 0.0;
             if (MODE != HS_STORE_MASKED || (k >= pd.kin0 && k < pd.kin1))
                 v = (double)E[(int64_t)k * g.P + (int64_t)cy * g.nc + cx0 + bc];
-            sm[uy * pw + bc * B + ux] = v;
+            sm[uy * pw + bc * (B + 1) + ux] = v;
         }
         __syncthreads();
         strip_wht(sm, B, W, L, pw);
@@ -137,16 +144,16 @@ k_haar_synthesis(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
         for (int q = threadIdx.x; q < B * W; q += blockDim.x) {
             const int r = q / W, x = q - r * W;
             const int64_t j = pd.img + (int64_t)(tl.y + r) * n + tl.z + x;
-            const double v = sm[r * pw + x] * scale;
+            const double v = sm[r * pw + padx(x, L)] * scale;
             if (MODE == HS_CORRECT) {
                 const double zv = a.z[j] + v;
                 a.z[j] = zv;
                 const TOut zt = (TOut)zv;
-                sm[r * pw + x] = (double)zt;
+                sm[r * pw + padx(x, L)] = (double)zt;
                 if (out) out[j] = zt;
             } else {
                 const TOut vt = (TOut)v;
-                sm[r * pw + x] = (double)vt;
+                sm[r * pw + padx(x, L)] = (double)vt;
                 out[j] = vt;
             }
         }
@@ -155,7 +162,7 @@ k_haar_synthesis(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
             TOut *outT = static_cast<TOut *>(a.outT);
             for (int q = threadIdx.x; q < B * W; q += blockDim.x) {
                 const int x = q / B, r = q - x * B;
-                outT[pd.img + (int64_t)(tl.z + x) * n + tl.y + r] = (TOut)sm[r * pw + x];
+                outT[pd.img + (int64_t)(tl.z + x) * n + tl.y + r] = (TOut)sm[r * pw + padx(x, L)];
             }
         }
         __syncthreads();

@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--no-comparator", action="store_true", help="skip the stored-W (CSR) comparator leg")
     ap.add_argument("--no-variant", action="store_true",
                     help="skip the smoothed-cycle variant (nu1 = nu2 = 1) of the main workload")
+    ap.add_argument("--no-joseph", action="store_true",
+                    help="skip the leg with Joseph's kernel as W (same batch and solver)")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 1024x1024 / 1024-angle leg (mixed FP32 path vs the FP64 GPU path)")
     ap.add_argument("--kernel-case", action="store_true",
@@ -374,6 +376,11 @@ def run_ours(args, rank, world, local):
             "stored_w_comparator": comparator,
             "smoothed_cycle_variant": variant,
         }
+        if not args.no_joseph and world == 1:
+            try:
+                line["joseph_kernel"] = joseph_leg(args, dev, probs, flush)
+            except Exception as e:
+                line["joseph_kernel"] = {"unavailable": f"{type(e).__name__}: {e}"}
         if not args.no_large and world == 1:
             try:
                 line["large"] = large_leg(dev)
@@ -392,6 +399,58 @@ def run_ours(args, rank, world, local):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# Joseph leg: the same batch and solver with W = Joseph's interpolating kernel
+# (the paper's projector, Section 2.1) in place of exact intersection lengths
+# ---------------------------------------------------------------------------
+def joseph_leg(args, dev, probs, flush) -> dict:
+    import torch
+    import paper_1310_0956_gb300 as wmg
+    P0 = probs[0]
+    B, N, M = len(probs), P0.N, P0.M
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = wmg.Plan(P0.n, P0.m, P0.D, levels=LEVELS, nu1=NU1, nu2=NU2, hybrid_depth=HYB,
+                    cycle=wmg.CYCLE_HYBRID, precision=wmg.PREC_F32, kernel=wmg.KERNEL_JOSEPH)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    plan64 = wmg.Plan(P0.n, P0.m, P0.D, levels=0, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE,
+                      precision=wmg.PREC_F64, kernel=wmg.KERNEL_JOSEPH)
+    imgs = torch.tensor(np.stack([p.image() for p in probs]).reshape(-1), dtype=torch.float64, device=dev)
+    b64 = plan64.project(imgs).view(B, M)
+    noise = torch.tensor(np.stack([p.noise_unit() for p in probs]), dtype=torch.float64, device=dev)
+    sigma = torch.tensor([p.noise for p in probs], dtype=torch.float64, device=dev)[:, None] * \
+        b64.abs().amax(dim=1, keepdim=True)
+    b = (b64 + sigma * noise).to(torch.float32).contiguous().view(-1)
+    plan64.close()
+    del imgs, b64, noise
+    x = torch.empty(B * N, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        plan.solve(b, wmg.SOLVER_GMRES, True, MAX_ITER, RTOL, RESTART, out=x)
+    ts, its, sts = [], [], []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, info, _, _ = plan.solve(b, wmg.SOLVER_GMRES, True, MAX_ITER, RTOL, RESTART, out=x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+        its.extend(i[0] for i in info)
+        sts.extend(i[1] for i in info)
+    prof = plan.profile_step(b, x, MAX_ITER, RTOL, RESTART)
+    out = {"workload": "256x256_180ang_363det_noise1pct, W = Joseph's kernel", "problems": B,
+           "solver": f"WMG-GMRES(20), hybrid cycle depth {HYB}, nu1=nu2={NU1}", "recon_per_s": B / float(np.mean(ts)),
+           "ms_per_step": float(np.mean(ts)) * 1e3, "iters_mean": float(np.mean(its)),
+           "all_converged": bool(all(s_ == 0 for s_ in sts)), "plan_setup_s": setup_s,
+           "nnz_per_image": prof["nnz_per_image"],
+           "project_ms_per_launch": prof["project"]["mean_ms"],
+           "backproject_ms_per_launch": prof["backproject"]["mean_ms"]}
+    plan.close()
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -66,6 +66,12 @@ extern "C" {
 #define WMG_CYCLE_SYMMETRIC  2  /* hybrid followed by a second LL correction
                                    (LL, rest, LL): symmetric, for CGLS */
 
+#define WMG_KERNEL_STRIP   0  /* w_ij = length of line i inside pixel j (exact) */
+#define WMG_KERNEL_JOSEPH  1  /* Joseph's kernel (Section 2.1): the line sampled
+                                 at every row (column) centre of the dominant
+                                 axis, linear interpolation between the two
+                                 nearest pixel centres, weight = step length */
+
 #define WMG_SOLVER_SIRT   0   /* eq. sirt_it */
 #define WMG_SOLVER_CGLS   1   /* CGLS / PCG on the normal equations */
 #define WMG_SOLVER_GMRES  2   /* restarted GMRES, right preconditioning */
@@ -81,6 +87,7 @@ typedef struct wmg_geom {
     int32_t D;              /* detector bins per angle, >= 1 */
     double det_spacing;     /* bin spacing in pixel widths; <= 0 means 1 */
     double det_offset;      /* detector centre offset in pixel widths */
+    int32_t kernel;         /* WMG_KERNEL_STRIP (0) or WMG_KERNEL_JOSEPH (1) */
 } wmg_geom;
 
 typedef struct wmg_opts {

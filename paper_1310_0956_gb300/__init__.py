@@ -29,6 +29,7 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "INVALID_ARG", -2: "OOM", -3: "
 PREC_F64, PREC_F32 = 0, 1
 CYCLE_ADDITIVE, CYCLE_HYBRID, CYCLE_SYMMETRIC = 0, 1, 2
 SOLVER_SIRT, SOLVER_CGLS, SOLVER_GMRES, SOLVER_BICGSTAB = 0, 1, 2, 3
+KERNEL_STRIP, KERNEL_JOSEPH = 0, 1          # W: exact intersection lengths, or Joseph's kernel
 REQ_QUEUED, REQ_RUNNING, REQ_DONE = 0, 1, 2
 
 
@@ -40,7 +41,7 @@ class WmgError(RuntimeError):
 
 class wmg_geom(C.Structure):
     _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("angles", C.c_void_p), ("D", C.c_int32),
-                ("det_spacing", C.c_double), ("det_offset", C.c_double)]
+                ("det_spacing", C.c_double), ("det_offset", C.c_double), ("kernel", C.c_int32)]
 
 
 class wmg_opts(C.Structure):
@@ -342,7 +343,7 @@ class Plan:
 
     def __init__(self, n, m, D, levels=3, nu1=1, nu2=1, omega=1.0, lam=0.0, hybrid_depth=2,
                  cycle=CYCLE_SYMMETRIC, precision=PREC_F64, angles=None, det_spacing=1.0,
-                 det_offset=0.0):
+                 det_offset=0.0, kernel=KERNEL_STRIP):
         import torch
         self._torch = torch
         self._angles = None
@@ -350,7 +351,7 @@ class Plan:
         if angles is not None:
             self._angles = (C.c_double * m)(*[float(a) for a in angles])
             ap = C.cast(self._angles, C.c_void_p)
-        self.geom = wmg_geom(n, m, ap, D, det_spacing, det_offset)
+        self.geom = wmg_geom(n, m, ap, D, det_spacing, det_offset, kernel)
         self.opts = wmg_opts(levels, nu1, nu2, omega, lam, hybrid_depth, cycle, precision)
         self.dtype = torch.float64 if precision == PREC_F64 else torch.float32
         self.n, self.m, self.D = n, m, D
@@ -497,7 +498,8 @@ class StoredOperator:
 class Batch:
     """Problems of different geometries solved together (torch CUDA tensors).
     `problems` is a list of dicts with keys n, m, D and optionally levels,
-    lam, angles; the cycle options are shared."""
+    lam, angles, det_spacing, det_offset, kernel; the cycle options are
+    shared."""
 
     def __init__(self, problems, nu1=1, nu2=1, omega=1.0, hybrid_depth=1, cycle=CYCLE_HYBRID,
                  precision=PREC_F32):
@@ -511,7 +513,8 @@ class Batch:
                 arr = (C.c_double * p["m"])(*[float(a) for a in p["angles"]])
                 self._keep.append(arr)
                 ap = C.cast(arr, C.c_void_p)
-            geoms.append(wmg_geom(p["n"], p["m"], ap, p["D"], p.get("det_spacing", 1.0), p.get("det_offset", 0.0)))
+            geoms.append(wmg_geom(p["n"], p["m"], ap, p["D"], p.get("det_spacing", 1.0), p.get("det_offset", 0.0),
+                                  p.get("kernel", KERNEL_STRIP)))
             opts.append(wmg_opts(p.get("levels", 1), nu1, nu2, omega, p.get("lam", 0.0), hybrid_depth, cycle,
                                  precision))
         self.count = len(problems)
@@ -548,7 +551,7 @@ class Batch:
 class Server:
     """Continuous-batching request server (torch CUDA tensors). Requests are
     dicts with keys n, m, D and optionally levels, lam, angles, det_spacing,
-    det_offset; submit() takes the request's sinogram b and returns a ticket;
+    det_offset, kernel; submit() takes the request's sinogram b and returns a ticket;
     the output image is allocated here and returned by poll() when done."""
 
     def __init__(self, hbm_budget, max_slots=64, state_bytes=0, sino_ratio=0.0, preconditioned=True,
@@ -589,7 +592,8 @@ class Server:
             arr = (C.c_double * m)(*[float(a) for a in req["angles"]])
             keep.append(arr)
             ap = C.cast(arr, C.c_void_p)
-        geom = wmg_geom(n, m, ap, D, req.get("det_spacing", 1.0), req.get("det_offset", 0.0))
+        geom = wmg_geom(n, m, ap, D, req.get("det_spacing", 1.0), req.get("det_offset", 0.0),
+                        req.get("kernel", KERNEL_STRIP))
         d = self.defaults
         opts = wmg_opts(req.get("levels", d["levels"]), d["nu1"], d["nu2"], d["omega"], req.get("lam", d["lam"]),
                         d["hybrid_depth"], d["cycle"], d["precision"])
@@ -618,7 +622,8 @@ class Server:
 
     def footprint(self, req) -> tuple[int, int, int]:
         d = self.defaults
-        geom = wmg_geom(req["n"], req["m"], None, req["D"], req.get("det_spacing", 1.0), req.get("det_offset", 0.0))
+        geom = wmg_geom(req["n"], req["m"], None, req["D"], req.get("det_spacing", 1.0), req.get("det_offset", 0.0),
+                        req.get("kernel", KERNEL_STRIP))
         opts = wmg_opts(req.get("levels", d["levels"]), d["nu1"], d["nu2"], d["omega"], req.get("lam", d["lam"]),
                         d["hybrid_depth"], d["cycle"], d["precision"])
         return wmg_server_footprint(self.handle, geom, opts)

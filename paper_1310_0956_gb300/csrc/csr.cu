@@ -36,7 +36,7 @@ k_csr_rays(const GeomDev *__restrict__ Gd, int64_t *__restrict__ rp, int *__rest
         load_cs(g, a, c, s);
         const bool steep = fabs(c) >= fabs(s);
         const double cc = steep ? c : s, ss = steep ? s : c;
-        const Chord<double> ch = make_chord<double>(cc, ss);
+        const Chord<double> ch = make_chord<double>(cc, ss, g.kernel);
         const double hwx = ch.hw / fabs(cc), half_n = 0.5 * n;
         const double tk = ray_offset<double>(g, k);
         LineD line;
@@ -99,7 +99,7 @@ k_csr_pixels(const GeomDev *__restrict__ Gd, int64_t *__restrict__ rp, int *__re
         for (int a = 0; a < m; ++a) {
             double c, s;
             load_cs(g, a, c, s);
-            const Chord<double> ch = make_chord<double>(c, s);
+            const Chord<double> ch = make_chord<double>(c, s, g.kernel);
             const double hwb = ch.hw * inv_dt;
             const int ncand = (int)floor(2.0 * hwb) + 1;
             LineD line;

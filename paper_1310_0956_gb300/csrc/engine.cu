@@ -719,6 +719,8 @@ int32_t validate(const wmg_geom *g, const wmg_opts *o)
 {
     if (!g || !o) return fail(WMG_ERR_INVALID_ARG, "geometry or options NULL");
     if (g->n < 1 || g->m < 1 || g->D < 1) return fail(WMG_ERR_INVALID_ARG, "n, m and D must be >= 1");
+    if (g->kernel != WMG_KERNEL_STRIP && g->kernel != WMG_KERNEL_JOSEPH)
+        return fail(WMG_ERR_INVALID_ARG, "kernel must be WMG_KERNEL_STRIP or WMG_KERNEL_JOSEPH");
     if (o->levels < 0 || o->levels > 12) return fail(WMG_ERR_INVALID_ARG, "levels must be in [0, 12]");
     const int L = o->levels >= 1 ? o->levels - 1 : 0;
     if (g->n % (1 << L) != 0) return fail(WMG_ERR_INVALID_ARG, "n must be divisible by 2^(levels-1)");
@@ -748,6 +750,7 @@ int32_t make_geo(const wmg_geom *g, const wmg_opts *o, Geo &G, cudaStream_t st)
     gd.h = 1.0 / g->n;
     gd.dt = g->det_spacing > 0 ? g->det_spacing : 1.0;
     gd.t0 = g->det_offset;
+    gd.kernel = g->kernel;
     gd.lambda = o->lambda;
     gd.omega = o->omega > 0 ? o->omega : 1.0;
     G.hd = (o->cycle == WMG_CYCLE_ADDITIVE || !G.has_wmg) ? 0 : std::min(o->hybrid_depth, L);
@@ -764,7 +767,7 @@ int32_t make_geo(const wmg_geom *g, const wmg_opts *o, Geo &G, cudaStream_t st)
         csx[a] = make_float4((float)ch, (float)(cs[a].x - ch), (float)sh, (float)(cs[a].y - sh));
     }
     std::vector<AngleF> angf(g->m);
-    fill_angle_table(cs.data(), g->m, angf.data());
+    fill_angle_table(cs.data(), g->m, gd.kernel, angf.data());
     // quarter-turn pairs: angle a + m/2 is angle a turned by pi/2 in the
     // FP32 table, (c, s) -> (-s, c) with the same chord constants
     gd.qpair = g->m % 2 == 0 && g->m >= 2;
@@ -1761,7 +1764,7 @@ struct wmg_batch {
 static bool same_geometry(const wmg_geom &a, const wmg_geom &b, const wmg_opts &oa, const wmg_opts &ob)
 {
     if (a.n != b.n || a.m != b.m || a.D != b.D || a.det_spacing != b.det_spacing || a.det_offset != b.det_offset ||
-        oa.levels != ob.levels || oa.lambda != ob.lambda)
+        a.kernel != b.kernel || oa.levels != ob.levels || oa.lambda != ob.lambda)
         return false;
     if ((a.angles == nullptr) != (b.angles == nullptr)) return false;
     if (a.angles && std::memcmp(a.angles, b.angles, a.m * sizeof(double)) != 0) return false;

@@ -91,14 +91,20 @@ __device__ __forceinline__ T ray_offset(const GeomDev &g, int k)
     return fma_t(T(k) - T(0.5) * T(g.D - 1), T(g.dt), T(g.t0));
 }
 
-// Trapezoid-law chord of a unit pixel, as a function of the distance d >= 0
-// between the pixel centre and the line (per-angle constants).
+// Weight of a unit pixel as a function of the distance d >= 0 between the
+// pixel centre and the line (per-angle constants):
+//  strip:  the trapezoid-law chord, min(max((hw - d) / (alpha beta), 0), 1/alpha)
+//          with hw = (alpha + beta) / 2 (a step at 1/2 when beta = 0);
+//  Joseph: (1 - d / alpha) / alpha for d < alpha, the same formula with
+//          hw = alpha, 1 / alpha^2 in place of 1 / (alpha beta): the line meets
+//          the dominant axis' row (column) centre line d / alpha away from the
+//          pixel centre, and each row (column) is 1 / alpha of line.
 template <class T>
 struct Chord {
-    T hw;        // (alpha + beta) / 2: half-width of the support
-    T inv_ab;    // 1 / (alpha beta)
+    T hw;        // half-width of the support
+    T inv_ab;    // slope: 1 / (alpha beta) (strip), 1 / alpha^2 (Joseph)
     T lmax;      // 1 / alpha: plateau
-    bool axis;   // beta == 0
+    bool axis;   // strip with beta == 0
     __device__ __forceinline__ T operator()(T d) const
     {
         if (axis) return d < T(0.5) ? T(1) : (d == T(0.5) ? T(0.5) : T(0));
@@ -107,15 +113,21 @@ struct Chord {
 };
 
 template <class T>
-__device__ __forceinline__ Chord<T> make_chord(T c, T s)
+__device__ __forceinline__ Chord<T> make_chord(T c, T s, int kernel)
 {
     const T ac = fabs(c), as = fabs(s);
     const T al = fmax(ac, as), be = fmin(ac, as);
     Chord<T> ch;
+    ch.lmax = T(1) / al;
+    if (kernel == WMG_KERNEL_JOSEPH) {
+        ch.hw = al;
+        ch.axis = false;
+        ch.inv_ab = ch.lmax * ch.lmax;
+        return ch;
+    }
     ch.hw = T(0.5) * (al + be);
     ch.axis = (be == T(0));
     ch.inv_ab = ch.axis ? T(0) : T(1) / (al * be);
-    ch.lmax = T(1) / al;
     return ch;
 }
 

@@ -139,7 +139,7 @@ extern "C" int32_t wmg_project_noalloc(int32_t n, int32_t m, int32_t D, const fl
         const double sh = std::nearbyint(sn * 4096.0) / 4096.0;
         h_csx[a] = make_float4((float)ch, (float)(c - ch), (float)sh, (float)(sn - sh));
     }
-    fill_angle_table(h_cs64, m, h_angf);
+    fill_angle_table(h_cs64, m, WMG_KERNEL_STRIP, h_angf);
     GeomDev g{};
     g.n = n; g.m = m; g.D = D; g.L = 0; g.nc = n; g.P = 0; g.K = 1; g.B = 1;
     g.h = 1.0 / n; g.t0 = 0.0; g.dt = 1.0; g.lambda = 0.0; g.omega = 1.0;

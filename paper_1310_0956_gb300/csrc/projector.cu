@@ -52,7 +52,7 @@ k_project(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
         const bool steep = fabs(c) >= fabs(s);
         const T cc = steep ? c : s, ss = steep ? s : c;
         const T *__restrict__ src = static_cast<const T *>(steep ? a.img : a.imgT) + pd.img;
-        const Chord<T> ch = make_chord<T>(cc, ss);
+        const Chord<T> ch = make_chord<T>(cc, ss, g.kernel);
         const T inv_cc = T(1) / cc;
         const T hwx = ch.hw / fabs(cc);
         const T half_n = T(0.5) * T(n);
@@ -158,7 +158,7 @@ k_backproject(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
         for (int ang = 0; ang < m; ++ang) {
             T c, s;
             load_cs(g, ang, c, s);
-            const Chord<T> ch = make_chord<T>(c, s);
+            const Chord<T> ch = make_chord<T>(c, s, g.kernel);
             const T hwb = ch.hw * inv_dt;
             const int ncand = (int)floor(T(2) * hwb) + 1;
             typename LineOf<T>::type line0, line;
@@ -245,7 +245,7 @@ k_count_nnz(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
         load_cs(g, ang, c, s);
         const bool steep = fabs(c) >= fabs(s);
         const double cc = steep ? c : s, ss = steep ? s : c;
-        const Chord<double> ch = make_chord<double>(cc, ss);
+        const Chord<double> ch = make_chord<double>(cc, ss, g.kernel);
         const double hwx = ch.hw / fabs(cc), half_n = 0.5 * n;
         const double tk = ray_offset<double>(g, k);
         LineD line;

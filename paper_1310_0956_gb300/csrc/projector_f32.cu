@@ -408,7 +408,7 @@ void launch_backproject_f32(const GeomDev *G, const ProbDev *P, const int4 *tile
 #undef WMG_BPF
 }
 
-void fill_angle_table(const double2 *cs, int m, AngleF *out)
+void fill_angle_table(const double2 *cs, int m, int kernel, AngleF *out)
 {
     for (int a = 0; a < m; ++a) {
         const double c = cs[a].x, s = cs[a].y;
@@ -418,6 +418,25 @@ void fill_angle_table(const double2 *cs, int m, AngleF *out)
         const double al = std::fmax(std::fabs(c), std::fabs(s)), be = std::fmin(std::fabs(c), std::fabs(s));
         const bool steep = std::fabs(c) >= std::fabs(s), axis = be == 0.0;
         const double cc = steep ? c : s, ss = steep ? s : c;
+        if (kernel == WMG_KERNEL_JOSEPH) {
+            // weight (1 - d/al)/al = lmax sat(1 - d lmax): no step at the axes
+            const double lm = 1.0 / al;
+            A.hw = (float)al;
+            A.inv_ab = (float)(lm * lm);
+            A.hw_inv = (float)lm;
+            A.lmax = (float)lm;
+            A.hwx = 1.f;
+            A.inv_cc = (float)(1.0 / cc);
+            A.slope = (float)(ss / cc);
+            A.inv_slope = ss != 0.0 ? (float)(cc / ss) : 0.f;
+            const int flags = steep ? 1 : 0;
+            std::memcpy(&A.flags, &flags, sizeof(int));
+            A.wa = (float)lm;
+            A.wb = 1.f;
+            A.cc = (float)cc;
+            out[a] = A;
+            continue;
+        }
         const double hw = 0.5 * (al + be);
         A.hw = (float)hw;
         A.inv_ab = axis ? 0.f : (float)(1.0 / (al * be));

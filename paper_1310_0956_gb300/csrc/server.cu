@@ -325,7 +325,7 @@ std::string geo_key(const wmg_geom &g, const wmg_opts &o)
 {
     std::string k;
     auto put = [&](const void *p, size_t n) { k.append(static_cast<const char *>(p), n); };
-    put(&g.n, 4); put(&g.m, 4); put(&g.D, 4); put(&g.det_spacing, 8); put(&g.det_offset, 8);
+    put(&g.n, 4); put(&g.m, 4); put(&g.D, 4); put(&g.det_spacing, 8); put(&g.det_offset, 8); put(&g.kernel, 4);
     put(&o.levels, 4); put(&o.lambda, 8); put(&o.hybrid_depth, 4);
     const char has = g.angles ? 1 : 0;
     put(&has, 1);
@@ -363,7 +363,7 @@ int64_t setup_transient_bytes(const wmg_geom &g, const wmg_opts &o, size_t esz)
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const double dt = g.det_spacing > 0 ? g.det_spacing : 1.0;
-        const int64_t R = (int64_t)std::floor((double)B * 1.4142135623730951 / dt) + 3;
+        const int64_t R = (int64_t)std::floor((double)B * 1.4142135623730951 / dt) + 4;
         const int64_t KT = std::min<int64_t>(K, 256);
         const double per_angle = (double)P * R * KT * esz;
         const int64_t chunk = (int64_t)std::max(1.0, std::min((double)g.m, 96.0 * 1024 * 1024 / per_angle));

@@ -45,7 +45,10 @@ __device__ __forceinline__ void block_ray_range(const GeomDev &g, int a, int b, 
     const double half_n = 0.5 * g.n;
     const double bx = (cx + 0.5) * g.B - half_n, by = (cy + 0.5) * g.B - half_n;
     const double tau = bx * cs.x + by * cs.y;
-    const double hw = 0.5 * g.B * (fabs(cs.x) + fabs(cs.y));
+    // the block's pixel centres lie within (B-1)(|c|+|s|)/2 of tau; a pixel's
+    // weight reaches (|c|+|s|)/2 (strip) or max(|c|,|s|) (Joseph) further
+    const double ac = fabs(cs.x), as = fabs(cs.y);
+    const double hw = 0.5 * (g.B - 1) * (ac + as) + (g.kernel == WMG_KERNEL_JOSEPH ? fmax(ac, as) : 0.5 * (ac + as));
     const double u = (tau - g.t0) / g.dt + 0.5 * (g.D - 1);
     klo = max(0, (int)ceil(u - hw / g.dt - 1e-9));
     khi = min(g.D - 1, (int)floor(u + hw / g.dt + 1e-9));
@@ -97,7 +100,7 @@ k_leaf_footprint(const GeomDev *__restrict__ Gd, const int *__restrict__ alist, 
         const double2 cs = g.cs64[a];
         const bool steep = fabs(cs.x) >= fabs(cs.y);
         const double cc = steep ? cs.x : cs.y, ss = steep ? cs.y : cs.x;
-        const Chord<double> ch = make_chord<double>(cc, ss);
+        const Chord<double> ch = make_chord<double>(cc, ss, g.kernel);
         const double inv_cc = 1.0 / cc, hwx = ch.hw / fabs(cc), half_n = 0.5 * n;
         const int cy = b / g.nc, cx = b - cy * g.nc;
         const int fr0 = (steep ? cy : cx) * B, fx0 = (steep ? cx : cy) * B;
@@ -387,7 +390,8 @@ template <class TG>
 static int32_t assemble(const GeomDev &gh, const GeomDev *gd, double *Dacc, cudaStream_t st)
 {
     const int P = gh.P, K = gh.K, B = gh.B;
-    const int R = (int)floor(gh.B * 1.4142135623730951 / gh.dt) + 3;
+    // rays per block: at most ((B-1) sqrt 2 + 2) / dt + 1 (Joseph), B sqrt 2 / dt + 1 (strip)
+    const int R = (int)floor(gh.B * 1.4142135623730951 / gh.dt) + 4;
     const int KT = std::min(K, 256), S = KT / B;
     // angle classes from the FP64 table (|cos| >= |sin|: class 0)
     std::vector<double2> cs(gh.m);

@@ -61,6 +61,7 @@ struct GeomDev {
                              // addition both candidate bins of every pixel of
                              // every 32 x 32 tile lie on the detector at every
                              // angle, so that path needs no bounds checks
+    int kernel;              // WMG_KERNEL_STRIP or WMG_KERNEL_JOSEPH
     int qpair;               // even m, angle a + m/2 = angle a turned by pi/2 in
                              // the FP32 table (the unit-bin backprojector pairs them)
 };
@@ -71,7 +72,7 @@ struct GeomDev {
 constexpr double kNnzEps = 1e-12;
 
 // Fills the FP32 per-angle table from FP64 (cos, sin) pairs.
-void fill_angle_table(const double2 *cs, int m, AngleF *out);
+void fill_angle_table(const double2 *cs, int m, int kernel, AngleF *out);
 
 // One problem slot (or one virtual image of a multi-image product).
 struct ProbDev {

@@ -75,6 +75,8 @@ def parse():
                     help="skip the smoothed-cycle variant (nu1 = nu2 = 1) of the main workload")
     ap.add_argument("--no-joseph", action="store_true",
                     help="skip the leg with Joseph's kernel as W (same batch and solver)")
+    ap.add_argument("--no-semiconv", action="store_true",
+                    help="skip the semi-convergence leg (160^2, 400 angles, Joseph's kernel, noisy data)")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 1024x1024 / 1024-angle leg (mixed FP32 path vs the FP64 GPU path)")
     ap.add_argument("--kernel-case", action="store_true",
@@ -381,6 +383,11 @@ def run_ours(args, rank, world, local):
                 line["joseph_kernel"] = joseph_leg(args, dev, probs, flush)
             except Exception as e:
                 line["joseph_kernel"] = {"unavailable": f"{type(e).__name__}: {e}"}
+        if not args.no_semiconv and world == 1:
+            try:
+                line["semiconvergence"] = semiconvergence_leg(dev)
+            except Exception as e:
+                line["semiconvergence"] = {"unavailable": f"{type(e).__name__}: {e}"}
         if not args.no_large and world == 1:
             try:
                 line["large"] = large_leg(dev)
@@ -450,6 +457,54 @@ def joseph_leg(args, dev, probs, flush) -> dict:
            "project_ms_per_launch": prof["project"]["mean_ms"],
            "backproject_ms_per_launch": prof["backproject"]["mean_ms"]}
     plan.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Semi-convergence leg (Section 4.2): the error of the k-th iterate against the
+# exact phantom for SIRT, BiCGStab and WMG-BiCGStab, without and with Tikhonov
+# regularisation, on the paper's noisy model problem sizes
+# ---------------------------------------------------------------------------
+def semiconvergence_leg(dev) -> dict:
+    import torch
+    import paper_1310_0956_gb300 as wmg
+    from paper_1310_0956_gb300 import study
+    n, m, D, levels = 160, 400, 160, 5
+    x = S.phantom(n, 12, S.seed_for(6, 0))
+    xd = torch.tensor(x.reshape(-1), dtype=torch.float32, device=dev)
+    p64 = wmg.Plan(n, m, D, levels=0, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F64,
+                   kernel=wmg.KERNEL_JOSEPH)
+    b = p64.project(xd.double())
+    b = b + 0.01 * b.abs().max() * torch.tensor(S.uniform_noise_draws(m * D, S.seed_for(6, 0)),
+                                                dtype=torch.float64, device=dev)
+    b = b.to(torch.float32).contiguous()
+    p64.close()
+    out = {"workload": f"{n}x{n}_{m}ang_{D}det, W = Joseph's kernel, 1% uniform white noise (eq. noise_term)",
+           "levels": levels, "cycle": f"hybrid at every depth ({levels - 1}), nu1=nu2=0",
+           "error": "||x_k - x_ex|| / ||x_ex|| (L2, Linf); x_k from a solve of exactly k iterations",
+           "lambda_regularised": 1e-3 * m / n}
+    stream = torch.cuda.current_stream()
+    for tag, lam in (("noisy", 0.0), ("regularised", 1e-3 * m / n)):
+        # the paper's cycle: the hybrid residual update at every depth
+        plan = wmg.Plan(n, m, D, levels=levels, nu1=0, nu2=0, lam=lam, hybrid_depth=levels - 1,
+                        cycle=wmg.CYCLE_HYBRID, precision=wmg.PREC_F32, kernel=wmg.KERNEL_JOSEPH)
+        res = {}
+        for name, solver, pre, kmax in (("SIRT", wmg.SOLVER_SIRT, False, 3000),
+                                        ("BiCGStab", wmg.SOLVER_BICGSTAB, False, 300),
+                                        ("WMG-BiCGStab", wmg.SOLVER_BICGSTAB, True, 100)):
+            curve = study.error_curve(plan, b, xd, solver, pre, study.log_ks(kmax, 6))
+            ko, row = study.k_opt(curve)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.solve(b, solver, pre, ko, 0.0, 20)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res[name] = {"k_opt": ko, "error_l2": row[2], "error_linf": row[3],
+                         "error_l2_at_kmax": curve[-1][2], "kmax": kmax,
+                         "ms_to_k_opt": e0.elapsed_time(e1)}
+        out[tag] = res
+        plan.close()
     return out
 
 

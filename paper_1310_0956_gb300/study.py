@@ -1,0 +1,46 @@
+"""Semi-convergence of the iterative solvers on noisy data (Section 4.2):
+the error of the k-th iterate against the exact object, e_k = x_k - x_ex,
+with x_0 = 0 so that ||e_0|| = ||x_ex||. Every iterate comes from a solve
+of exactly k iterations (rtol 0) through the library's own solvers, which
+are deterministic, so x_k is the k-th iterate of one long run."""
+from __future__ import annotations
+
+from . import Plan
+
+
+def error_curve(plan: Plan, b, x_true, solver: int, preconditioned: bool, ks, restart: int = 20):
+    """For each k in ks: (k, iterations done, ||e_k||_2 / ||e_0||_2,
+    ||e_k||_inf / ||e_0||_inf) for one problem of `plan` (b and x_true CUDA
+    tensors of sizes M and N). A solve that ends early (breakdown) reports
+    the iterations it did."""
+    xt = x_true.double()
+    n2, ninf = float(xt.norm()), float(xt.abs().max())
+    out = []
+    for k in ks:
+        x, info, _, _ = plan.solve(b, solver, preconditioned, int(k), 0.0, restart)
+        e = x.double() - xt
+        out.append((int(k), int(info[0][0]), float(e.norm()) / n2, float(e.abs().max()) / ninf))
+    return out
+
+
+def k_opt(curve):
+    """The iterate count with the smallest L2 error, and that row of the
+    curve (Section 4.2: k_opt = argmin_k ||e_k||)."""
+    best = min(curve, key=lambda r: r[2])
+    return best[0], best
+
+
+def log_ks(kmax: int, per_decade: int = 8):
+    """Iterate counts 1 .. kmax spread evenly on a log scale (the paper plots
+    these curves against log k)."""
+    import math
+    ks, k = [], 1
+    while k <= kmax:
+        ks.append(k)
+        k = max(k + 1, int(round(10 ** (math.log10(k) + 1.0 / per_decade))))
+    if ks[-1] != kmax:
+        ks.append(kmax)
+    return ks
+
+
+__all__ = ["error_curve", "k_opt", "log_ks"]

@@ -312,3 +312,60 @@ def bicgstab(op: Op, b, max_iter: int, rtol: float = 0.0, lam: float = 0.0, prec
     k = _load().or_bicgstab(op._h, precond._h if precond else None, lam, _f64(b), x, max_iter, rtol,
                             hist.ctypes.data_as(C.c_void_p), C.byref(st))
     return x, k, hist[:k + 1], st.value
+
+
+# ---------------------------------------------------------------------------
+# Spectral check (Section 3.2): dense two-grid error propagators for small
+# problems, and the condition numbers the paper compares
+# ---------------------------------------------------------------------------
+def haar_band_restrictions(n: int):
+    """The four one-level Haar restrictions I_{h,id}^{2h} (eq. intops_wav,
+    eq. 1of4-4of4) as dense (N/4) x N matrices, in the band order LL, LH, HL,
+    HH: row-blocks of the packet analysis matrix at depth 1."""
+    N = n * n
+    Q = np.stack([packet_analysis(np.eye(N)[j], n, 1) for j in range(N)], axis=1)
+    return [Q[k * N // 4:(k + 1) * N // 4] for k in range(4)]
+
+
+def _coarse_correction(A, R):
+    """I - I_{2h}^h (A^{2h})^{-1} I_h^{2h} A with the Galerkin A^{2h} = R A R^T."""
+    Ac = R @ A @ R.T
+    return np.eye(A.shape[0]) - R.T @ np.linalg.solve(Ac, R @ A)
+
+
+def wtg_propagator(op: Op, lam: float = 0.0) -> np.ndarray:
+    """Error propagator of the wavelet two-grid scheme, eq. wmg: the four band
+    corrections applied one after the other (LL, LH, HL, HH), each from the
+    residual of the corrected iterate (fully multiplicative)."""
+    W = op.dense()
+    A = W.T @ W + lam * np.eye(op.N)
+    E = np.eye(op.N)
+    for R in haar_band_restrictions(op.n):
+        E = _coarse_correction(A, R) @ E
+    return E
+
+
+def tg_sirt_propagator(op: Op, nu1: int = 1, nu2: int = 1, lam: float = 0.0) -> np.ndarray:
+    """Error propagator of the classical two-grid scheme, eq. mg_error:
+    S^nu2 (I - I_{2h}^h (A^{2h})^{-1} I_h^{2h} A) S^nu1 with the first-order
+    restriction of eq. intops (the Haar LL band) and S the SIRT iteration
+    matrix I - C W^T R W (Section 2.2.1)."""
+    W = op.dense()
+    A = W.T @ W + lam * np.eye(op.N)
+    R, C = op.sirt_scalings()
+    S = np.eye(op.N) - (C[:, None] * W.T) @ (R[:, None] * W)
+    K = _coarse_correction(A, haar_band_restrictions(op.n)[0])
+    return np.linalg.matrix_power(S, nu2) @ K @ np.linalg.matrix_power(S, nu1)
+
+
+def condition_number(M: np.ndarray, symmetric: bool = False) -> float:
+    """kappa = max |lambda_i| / min |lambda_i| (eq. condnr)."""
+    ev = np.linalg.eigvalsh(M) if symmetric else np.linalg.eigvals(M)
+    a = np.abs(ev)
+    return float(a.max() / a.min())
+
+
+def preconditioned_condition_number(E: np.ndarray) -> float:
+    """kappa of I - A B A^{-1} for a scheme with error propagator E = I - B A:
+    its eigenvalues are 1 - eig(E) (eq. spec_wavelet, eq. spec_classic)."""
+    return condition_number(np.eye(E.shape[0]) - E)

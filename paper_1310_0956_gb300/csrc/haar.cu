@@ -22,53 +22,73 @@ namespace wmg {
 
 __device__ __forceinline__ int bitrev_bits(int u, int L) { return L ? (int)(__brev((unsigned)u) >> (32 - L)) : 0; }
 
-__device__ __forceinline__ int spread_bits(int v, int L)
+// Bits 0..7 of v moved to the even positions 0, 2, .., 14.
+__device__ __forceinline__ int spread_bits(int v)
 {
-    int r = 0;
-    for (int i = 0; i < L; ++i) r |= ((v >> i) & 1) << (2 * i);
-    return r;
+    v = (v | (v << 4)) & 0x0F0F;
+    v = (v | (v << 2)) & 0x3333;
+    v = (v | (v << 1)) & 0x5555;
+    return v;
 }
 
-// Leaf index of Walsh position (uy, ux) inside a block.
+// Leaf index of Walsh position (uy, ux) inside a block (L <= 8).
 __device__ __forceinline__ int leaf_of(int uy, int ux, int L)
 {
-    return (spread_bits(bitrev_bits(uy, L), L) << 1) | spread_bits(bitrev_bits(ux, L), L);
+    return (spread_bits(bitrev_bits(uy, L)) << 1) | spread_bits(bitrev_bits(ux, L));
 }
 
 // Shared-memory column of strip column x: one pad slot after every B-wide
-// segment, so that the 16 block columns a warp touches at one Walsh position
+// segment, so that the block columns a warp touches at one Walsh position
 // (stride B + 1 doubles) fall in different banks.
 __device__ __forceinline__ int padx(int x, int L) { return x + (x >> L); }
+
+// Thread layout over a 2D loop of `width` columns: tx runs along the
+// columns, ty along the rows (threads with ty >= ny idle). One division per
+// tile instead of one per element.
+struct Lay {
+    int tx, ty, nx, ny;
+};
+__device__ __forceinline__ Lay lay(int width)
+{
+    const int nx = min(width, (int)blockDim.x);
+    return Lay{(int)threadIdx.x % nx, (int)threadIdx.x / nx, nx, (int)blockDim.x / nx};
+}
 
 // In-place Walsh-Hadamard butterflies over a B x W strip in shared memory
 // (pitch pw, columns padded by padx), along x (within every B-wide segment)
 // then along y.
 __device__ __forceinline__ void strip_wht(double *sm, int B, int W, int L, int pw)
 {
-    const int halfx = B * (W >> 1);
+    const Lay lx = lay(W >> 1);
     for (int st = 0; st < L; ++st) {
         const int hbit = 1 << st;
-        for (int q = threadIdx.x; q < halfx; q += blockDim.x) {
-            const int r = q / (W >> 1), pi = q - r * (W >> 1);
-            const int i = ((pi >> st) << (st + 1)) | (pi & (hbit - 1));
-            double *row = sm + r * pw;
-            const int i0 = padx(i, L), i1 = padx(i + hbit, L);
-            const double a = row[i0], b = row[i1];
-            row[i0] = a + b;
-            row[i1] = a - b;
-        }
+        if (lx.ty < lx.ny)
+            for (int r = lx.ty; r < B; r += lx.ny) {
+                double *row = sm + r * pw;
+                for (int pi = lx.tx; pi < (W >> 1); pi += lx.nx) {
+                    const int i = ((pi >> st) << (st + 1)) | (pi & (hbit - 1));
+                    const int i0 = padx(i, L), i1 = padx(i + hbit, L);
+                    const double a = row[i0], b = row[i1];
+                    row[i0] = a + b;
+                    row[i1] = a - b;
+                }
+            }
         __syncthreads();
     }
-    const int halfy = (B >> 1) * W;
+    const Lay ly = lay(W);
     for (int st = 0; st < L; ++st) {
         const int hbit = 1 << st;
-        for (int q = threadIdx.x; q < halfy; q += blockDim.x) {
-            const int col = padx(q % W, L), pi = q / W;
-            const int i = ((pi >> st) << (st + 1)) | (pi & (hbit - 1));
-            const double a = sm[i * pw + col], b = sm[(i + hbit) * pw + col];
-            sm[i * pw + col] = a + b;
-            sm[(i + hbit) * pw + col] = a - b;
-        }
+        if (ly.ty < ly.ny)
+            for (int pi = ly.ty; pi < (B >> 1); pi += ly.ny) {
+                const int i = ((pi >> st) << (st + 1)) | (pi & (hbit - 1));
+                double *r0 = sm + i * pw, *r1 = sm + (i + hbit) * pw;
+                for (int x = ly.tx; x < W; x += ly.nx) {
+                    const int col = padx(x, L);
+                    const double a = r0[col], b = r1[col];
+                    r0[col] = a + b;
+                    r1[col] = a - b;
+                }
+            }
         __syncthreads();
     }
 }
@@ -88,26 +108,35 @@ k_haar_analysis(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
         if (!slot_active(a.S, pd.slot)) continue;
         const GeomDev &g = G[pd.geom];
         const int n = g.n, B = g.B, L = g.L, W = tl.w, pw = W + (W >> L) + 1;
-        const TIn *in = static_cast<const TIn *>(a.in) + pd.img;
-        for (int q = threadIdx.x; q < B * W; q += blockDim.x) {
-            const int r = q / W, x = q - r * W;
-            sm[r * pw + padx(x, L)] = (double)in[(int64_t)(tl.y + r) * n + tl.z + x];
+        const TIn *in = static_cast<const TIn *>(a.in) + pd.img + (int64_t)tl.y * n + tl.z;
+        {
+            const Lay l = lay(W);
+            if (l.ty < l.ny)
+                for (int r = l.ty; r < B; r += l.ny)
+                    for (int x = l.tx; x < W; x += l.nx) sm[r * pw + padx(x, L)] = (double)in[(int64_t)r * n + x];
         }
         __syncthreads();
         strip_wht(sm, B, W, L, pw);
         const double scale = 1.0 / (double)B;
-        const int nb = W / B, cy = tl.y / B, cx0 = tl.z / B;
-        TOut *C = static_cast<TOut *>(a.out) + pd.coef;
-        for (int q = threadIdx.x; q < B * W; q += blockDim.x) {
-            const int bc = q % nb, rest = q / nb, ux = rest % B, uy = rest / B;
-            const int k = leaf_of(uy, ux, L);
-            const TOut v = (TOut)(sm[uy * pw + bc * (B + 1) + ux] * scale);
-            const int64_t o = (int64_t)k * g.P + (int64_t)cy * g.nc + cx0 + bc;
-            if (MODE == HA_STORE) C[o] = v;
-            else if (k >= pd.kout0 && k < pd.kout1) {
-                if (MODE == HA_SUB_MASKED) C[o] -= v;
-                else C[o] = v;
-            }
+        const int nb = W >> L, cy = tl.y >> L, cx0 = tl.z >> L;
+        TOut *C = static_cast<TOut *>(a.out) + pd.coef + (int64_t)cy * g.nc + cx0;
+        {
+            // consecutive threads: consecutive blocks of one Walsh position,
+            // i.e. consecutive entries of one leaf's coefficient vector
+            const Lay l = lay(nb);
+            if (l.ty < l.ny)
+                for (int u = l.ty; u < B * B; u += l.ny) {
+                    const int uy = u >> L, ux = u & (B - 1);
+                    const int k = leaf_of(uy, ux, L);
+                    if (MODE != HA_STORE && (k < pd.kout0 || k >= pd.kout1)) continue;
+                    TOut *Ck = C + (int64_t)k * g.P;
+                    const double *src = sm + uy * pw + ux;
+                    for (int bc = l.tx; bc < nb; bc += l.nx) {
+                        const TOut v = (TOut)(src[bc * (B + 1)] * scale);
+                        if (MODE == HA_SUB_MASKED) Ck[bc] -= v;
+                        else Ck[bc] = v;
+                    }
+                }
         }
         __syncthreads();
     }
@@ -127,43 +156,55 @@ k_haar_synthesis(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
         if (!slot_active(a.S, pd.slot)) continue;
         const GeomDev &g = G[pd.geom];
         const int n = g.n, B = g.B, L = g.L, W = tl.w, pw = W + (W >> L) + 1;
-        const int nb = W / B, cy = tl.y / B, cx0 = tl.z / B;
-        const TIn *E = static_cast<const TIn *>(a.in) + pd.coef;
-        for (int q = threadIdx.x; q < B * W; q += blockDim.x) {
-            const int bc = q % nb, rest = q / nb, ux = rest % B, uy = rest / B;
-            const int k = leaf_of(uy, ux, L);
-            double v = 0.0;
-            if (MODE != HS_STORE_MASKED || (k >= pd.kin0 && k < pd.kin1))
-                v = (double)E[(int64_t)k * g.P + (int64_t)cy * g.nc + cx0 + bc];
-            sm[uy * pw + bc * (B + 1) + ux] = v;
+        const int nb = W >> L, cy = tl.y >> L, cx0 = tl.z >> L;
+        const TIn *E = static_cast<const TIn *>(a.in) + pd.coef + (int64_t)cy * g.nc + cx0;
+        {
+            const Lay l = lay(nb);
+            if (l.ty < l.ny)
+                for (int u = l.ty; u < B * B; u += l.ny) {
+                    const int uy = u >> L, ux = u & (B - 1);
+                    const int k = leaf_of(uy, ux, L);
+                    const bool in = MODE != HS_STORE_MASKED || (k >= pd.kin0 && k < pd.kin1);
+                    const TIn *Ek = E + (int64_t)k * g.P;
+                    double *dst = sm + uy * pw + ux;
+                    for (int bc = l.tx; bc < nb; bc += l.nx) dst[bc * (B + 1)] = in ? (double)Ek[bc] : 0.0;
+                }
         }
         __syncthreads();
         strip_wht(sm, B, W, L, pw);
         const double scale = 1.0 / (double)B;
         TOut *out = static_cast<TOut *>(a.out);
-        for (int q = threadIdx.x; q < B * W; q += blockDim.x) {
-            const int r = q / W, x = q - r * W;
-            const int64_t j = pd.img + (int64_t)(tl.y + r) * n + tl.z + x;
-            const double v = sm[r * pw + padx(x, L)] * scale;
-            if (MODE == HS_CORRECT) {
-                const double zv = a.z[j] + v;
-                a.z[j] = zv;
-                const TOut zt = (TOut)zv;
-                sm[r * pw + padx(x, L)] = (double)zt;
-                if (out) out[j] = zt;
-            } else {
-                const TOut vt = (TOut)v;
-                sm[r * pw + padx(x, L)] = (double)vt;
-                out[j] = vt;
-            }
+        {
+            const Lay l = lay(W);
+            if (l.ty < l.ny)
+                for (int r = l.ty; r < B; r += l.ny)
+                    for (int x = l.tx; x < W; x += l.nx) {
+                        const int64_t j = pd.img + (int64_t)(tl.y + r) * n + tl.z + x;
+                        double *cell = sm + r * pw + padx(x, L);
+                        const double v = *cell * scale;
+                        if (MODE == HS_CORRECT) {
+                            const double zv = a.z[j] + v;
+                            a.z[j] = zv;
+                            const TOut zt = (TOut)zv;
+                            *cell = (double)zt;
+                            if (out) out[j] = zt;
+                        } else {
+                            const TOut vt = (TOut)v;
+                            *cell = (double)vt;
+                            out[j] = vt;
+                        }
+                    }
         }
         if (a.outT) {
             __syncthreads();
-            TOut *outT = static_cast<TOut *>(a.outT);
-            for (int q = threadIdx.x; q < B * W; q += blockDim.x) {
-                const int x = q / B, r = q - x * B;
-                outT[pd.img + (int64_t)(tl.z + x) * n + tl.y + r] = (TOut)sm[r * pw + padx(x, L)];
-            }
+            TOut *outT = static_cast<TOut *>(a.outT) + pd.img + tl.y;
+            const Lay l = lay(B);
+            if (l.ty < l.ny)
+                for (int x = l.ty; x < W; x += l.ny) {
+                    const int col = padx(x, L);
+                    for (int r = l.tx; r < B; r += l.nx)
+                        outT[(int64_t)(tl.z + x) * n + r] = (TOut)sm[r * pw + col];
+                }
         }
         __syncthreads();
     }

@@ -1266,8 +1266,8 @@ static int32_t collect(wmg_plan *pl, int max_iter, wmg_solve_info *info, double 
     WMG_CUDA(cudaStreamSynchronize(st));
     WMG_CUDA(cudaGetLastError());
     if (const int e = tma_error_take())
-        return fail(WMG_ERR_CUDA, e == 1 ? "projector: a wait for staged pixels timed out"
-                                         : "projector: a candidate pixel fell outside its staged box");
+        return e == 1 ? fail(WMG_ERR_TIMEOUT, "projector: a wait for staged pixels timed out")
+                      : fail(WMG_ERR_CUDA, "projector: a candidate pixel fell outside its staged box");
     int32_t rc = WMG_OK;
     for (int i = 0; i < count; ++i) {
         const int q = pl->batch ? pl->order[i] : i;

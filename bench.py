@@ -757,8 +757,8 @@ def load_peaks():
 KERNEL_TRAFFIC = {
     "project": {"source": "paper_1310_0956_gb300/csrc/projector_tma.cu", "sha256_16": "6115a9f383afc7ae",
                 "bytes_per_image": (8497664 + 8498432) / 2 / 16.0},
-    "backproject": {"source": "paper_1310_0956_gb300/csrc/projector_f32.cu", "sha256_16": "57f012eb8cf87922",
-                    "bytes_per_image": (4067840 + 4100096) / 2 / 16.0},
+    "backproject": {"source": "paper_1310_0956_gb300/csrc/projector_f32.cu", "sha256_16": "f970788f2cb7205d",
+                    "bytes_per_image": (4068608 + 4069632) / 2 / 16.0},
 }
 
 

@@ -2,8 +2,11 @@
 relative normal-equation residual on the 256x256 parallel-beam workload
 (180 angles, 363 detector bins, seeded 20-ellipse phantoms, 1% Gaussian
 noise, 5 WMG levels), solved by restarted GMRES(20) with right
-preconditioning by the hybrid WMG cycle (hybrid depth 1, one l1-Jacobi pre-
-and post-sweep), FP32 operator with FP64 Krylov vectors and reductions.
+preconditioning by the paper's WMG cycle (hybrid residual update at depth 0,
+no smoothing sweeps), FP32 operator with FP64 Krylov vectors and reductions.
+Further legs of the same run (the smoothed cycle, BiCGStab, Joseph's kernel,
+the semi-convergence study, 1024^2, an uneven batch, a request stream, the
+stored-matrix comparator) are reported beside the headline.
 
 One step = one batch of `--batch` independent reconstructions (distinct
 phantoms and noise), all iterated together until each reaches the tolerance.
@@ -93,7 +96,27 @@ def dist_env():
 
 
 def workload_problems(batch: int, rank: int):
+    """Rank `rank`'s shard: problems batch*rank .. batch*(rank+1)-1 of the
+    workload's seeded problem sequence (disjoint across ranks)."""
     return S.workload_mid(batch * (rank + 1)).problems[batch * rank: batch * (rank + 1)]
+
+
+def max_over_ranks(t: float, world: int, device=None) -> float:
+    """The largest of the ranks' values, on every rank (the job is as slow as
+    its slowest replica)."""
+    if world <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_value(batch: int, world: int, steps: int, t_total: float) -> float:
+    """Reconstructions per second of the whole job: every rank solved `steps`
+    batches of `batch` problems in at most t_total seconds."""
+    return batch * world * steps / t_total
 
 
 # ---------------------------------------------------------------------------
@@ -262,11 +285,9 @@ def run_ours(args, rank, world, local):
     t_step = float(np.mean(times))
     t_total = float(np.sum(times))
     if world > 1:
-        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(tt.item())
+        t_total = max_over_ranks(t_total, world, dev)
         torch.distributed.barrier()
-    value = B * world * args.steps / t_total
+    value = whole_job_value(B, world, args.steps, t_total)
 
     # the smoothed cycle on the same batch (one l1-Jacobi pre- and post-sweep:
     # two more A-pairs per iteration, fewer iterations)

@@ -520,6 +520,7 @@ static int32_t band_update(wmg_plan *pl, int d, const std::vector<int> &nodes, c
     hs.out = pl->band_img.p;
     hs.outT = pl->band_imgT.p;
     hs.S = S;
+    hs.fp32 = pl->prec == WMG_PREC_F32;
     launch_haar_synthesis<double, T>(G, bs->d.as<ProbDev>(), bs->haar.tiles.as<int4>(), bs->haar.n,
                                      bs->haar_smem, hs, st);
     project<T>(pl, *bs, pl->band_img.p, pl->band_imgT.p, pl->band_sino.p, nullptr, S, st);
@@ -532,6 +533,7 @@ static int32_t band_update(wmg_plan *pl, int d, const std::vector<int> &nodes, c
     ha.in = pl->band_img2.p;
     ha.out = Cb.p;
     ha.S = S;
+    ha.fp32 = pl->prec == WMG_PREC_F32;
     launch_haar_analysis<double, double>(G, bs->d.as<ProbDev>(), bs->haar.tiles.as<int4>(), bs->haar.n,
                                          bs->haar_smem, ha, st);
     return WMG_OK;
@@ -667,14 +669,14 @@ int32_t wmg_apply(wmg_plan *pl, double *s, double *z, bool first_done, bool copi
     }
     const GeomDev *G = pl->d_geom.as<GeomDev>();
     HaarArgs ha{};
-    ha.mode = HA_STORE; ha.in = pl->r1.p; ha.out = pl->C.p; ha.S = S;
+    ha.mode = HA_STORE; ha.in = pl->r1.p; ha.out = pl->C.p; ha.S = S; ha.fp32 = pl->prec == WMG_PREC_F32;
     launch_haar_analysis<double, double>(G, ps.d.as<ProbDev>(), ps.haar.tiles.as<int4>(), ps.haar.n,
                                          ps.haar_smem, ha, st);
     int32_t rc = coarse<T>(pl, 0, std::vector<int>{0}, pl->live, pl->C, pl->E, st);
     if (rc) return rc;
     const bool need_copies_after_syn = copies || o.nu2 > 0;
     HaarArgs hs{};
-    hs.mode = HS_CORRECT; hs.in = pl->E.p; hs.z = z; hs.S = S;
+    hs.mode = HS_CORRECT; hs.in = pl->E.p; hs.z = z; hs.S = S; hs.fp32 = pl->prec == WMG_PREC_F32;
     hs.out = need_copies_after_syn ? pl->z_op.p : nullptr;
     hs.outT = need_copies_after_syn ? pl->zT_op.p : nullptr;
     launch_haar_synthesis<double, T>(G, ps.d.as<ProbDev>(), ps.haar.tiles.as<int4>(), ps.haar.n,

@@ -56,19 +56,20 @@ __device__ __forceinline__ Lay lay(int width)
 
 // In-place Walsh-Hadamard butterflies over a B x W strip in shared memory
 // (pitch pw, columns padded by padx), along x (within every B-wide segment)
-// then along y.
-__device__ __forceinline__ void strip_wht(double *sm, int B, int W, int L, int pw)
+// then along y, in the compute type TC.
+template <class TC>
+__device__ __forceinline__ void strip_wht(TC *sm, int B, int W, int L, int pw)
 {
     const Lay lx = lay(W >> 1);
     for (int st = 0; st < L; ++st) {
         const int hbit = 1 << st;
         if (lx.ty < lx.ny)
             for (int r = lx.ty; r < B; r += lx.ny) {
-                double *row = sm + r * pw;
+                TC *row = sm + r * pw;
                 for (int pi = lx.tx; pi < (W >> 1); pi += lx.nx) {
                     const int i = ((pi >> st) << (st + 1)) | (pi & (hbit - 1));
                     const int i0 = padx(i, L), i1 = padx(i + hbit, L);
-                    const double a = row[i0], b = row[i1];
+                    const TC a = row[i0], b = row[i1];
                     row[i0] = a + b;
                     row[i1] = a - b;
                 }
@@ -81,10 +82,10 @@ __device__ __forceinline__ void strip_wht(double *sm, int B, int W, int L, int p
         if (ly.ty < ly.ny)
             for (int pi = ly.ty; pi < (B >> 1); pi += ly.ny) {
                 const int i = ((pi >> st) << (st + 1)) | (pi & (hbit - 1));
-                double *r0 = sm + i * pw, *r1 = sm + (i + hbit) * pw;
+                TC *r0 = sm + i * pw, *r1 = sm + (i + hbit) * pw;
                 for (int x = ly.tx; x < W; x += ly.nx) {
                     const int col = padx(x, L);
-                    const double a = r0[col], b = r1[col];
+                    const TC a = r0[col], b = r1[col];
                     r0[col] = a + b;
                     r1[col] = a - b;
                 }
@@ -94,14 +95,16 @@ __device__ __forceinline__ void strip_wht(double *sm, int B, int W, int L, int p
 }
 
 // Analysis: tile = {prob, y0, x0, W}; strip of B rows x W columns. The
-// butterflies run in FP64 whatever the storage types.
-template <class TIn, class TOut, int MODE>
+// butterflies run in TC (FP64, or FP32 in the WMG cycle of FP32 plans:
+// GB300 issues FP64 arithmetic at a small fraction of the FP32 rate)
+// whatever the storage types.
+template <class TIn, class TOut, int MODE, class TC>
 __global__ void __launch_bounds__(256)
 k_haar_analysis(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
                 const int4 *__restrict__ tiles, int ntiles, HaarArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    double *sm = reinterpret_cast<double *>(smraw);
+    TC *sm = reinterpret_cast<TC *>(smraw);
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 tl = tiles[t];
         const ProbDev pd = P[tl.x];
@@ -113,11 +116,11 @@ k_haar_analysis(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
             const Lay l = lay(W);
             if (l.ty < l.ny)
                 for (int r = l.ty; r < B; r += l.ny)
-                    for (int x = l.tx; x < W; x += l.nx) sm[r * pw + padx(x, L)] = (double)in[(int64_t)r * n + x];
+                    for (int x = l.tx; x < W; x += l.nx) sm[r * pw + padx(x, L)] = (TC)in[(int64_t)r * n + x];
         }
         __syncthreads();
         strip_wht(sm, B, W, L, pw);
-        const double scale = 1.0 / (double)B;
+        const TC scale = TC(1) / (TC)B;                              // a power of two: exact
         const int nb = W >> L, cy = tl.y >> L, cx0 = tl.z >> L;
         TOut *C = static_cast<TOut *>(a.out) + pd.coef + (int64_t)cy * g.nc + cx0;
         {
@@ -130,7 +133,7 @@ k_haar_analysis(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
                     const int k = leaf_of(uy, ux, L);
                     if (MODE != HA_STORE && (k < pd.kout0 || k >= pd.kout1)) continue;
                     TOut *Ck = C + (int64_t)k * g.P;
-                    const double *src = sm + uy * pw + ux;
+                    const TC *src = sm + uy * pw + ux;
                     for (int bc = l.tx; bc < nb; bc += l.nx) {
                         const TOut v = (TOut)(src[bc * (B + 1)] * scale);
                         if (MODE == HA_SUB_MASKED) Ck[bc] -= v;
@@ -142,14 +145,14 @@ k_haar_analysis(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
     }
 }
 
-// Synthesis: the transpose of the analysis (FP64 butterflies).
-template <class TIn, class TOut, int MODE>
+// Synthesis: the transpose of the analysis (butterflies in TC).
+template <class TIn, class TOut, int MODE, class TC>
 __global__ void __launch_bounds__(256)
 k_haar_synthesis(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
                  const int4 *__restrict__ tiles, int ntiles, HaarArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    double *sm = reinterpret_cast<double *>(smraw);
+    TC *sm = reinterpret_cast<TC *>(smraw);
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 tl = tiles[t];
         const ProbDev pd = P[tl.x];
@@ -166,13 +169,13 @@ k_haar_synthesis(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
                     const int k = leaf_of(uy, ux, L);
                     const bool in = MODE != HS_STORE_MASKED || (k >= pd.kin0 && k < pd.kin1);
                     const TIn *Ek = E + (int64_t)k * g.P;
-                    double *dst = sm + uy * pw + ux;
-                    for (int bc = l.tx; bc < nb; bc += l.nx) dst[bc * (B + 1)] = in ? (double)Ek[bc] : 0.0;
+                    TC *dst = sm + uy * pw + ux;
+                    for (int bc = l.tx; bc < nb; bc += l.nx) dst[bc * (B + 1)] = in ? (TC)Ek[bc] : TC(0);
                 }
         }
         __syncthreads();
         strip_wht(sm, B, W, L, pw);
-        const double scale = 1.0 / (double)B;
+        const TC scale = TC(1) / (TC)B;
         TOut *out = static_cast<TOut *>(a.out);
         {
             const Lay l = lay(W);
@@ -180,17 +183,17 @@ k_haar_synthesis(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
                 for (int r = l.ty; r < B; r += l.ny)
                     for (int x = l.tx; x < W; x += l.nx) {
                         const int64_t j = pd.img + (int64_t)(tl.y + r) * n + tl.z + x;
-                        double *cell = sm + r * pw + padx(x, L);
-                        const double v = *cell * scale;
+                        TC *cell = sm + r * pw + padx(x, L);
+                        const TC v = *cell * scale;
                         if (MODE == HS_CORRECT) {
-                            const double zv = a.z[j] + v;
+                            const double zv = a.z[j] + (double)v;
                             a.z[j] = zv;
                             const TOut zt = (TOut)zv;
-                            *cell = (double)zt;
+                            *cell = (TC)zt;
                             if (out) out[j] = zt;
                         } else {
                             const TOut vt = (TOut)v;
-                            *cell = (double)vt;
+                            *cell = (TC)vt;
                             out[j] = vt;
                         }
                     }
@@ -221,12 +224,18 @@ void launch_haar_analysis(const GeomDev *G, const ProbDev *P, const int4 *tiles,
 {
     if (ntiles <= 0) return;
     count_launches(1);
-    const int bytes = smem_elems * (int)sizeof(double);
     const int grid = min(ntiles, num_sms() * 8);
 #define WMG_HA(M)                                                                                  \
     case M:                                                                                        \
-        set_smem((const void *)k_haar_analysis<TIn, TOut, M>, bytes);                              \
-        k_haar_analysis<TIn, TOut, M><<<grid, 256, bytes, st>>>(G, P, tiles, ntiles, a);           \
+        if (a.fp32) {                                                                              \
+            const int bytes = smem_elems * (int)sizeof(float);                                     \
+            set_smem((const void *)k_haar_analysis<TIn, TOut, M, float>, bytes);                   \
+            k_haar_analysis<TIn, TOut, M, float><<<grid, 256, bytes, st>>>(G, P, tiles, ntiles, a); \
+        } else {                                                                                   \
+            const int bytes = smem_elems * (int)sizeof(double);                                    \
+            set_smem((const void *)k_haar_analysis<TIn, TOut, M, double>, bytes);                  \
+            k_haar_analysis<TIn, TOut, M, double><<<grid, 256, bytes, st>>>(G, P, tiles, ntiles, a); \
+        }                                                                                          \
         break;
     switch (a.mode) { WMG_HA(HA_STORE) WMG_HA(HA_SUB_MASKED) WMG_HA(HA_STORE_MASKED) default: break; }
 #undef WMG_HA
@@ -238,12 +247,18 @@ void launch_haar_synthesis(const GeomDev *G, const ProbDev *P, const int4 *tiles
 {
     if (ntiles <= 0) return;
     count_launches(1);
-    const int bytes = smem_elems * (int)sizeof(double);
     const int grid = min(ntiles, num_sms() * 8);
 #define WMG_HS(M)                                                                                  \
     case M:                                                                                        \
-        set_smem((const void *)k_haar_synthesis<TIn, TOut, M>, bytes);                             \
-        k_haar_synthesis<TIn, TOut, M><<<grid, 256, bytes, st>>>(G, P, tiles, ntiles, a);          \
+        if (a.fp32) {                                                                              \
+            const int bytes = smem_elems * (int)sizeof(float);                                     \
+            set_smem((const void *)k_haar_synthesis<TIn, TOut, M, float>, bytes);                  \
+            k_haar_synthesis<TIn, TOut, M, float><<<grid, 256, bytes, st>>>(G, P, tiles, ntiles, a); \
+        } else {                                                                                   \
+            const int bytes = smem_elems * (int)sizeof(double);                                    \
+            set_smem((const void *)k_haar_synthesis<TIn, TOut, M, double>, bytes);                 \
+            k_haar_synthesis<TIn, TOut, M, double><<<grid, 256, bytes, st>>>(G, P, tiles, ntiles, a); \
+        }                                                                                          \
         break;
     switch (a.mode) { WMG_HS(HS_STORE) WMG_HS(HS_STORE_MASKED) WMG_HS(HS_CORRECT) default: break; }
 #undef WMG_HS

@@ -213,6 +213,7 @@ struct HaarArgs {
     void *outT;              // synthesis: transposed T copy (or NULL)
     double *z;               // HS_CORRECT: FP64 vector updated in place
     const double *S;         // scalars (active flags) or NULL
+    int fp32;                // butterflies in FP32 (the WMG cycle of FP32 plans), else FP64
 };
 template <class TIn, class TOut>
 void launch_haar_analysis(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,

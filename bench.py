@@ -82,6 +82,9 @@ def parse():
                     help="skip the semi-convergence leg (160^2, 400 angles, Joseph's kernel, noisy data)")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 1024x1024 / 1024-angle leg (mixed FP32 path vs the FP64 GPU path)")
+    ap.add_argument("--solve-case", action="store_true",
+                    help="run three solves of the workload batch and exit: the case for ncu captures of the "
+                         "solve's secondary kernels (Gram-Schmidt, leaf solves, Haar packets)")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run 3 projector and 3 backprojector launches on a batch of 16 images of the "
                          "workload geometry (FP32) and exit: the small case for ncu captures")
@@ -817,6 +820,31 @@ def roofline_entry(prof: dict, P0, B: int) -> dict:
                      f"peak derived: 152 SMs x 128 FP32 lanes x 2 FLOP x {clk:.0f} MHz")}
 
 
+def solve_case(batch: int):
+    """Three solves of the workload batch (the bench's inputs and solver) and
+    exit: the case for ncu captures of the solve's secondary kernels."""
+    import torch
+    import paper_1310_0956_gb300 as wmg
+    probs = workload_problems(batch, 0)
+    P0 = probs[0]
+    plan = wmg.Plan(P0.n, P0.m, P0.D, levels=LEVELS, nu1=NU1, nu2=NU2, hybrid_depth=HYB,
+                    cycle=wmg.CYCLE_HYBRID, precision=wmg.PREC_F32)
+    p64 = wmg.Plan(P0.n, P0.m, P0.D, levels=0, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F64)
+    imgs = torch.tensor(np.stack([p.image() for p in probs]).reshape(-1), dtype=torch.float64, device="cuda")
+    b64 = p64.project(imgs).view(len(probs), P0.M)
+    noise = torch.tensor(np.stack([p.noise_unit() for p in probs]), dtype=torch.float64, device="cuda")
+    sigma = torch.tensor([p.noise for p in probs], dtype=torch.float64, device="cuda")[:, None] * \
+        b64.abs().amax(dim=1, keepdim=True)
+    b = (b64 + sigma * noise).to(torch.float32).contiguous().view(-1)
+    x = torch.empty(len(probs) * P0.N, dtype=torch.float32, device="cuda")
+    its = []
+    for _ in range(3):
+        _, info, _, _ = plan.solve(b, wmg.SOLVER_GMRES, True, MAX_ITER, RTOL, RESTART, out=x)
+        its.append(float(np.mean([i[0] for i in info])))
+    torch.cuda.synchronize()
+    print(json.dumps({"solve_case": "ok", "iters_mean": its}))
+
+
 def kernel_case():
     import torch
     import paper_1310_0956_gb300 as wmg
@@ -839,6 +867,9 @@ def main():
     rank, world, local = dist_env()
     if args.kernel_case:
         kernel_case()
+        return
+    if args.solve_case:
+        solve_case(args.batch)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)

@@ -814,12 +814,21 @@ def roofline_entry(prof: dict, P0, B: int) -> dict:
     peaks = load_peaks()
     clk = peaks.get("sm_max_mhz", 2070.0)
     peak = 152 * 128 * 2 * clk * 1e6 / 1e12
+    # the same launch as an HBM client: algorithmic bytes = the FP32 input
+    # (the projector reads each image and its transpose) and output vectors
+    n_in = 2 * P0.N if name == "project" else P0.M
+    n_out = P0.M if name == "project" else P0.N
+    gbs = p["images_per_launch"] * (n_in + n_out) * 4 / (p["mean_ms"] * 1e-3) / 1e9
+    hbm = peaks.get("hbm_gbs")
     return {"kernel": f"k_{name}", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": _kernel_traffic(name, p["images_per_launch"]),
             "traffic_unit": "bytes per launch (DRAM read + write)",
+            "algorithmic_gbs": gbs, "hbm_frac_of_measured": (gbs / hbm) if hbm else None,
             "note": (f"{p['launches']} launches, mean {p['mean_ms']:.3f} ms, "
                      f"{nnz_per_image * p['images_per_launch'] / (p['mean_ms'] * 1e-3) / 1e9:.0f} Gnnz/s; "
-                     f"peak derived: 152 SMs x 128 FP32 lanes x 2 FLOP x {clk:.0f} MHz")}
+                     f"peak derived: 152 SMs x 128 FP32 lanes x 2 FLOP x {clk:.0f} MHz; as an HBM client "
+                     f"{gbs:.0f} GB/s of algorithmic bytes"
+                     + (f" = {gbs / hbm:.3f} of the measured {hbm:.0f} GB/s" if hbm else ""))}
 
 
 def solve_case(batch: int):

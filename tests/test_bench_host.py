@@ -1,0 +1,27 @@
+"""Host-side arithmetic of bench.py's roofline entry (no GPU): the dominant
+kernel's achieved FP32 rate, its fraction of the derived peak, and its
+algorithmic HBM bytes per second."""
+import bench
+
+
+class P0:
+    N, M = 65536, 65340
+
+
+def test_roofline_entry_arithmetic():
+    prof = {"nnz_per_image": 15149028.0,
+            "project": {"launches": 60, "total_ms": 138.0, "mean_ms": 2.3, "images_per_launch": 256.0},
+            "backproject": {"launches": 60, "total_ms": 120.0, "mean_ms": 2.0, "images_per_launch": 256.0}}
+    r = bench.roofline_entry(prof, P0, 256)
+    assert r["kernel"] == "k_project" and r["bound"] == "alu"
+    flops = 2 * 15149028.0 * 256 / 2.3e-3
+    assert abs(r["achieved"] - flops / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    assert abs(r["peak"] - 152 * 128 * 2 * 2070e6 / 1e12) < 1e-9
+    gbs = 256 * (2 * 65536 + 65340) * 4 / 2.3e-3 / 1e9
+    assert abs(r["algorithmic_gbs"] - gbs) < 1e-6
+    assert 0.0 < r["hbm_frac_of_measured"] < 0.1
+
+
+def test_whole_job_value():
+    assert bench.whole_job_value(256, 2, 5, 2.0) == 256 * 2 * 5 / 2.0

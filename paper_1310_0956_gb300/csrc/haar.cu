@@ -331,7 +331,10 @@ k_leaf_apply32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
                const int4 *__restrict__ tiles, int ntiles, const double *__restrict__ C,
                double *__restrict__ E, int accumulate, const double *__restrict__ S)
 {
-    __shared__ float cb[NPB][256];
+    // coefficient j of the group's problems side by side (row pitch NPB + 4:
+    // 16-byte rows for vector loads, fewer bank conflicts when filling)
+    constexpr int kPitch = NPB + 4;
+    __shared__ __align__(16) float cb[256][kPitch];
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 tl = tiles[t];
         const GeomDev &g = G[P[tl.x].geom];
@@ -346,7 +349,7 @@ k_leaf_apply32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
                 const ProbDev pd = P[tl.x + pb + pi];
                 if (slot_active(S, pd.slot)) v = (float)C[pd.coef + (int64_t)k * Pn + j];
             }
-            cb[pi][j] = v;
+            cb[j][pi] = v;
         }
         __syncthreads();
         const int i = threadIdx.x;
@@ -357,8 +360,15 @@ k_leaf_apply32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
 #pragma unroll 4
             for (int j = 0; j < Pn; ++j) {
                 const float d = __ldg(Dk + (int64_t)j * Pn + i);
+                const float4 *cj = reinterpret_cast<const float4 *>(cb[j]);
 #pragma unroll
-                for (int u = 0; u < NPB; ++u) acc[u] = __fmaf_rn(d, cb[u][j], acc[u]);
+                for (int u4 = 0; u4 < NPB / 4; ++u4) {
+                    const float4 c = cj[u4];
+                    acc[4 * u4 + 0] = __fmaf_rn(d, c.x, acc[4 * u4 + 0]);
+                    acc[4 * u4 + 1] = __fmaf_rn(d, c.y, acc[4 * u4 + 1]);
+                    acc[4 * u4 + 2] = __fmaf_rn(d, c.z, acc[4 * u4 + 2]);
+                    acc[4 * u4 + 3] = __fmaf_rn(d, c.w, acc[4 * u4 + 3]);
+                }
             }
 #pragma unroll
             for (int u = 0; u < NPB; ++u) {

@@ -25,3 +25,13 @@ def test_roofline_entry_arithmetic():
 
 def test_whole_job_value():
     assert bench.whole_job_value(256, 2, 5, 2.0) == 256 * 2 * 5 / 2.0
+
+
+def test_study_helpers():
+    from paper_1310_0956_gb300 import study
+    ks = study.log_ks(3000, 6)
+    assert ks[0] == 1 and ks[-1] == 3000 and all(b > a for a, b in zip(ks, ks[1:]))
+    assert len(ks) < 30
+    curve = [(1, 1, 0.9, 1.0), (2, 2, 0.5, 0.7), (4, 4, 0.3, 0.6), (8, 8, 0.35, 0.5)]
+    k, row = study.k_opt(curve)
+    assert k == 4 and row[2] == 0.3

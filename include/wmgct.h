@@ -52,9 +52,10 @@ extern "C" {
 #define WMG_ERR_LEAF_NOT_SPD  -4   /* a leaf matrix failed its Cholesky pivot test */
 #define WMG_ERR_BREAKDOWN     -5   /* Krylov breakdown: zero curvature / Hessenberg */
 #define WMG_ERR_TIMEOUT       -6   /* a kernel's bounded wait for staged data ran out
-                                      (TMA projector); that call's results are invalid,
-                                      the CUDA context stays usable. Reported by the
-                                      next synchronising call on the plan */
+                                      (TMA projector); the results computed since are
+                                      invalid, the CUDA context stays usable. Reported
+                                      when the next wmg_solve (any plan of the process)
+                                      completes */
 #define WMG_ERR_NAN           -7   /* non-finite value in a reduction */
 #define WMG_ERR_REJECTED      -8   /* server: request larger than the memory budget */
 

@@ -387,8 +387,9 @@ int32_t wmg_profile_end(wmg_plan *plan, wmg_profile_stats *out, void *stream);
  * free device memory. The paper has no counterpart: this is an interface
  * variant of wmg_project, not part of the method.
  * Geometry: n x n image, m equiangular angles over [0, pi), D bins of one
- * pixel width, centred; FP32 image x (n*n) and sinogram b (m*D), device
- * memory, one image per call. Results equal wmg_project's for that geometry.
+ * pixel width, centred, W = exact intersection lengths (WMG_KERNEL_STRIP);
+ * FP32 image x (n*n) and sinogram b (m*D), device memory, one image per call.
+ * Results equal wmg_project's for that geometry.
  * Limits: n <= 1024, m <= 4096, D <= 2048; larger sizes return
  * WMG_ERR_INVALID_ARG. The scratch (transposed image, work lists, angle
  * tables; about 12 MiB) lives in fixed __device__ arrays that every GPU which

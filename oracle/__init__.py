@@ -94,13 +94,13 @@ def _load():
         lib.or_wmg_free.argtypes = [vp]
         lib.or_wmg_apply.argtypes = [vp, _dp, _dp]
         lib.or_cgls.restype = C.c_int
-        lib.or_cgls.argtypes = [vp, vp, C.c_double, _dp, _dp, C.c_int, C.c_double, C.c_void_p]
+        lib.or_cgls.argtypes = [vp, vp, C.c_double, _dp, _dp, C.c_int, C.c_int, C.c_double, C.c_void_p]
         lib.or_set_reverse.argtypes = [C.c_int]
         lib.or_bicgstab.restype = C.c_int
-        lib.or_bicgstab.argtypes = [vp, vp, C.c_double, _dp, _dp, C.c_int, C.c_double, vp,
+        lib.or_bicgstab.argtypes = [vp, vp, C.c_double, _dp, _dp, C.c_int, C.c_int, C.c_double, vp,
                                     C.POINTER(C.c_int)]
         lib.or_gmres.restype = C.c_int
-        lib.or_gmres.argtypes = [vp, vp, C.c_double, _dp, _dp, C.c_int, C.c_int, C.c_double,
+        lib.or_gmres.argtypes = [vp, vp, C.c_double, _dp, _dp, C.c_int, C.c_int, C.c_int, C.c_double,
                                  C.c_void_p]
         _lib = lib
         return lib
@@ -282,34 +282,43 @@ def sirt(op: Op, b, iters: int, lam: float = 0.0, x0=None):
     return x, hist
 
 
-def cgls(op: Op, b, max_iter: int, rtol: float = 0.0, lam: float = 0.0, precond: Wmg = None):
-    """(Preconditioned) CGLS; returns (x, iterations, relative NE residual history)."""
-    x = np.zeros(op.N)
+def _start(op: Op, x0):
+    """The solver's x buffer: x0 (copied) and use_x0 = 1, or zeros and 0."""
+    if x0 is None:
+        return np.zeros(op.N), 0
+    return _f64(x0).copy(), 1
+
+
+def cgls(op: Op, b, max_iter: int, rtol: float = 0.0, lam: float = 0.0, precond: Wmg = None, x0=None):
+    """(Preconditioned) CGLS from x0 (default 0); returns (x, iterations,
+    relative NE residual history, relative to the residual of x0)."""
+    x, warm = _start(op, x0)
     hist = np.zeros(max_iter + 1)
-    k = _load().or_cgls(op._h, precond._h if precond else None, lam, _f64(b), x, max_iter, rtol,
+    k = _load().or_cgls(op._h, precond._h if precond else None, lam, _f64(b), x, warm, max_iter, rtol,
                         hist.ctypes.data_as(C.c_void_p))
     return x, k, hist[:k + 1]
 
 
 def gmres(op: Op, b, max_iter: int, restart: int = 20, rtol: float = 0.0, lam: float = 0.0,
-          precond: Wmg = None):
-    """Restarted right-preconditioned GMRES on (W^T W + lam) x = W^T b;
-    returns (x, iterations, relative residual history)."""
-    x = np.zeros(op.N)
+          precond: Wmg = None, x0=None):
+    """Restarted right-preconditioned GMRES on (W^T W + lam) x = W^T b from
+    x0 (default 0); returns (x, iterations, relative residual history)."""
+    x, warm = _start(op, x0)
     hist = np.zeros(max_iter + 1)
-    k = _load().or_gmres(op._h, precond._h if precond else None, lam, _f64(b), x, restart,
+    k = _load().or_gmres(op._h, precond._h if precond else None, lam, _f64(b), x, warm, restart,
                          max_iter, rtol, hist.ctypes.data_as(C.c_void_p))
     return x, k, hist[:k + 1]
 
 
-def bicgstab(op: Op, b, max_iter: int, rtol: float = 0.0, lam: float = 0.0, precond: Wmg = None):
+def bicgstab(op: Op, b, max_iter: int, rtol: float = 0.0, lam: float = 0.0, precond: Wmg = None, x0=None):
     """Right-preconditioned BiCGStab on (W^T W + lam) x = W^T b, the paper's
-    Krylov solver (Section 2.3.1, Section 4); returns (x, iterations, relative
-    residual history, status: 0 converged, 1 iteration cap, -5 breakdown)."""
-    x = np.zeros(op.N)
+    Krylov solver (Section 2.3.1, Section 4), from x0 (default 0); returns
+    (x, iterations, relative residual history, status: 0 converged, 1
+    iteration cap, -5 breakdown)."""
+    x, warm = _start(op, x0)
     hist = np.zeros(max_iter + 1)
     st = C.c_int(0)
-    k = _load().or_bicgstab(op._h, precond._h if precond else None, lam, _f64(b), x, max_iter, rtol,
+    k = _load().or_bicgstab(op._h, precond._h if precond else None, lam, _f64(b), x, warm, max_iter, rtol,
                             hist.ctypes.data_as(C.c_void_p), C.byref(st))
     return x, k, hist[:k + 1], st.value
 

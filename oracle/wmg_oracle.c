@@ -831,22 +831,26 @@ void or_wmg_apply(const or_wmg *M, const double *s, double *z)
 /* ------------------------------------------------------------------------ */
 
 /* CGLS for min ||Wx - b||^2 + lambda ||x||^2, optionally preconditioned by a
- * symmetric positive definite B (WMG): x0 = 0, r = b, s = W^T r,
+ * symmetric positive definite B (WMG): from x0 (the x passed in when use_x0,
+ * else 0), r = b - W x0, s = W^T r - lambda x0,
  * z = B s, p = z, gamma = s.z; then per iteration q = W p,
  * delta = ||q||^2 + lambda ||p||^2, alpha = gamma/delta, x += alpha p,
  * r -= alpha q, s = W^T r - lambda x, z = B s, beta = (s.z)/gamma, p = z + beta p.
  * res_hist[k] = ||s_k|| / ||s_0|| (the relative NE residual). Stops when it
  * drops below rtol or after max_iter iterations; returns the count. */
-int or_cgls(const or_op *op, const or_wmg *M, double lambda, const double *b, double *x,
+int or_cgls(const or_op *op, const or_wmg *M, double lambda, const double *b, double *x, int use_x0,
             int max_iter, double rtol, double *res_hist)
 {
     const int64_t Mr = (int64_t)op->m * op->D, N = (int64_t)op->n * op->n;
     double *r = malloc((size_t)Mr * sizeof(double)), *q = malloc((size_t)Mr * sizeof(double));
     double *s = malloc((size_t)N * sizeof(double)), *z = malloc((size_t)N * sizeof(double));
     double *p = malloc((size_t)N * sizeof(double));
-    for (int64_t j = 0; j < N; j++) x[j] = 0.0;
-    memcpy(r, b, (size_t)Mr * sizeof(double));
+    if (!use_x0)
+        for (int64_t j = 0; j < N; j++) x[j] = 0.0;
+    or_project(op, x, q);
+    for (int64_t i = 0; i < Mr; i++) r[i] = b[i] - q[i];
     or_backproject(op, r, s);
+    for (int64_t j = 0; j < N; j++) s[j] -= lambda * x[j];
     if (M) or_wmg_apply(M, s, z); else memcpy(z, s, (size_t)N * sizeof(double));
     memcpy(p, z, (size_t)N * sizeof(double));
     double gamma = dot(s, z, N);
@@ -880,11 +884,12 @@ done:
 
 /* Restarted GMRES(restart) with right preconditioning (Section 2.3.1, the
  * paper's experiments use right preconditioning) on A x = f, A = W^T W +
- * lambda I, f = W^T b, x0 = 0. Arnoldi by modified Gram-Schmidt, Givens
- * rotations for the least-squares problem; at the end of each cycle
- * x += B (V y). res_hist[k] = |g_{k}| / ||f|| after k Arnoldi steps (the
- * residual estimate), replaced at each restart by the true relative residual. */
-int or_gmres(const or_op *op, const or_wmg *M, double lambda, const double *b, double *x,
+ * lambda I, f = W^T b, from x0 (the x passed in when use_x0, else 0).
+ * Arnoldi by modified Gram-Schmidt, Givens rotations for the least-squares
+ * problem; at the end of each cycle x += B (V y). res_hist[k] = |g_{k}| /
+ * ||r0|| after k Arnoldi steps (the residual estimate; r0 = f - A x0),
+ * replaced at each restart by the true relative residual. */
+int or_gmres(const or_op *op, const or_wmg *M, double lambda, const double *b, double *x, int use_x0,
              int restart, int max_iter, double rtol, double *res_hist)
 {
     const int64_t Mr = (int64_t)op->m * op->D, N = (int64_t)op->n * op->n;
@@ -895,13 +900,18 @@ int or_gmres(const or_op *op, const or_wmg *M, double lambda, const double *b, d
     double *g = malloc((size_t)(mr + 1) * sizeof(double)), *y = malloc((size_t)mr * sizeof(double));
     double *f = malloc((size_t)N * sizeof(double)), *w = malloc((size_t)N * sizeof(double));
     double *u = malloc((size_t)N * sizeof(double)), *tmpM = malloc((size_t)Mr * sizeof(double));
-    for (int64_t j = 0; j < N; j++) x[j] = 0.0;
     or_backproject(op, b, f);
-    const double fn = sqrt(dot(f, f, N));
+    if (use_x0) {
+        apply_A(op, lambda, x, w, tmpM);
+        for (int64_t t = 0; t < N; t++) V[t] = f[t] - w[t];
+    } else {
+        for (int64_t j = 0; j < N; j++) x[j] = 0.0;
+        memcpy(V, f, (size_t)N * sizeof(double));    /* r0 = f since x0 = 0 */
+    }
+    const double fn = sqrt(dot(V, V, N));
     if (res_hist) res_hist[0] = 1.0;
     int k = 0;
     if (fn == 0.0) goto done;
-    memcpy(V, f, (size_t)N * sizeof(double));        /* r0 = f since x0 = 0 */
     double beta = fn;
     while (k < max_iter) {
         for (int64_t j = 0; j < N; j++) V[j] /= beta;
@@ -961,7 +971,8 @@ done:
 }
 
 /* Right-preconditioned BiCGStab (van der Vorst, 1992) on (W^T W + lambda) x =
- * W^T b from x0 = 0 -- the Krylov solver of the paper's experiments
+ * W^T b from x0 (the x passed in when use_x0, else 0) -- the Krylov solver
+ * of the paper's experiments
  * (Section 2.3.1 and Section 4): the shadow residual is r0; per iteration
  *   rho = <rh, r>, beta = (rho / rho_prev)(alpha / omega),
  *   p = r + beta (p - omega v), ph = B p, v = A ph, alpha = rho / <rh, v>,
@@ -970,7 +981,7 @@ done:
  * with B the WMG cycle (identity when M is NULL). res_hist[k] = |r_k| / |r_0|.
  * *status: 0 converged (rtol) or r = 0, 1 iteration cap, -5 breakdown
  * (rho or <rh, v> zero, or omega zero with r nonzero). Returns the count. */
-int or_bicgstab(const or_op *op, const or_wmg *M, double lambda, const double *b, double *x,
+int or_bicgstab(const or_op *op, const or_wmg *M, double lambda, const double *b, double *x, int use_x0,
                 int max_iter, double rtol, double *res_hist, int *status)
 {
     const int64_t Mr = (int64_t)op->m * op->D, N = (int64_t)op->n * op->n;
@@ -979,8 +990,13 @@ int or_bicgstab(const or_op *op, const or_wmg *M, double lambda, const double *b
     double *ph = malloc((size_t)N * sizeof(double)), *sv = malloc((size_t)N * sizeof(double));
     double *sh = malloc((size_t)N * sizeof(double)), *t = malloc((size_t)N * sizeof(double));
     double *tmpM = malloc((size_t)Mr * sizeof(double));
-    for (int64_t j = 0; j < N; j++) x[j] = 0.0;
-    or_backproject(op, b, r);                          /* r0 = f - A 0 */
+    or_backproject(op, b, r);                          /* r0 = f - A x0 */
+    if (use_x0) {
+        apply_A(op, lambda, x, t, tmpM);
+        for (int64_t j = 0; j < N; j++) r[j] -= t[j];
+    } else {
+        for (int64_t j = 0; j < N; j++) x[j] = 0.0;
+    }
     memcpy(rh, r, (size_t)N * sizeof(double));
     const double r0 = sqrt(dot(r, r, N));
     if (res_hist) res_hist[0] = 1.0;

@@ -174,7 +174,8 @@ int32_t wmg_haar_synthesis(wmg_plan *plan, int32_t count, const void *c, void *x
 int32_t wmg_leaf_inverse(wmg_plan *plan, int64_t k, void *out, void *stream);
 
 /* Solve `count` problems of the plan's geometry: b (count sinograms) ->
- * x (count images). x0 = 0 (x is output only). solver = WMG_SOLVER_*;
+ * x (count images). x0 = 0 (x is output only; wmg_solve_x0 takes an
+ * initial guess). solver = WMG_SOLVER_*;
  * preconditioned = 1 uses one WMG cycle per iteration (two for BiCGStab;
  * CGLS needs the SYMMETRIC or ADDITIVE cycle; GMRES and BiCGStab any; SIRT
  * ignores it). A BiCGStab iteration counts as one (two A-pairs); its
@@ -190,6 +191,62 @@ int32_t wmg_leaf_inverse(wmg_plan *plan, int64_t k, void *out, void *stream);
 int32_t wmg_solve(wmg_plan *plan, int32_t solver, int32_t preconditioned, int32_t count,
                   const void *b, void *x, int32_t max_iter, double rtol, int32_t restart,
                   wmg_solve_info *info, double *res_hist, void *stream);
+
+/* As wmg_solve, from the initial guess x0 (count images, device, plan
+ * precision; NULL means x0 = 0, which is wmg_solve; x0 may be x itself).
+ * Each solver starts from the NE residual of x0, r0 = W^T (b - W x0) -
+ * lambda x0 (Section 2.1, eq. sys_reg): CGLS with r = b - W x0 and s = r0,
+ * GMRES and BiCGStab with r0 (BiCGStab's shadow residual is r0), SIRT
+ * iterates eq. sirt_it from x0. rel_res, rtol and res_hist are relative to
+ * |r0| (to |W^T b| when x0 = 0); a Krylov solve with r0 = 0 ends at once
+ * with WMG_OK and x = x0. Synchronising. */
+int32_t wmg_solve_x0(wmg_plan *plan, int32_t solver, int32_t preconditioned, int32_t count,
+                     const void *b, const void *x0, void *x, int32_t max_iter, double rtol, int32_t restart,
+                     wmg_solve_info *info, double *res_hist, void *stream);
+
+/* ---- checkpoint / resume ----------------------------------------------------
+ * A plan (wmg_plan_create) keeps the state of its last wmg_solve or
+ * wmg_solve_x0 that returned WMG_OK or WMG_NOT_CONVERGED: the FP64 iterate,
+ * the solver's other vectors (CGLS: r, p, s; GMRES at its last restart:
+ * W^T b, the true residual, rotation data; BiCGStab: r, the shadow
+ * residual, p, v; operator-precision copies included) and per-problem
+ * scalars, iteration counts, status and residual histories.
+ * wmg_solve_resume continues that solve; wmg_state_export copies the state
+ * to a host buffer and wmg_state_import copies it back, into the same plan
+ * or into another plan made with the same geometry and options (as in a
+ * restarted process). Any wmg_project, wmg_precond_apply or solve call on
+ * the plan, or a call with another problem count, discards the state.
+ * Batches and the server keep none. The contents of the buffer are native
+ * binary (same machine architecture and library version). */
+
+/* Bytes wmg_state_export writes. WMG_ERR_INVALID_ARG if the plan holds no
+ * state. */
+int32_t wmg_state_bytes(wmg_plan *plan, int64_t *bytes);
+
+/* Copies the state into host (HOST, at least wmg_state_bytes bytes).
+ * Synchronising. */
+int32_t wmg_state_export(wmg_plan *plan, void *host, int64_t bytes, void *stream);
+
+/* Makes host (HOST, bytes long; written by wmg_state_export) the plan's
+ * state. WMG_ERR_INVALID_ARG when it is not a state, or the state of a
+ * plan with another geometry, options, precision or problem sizes; the
+ * plan then holds no state. Synchronising. */
+int32_t wmg_state_import(wmg_plan *plan, const void *host, int64_t bytes, void *stream);
+
+/* Continues the plan's state to max_iter iterations IN TOTAL (the state's
+ * iterations included; max_iter below them is WMG_ERR_INVALID_ARG), with
+ * the same solver, preconditioning, restart length and problem count, and
+ * a new rtol. b: the same right-hand side (count sinograms, device). x
+ * receives the iterates (count images). Problems that stopped at the old
+ * iteration cap run on; converged or failed ones keep their result (SIRT
+ * runs every problem to max_iter, as its fixed count). info, res_hist and
+ * the return value as wmg_solve over all max_iter iterations. The kernels'
+ * summation orders are fixed, so the results are bitwise those of one
+ * uninterrupted solve with this max_iter; for GMRES when the checkpoint is
+ * at a restart of that solve (its iteration count a multiple of restart),
+ * else the continuation restarts at the checkpoint. Synchronising. */
+int32_t wmg_solve_resume(wmg_plan *plan, const void *b, void *x, int32_t max_iter, double rtol,
+                         wmg_solve_info *info, double *res_hist, void *stream);
 
 /* ---- batches of problems of different geometries ------------------------- */
 /* A batch solves `count` independent reconstructions, each with its own

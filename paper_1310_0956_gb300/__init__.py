@@ -94,6 +94,12 @@ _SIGNATURES = {
     "wmg_leaf_inverse": (_i32, [_vp, _i64, _vp, _vp]),
     "wmg_solve": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _i32, _dbl, _i32,
                          C.POINTER(wmg_solve_info), C.POINTER(_dbl), _vp]),
+    "wmg_solve_x0": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _vp, _i32, _dbl, _i32,
+                            C.POINTER(wmg_solve_info), C.POINTER(_dbl), _vp]),
+    "wmg_state_bytes": (_i32, [_vp, C.POINTER(_i64)]),
+    "wmg_state_export": (_i32, [_vp, _vp, _i64, _vp]),
+    "wmg_state_import": (_i32, [_vp, _vp, _i64, _vp]),
+    "wmg_solve_resume": (_i32, [_vp, _vp, _vp, _i32, _dbl, C.POINTER(wmg_solve_info), C.POINTER(_dbl), _vp]),
     "wmg_plan_nnz": (_i32, [_vp, C.POINTER(_i64)]),
     "wmg_launch_count": (_i64, [_i32]),
     "wmg_plan_get_tuning": (_i32, [_vp, C.POINTER(_i32), C.POINTER(_i32)]),
@@ -204,6 +210,31 @@ def wmg_solve(plan, solver, preconditioned, count, b, x, max_iter, rtol, restart
               stream=None) -> int:
     return _check(lib().wmg_solve(plan, solver, preconditioned, count, b, x, max_iter, rtol, restart,
                                   info, res_hist, stream), allow_not_converged=True)
+
+
+def wmg_solve_x0(plan, solver, preconditioned, count, b, x0, x, max_iter, rtol, restart, info, res_hist,
+                 stream=None) -> int:
+    return _check(lib().wmg_solve_x0(plan, solver, preconditioned, count, b, x0, x, max_iter, rtol, restart,
+                                     info, res_hist, stream), allow_not_converged=True)
+
+
+def wmg_state_bytes(plan) -> int:
+    n = _i64()
+    _check(lib().wmg_state_bytes(plan, C.byref(n)))
+    return n.value
+
+
+def wmg_state_export(plan, host, nbytes, stream=None) -> None:
+    _check(lib().wmg_state_export(plan, host, nbytes, stream))
+
+
+def wmg_state_import(plan, host, nbytes, stream=None) -> None:
+    _check(lib().wmg_state_import(plan, host, nbytes, stream))
+
+
+def wmg_solve_resume(plan, b, x, max_iter, rtol, info, res_hist, stream=None) -> int:
+    return _check(lib().wmg_solve_resume(plan, b, x, max_iter, rtol, info, res_hist, stream),
+                  allow_not_converged=True)
 
 
 def wmg_project_noalloc(n, m, D, x, b, stream=None):
@@ -451,21 +482,57 @@ class Plan:
         return res
 
     def solve(self, b, solver=SOLVER_CGLS, preconditioned=True, max_iter=100, rtol=1e-4, restart=20,
-              out=None, history=False):
-        """Returns (x, info list, residual histories or None)."""
+              out=None, history=False, x0=None):
+        """Returns (x, info list, residual histories or None). x0: initial
+        guess (wmg_solve_x0), default 0."""
         bp, cnt = self._arg(b, self.M)
         out = out if out is not None else self._torch.empty(cnt * self.N, dtype=self.dtype, device=b.device)
         info = (wmg_solve_info * cnt)()
         hist = (C.c_double * (cnt * (max_iter + 1)))() if history else None
-        rc = wmg_solve(self.handle, solver, 1 if preconditioned else 0, cnt, bp, self._arg(out, self.N)[0],
-                       max_iter, rtol, restart, info, hist, self._stream())
+        xp = self._arg(out, self.N)[0]
+        if x0 is None:
+            rc = wmg_solve(self.handle, solver, 1 if preconditioned else 0, cnt, bp, xp, max_iter, rtol, restart,
+                           info, hist, self._stream())
+        else:
+            x0p, c0 = self._arg(x0, self.N)
+            if c0 != cnt:
+                raise ValueError("x0 must hold as many images as b has sinograms")
+            rc = wmg_solve_x0(self.handle, solver, 1 if preconditioned else 0, cnt, bp, x0p, xp, max_iter, rtol,
+                              restart, info, hist, self._stream())
+        return (out,) + self._results(cnt, max_iter, info, hist) + (rc,)
+
+    def _results(self, cnt, max_iter, info, hist):
         infos = [(info[i].iters, info[i].status, info[i].rel_res) for i in range(cnt)]
         hists = None
-        if history:
+        if hist is not None:
             import numpy as np
             h = np.frombuffer(hist, dtype=np.float64).reshape(cnt, max_iter + 1)
             hists = [h[i, :infos[i][0] + 1].copy() for i in range(cnt)]
-        return out, infos, hists, rc
+        return infos, hists
+
+    def state_export(self) -> bytes:
+        """The state of the last solve (wmg_state_export) as bytes."""
+        n = wmg_state_bytes(self.handle)
+        buf = C.create_string_buffer(n)
+        wmg_state_export(self.handle, buf, n, self._stream())
+        return buf.raw
+
+    def state_import(self, state: bytes) -> None:
+        """Makes `state` (from state_export of a plan of the same geometry
+        and options) this plan's solver state (wmg_state_import)."""
+        buf = C.create_string_buffer(bytes(state), len(state))
+        wmg_state_import(self.handle, buf, len(state), self._stream())
+
+    def resume(self, b, max_iter, rtol=1e-4, out=None, history=False):
+        """Continues the plan's solver state to max_iter iterations in total
+        (wmg_solve_resume); returns as solve."""
+        bp, cnt = self._arg(b, self.M)
+        out = out if out is not None else self._torch.empty(cnt * self.N, dtype=self.dtype, device=b.device)
+        info = (wmg_solve_info * cnt)()
+        hist = (C.c_double * (cnt * (max_iter + 1)))() if history else None
+        rc = wmg_solve_resume(self.handle, bp, self._arg(out, self.N)[0], max_iter, rtol, info, hist,
+                              self._stream())
+        return (out,) + self._results(cnt, max_iter, info, hist) + (rc,)
 
 
 class StoredOperator:

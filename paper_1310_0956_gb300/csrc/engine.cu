@@ -202,6 +202,7 @@ static int32_t set_slots(wmg_plan *pl, cudaStream_t st)
         d.img = pl->img_off[q]; d.sino = pl->sino_off[q]; d.coef = pl->img_off[q];
         d.kin0 = 0; d.kin1 = pl->geo(q).g.K; d.kout0 = 0; d.kout1 = pl->geo(q).g.K;
     }
+    pl->state.valid = false;
     build_tiles(pl, ps);
     if (!upload_set(ps, st)) return fail(WMG_ERR_OOM, "work-list allocation failed");
     pl->bands.clear();
@@ -941,6 +942,28 @@ extern "C" int32_t wmg_last_error(char *buf, size_t len)
 
 extern "C" int32_t wmg_version(void) { return 100; }
 
+// FNV-1a over everything that shapes a plan's arithmetic: the geometry
+// (with every angle) and the WMG and solver options. A solver state is
+// accepted only by a plan with the same fingerprint.
+static uint64_t plan_fingerprint(const wmg_geom &g, const wmg_opts &o)
+{
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void *p, size_t n) {
+        const unsigned char *c = static_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    };
+    const double ds = g.det_spacing > 0 ? g.det_spacing : 1.0;
+    const int32_t ints[] = {g.n, g.m, g.D, g.kernel, o.levels, o.nu1, o.nu2, o.hybrid_depth, o.cycle, o.precision};
+    const double dbls[] = {ds, g.det_offset, o.omega, o.lambda};
+    mix(ints, sizeof ints);
+    mix(dbls, sizeof dbls);
+    for (int a = 0; a < g.m; ++a) {
+        const double t = g.angles ? g.angles[a] : a * (M_PI / g.m);
+        mix(&t, sizeof t);
+    }
+    return h;
+}
+
 extern "C" int32_t wmg_plan_create(const wmg_geom *g, const wmg_opts *o, void *stream, wmg_plan **out)
 {
     if (!out) return fail(WMG_ERR_INVALID_ARG, "out is NULL");
@@ -953,6 +976,7 @@ extern "C" int32_t wmg_plan_create(const wmg_geom *g, const wmg_opts *o, void *s
     pl->esz = o->precision == WMG_PREC_F64 ? 8 : 4;
     pl->opts = *o;
     if (pl->opts.omega <= 0) pl->opts.omega = 1.0;
+    pl->fingerprint = plan_fingerprint(*g, pl->opts);
     pl->geos.push_back(std::make_unique<Geo>());
     if ((rc = make_geo(g, o, *pl->geos[0], st))) return rc;
     if ((rc = upload_geoms(pl.get(), st))) return rc;
@@ -1072,6 +1096,7 @@ extern "C" int32_t wmg_project(wmg_plan *pl, int32_t count, const void *x, void 
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((rc = ensure_count(pl, count, st))) return rc;
+    pl->state.valid = false;                 // the transposed copy lives in a solver pool
     return WMG_DISPATCH(pl, do_project, pl, x, b, st);
 }
 
@@ -1147,7 +1172,9 @@ extern "C" int32_t wmg_leaf_inverse(wmg_plan *pl, int64_t k, void *out, void *st
     return WMG_OK;
 }
 
-static void init_scalars(wmg_plan *pl, double rtol, int max_iter, cudaStream_t st)
+// Fresh per-problem scalars. `warm`: CGLS from a given x0 takes its first
+// residual as r = b - 1 * W x0 through the alpha-scaled residual update.
+static void init_scalars(wmg_plan *pl, double rtol, int max_iter, cudaStream_t st, bool warm = false)
 {
     const int count = pl->cap;
     std::vector<double> S((size_t)count * NSCAL, 0.0);
@@ -1157,6 +1184,7 @@ static void init_scalars(wmg_plan *pl, double rtol, int max_iter, cudaStream_t s
         s[SC_STATUS] = WMG_NOT_CONVERGED;
         s[SC_RTOL] = rtol;
         s[SC_MAXIT] = max_iter;
+        if (warm) s[SC_ALPHA] = 1.0;
     }
     cudaMemcpyAsync(pl->S.p, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice, st);
     cudaStreamSynchronize(st);
@@ -1192,6 +1220,7 @@ extern "C" int32_t wmg_precond_apply(wmg_plan *pl, int32_t count, const void *s,
     if (!pl->has_wmg()) return fail(WMG_ERR_INVALID_ARG, "wmg_precond_apply: the plan has no WMG levels");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((rc = ensure_count(pl, count, st))) return rc;
+    pl->state.valid = false;                 // runs in the solver pools
     return WMG_DISPATCH(pl, do_precond, pl, s, z, st);
 }
 
@@ -1290,71 +1319,115 @@ static int32_t collect(wmg_plan *pl, int max_iter, wmg_solve_info *info, double 
     return rc;
 }
 
-template <class T>
-static int32_t solve_cgls(wmg_plan *pl, bool pre, const void *b, void *xout, int max_iter, cudaStream_t st)
+// The pools each solver keeps its vectors in (all slots back to back). A
+// resumed solve and a state import ask for the same sizes, so neither moves
+// (and so empties) a pool the other filled.
+static int32_t solver_pools(wmg_plan *pl, int solver, bool pre, int restart)
 {
+    const int count = pl->cap;
     const int64_t nN = pl->Ntot, nM = pl->Mtot;
     const size_t e = pl->esz;
-    if (!ensure_pool(pl->x, nN, 8) || !ensure_pool(pl->s, nN, 8) || !ensure_pool(pl->z, nN, 8) ||
-        !ensure_pool(pl->p, nN, 8) || !ensure_pool(pl->r, nM, 8) || !ensure_pool(pl->p_op, nN, e) ||
-        !ensure_pool(pl->pT_op, nN, e) || !ensure_pool(pl->q, nM, e) || !ensure_pool(pl->r_op, nM, e) ||
-        !ensure_partials(pl, 1))
-        return fail(WMG_ERR_OOM, "CGLS pools");
-    if (pre) {
-        int32_t rc = ensure_wmg_pools(pl);
-        if (rc) return rc;
+    bool ok;
+    const char *what;
+    if (solver == WMG_SOLVER_CGLS) {
+        what = "CGLS pools";
+        ok = ensure_pool(pl->x, nN, 8) && ensure_pool(pl->s, nN, 8) && ensure_pool(pl->z, nN, 8) &&
+             ensure_pool(pl->p, nN, 8) && ensure_pool(pl->r, nM, 8) && ensure_pool(pl->p_op, nN, e) &&
+             ensure_pool(pl->pT_op, nN, e) && ensure_pool(pl->q, nM, e) && ensure_pool(pl->r_op, nM, e) &&
+             ensure_partials(pl, 1);
+    } else if (solver == WMG_SOLVER_SIRT) {
+        what = "SIRT pools";
+        ok = ensure_pool(pl->x, nN, 8) && ensure_pool(pl->p_op, nN, e) && ensure_pool(pl->pT_op, nN, e) &&
+             ensure_pool(pl->q, nM, e) && ensure_pool(pl->r_op, nM, e) && ensure_pool(pl->s, nN, 8) &&
+             ensure_partials(pl, 1);
+    } else if (solver == WMG_SOLVER_GMRES) {
+        what = "GMRES pools";
+        const int ldp = restart + 1;
+        ok = ensure_pool(pl->x, nN, 8) && ensure_pool(pl->f, nN, 8) && ensure_pool(pl->w, nN, 8) &&
+             ensure_pool(pl->t, nN, 8) && ensure_pool(pl->u, nN, 8) && ensure_pool(pl->V, nN * ldp, 8) &&
+             ensure_pool(pl->z_op, nN, e) && ensure_pool(pl->zT_op, nN, e) && ensure_pool(pl->sinoS, nM, e) &&
+             ensure_partials(pl, ldp) && pl->H.ensure((size_t)count * ldp * restart * 8) &&
+             pl->gcs.ensure((size_t)count * restart * 8) && pl->gsn.ensure((size_t)count * restart * 8) &&
+             pl->gg.ensure((size_t)count * ldp * 8) && pl->gy.ensure((size_t)count * ldp * 8) &&
+             pl->h1.ensure((size_t)count * ldp * 8) && pl->h2.ensure((size_t)count * ldp * 8) &&
+             pl->jn.ensure((size_t)count * 4) && pl->done.ensure((size_t)count * 4);
+    } else {
+        what = "BiCGStab pools";
+        ok = ensure_pool(pl->x, nN, 8) && ensure_pool(pl->f, nN, 8) && ensure_pool(pl->w, nN, 8) &&
+             ensure_pool(pl->p, nN, 8) && ensure_pool(pl->t, nN, 8) && ensure_pool(pl->u, nN, 8) &&
+             ensure_pool(pl->z, nN, 8) && ensure_pool(pl->bi_t, nN, 8) && ensure_pool(pl->bi_sh, nN, 8) &&
+             ensure_pool(pl->z_op, nN, e) && ensure_pool(pl->zT_op, nN, e) && ensure_pool(pl->sinoS, nM, e) &&
+             ensure_partials(pl, 1);
     }
+    if (!ok) return fail(WMG_ERR_OOM, what);
+    if (pre && solver != WMG_SOLVER_SIRT) return ensure_wmg_pools(pl);
+    return WMG_OK;
+}
+
+// The device ranges that hold the state of the plan's last solve: the
+// per-problem scalars and residual histories, and every vector a later
+// iteration reads (operator-precision copies included, so that nothing is
+// rounded again on the way back).
+struct Region {
+    void *p;
+    size_t bytes;
+};
+
+static std::vector<Region> state_regions(wmg_plan *pl)
+{
+    const SolveState &st = pl->state;
+    const size_t count = (size_t)pl->cap, nN8 = (size_t)pl->Ntot * 8, nM8 = (size_t)pl->Mtot * 8;
+    const size_t nNe = (size_t)pl->Ntot * pl->esz, ldp = (size_t)st.restart + 1;
+    std::vector<Region> r{{pl->S.p, count * NSCAL * 8}, {pl->hist.p, count * st.hist_ld * 8}, {pl->x.p, nN8}};
+    if (st.solver == WMG_SOLVER_SIRT) {
+        // x and its operator copies (the next projection's input)
+        r.insert(r.end(), {{pl->p_op.p, nNe}, {pl->pT_op.p, nNe}});
+    } else if (st.solver == WMG_SOLVER_CGLS) {
+        // r, p and their copies; s (and with a preconditioner z and its
+        // copies, the fused first smoothing sweep) for the end of the step
+        r.insert(r.end(), {{pl->r.p, nM8}, {pl->p.p, nN8}, {pl->s.p, nN8}, {pl->z.p, nN8},
+                           {pl->p_op.p, nNe}, {pl->pT_op.p, nNe}});
+        if (st.pre) r.insert(r.end(), {{pl->z_op.p, nNe}, {pl->zT_op.p, nNe}});
+    } else if (st.solver == WMG_SOLVER_GMRES) {
+        // at a restart: W^T b, the true residual in basis slot 0, the
+        // least-squares and rotation data
+        r.insert(r.end(), {{pl->f.p, nN8}, {pl->V.p, nN8}, {pl->H.p, count * ldp * st.restart * 8},
+                           {pl->gcs.p, count * st.restart * 8}, {pl->gsn.p, count * st.restart * 8},
+                           {pl->gg.p, count * ldp * 8}, {pl->jn.p, count * 4}, {pl->done.p, count * 4}});
+    } else {
+        // r, the shadow residual, p and v
+        r.insert(r.end(), {{pl->f.p, nN8}, {pl->w.p, nN8}, {pl->p.p, nN8}, {pl->t.p, nN8}});
+    }
+    return r;
+}
+
+// CGLS from x0 (NULL: 0), or, with start > 0, the continuation of the solve
+// whose state the plan holds after `start` iterations.
+template <class T>
+static int32_t solve_cgls(wmg_plan *pl, bool pre, const void *b, const void *x0, void *xout, int max_iter,
+                          int start, cudaStream_t st)
+{
+    const int64_t nN = pl->Ntot;
+    int32_t rc0 = solver_pools(pl, WMG_SOLVER_CGLS, pre, 0);
+    if (rc0) return rc0;
     const ProbSet &ps = pl->real;
     const double *S = pl->S.as<double>();
     double *hist = pl->hist.as<double>();
     const int hld = max_iter + 1;
     double *pa = pl->part_a.as<double>(), *pb = pl->part_b.as<double>(), *pc = pl->part_c.as<double>();
     const bool smooth_fused = pre && pl->opts.nu1 >= 1;
-    cudaMemsetAsync(pl->x.p, 0, nN * 8, st);
-    cudaMemsetAsync(pl->p.p, 0, nN * 8, st);
-    // r = b, s = W^T r (x = 0, alpha = 0)
-    VecArgs va{};
-    va.r = pl->r.as<double>(); va.b_op = b; va.r_op = pl->r_op.p; va.S = S;
-    vec_op<T>(pl, VEC_R_INIT, true, va, st);
-    auto bp_s = [&](void) {
-        BpArgs a = bp_args(BP_CGLS_S, pl->r_op.p, S);
-        a.x = pl->x.as<double>(); a.p = pl->p.as<double>(); a.s = pl->s.as<double>();
-        a.part = pa;
-        if (smooth_fused) { a.z = pl->z.as<double>(); a.copy_op = pl->z_op.p; a.copyT_op = pl->zT_op.p; }
-        backproject<T>(pl, ps, a, st);
-    };
-    bp_s();
     double *zvec = pre ? pl->z.as<double>() : pl->s.as<double>();
     bool have_sz = false;
-    if (pre) {
-        int32_t rc = wmg_apply<T>(pl, pl->s.as<double>(), pl->z.as<double>(), smooth_fused, false, true,
-                                  &have_sz, st);
-        if (rc) return rc;
-        if (!have_sz) {
-            ImgArgs ia{};
-            ia.s = pl->s.as<double>(); ia.z = pl->z.as<double>(); ia.part = pb; ia.S = S;
-            img_op<T>(pl, IMG_DOT_SZ, ia, st);
-        }
-    }
-    finalize(pl, FIN_CGLS_INIT, ps.bp, pa, 1, pre ? &ps.bp : nullptr, pre ? pb : nullptr, pre, hist, hld, st);
-    ImgArgs pi{};
-    pi.z = zvec; pi.p = pl->p.as<double>(); pi.copy_op = pl->p_op.p; pi.copyT_op = pl->pT_op.p; pi.part = pc; pi.S = S;
-    img_op<T>(pl, IMG_PINIT, pi, st);
-    finalize(pl, FIN_PNORM, ps.bp, pc, 1, nullptr, nullptr, pre, hist, hld, st);
-    // one iteration (a fixed launch sequence: every per-iteration decision is
-    // taken on the device from the scalars)
-    auto iteration = [&](cudaStream_t s) -> int32_t {
-        project<T>(pl, ps, pl->p_op.p, pl->pT_op.p, pl->q.p, pa, S, s);
-        finalize(pl, FIN_CGLS_ALPHA, ps.proj, pa, 1, nullptr, nullptr, pre, hist, hld, s);
-        VecArgs vr{};
-        vr.r = pl->r.as<double>(); vr.q = pl->q.p; vr.r_op = pl->r_op.p; vr.S = S;
-        vec_op<T>(pl, VEC_R_UPDATE, true, vr, s);
+    auto bp_s = [&](cudaStream_t s) {
         BpArgs a = bp_args(BP_CGLS_S, pl->r_op.p, S);
         a.x = pl->x.as<double>(); a.p = pl->p.as<double>(); a.s = pl->s.as<double>();
         a.part = pa;
         if (smooth_fused) { a.z = pl->z.as<double>(); a.copy_op = pl->z_op.p; a.copyT_op = pl->zT_op.p; }
         backproject<T>(pl, ps, a, s);
-        finalize(pl, FIN_CGLS_RES, ps.bp, pa, 1, nullptr, nullptr, pre, hist, hld, s);
+    };
+    // z = B s, beta, p = z + beta p: the end of an iteration, after the
+    // residual test
+    auto step_end = [&](cudaStream_t s) -> int32_t {
         if (pre) {
             int32_t rc = wmg_apply<T>(pl, pl->s.as<double>(), pl->z.as<double>(), smooth_fused, false, true,
                                       &have_sz, s);
@@ -1373,13 +1446,69 @@ static int32_t solve_cgls(wmg_plan *pl, bool pre, const void *b, void *xout, int
         finalize(pl, FIN_PNORM, ps.bp, pc, 1, nullptr, nullptr, pre, hist, hld, s);
         return WMG_OK;
     };
+    if (start == 0) {
+        cudaMemsetAsync(pl->p.p, 0, nN * 8, st);
+        VecArgs va{};
+        va.r = pl->r.as<double>(); va.b_op = b; va.r_op = pl->r_op.p; va.S = S;
+        if (x0) {
+            // x = x0; r = b - alpha W x0 with alpha = 1 (init_scalars), so that
+            // the x update of the backprojection below (x += alpha p, p = 0)
+            // leaves x0 as it is
+            ImgArgs il{};
+            il.in_op = x0; il.z = pl->x.as<double>(); il.copy_op = pl->p_op.p; il.copyT_op = pl->pT_op.p; il.S = S;
+            img_op<T>(pl, IMG_LOAD, il, st);
+            project<T>(pl, ps, pl->p_op.p, pl->pT_op.p, pl->q.p, nullptr, S, st);
+            vec_op<T>(pl, VEC_R_INIT, true, va, st);
+            VecArgs vr{};
+            vr.r = pl->r.as<double>(); vr.q = pl->q.p; vr.r_op = pl->r_op.p; vr.S = S;
+            vec_op<T>(pl, VEC_R_UPDATE, true, vr, st);
+        } else {
+            // r = b, s = W^T r (x = 0, alpha = 0)
+            cudaMemsetAsync(pl->x.p, 0, nN * 8, st);
+            vec_op<T>(pl, VEC_R_INIT, true, va, st);
+        }
+        bp_s(st);
+        if (pre) {
+            int32_t rc = wmg_apply<T>(pl, pl->s.as<double>(), pl->z.as<double>(), smooth_fused, false, true,
+                                      &have_sz, st);
+            if (rc) return rc;
+            if (!have_sz) {
+                ImgArgs ia{};
+                ia.s = pl->s.as<double>(); ia.z = pl->z.as<double>(); ia.part = pb; ia.S = S;
+                img_op<T>(pl, IMG_DOT_SZ, ia, st);
+            }
+        }
+        finalize(pl, FIN_CGLS_INIT, ps.bp, pa, 1, pre ? &ps.bp : nullptr, pre ? pb : nullptr, pre, hist, hld, st);
+        ImgArgs pi{};
+        pi.z = zvec; pi.p = pl->p.as<double>(); pi.copy_op = pl->p_op.p; pi.copyT_op = pl->pT_op.p; pi.part = pc;
+        pi.S = S;
+        img_op<T>(pl, IMG_PINIT, pi, st);
+        finalize(pl, FIN_PNORM, ps.bp, pc, 1, nullptr, nullptr, pre, hist, hld, st);
+    } else {
+        // the problems resumed stopped at the residual test of their last
+        // iteration: finish that iteration
+        int32_t rc = step_end(st);
+        if (rc) return rc;
+    }
+    // one iteration (a fixed launch sequence: every per-iteration decision is
+    // taken on the device from the scalars)
+    auto iteration = [&](cudaStream_t s) -> int32_t {
+        project<T>(pl, ps, pl->p_op.p, pl->pT_op.p, pl->q.p, pa, S, s);
+        finalize(pl, FIN_CGLS_ALPHA, ps.proj, pa, 1, nullptr, nullptr, pre, hist, hld, s);
+        VecArgs vr{};
+        vr.r = pl->r.as<double>(); vr.q = pl->q.p; vr.r_op = pl->r_op.p; vr.S = S;
+        vec_op<T>(pl, VEC_R_UPDATE, true, vr, s);
+        bp_s(s);
+        finalize(pl, FIN_CGLS_RES, ps.bp, pa, 1, nullptr, nullptr, pre, hist, hld, s);
+        return step_end(s);
+    };
     const int chunk = 4;
     Graph graph;
     bool graphed = false;
-    for (int it = 0; it < max_iter; ++it) {
+    for (int it = start; it < max_iter; ++it) {
         // the first iteration runs eagerly (it fills the work-list caches),
         // the others replay its captured graph
-        if (it == 1) graphed = capture(pl, graph, iteration);
+        if (it == start + 1) graphed = capture(pl, graph, iteration);
         int32_t rc = graphed ? replay(graph, st) : iteration(st);
         if (rc) return rc;
         if ((it + 1) % chunk == 0 || it + 1 == max_iter) {
@@ -1396,22 +1525,52 @@ static int32_t solve_cgls(wmg_plan *pl, bool pre, const void *b, void *xout, int
     return WMG_OK;
 }
 
+// SIRT from x0 (NULL: 0), or its continuation after `start` iterations.
 template <class T>
-static int32_t solve_sirt(wmg_plan *pl, const void *b, void *xout, int max_iter, cudaStream_t st)
+static int32_t solve_sirt(wmg_plan *pl, const void *b, const void *x0, void *xout, int max_iter, int start,
+                          cudaStream_t st)
 {
     const int count = pl->cap;
-    const int64_t nN = pl->Ntot, nM = pl->Mtot;
+    const int64_t nN = pl->Ntot;
     const size_t e = pl->esz;
-    if (!ensure_pool(pl->x, nN, 8) || !ensure_pool(pl->p_op, nN, e) || !ensure_pool(pl->pT_op, nN, e) ||
-        !ensure_pool(pl->q, nM, e) || !ensure_pool(pl->r_op, nM, e) || !ensure_pool(pl->s, nN, 8) ||
-        !ensure_partials(pl, 1))
-        return fail(WMG_ERR_OOM, "SIRT pools");
+    int32_t rc0 = solver_pools(pl, WMG_SOLVER_SIRT, false, 0);
+    if (rc0) return rc0;
     const ProbSet &ps = pl->real;
     const double *S = pl->S.as<double>();
-    cudaMemsetAsync(pl->x.p, 0, nN * 8, st);
-    cudaMemsetAsync(pl->p_op.p, 0, nN * e, st);
-    cudaMemsetAsync(pl->pT_op.p, 0, nN * e, st);
-    for (int it = 0; it < max_iter; ++it) {
+    double *pb = pl->part_b.as<double>();
+    // |W^T (b - W x) - lambda x|^2 of the current x, finished by `fin`
+    auto ne_residual = [&](int fin, int slot) {
+        project<T>(pl, ps, pl->p_op.p, pl->pT_op.p, pl->q.p, nullptr, S, st);
+        VecArgs vd{};
+        vd.b_op = b; vd.q = pl->q.p; vd.r_op = pl->r_op.p; vd.S = S;
+        vec_op<T>(pl, VEC_SINO_DIFF, true, vd, st);
+        BpArgs ra = bp_args(BP_ATB, pl->r_op.p, S);
+        ra.out64 = pl->s.as<double>();
+        backproject<T>(pl, ps, ra, st);
+        VecArgs vn{};
+        vn.w = pl->s.as<double>(); vn.x = pl->x.as<double>(); vn.part = pb; vn.S = S;
+        vec_op<T>(pl, VEC_NE_RES, false, vn, st);
+        finalize(pl, fin, ps.vimg, pb, 1, nullptr, nullptr, 0, nullptr, 0, st, slot);
+    };
+    if (start == 0) {
+        // the reference of the relative residual: |W^T b|, or from x0 the
+        // NE residual of x0
+        if (x0) {
+            ImgArgs il{};
+            il.in_op = x0; il.z = pl->x.as<double>(); il.copy_op = pl->p_op.p; il.copyT_op = pl->pT_op.p; il.S = S;
+            img_op<T>(pl, IMG_LOAD, il, st);
+            ne_residual(FIN_STORE, SC_S0);
+        } else {
+            cudaMemsetAsync(pl->x.p, 0, nN * 8, st);
+            cudaMemsetAsync(pl->p_op.p, 0, nN * e, st);
+            cudaMemsetAsync(pl->pT_op.p, 0, nN * e, st);
+            BpArgs fa = bp_args(BP_ATB, b, S);
+            fa.out64 = pl->s.as<double>(); fa.part = pb;
+            backproject<T>(pl, ps, fa, st);
+            finalize(pl, FIN_STORE, ps.bp, pb, 1, nullptr, nullptr, 0, nullptr, 0, st, SC_S0);
+        }
+    }
+    for (int it = start; it < max_iter; ++it) {
         project<T>(pl, ps, pl->p_op.p, pl->pT_op.p, pl->q.p, nullptr, S, st);
         VecArgs va{};
         va.b_op = b; va.q = pl->q.p; va.r_op = pl->r_op.p; va.S = S;
@@ -1420,27 +1579,12 @@ static int32_t solve_sirt(wmg_plan *pl, const void *b, void *xout, int max_iter,
         a.x = pl->x.as<double>(); a.copy_op = pl->p_op.p; a.copyT_op = pl->pT_op.p;
         backproject<T>(pl, ps, a, st);
     }
-    // relative NE residual of the final iterate: |W^T (b - W x) - lambda x| / |W^T b|
-    double *pb = pl->part_b.as<double>();
-    BpArgs fa = bp_args(BP_ATB, b, S);
-    fa.out64 = pl->s.as<double>(); fa.part = pb;
-    backproject<T>(pl, ps, fa, st);
-    finalize(pl, FIN_STORE, ps.bp, pb, 1, nullptr, nullptr, 0, nullptr, 0, st, SC_S0);
-    project<T>(pl, ps, pl->p_op.p, pl->pT_op.p, pl->q.p, nullptr, S, st);
-    VecArgs vd{};
-    vd.b_op = b; vd.q = pl->q.p; vd.r_op = pl->r_op.p; vd.S = S;
-    vec_op<T>(pl, VEC_SINO_DIFF, true, vd, st);
-    BpArgs ra = bp_args(BP_ATB, pl->r_op.p, S);
-    ra.out64 = pl->s.as<double>();
-    backproject<T>(pl, ps, ra, st);
-    VecArgs vn{};
-    vn.w = pl->s.as<double>(); vn.x = pl->x.as<double>(); vn.part = pb; vn.S = S;
-    vec_op<T>(pl, VEC_NE_RES, false, vn, st);
-    finalize(pl, FIN_SET_RES, ps.vimg, pb, 1, nullptr, nullptr, 0, nullptr, 0, st);
+    // relative NE residual of the final iterate: |W^T (b - W x) - lambda x| / S0
+    ne_residual(FIN_SET_RES, 0);
     std::vector<double> Sh((size_t)count * NSCAL);
     WMG_CUDA(cudaMemcpyAsync(Sh.data(), pl->S.p, Sh.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     WMG_CUDA(cudaStreamSynchronize(st));
-    for (int q = 0; q < count; ++q) Sh[(size_t)q * NSCAL + SC_ITERS] = max_iter;
+    for (int q = 0; q < count; ++q) Sh[(size_t)q * NSCAL + SC_ITERS] = std::max(max_iter, start);
     WMG_CUDA(cudaMemcpyAsync(pl->S.p, Sh.data(), Sh.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     ImgArgs io{};
     io.z = pl->x.as<double>(); io.out_op = xout;
@@ -1449,27 +1593,17 @@ static int32_t solve_sirt(wmg_plan *pl, const void *b, void *xout, int max_iter,
     return WMG_OK;
 }
 
+// Restarted GMRES from x0 (NULL: 0), or, with start > 0, the continuation of
+// the solve whose state (at a restart) the plan holds after `start` steps.
 template <class T>
-static int32_t solve_gmres(wmg_plan *pl, bool pre, const void *b, void *xout, int max_iter, int restart,
-                           cudaStream_t st)
+static int32_t solve_gmres(wmg_plan *pl, bool pre, const void *b, const void *x0, void *xout, int max_iter,
+                           int restart, int start, cudaStream_t st)
 {
     const int count = pl->cap;
-    const int64_t nN = pl->Ntot, nM = pl->Mtot;
-    const size_t e = pl->esz;
+    const int64_t nN = pl->Ntot;
     const int ldp = restart + 1;
-    if (!ensure_pool(pl->x, nN, 8) || !ensure_pool(pl->f, nN, 8) || !ensure_pool(pl->w, nN, 8) ||
-        !ensure_pool(pl->t, nN, 8) || !ensure_pool(pl->u, nN, 8) || !ensure_pool(pl->V, nN * ldp, 8) ||
-        !ensure_pool(pl->z_op, nN, e) || !ensure_pool(pl->zT_op, nN, e) || !ensure_pool(pl->sinoS, nM, e) ||
-        !ensure_partials(pl, ldp) || !pl->H.ensure((size_t)count * ldp * restart * 8) ||
-        !pl->gcs.ensure((size_t)count * restart * 8) || !pl->gsn.ensure((size_t)count * restart * 8) ||
-        !pl->gg.ensure((size_t)count * ldp * 8) || !pl->gy.ensure((size_t)count * ldp * 8) ||
-        !pl->h1.ensure((size_t)count * ldp * 8) || !pl->h2.ensure((size_t)count * ldp * 8) ||
-        !pl->jn.ensure((size_t)count * 4) || !pl->done.ensure((size_t)count * 4))
-        return fail(WMG_ERR_OOM, "GMRES pools");
-    if (pre) {
-        int32_t rc = ensure_wmg_pools(pl);
-        if (rc) return rc;
-    }
+    int32_t rc0 = solver_pools(pl, WMG_SOLVER_GMRES, pre, restart);
+    if (rc0) return rc0;
     const ProbSet &ps = pl->real;
     const double *S = pl->S.as<double>();
     double *hist = pl->hist.as<double>();
@@ -1483,21 +1617,40 @@ static int32_t solve_gmres(wmg_plan *pl, bool pre, const void *b, void *xout, in
     ga.sn = pl->gsn.as<double>(); ga.g = pl->gg.as<double>(); ga.y = pl->gy.as<double>();
     ga.h1 = pl->h1.as<double>(); ga.h2 = pl->h2.as<double>(); ga.jn = pl->jn.as<int>();
     ga.done = pl->done.as<int>(); ga.hist = hist; ga.hist_ld = hld;
-    cudaMemsetAsync(pl->x.p, 0, nN * 8, st);
-    cudaMemsetAsync(pl->H.p, 0, (size_t)count * ldp * restart * 8, st);
-    // f = W^T b ; V_0 = f / |f|
-    BpArgs fa = bp_args(BP_ATB, b, S);
-    fa.out64 = pl->f.as<double>(); fa.part = pb;
-    backproject<T>(pl, ps, fa, st);
-    finalize(pl, FIN_STORE, ps.bp, pb, 1, nullptr, nullptr, 0, nullptr, 0, st, SC_WNORM2);
-    ga.init = 1;
-    launch_gm_scalar(2, ga, st);
-    ga.init = 0;
-    launch_gm_setv(ps.d.as<ProbDev>(), ps.vimg.tiles.as<int4>(), ps.vimg.n, V, vstride, ldp, 0,
-                   pl->f.as<double>(), S, st);
     const ProbDev *P = ps.d.as<ProbDev>();
     const int4 *vt = ps.vimg.tiles.as<int4>();
     const int nv = ps.vimg.n;
+    if (start == 0) {
+        cudaMemsetAsync(pl->H.p, 0, (size_t)count * ldp * restart * 8, st);
+        // f = W^T b ; r0 = f - A x0 ; V_0 = r0 / |r0|
+        BpArgs fa = bp_args(BP_ATB, b, S);
+        fa.out64 = pl->f.as<double>(); fa.part = pb;
+        backproject<T>(pl, ps, fa, st);
+        if (x0) {
+            ImgArgs il{};
+            il.in_op = x0; il.z = pl->x.as<double>(); il.copy_op = pl->z_op.p; il.copyT_op = pl->zT_op.p; il.S = S;
+            img_op<T>(pl, IMG_LOAD, il, st);
+            project<T>(pl, ps, pl->z_op.p, pl->zT_op.p, pl->sinoS.p, nullptr, S, st);
+            BpArgs wa = bp_args(BP_GMRES_W, pl->sinoS.p, S);
+            wa.z = pl->x.as<double>(); wa.out64 = pl->w.as<double>();
+            backproject<T>(pl, ps, wa, st);
+            VecArgs rv{};
+            rv.f = pl->f.as<double>(); rv.w = pl->w.as<double>(); rv.v = V; rv.part = pb; rv.S = S;
+            vec_op<T>(pl, VEC_RESID64, false, rv, st);
+            finalize(pl, FIN_STORE, ps.vimg, pb, 1, nullptr, nullptr, 0, nullptr, 0, st, SC_WNORM2);
+        } else {
+            cudaMemsetAsync(pl->x.p, 0, nN * 8, st);
+            finalize(pl, FIN_STORE, ps.bp, pb, 1, nullptr, nullptr, 0, nullptr, 0, st, SC_WNORM2);
+        }
+        ga.init = 1;
+        launch_gm_scalar(2, ga, st);
+        ga.init = 0;
+        launch_gm_setv(P, vt, nv, V, vstride, ldp, 0, x0 ? V : pl->f.as<double>(), S, st);
+    } else {
+        // the problems resumed stopped at the restart test, before their
+        // true residual was scaled into v_0
+        launch_gm_setv(P, vt, nv, V, vstride, ldp, 0, V, S, st);
+    }
     const int *jv = pl->jn.as<int>();
     ga.jslot = 1;
     // One Arnoldi step for every problem at its own column j = jn[slot]
@@ -1567,13 +1720,13 @@ static int32_t solve_gmres(wmg_plan *pl, bool pre, const void *b, void *xout, in
     };
     Graph g_step, g_end;
     bool step_graphed = false, end_graphed = false, step_tried = false, end_tried = false;
-    int done_iters = 0;
+    int done_iters = start;
     while (true) {
         cudaMemsetAsync(pl->done.p, 0, (size_t)count * 4, st);
         int j = 0;
         for (; j < restart && done_iters < max_iter; ++j, ++done_iters) {
             // first step eager (fills the work-list caches), then the graph
-            if (!step_tried && done_iters == 1) {
+            if (!step_tried && done_iters == start + 1) {
                 step_tried = true;
                 step_graphed = capture(pl, g_step, arnoldi);
             }
@@ -1621,20 +1774,12 @@ static int32_t solve_gmres(wmg_plan *pl, bool pre, const void *b, void *xout, in
 // device, so one iteration is a fixed launch sequence (a graph after its first
 // run). Vectors: r = f, rh = w, p = p, v = t, s = u, t = bi_t, ph = z, sh = bi_sh.
 template <class T>
-static int32_t solve_bicgstab(wmg_plan *pl, bool pre, const void *b, void *xout, int max_iter, cudaStream_t st)
+static int32_t solve_bicgstab(wmg_plan *pl, bool pre, const void *b, const void *x0, void *xout, int max_iter,
+                              int start, cudaStream_t st)
 {
-    const int64_t nN = pl->Ntot, nM = pl->Mtot;
-    const size_t e = pl->esz;
-    if (!ensure_pool(pl->x, nN, 8) || !ensure_pool(pl->f, nN, 8) || !ensure_pool(pl->w, nN, 8) ||
-        !ensure_pool(pl->p, nN, 8) || !ensure_pool(pl->t, nN, 8) || !ensure_pool(pl->u, nN, 8) ||
-        !ensure_pool(pl->z, nN, 8) || !ensure_pool(pl->bi_t, nN, 8) || !ensure_pool(pl->bi_sh, nN, 8) ||
-        !ensure_pool(pl->z_op, nN, e) || !ensure_pool(pl->zT_op, nN, e) || !ensure_pool(pl->sinoS, nM, e) ||
-        !ensure_partials(pl, 1))
-        return fail(WMG_ERR_OOM, "BiCGStab pools");
-    if (pre) {
-        int32_t rc = ensure_wmg_pools(pl);
-        if (rc) return rc;
-    }
+    const int64_t nN = pl->Ntot;
+    int32_t rc0 = solver_pools(pl, WMG_SOLVER_BICGSTAB, pre, 0);
+    if (rc0) return rc0;
     const ProbSet &ps = pl->real;
     const ProbDev *P = ps.d.as<ProbDev>();
     const int4 *vt = ps.vimg.tiles.as<int4>();
@@ -1648,13 +1793,30 @@ static int32_t solve_bicgstab(wmg_plan *pl, bool pre, const void *b, void *xout,
     ba.v = pl->t.as<double>(); ba.s = pl->u.as<double>(); ba.t = pl->bi_t.as<double>();
     ba.ph = pl->z.as<double>(); ba.sh = pl->bi_sh.as<double>();
     ba.part_a = pa; ba.part_b = pb; ba.S = S;
-    cudaMemsetAsync(pl->x.p, 0, nN * 8, st);
-    // r0 = W^T b (x0 = 0), rh = r0, p = v = 0
-    BpArgs fa = bp_args(BP_ATB, b, S);
-    fa.out64 = ba.r; fa.part = pb;
-    backproject<T>(pl, ps, fa, st);
-    finalize(pl, FIN_BI_INIT, ps.bp, pb, 1, nullptr, nullptr, 0, hist, hld, st);
-    launch_bicg(BI_INIT, P, vt, nv, ba, st);
+    if (start == 0) {
+        // r0 = W^T b - A x0, rh = r0, p = v = 0
+        BpArgs fa = bp_args(BP_ATB, b, S);
+        fa.out64 = ba.r; fa.part = pb;
+        backproject<T>(pl, ps, fa, st);
+        if (x0) {
+            ImgArgs il{};
+            il.in_op = x0; il.z = ba.x; il.copy_op = pl->z_op.p; il.copyT_op = pl->zT_op.p; il.S = S;
+            img_op<T>(pl, IMG_LOAD, il, st);
+            project<T>(pl, ps, pl->z_op.p, pl->zT_op.p, pl->sinoS.p, nullptr, S, st);
+            BpArgs wa = bp_args(BP_GMRES_W, pl->sinoS.p, S);
+            wa.z = ba.x; wa.out64 = ba.s;
+            backproject<T>(pl, ps, wa, st);
+            VecArgs rv{};
+            rv.f = ba.r; rv.w = ba.s; rv.v = ba.sh; rv.part = pb; rv.S = S;
+            vec_op<T>(pl, VEC_RESID64, false, rv, st);
+            WMG_CUDA(cudaMemcpyAsync(ba.r, ba.sh, nN * 8, cudaMemcpyDeviceToDevice, st));
+            finalize(pl, FIN_BI_INIT, ps.vimg, pb, 1, nullptr, nullptr, 0, hist, hld, st);
+        } else {
+            cudaMemsetAsync(pl->x.p, 0, nN * 8, st);
+            finalize(pl, FIN_BI_INIT, ps.bp, pb, 1, nullptr, nullptr, 0, hist, hld, st);
+        }
+        launch_bicg(BI_INIT, P, vt, nv, ba, st);
+    }
     // z_out = B z_in (FP64) with the operator copies of z_out; then w_out = A z_out
     auto precond_then_A = [&](double *z_in, double *z_out, double *w_out, cudaStream_t s) -> int32_t {
         if (pre) {
@@ -1689,8 +1851,8 @@ static int32_t solve_bicgstab(wmg_plan *pl, bool pre, const void *b, void *xout,
     };
     Graph graph;
     bool graphed = false;
-    for (int it = 0; it < max_iter; ++it) {
-        if (it == 1) graphed = capture(pl, graph, iteration);
+    for (int it = start; it < max_iter; ++it) {
+        if (it == start + 1) graphed = capture(pl, graph, iteration);
         int32_t rc = graphed ? replay(graph, st) : iteration(st);
         if (rc) return rc;
         if ((it + 1) % 4 == 0 || it + 1 == max_iter) {
@@ -1707,13 +1869,13 @@ static int32_t solve_bicgstab(wmg_plan *pl, bool pre, const void *b, void *xout,
 }
 
 template <class T>
-static int32_t do_solve(wmg_plan *pl, int solver, bool pre, const void *b, void *x, int max_iter, int restart,
-                        cudaStream_t st)
+static int32_t do_solve(wmg_plan *pl, int solver, bool pre, const void *b, const void *x0, void *x, int max_iter,
+                        int restart, int start, cudaStream_t st)
 {
-    if (solver == WMG_SOLVER_CGLS) return solve_cgls<T>(pl, pre, b, x, max_iter, st);
-    if (solver == WMG_SOLVER_GMRES) return solve_gmres<T>(pl, pre, b, x, max_iter, restart, st);
-    if (solver == WMG_SOLVER_BICGSTAB) return solve_bicgstab<T>(pl, pre, b, x, max_iter, st);
-    return solve_sirt<T>(pl, b, x, max_iter, st);
+    if (solver == WMG_SOLVER_CGLS) return solve_cgls<T>(pl, pre, b, x0, x, max_iter, start, st);
+    if (solver == WMG_SOLVER_GMRES) return solve_gmres<T>(pl, pre, b, x0, x, max_iter, restart, start, st);
+    if (solver == WMG_SOLVER_BICGSTAB) return solve_bicgstab<T>(pl, pre, b, x0, x, max_iter, start, st);
+    return solve_sirt<T>(pl, b, x0, x, max_iter, start, st);
 }
 
 static int32_t check_solve_args(wmg_plan *pl, int32_t solver, int32_t preconditioned, int32_t max_iter,
@@ -1730,22 +1892,30 @@ static int32_t check_solve_args(wmg_plan *pl, int32_t solver, int32_t preconditi
     return WMG_OK;
 }
 
-static int32_t run_solve(wmg_plan *pl, int32_t solver, int32_t preconditioned, const void *b, void *x,
-                         int32_t max_iter, double rtol, int32_t restart, wmg_solve_info *info, double *res_hist,
-                         cudaStream_t st)
+static int32_t run_solve(wmg_plan *pl, int32_t solver, int32_t preconditioned, const void *b, const void *x0,
+                         void *x, int32_t max_iter, double rtol, int32_t restart, wmg_solve_info *info,
+                         double *res_hist, cudaStream_t st)
 {
+    pl->state.valid = false;
     if (!pl->hist.ensure((size_t)pl->cap * (max_iter + 1) * sizeof(double)))
         return fail(WMG_ERR_OOM, "history");
     cudaMemsetAsync(pl->hist.p, 0, (size_t)pl->cap * (max_iter + 1) * sizeof(double), st);
-    init_scalars(pl, rtol, max_iter, st);
-    int32_t rc = WMG_DISPATCH(pl, do_solve, pl, solver, preconditioned != 0, b, x, max_iter, restart, st);
+    init_scalars(pl, rtol, max_iter, st, x0 != nullptr && solver == WMG_SOLVER_CGLS);
+    int32_t rc = WMG_DISPATCH(pl, do_solve, pl, solver, preconditioned != 0, b, x0, x, max_iter, restart, 0, st);
     if (rc) return rc;
-    return collect(pl, max_iter, info, res_hist, st);
+    rc = collect(pl, max_iter, info, res_hist, st);
+    if (rc >= 0 && !pl->batch) {
+        SolveState &s = pl->state;
+        s.valid = true;
+        s.solver = solver; s.pre = preconditioned != 0; s.restart = solver == WMG_SOLVER_GMRES ? restart : 0;
+        s.count = pl->cap; s.steps = max_iter; s.hist_ld = max_iter + 1;
+    }
+    return rc;
 }
 
-extern "C" int32_t wmg_solve(wmg_plan *pl, int32_t solver, int32_t preconditioned, int32_t count,
-                             const void *b, void *x, int32_t max_iter, double rtol, int32_t restart,
-                             wmg_solve_info *info, double *res_hist, void *stream)
+extern "C" int32_t wmg_solve_x0(wmg_plan *pl, int32_t solver, int32_t preconditioned, int32_t count,
+                                const void *b, const void *x0, void *x, int32_t max_iter, double rtol,
+                                int32_t restart, wmg_solve_info *info, double *res_hist, void *stream)
 {
     if (!pl || !b || !x || count < 1) return fail(WMG_ERR_INVALID_ARG, "wmg_solve: bad arguments");
     int32_t rc = single_geometry(pl, "wmg_solve");
@@ -1753,7 +1923,191 @@ extern "C" int32_t wmg_solve(wmg_plan *pl, int32_t solver, int32_t preconditione
     if ((rc = check_solve_args(pl, solver, preconditioned, max_iter, restart))) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((rc = ensure_count(pl, count, st))) return rc;
-    return run_solve(pl, solver, preconditioned, b, x, max_iter, rtol, restart, info, res_hist, st);
+    return run_solve(pl, solver, preconditioned, b, x0, x, max_iter, rtol, restart, info, res_hist, st);
+}
+
+extern "C" int32_t wmg_solve(wmg_plan *pl, int32_t solver, int32_t preconditioned, int32_t count,
+                             const void *b, void *x, int32_t max_iter, double rtol, int32_t restart,
+                             wmg_solve_info *info, double *res_hist, void *stream)
+{
+    return wmg_solve_x0(pl, solver, preconditioned, count, b, nullptr, x, max_iter, rtol, restart, info,
+                        res_hist, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint / resume: the state of the last solve, copied out and back
+// ---------------------------------------------------------------------------
+namespace {
+struct StateHeader {
+    char magic[8];
+    int32_t version, solver, pre, restart, count, prec, steps, hist_ld, nregions, pad;
+    uint64_t fingerprint;
+    int64_t N, M;
+    int64_t bytes[20];
+};
+constexpr char kStateMagic[8] = {'W', 'M', 'G', 'S', 'T', 'A', 'T', 'E'};
+}  // namespace
+
+static int64_t state_total(wmg_plan *pl)
+{
+    int64_t t = sizeof(StateHeader);
+    for (const Region &r : state_regions(pl)) t += (int64_t)r.bytes;
+    return t;
+}
+
+extern "C" int32_t wmg_state_bytes(wmg_plan *pl, int64_t *bytes)
+{
+    if (!pl || !bytes) return fail(WMG_ERR_INVALID_ARG, "wmg_state_bytes: bad arguments");
+    if (!pl->state.valid) return fail(WMG_ERR_INVALID_ARG, "wmg_state_bytes: the plan holds no solver state");
+    *bytes = state_total(pl);
+    return WMG_OK;
+}
+
+extern "C" int32_t wmg_state_export(wmg_plan *pl, void *host, int64_t bytes, void *stream)
+{
+    if (!pl || !host) return fail(WMG_ERR_INVALID_ARG, "wmg_state_export: bad arguments");
+    if (!pl->state.valid) return fail(WMG_ERR_INVALID_ARG, "wmg_state_export: the plan holds no solver state");
+    const std::vector<Region> regs = state_regions(pl);
+    if (bytes < state_total(pl) || regs.size() > 20)
+        return fail(WMG_ERR_INVALID_ARG, "wmg_state_export: buffer smaller than wmg_state_bytes");
+    const SolveState &s = pl->state;
+    StateHeader h{};
+    std::memcpy(h.magic, kStateMagic, 8);
+    h.version = 1; h.solver = s.solver; h.pre = s.pre; h.restart = s.restart; h.count = s.count;
+    h.prec = pl->prec; h.steps = s.steps; h.hist_ld = s.hist_ld; h.nregions = (int)regs.size();
+    h.fingerprint = pl->fingerprint; h.N = pl->Ntot; h.M = pl->Mtot;
+    for (size_t k = 0; k < regs.size(); ++k) h.bytes[k] = (int64_t)regs[k].bytes;
+    char *out = static_cast<char *>(host);
+    std::memcpy(out, &h, sizeof h);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    size_t off = sizeof h;
+    for (const Region &r : regs) {
+        WMG_CUDA(cudaMemcpyAsync(out + off, r.p, r.bytes, cudaMemcpyDeviceToHost, st));
+        off += r.bytes;
+    }
+    WMG_CUDA(cudaStreamSynchronize(st));
+    return WMG_OK;
+}
+
+extern "C" int32_t wmg_state_import(wmg_plan *pl, const void *host, int64_t bytes, void *stream)
+{
+    if (!pl || !host || bytes < (int64_t)sizeof(StateHeader))
+        return fail(WMG_ERR_INVALID_ARG, "wmg_state_import: bad arguments");
+    int32_t rc = single_geometry(pl, "wmg_state_import");
+    if (rc) return rc;
+    pl->state.valid = false;
+    StateHeader h;
+    std::memcpy(&h, host, sizeof h);
+    if (std::memcmp(h.magic, kStateMagic, 8) != 0 || h.version != 1)
+        return fail(WMG_ERR_INVALID_ARG, "wmg_state_import: not a solver state");
+    if (h.fingerprint != pl->fingerprint || h.prec != pl->prec)
+        return fail(WMG_ERR_INVALID_ARG, "wmg_state_import: the state belongs to another geometry or options");
+    if (h.count < 1 || h.steps < 0 || h.hist_ld != h.steps + 1 || h.nregions < 1 || h.nregions > 20)
+        return fail(WMG_ERR_INVALID_ARG, "wmg_state_import: corrupt header");
+    if ((rc = check_solve_args(pl, h.solver, h.pre, h.steps, h.solver == WMG_SOLVER_GMRES ? h.restart : 1)))
+        return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((rc = ensure_count(pl, h.count, st))) return rc;
+    if (h.N != pl->Ntot || h.M != pl->Mtot)
+        return fail(WMG_ERR_INVALID_ARG, "wmg_state_import: problem sizes differ");
+    if ((rc = solver_pools(pl, h.solver, h.pre != 0, h.restart))) return rc;
+    if (!pl->hist.ensure((size_t)h.count * h.hist_ld * sizeof(double))) return fail(WMG_ERR_OOM, "history");
+    SolveState s;
+    s.solver = h.solver; s.pre = h.pre != 0; s.restart = h.restart; s.count = h.count;
+    s.steps = h.steps; s.hist_ld = h.hist_ld;
+    pl->state = s;
+    const std::vector<Region> regs = state_regions(pl);
+    int64_t need = sizeof h;
+    bool same = (int)regs.size() == h.nregions;
+    for (size_t k = 0; same && k < regs.size(); ++k) {
+        same = h.bytes[k] == (int64_t)regs[k].bytes;
+        need += h.bytes[k];
+    }
+    if (!same || bytes < need) {
+        pl->state.valid = false;
+        return fail(WMG_ERR_INVALID_ARG, "wmg_state_import: sizes do not match the plan");
+    }
+    const char *in = static_cast<const char *>(host);
+    size_t off = sizeof h;
+    for (const Region &r : regs) {
+        WMG_CUDA(cudaMemcpyAsync(r.p, in + off, r.bytes, cudaMemcpyHostToDevice, st));
+        off += r.bytes;
+    }
+    WMG_CUDA(cudaStreamSynchronize(st));
+    pl->state.valid = true;
+    return WMG_OK;
+}
+
+template <class T>
+static int32_t store_x(wmg_plan *pl, void *x, cudaStream_t st)
+{
+    ImgArgs io{};
+    io.z = pl->x.as<double>(); io.out_op = x;
+    img_op<T>(pl, IMG_STORE_OUT, io, st);
+    WMG_CUDA(cudaGetLastError());
+    return WMG_OK;
+}
+
+extern "C" int32_t wmg_solve_resume(wmg_plan *pl, const void *b, void *x, int32_t max_iter, double rtol,
+                                    wmg_solve_info *info, double *res_hist, void *stream)
+{
+    if (!pl || !b || !x || max_iter < 0) return fail(WMG_ERR_INVALID_ARG, "wmg_solve_resume: bad arguments");
+    if (!pl->state.valid) return fail(WMG_ERR_INVALID_ARG, "wmg_solve_resume: the plan holds no solver state");
+    const SolveState s0 = pl->state;
+    if (max_iter < s0.steps)
+        return fail(WMG_ERR_INVALID_ARG, "wmg_solve_resume: max_iter is below the iterations already done");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int count = pl->cap;
+    // histories: the entries so far, in rows of the new length
+    const int new_ld = max_iter + 1;
+    {
+        std::vector<double> H0((size_t)count * s0.hist_ld), H1((size_t)count * new_ld, 0.0);
+        WMG_CUDA(cudaMemcpyAsync(H0.data(), pl->hist.p, H0.size() * 8, cudaMemcpyDeviceToHost, st));
+        WMG_CUDA(cudaStreamSynchronize(st));
+        for (int q = 0; q < count; ++q)
+            std::memcpy(&H1[(size_t)q * new_ld], &H0[(size_t)q * s0.hist_ld], (size_t)s0.hist_ld * 8);
+        if (!pl->hist.ensure(H1.size() * 8)) {
+            pl->state.valid = false;
+            return fail(WMG_ERR_OOM, "history");
+        }
+        WMG_CUDA(cudaMemcpyAsync(pl->hist.p, H1.data(), H1.size() * 8, cudaMemcpyHostToDevice, st));
+    }
+    pl->state.hist_ld = new_ld;
+    int32_t rc;
+    if (max_iter > s0.steps) {
+        // problems that stopped at the old iteration cap run on (SIRT: every
+        // problem, it runs a fixed count); converged or failed ones stay
+        std::vector<double> S((size_t)count * NSCAL);
+        WMG_CUDA(cudaMemcpyAsync(S.data(), pl->S.p, S.size() * 8, cudaMemcpyDeviceToHost, st));
+        WMG_CUDA(cudaStreamSynchronize(st));
+        for (int q = 0; q < count; ++q) {
+            double *v = &S[(size_t)q * NSCAL];
+            const int status = (int)v[SC_STATUS];
+            bool run = status == WMG_NOT_CONVERGED;
+            if (s0.solver == WMG_SOLVER_SIRT) run = status != WMG_ERR_NAN;
+            if (run && s0.solver == WMG_SOLVER_BICGSTAB && v[SC_GNEW] != 0.0) {
+                v[SC_STATUS] = WMG_ERR_BREAKDOWN;     // the capped step had broken down
+                run = false;
+            }
+            if (run) { v[SC_ACTIVE] = 1.0; v[SC_STATUS] = WMG_NOT_CONVERGED; }
+            v[SC_RTOL] = rtol;
+            v[SC_MAXIT] = max_iter;
+        }
+        WMG_CUDA(cudaMemcpyAsync(pl->S.p, S.data(), S.size() * 8, cudaMemcpyHostToDevice, st));
+        pl->state.valid = false;
+        rc = WMG_DISPATCH(pl, do_solve, pl, s0.solver, s0.pre != 0, b, nullptr, x, max_iter, s0.restart,
+                          s0.steps, st);
+        if (rc) return rc;
+        pl->state = s0;
+        pl->state.steps = max_iter;
+        pl->state.hist_ld = new_ld;
+    } else {
+        rc = WMG_DISPATCH(pl, store_x, pl, x, st);
+        if (rc) return rc;
+    }
+    rc = collect(pl, max_iter, info, res_hist, st);
+    if (rc < 0) pl->state.valid = false;
+    return rc;
 }
 
 // ---------------------------------------------------------------------------
@@ -1883,7 +2237,8 @@ extern "C" int32_t wmg_batch_solve(wmg_batch *batch, int32_t solver, int32_t pre
     rc = pl->prec == WMG_PREC_F64 ? gather_scatter<double>(pl, b, nullptr, true, pl->b_op.p, false, st)
                                   : gather_scatter<float>(pl, b, nullptr, true, pl->b_op.p, false, st);
     if (rc) return rc;
-    rc = run_solve(pl, solver, preconditioned, pl->b_op.p, pl->x_io.p, max_iter, rtol, restart, info, res_hist, st);
+    rc = run_solve(pl, solver, preconditioned, pl->b_op.p, nullptr, pl->x_io.p, max_iter, rtol, restart, info, res_hist,
+                   st);
     if (rc < 0) return rc;
     const int32_t rc2 = pl->prec == WMG_PREC_F64 ? gather_scatter<double>(pl, nullptr, x, false, pl->x_io.p, true, st)
                                                  : gather_scatter<float>(pl, nullptr, x, false, pl->x_io.p, true, st);

@@ -133,6 +133,18 @@ struct Geo {
 // CUDA graphs for the solver iterations unless WMG_GRAPHS=0 in the environment.
 bool graphs_default();
 
+// What the last solve on a single-geometry plan left in the plan's pools:
+// enough to continue it (wmg_solve_resume) or to copy it out and back
+// (wmg_state_export / wmg_state_import). Any call that reuses those pools
+// (a solve, a projection, a preconditioner application, a change of the
+// problem count) clears `valid`.
+struct SolveState {
+    bool valid = false;
+    int solver = 0, pre = 0, restart = 0, count = 0;
+    int steps = 0;        // iterations the solve's loop ran (the same for every problem)
+    int hist_ld = 1;      // row length of the residual histories in the hist pool
+};
+
 }  // namespace wmg
 
 // ---------------------------------------------------------------------------
@@ -179,6 +191,8 @@ struct wmg_plan {
     cudaStream_t cap_stream = nullptr;
     bool use_graphs = wmg::graphs_default();
     int tuned_pj = 8, tuned_bp = 8;     // last autotune result (CTAs per SM)
+    wmg::SolveState state;              // continuation point of the last solve
+    uint64_t fingerprint = 0;           // geometry and options (single-geometry plans)
     ~wmg_plan()
     {
         if (cap_stream) cudaStreamDestroy(cap_stream);

@@ -430,7 +430,17 @@ k_finalize(FinArgs f)
             const double omega = S[SC_DELTA];
             if (!isfinite(rel)) stop(WMG_ERR_NAN);
             else if (rel < S[SC_RTOL] || rel == 0.0) stop(WMG_OK);
-            else if (it >= (int)S[SC_MAXIT]) stop(WMG_NOT_CONVERGED);
+            else if (it >= (int)S[SC_MAXIT]) {
+                stop(WMG_NOT_CONVERGED);
+                // what a resumed solve needs for its next step: beta and rho,
+                // or the mark that this step broke down (SC_GNEW = 1)
+                const bool broke = omega == 0.0 || sb == 0.0;
+                S[SC_GNEW] = broke ? 1.0 : 0.0;
+                if (!broke) {
+                    S[SC_BETA] = (sb / S[SC_GAMMA]) * (S[SC_ALPHA] / omega);
+                    S[SC_GAMMA] = sb;
+                }
+            }
             else if (omega == 0.0 || sb == 0.0) stop(WMG_ERR_BREAKDOWN);
             else {
                 S[SC_BETA] = (sb / S[SC_GAMMA]) * (S[SC_ALPHA] / omega);
@@ -439,7 +449,7 @@ k_finalize(FinArgs f)
             break;
         }
         case FIN_SET_RES: {              // sa = |NE residual|^2 of the final iterate
-            const double s0 = S[SC_S0];
+            const double s0 = sqrt(S[SC_S0]);        // FIN_STORE left the squared norm there
             // W^T b = 0 (e.g. b = 0): x = 0 is exact when the residual is 0
             const double rel = s0 > 0.0 ? sqrt(sa) / s0 : (sa == 0.0 ? 0.0 : INFINITY);
             S[SC_RES] = rel;

@@ -1,25 +1,35 @@
 """Semi-convergence of the iterative solvers on noisy data (Section 4.2):
 the error of the k-th iterate against the exact object, e_k = x_k - x_ex,
-with x_0 = 0 so that ||e_0|| = ||x_ex||. Every iterate comes from a solve
-of exactly k iterations (rtol 0) through the library's own solvers, which
-are deterministic, so x_k is the k-th iterate of one long run."""
+with x_0 = 0 so that ||e_0|| = ||x_ex||. Every iterate is that of a solve of
+exactly k iterations (rtol 0) through the library's own solvers: the run is
+continued from one k to the next (wmg_solve_resume), which gives bitwise the
+iterate of a fresh k-iteration solve, so the whole curve costs one run to
+the largest k."""
 from __future__ import annotations
 
-from . import Plan
+from . import SOLVER_GMRES, Plan
 
 
 def error_curve(plan: Plan, b, x_true, solver: int, preconditioned: bool, ks, restart: int = 20):
     """For each k in ks: (k, iterations done, ||e_k||_2 / ||e_0||_2,
     ||e_k||_inf / ||e_0||_inf) for one problem of `plan` (b and x_true CUDA
     tensors of sizes M and N). A solve that ends early (breakdown) reports
-    the iterations it did."""
+    the iterations it did. GMRES continues a run only from a k that is a
+    multiple of the restart length (a restart of the fresh solve) and solves
+    afresh otherwise."""
     xt = x_true.double()
     n2, ninf = float(xt.norm()), float(xt.abs().max())
     out = []
-    for k in ks:
-        x, info, _, _ = plan.solve(b, solver, preconditioned, int(k), 0.0, restart)
+    prev = None
+    for k in (int(k) for k in ks):
+        resumable = prev is not None and prev <= k and (solver != SOLVER_GMRES or prev % restart == 0)
+        if resumable:
+            x, info, _, _ = plan.resume(b, k, 0.0)
+        else:
+            x, info, _, _ = plan.solve(b, solver, preconditioned, k, 0.0, restart)
+        prev = k
         e = x.double() - xt
-        out.append((int(k), int(info[0][0]), float(e.norm()) / n2, float(e.abs().max()) / ninf))
+        out.append((k, int(info[0][0]), float(e.norm()) / n2, float(e.abs().max()) / ninf))
     return out
 
 

@@ -82,6 +82,32 @@ extern "C" {
 #define WMG_SOLVER_BICGSTAB 3 /* BiCGStab, right preconditioning: the solver of
                                  the paper's experiments (Section 4) */
 
+/* ---- workspace allocator ---------------------------------------------------
+ * By default plans, batches and servers take their device workspace with
+ * cudaMalloc (a server's geometry setups with stream-ordered
+ * cudaMallocAsync on their own stream). wmg_set_allocator sends every later
+ * workspace allocation of the process to the caller's functions instead,
+ * e.g. a framework's caching allocator, so that the library's memory is
+ * counted and reused there:
+ *   alloc(bytes, stream, ctx) returns device memory of at least `bytes`
+ *     bytes on the current device, aligned to 256 bytes, or NULL (the call
+ *     that needed it fails with WMG_ERR_OOM);
+ *   free(ptr, bytes, stream, ctx) takes it back.
+ * stream: the stream the memory is allocated for; NULL when that is the
+ * stream of the library call in progress (which the allocator is not told:
+ * a binding that passes its framework's current stream to every call can
+ * take that one), a server's setup stream otherwise. Each buffer goes back to the functions that allocated
+ * it, so the allocator may change while plans exist; ctx must stay valid
+ * until all of its buffers are freed. Plans free their buffers in
+ * wmg_plan_destroy (and batches, servers and stored matrices in their
+ * destroy calls) or when a pool grows. Both functions may be called from a
+ * server's setup thread. Short-lived setup temporaries (the leaf Galerkin
+ * assembly's chunk buffers, one counter) still use cudaMallocAsync.
+ * alloc = NULL restores cudaMalloc. */
+typedef void *(*wmg_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*wmg_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+int32_t wmg_set_allocator(wmg_alloc_fn alloc, wmg_free_fn free, void *ctx);
+
 /* ---- parameter blocks ----------------------------------------------------- */
 typedef struct wmg_geom {
     int32_t n;              /* image side in pixels, >= 1 */

@@ -23,6 +23,8 @@ LIB_PATH = _build.LIB
 
 WMG_OK = 0
 WMG_NOT_CONVERGED = 1
+(WMG_ERR_INVALID_ARG, WMG_ERR_OOM, WMG_ERR_CUDA, WMG_ERR_LEAF_NOT_SPD, WMG_ERR_BREAKDOWN, WMG_ERR_TIMEOUT,
+ WMG_ERR_NAN, WMG_ERR_REJECTED) = range(-1, -9, -1)
 STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA_ERROR",
                 -4: "LEAF_NOT_SPD", -5: "BREAKDOWN", -6: "TIMEOUT", -7: "NAN", -8: "REJECTED"}
 
@@ -100,6 +102,7 @@ _SIGNATURES = {
     "wmg_state_export": (_i32, [_vp, _vp, _i64, _vp]),
     "wmg_state_import": (_i32, [_vp, _vp, _i64, _vp]),
     "wmg_solve_resume": (_i32, [_vp, _vp, _vp, _i32, _dbl, C.POINTER(wmg_solve_info), C.POINTER(_dbl), _vp]),
+    "wmg_set_allocator": (_i32, [_vp, _vp, _vp]),
     "wmg_plan_nnz": (_i32, [_vp, C.POINTER(_i64)]),
     "wmg_launch_count": (_i64, [_i32]),
     "wmg_plan_get_tuning": (_i32, [_vp, C.POINTER(_i32), C.POINTER(_i32)]),
@@ -235,6 +238,49 @@ def wmg_state_import(plan, host, nbytes, stream=None) -> None:
 def wmg_solve_resume(plan, b, x, max_iter, rtol, info, res_hist, stream=None) -> int:
     return _check(lib().wmg_solve_resume(plan, b, x, max_iter, rtol, info, res_hist, stream),
                   allow_not_converged=True)
+
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_allocator_refs = None
+
+
+def wmg_set_allocator(alloc, free, ctx=None) -> None:
+    """alloc / free: ctypes callbacks of wmg_alloc_fn / wmg_free_fn (or None
+    to restore cudaMalloc)."""
+    _check(lib().wmg_set_allocator(C.cast(alloc, _vp) if alloc else None,
+                                   C.cast(free, _vp) if free else None, ctx))
+
+
+def _torch_alloc(nbytes, stream, ctx):
+    try:
+        import torch
+        s = stream if stream else torch.cuda.current_stream().cuda_stream
+        return torch.cuda.caching_allocator_alloc(int(nbytes), stream=s)
+    except Exception:                      # reported to the library as out of memory
+        return None
+
+
+def _torch_free(ptr, nbytes, stream, ctx):
+    import torch
+    torch.cuda.caching_allocator_delete(ptr)
+
+
+def use_torch_allocator(enable: bool = True) -> None:
+    """Routes the library's later workspace allocations through torch's
+    caching allocator (wmg_set_allocator): plans, batches and servers then
+    hold torch memory, counted by torch.cuda.memory_allocated and reused
+    from its cache. enable=False restores cudaMalloc for later allocations
+    (buffers already taken go back to torch when freed)."""
+    global _allocator_refs
+    if enable:
+        refs = (_ALLOC_FN(_torch_alloc), _FREE_FN(_torch_free))
+        wmg_set_allocator(refs[0], refs[1])
+        # the callbacks stay referenced for the life of the process: buffers
+        # taken through them are returned through them
+        _allocator_refs = (_allocator_refs or ()) + (refs,)
+    else:
+        wmg_set_allocator(None, None)
 
 
 def wmg_project_noalloc(n, m, D, x, b, stream=None):

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -28,6 +29,15 @@ int32_t fail(int32_t code, const std::string &msg)
 }
 
 thread_local cudaStream_t g_alloc_stream = nullptr;
+
+static std::mutex g_allocator_mu;
+static Allocator g_allocator;
+
+Allocator current_allocator()
+{
+    std::lock_guard<std::mutex> lk(g_allocator_mu);
+    return g_allocator;
+}
 
 bool graphs_default()
 {
@@ -941,6 +951,14 @@ extern "C" int32_t wmg_last_error(char *buf, size_t len)
 }
 
 extern "C" int32_t wmg_version(void) { return 100; }
+
+extern "C" int32_t wmg_set_allocator(wmg_alloc_fn alloc, wmg_free_fn free, void *ctx)
+{
+    if (alloc && !free) return fail(WMG_ERR_INVALID_ARG, "wmg_set_allocator: an allocator needs its free function");
+    std::lock_guard<std::mutex> lk(g_allocator_mu);
+    g_allocator = alloc ? Allocator{alloc, free, ctx} : Allocator{};
+    return WMG_OK;
+}
 
 // FNV-1a over everything that shapes a plan's arithmetic: the geometry
 // (with every angle) and the WMG and solver options. A solver state is

@@ -25,11 +25,21 @@ int num_sms();
 // a temporary does not synchronise the device.
 extern thread_local cudaStream_t g_alloc_stream;
 
+// The caller's workspace allocator (wmg_set_allocator), or none (cudaMalloc).
+struct Allocator {
+    wmg_alloc_fn alloc = nullptr;
+    wmg_free_fn free = nullptr;
+    void *ctx = nullptr;
+};
+Allocator current_allocator();
+
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
     bool persistent = false;       // outlives the thread's allocation stream
     cudaStream_t ast = nullptr;    // stream of a stream-ordered allocation
+    Allocator owner;               // the caller's allocator that made p, if any
+    void *owner_stream = nullptr;
     DevBuf() = default;
     explicit DevBuf(bool persist) : persistent(persist) {}
     DevBuf(const DevBuf &) = delete;
@@ -38,12 +48,15 @@ struct DevBuf {
     void release()
     {
         if (p) {
-            if (ast) cudaFreeAsync(p, ast);
+            if (owner.free) owner.free(p, bytes, owner_stream, owner.ctx);
+            else if (ast) cudaFreeAsync(p, ast);
             else cudaFree(p);
         }
         p = nullptr;
         bytes = 0;
         ast = nullptr;
+        owner = Allocator{};
+        owner_stream = nullptr;
     }
     // grow-only; contents are not preserved
     bool ensure(size_t b)
@@ -51,6 +64,23 @@ struct DevBuf {
         if (b <= bytes && p) return true;
         release();
         if (b == 0) b = 16;
+        const Allocator a = current_allocator();
+        if (a.alloc) {
+            // the caller's allocator: returned to the same functions; the
+            // kernels and tensor maps want 256-byte aligned bases
+            void *st = !persistent && g_alloc_stream ? static_cast<void *>(g_alloc_stream) : nullptr;
+            void *q = a.alloc(b, st, a.ctx);
+            if (!q) return false;
+            if (reinterpret_cast<uintptr_t>(q) % 256 != 0) {
+                a.free(q, b, st, a.ctx);
+                return false;
+            }
+            p = q;
+            bytes = b;
+            owner = a;
+            owner_stream = st;
+            return true;
+        }
         cudaError_t e;
         if (!persistent && g_alloc_stream) {
             e = cudaMallocAsync(&p, b, g_alloc_stream);

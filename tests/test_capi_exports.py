@@ -45,3 +45,15 @@ def test_invalid_arguments_are_rejected_without_gpu_work():
     opts = wmg.wmg_opts(1, 0, 0, 1.0, -1.0, 0, 0, 0)                                 # lambda < 0
     rc = wmg.lib().wmg_plan_create(ctypes.byref(geom), ctypes.byref(opts), None, ctypes.byref(out))
     assert rc == -1
+
+
+def test_allocator_arguments_are_checked_without_gpu_work():
+    # wmg_set_allocator only records the functions: no CUDA call
+    alloc = wmg._ALLOC_FN(lambda nbytes, stream, ctx: None)
+    try:
+        wmg.wmg_set_allocator(alloc, None)
+        raise AssertionError("an allocator without its free function was accepted")
+    except wmg.WmgError as e:
+        assert e.code == wmg.WMG_ERR_INVALID_ARG
+    wmg.wmg_set_allocator(None, None)
+    assert wmg.WMG_ERR_OOM == -2 and wmg.WMG_ERR_REJECTED == -8

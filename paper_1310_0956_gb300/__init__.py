@@ -435,7 +435,10 @@ class Plan:
         self.N, self.M = n * n, m * D
         self.K = 4 ** (levels - 1) if levels >= 1 else 0
         self.P = (n >> (levels - 1)) ** 2 if levels >= 1 else 0
+        import time
+        t0 = time.perf_counter()
         self.handle = wmg_plan_create(self.geom, self.opts, self._stream())
+        self.setup_s = time.perf_counter() - t0          # plan creation (geometry and leaf setup) is synchronising
 
     def _stream(self):
         return C.c_void_p(self._torch.cuda.current_stream().cuda_stream)

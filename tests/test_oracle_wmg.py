@@ -142,3 +142,19 @@ def test_hybrid_cycle_is_not_symmetric():
     op = oracle.Op(*GEOM)
     B = dense_B(oracle.Wmg(op, 3, 0, 0, 1.0, 0.0, oracle.CYCLE_HYBRID, 2), op.N)
     assert np.abs(B - B.T).max() > 1e-6 * np.abs(B).max()
+
+
+def test_leaf_without_rays_is_not_spd_unless_regularised():
+    # one angle (vertical rays) and a 4-bin detector: the rays cover the
+    # central 4 pixel columns only, so the leaf Galerkin matrices
+    # Q_k^T W^T W Q_k have exactly zero rows for the 2x2 blocks off that band
+    # and Cholesky meets a zero pivot; lambda I (eq. sys_reg) makes every
+    # leaf SPD
+    op = oracle.Op(16, 1, 4)
+    assert oracle.Wmg(op, 2).status == -4
+    assert oracle.Wmg(op, 2, lam=0.1).status == 0
+    bare = oracle.Wmg(op, 2, factor=False)
+    assert any((np.abs(bare.leaf(k)).sum(axis=1) == 0).any() for k in range(bare.K))
+    reg = oracle.Wmg(op, 2, lam=0.1, factor=False)
+    for k in range(reg.K):
+        assert np.linalg.eigvalsh(reg.leaf(k)).min() >= 0.1 * (1 - 1e-12)

@@ -262,8 +262,9 @@ int32_t wmg_state_import(wmg_plan *plan, const void *host, int64_t bytes, void *
 /* Continues the plan's state to max_iter iterations IN TOTAL (the state's
  * iterations included; max_iter below them is WMG_ERR_INVALID_ARG), with
  * the same solver, preconditioning, restart length and problem count, and
- * a new rtol. b: the same right-hand side (count sinograms, device). x
- * receives the iterates (count images). Problems that stopped at the old
+ * a new rtol. count: the state's problem count (checked: b and x are read
+ * and written for that many problems). b: the same right-hand side (count
+ * sinograms, device). x receives the iterates (count images). Problems that stopped at the old
  * iteration cap run on; converged or failed ones keep their result (SIRT
  * runs every problem to max_iter, as its fixed count). info, res_hist and
  * the return value as wmg_solve over all max_iter iterations. The kernels'
@@ -271,7 +272,7 @@ int32_t wmg_state_import(wmg_plan *plan, const void *host, int64_t bytes, void *
  * uninterrupted solve with this max_iter; for GMRES when the checkpoint is
  * at a restart of that solve (its iteration count a multiple of restart),
  * else the continuation restarts at the checkpoint. Synchronising. */
-int32_t wmg_solve_resume(wmg_plan *plan, const void *b, void *x, int32_t max_iter, double rtol,
+int32_t wmg_solve_resume(wmg_plan *plan, int32_t count, const void *b, void *x, int32_t max_iter, double rtol,
                          wmg_solve_info *info, double *res_hist, void *stream);
 
 /* ---- batches of problems of different geometries ------------------------- */

@@ -101,7 +101,8 @@ _SIGNATURES = {
     "wmg_state_bytes": (_i32, [_vp, C.POINTER(_i64)]),
     "wmg_state_export": (_i32, [_vp, _vp, _i64, _vp]),
     "wmg_state_import": (_i32, [_vp, _vp, _i64, _vp]),
-    "wmg_solve_resume": (_i32, [_vp, _vp, _vp, _i32, _dbl, C.POINTER(wmg_solve_info), C.POINTER(_dbl), _vp]),
+    "wmg_solve_resume": (_i32, [_vp, _i32, _vp, _vp, _i32, _dbl, C.POINTER(wmg_solve_info), C.POINTER(_dbl),
+                                _vp]),
     "wmg_set_allocator": (_i32, [_vp, _vp, _vp]),
     "wmg_plan_nnz": (_i32, [_vp, C.POINTER(_i64)]),
     "wmg_launch_count": (_i64, [_i32]),
@@ -235,8 +236,8 @@ def wmg_state_import(plan, host, nbytes, stream=None) -> None:
     _check(lib().wmg_state_import(plan, host, nbytes, stream))
 
 
-def wmg_solve_resume(plan, b, x, max_iter, rtol, info, res_hist, stream=None) -> int:
-    return _check(lib().wmg_solve_resume(plan, b, x, max_iter, rtol, info, res_hist, stream),
+def wmg_solve_resume(plan, count, b, x, max_iter, rtol, info, res_hist, stream=None) -> int:
+    return _check(lib().wmg_solve_resume(plan, count, b, x, max_iter, rtol, info, res_hist, stream),
                   allow_not_converged=True)
 
 
@@ -451,6 +452,13 @@ class Plan:
             raise ValueError("tensor size is not a multiple of the problem size")
         return C.c_void_p(t.data_ptr()), t.numel() // size
 
+    def _out(self, out, size, cnt):
+        """Pointer of a caller-given output holding exactly `cnt` problems."""
+        p, c = self._arg(out, size)
+        if c != cnt:
+            raise ValueError(f"out holds {c} problems, the input {cnt}")
+        return p
+
     def close(self):
         if getattr(self, "handle", None):
             wmg_plan_destroy(self.handle)
@@ -465,31 +473,31 @@ class Plan:
     def project(self, x, out=None):
         xp, cnt = self._arg(x, self.N)
         out = out if out is not None else self._torch.empty(cnt * self.M, dtype=self.dtype, device=x.device)
-        wmg_project(self.handle, cnt, xp, self._arg(out, self.M)[0], self._stream())
+        wmg_project(self.handle, cnt, xp, self._out(out, self.M, cnt), self._stream())
         return out
 
     def backproject(self, b, out=None):
         bp, cnt = self._arg(b, self.M)
         out = out if out is not None else self._torch.empty(cnt * self.N, dtype=self.dtype, device=b.device)
-        wmg_backproject(self.handle, cnt, bp, self._arg(out, self.N)[0], self._stream())
+        wmg_backproject(self.handle, cnt, bp, self._out(out, self.N, cnt), self._stream())
         return out
 
     def precond(self, s, out=None):
         sp, cnt = self._arg(s, self.N)
         out = out if out is not None else self._torch.empty_like(s)
-        wmg_precond_apply(self.handle, cnt, sp, self._arg(out, self.N)[0], self._stream())
+        wmg_precond_apply(self.handle, cnt, sp, self._out(out, self.N, cnt), self._stream())
         return out
 
     def haar_analysis(self, x, out=None):
         xp, cnt = self._arg(x, self.N)
         out = out if out is not None else self._torch.empty_like(x)
-        wmg_haar_analysis(self.handle, cnt, xp, self._arg(out, self.N)[0], self._stream())
+        wmg_haar_analysis(self.handle, cnt, xp, self._out(out, self.N, cnt), self._stream())
         return out
 
     def haar_synthesis(self, c, out=None):
         cp, cnt = self._arg(c, self.N)
         out = out if out is not None else self._torch.empty_like(c)
-        wmg_haar_synthesis(self.handle, cnt, cp, self._arg(out, self.N)[0], self._stream())
+        wmg_haar_synthesis(self.handle, cnt, cp, self._out(out, self.N, cnt), self._stream())
         return out
 
     def leaf_inverse(self, k):
@@ -538,7 +546,7 @@ class Plan:
         out = out if out is not None else self._torch.empty(cnt * self.N, dtype=self.dtype, device=b.device)
         info = (wmg_solve_info * cnt)()
         hist = (C.c_double * (cnt * (max_iter + 1)))() if history else None
-        xp = self._arg(out, self.N)[0]
+        xp = self._out(out, self.N, cnt)
         if x0 is None:
             rc = wmg_solve(self.handle, solver, 1 if preconditioned else 0, cnt, bp, xp, max_iter, rtol, restart,
                            info, hist, self._stream())
@@ -579,8 +587,8 @@ class Plan:
         out = out if out is not None else self._torch.empty(cnt * self.N, dtype=self.dtype, device=b.device)
         info = (wmg_solve_info * cnt)()
         hist = (C.c_double * (cnt * (max_iter + 1)))() if history else None
-        rc = wmg_solve_resume(self.handle, bp, self._arg(out, self.N)[0], max_iter, rtol, info, hist,
-                              self._stream())
+        xp = self._out(out, self.N, cnt)
+        rc = wmg_solve_resume(self.handle, cnt, bp, xp, max_iter, rtol, info, hist, self._stream())
         return (out,) + self._results(cnt, max_iter, info, hist) + (rc,)
 
 
@@ -596,7 +604,7 @@ class StoredOperator:
     def apply(self, x, out=None):
         xp, cnt = self._plan._arg(x, self.cols)
         out = out if out is not None else self._plan._torch.empty(cnt * self.rows, dtype=x.dtype, device=x.device)
-        wmg_csr_apply(self.handle, cnt, xp, self._plan._arg(out, self.rows)[0], self._plan._stream())
+        wmg_csr_apply(self.handle, cnt, xp, self._plan._out(out, self.rows, cnt), self._plan._stream())
         return out
 
     def close(self):
@@ -654,9 +662,13 @@ class Batch:
         torch = self._torch
         if outs is None:
             outs = [torch.empty(N, dtype=self.dtype, device="cuda") for N, _ in self.sizes]
-        for t, (N, M) in zip(bs, self.sizes):
+        if len(bs) != self.count or len(outs) != self.count:
+            raise ValueError(f"the batch has {self.count} problems: give as many sinograms and outputs")
+        for t, o, (N, M) in zip(bs, outs, self.sizes):
             if t.dtype != self.dtype or t.numel() != M or not t.is_cuda or not t.is_contiguous():
                 raise TypeError("sinogram tensors must match the batch's sizes and dtype")
+            if o.dtype != self.dtype or o.numel() != N or not o.is_cuda or not o.is_contiguous():
+                raise TypeError("output tensors must match the batch's sizes and dtype")
         info = (wmg_solve_info * self.count)()
         rc = wmg_batch_solve(self.handle, solver, 1 if preconditioned else 0, [t.data_ptr() for t in bs],
                              [t.data_ptr() for t in outs], max_iter, rtol, restart, info, None,

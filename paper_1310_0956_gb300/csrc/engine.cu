@@ -2066,16 +2066,17 @@ static int32_t store_x(wmg_plan *pl, void *x, cudaStream_t st)
     return WMG_OK;
 }
 
-extern "C" int32_t wmg_solve_resume(wmg_plan *pl, const void *b, void *x, int32_t max_iter, double rtol,
-                                    wmg_solve_info *info, double *res_hist, void *stream)
+extern "C" int32_t wmg_solve_resume(wmg_plan *pl, int32_t count, const void *b, void *x, int32_t max_iter,
+                                    double rtol, wmg_solve_info *info, double *res_hist, void *stream)
 {
     if (!pl || !b || !x || max_iter < 0) return fail(WMG_ERR_INVALID_ARG, "wmg_solve_resume: bad arguments");
     if (!pl->state.valid) return fail(WMG_ERR_INVALID_ARG, "wmg_solve_resume: the plan holds no solver state");
+    if (count != pl->state.count || count != pl->cap)
+        return fail(WMG_ERR_INVALID_ARG, "wmg_solve_resume: count differs from the state's problem count");
     const SolveState s0 = pl->state;
     if (max_iter < s0.steps)
         return fail(WMG_ERR_INVALID_ARG, "wmg_solve_resume: max_iter is below the iterations already done");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int count = pl->cap;
     // histories: the entries so far, in rows of the new length
     const int new_ld = max_iter + 1;
     {

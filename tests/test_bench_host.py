@@ -35,3 +35,18 @@ def test_study_helpers():
     curve = [(1, 1, 0.9, 1.0), (2, 2, 0.5, 0.7), (4, 4, 0.3, 0.6), (8, 8, 0.35, 0.5)]
     k, row = study.k_opt(curve)
     assert k == 4 and row[2] == 0.3
+
+
+def test_traffic_is_reported_only_for_the_measured_source(monkeypatch, tmp_path):
+    import hashlib
+    src = tmp_path / "kernel.cu"
+    src.write_bytes(b"// kernel source\n")
+    h = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setitem(bench.KERNEL_TRAFFIC, "project",
+                        {"source": "kernel.cu", "sha256_16": h, "bytes_per_image": 1000.0})
+    assert bench._kernel_traffic("project", 256) == 256000.0
+    src.write_bytes(b"// kernel source, changed\n")
+    assert bench._kernel_traffic("project", 256) is None
+    src.unlink()
+    assert bench._kernel_traffic("project", 256) is None

@@ -1956,12 +1956,13 @@ extern "C" int32_t wmg_solve(wmg_plan *pl, int32_t solver, int32_t preconditione
 // Checkpoint / resume: the state of the last solve, copied out and back
 // ---------------------------------------------------------------------------
 namespace {
+constexpr int kMaxRegions = 20;     // device ranges of a state (the GMRES state has 11)
 struct StateHeader {
     char magic[8];
     int32_t version, solver, pre, restart, count, prec, steps, hist_ld, nregions, pad;
     uint64_t fingerprint;
     int64_t N, M;
-    int64_t bytes[20];
+    int64_t bytes[kMaxRegions];
 };
 constexpr char kStateMagic[8] = {'W', 'M', 'G', 'S', 'T', 'A', 'T', 'E'};
 }  // namespace
@@ -1986,7 +1987,7 @@ extern "C" int32_t wmg_state_export(wmg_plan *pl, void *host, int64_t bytes, voi
     if (!pl || !host) return fail(WMG_ERR_INVALID_ARG, "wmg_state_export: bad arguments");
     if (!pl->state.valid) return fail(WMG_ERR_INVALID_ARG, "wmg_state_export: the plan holds no solver state");
     const std::vector<Region> regs = state_regions(pl);
-    if (bytes < state_total(pl) || regs.size() > 20)
+    if (bytes < state_total(pl) || regs.size() > (size_t)kMaxRegions)
         return fail(WMG_ERR_INVALID_ARG, "wmg_state_export: buffer smaller than wmg_state_bytes");
     const SolveState &s = pl->state;
     StateHeader h{};
@@ -2020,7 +2021,7 @@ extern "C" int32_t wmg_state_import(wmg_plan *pl, const void *host, int64_t byte
         return fail(WMG_ERR_INVALID_ARG, "wmg_state_import: not a solver state");
     if (h.fingerprint != pl->fingerprint || h.prec != pl->prec)
         return fail(WMG_ERR_INVALID_ARG, "wmg_state_import: the state belongs to another geometry or options");
-    if (h.count < 1 || h.steps < 0 || h.hist_ld != h.steps + 1 || h.nregions < 1 || h.nregions > 20)
+    if (h.count < 1 || h.steps < 0 || h.hist_ld != h.steps + 1 || h.nregions < 1 || h.nregions > kMaxRegions)
         return fail(WMG_ERR_INVALID_ARG, "wmg_state_import: corrupt header");
     if ((rc = check_solve_args(pl, h.solver, h.pre, h.steps, h.solver == WMG_SOLVER_GMRES ? h.restart : 1)))
         return rc;

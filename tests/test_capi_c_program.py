@@ -63,3 +63,19 @@ int main(void) {{
     assert out.returncode == 0, out
     count, version = map(int, out.stdout.split())
     assert count == len(names) and version >= 100
+
+
+def test_readme_c_example_compiles(tmp_path):
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    readme = open(os.path.join(ROOT, "README.md")).read()
+    snippet = re.search(r"```c\n(.*?)```", readme, flags=re.S).group(1)
+    lines = [ln for ln in snippet.splitlines() if not ln.startswith("#include")]
+    prog = ('#include "wmgct.h"\n'
+            "int example(void *stream, const float *d_b, float *d_x) {\n" + "\n".join(lines) +
+            "\n    return rc;\n}\n")
+    src = tmp_path / "readme_example.c"
+    src.write_text(prog)
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-Wno-unused-variable", "-I", INC, "-c", str(src),
+                    "-o", str(tmp_path / "readme_example.o")], check=True)

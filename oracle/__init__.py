@@ -17,6 +17,15 @@ Every function follows a passage of Cools et al., arXiv 1310.0956:
                               residual rule, leaf exact solves (Section 4.1)
   cgls, gmres                 Krylov solvers on the normal equations
                               (Section 2.3.1), right preconditioning for GMRES
+  wtg_propagator,             dense error propagators of the wavelet two-grid
+  tg_sirt_propagator          scheme (eq. wmg) and the classical TG(1,1)-SIRT
+                              scheme (eq. mg_error), and the condition numbers
+                              of Section 3.2 (eq. condnr, eq. spec_wavelet,
+                              eq. spec_classic). The values Figure 4 prints
+                              are for the paper's Joseph kernel and unstated
+                              detector width: parity unpinned for those exact
+                              values; their orders of magnitude and ordering
+                              are checked.
 """
 from __future__ import annotations
 

@@ -115,10 +115,23 @@ def _load():
         return lib
 
 
+SUMMATION_NATURAL, SUMMATION_REVERSED, SUMMATION_PAIRWISE = 0, 1, 2
+
+
+def set_summation(mode: int) -> None:
+    """Order of every later SpMV row sum and dot product: natural, reversed,
+    or pairwise (recursive halving). The three evaluate the same arithmetic
+    with different rounding; their spread is the floor below which two
+    correct FP64 implementations need not agree."""
+    if mode not in (SUMMATION_NATURAL, SUMMATION_REVERSED, SUMMATION_PAIRWISE):
+        raise ValueError("unknown summation order")
+    _load().or_set_reverse(int(mode))
+
+
 def set_reverse_summation(flag: bool) -> None:
     """Run every later SpMV and dot product in reversed order (a second,
     differently rounded evaluation of the same arithmetic)."""
-    _load().or_set_reverse(1 if flag else 0)
+    set_summation(SUMMATION_REVERSED if flag else SUMMATION_NATURAL)
 
 
 def _f64(a) -> np.ndarray:

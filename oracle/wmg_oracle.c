@@ -352,11 +352,37 @@ void or_op_trig(const or_op *op, double *c, double *s)
 }
 
 /* Summation order: 0 = natural, 1 = reversed (every SpMV row, the
- * backprojection's row sweep and every dot product run backwards). The
- * reversed run gives the same results up to rounding; the difference between
- * the two runs measures how much rounding the computed iterates carry. */
+ * backprojection's row sweep and every dot product run backwards), 2 =
+ * pairwise (every SpMV row and every dot product summed by recursive halving;
+ * the backprojection's sweep in natural order). Each run gives the same
+ * results up to rounding; the differences between the runs measure how much
+ * rounding the computed iterates carry. */
 static int g_reverse = 0;
 void or_set_reverse(int r) { g_reverse = r; }
+
+/* sum of a[i] * b[i] over i < len by recursive halving */
+static double pairwise_dot(const double *a, const double *b, int64_t len)
+{
+    if (len <= 4) {
+        double acc = 0.0;
+        for (int64_t i = 0; i < len; i++) acc += a[i] * b[i];
+        return acc;
+    }
+    const int64_t h = len / 2;
+    return pairwise_dot(a, b, h) + pairwise_dot(a + h, b + h, len - h);
+}
+
+/* sum of val[q] * x[col[q]] over q in [q0, q1) by recursive halving */
+static double pairwise_row(const or_op *op, const double *x, int64_t q0, int64_t q1)
+{
+    if (q1 - q0 <= 4) {
+        double acc = 0.0;
+        for (int64_t q = q0; q < q1; q++) acc += op->val[q] * x[op->col[q]];
+        return acc;
+    }
+    const int64_t h = q0 + (q1 - q0) / 2;
+    return pairwise_row(op, x, q0, h) + pairwise_row(op, x, h, q1);
+}
 
 /* y = W x  (one SpMV, Section 2.1) */
 void or_project(const or_op *op, const double *x, double *y)
@@ -364,7 +390,9 @@ void or_project(const or_op *op, const double *x, double *y)
     const int64_t M = (int64_t)op->m * op->D;
     for (int64_t i = 0; i < M; i++) {
         double acc = 0.0;
-        if (g_reverse)
+        if (g_reverse == 2)
+            acc = pairwise_row(op, x, op->rowptr[i], op->rowptr[i + 1]);
+        else if (g_reverse)
             for (int64_t q = op->rowptr[i + 1] - 1; q >= op->rowptr[i]; q--)
                 acc += op->val[q] * x[op->col[q]];
         else
@@ -380,7 +408,7 @@ void or_backproject(const or_op *op, const double *y, double *x)
     const int64_t M = (int64_t)op->m * op->D, N = (int64_t)op->n * op->n;
     for (int64_t j = 0; j < N; j++) x[j] = 0.0;
     for (int64_t ii = 0; ii < M; ii++) {
-        const int64_t i = g_reverse ? M - 1 - ii : ii;
+        const int64_t i = g_reverse == 1 ? M - 1 - ii : ii;
         for (int64_t q = op->rowptr[i]; q < op->rowptr[i + 1]; q++)
             x[op->col[q]] += op->val[q] * y[i];
     }
@@ -398,6 +426,8 @@ static void apply_A(const or_op *op, double lambda, const double *v, double *z, 
 static double dot(const double *a, const double *b, int64_t len)
 {
     double acc = 0.0;
+    if (g_reverse == 2)
+        return pairwise_dot(a, b, len);
     if (g_reverse)
         for (int64_t i = len - 1; i >= 0; i--) acc += a[i] * b[i];
     else

@@ -91,3 +91,22 @@ def test_batch_needs_every_problem():
         bt.solve([b0], outs=outs)
     with pytest.raises(ValueError):
         bt.solve([b0, torch.zeros(12, dtype=torch.float64)], outs=outs[:1])
+
+
+def test_noalloc_projection_checks_its_buffers(monkeypatch):
+    # a short b would be written past its end on the device: every size,
+    # dtype and device is checked before the library is reached
+    def never():
+        raise AssertionError("the library was called")
+    monkeypatch.setattr(wmg, "lib", never)
+    n, m, D = 8, 5, 13
+    x = torch.zeros(n * n, dtype=torch.float32)
+    b = torch.zeros(m * D, dtype=torch.float32)
+    with pytest.raises(ValueError):
+        wmg.wmg_project_noalloc(n, m, D, x, torch.zeros(m * D - 1, dtype=torch.float32))
+    with pytest.raises(ValueError):
+        wmg.wmg_project_noalloc(n, m, D, torch.zeros(n * n + 1, dtype=torch.float32), b)
+    with pytest.raises(TypeError):
+        wmg.wmg_project_noalloc(n, m, D, x, b)                  # host tensors
+    with pytest.raises(TypeError):
+        wmg.wmg_project_noalloc(n, m, D, x.data_ptr(), b)       # a raw pointer

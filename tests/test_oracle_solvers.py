@@ -218,3 +218,28 @@ def test_bicgstab_first_step_galerkin_conditions():
     assert abs(r1 @ (A @ s)) < 1e-10 * np.linalg.norm(r1) * np.linalg.norm(A @ s)
     omega = (x1 - alpha * r0) @ s / (s @ s)
     np.testing.assert_allclose(x1, alpha * r0 + omega * s, rtol=0, atol=1e-12 * np.abs(x1).max())
+
+
+@pytest.mark.parametrize("mode", [oracle.SUMMATION_REVERSED, oracle.SUMMATION_PAIRWISE])
+def test_summation_orders_evaluate_the_same_arithmetic(mode):
+    # the rounding variants behind the parity floor: the products agree with
+    # dense ones to rounding, and the converged solution is the dense one
+    op, b = setup()
+    W = op.dense()
+    rng = np.random.default_rng(3)
+    x, y = rng.random(op.N), rng.random(op.M)
+    lam = 0.05
+    xs = ls_solution(op, b, lam)
+    try:
+        oracle.set_summation(mode)
+        p, q = op.project(x), op.backproject(y)
+        assert np.abs(p - W @ x).max() < 1e-14 * np.abs(W @ x).max()
+        assert np.abs(q - W.T @ y).max() < 1e-14 * np.abs(W.T @ y).max()
+        xc, _, _ = oracle.cgls(op, b, 2000, 1e-13, lam)
+        xg, _, _ = oracle.gmres(op, b, 400, 20, 1e-13, lam)
+    finally:
+        oracle.set_summation(oracle.SUMMATION_NATURAL)
+    assert np.linalg.norm(xc - xs) < 1e-10 * np.linalg.norm(xs)
+    assert np.linalg.norm(xg - xs) < 1e-10 * np.linalg.norm(xs)
+    with pytest.raises(ValueError):
+        oracle.set_summation(7)

@@ -473,14 +473,20 @@ int32_t wmg_profile_end(wmg_plan *plan, wmg_profile_stats *out, void *stream);
  * Geometry: n x n image, m equiangular angles over [0, pi), D bins of one
  * pixel width, centred, W = exact intersection lengths (WMG_KERNEL_STRIP);
  * FP32 image x (n*n) and sinogram b (m*D), device memory, one image per call.
- * Results equal wmg_project's for that geometry.
+ * Results equal wmg_project's for that geometry bit for bit (the same
+ * angle tables and the same projector kernel).
  * Limits: n <= 1024, m <= 4096, D <= 2048; larger sizes return
  * WMG_ERR_INVALID_ARG. The scratch (transposed image, work lists, angle
- * tables; about 12 MiB) lives in fixed __device__ arrays that every GPU which
- * loads the library keeps until the process exits. The first call on a
- * device looks up those arrays' device addresses; make that first call before
- * any stream capture. Every call shares the same arrays, so calls whose work
- * overlaps on the GPU (other streams, other host threads) race: serialise
+ * tables: 8,830,976 bytes, about 8.4 MiB) lives in fixed __device__ arrays
+ * that every GPU on which the library's device code is loaded keeps until
+ * the process exits. With lazy module loading (the CUDA default) that
+ * memory is taken by the first call on each device, when the call looks up
+ * the arrays' device addresses: make that first call at start-up, before
+ * the caller's allocator takes the free memory, and before any stream
+ * capture. Later calls take no device memory. The host side is locked, so
+ * calls from several host threads and on several devices are safe to issue;
+ * every call on one device shares the same arrays, so calls whose work
+ * overlaps on that GPU (other streams, other host threads) race: serialise
  * them. Asynchronous on `stream`. */
 int32_t wmg_project_noalloc(int32_t n, int32_t m, int32_t D, const float *x, float *b, void *stream);
 

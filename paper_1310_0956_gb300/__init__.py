@@ -285,9 +285,23 @@ def use_torch_allocator(enable: bool = True) -> None:
 
 
 def wmg_project_noalloc(n, m, D, x, b, stream=None):
-    """Forward projection without device allocation (FP32, equiangular
-    geometry, unit bins; see include/wmgct.h for the limits)."""
-    _check(lib().wmg_project_noalloc(n, m, D, x, b, stream))
+    """Forward projection b = W x without device allocation (FP32,
+    equiangular geometry, unit bins; n <= 1024, m <= 4096, D <= 2048). x and
+    b are contiguous float32 CUDA tensors of n*n and m*D elements; runs on
+    `stream` (default: torch's current stream)."""
+    import torch
+    bufs = (("x", x, n * n), ("b", b, m * D))
+    for name, t, size in bufs:
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch tensor")
+        if t.numel() != size:
+            raise ValueError(f"{name} holds {t.numel()} elements, the geometry needs {size}")
+    for name, t, _ in bufs:
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    if stream is None:
+        stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _check(lib().wmg_project_noalloc(n, m, D, C.c_void_p(x.data_ptr()), C.c_void_p(b.data_ptr()), stream))
 
 
 def wmg_batch_create(geoms, opts, stream=None) -> C.c_void_p:

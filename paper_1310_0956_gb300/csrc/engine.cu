@@ -73,12 +73,15 @@ int num_sms()
     return v;
 }
 
-// Equiangular angle table: theta_a = pi*a/m reduced to the first octant so
-// that multiples of pi/2 are exactly 0 / +-1, odd multiples of pi/4 give
-// cos = sin = sqrt(1/2), and theta + pi/2 gets exactly (-sin, cos).
-static void angle_table(int m, const double *angles, std::vector<double2> &cs)
+// Angle tables of a geometry, into caller-provided arrays of m entries.
+// Equiangular angles (angles == NULL): theta_a = pi*a/m reduced to the first
+// octant so that multiples of pi/2 are exactly 0 / +-1, odd multiples of pi/4
+// give cos = sin = sqrt(1/2), and theta + pi/2 gets exactly (-sin, cos).
+// cs32 is the round-to-nearest FP32 copy; csx the split (12-significant-bit
+// head, a multiple of 2^-12, and FP32 tail); angf the FP32 kernels' table.
+void geometry_tables(int m, const double *angles, int kernel, double2 *cs, float2 *cs32, float4 *csx,
+                     AngleF *angf)
 {
-    cs.resize(m);
     for (int a = 0; a < m; ++a) {
         double c, s;
         if (angles) {
@@ -98,6 +101,42 @@ static void angle_table(int m, const double *angles, std::vector<double2> &cs)
             if (quad & 1) { const double t = c; c = -s; s = t; }
         }
         cs[a] = make_double2(c, s);
+        cs32[a] = make_float2((float)c, (float)s);
+        const double ch = std::nearbyint(c * 4096.0) / 4096.0;
+        const double sh = std::nearbyint(s * 4096.0) / 4096.0;
+        csx[a] = make_float4((float)ch, (float)(c - ch), (float)sh, (float)(s - sh));
+    }
+    fill_angle_table(cs, m, kernel, angf);
+}
+
+// FP32 scalars and the backprojector's path flags of a geometry whose n, m,
+// D, h, dt and t0 are set, from its FP32 angle table (host copy).
+void geometry_scalars(GeomDev &gd, const AngleF *angf)
+{
+    // quarter-turn pairs: angle a + m/2 is angle a turned by pi/2 in the
+    // FP32 table, (c, s) -> (-s, c) with the same chord constants
+    gd.qpair = gd.m % 2 == 0 && gd.m >= 2;
+    for (int a = 0; gd.qpair && a < gd.m / 2; ++a) {
+        const AngleF &u = angf[a], &v = angf[a + gd.m / 2];
+        gd.qpair = v.chi == -u.shi && v.clo == -u.slo && v.shi == u.chi && v.slo == u.clo && v.wa == u.wa &&
+                   v.wb == u.wb && v.lmax == u.lmax;
+    }
+    gd.hf = (float)gd.h;
+    gd.dtf = (float)gd.dt;
+    gd.t0f = (float)gd.t0;
+    gd.hDf = 0.5f * (float)(gd.D - 1);
+    gd.unit = gd.dt == 1.0 && gd.t0 == 0.0 ? 1 : 0;
+    if (gd.unit) {
+        // Pixel centres of the 32 x 32 backprojection tiles (the last tile
+        // row and column may reach past the image) lie within rmax of the
+        // centre, so |tau| <= rmax at every angle. The unit-bin path takes
+        // bins k0 = rint(tau + hD - 1/2) and k0 + 1 (up to FP32 rounding of
+        // tau, far below the 0.01 margin): both lie in [0, D) when
+        // rmax < hD.
+        const double half = 0.5 * gd.n;
+        const double xmax = std::max(half - 0.5, 32.0 * ((gd.n + 31) / 32) - half - 0.5);
+        const double rmax = std::sqrt(2.0) * xmax;
+        if (rmax + 0.01 < 0.5 * (gd.D - 1)) gd.unit = 2;
     }
 }
 
@@ -768,27 +807,11 @@ int32_t make_geo(const wmg_geom *g, const wmg_opts *o, Geo &G, cudaStream_t st)
     gd.omega = o->omega > 0 ? o->omega : 1.0;
     G.hd = (o->cycle == WMG_CYCLE_ADDITIVE || !G.has_wmg) ? 0 : std::min(o->hybrid_depth, L);
     G.haar_W = haar_width(gd);
-    std::vector<double2> cs;
-    angle_table(g->m, g->angles, cs);
+    std::vector<double2> cs(g->m);
     std::vector<float2> cs32(g->m);
     std::vector<float4> csx(g->m);
-    for (int a = 0; a < g->m; ++a) {
-        cs32[a] = make_float2((float)cs[a].x, (float)cs[a].y);
-        // split: 12-significant-bit head (a multiple of 2^-12) and FP32 tail
-        const double ch = std::nearbyint(cs[a].x * 4096.0) / 4096.0;
-        const double sh = std::nearbyint(cs[a].y * 4096.0) / 4096.0;
-        csx[a] = make_float4((float)ch, (float)(cs[a].x - ch), (float)sh, (float)(cs[a].y - sh));
-    }
     std::vector<AngleF> angf(g->m);
-    fill_angle_table(cs.data(), g->m, gd.kernel, angf.data());
-    // quarter-turn pairs: angle a + m/2 is angle a turned by pi/2 in the
-    // FP32 table, (c, s) -> (-s, c) with the same chord constants
-    gd.qpair = g->m % 2 == 0 && g->m >= 2;
-    for (int a = 0; gd.qpair && a < g->m / 2; ++a) {
-        const AngleF &u = angf[a], &v = angf[a + g->m / 2];
-        gd.qpair = v.chi == -u.shi && v.clo == -u.slo && v.shi == u.chi && v.slo == u.clo && v.wa == u.wa &&
-                   v.wb == u.wb && v.lmax == u.lmax;
-    }
+    geometry_tables(g->m, g->angles, gd.kernel, cs.data(), cs32.data(), csx.data(), angf.data());
     if (!G.cs64.ensure(g->m * sizeof(double2)) || !G.cs32.ensure(g->m * sizeof(float2)) ||
         !G.csx.ensure(g->m * sizeof(float4)) || !G.angf.ensure(g->m * sizeof(AngleF)))
         return fail(WMG_ERR_OOM, "plan allocation failed");
@@ -801,24 +824,8 @@ int32_t make_geo(const wmg_geom *g, const wmg_opts *o, Geo &G, cudaStream_t st)
     gd.cs32 = G.cs32.as<float2>();
     gd.csx = G.csx.as<float4>();
     gd.angf = G.angf.as<AngleF>();
-    gd.hf = (float)gd.h;
-    gd.dtf = (float)gd.dt;
-    gd.t0f = (float)gd.t0;
-    gd.hDf = 0.5f * (float)(g->D - 1);
-    G.unit_bins = gd.dt == 1.0 && gd.t0 == 0.0;
-    gd.unit = G.unit_bins ? 1 : 0;
-    if (G.unit_bins) {
-        // Pixel centres of the 32 x 32 backprojection tiles (the last tile
-        // row and column may reach past the image) lie within rmax of the
-        // centre, so |tau| <= rmax at every angle. The unit-bin path takes
-        // bins k0 = rint(tau + hD - 1/2) and k0 + 1 (up to FP32 rounding of
-        // tau, far below the 0.01 margin): both lie in [0, D) when
-        // rmax < hD.
-        const double half = 0.5 * g->n;
-        const double xmax = std::max(half - 0.5, 32.0 * ((g->n + 31) / 32) - half - 0.5);
-        const double rmax = std::sqrt(2.0) * xmax;
-        if (rmax + 0.01 < 0.5 * (g->D - 1)) gd.unit = 2;
-    }
+    geometry_scalars(gd, angf.data());
+    G.unit_bins = gd.unit != 0;
     return WMG_OK;
 }
 

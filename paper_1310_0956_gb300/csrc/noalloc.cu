@@ -13,6 +13,7 @@
 // calls neither cudaMalloc nor cudaFree nor any allocating routine.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "kern_common.cuh"
 
@@ -25,8 +26,7 @@ constexpr int kMaxBins = 2048;
 constexpr int kMaxProjTiles = kMaxAngles * ((kMaxBins + 31) / 32);
 constexpr int kMaxImgTiles = (kMaxSide / 32) * (kMaxSide / 32);
 
-// Shared by every call on a device; the last call's contents stay in place
-// (about 12.4 MiB in all).
+// Shared by every call on a device; the last call's contents stay in place.
 static __device__ __align__(256) float g_scratch_T[(size_t)kMaxSide * kMaxSide];
 static __device__ __align__(256) int4 g_proj_tiles[kMaxProjTiles];
 static __device__ __align__(256) int4 g_img_tiles[kMaxImgTiles];
@@ -36,6 +36,14 @@ static __device__ __align__(256) float4 g_csx[kMaxAngles];
 static __device__ __align__(256) AngleF g_angf[kMaxAngles];
 static __device__ __align__(256) GeomDev g_geom;
 static __device__ __align__(256) ProbDev g_prob;
+
+// Device memory the arrays above hold on every GPU that loads them:
+// 8,830,976 bytes of arrays (about 8.4 MiB) plus the two small records.
+constexpr size_t kArrayBytes = sizeof(float) * (size_t)kMaxSide * kMaxSide +
+                               sizeof(int4) * (size_t)(kMaxProjTiles + kMaxImgTiles) +
+                               (sizeof(double2) + sizeof(float2) + sizeof(float4) + sizeof(AngleF)) *
+                                   (size_t)kMaxAngles;
+static_assert(kArrayBytes == 8830976, "the documented scratch size is 8,830,976 bytes of arrays");
 
 struct DeviceSlots {
     bool ready = false;
@@ -51,35 +59,20 @@ struct DeviceSlots {
 constexpr int kMaxDevices = 64;
 static DeviceSlots g_slots[kMaxDevices];
 
-// Host staging of the angle tables (fixed size, no heap use).
+// Host staging of the angle tables (fixed size, no heap use), shared by every
+// host thread and device: a call holds g_host_lock from the first write into
+// it until its copies have been issued. A copy from pageable host memory
+// returns once the source has been read, so the lock need not outlast it.
 static double2 h_cs64[kMaxAngles];
 static float2 h_cs32[kMaxAngles];
 static float4 h_csx[kMaxAngles];
 static AngleF h_angf[kMaxAngles];
-
-// cos / sin of theta_a = pi a / m, reduced to the first octant as the plans
-// do: multiples of pi/2 exact, odd multiples of pi/4 give sqrt(1/2), and
-// theta + pi/2 gets exactly (-sin, cos).
-void equiangular(int a, int m, double *c, double *s)
-{
-    const long twice = 2L * a, quad = twice / m, rem = twice - quad * m;
-    double cv, sv;
-    if (rem == 0) { cv = 1.0; sv = 0.0; }
-    else if (2 * rem == m) { cv = std::sqrt(0.5); sv = cv; }
-    else if (2 * rem < m) {
-        const double phi = (M_PI / 2.0) * ((double)rem / (double)m);
-        cv = std::cos(phi); sv = std::sin(phi);
-    } else {
-        const double phi = (M_PI / 2.0) * ((double)(m - rem) / (double)m);
-        cv = std::sin(phi); sv = std::cos(phi);
-    }
-    if (quad & 1) { const double t = cv; cv = -sv; sv = t; }
-    *c = cv;
-    *s = sv;
-}
+static std::mutex g_host_lock;
 
 // Device addresses of the arrays above, looked up once per device with that
 // device current (host code may not use the symbols' names as addresses).
+// The first lookup on a device loads the module there, which is when the
+// arrays take their device memory. Called with g_host_lock held.
 int32_t device_slots(DeviceSlots **out)
 {
     int dev = 0;
@@ -126,25 +119,19 @@ extern "C" int32_t wmg_project_noalloc(int32_t n, int32_t m, int32_t D, const fl
         return fail(WMG_ERR_INVALID_ARG, "wmg_project_noalloc: n <= 1024, m <= 4096 and D <= 2048 "
                                          "(fixed scratch size); use wmg_project for larger problems");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> hold(g_host_lock);
     DeviceSlots *s = nullptr;
     int32_t rc = device_slots(&s);
     if (rc) return rc;
-    // geometry tables (host-computed, copied into the fixed device arrays)
-    for (int a = 0; a < m; ++a) {
-        double c, sn;
-        equiangular(a, m, &c, &sn);
-        h_cs64[a] = make_double2(c, sn);
-        h_cs32[a] = make_float2((float)c, (float)sn);
-        const double ch = std::nearbyint(c * 4096.0) / 4096.0;
-        const double sh = std::nearbyint(sn * 4096.0) / 4096.0;
-        h_csx[a] = make_float4((float)ch, (float)(c - ch), (float)sh, (float)(sn - sh));
-    }
-    fill_angle_table(h_cs64, m, WMG_KERNEL_STRIP, h_angf);
+    // geometry: the same host routines as a plan's (equiangular angles,
+    // exact intersection lengths, unit bins centred on the image)
+    geometry_tables(m, nullptr, WMG_KERNEL_STRIP, h_cs64, h_cs32, h_csx, h_angf);
     GeomDev g{};
-    g.n = n; g.m = m; g.D = D; g.L = 0; g.nc = n; g.P = 0; g.K = 1; g.B = 1;
+    g.n = n; g.m = m; g.D = D; g.L = 0; g.nc = n; g.P = n * n; g.K = 1; g.B = 1;
     g.h = 1.0 / n; g.t0 = 0.0; g.dt = 1.0; g.lambda = 0.0; g.omega = 1.0;
+    g.kernel = WMG_KERNEL_STRIP;
     g.cs64 = s->cs64; g.cs32 = s->cs32; g.csx = s->csx; g.angf = s->angf;
-    g.hf = (float)g.h; g.dtf = 1.f; g.t0f = 0.f; g.hDf = 0.5f * (float)(D - 1);
+    geometry_scalars(g, h_angf);
     ProbDev p{};
     p.geom = 0; p.slot = 0; p.img = 0; p.sino = 0; p.coef = 0;
     WMG_CUDA(cudaMemcpyAsync(s->cs64, h_cs64, m * sizeof(double2), cudaMemcpyHostToDevice, st));
@@ -160,7 +147,7 @@ extern "C" int32_t wmg_project_noalloc(int32_t n, int32_t m, int32_t D, const fl
     // the transposed copy overwrites every element the projector reads, so
     // nothing has to be cleared between calls
     launch_transpose<float>(s->geom, s->prob, s->img_tiles, nimg, x, s->scratch_T, st);
-    PjArgs a{0, x, s->scratch_T, b, nullptr, nullptr};
+    PjArgs a{0, x, s->scratch_T, b, nullptr, nullptr, nullptr, 1};
     launch_project<float>(s->geom, s->prob, s->proj_tiles, nproj, a, st);
     WMG_CUDA(cudaGetLastError());
     return WMG_OK;

@@ -74,6 +74,15 @@ constexpr double kNnzEps = 1e-12;
 // Fills the FP32 per-angle table from FP64 (cos, sin) pairs.
 void fill_angle_table(const double2 *cs, int m, int kernel, AngleF *out);
 
+// Host tables of one geometry (engine.cu): angles == NULL means equiangular
+// in [0, pi); every array holds m entries and is the caller's. Allocates
+// nothing, so the allocation-free entry point builds its tables with it too.
+void geometry_tables(int m, const double *angles, int kernel, double2 *cs, float2 *cs32, float4 *csx,
+                     AngleF *angf);
+// Fields of a geometry derived from n, m, D, h, dt, t0 and its FP32 angle
+// table: FP32 copies of the scalars, the unit-bin flag and quarter-turn pairs.
+void geometry_scalars(GeomDev &gd, const AngleF *angf);
+
 // One problem slot (or one virtual image of a multi-image product).
 struct ProbDev {
     int geom;                // index into the GeomDev table

@@ -48,6 +48,10 @@ RESTART = 20
 # The smoothed cycle (one l1-Jacobi pre- and post-sweep) is measured beside it.
 LEVELS, NU1, NU2, HYB = 5, 0, 0, 1
 NU_SMOOTHED = 1
+# Tikhonov parameters of the semi-convergence leg's sweep, relative to m / n
+LAMBDA_SWEEP = (0.0, 1e-4, 1e-3, 1e-2, 1e-1)
+# problems of the plain FP64 one-problem-per-launch comparison arms
+FP64_SAMPLE = 8
 # serving stream: Tikhonov parameter relative to m / n, the scale of the
 # spectral radius of W^T W in unit-square units (noisy, often underdetermined
 # requests; regularised normal equations as in the paper's noisy experiments)
@@ -76,6 +80,8 @@ def parse():
                     help="serving leg with every request arriving at t = 0 (saturated throughput)")
     ap.add_argument("--no-batched", action="store_true", help="skip the uneven-batch leg")
     ap.add_argument("--no-comparator", action="store_true", help="skip the stored-W (CSR) comparator leg")
+    ap.add_argument("--no-fp64-single", action="store_true",
+                    help="skip the plain FP64 one-problem-per-launch arm of the main workload")
     ap.add_argument("--no-variant", action="store_true",
                     help="skip the smoothed-cycle variant (nu1 = nu2 = 1) of the main workload")
     ap.add_argument("--no-joseph", action="store_true",
@@ -357,6 +363,19 @@ def run_ours(args, rank, world, local):
         e2e_times.append(e0.elapsed_time(e1) / 1e3)
     e2e_val = B * world / float(np.mean(e2e_times))
 
+    # the plain form: FP64, one problem per launch, the same cycle and solver
+    single = None
+    if rank == 0 and not args.no_fp64_single:
+        try:
+            ns = min(FP64_SAMPLE, B)
+            single = fp64_single_leg([dict(n=P0.n, m=P0.m, D=P0.D, levels=LEVELS)] * ns,
+                                     [b.view(B, M)[i].double().contiguous() for i in range(ns)],
+                                     wmg.SOLVER_GMRES, HYB, wmg.CYCLE_HYBRID,
+                                     [x.view(B, N)[i].double() for i in range(ns)], dev)
+            single["mixed_batched_over_fp64_single"] = value / world / single["recon_per_s"]
+        except Exception as e:
+            single = {"unavailable": f"{type(e).__name__}: {e}"}
+
     # dominant-kernel timing: projector and backprojector launches of one
     # profiled step (CUDA events around every launch on the plan's stream)
     prof = plan.profile_step(b, x, MAX_ITER, RTOL, RESTART)
@@ -405,6 +424,7 @@ def run_ours(args, rank, world, local):
             "cpu_baseline": cpu,
             "stored_w_comparator": comparator,
             "smoothed_cycle_variant": variant,
+            "fp64_one_problem_per_launch": single,
         }
         if not args.no_joseph and world == 1:
             try:
@@ -533,6 +553,22 @@ def semiconvergence_leg(dev) -> dict:
                          "ms_to_k_opt": e0.elapsed_time(e1)}
         out[tag] = res
         plan.close()
+    # Tikhonov sweep (eq. sys_reg, Tables 2-3): for each lambda the k_opt and
+    # the error at k_opt and at k_max of the Krylov solvers, plain and WMG
+    sweep = []
+    for rel in LAMBDA_SWEEP:
+        lam = rel * m / n
+        plan = wmg.Plan(n, m, D, levels=levels, nu1=0, nu2=0, lam=lam, hybrid_depth=levels - 1,
+                        cycle=wmg.CYCLE_HYBRID, precision=wmg.PREC_F32, kernel=wmg.KERNEL_JOSEPH)
+        row = {"lambda_over_m_per_n": rel, "lambda": lam}
+        for name, solver, pre, kmax in (("BiCGStab", wmg.SOLVER_BICGSTAB, False, 300),
+                                        ("WMG-BiCGStab", wmg.SOLVER_BICGSTAB, True, 100)):
+            curve = study.error_curve(plan, b, xd, solver, pre, study.log_ks(kmax, 6))
+            ko, best = study.k_opt(curve)
+            row[name] = {"k_opt": ko, "error_l2": best[2], "error_l2_at_kmax": curve[-1][2], "kmax": kmax}
+        sweep.append(row)
+        plan.close()
+    out["lambda_sweep"] = sweep
     return out
 
 
@@ -612,6 +648,38 @@ def serving_leg(args, dev) -> dict:
 # Uneven-batch leg: 64 problems of different sizes and angle counts solved
 # together (one launch per operator application over all of them)
 # ---------------------------------------------------------------------------
+def fp64_single_leg(geoms, bs64, solver, hybrid_depth, cycle, x_mixed, dev) -> dict:
+    """The plain form the mixed batched one is compared with: FP64 plans (FP64
+    operator, leaf solves and Krylov), one problem per solve call, so every
+    operator application is a launch over one problem; the same cycle,
+    solver and tolerance. Plan setup excluded (as for the batched form);
+    solve time by the host clock around each synchronising solve.
+    x_mixed: the mixed batched solutions of the same problems, for the
+    relative image difference of the two forms at equal tolerance."""
+    import torch
+    import paper_1310_0956_gb300 as wmg
+    times, iters, statuses, diffs = [], [], [], []
+    for g, b64, xm in zip(geoms, bs64, x_mixed):
+        pl = wmg.Plan(g["n"], g["m"], g["D"], levels=g["levels"], nu1=NU1, nu2=NU2, lam=g.get("lam", 0.0),
+                      hybrid_depth=hybrid_depth, cycle=cycle, precision=wmg.PREC_F64)
+        out = torch.empty(g["n"] * g["n"], dtype=torch.float64, device=dev)
+        pl.solve(b64, solver, True, MAX_ITER, RTOL, RESTART, out=out)          # warm-up (graphs, tuning)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info, _, _ = pl.solve(b64, solver, True, MAX_ITER, RTOL, RESTART, out=out)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        iters.append(info[0][0])
+        statuses.append(info[0][1])
+        diffs.append(float(torch.linalg.norm(out - xm) / torch.linalg.norm(out)))
+        pl.close()
+    return {"precision": "fp64 operator, leaf solves and Krylov", "problems_timed": len(times),
+            "recon_per_s": len(times) / float(np.sum(times)), "ms_per_recon": 1e3 * float(np.mean(times)),
+            "iters_mean": float(np.mean(iters)), "all_converged": bool(all(s_ == 0 for s_ in statuses)),
+            "rel_image_diff_vs_mixed_max": float(np.max(diffs)),
+            "timing": "host clock around each synchronising one-problem solve, setup excluded"}
+
+
 def batched_leg(args, dev) -> dict:
     import torch
     import paper_1310_0956_gb300 as wmg
@@ -641,8 +709,14 @@ def batched_leg(args, dev) -> dict:
         times.append(time.perf_counter() - t0)
     bt.close()
     t = float(np.mean(times))
+    single = fp64_single_leg(
+        [dict(n=p.n, m=p.m, D=p.D, levels=p.levels, lam=SERVING_EPS * p.m / p.n) for p in probs[:FP64_SAMPLE]],
+        [b_.to(torch.float64) for b_ in bs[:FP64_SAMPLE]], wmg.SOLVER_CGLS, 0, wmg.CYCLE_ADDITIVE,
+        [o.double() for o in outs[:FP64_SAMPLE]], dev)
+    single["mixed_batched_over_fp64_single"] = (len(probs) / t) / single["recon_per_s"]
     return {
         "workload": "batched64_n128-512_m60-360_noise1pct", "problems": len(probs),
+        "fp64_one_problem_per_launch": single,
         "recon_per_s": len(probs) / t, "ms_per_batch": t * 1e3,
         "solver": f"WMG-CGLS (PCG on the normal equations), additive cycle, nu1=nu2={NU1}, rtol {RTOL:g}",
         "lambda": f"lambda = {SERVING_EPS:g} * m / n",
@@ -816,9 +890,9 @@ def roofline_entry(prof: dict, P0, B: int) -> dict:
     peaks = load_peaks()
     clk = peaks.get("sm_max_mhz", 2070.0)
     peak = 152 * 128 * 2 * clk * 1e6 / 1e12
-    # the same launch as an HBM client: algorithmic bytes = the FP32 input
-    # (the projector reads each image and its transpose) and output vectors
-    n_in = 2 * P0.N if name == "project" else P0.M
+    # the same launch as an HBM client: algorithmic bytes = s (N + M), the
+    # FP32 input read once and the output written once
+    n_in = P0.N if name == "project" else P0.M
     n_out = P0.M if name == "project" else P0.N
     gbs = p["images_per_launch"] * (n_in + n_out) * 4 / (p["mean_ms"] * 1e-3) / 1e9
     hbm = peaks.get("hbm_gbs")

@@ -146,15 +146,19 @@ k_project_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
                         v0[r] = ok0[r] ? __ldg(src[b] + idx[r]) : 0.f;
                         v1[r] = ok1[r] ? __ldg(src[b] + idx[r] + 1) : 0.f;
                     }
+                    // one product chain over the step's rows in row order,
+                    // then one compensated (Kahan) step
+                    float rs = w0[0] * v0[0];
+                    rs = __fmaf_rn(w1[0], v1[0], rs);
 #pragma unroll
-                    for (int r = 0; r < R; r += 2) {
-                        const float rs = __fmaf_rn(w0[r], v0[r], __fmaf_rn(w1[r], v1[r],
-                                         __fmaf_rn(w0[r + 1], v0[r + 1], w1[r + 1] * v1[r + 1])));
-                        const float y = rs - c[b];                 // Kahan step
-                        const float tt = s[b] + y;
-                        c[b] = (tt - s[b]) - y;
-                        s[b] = tt;
+                    for (int r = 1; r < R; ++r) {
+                        rs = __fmaf_rn(w0[r], v0[r], rs);
+                        rs = __fmaf_rn(w1[r], v1[r], rs);
                     }
+                    const float y = rs - c[b];
+                    const float tt = s[b] + y;
+                    c[b] = (tt - s[b]) - y;
+                    s[b] = tt;
                 }
             }
         }

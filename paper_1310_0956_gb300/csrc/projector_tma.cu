@@ -28,6 +28,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -46,6 +47,7 @@ constexpr int kBoxFloats = kBoxW * kBoxH * kIB;         // one box: 8 rows of al
 constexpr int kStageFloats = kSub * kBoxFloats;         // 32 KB
 constexpr uint32_t kStageBytes = kStageFloats * 4;
 constexpr long long kWaitCycles = 1LL << 31;            // about a second
+constexpr long long kStallWaitCycles = 1LL << 22;       // about 2 ms: the test hook's limit
 constexpr size_t kSmemBytes = (size_t)kStages * kStageFloats * sizeof(float);
 }  // namespace
 
@@ -81,13 +83,15 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
 }
 // Waits for the phase of parity `parity` of the barrier; false if the CTA
 // has aborted or the wait timed out (then it aborts the CTA).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                          long long limit)
 {
+    if (mbar_try(bar, parity)) return true;                 // the phase has completed: data in place
     if (*abort_flag) return false;
     const long long t0 = clock64();
     while (!mbar_try(bar, parity)) {
         if (*abort_flag) return false;
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > limit) {
             *abort_flag = 1;
             atomicExch(&g_tma_error, 1);
             return false;
@@ -96,11 +100,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     return true;
 }
 // The same wait without the abort check (draining the producer's copies).
-__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity)
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity, long long limit)
 {
     const long long t0 = clock64();
     while (!mbar_try(bar, parity))
-        if (clock64() - t0 > kWaitCycles) return;
+        if (clock64() - t0 > limit) return;
 }
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z, uint32_t bar)
 {
@@ -157,11 +161,11 @@ __device__ __forceinline__ void tile_rays(const GeomDev *__restrict__ G, const P
 __global__ void __launch_bounds__(32 * (kNW + 1), 2)
 k_project_f32_tma(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P, const int4 *__restrict__ tiles,
                   int ntiles, PjArgs a, const __grid_constant__ CUtensorMap map_img,
-                  const __grid_constant__ CUtensorMap map_imgT)
+                  const __grid_constant__ CUtensorMap map_imgT, int stall, long long wait_limit)
 {
     // stage s, box q: [image][row][column] (the TMA box order)
     extern __shared__ __align__(1024) float ring[];
-    __shared__ float red_s[kNW][kIB][32], red_c[kNW][kIB][32];
+    __shared__ float red[kNW][kIB][32];            // per warp, image and lane: s - c
     __shared__ __align__(8) unsigned long long full[kStages], empty[kStages];
     __shared__ int xoff[kStages][kSub];
     __shared__ int abort_flag;
@@ -180,7 +184,9 @@ k_project_f32_tma(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P, 
 
     if (w == kNW) {
         // ---------------- producer warp ----------------
-        int seq = 0;
+        if (stall) return;          // test hook: no copies, so the consumers' waits run out
+        int seq = 0, st = 0;
+        uint32_t ph = 0;
         for (int t = blockIdx.x; t < ntiles && !*abort_v; t += gridDim.x) {
             const int4 tl = tiles[t];
             TileRays tr;
@@ -191,27 +197,27 @@ k_project_f32_tma(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P, 
             const int n = g.n;
             const AngleF &A = g.angf[tl.y];
             const CUtensorMap *map = tr.steep ? &map_img : &map_imgT;
-            const float off = tr.half_n - 0.5f, xs0 = tr.tk * A.inv_cc;
+            const float off = tr.half_n - 0.5f;
+            // leftmost crossing of the row y = 0 over the tile's rays; a
+            // box's first column follows from it without a warp reduction
+            const float xs_min = warp_min_f(tr.valid ? tr.tk * A.inv_cc : INFINITY);
             const int z0 = (int)(P[tl.x].img / ((int64_t)n * n));
             // two stages of 16 rows per step of 4 rows of each consumer warp
             const int nst = 2 * ((nrows + 31) / 32);
             for (int c = 0; c < nst; ++c, ++seq) {
-                const int s = seq % kStages;
-                const uint32_t u = (uint32_t)(seq / kStages);
-                if (u > 0 && !mbar_wait(smem_u32(&empty[s]), (u - 1) & 1, abort_v)) break;
+                const int s = st;
+                if (seq >= kStages && !mbar_wait(smem_u32(&empty[s]), ph ^ 1, abort_v, wait_limit)) break;
                 // box q holds rows ya .. ya + 7; its first column: two pixels
-                // left of the leftmost candidate, rounded down to a multiple of 4
-#pragma unroll
-                for (int q = 0; q < kSub; ++q) {
-                    const int ya = tr.lo + 16 * c + 8 * q;
-                    int xl = INT_MAX;
-                    if (tr.valid) {
-                        const float y0 = (float)ya + 0.5f - tr.half_n, y1 = y0 + 7.f;
-                        const float f0 = __fmaf_rn(-y0, A.slope, xs0) + off, f1 = __fmaf_rn(-y1, A.slope, xs0) + off;
-                        xl = (int)floorf(fminf(f0, f1));
-                    }
-                    xl = warp_min(xl);
-                    if (lane == 0) xoff[s][q] = ((xl - 2) >> 2) << 2;     // floor to a multiple of 4
+                // left of the leftmost crossing of its rows (the row centre
+                // line's crossing is linear in the row), rounded down to a
+                // multiple of 4. Consumers check that every candidate they
+                // read lies in the box.
+                if (lane < kSub) {
+                    const int ya = tr.lo + 16 * c + 8 * lane;
+                    const float y0 = (float)ya + 0.5f - tr.half_n, y1 = y0 + 7.f;
+                    const float f0 = __fmaf_rn(-y0, A.slope, xs_min), f1 = __fmaf_rn(-y1, A.slope, xs_min);
+                    const int xl = (int)floorf(fminf(f0, f1) + off);
+                    xoff[s][lane] = ((xl - 2) >> 2) << 2;                 // floor to a multiple of 4
                 }
                 __syncwarp();
                 if (lane == 0) {
@@ -224,18 +230,26 @@ k_project_f32_tma(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P, 
                                     fb);
                 }
                 __syncwarp();
+                if (++st == kStages) { st = 0; ph ^= 1; }
             }
         }
         if (*abort_v) {
             // wait (bounded) for the copies of the stages still in flight
             for (int d = max(0, seq - kStages); d < seq; ++d)
-                mbar_drain(smem_u32(&full[d % kStages]), (uint32_t)(d / kStages) & 1);
+                mbar_drain(smem_u32(&full[d % kStages]), (uint32_t)(d / kStages) & 1, wait_limit);
         }
         return;
     }
 
     // ---------------- consumer warps ----------------
-    int seq = 0;
+    // Pairs of images go through the paired FP32 instructions (two IEEE
+    // single-precision operations, each rounded to nearest, per
+    // instruction): the per-image arithmetic is exactly the one-image
+    // kernel's, in half the arithmetic instructions.
+    constexpr int kP = kIB / 2;
+    const float2 neg1 = make_float2(-1.f, -1.f);
+    int st = 0;                                                      // ring stage and its phase parity
+    uint32_t ph = 0;
     bool bad = false;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 tl = tiles[t];
@@ -248,9 +262,9 @@ k_project_f32_tma(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P, 
         const float cc_hi = tr.steep ? A.chi : A.shi, cc_lo = tr.steep ? A.clo : A.slo;
         const float ss_hi = tr.steep ? A.shi : A.chi, ss_lo = tr.steep ? A.slo : A.clo;
         const float half_n = tr.half_n, tk = tr.tk;
-        float s[kIB], cmp[kIB];
+        float2 s2[kP], c2[kP], acc[kP];
 #pragma unroll
-        for (int b = 0; b < kIB; ++b) { s[b] = 0.f; cmp[b] = 0.f; }
+        for (int q = 0; q < kP; ++q) { s2[q] = make_float2(0.f, 0.f); c2[q] = s2[q]; acc[q] = s2[q]; }
         const int nrows = tr.hi - tr.lo + 1;
         if (nrows > 0) {
             const int iy0 = tr.lo + w;
@@ -263,63 +277,75 @@ k_project_f32_tma(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P, 
             const float off = half_n - 0.5f;
             const int nmine = (nrows - w + kNW - 1) / kNW;           // rows of this warp
             const float wa = A.wa, wb = A.wb, ccf = A.cc;
-            const int nst = 2 * ((nrows + 31) / 32);
-            for (int c = 0; c < nst; ++c, ++seq) {
-                const int st = seq % kStages;
-                mbar_wait(smem_u32(&full[st]), (uint32_t)(seq / kStages) & 1, abort_v);
-                // this stage holds rows 2h, 2h + 1 (h = c & 1) of the warp's
-                // step of 4 rows j .. j + 3: one compensated step. A warp
+            const int nsteps = (nrows + 31) / 32;                    // two stages of 16 rows per step
+            for (int c = 0; c < nsteps; ++c) {
+                // the warp's step of 4 rows j .. j + 3: rows 0, 1 in the
+                // first stage, 2, 3 in the second, one product chain per
+                // image over the 4 rows and one compensated step. A warp
                 // whose rows have all been summed takes no further step (as
                 // in the one-image kernel: a step of zeros still moves a sum)
-                const int j = 4 * (c >> 1), h = c & 1;
-                if (j < nmine) {
-                    const float *stage = ring + (size_t)st * kStageFloats + w * kBoxW;
-                    int li[2];
-                    bool live[2];
-                    float w0[2], w1[2];
+                const int j = 4 * c;
 #pragma unroll
-                    for (int r = 0; r < 2; ++r) {
-                        live[r] = tr.valid && (j + 2 * h + r < nmine);
-                        const int ix0 = __float2int_rd(xs + off);
-                        const int l = ix0 - xoff[st][r];
-                        bad |= live[r] && (unsigned)l > (unsigned)(kBoxW - 2);
-                        li[r] = min(max(l, 0), kBoxW - 2);
-                        const float xc = (float)ix0 + 0.5f - half_n;
-                        const float dl0 = __fmaf_rn(-xc, cc_hi, brow) - __fmaf_rn(xc, cc_lo, cy);
-                        // rows past the warp's last one weigh 0 (the one-image
-                        // kernel reads 0 there instead: the same sums)
-                        w0[r] = live[r] ? __saturatef(__fmaf_rn(-fabsf(dl0), wa, wb)) : 0.f;
-                        w1[r] = live[r] ? __saturatef(__fmaf_rn(-fabsf(dl0 - ccf), wa, wb)) : 0.f;
-                        brow += dbrow;
-                        cy += dcy;
-                        xs += dxs;
-                    }
-#pragma unroll
-                    for (int b = 0; b < kIB; ++b) {
-                        if (!tr.act[b]) continue;                        // uniform across the CTA
-                        float v0[2], v1[2];
+                for (int h = 0; h < 2; ++h) {
+                    mbar_wait(smem_u32(&full[st]), ph, abort_v, wait_limit);
+                    if (j < nmine) {
+                        const float *stage = ring + (size_t)st * kStageFloats + w * kBoxW;
+                        int li[2];
+                        float2 w0[2], w1[2];
 #pragma unroll
                         for (int r = 0; r < 2; ++r) {
-                            const float *px = stage + r * kBoxFloats + b * (kBoxW * kBoxH) + li[r];
-                            v0[r] = px[0];
-                            v1[r] = px[1];
+                            const bool live = tr.valid && (j + 2 * h + r < nmine);
+                            const int ix0 = __float2int_rd(xs + off);
+                            const int l = ix0 - xoff[st][r];
+                            bad |= live && (unsigned)l > (unsigned)(kBoxW - 2);
+                            li[r] = min(max(l, 0), kBoxW - 2);
+                            const float xc = (float)ix0 + 0.5f - half_n;
+                            const float dl0 = __fmaf_rn(-xc, cc_hi, brow) - __fmaf_rn(xc, cc_lo, cy);
+                            // rows past the warp's last one weigh 0 (the one-
+                            // image kernel reads 0 there instead: the same sums)
+                            const float u0 = live ? __saturatef(__fmaf_rn(-fabsf(dl0), wa, wb)) : 0.f;
+                            const float u1 = live ? __saturatef(__fmaf_rn(-fabsf(dl0 - ccf), wa, wb)) : 0.f;
+                            w0[r] = make_float2(u0, u0);
+                            w1[r] = make_float2(u1, u1);
+                            brow += dbrow;
+                            cy += dcy;
+                            xs += dxs;
                         }
-                        const float rs = __fmaf_rn(w0[0], v0[0], __fmaf_rn(w1[0], v1[0],
-                                         __fmaf_rn(w0[1], v0[1], w1[1] * v1[1])));
-                        const float y = rs - cmp[b];                     // Kahan step
-                        const float tt = s[b] + y;
-                        cmp[b] = (tt - s[b]) - y;
-                        s[b] = tt;
+#pragma unroll
+                        for (int q = 0; q < kP; ++q) {
+                            // images 2q, 2q + 1 (inactive ones are computed
+                            // and not written: the pair stays uniform)
+                            const float *pa = stage + (2 * q) * (kBoxW * kBoxH);
+                            const float *pb = pa + kBoxW * kBoxH;
+                            const float2 v00 = make_float2(pa[li[0]], pb[li[0]]);
+                            const float2 v01 = make_float2(pa[li[0] + 1], pb[li[0] + 1]);
+                            const float2 v10 = make_float2(pa[kBoxFloats + li[1]], pb[kBoxFloats + li[1]]);
+                            const float2 v11 = make_float2(pa[kBoxFloats + li[1] + 1], pb[kBoxFloats + li[1] + 1]);
+                            float2 x = h == 0 ? __fmul2_rn(w0[0], v00) : __ffma2_rn(w0[0], v00, acc[q]);
+                            x = __ffma2_rn(w1[0], v01, x);
+                            x = __ffma2_rn(w0[1], v10, x);
+                            acc[q] = __ffma2_rn(w1[1], v11, x);
+                        }
+                        if (h == 1) {
+#pragma unroll
+                            for (int q = 0; q < kP; ++q) {                 // Kahan step
+                                const float2 y = __ffma2_rn(c2[q], neg1, acc[q]);
+                                const float2 tt = __fadd2_rn(s2[q], y);
+                                c2[q] = __ffma2_rn(y, neg1, __ffma2_rn(s2[q], neg1, tt));
+                                s2[q] = tt;
+                            }
+                        }
                     }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&empty[st]));
+                    if (++st == kStages) { st = 0; ph ^= 1; }
                 }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&empty[st]));
             }
         }
 #pragma unroll
-        for (int b = 0; b < kIB; ++b) {
-            red_s[w][b][lane] = s[b];
-            red_c[w][b][lane] = cmp[b];
+        for (int q = 0; q < kP; ++q) {
+            red[w][2 * q][lane] = s2[q].x - c2[q].x;
+            red[w][2 * q + 1][lane] = s2[q].y - c2[q].y;
         }
         asm volatile("bar.sync 1, %0;" ::"r"(32 * kNW) : "memory");
         bool mine = false;
@@ -330,7 +356,7 @@ k_project_f32_tma(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P, 
             float S = 0.f, Cc = 0.f;
 #pragma unroll
             for (int i = 0; i < kNW; ++i) {
-                const float y = (red_s[i][b][lane] - red_c[i][b][lane]) - Cc;
+                const float y = red[i][b][lane] - Cc;
                 const float tt = S + y;
                 Cc = (tt - S) - y;
                 S = tt;
@@ -347,7 +373,9 @@ k_project_f32_tma(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P, 
         }
         asm volatile("bar.sync 1, %0;" ::"r"(32 * kNW) : "memory");
     }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicExch(&g_tma_error, 2);
+    // an aborted CTA read stages that never arrived: its box checks mean nothing
+    const bool aborted = *abort_v;
+    if (__any_sync(0xffffffffu, bad) && lane == 0 && !aborted) atomicExch(&g_tma_error, 2);
 }
 
 // ---------------------------------------------------------------------------
@@ -387,6 +415,17 @@ static bool encode_pool_map(CUtensorMap *m, const void *base, int n, int64_t cou
 
 bool project_tma_available() { return tensor_map_encoder() != nullptr; }
 
+// Test hook for the bounded waits: with WMG_TEST_STALL_STAGED_COPIES=1 in the
+// environment at launch time, the producer warp issues no copies and the
+// consumers' waits run out after kStallWaitCycles, so the timeout path
+// (abort, error flag, WMG_ERR_TIMEOUT at the next synchronising call) runs
+// without any fault: every wait is bounded and no copy is in flight.
+static bool stall_requested()
+{
+    const char *v = std::getenv("WMG_TEST_STALL_STAGED_COPIES");
+    return v && v[0] == '1';
+}
+
 bool launch_project_f32_tma(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles, const PjArgs &a,
                             int n, int64_t count, cudaStream_t st)
 {
@@ -402,7 +441,9 @@ bool launch_project_f32_tma(const GeomDev *G, const ProbDev *P, const int4 *tile
     });
     count_launches(1);
     const int grid = min(ntiles, 2 * num_sms());               // two CTAs per SM
-    k_project_f32_tma<<<grid, 32 * (kNW + 1), kSmemBytes, st>>>(G, P, tiles, ntiles, a, mi, mt);
+    const bool stall = stall_requested();
+    k_project_f32_tma<<<grid, 32 * (kNW + 1), kSmemBytes, st>>>(G, P, tiles, ntiles, a, mi, mt, stall ? 1 : 0,
+                                                                stall ? kStallWaitCycles : kWaitCycles);
     return true;
 }
 

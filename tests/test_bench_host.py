@@ -18,7 +18,7 @@ def test_roofline_entry_arithmetic():
     assert abs(r["achieved"] - flops / 1e12) < 1e-9
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
     assert abs(r["peak"] - 152 * 128 * 2 * 2070e6 / 1e12) < 1e-9
-    gbs = 256 * (2 * 65536 + 65340) * 4 / 2.3e-3 / 1e9
+    gbs = 256 * (65536 + 65340) * 4 / 2.3e-3 / 1e9          # s (N + M)
     assert abs(r["algorithmic_gbs"] - gbs) < 1e-6
     assert 0.0 < r["hbm_frac_of_measured"] < 0.1
 

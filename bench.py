@@ -133,23 +133,104 @@ def whole_job_value(batch: int, world: int, steps: int, t_total: float) -> float
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (one reconstruction of the workload, FP64, 1 thread)
 # ---------------------------------------------------------------------------
-def cpu_baseline(problem) -> dict:
-    import oracle
+def host_cpu() -> dict:
+    """The host's CPU model, logical core count and the cores this process
+    may run on."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "processor name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    try:
+        allowed = len(os.sched_getaffinity(0))
+    except AttributeError:
+        allowed = os.cpu_count()
+    return {"cpu_model": model or "unknown", "nproc": os.cpu_count(), "cores_allowed": allowed}
 
+
+_ORACLE_BARRIER = None
+
+
+def _oracle_worker_init(barrier):
+    global _ORACLE_BARRIER
+    _ORACLE_BARRIER = barrier
+
+
+def _oracle_solve(seed_index: int, cpu: int) -> dict:
+    """One oracle reconstruction of problem `seed_index` of the workload,
+    pinned to host core `cpu`: plan setup, then (after every worker of the
+    pool has finished its setup) the timed WMG-GMRES(20) solve."""
+    import oracle
+    try:
+        os.sched_setaffinity(0, {cpu})
+        pinned = True
+    except (AttributeError, OSError):
+        pinned = False
+    problem = workload_problems(seed_index + 1, 0)[seed_index]
     op = oracle.Op(problem.n, problem.m, problem.D)
     b0 = op.project(problem.image())
     b = b0 + problem.noise * np.abs(b0).max() * problem.noise_unit()
     t0 = time.perf_counter()
     M = oracle.Wmg(op, LEVELS, NU1, NU2, 1.0, 0.0, oracle.CYCLE_HYBRID, HYB)
     setup = time.perf_counter() - t0
+    if _ORACLE_BARRIER is not None:
+        _ORACLE_BARRIER.wait()
+    t_start = time.time()
     t0 = time.perf_counter()
     x, k, hist = oracle.gmres(op, b, MAX_ITER, RESTART, RTOL, 0.0, M)
     solve = time.perf_counter() - t0
-    return {"value": 1.0 / solve, "unit": "recon/s", "cores": 1, "kind": "oracle",
-            "sample": (f"1 reconstruction of the workload (problem seed {problem.seed}): WMG-GMRES(20) "
-                       f"to {RTOL:g} in {k} iterations, {solve:.1f} s; plan setup {setup:.1f} s "
-                       "excluded like the GPU plan's"),
-            "iters": int(k), "setup_s": setup}
+    return {"solve_s": solve, "setup_s": setup, "iters": int(k), "seed": problem.seed, "pinned": pinned,
+            "start": t_start, "end": time.time()}
+
+
+def cpu_baseline(problem, all_cores: bool = True) -> dict:
+    """The oracle timed on the host: one reconstruction pinned to one core,
+    and (all_cores) one reconstruction per allowed core run at once, each
+    pinned to its core (independent problems; recon/s = reconstructions /
+    the span from the first solve's start to the last one's end). Plan setup
+    is excluded like the GPU plan's. Runs in spawned processes (the calling
+    process holds a CUDA context)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    info = host_cpu()
+    try:
+        cores = sorted(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = list(range(os.cpu_count() or 1))
+    ctx = mp.get_context("spawn")
+    with cf.ProcessPoolExecutor(1, mp_context=ctx) as ex:
+        one = ex.submit(_oracle_solve, 0, cores[0]).result()
+    line = {"value": 1.0 / one["solve_s"], "unit": "recon/s", "cores": 1, "kind": "oracle",
+            "sample": (f"1 reconstruction of the workload (problem seed {one['seed']}): WMG-GMRES(20) "
+                       f"to {RTOL:g} in {one['iters']} iterations, {one['solve_s']:.1f} s on one core"
+                       f"{' (pinned)' if one['pinned'] else ''}; plan setup {one['setup_s']:.1f} s excluded "
+                       "like the GPU plan's"),
+            "iters": one["iters"], "setup_s": one["setup_s"], **info}
+    if all_cores and len(cores) > 1:
+        n = len(cores)
+        barrier = ctx.Barrier(n)
+        with cf.ProcessPoolExecutor(n, mp_context=ctx, initializer=_oracle_worker_init,
+                                    initargs=(barrier,)) as ex:
+            rs = list(ex.map(_oracle_solve, range(n), cores))
+        span = max(r["end"] for r in rs) - min(r["start"] for r in rs)
+        line["all_cores"] = {"value": n / span, "unit": "recon/s", "cores": n,
+                             "sample": f"{n} independent reconstructions (problems 0..{n - 1}), one per core, "
+                                       f"solved at once; mean {np.mean([r['solve_s'] for r in rs]):.1f} s each"}
+    return line
 
 
 def run_reference(args, rank, world):
@@ -159,7 +240,7 @@ def run_reference(args, rank, world):
     per = []
     base = None
     for _ in range(max(1, args.warmup and 0) + args.steps):
-        base = cpu_baseline(P)
+        base = cpu_baseline(P, all_cores=False)
         per.append(1.0 / base["value"])
     t = float(np.mean(per))
     val = 1.0 / t
@@ -169,7 +250,7 @@ def run_reference(args, rank, world):
             "config": {"workload": "256x256_180ang_363det_noise1pct", "batch": 1, "solver": "WMG-GMRES(20)",
                        "levels": LEVELS, "precision": "fp64 oracle (CPU)"},
             "cpu_baseline": {"value": val, "unit": "recon/s", "cores": 1, "kind": "oracle",
-                             "sample": base["sample"]},
+                             "sample": base["sample"], **host_cpu()},
             "e2e": {"value": val, "unit": "recon/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -381,7 +462,12 @@ def run_ours(args, rank, world, local):
     prof = plan.profile_step(b, x, MAX_ITER, RTOL, RESTART)
     roofline = None
     if prof:
+        peaks = {name: wmg.wmg_measure_peak(kind) for name, kind in
+                 (("fp32_fma", wmg.PEAK_FP32_FMA), ("fp32_fma_paired", wmg.PEAK_FP32_FMA2),
+                  ("fp64_fma", wmg.PEAK_FP64_FMA))}
+        prof["fp32_fma_tflops_measured"] = max(peaks["fp32_fma"], peaks["fp32_fma_paired"])
         roofline = roofline_entry(prof, P0, B)
+        roofline["measured_peaks_tflops"] = peaks
     comparator = None
     if not args.no_comparator and rank == 0:
         try:
@@ -889,7 +975,11 @@ def roofline_entry(prof: dict, P0, B: int) -> dict:
     achieved = flops_per_launch / (p["mean_ms"] * 1e-3) / 1e12
     peaks = load_peaks()
     clk = peaks.get("sm_max_mhz", 2070.0)
-    peak = 152 * 128 * 2 * clk * 1e6 / 1e12
+    derived = 152 * 128 * 2 * clk * 1e6 / 1e12
+    # measured FP32 multiply-add peak (the better of one and two multiply-adds
+    # per instruction) when given, else unit counts x the maximum clock
+    measured = prof.get("fp32_fma_tflops_measured")
+    peak = measured if measured else derived
     # the same launch as an HBM client: algorithmic bytes = s (N + M), the
     # FP32 input read once and the output written once
     n_in = P0.N if name == "project" else P0.M
@@ -902,7 +992,10 @@ def roofline_entry(prof: dict, P0, B: int) -> dict:
             "algorithmic_gbs": gbs, "hbm_frac_of_measured": (gbs / hbm) if hbm else None,
             "note": (f"{p['launches']} launches, mean {p['mean_ms']:.3f} ms, "
                      f"{nnz_per_image * p['images_per_launch'] / (p['mean_ms'] * 1e-3) / 1e9:.0f} Gnnz/s; "
-                     f"peak derived: 152 SMs x 128 FP32 lanes x 2 FLOP x {clk:.0f} MHz; as an HBM client "
+                     + (f"peak measured (FP32 multiply-add chains, best of scalar and paired); derived "
+                        f"152 SMs x 128 FP32 lanes x 2 FLOP x {clk:.0f} MHz = {derived:.1f}; " if measured else
+                        f"peak derived: 152 SMs x 128 FP32 lanes x 2 FLOP x {clk:.0f} MHz; ")
+                     + "as an HBM client "
                      f"{gbs:.0f} GB/s of algorithmic bytes"
                      + (f" = {gbs / hbm:.3f} of the measured {hbm:.0f} GB/s" if hbm else ""))}
 

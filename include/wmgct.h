@@ -464,6 +464,20 @@ typedef struct wmg_profile_stats {
 int32_t wmg_profile_begin(wmg_plan *plan);
 int32_t wmg_profile_end(wmg_plan *plan, wmg_profile_stats *out, void *stream);
 
+/* Measured arithmetic peak of the current GPU, for the roofline of the
+ * library's ALU-bound kernels (the matrix-free projector and backprojector
+ * recompute their weights and are bound by FP32 arithmetic and issue, not by
+ * memory). The paper has no counterpart: this is measurement support.
+ * kind: WMG_PEAK_FP32_FMA (one FP32 multiply-add per instruction),
+ * WMG_PEAK_FP32_FMA2 (the paired FP32 multiply-add, two per instruction) or
+ * WMG_PEAK_FP64_FMA. *tflops receives 2 x multiply-adds per second / 1e12,
+ * the best of five timed launches of independent multiply-add chains (8
+ * CTAs of 256 threads per SM, no memory traffic). Synchronising on
+ * `stream`; allocates 16 bytes of device memory for the duration of the call.
+ * WMG_ERR_INVALID_ARG for an unknown kind or a NULL result pointer. */
+enum { WMG_PEAK_FP32_FMA = 0, WMG_PEAK_FP32_FMA2 = 1, WMG_PEAK_FP64_FMA = 2 };
+int32_t wmg_measure_peak(int32_t kind, double *tflops, void *stream);
+
 /* Forward projection b = W x that allocates no device memory, for callers
  * that cannot call cudaMalloc once they are running: an acquisition loop that
  * reserves all its device memory at start-up so that nothing can fail or

@@ -111,6 +111,7 @@ _SIGNATURES = {
     "wmg_profile_begin": (_i32, [_vp]),
     "wmg_profile_end": (_i32, [_vp, C.POINTER(wmg_profile_stats), _vp]),
     "wmg_project_noalloc": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp]),
+    "wmg_measure_peak": (_i32, [_i32, C.POINTER(_dbl), _vp]),
     "wmg_batch_create": (_i32, [C.POINTER(wmg_geom), C.POINTER(wmg_opts), _i32, _vp, C.POINTER(_vp)]),
     "wmg_batch_destroy": (_i32, [_vp]),
     "wmg_batch_sizes": (_i32, [_vp, _i32, C.POINTER(_i64), C.POINTER(_i64)]),
@@ -282,6 +283,21 @@ def use_torch_allocator(enable: bool = True) -> None:
         _allocator_refs = (_allocator_refs or ()) + (refs,)
     else:
         wmg_set_allocator(None, None)
+
+
+PEAK_FP32_FMA, PEAK_FP32_FMA2, PEAK_FP64_FMA = 0, 1, 2
+
+
+def wmg_measure_peak(kind, stream=None) -> float:
+    """Measured multiply-add peak of the current GPU in TFLOP/s (2 FLOP per
+    multiply-add): PEAK_FP32_FMA, PEAK_FP32_FMA2 (paired FP32) or
+    PEAK_FP64_FMA."""
+    if stream is None:
+        import torch
+        stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    v = C.c_double()
+    _check(lib().wmg_measure_peak(int(kind), C.byref(v), stream))
+    return v.value
 
 
 def wmg_project_noalloc(n, m, D, x, b, stream=None):

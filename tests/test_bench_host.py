@@ -1,5 +1,6 @@
 """Host-side arithmetic of bench.py's roofline entry (no GPU): the dominant
-kernel's achieved FP32 rate, its fraction of the derived peak, and its
+kernel's achieved FP32 rate, its fraction of the measured (else derived)
+peak, and its
 algorithmic HBM bytes per second."""
 import bench
 
@@ -21,6 +22,15 @@ def test_roofline_entry_arithmetic():
     gbs = 256 * (65536 + 65340) * 4 / 2.3e-3 / 1e9          # s (N + M)
     assert abs(r["algorithmic_gbs"] - gbs) < 1e-6
     assert 0.0 < r["hbm_frac_of_measured"] < 0.1
+
+
+def test_roofline_uses_the_measured_peak_when_given():
+    prof = {"nnz_per_image": 15149028.0, "fp32_fma_tflops_measured": 75.0,
+            "project": {"launches": 60, "total_ms": 138.0, "mean_ms": 2.3, "images_per_launch": 256.0},
+            "backproject": {"launches": 60, "total_ms": 120.0, "mean_ms": 2.0, "images_per_launch": 256.0}}
+    r = bench.roofline_entry(prof, P0, 256)
+    assert r["peak"] == 75.0 and abs(r["frac"] - r["achieved"] / 75.0) < 1e-12
+    assert "peak measured" in r["note"]
 
 
 def test_whole_job_value():

@@ -49,6 +49,8 @@ _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 
 CYCLE_ADDITIVE = 0
 CYCLE_HYBRID = 1
+CYCLE_SYMMETRIC = 2
+CYCLE_MULTIPLICATIVE = 3
 
 
 def build(force: bool = False) -> str:
@@ -256,8 +258,12 @@ def packet_synthesis(c, n: int, L: int) -> np.ndarray:
 class Wmg:
     """WMG preconditioner B for A = W^T W + lambda I: `levels` = l (L = l-1
     Haar levels, leaves nc x nc with nc = n / 2^L), nu1/nu2 l1-Jacobi sweeps
-    (damping omega), cycle ADDITIVE or HYBRID (residual update after the LL
-    band at depths < hybrid_depth). factor=False keeps the unfactored leaf
+    (damping omega), cycle ADDITIVE, HYBRID (residual update after the LL
+    band at depths < hybrid_depth), SYMMETRIC (hybrid, then the LL band once
+    more from the residual of the whole node correction) or MULTIPLICATIVE
+    (the fully multiplicative WTG of eq. wmg at depths < hybrid_depth: each
+    of LL, LH, HL, HH corrected from the residual the corrections before it
+    leave). factor=False keeps the unfactored leaf
     matrices for inspection (apply is then invalid)."""
 
     def __init__(self, op: Op, levels: int, nu1: int = 0, nu2: int = 0, omega: float = 1.0,

@@ -796,9 +796,32 @@ static void wtg_correct(const or_wmg *M, int d, int *path, int64_t leaf, const d
         e[id] = malloc((size_t)sub * sizeof(double));
     }
     haar_analysis_step(side, cp, c);
+    if (M->cycle == 3 && d < M->hdepth) {
+        /* fully multiplicative WTG (eq. wmg): the bands LL, LH, HL, HH in
+         * turn, each corrected from the node residual left by the
+         * corrections before it, c_p - A_p sum_{j < id} I_{2h,j}^h e_j */
+        double *v = malloc((size_t)side * side * sizeof(double));
+        double *w = malloc((size_t)side * side * sizeof(double));
+        for (int id = 0; id < 4; id++) {
+            if (id > 0) {
+                double *in[4] = {NULL, NULL, NULL, NULL};
+                for (int j = 0; j < id; j++) in[j] = e[j];
+                haar_synthesis_step(side, in, v);
+                node_operator(M, d, path, v, w);
+                for (int64_t i = 0; i < (int64_t)side * side; i++) w[i] = cp[i] - w[i];
+                haar_analysis_step(side, w, c);
+            }
+            path[d] = id;
+            wtg_correct(M, d + 1, path, leaf * 4 + id, c[id], e[id]);
+        }
+        haar_synthesis_step(side, e, ep);
+        free(v); free(w);
+        for (int id = 0; id < 4; id++) { free(c[id]); free(e[id]); }
+        return;
+    }
     path[d] = 0;
     wtg_correct(M, d + 1, path, leaf * 4 + 0, c[0], e[0]);
-    if (M->cycle >= 1 && d < M->hdepth) {
+    if ((M->cycle == 1 || M->cycle == 2) && d < M->hdepth) {
         double *v = malloc((size_t)side * side * sizeof(double));
         double *w = malloc((size_t)side * side * sizeof(double));
         double *in[4] = {e[0], NULL, NULL, NULL};

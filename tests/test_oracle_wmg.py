@@ -54,25 +54,28 @@ def test_single_level_is_exact_inverse():
     assert k == 1 and hist[-1] < 1e-10
 
 
-def wtg_dense(A, c, side, depth, L, hybrid_depth, symmetric):
+def wtg_dense(A, c, side, depth, L, hybrid_depth, symmetric, multiplicative=False):
     """The WTG correction scheme on A e = c, recursively: LL band first, then
     (hybrid) one residual recomputation, then LH, HL, HH; coarse operators by
     Galerkin products I_id A I_id^T; exact solves at depth L. With `symmetric`
-    the LL band is corrected once more from the residual of the whole step."""
+    the LL band is corrected once more from the residual of the whole step;
+    with `multiplicative` the residual is recomputed before every band."""
     if depth == L:
         return np.linalg.solve(A, c)
     ops = band_ops(side)
     sub = [B @ A @ B.T for B in ops]
-    x = ops[0].T @ wtg_dense(sub[0], ops[0] @ c, side // 2, depth + 1, L, hybrid_depth, symmetric)
+    inner = (lambda Ai, ci: wtg_dense(Ai, ci, side // 2, depth + 1, L, hybrid_depth, symmetric,
+                                      multiplicative))
+    x = ops[0].T @ inner(sub[0], ops[0] @ c)
     active = depth < hybrid_depth
     r = c - A @ x if active else c
     for i in (1, 2, 3):
-        x = x + ops[i].T @ wtg_dense(sub[i], ops[i] @ r, side // 2, depth + 1, L, hybrid_depth,
-                                     symmetric)
+        if multiplicative and active and i > 1:
+            r = c - A @ x
+        x = x + ops[i].T @ inner(sub[i], ops[i] @ r)
     if symmetric and active:
         r = c - A @ x
-        x = x + ops[0].T @ wtg_dense(sub[0], ops[0] @ r, side // 2, depth + 1, L, hybrid_depth,
-                                     symmetric)
+        x = x + ops[0].T @ inner(sub[0], ops[0] @ r)
     return x
 
 
@@ -96,6 +99,9 @@ CASES = [  # levels, nu1, nu2, cycle, hybrid_depth, lam
     (3, 0, 0, 2, 2, 0.0),
     (4, 1, 1, 2, 2, 0.2),
     (3, 2, 1, oracle.CYCLE_HYBRID, 1, 0.0),
+    (3, 0, 0, oracle.CYCLE_MULTIPLICATIVE, 2, 0.0),
+    (4, 0, 0, oracle.CYCLE_MULTIPLICATIVE, 1, 0.0),
+    (4, 1, 1, oracle.CYCLE_MULTIPLICATIVE, 3, 0.3),
 ]
 
 
@@ -111,7 +117,8 @@ def test_wmg_apply_matches_dense_wtg(levels, nu1, nu2, cycle, hd, lam):
     for _ in range(3):
         s = rng.standard_normal(op.N)
         want = smoothed_dense(A, s, Dinv, nu1, nu2, 1.0,
-                              lambda r: wtg_dense(A, r, op.n, 0, L, hyb_depth, cycle == 2))
+                              lambda r: wtg_dense(A, r, op.n, 0, L, hyb_depth, cycle == 2,
+                                                  cycle == oracle.CYCLE_MULTIPLICATIVE))
         got = wmg.apply(s)
         assert np.abs(got - want).max() < 1e-9 * np.abs(want).max()
 
@@ -158,3 +165,15 @@ def test_leaf_without_rays_is_not_spd_unless_regularised():
     reg = oracle.Wmg(op, 2, lam=0.1, factor=False)
     for k in range(reg.K):
         assert np.linalg.eigvalsh(reg.leaf(k)).min() >= 0.1 * (1 - 1e-12)
+
+
+def test_two_level_multiplicative_cycle_is_the_wtg_propagator():
+    # two levels, the multiplicative rule at the root, exact band solves: the
+    # error propagator I - B A is eq. wmg's product of the four band
+    # corrections, built densely from the Haar band restrictions
+    op = oracle.Op(16, 20, 23)
+    for lam in (0.0, 0.4):
+        A = dense_A(op, lam)
+        B = dense_B(oracle.Wmg(op, 2, 0, 0, 1.0, lam, oracle.CYCLE_MULTIPLICATIVE, 1), op.N)
+        E = oracle.wtg_propagator(op, lam)
+        assert np.abs((np.eye(op.N) - B @ A) - E).max() < 1e-9

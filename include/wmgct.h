@@ -69,6 +69,13 @@ extern "C" {
                                    LL band at every node above hybrid_depth */
 #define WMG_CYCLE_SYMMETRIC  2  /* hybrid followed by a second LL correction
                                    (LL, rest, LL): symmetric, for CGLS */
+#define WMG_CYCLE_MULTIPLICATIVE 3  /* Section 3.1.2, eq. wmg: the fully
+                                   multiplicative WTG at every node above
+                                   hybrid_depth: LL, LH, HL, HH corrected in
+                                   turn, each from the residual the corrections
+                                   before it leave (three band-local residual
+                                   updates per node); not symmetric: for GMRES
+                                   and BiCGStab */
 
 #define WMG_KERNEL_STRIP   0  /* w_ij = length of line i inside pixel j (exact) */
 #define WMG_KERNEL_JOSEPH  1  /* Joseph's kernel (Section 2.1): the line sampled

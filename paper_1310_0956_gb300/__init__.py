@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "INVALID_ARG", -2: "OOM", -3: "
                 -4: "LEAF_NOT_SPD", -5: "BREAKDOWN", -6: "TIMEOUT", -7: "NAN", -8: "REJECTED"}
 
 PREC_F64, PREC_F32 = 0, 1
-CYCLE_ADDITIVE, CYCLE_HYBRID, CYCLE_SYMMETRIC = 0, 1, 2
+CYCLE_ADDITIVE, CYCLE_HYBRID, CYCLE_SYMMETRIC, CYCLE_MULTIPLICATIVE = 0, 1, 2, 3
 SOLVER_SIRT, SOLVER_CGLS, SOLVER_GMRES, SOLVER_BICGSTAB = 0, 1, 2, 3
 KERNEL_STRIP, KERNEL_JOSEPH = 0, 1          # W: exact intersection lengths, or Joseph's kernel
 REQ_QUEUED, REQ_RUNNING, REQ_DONE = 0, 1, 2

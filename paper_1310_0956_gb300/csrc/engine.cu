@@ -478,10 +478,15 @@ static std::vector<int> make_key(int tag, int d, const std::vector<int> &nodes, 
 
 // Band-update group tables: one virtual image per (slot, node); it reads the
 // slot's correction coefficients and writes the slot's residual coefficients.
+// Band-local products of a group of nodes. mode 0: the LL child in, the
+// three other children out (the hybrid step, and the multiplicative cycle's
+// first); 1: the whole node in, its LL child out (the symmetric closing
+// step); 2, 3: child 1 (LH) or 2 (HL) in, the children after it out (the
+// multiplicative cycle's later steps).
 static ProbSet *band_set(wmg_plan *pl, int d, const std::vector<int> &nodes, const std::vector<int> &slots,
-                         bool full_in, cudaStream_t st)
+                         int mode, cudaStream_t st)
 {
-    const std::vector<int> key = make_key(full_in ? 1 : 0, d, nodes, slots);
+    const std::vector<int> key = make_key(mode, d, nodes, slots);
     auto it = pl->bands.find(key);
     if (it != pl->bands.end()) return it->second.get();
     auto ps = std::make_unique<ProbSet>();
@@ -499,10 +504,13 @@ static ProbSet *band_set(wmg_plan *pl, int d, const std::vector<int> &nodes, con
             oi += G.N; os += G.M;
             const int lo = node_lo(L, d, q), hi = node_hi(L, d, q);
             const int ll_hi = node_hi(L, d + 1, 4 * q);
-            if (full_in) {          // symmetric closing step: the whole node in, its LL child out
+            if (mode == 1) {        // symmetric closing step: the whole node in, its LL child out
                 pd.kin0 = lo; pd.kin1 = hi; pd.kout0 = lo; pd.kout1 = ll_hi;
-            } else {                // hybrid step: the LL child in, the three other children out
+            } else if (mode == 0) { // hybrid step: the LL child in, the three other children out
                 pd.kin0 = lo; pd.kin1 = ll_hi; pd.kout0 = ll_hi; pd.kout1 = hi;
+            } else {                // child mode - 1 in, the children after it out
+                pd.kin0 = node_lo(L, d + 1, 4 * q + mode - 1); pd.kin1 = node_hi(L, d + 1, 4 * q + mode - 1);
+                pd.kout0 = pd.kin1; pd.kout1 = hi;
             }
         }
     build_tiles(pl, *ps);
@@ -553,9 +561,9 @@ __global__ void k_coef_add(double *E, const double *E2, const longlong2 *segs, i
 // every slot and node, C[out range] -= Q_out^T (W^T W + lambda) Q_in E[in range].
 template <class T>
 static int32_t band_update(wmg_plan *pl, int d, const std::vector<int> &nodes, const std::vector<int> &slots,
-                           bool full_in, DevBuf &Cb, DevBuf &Eb, cudaStream_t st)
+                           int mode, DevBuf &Cb, DevBuf &Eb, cudaStream_t st)
 {
-    ProbSet *bs = band_set(pl, d, nodes, slots, full_in, st);
+    ProbSet *bs = band_set(pl, d, nodes, slots, mode, st);
     if (!bs) return fail(WMG_ERR_OOM, "band tables");
     int64_t VN = 0, VM = 0;
     for (const ProbDev &pd : bs->h) { VN += pl->geos[pd.geom]->N; VM += pl->geos[pd.geom]->M; }
@@ -614,17 +622,30 @@ static int32_t coarse(wmg_plan *pl, int d, const std::vector<int> &nodes, const 
         lls.push_back(4 * q);
         for (int c = 1; c < 4; ++c) rests.push_back(4 * q + c);
     }
+    if (pl->opts.cycle == WMG_CYCLE_MULTIPLICATIVE) {
+        // eq. wmg: LL, LH, HL, HH in turn; before each of the last three, the
+        // residual of the children still to come loses A_p times the
+        // correction just made
+        int32_t rc = coarse<T>(pl, d + 1, lls, deeper, Cb, Eb, st);
+        for (int c = 1; c < 4 && !rc; ++c) {
+            std::vector<int> kids;
+            for (int q : nodes) kids.push_back(4 * q + c);
+            if ((rc = band_update<T>(pl, d, nodes, deeper, c == 1 ? 0 : c, Cb, Eb, st))) break;
+            rc = coarse<T>(pl, d + 1, kids, deeper, Cb, Eb, st);
+        }
+        return rc;
+    }
     const bool sym = pl->opts.cycle == WMG_CYCLE_SYMMETRIC;
     const size_t cbytes = (size_t)pl->Ntot * sizeof(double);
     if (sym) cudaMemcpyAsync(pl->csave[d]->p, Cb.p, cbytes, cudaMemcpyDeviceToDevice, st);
     int32_t rc = coarse<T>(pl, d + 1, lls, deeper, Cb, Eb, st);
     if (rc) return rc;
-    if ((rc = band_update<T>(pl, d, nodes, deeper, false, Cb, Eb, st))) return rc;
+    if ((rc = band_update<T>(pl, d, nodes, deeper, 0, Cb, Eb, st))) return rc;
     if ((rc = coarse<T>(pl, d + 1, rests, deeper, Cb, Eb, st))) return rc;
     if (sym) {
         DevBuf &C2 = *pl->c2[d], &E2 = *pl->e2[d];
         cudaMemcpyAsync(C2.p, pl->csave[d]->p, cbytes, cudaMemcpyDeviceToDevice, st);
-        if ((rc = band_update<T>(pl, d, nodes, deeper, true, C2, Eb, st))) return rc;
+        if ((rc = band_update<T>(pl, d, nodes, deeper, 1, C2, Eb, st))) return rc;
         if ((rc = coarse<T>(pl, d + 1, lls, deeper, C2, E2, st))) return rc;
         const std::vector<int> key = make_key(3, d, nodes, deeper);
         auto it = pl->segsets.find(key);
@@ -780,7 +801,7 @@ int32_t validate(const wmg_geom *g, const wmg_opts *o)
     if (o->levels >= 1 && nc * nc > 256) return fail(WMG_ERR_INVALID_ARG, "leaf side n/2^(levels-1) must be <= 16");
     if ((1 << L) > 128) return fail(WMG_ERR_INVALID_ARG, "block side 2^(levels-1) must be <= 128");
     if (o->nu1 < 0 || o->nu2 < 0 || o->lambda < 0 || o->hybrid_depth < 0 ||
-        o->cycle < WMG_CYCLE_ADDITIVE || o->cycle > WMG_CYCLE_SYMMETRIC ||
+        o->cycle < WMG_CYCLE_ADDITIVE || o->cycle > WMG_CYCLE_MULTIPLICATIVE ||
         (o->precision != WMG_PREC_F64 && o->precision != WMG_PREC_F32))
         return fail(WMG_ERR_INVALID_ARG, "invalid options");
     if ((int64_t)g->n * g->n > (int64_t)1 << 30 || (int64_t)g->m * g->D > (int64_t)1 << 31)
@@ -1912,7 +1933,8 @@ static int32_t check_solve_args(wmg_plan *pl, int32_t solver, int32_t preconditi
         return fail(WMG_ERR_INVALID_ARG, "wmg_solve: restart must be in [1, 64]");
     if (preconditioned && !pl->has_wmg() && solver != WMG_SOLVER_SIRT)
         return fail(WMG_ERR_INVALID_ARG, "wmg_solve: the plan has no WMG levels to precondition with");
-    if (solver == WMG_SOLVER_CGLS && preconditioned && pl->opts.cycle == WMG_CYCLE_HYBRID)
+    if (solver == WMG_SOLVER_CGLS && preconditioned &&
+        (pl->opts.cycle == WMG_CYCLE_HYBRID || pl->opts.cycle == WMG_CYCLE_MULTIPLICATIVE))
         return fail(WMG_ERR_INVALID_ARG, "CGLS needs a symmetric preconditioner (ADDITIVE or SYMMETRIC cycle)");
     return WMG_OK;
 }

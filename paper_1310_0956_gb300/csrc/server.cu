@@ -680,7 +680,7 @@ extern "C" int32_t wmg_server_create(const wmg_server_config *cfg, void *stream,
     if (cfg->max_slots < 1 || cfg->max_iter < 1 || cfg->restart < 1 || cfg->restart > 64 || cfg->hbm_budget <= 0 ||
         cfg->state_bytes < 0 || cfg->state_bytes > cfg->hbm_budget || cfg->sino_ratio < 0 ||
         (o.precision != WMG_PREC_F64 && o.precision != WMG_PREC_F32) || o.cycle < WMG_CYCLE_ADDITIVE ||
-        o.cycle > WMG_CYCLE_SYMMETRIC || o.nu1 < 0 || o.nu2 < 0 || o.hybrid_depth < 0)
+        o.cycle > WMG_CYCLE_MULTIPLICATIVE || o.nu1 < 0 || o.nu2 < 0 || o.hybrid_depth < 0)
         return fail(WMG_ERR_INVALID_ARG, "wmg_server_create: invalid configuration");
     auto s = std::make_unique<wmg_server>();
     s->cfg = *cfg;

@@ -109,6 +109,9 @@ CYCLES = [  # levels, nu1, nu2, cycle, hybrid depth, lambda
     (4, 1, 1, wmg.CYCLE_HYBRID, 3, 0.0),
     (3, 1, 1, wmg.CYCLE_SYMMETRIC, 2, 0.0),
     (4, 2, 1, wmg.CYCLE_SYMMETRIC, 2, 0.1),
+    (3, 0, 0, wmg.CYCLE_MULTIPLICATIVE, 2, 0.0),
+    (4, 0, 0, wmg.CYCLE_MULTIPLICATIVE, 1, 0.0),
+    (4, 1, 1, wmg.CYCLE_MULTIPLICATIVE, 3, 0.2),
 ]
 
 

@@ -57,7 +57,8 @@ def test_pcg_small_50_iterations(small, pre, cycle, hd):
     assert np.abs(hist[0] - h_ref).max() < 1e-9
 
 
-@pytest.mark.parametrize("pre,cycle,hd", [(True, wmg.CYCLE_HYBRID, 2), (True, wmg.CYCLE_ADDITIVE, 0)])
+@pytest.mark.parametrize("pre,cycle,hd", [(True, wmg.CYCLE_HYBRID, 2), (True, wmg.CYCLE_ADDITIVE, 0),
+                                          (True, wmg.CYCLE_MULTIPLICATIVE, 2)])
 def test_gmres_small(small, pre, cycle, hd):
     P, op, b = small
     M = oracle.Wmg(op, P.levels, 1, 1, 1.0, 0.0, cycle, hd)
@@ -206,4 +207,25 @@ def test_gmres_mid_f32_against_f64_oracle(mid):
                     precision=wmg.PREC_F32)
     x, info, _, _ = plan.solve(dev(b, torch.float32), wmg.SOLVER_GMRES, True, max_iter=16, rtol=0.0)
     assert info[0][0] == 16
+    assert rel(host(x), x_ref) < 1e-4
+
+
+def test_multiplicative_cycle_is_refused_by_cgls(small):
+    # the fully multiplicative WTG is not symmetric: CGLS needs an SPD B
+    P, op, b = small
+    plan = wmg.Plan(P.n, P.m, P.D, levels=P.levels, nu1=0, nu2=0, hybrid_depth=2,
+                    cycle=wmg.CYCLE_MULTIPLICATIVE)
+    with pytest.raises(wmg.WmgError) as e:
+        plan.solve(dev(b), wmg.SOLVER_CGLS, True, max_iter=5, rtol=0.0)
+    assert e.value.code == wmg.WMG_ERR_INVALID_ARG
+
+
+def test_gmres_mid_f32_multiplicative_against_f64_oracle(mid):
+    P, op, b = mid
+    M = oracle.Wmg(op, P.levels, 0, 0, 1.0, 0.0, oracle.CYCLE_MULTIPLICATIVE, 1)
+    x_ref, _, _ = oracle.gmres(op, b, 12, 20, 0.0, 0.0, M)
+    plan = wmg.Plan(P.n, P.m, P.D, levels=P.levels, nu1=0, nu2=0, hybrid_depth=1,
+                    cycle=wmg.CYCLE_MULTIPLICATIVE, precision=wmg.PREC_F32)
+    x, info, _, _ = plan.solve(dev(b, torch.float32), wmg.SOLVER_GMRES, True, max_iter=12, rtol=0.0)
+    assert info[0][0] == 12
     assert rel(host(x), x_ref) < 1e-4

@@ -304,6 +304,81 @@ __device__ __forceinline__ void bp_unit_sums(const GeomDev &g, const float *__re
     }
 }
 
+// The quarter-turn pairs of bp_unit_sums with the two angles' candidate and
+// distance arithmetic, and the compensated steps of rows r, r + 1, in paired
+// FP32 instructions (two IEEE single-precision operations, each rounded to
+// nearest, per instruction): every value is the one bp_unit_sums<COVERED,
+// true> computes, in fewer instructions.
+template <bool COVERED>
+__device__ __forceinline__ void bp_unit_sums_qpair(const GeomDev &g, const float *__restrict__ sg, float xo,
+                                                   float yo0, float (&s)[kBpRows], float (&cmp)[kBpRows])
+{
+    constexpr float kRound = 12582912.f;   // 1.5 * 2^23
+    constexpr int kRoundBits = 0x4B400000;
+    const int m = g.m, D = g.D;
+    const bool odd = D & 1;
+    const float e = odd ? 0.5f : 0.f;
+    const int kofs = odd ? (D - 1) / 2 : D / 2 - 1;
+    const float dy = (float)kBpWarps;
+    const float2 kr2 = make_float2(kRound, kRound), nkr2 = make_float2(-kRound, -kRound);
+    const float2 m1 = make_float2(-1.f, -1.f), mh = make_float2(-0.5f, -0.5f), one = make_float2(1.f, 1.f);
+    float2 s2[kBpRows / 2], c2[kBpRows / 2];
+#pragma unroll
+    for (int r = 0; r < kBpRows / 2; ++r) {
+        s2[r] = make_float2(s[2 * r], s[2 * r + 1]);
+        c2[r] = make_float2(cmp[2 * r], cmp[2 * r + 1]);
+    }
+    for (int pr = 0; pr < m / 2; ++pr) {
+        const int a0 = pr, a1 = pr + m / 2;
+        const float4 *q0 = reinterpret_cast<const float4 *>(g.angf + a0);
+        const float4 t0 = __ldg(q0), c0 = __ldg(q0 + 1);
+        const float4 t1 = make_float4(-t0.z, -t0.w, t0.x, t0.y);
+        const float l0 = c0.z;
+        const float *row0 = sg + ((int64_t)a0 * D + kofs - kRoundBits);
+        const float *row1 = sg + ((int64_t)a1 * D + kofs - kRoundBits);
+        float2 ph = make_float2(__fmaf_rn(xo, t0.x, yo0 * t0.z) - e, __fmaf_rn(xo, t1.x, yo0 * t1.z) - e);
+        float2 pc = make_float2(__fmaf_rn(xo, t0.y, yo0 * t0.w), __fmaf_rn(xo, t1.y, yo0 * t1.w));
+        const float2 dph = make_float2(dy * t0.z, dy * t1.z), dpc = make_float2(dy * t0.w, dy * t1.w);
+#pragma unroll
+        for (int r2 = 0; r2 < kBpRows / 2; ++r2) {
+            float rs[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float2 y = __fadd2_rn(__fadd2_rn(ph, pc), kr2);
+                const int b0 = __float_as_int(y.x), b1 = __float_as_int(y.y);    // m0 + kRoundBits
+                // ((y - kRound) - ph - 1/2) - pc, each step rounded as in the scalar form
+                float2 d = __ffma2_rn(ph, m1, __fadd2_rn(y, nkr2));
+                d = __ffma2_rn(pc, m1, __fadd2_rn(d, mh));
+                const float2 d1 = __fadd2_rn(d, one);
+                const float wa0 = chord_n(c0.x, c0.y, fabsf(d.x)), wb0 = chord_n(c0.x, c0.y, fabsf(d1.x));
+                const float wa1 = chord_n(c0.x, c0.y, fabsf(d.y)), wb1 = chord_n(c0.x, c0.y, fabsf(d1.y));
+                bool o00 = true, o01 = true, o10 = true, o11 = true;
+                if (!COVERED) {
+                    const int k0 = b0 - kRoundBits + kofs, k1 = b1 - kRoundBits + kofs;
+                    o00 = (unsigned)k0 < (unsigned)D; o01 = (unsigned)(k0 + 1) < (unsigned)D;
+                    o10 = (unsigned)k1 < (unsigned)D; o11 = (unsigned)(k1 + 1) < (unsigned)D;
+                }
+                const float u0 = o00 ? __ldg(row0 + b0) : 0.f, u1 = o01 ? __ldg(row0 + b0 + 1) : 0.f;
+                const float v0 = o10 ? __ldg(row1 + b1) : 0.f, v1 = o11 ? __ldg(row1 + b1 + 1) : 0.f;
+                const float x0 = __fmaf_rn(wa0, u0, __fmul_rn(wb0, u1));
+                rs[h] = __fmul_rn(__fmaf_rn(wa1, v0, __fmaf_rn(wb1, v1, x0)), l0);
+                ph = __fadd2_rn(ph, dph);
+                pc = __fadd2_rn(pc, dpc);
+            }
+            // compensated steps of rows 2 r2 and 2 r2 + 1 together
+            const float2 yk = __ffma2_rn(c2[r2], m1, make_float2(rs[0], rs[1]));
+            const float2 tt = __fadd2_rn(s2[r2], yk);
+            c2[r2] = __ffma2_rn(yk, m1, __ffma2_rn(s2[r2], m1, tt));
+            s2[r2] = tt;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kBpRows / 2; ++r) {
+        s[2 * r] = s2[r].x; s[2 * r + 1] = s2[r].y;
+        cmp[2 * r] = c2[r].x; cmp[2 * r + 1] = c2[r].y;
+    }
+}
+
 template <int EPI, bool ALL_UNIT>
 __global__ void __launch_bounds__(32 * kBpWarps, 4)
 k_backproject_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
@@ -329,10 +404,10 @@ k_backproject_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
         if (unit) {
             const bool qp = g.qpair;
             if (g.unit == 2) {
-                if (qp) bp_unit_sums<true, true>(g, sg, xo, yo0, s, cmp);
+                if (qp) bp_unit_sums_qpair<true>(g, sg, xo, yo0, s, cmp);
                 else bp_unit_sums<true, false>(g, sg, xo, yo0, s, cmp);
             } else {
-                if (qp) bp_unit_sums<false, true>(g, sg, xo, yo0, s, cmp);
+                if (qp) bp_unit_sums_qpair<false>(g, sg, xo, yo0, s, cmp);
                 else bp_unit_sums<false, false>(g, sg, xo, yo0, s, cmp);
             }
         } else {

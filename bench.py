@@ -93,6 +93,10 @@ def parse():
     ap.add_argument("--solve-case", action="store_true",
                     help="run three solves of the workload batch and exit: the case for ncu captures of the "
                          "solve's secondary kernels (Gram-Schmidt, leaf solves, Haar packets)")
+    ap.add_argument("--setup-case", default=None, metavar="N:M",
+                    help="create one FP32 plan of an N x N image and M angles (detectors and levels by the "
+                         "uneven-batch rule, hybrid depth 1), print its setup time and exit: the case for "
+                         "ncu launch lists of the leaf setup")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run 3 projector and 3 backprojector launches on a batch of 16 images of the "
                          "workload geometry (FP32) and exit: the small case for ncu captures")
@@ -1062,9 +1066,27 @@ def kernel_case():
     print(json.dumps({"kernel_case": "ok", "nnz_per_image": plan.nnz()}))
 
 
+def setup_case(spec: str):
+    import torch
+    import paper_1310_0956_gb300 as wmg
+    n, m = (int(v) for v in spec.split(":"))
+    D, levels = S.detectors_for(n), S.levels_for(n)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = wmg.Plan(n, m, D, levels=levels, nu1=0, nu2=0, hybrid_depth=1, cycle=wmg.CYCLE_HYBRID,
+                    precision=wmg.PREC_F32)
+    torch.cuda.synchronize()
+    print(json.dumps({"setup_case": f"{n}x{n}_{m}ang_{D}det", "levels": levels,
+                      "setup_s": time.perf_counter() - t0}))
+    plan.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.setup_case:
+        setup_case(args.setup_case)
+        return
     if args.kernel_case:
         kernel_case()
         return

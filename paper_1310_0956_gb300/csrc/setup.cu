@@ -223,97 +223,103 @@ static void launch_profiles(int B, int S, const GeomDev *gd, int na, int cls, in
     (void)S;
 }
 
-// Pass 2. CTA = (group of up to GB blocks along the rays' direction -- a
-// column of blocks for class 0, a row for class 1 -- and a sub-tile of 32
-// coefficients, one per lane). The members' coefficients of the angle are
-// staged in shared memory; warps take the partner blocks b2 in turn, load a
-// partner's coefficients once per ray and use them for every member b1 <= b2
-// whose ray range covers that ray. Dacc[(b1 * P + b2) * K + c] += the pair's
-// sum over shared rays (c = HY * B + HX). Row b1 of Dacc belongs to b1's
-// group only, so no two threads of a launch write the same entry.
-constexpr int kPairGroup = 4;
+// Four consecutive coefficients t .. t + 3 of a profile row (t a multiple
+// of 4; entries at or past KT read as 0).
+__device__ __forceinline__ void load4(const float *__restrict__ p, int t, int KT, float (&v)[4])
+{
+    if (t + 4 <= KT && !(KT & 3)) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(p + t));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = t + j < KT ? __ldg(p + t + j) : 0.f;
+    }
+}
+__device__ __forceinline__ void load4(const double *__restrict__ p, int t, int KT, double (&v)[4])
+{
+    if (t + 4 <= KT && !(KT & 3)) {
+        const double2 a = __ldg(reinterpret_cast<const double2 *>(p + t));
+        const double2 b = __ldg(reinterpret_cast<const double2 *>(p + t + 2));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = t + j < KT ? __ldg(p + t + j) : 0.0;
+    }
+}
 
+// Pass 2. Thread = (block pair b1 <= b2, four consecutive coefficients of
+// the tile); a warp takes 128 coefficients of one pair, so its loads of a
+// ray's coefficients are 512 contiguous bytes per block. For each angle of
+// the chunk the thread sums, over the rays the two blocks share (in
+// ascending order, FP32 for F32 plans), the products of their coefficients
+// and adds each sum to the pair's FP64 total, which is read from Dacc before
+// the first angle and written back after the last: no shared memory, no
+// barrier, no range test inside the ray loop. Every Dacc entry belongs to one
+// thread of a launch; the launches run in a fixed order.
 template <class TG>
 __global__ void __launch_bounds__(256)
 k_leaf_pairs(const GeomDev *__restrict__ Gd, const int2 *__restrict__ rng, int na, int cls, int q0, int S,
              int R, int KT, const TG *__restrict__ Gbuf, double *__restrict__ Dacc)
 {
-    extern __shared__ unsigned char smem_raw[];
-    TG *g1 = reinterpret_cast<TG *>(smem_raw);                     // GB x R x 32
     const GeomDev &g = *Gd;
-    const int P = g.P, B = g.B, K = g.K, nc = g.nc;
-    const int ngq = (nc + kPairGroup - 1) / kPairGroup;
-    const int gq = blockIdx.x / nc, gl = blockIdx.x - gq * nc;       // group along / across
-    const int t0 = blockIdx.y * 32;
+    const int P = g.P, B = g.B, K = g.K;
     const int lane = threadIdx.x & 31;
-    // partner b2 = bmin + warp + i * nw: blockIdx.z splits the partners
-    // between CTAs (disjoint Dacc entries)
-    const int warp = (threadIdx.x >> 5) * gridDim.z + blockIdx.z, nw = (blockDim.x >> 5) * gridDim.z;
-    if (gq >= ngq) return;
-    int mb[kPairGroup];
-    int nm = 0;
-    for (int i = 0; i < kPairGroup; ++i) {
-        const int along = gq * kPairGroup + i;
-        mb[i] = -1;
-        if (along < nc) { mb[i] = cls == 0 ? along * nc + gl : gl * nc + along; ++nm; }
-    }
-    const bool have = t0 + lane < KT;
-    const int c = have ? tile_c(cls, t0 + lane, q0, S, B) : 0;
-    const int bmin = mb[0];                                          // members ascend in index
-    for (int al = 0; al < na; ++al) {
-        int2 r1[kPairGroup];
-#pragma unroll
-        for (int i = 0; i < kPairGroup; ++i) r1[i] = mb[i] >= 0 ? rng[al * P + mb[i]] : make_int2(0, 0);
-        for (int i = 0; i < nm; ++i)
-            for (int e = threadIdx.x; e < r1[i].y * 32; e += blockDim.x) {
-                const int kk = e >> 5, tt = e & 31;
-                g1[(i * R + kk) * 32 + tt] =
-                    t0 + tt < KT ? Gbuf[(((int64_t)al * P + mb[i]) * R + kk) * KT + t0 + tt] : TG(0);
-            }
-        __syncthreads();
-        for (int b2 = bmin + warp; b2 < P; b2 += nw) {
-            const int2 r2 = rng[al * P + b2];
-            int lo[kPairGroup], hi[kPairGroup];
-            int ulo = INT_MAX, uhi = INT_MIN;
-#pragma unroll
-            for (int i = 0; i < kPairGroup; ++i) {
-                lo[i] = max(r1[i].x, r2.x);
-                hi[i] = min(r1[i].x + r1[i].y, r2.x + r2.y);
-                if (mb[i] < 0 || mb[i] > b2 || lo[i] >= hi[i]) { lo[i] = 0; hi[i] = 0; continue; }
-                ulo = min(ulo, lo[i]);
-                uhi = max(uhi, hi[i]);
-            }
-            if (ulo >= uhi) continue;
-            // the D values are read before the sums so that their latency
-            // overlaps the arithmetic
-            double dold[kPairGroup];
-#pragma unroll
-            for (int i = 0; i < kPairGroup; ++i)
-                dold[i] = (have && hi[i] > lo[i]) ? Dacc[((int64_t)mb[i] * P + b2) * K + c] : 0.0;
-            TG acc[kPairGroup];
-#pragma unroll
-            for (int i = 0; i < kPairGroup; ++i) acc[i] = TG(0);
-            const TG *g2 = Gbuf + (((int64_t)al * P + b2) * R + (ulo - r2.x)) * KT + t0 + lane;
-            // eight rays per step: the partner's loads are issued together
-            for (int k = ulo; k < uhi; k += 8) {
-                TG v2[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) v2[u] = (have && k + u < uhi) ? g2[(int64_t)(k + u - ulo) * KT] : TG(0);
-#pragma unroll
-                for (int i = 0; i < kPairGroup; ++i)
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int kk = k + u;
-                        if (kk >= lo[i] && kk < hi[i])
-                            acc[i] = fma_t(g1[(i * R + kk - r1[i].x) * 32 + lane], v2[u], acc[i]);
-                    }
-            }
-            if (have)
-#pragma unroll
-                for (int i = 0; i < kPairGroup; ++i)
-                    if (hi[i] > lo[i]) Dacc[((int64_t)mb[i] * P + b2) * K + c] = dold[i] + (double)acc[i];
+    const int halves = (KT + 127) / 128;                          // warps per pair
+    const int64_t ntasks = (int64_t)P * P * halves;
+    const int wpb = blockDim.x >> 5;
+    for (int64_t task = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); task < ntasks;
+         task += (int64_t)gridDim.x * wpb) {
+        const int h = (int)(task % halves);
+        const int64_t pr = task / halves;
+        const int b1 = (int)(pr / P), b2 = (int)(pr - (int64_t)b1 * P);
+        if (b2 < b1) continue;                                     // each unordered pair once
+        const int t = 4 * (h * 32 + lane);
+        bool any = false;                                          // the pair shares a ray at some angle
+        for (int al = 0; al < na && !any; ++al) {
+            const int2 r1 = rng[al * P + b1], r2 = rng[al * P + b2];
+            any = max(r1.x, r2.x) < min(r1.x + r1.y, r2.x + r2.y);
         }
-        __syncthreads();
+        if (!any) continue;                                        // warp-uniform
+        int cj[4];
+        double d64[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            cj[j] = t + j < KT ? tile_c(cls, t + j, q0, S, B) : -1;
+            d64[j] = cj[j] >= 0 ? Dacc[((int64_t)b1 * P + b2) * K + cj[j]] : 0.0;
+        }
+        for (int al = 0; al < na; ++al) {
+            const int2 r1 = rng[al * P + b1], r2 = rng[al * P + b2];
+            const int lo = max(r1.x, r2.x), hi = min(r1.x + r1.y, r2.x + r2.y);
+            if (lo >= hi) continue;                                // warp-uniform
+            const TG *p1 = Gbuf + (((int64_t)al * P + b1) * R + (lo - r1.x)) * KT;
+            const TG *p2 = Gbuf + (((int64_t)al * P + b2) * R + (lo - r2.x)) * KT;
+            TG acc[4] = {TG(0), TG(0), TG(0), TG(0)};
+            const int nk = hi - lo;
+            int k = 0;
+            for (; k + 2 <= nk; k += 2) {                          // two rays' loads in flight
+                TG u0[4], v0[4], u1[4], v1[4];
+                load4(p1 + (int64_t)k * KT, t, KT, u0);
+                load4(p2 + (int64_t)k * KT, t, KT, v0);
+                load4(p1 + (int64_t)(k + 1) * KT, t, KT, u1);
+                load4(p2 + (int64_t)(k + 1) * KT, t, KT, v1);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[j] = fma_t(u0[j], v0[j], acc[j]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[j] = fma_t(u1[j], v1[j], acc[j]);
+            }
+            if (k < nk) {
+                TG u0[4], v0[4];
+                load4(p1 + (int64_t)k * KT, t, KT, u0);
+                load4(p2 + (int64_t)k * KT, t, KT, v0);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[j] = fma_t(u0[j], v0[j], acc[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) d64[j] += (double)acc[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (cj[j] >= 0) Dacc[((int64_t)b1 * P + b2) * K + cj[j]] = d64[j];
     }
 }
 
@@ -322,7 +328,9 @@ k_leaf_pairs(const GeomDev *__restrict__ Gd, const int2 *__restrict__ rng, int n
 // stored by columns of L (M[q * P + i] = L[i][q]: thread i's loads are
 // consecutive across threads), pivot test, then the inverse columns by two
 // triangular solves (thread c owns column c of Y; the factor entries it
-// reads are the same for every thread). One CTA per leaf. status[k] = 0 ok,
+// reads are the same for every thread; only the lower triangle of the
+// symmetric inverse is solved, the upper one is its mirror image). One CTA
+// per leaf. status[k] = 0 ok,
 // -1 if a pivot is not positive.
 template <class T>
 __global__ void __launch_bounds__(256)
@@ -365,18 +373,25 @@ k_leaf_invert(const GeomDev *__restrict__ Gd, const double *__restrict__ Dacc, d
         if (threadIdx.x == 0) status[k] = bad ? -1 : 0;
         const int col = threadIdx.x;
         if (col < P) {
-            for (int i = 0; i < P; ++i) {            // L y = e_col
+            // L y = e_col: y is 0 above row col, so the sums start there
+            for (int i = col; i < P; ++i) {
                 double y = (i == col) ? 1.0 : 0.0;
-                for (int q = 0; q < i; ++q) y -= M[(int64_t)q * P + i] * Y[(int64_t)q * P + col];
+                for (int q = col; q < i; ++q) y -= M[(int64_t)q * P + i] * Y[(int64_t)q * P + col];
                 Y[(int64_t)i * P + col] = y / M[(int64_t)i * P + i];
             }
-            for (int i = P - 1; i >= 0; --i) {       // L^T x = y
+            // L^T x = y for the rows i >= col only: the inverse is symmetric,
+            // its lower triangle is solved and the upper one mirrors it
+            for (int i = P - 1; i >= col; --i) {
                 double x = Y[(int64_t)i * P + col];
                 for (int q = i + 1; q < P; ++q) x -= M[(int64_t)i * P + q] * Y[(int64_t)q * P + col];
                 x /= M[(int64_t)i * P + i];
                 Y[(int64_t)i * P + col] = x;
             }
-            for (int i = 0; i < P; ++i) inv[(int64_t)k * P * P + (int64_t)i * P + col] = (T)Y[(int64_t)i * P + col];
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
+            const int i = e / P, j = e - i * P;
+            inv[(int64_t)k * P * P + e] = (T)Y[(int64_t)max(i, j) * P + min(i, j)];
         }
         __syncthreads();
     }
@@ -422,10 +437,8 @@ static int32_t assemble(const GeomDev &gh, const GeomDev *gd, double *Dacc, cuda
         cleanup();
         return fail(WMG_ERR_OOM, "leaf setup: device allocation failed");
     }
-    const size_t sm2 = (size_t)kPairGroup * R * 32 * sizeof(TG);
-    const int ngq = (gh.nc + kPairGroup - 1) / kPairGroup;
-    if (sm2 > 48 * 1024)
-        cudaFuncSetAttribute(k_leaf_pairs<TG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+    const int64_t pair_warps = (int64_t)P * P * ((KT + 127) / 128);
+    const int pair_grid = (int)std::min<int64_t>((pair_warps + 7) / 8, (int64_t)num_sms() * 64);
     int off = 0;
     for (int cls = 0; cls < 2; ++cls) {
         const std::vector<int> &lst = lists[cls];
@@ -439,13 +452,13 @@ static int32_t assemble(const GeomDev &gh, const GeomDev *gd, double *Dacc, cuda
             for (int q0 = 0; q0 < B; q0 += S) {
                 launch_profiles<TG>(B, S, gd, na, cls, q0, R, KT, P, rng, Fw, Fc, Gbuf, st);
                 count_launches(1);
-                k_leaf_pairs<TG><<<dim3(ngq * gh.nc, (KT + 31) / 32, 1), 256, sm2, st>>>(gd, rng, na, cls, q0, S,
-                                                                                         R, KT, Gbuf, Dacc);
+                k_leaf_pairs<TG><<<pair_grid, 256, 0, st>>>(gd, rng, na, cls, q0, S, R, KT, Gbuf, Dacc);
             }
         }
         off += (int)lst.size();
     }
     cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaGetLastError();              // a launch that did not start
     cleanup();
     if (e != cudaSuccess) return fail(WMG_ERR_CUDA, std::string("leaf setup: ") + cudaGetErrorString(e));
     return WMG_OK;
@@ -476,8 +489,9 @@ int32_t build_leaf_inverses(const GeomDev &gh, const GeomDev *gd, void *leafinv_
     if (fp32) k_leaf_invert<float><<<inv_ctas, 256, 0, st>>>(gd, Dacc, A, Y, static_cast<float *>(leafinv_out), status);
     else k_leaf_invert<double><<<inv_ctas, 256, 0, st>>>(gd, Dacc, A, Y, static_cast<double *>(leafinv_out), status);
     std::vector<int> hs(K);
+    cudaError_t e = cudaGetLastError();                         // a launch that did not start
     cudaMemcpyAsync(hs.data(), status, (size_t)K * sizeof(int), cudaMemcpyDeviceToHost, st);
-    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         rc = fail(WMG_ERR_CUDA, std::string("leaf setup: ") + cudaGetErrorString(e));
     } else {

@@ -56,6 +56,9 @@ FP64_SAMPLE = 8
 # spectral radius of W^T W in unit-square units (noisy, often underdetermined
 # requests; regularised normal equations as in the paper's noisy experiments)
 SERVING_EPS = 1e-3
+# arrival rate of the full-size request stream (requests/s): 0.7 x the
+# saturated throughput measured once with --serving-burst, then fixed
+SERVING_RATE_FULL = 0.7
 
 
 def parse():
@@ -70,11 +73,17 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the serving leg (request stream through the continuous-batching server)")
-    ap.add_argument("--serving-requests", type=int, default=48)
-    ap.add_argument("--serving-rate", type=float, default=8.0,
-                    help="mean arrivals per second (Poisson); 8 = 0.7 x the saturated throughput measured once")
-    ap.add_argument("--serving-max-n", type=int, default=512,
-                    help="largest image side of the serving stream (sizes 128 .. 2048 in the full stream)")
+    ap.add_argument("--serving-requests", type=int, default=40,
+                    help="requests of the full-size stream (n 128 .. 2048, m 90 .. 720)")
+    ap.add_argument("--serving-rate", type=float, default=SERVING_RATE_FULL,
+                    help="mean arrivals per second (Poisson) of the full-size stream: 0.7 x its saturated "
+                         "throughput measured once")
+    ap.add_argument("--serving-max-n", type=int, default=2048,
+                    help="largest image side of the stream (sizes 128 .. 2048 in the configured stream)")
+    ap.add_argument("--serving-small-requests", type=int, default=48,
+                    help="requests of the second stream, restricted to n <= 512 (0: skip it)")
+    ap.add_argument("--serving-small-rate", type=float, default=8.0,
+                    help="mean arrivals per second of the n <= 512 stream (0.7 x its saturated throughput)")
     ap.add_argument("--serving-only", action="store_true", help="run the serving leg alone and print its JSON")
     ap.add_argument("--serving-burst", action="store_true",
                     help="serving leg with every request arriving at t = 0 (saturated throughput)")
@@ -559,8 +568,15 @@ def run_ours(args, rank, world, local):
         if not args.no_serving and world == 1:
             try:
                 line["serving"] = serving_leg(args, dev)
+                line["serving"]["setup_s_per_geometry"] = setup_times(((1024, 405), (2048, 405)))
             except Exception as e:
                 line["serving"] = {"unavailable": f"{type(e).__name__}: {e}"}
+            if args.serving_small_requests > 0:
+                try:
+                    line["serving_n_le_512"] = serving_leg(args, dev, args.serving_small_requests, 512,
+                                                           args.serving_small_rate)
+                except Exception as e:
+                    line["serving_n_le_512"] = {"unavailable": f"{type(e).__name__}: {e}"}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -686,14 +702,20 @@ def semiconvergence_leg(dev) -> dict:
 # Serving leg: a seeded Poisson stream of reconstruction requests of mixed
 # image sizes and angle counts through the continuous-batching server
 # ---------------------------------------------------------------------------
-def serving_leg(args, dev) -> dict:
+def serving_leg(args, dev, requests=None, max_n=None, rate=None) -> dict:
+    """A seeded Poisson stream through the continuous-batching server: the
+    first `requests` requests of the configured stream with n <= max_n,
+    arriving at `rate` per second (all at t = 0 with --serving-burst)."""
     import torch
     import paper_1310_0956_gb300 as wmg
 
-    wl, gaps = S.workload_serving(max(2000, args.serving_requests))
-    picked = [(p, g) for p, g in zip(wl.problems, gaps) if p.n <= args.serving_max_n][:args.serving_requests]
+    requests = args.serving_requests if requests is None else requests
+    max_n = args.serving_max_n if max_n is None else max_n
+    rate = args.serving_rate if rate is None else rate
+    wl, gaps = S.workload_serving(max(2000, requests))
+    picked = [(p, g) for p, g in zip(wl.problems, gaps) if p.n <= max_n][:requests]
     probs = [p for p, _ in picked]
-    arrivals = np.cumsum([g for _, g in picked]) / args.serving_rate
+    arrivals = np.cumsum([g for _, g in picked]) / rate
     arrivals -= arrivals[0]
     if args.serving_burst:
         arrivals[:] = 0.0
@@ -706,7 +728,10 @@ def serving_leg(args, dev) -> dict:
         bs.append(b64.to(torch.float32).contiguous())
         op.close()
     torch.cuda.synchronize()
-    srv = wmg.Server(64 << 30, max_slots=64, state_bytes=32 << 30, sino_ratio=4.0, preconditioned=True,
+    # device memory for the server: 160 GB (2048^2 geometries hold 4.3 GB of
+    # FP32 leaf inverses each and their setups ~9 GB of transient FP64 Gram
+    # blocks), 48 GB of it for request state
+    srv = wmg.Server(160 << 30, max_slots=64, state_bytes=48 << 30, sino_ratio=4.0, preconditioned=True,
                      max_iter=MAX_ITER, rtol=RTOL, restart=RESTART, levels=1, nu1=NU1, nu2=NU2, hybrid_depth=HYB,
                      cycle=wmg.CYCLE_HYBRID, precision=wmg.PREC_F32)
     launches0 = wmg.wmg_launch_count(False)
@@ -737,14 +762,23 @@ def serving_leg(args, dev) -> dict:
     lat = np.array([(done[i][0] - arrivals[i]) * 1e3 for i in range(len(probs))])
     infos = [done[i][1] for i in range(len(probs))]
     sizes = sorted({p.n for p in probs})
+    by_size = {}
+    for nn in sizes:
+        ls = np.array([lat[i] for i, p in enumerate(probs) if p.n == nn])
+        by_size[str(nn)] = {"requests": int(ls.size), "p50_latency_ms": float(np.percentile(ls, 50)),
+                            "p99_latency_ms": float(np.percentile(ls, 99))}
     return {
-        "workload": ("burst" if args.serving_burst else f"poisson_rate{args.serving_rate:g}") +
+        "latency_by_image_side": by_size,
+        "workload": ("burst" if args.serving_burst else f"poisson_rate{rate:g}") +
                     f"_{len(probs)}req_n" + "-".join(map(str, sizes)) + "_m90-720",
         "requests": len(probs), "recon_per_s": len(probs) / wall, "wall_s": wall,
         "p50_latency_ms": float(np.percentile(lat, 50)), "p99_latency_ms": float(np.percentile(lat, 99)),
         "mean_latency_ms": float(lat.mean()),
         "latency_from": "scheduled arrival to retirement seen by the host",
         "all_converged": bool(all(i[1] == 0 for i in infos)),
+        "status_counts": {str(k): int(v) for k, v in zip(*np.unique([i[1] for i in infos], return_counts=True))},
+        "not_converged": [{"n": probs[i].n, "m": probs[i].m, "iters": infos[i][0], "status": infos[i][1],
+                           "rel_res": infos[i][2]} for i in range(len(probs)) if infos[i][1] != 0][:8],
         "iters_mean": float(np.mean([i[0] for i in infos])),
         "max_running": peak, "ticks": st["ticks"], "geometry_setups": st["geometry_setups"],
         "gpu_launches": wmg.wmg_launch_count(False) - launches0,
@@ -1064,6 +1098,24 @@ def kernel_case():
         plan.backproject(b, out=y)
     torch.cuda.synchronize()
     print(json.dumps({"kernel_case": "ok", "nnz_per_image": plan.nnz()}))
+
+
+def setup_times(cases) -> dict:
+    """Plan creation (geometry, smoother diagonal, leaf Galerkin setup and
+    inverses) of the serving configuration, FP32, per (n, m): seconds."""
+    import torch
+    import paper_1310_0956_gb300 as wmg
+    out = {}
+    for n, m in cases:
+        D, levels = S.detectors_for(n), S.levels_for(n)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan = wmg.Plan(n, m, D, levels=levels, nu1=NU1, nu2=NU2, lam=SERVING_EPS * m / n, hybrid_depth=HYB,
+                        cycle=wmg.CYCLE_HYBRID, precision=wmg.PREC_F32)
+        torch.cuda.synchronize()
+        out[f"{n}x{n}_{m}ang_{D}det_levels{levels}"] = time.perf_counter() - t0
+        plan.close()
+    return out
 
 
 def setup_case(spec: str):

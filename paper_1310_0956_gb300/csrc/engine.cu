@@ -1396,7 +1396,8 @@ static int32_t solver_pools(wmg_plan *pl, int solver, bool pre, int restart)
              pl->gcs.ensure((size_t)count * restart * 8) && pl->gsn.ensure((size_t)count * restart * 8) &&
              pl->gg.ensure((size_t)count * ldp * 8) && pl->gy.ensure((size_t)count * ldp * 8) &&
              pl->h1.ensure((size_t)count * ldp * 8) && pl->h2.ensure((size_t)count * ldp * 8) &&
-             pl->jn.ensure((size_t)count * 4) && pl->done.ensure((size_t)count * 4);
+             pl->jn.ensure((size_t)count * 4) && pl->done.ensure((size_t)count * 4) &&
+             pl->reo.ensure((size_t)count * 4);
     } else {
         what = "BiCGStab pools";
         ok = ensure_pool(pl->x, nN, 8) && ensure_pool(pl->f, nN, 8) && ensure_pool(pl->w, nN, 8) &&
@@ -1662,7 +1663,7 @@ static int32_t solve_gmres(wmg_plan *pl, bool pre, const void *b, const void *x0
     ga.S = pl->S.as<double>(); ga.H = pl->H.as<double>(); ga.cs = pl->gcs.as<double>();
     ga.sn = pl->gsn.as<double>(); ga.g = pl->gg.as<double>(); ga.y = pl->gy.as<double>();
     ga.h1 = pl->h1.as<double>(); ga.h2 = pl->h2.as<double>(); ga.jn = pl->jn.as<int>();
-    ga.done = pl->done.as<int>(); ga.hist = hist; ga.hist_ld = hld;
+    ga.done = pl->done.as<int>(); ga.skip = pl->reo.as<int>(); ga.hist = hist; ga.hist_ld = hld;
     const ProbDev *P = ps.d.as<ProbDev>();
     const int4 *vt = ps.vimg.tiles.as<int4>();
     const int nv = ps.vimg.n;
@@ -1720,13 +1721,19 @@ static int32_t solve_gmres(wmg_plan *pl, bool pre, const void *b, const void *x0
         BpArgs wa = bp_args(BP_GMRES_W, pl->sinoS.p, S);
         wa.z = pl->u.as<double>(); wa.out64 = pl->w.as<double>();
         backproject<T>(pl, ps, wa, s);
+        // classical Gram-Schmidt, the second pass only where the first one
+        // cancelled (k_gm_reorth); |w|^2 partials from the last pass run
+        int *skip = pl->reo.as<int>();
         for (int pass = 0; pass < 2; ++pass) {
-            launch_gm_dots(P, vt, nv, V, vstride, pl->w.as<double>(), 0, ldp, pa, S, s, jv);
+            launch_gm_dots(P, vt, nv, V, vstride, pl->w.as<double>(), 0, ldp, pa, S, s, jv, pass == 0,
+                           pass == 1 ? skip : nullptr);
             double *hv = pass == 0 ? pl->h1.as<double>() : pl->h2.as<double>();
             // all ldp columns are summed; the Arnoldi step reads those <= j
+            // (and the reorthogonalisation test column j + 1 of the first)
             finalize(pl, FIN_STORE, ps.vimg, pa, ldp, nullptr, nullptr, 0, nullptr, 0, s, 0, hv, ldp, ldp);
-            launch_gm_axpy(P, vt, nv, V, vstride, pl->w.as<double>(), 0, ldp, hv, pass == 1 ? pb : nullptr, S, s,
-                           jv);
+            launch_gm_axpy(P, vt, nv, V, vstride, pl->w.as<double>(), 0, ldp, hv, pb, S, s, jv,
+                           pass == 1 ? skip : nullptr);
+            if (pass == 0) launch_gm_scalar(3, ga, s);
         }
         finalize(pl, FIN_STORE, ps.vimg, pb, 1, nullptr, nullptr, 0, nullptr, 0, s, SC_WNORM2);
         launch_gm_scalar(0, ga, s);

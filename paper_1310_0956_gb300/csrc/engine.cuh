@@ -210,7 +210,7 @@ struct wmg_plan {
     // scalars and partials
     wmg::DevBuf S, part_a, part_b, part_c, lam, hist;
     // GMRES
-    wmg::DevBuf V, H, gcs, gsn, gg, gy, h1, h2, jn, done;
+    wmg::DevBuf V, H, gcs, gsn, gg, gy, h1, h2, jn, done, reo;
     // BiCGStab (t and the preconditioned s)
     wmg::DevBuf bi_t, bi_sh;
     // profiling: (kind 0 = project / 1 = backproject, images, start, stop)

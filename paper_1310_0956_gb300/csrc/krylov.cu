@@ -203,11 +203,14 @@ k_bicg(const ProbDev *__restrict__ P, const int4 *__restrict__ tiles, int ntiles
 // index j is one for all problems, or, when `jv` is given, jv[slot] per
 // problem (problems at different Arnoldi steps in one launch).
 // ---------------------------------------------------------------------------
-// Partial dots part[t * (jmax+1) + i] = <V_i, w> over the tile, i <= j.
+// Partial dots part[t * ldp + i] = <V_i, w> over the tile, i <= j; with
+// `wnorm`, also part[t * ldp + j + 1] = <w, w>. Slots with skip[slot] set
+// (the second pass skipped) get zero partials and read nothing.
 __global__ void __launch_bounds__(256)
 k_gm_dots(const ProbDev *__restrict__ P, const int4 *__restrict__ tiles, int ntiles,
           const double *__restrict__ V, int64_t vstride, const double *__restrict__ w, int j0,
-          const int *__restrict__ jv, int ldp, double *__restrict__ part, const double *__restrict__ S)
+          const int *__restrict__ jv, int ldp, double *__restrict__ part, const double *__restrict__ S,
+          int wnorm, const int *__restrict__ skip)
 {
     __shared__ double red[8];
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -215,6 +218,20 @@ k_gm_dots(const ProbDev *__restrict__ P, const int4 *__restrict__ tiles, int nti
         const ProbDev pd = P[tl.x];
         if (!slot_active(S, pd.slot)) continue;
         const int j = jv ? jv[pd.slot] : j0;
+        if (skip && skip[pd.slot]) {                                  // CTA-uniform
+            for (int i = threadIdx.x; i <= j; i += blockDim.x) part[(int64_t)t * ldp + i] = 0.0;
+            continue;
+        }
+        if (wnorm) {
+            double acc = 0.0;
+            for (int e = threadIdx.x; e < tl.z; e += blockDim.x) {
+                const double v = w[pd.img + tl.y + e];
+                acc += v * v;
+            }
+            const double tot = block_sum_fixed(acc, red);
+            if (threadIdx.x == 0) part[(int64_t)t * ldp + j + 1] = tot;
+            __syncthreads();
+        }
         for (int i = 0; i <= j; ++i) {
             const double *Vi = V + (int64_t)i * vstride + pd.img;
             double acc = 0.0;
@@ -230,17 +247,19 @@ k_gm_dots(const ProbDev *__restrict__ P, const int4 *__restrict__ tiles, int nti
 }
 
 // w -= sum_i h_i V_i (h from Hc[slot*ldp + i]); part = |w|^2 after the update.
+// Slots with skip[slot] set are left alone (w and their partials).
 __global__ void __launch_bounds__(256)
 k_gm_axpy(const ProbDev *__restrict__ P, const int4 *__restrict__ tiles, int ntiles,
           const double *__restrict__ V, int64_t vstride, double *__restrict__ w, int j0,
           const int *__restrict__ jv, int ldp, const double *__restrict__ Hc, double *__restrict__ part,
-          const double *__restrict__ S)
+          const double *__restrict__ S, const int *__restrict__ skip)
 {
     __shared__ double red[8];
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 tl = tiles[t];
         const ProbDev pd = P[tl.x];
         if (!slot_active(S, pd.slot)) continue;
+        if (skip && skip[pd.slot]) continue;                          // CTA-uniform
         const int j = jv ? jv[pd.slot] : j0;
         const double *h = Hc + (int64_t)pd.slot * ldp;
         const double *Vb = V + pd.img;
@@ -515,6 +534,29 @@ __global__ void k_gm_arnoldi(GmArgs a)
     if (rel < S[SC_RTOL] || it >= (int)S[SC_MAXIT] || hn == 0.0) a.done[p] = 1;
 }
 
+// Selective reorthogonalisation ("twice is enough", decided per problem):
+// after the first classical Gram-Schmidt pass, |w'|^2 = |w|^2 - |h|^2 in
+// exact arithmetic; the second pass runs only when the first removed more
+// than 1 - kReorthEta^2 of |w|^2, i.e. |w'| < kReorthEta |w| (cancellation,
+// where one pass leaves w' measurably non-orthogonal to the basis). With
+// |w'| >= kReorthEta |w| one pass keeps the loss of orthogonality below
+// about 1 / kReorthEta units in the last place. skip[p] = 1: no second pass.
+constexpr double kReorthEta2 = 1.0 / 64.0;                             // kReorthEta = 1/8
+
+__global__ void k_gm_reorth(GmArgs a)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.nprob) return;
+    const double *S = a.S + (int64_t)p * NSCAL;
+    if (S[SC_ACTIVE] == 0.0 || a.done[p]) { a.skip[p] = 1; return; }
+    const int j = a.jslot ? a.jn[p] : a.j;
+    const double *h1 = a.h1 + (int64_t)p * a.ldp;
+    const double wn2 = h1[j + 1];
+    double hh = 0.0;
+    for (int i = 0; i <= j; ++i) hh += h1[i] * h1[i];
+    a.skip[p] = (wn2 > 0.0 && isfinite(wn2) && wn2 - hh >= kReorthEta2 * wn2) ? 1 : 0;
+}
+
 // End of cycle: y = H^-1 g (upper triangular jn x jn).
 __global__ void k_gm_solve_y(GmArgs a)
 {
@@ -623,19 +665,20 @@ void launch_finalize(const FinArgs &f, cudaStream_t st)
 
 void launch_gm_dots(const ProbDev *P, const int4 *tiles, int ntiles, const double *V, int64_t vstride,
                     const double *w, int j, int ldp, double *part, const double *S, cudaStream_t st,
-                    const int *jv)
+                    const int *jv, bool wnorm, const int *skip)
 {
     if (ntiles <= 0) return;
     count_launches(1);
-    k_gm_dots<<<grid_for(ntiles), 256, 0, st>>>(P, tiles, ntiles, V, vstride, w, j, jv, ldp, part, S);
+    k_gm_dots<<<grid_for(ntiles), 256, 0, st>>>(P, tiles, ntiles, V, vstride, w, j, jv, ldp, part, S,
+                                                wnorm ? 1 : 0, skip);
 }
 void launch_gm_axpy(const ProbDev *P, const int4 *tiles, int ntiles, const double *V, int64_t vstride,
                     double *w, int j, int ldp, const double *Hc, double *part, const double *S,
-                    cudaStream_t st, const int *jv)
+                    cudaStream_t st, const int *jv, const int *skip)
 {
     if (ntiles <= 0) return;
     count_launches(1);
-    k_gm_axpy<<<grid_for(ntiles), 256, 0, st>>>(P, tiles, ntiles, V, vstride, w, j, jv, ldp, Hc, part, S);
+    k_gm_axpy<<<grid_for(ntiles), 256, 0, st>>>(P, tiles, ntiles, V, vstride, w, j, jv, ldp, Hc, part, S, skip);
 }
 void launch_gm_combine(const ProbDev *P, const int4 *tiles, int ntiles, const double *V,
                        int64_t vstride, int ldp, const double *Yv, const int *jn, double *out,
@@ -681,6 +724,7 @@ void launch_gm_scalar(int which, const GmArgs &a, cudaStream_t st)
     count_launches(1);
     if (which == 0) k_gm_arnoldi<<<blocks, 128, 0, st>>>(a);
     else if (which == 1) k_gm_solve_y<<<blocks, 128, 0, st>>>(a);
+    else if (which == 3) k_gm_reorth<<<blocks, 128, 0, st>>>(a);
     else k_gm_restart<<<blocks, 128, 0, st>>>(a);
 }
 

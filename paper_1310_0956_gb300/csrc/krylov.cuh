@@ -106,6 +106,7 @@ struct GmArgs {
     double *S, *H, *cs, *sn, *g, *y;
     const double *h1, *h2;
     int *jn, *done;
+    int *skip;               // per problem: 1 = no second Gram-Schmidt pass (which = 3 writes it)
     double *hist;
     int hist_ld;
 };
@@ -117,13 +118,15 @@ template <class T>
 void launch_vec(int op, const ProbDev *P, const int4 *tiles, int ntiles, const VecArgs &a,
                 cudaStream_t st);
 void launch_finalize(const FinArgs &f, cudaStream_t st);
-// jv (optional): per-slot column index replacing j
+// jv (optional): per-slot column index replacing j; wnorm: also <w, w> into
+// column j + 1 of the partials; skip (optional): per-slot flag of problems
+// whose second Gram-Schmidt pass is skipped (zero dots, w untouched)
 void launch_gm_dots(const ProbDev *P, const int4 *tiles, int ntiles, const double *V, int64_t vstride,
                     const double *w, int j, int ldp, double *part, const double *S, cudaStream_t st,
-                    const int *jv = nullptr);
+                    const int *jv = nullptr, bool wnorm = false, const int *skip = nullptr);
 void launch_gm_axpy(const ProbDev *P, const int4 *tiles, int ntiles, const double *V, int64_t vstride,
                     double *w, int j, int ldp, const double *Hc, double *part, const double *S,
-                    cudaStream_t st, const int *jv = nullptr);
+                    cudaStream_t st, const int *jv = nullptr, const int *skip = nullptr);
 void launch_gm_combine(const ProbDev *P, const int4 *tiles, int ntiles, const double *V,
                        int64_t vstride, int ldp, const double *Yv, const int *jn, double *out,
                        const double *S, cudaStream_t st);
@@ -134,7 +137,8 @@ void launch_gm_setv(const ProbDev *P, const int4 *tiles, int ntiles, double *V, 
 void launch_gm_getv(const ProbDev *P, const int4 *tiles, int ntiles, const double *V, int64_t vstride,
                     const int *jv, double *out, const double *S, cudaStream_t st);
 void launch_bicg(int op, const ProbDev *P, const int4 *tiles, int ntiles, const BicgArgs &a, cudaStream_t st);
-// which: 0 = Arnoldi scalar step, 1 = solve H y = g, 2 = restart
+// which: 0 = Arnoldi scalar step, 1 = solve H y = g, 2 = restart,
+// 3 = selective reorthogonalisation test (skip[] from the first pass)
 void launch_gm_scalar(int which, const GmArgs &a, cudaStream_t st);
 
 }  // namespace wmg

@@ -552,6 +552,7 @@ int32_t tick(wmg_server *s)
     ga.S = S; ga.H = pl->H.as<double>(); ga.cs = pl->gcs.as<double>(); ga.sn = pl->gsn.as<double>();
     ga.g = pl->gg.as<double>(); ga.y = pl->gy.as<double>(); ga.h1 = pl->h1.as<double>();
     ga.h2 = pl->h2.as<double>(); ga.jn = pl->jn.as<int>(); ga.done = pl->done.as<int>();
+    ga.skip = pl->reo.as<int>();
     ga.hist = pl->hist.as<double>(); ga.hist_ld = s->hld;
     // INIT: f = W^T b, beta = |f|, v_0 = f / beta; the slots join ARN at j = 0
     if (any_init) {
@@ -609,12 +610,20 @@ int32_t tick(wmg_server *s)
     if (any_arn) {
         hold(s, PH_ARN, 0);
         const int *jv = pl->jn.as<int>();
+        // classical Gram-Schmidt, the second pass only where the first one
+        // cancelled (k_gm_reorth); |w|^2 partials from the last pass run
+        int *skip = pl->reo.as<int>();
         for (int pass = 0; pass < 2; ++pass) {
-            launch_gm_dots(P, vt, nv, V, vstride, pl->w.as<double>(), 0, ldp, pa, S, st, jv);
+            launch_gm_dots(P, vt, nv, V, vstride, pl->w.as<double>(), 0, ldp, pa, S, st, jv, pass == 0,
+                           pass == 1 ? skip : nullptr);
             double *hv = pass == 0 ? pl->h1.as<double>() : pl->h2.as<double>();
-            finalize(pl, FIN_STORE, ps.vimg, pa, jmax + 1, nullptr, nullptr, 0, nullptr, 0, st, 0, hv, ldp, ldp);
-            launch_gm_axpy(P, vt, nv, V, vstride, pl->w.as<double>(), 0, ldp, hv, pass == 1 ? pb : nullptr, S, st,
-                           jv);
+            finalize(pl, FIN_STORE, ps.vimg, pa, jmax + 2, nullptr, nullptr, 0, nullptr, 0, st, 0, hv, ldp, ldp);
+            launch_gm_axpy(P, vt, nv, V, vstride, pl->w.as<double>(), 0, ldp, hv, pb, S, st, jv,
+                           pass == 1 ? skip : nullptr);
+            if (pass == 0) {
+                ga.jslot = 1;
+                launch_gm_scalar(3, ga, st);
+            }
         }
         finalize(pl, FIN_STORE, ps.vimg, pb, 1, nullptr, nullptr, 0, nullptr, 0, st, SC_WNORM2);
         ga.jslot = 1;
@@ -748,7 +757,8 @@ extern "C" int32_t wmg_server_create(const wmg_server_config *cfg, void *stream,
          pl->gsn.ensure((size_t)cap * cfg->restart * 8) && pl->gg.ensure((size_t)cap * s->ldp * 8) &&
          pl->gy.ensure((size_t)cap * s->ldp * 8) && pl->h1.ensure((size_t)cap * s->ldp * 8) &&
          pl->h2.ensure((size_t)cap * s->ldp * 8) && pl->jn.ensure((size_t)cap * 4) &&
-         pl->done.ensure((size_t)cap * 4) && pl->hist.ensure((size_t)cap * s->hld * 8) &&
+         pl->done.ensure((size_t)cap * 4) && pl->reo.ensure((size_t)cap * 4) &&
+         pl->hist.ensure((size_t)cap * s->hld * 8) &&
          s->d_phase.ensure((size_t)cap * 4);
     if (!ok) return fail(WMG_ERR_OOM, "wmg_server_create: state pools do not fit in device memory");
     if (cudaMallocHost(&s->h_phase, cap * sizeof(int)) != cudaSuccess ||

@@ -63,6 +63,19 @@ extern "C" {
 #define WMG_PREC_F64   0   /* operator, vectors and reductions in FP64 */
 #define WMG_PREC_F32   1   /* operator (W, W^T, Haar, leaf solves) in FP32,
                               Krylov vectors, scalars and reductions in FP64 */
+#define WMG_PREC_F32_BF16STORE 2  /* as WMG_PREC_F32, and inside the Arnoldi
+                              steps of preconditioned GMRES the operator's
+                              stored inputs -- the preconditioned image and
+                              the sinogram W applies to it, with the band
+                              images of the hybrid update -- are bfloat16,
+                              widened to FP32 for the arithmetic (FP32
+                              accumulation). Each restart recomputes the true
+                              residual with the FP32 operator (residual
+                              replacement), which wins back the accuracy the
+                              rounded inputs cost. Other solvers, unpreconditioned
+                              GMRES and the operator calls run as WMG_PREC_F32.
+                              Buffers passed in and out are FP32. Plans only
+                              (not batches or the server). */
 
 #define WMG_CYCLE_ADDITIVE   0  /* all leaf corrections from one residual */
 #define WMG_CYCLE_HYBRID     1  /* Section 3.1.2: residual recomputed after the

@@ -8,20 +8,22 @@
 
 namespace wmg {
 
-template <class T, int EPI>
+// T: the plan's operator type (tables); TS: the storage of the operator
+// copies and outputs written here and of v_op (T, or bfloat16 for plans with
+// BF16 operator storage).
+template <class T, int EPI, class TS = T>
 __device__ __forceinline__ double bp_epilogue(const GeomDev &g, const ProbDev &pd,
                                               const BpArgs &a, int ix, int iy, double y)
 {
     const int n = g.n;
     const int64_t j = pd.img + (int64_t)iy * n + ix;
     const int64_t jt = pd.img + (int64_t)ix * n + iy;
-    const T yT = (T)y;
     const double lam = g.lambda;
     const double *S = a.S + (int64_t)pd.slot * NSCAL;
     const T *dinv = static_cast<const T *>(g.dinv) + (j - pd.img);
     double contrib = 0.0;
     if (EPI == BP_STORE) {
-        static_cast<T *>(a.out_op)[j] = yT;
+        st_op(static_cast<TS *>(a.out_op) + j, y);
     } else if (EPI == BP_CGLS_S) {
         const double xv = a.x[j] + S[SC_ALPHA] * a.p[j];
         a.x[j] = xv;
@@ -31,8 +33,8 @@ __device__ __forceinline__ double bp_epilogue(const GeomDev &g, const ProbDev &p
         if (a.z) {                        // first pre-smoothing sweep from z = 0
             const double zv = g.omega * (double)dinv[0] * sv;
             a.z[j] = zv;
-            static_cast<T *>(a.copy_op)[j] = (T)zv;
-            static_cast<T *>(a.copyT_op)[jt] = (T)zv;
+            st_op(static_cast<TS *>(a.copy_op) + j, zv);
+            st_op(static_cast<TS *>(a.copyT_op) + jt, zv);
         }
     } else if (EPI == BP_RESID) {
         a.out64[j] = a.s[j] - y - lam * a.z[j];
@@ -41,19 +43,19 @@ __device__ __forceinline__ double bp_epilogue(const GeomDev &g, const ProbDev &p
         a.z[j] = zv;
         contrib = a.s[j] * zv;
         if (a.copy_op) {
-            static_cast<T *>(a.copy_op)[j] = (T)zv;
-            static_cast<T *>(a.copyT_op)[jt] = (T)zv;
+            st_op(static_cast<TS *>(a.copy_op) + j, zv);
+            st_op(static_cast<TS *>(a.copyT_op) + jt, zv);
         }
     } else if (EPI == BP_APPLY_A) {
-        const double v = (double)static_cast<const T *>(a.v_op)[j];
+        const double v = (double)ld_op(static_cast<const TS *>(a.v_op) + j);
         if (a.out64) a.out64[j] = y + lam * v;
-        else static_cast<T *>(a.out_op)[j] = (T)(y + lam * v);
+        else st_op(static_cast<TS *>(a.out_op) + j, y + lam * v);
     } else if (EPI == BP_SIRT) {
         const T *C = static_cast<const T *>(g.sirtC) + (j - pd.img);
         const double xv = a.x[j] + (double)C[0] * (y - lam * a.x[j]);
         a.x[j] = xv;
-        static_cast<T *>(a.copy_op)[j] = (T)xv;
-        static_cast<T *>(a.copyT_op)[jt] = (T)xv;
+        st_op(static_cast<TS *>(a.copy_op) + j, xv);
+        st_op(static_cast<TS *>(a.copyT_op) + jt, xv);
     } else if (EPI == BP_GMRES_W) {
         const double wv = y + lam * a.z[j];
         a.out64[j] = wv;

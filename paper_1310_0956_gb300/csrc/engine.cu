@@ -313,12 +313,14 @@ void project(wmg_plan *pl, const ProbSet &ps, const void *img, const void *imgT,
                     double *part, const double *S, cudaStream_t st)
 {
     PjArgs a{ps.pj_ctas, img, imgT, sino, part, S, ps.proj.tb.as<int>(), 1};
+    a.bf16 = pl->bf16_now ? 1 : 0;
     if (pl->profiling) prof_begin(pl, 0, ps.nprob, st);
     if (sizeof(T) == 4) {
         // FP32: groups of kProjGroup images share the weights; the rest run
-        // one image per tile (the same per-image arithmetic in both)
+        // one image per tile (the same per-image arithmetic in both). The
+        // staged-pixel kernel reads FP32 pools only.
         a.group = kProjGroup;
-        if (!(ps.tma_n > 0 && launch_project_f32_tma(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(),
+        if (!(ps.tma_n > 0 && !a.bf16 && launch_project_f32_tma(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(),
                                                       ps.projg.tiles.as<int4>(), ps.projg.n, a, ps.tma_n,
                                                       ps.tma_count, st)))
             launch_project<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.projg.tiles.as<int4>(), ps.projg.n,
@@ -336,6 +338,7 @@ template <class T>
 void backproject(wmg_plan *pl, const ProbSet &ps, BpArgs a, cudaStream_t st)
 {
     a.unit = pl->unit_bins ? 1 : 0;
+    a.bf16 = pl->bf16_now ? 1 : 0;
     a.ctas_per_sm = ps.bp_ctas;
     a.part_base = ps.bp.tb.as<int>();
     if (pl->profiling) prof_begin(pl, 1, ps.nprob, st);
@@ -421,6 +424,7 @@ template <class T>
 void img_op(wmg_plan *pl, int op, ImgArgs a, cudaStream_t st)
 {
     const ProbSet &ps = pl->real;
+    a.bf16 = pl->bf16_now ? 1 : 0;
     launch_img<T>(op, pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.bp.tiles.as<int4>(), ps.bp.n, a, st);
 }
 
@@ -557,6 +561,16 @@ __global__ void k_coef_add(double *E, const double *E2, const longlong2 *segs, i
     }
 }
 
+// Haar synthesis whose outputs are operator copies: bfloat16 when the
+// operator calls being issued use bfloat16 storage, else the plan's type.
+template <class T>
+static void syn_op(wmg_plan *pl, const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles, int smem,
+                   const HaarArgs &a, cudaStream_t st)
+{
+    if (sizeof(T) == 4 && pl->bf16_now) launch_haar_synthesis<double, __nv_bfloat16>(G, P, tiles, ntiles, smem, a, st);
+    else launch_haar_synthesis<double, T>(G, P, tiles, ntiles, smem, a, st);
+}
+
 // One band-local residual update for a group of nodes (hybrid cycle): for
 // every slot and node, C[out range] -= Q_out^T (W^T W + lambda) Q_in E[in range].
 template <class T>
@@ -579,7 +593,7 @@ static int32_t band_update(wmg_plan *pl, int d, const std::vector<int> &nodes, c
     hs.outT = pl->band_imgT.p;
     hs.S = S;
     hs.fp32 = pl->prec == WMG_PREC_F32;
-    launch_haar_synthesis<double, T>(G, bs->d.as<ProbDev>(), bs->haar.tiles.as<int4>(), bs->haar.n,
+    syn_op<T>(pl, G, bs->d.as<ProbDev>(), bs->haar.tiles.as<int4>(), bs->haar.n,
                                      bs->haar_smem, hs, st);
     project<T>(pl, *bs, pl->band_img.p, pl->band_imgT.p, pl->band_sino.p, nullptr, S, st);
     BpArgs a = bp_args(BP_APPLY_A, pl->band_sino.p, S);
@@ -750,8 +764,7 @@ int32_t wmg_apply(wmg_plan *pl, double *s, double *z, bool first_done, bool copi
     hs.mode = HS_CORRECT; hs.in = pl->E.p; hs.z = z; hs.S = S; hs.fp32 = pl->prec == WMG_PREC_F32;
     hs.out = need_copies_after_syn ? pl->z_op.p : nullptr;
     hs.outT = need_copies_after_syn ? pl->zT_op.p : nullptr;
-    launch_haar_synthesis<double, T>(G, ps.d.as<ProbDev>(), ps.haar.tiles.as<int4>(), ps.haar.n,
-                                     ps.haar_smem, hs, st);
+    syn_op<T>(pl, G, ps.d.as<ProbDev>(), ps.haar.tiles.as<int4>(), ps.haar.n, ps.haar_smem, hs, st);
     for (int it = 0; it < o.nu2; ++it) {
         const bool last = it == o.nu2 - 1;
         project<T>(pl, ps, pl->z_op.p, pl->zT_op.p, pl->sinoS.p, nullptr, S, st);
@@ -802,7 +815,7 @@ int32_t validate(const wmg_geom *g, const wmg_opts *o)
     if ((1 << L) > 128) return fail(WMG_ERR_INVALID_ARG, "block side 2^(levels-1) must be <= 128");
     if (o->nu1 < 0 || o->nu2 < 0 || o->lambda < 0 || o->hybrid_depth < 0 ||
         o->cycle < WMG_CYCLE_ADDITIVE || o->cycle > WMG_CYCLE_MULTIPLICATIVE ||
-        (o->precision != WMG_PREC_F64 && o->precision != WMG_PREC_F32))
+        (o->precision != WMG_PREC_F64 && o->precision != WMG_PREC_F32 && o->precision != WMG_PREC_F32_BF16STORE))
         return fail(WMG_ERR_INVALID_ARG, "invalid options");
     if ((int64_t)g->n * g->n > (int64_t)1 << 30 || (int64_t)g->m * g->D > (int64_t)1 << 31)
         return fail(WMG_ERR_INVALID_ARG, "problem too large");
@@ -1018,7 +1031,8 @@ extern "C" int32_t wmg_plan_create(const wmg_geom *g, const wmg_opts *o, void *s
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     auto pl = std::make_unique<wmg_plan>();
-    pl->prec = o->precision;
+    pl->bf16 = o->precision == WMG_PREC_F32_BF16STORE;
+    pl->prec = pl->bf16 ? WMG_PREC_F32 : o->precision;
     pl->esz = o->precision == WMG_PREC_F64 ? 8 : 4;
     pl->opts = *o;
     if (pl->opts.omega <= 0) pl->opts.omega = 1.0;
@@ -1706,6 +1720,13 @@ static int32_t solve_gmres(wmg_plan *pl, bool pre, const void *b, const void *x0
     // Every index lives on the device, so the step is one fixed launch
     // sequence (a graph after its first run).
     auto arnoldi = [&](cudaStream_t s) -> int32_t {
+        // BF16 operator storage (WMG_PREC_F32_BF16STORE): the operator inputs
+        // of the step; the restarts' true residuals stay FP32
+        struct Bf16Scope {
+            wmg_plan *p;
+            Bf16Scope(wmg_plan *q, bool on) : p(q) { p->bf16_now = on; }
+            ~Bf16Scope() { p->bf16_now = false; }
+        } bf16_scope(pl, pl->bf16 && pre);
         launch_gm_getv(P, vt, nv, V, vstride, jv, pl->t.as<double>(), S, s);
         if (pre) {
             bool have = false;
@@ -2189,6 +2210,8 @@ extern "C" int32_t wmg_batch_create(const wmg_geom *gs, const wmg_opts *os, int3
     if (!out) return fail(WMG_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!gs || !os || count < 1) return fail(WMG_ERR_INVALID_ARG, "wmg_batch_create: bad arguments");
+    if (os[0].precision == WMG_PREC_F32_BF16STORE)
+        return fail(WMG_ERR_INVALID_ARG, "wmg_batch_create: BF16 operator storage is for plans only");
     for (int i = 0; i < count; ++i) {
         int32_t rc = validate(&gs[i], &os[i]);
         if (rc) return rc;

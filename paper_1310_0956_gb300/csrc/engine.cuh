@@ -184,7 +184,9 @@ struct SolveState {
 // of several geometries, stored grouped by geometry.
 // ---------------------------------------------------------------------------
 struct wmg_plan {
-    int prec = WMG_PREC_F64;
+    int prec = WMG_PREC_F64;      // arithmetic of the operator: F64 or F32 (also for BF16 storage)
+    bool bf16 = false;            // WMG_PREC_F32_BF16STORE: bfloat16 operator inputs in the Arnoldi steps
+    bool bf16_now = false;        // the operator calls being issued use bfloat16 storage
     size_t esz = 8;
     wmg_opts opts{};
     std::vector<std::unique_ptr<wmg::Geo>> geos;

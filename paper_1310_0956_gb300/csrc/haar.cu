@@ -411,5 +411,8 @@ WMG_INST(double, double)
 WMG_INST(float, double)
 WMG_INST(double, float)
 #undef WMG_INST
+// synthesis into bfloat16 operator copies (plans with BF16 operator storage)
+template void launch_haar_synthesis<double, __nv_bfloat16>(const GeomDev *, const ProbDev *, const int4 *, int, int,
+                                                           const HaarArgs &, cudaStream_t);
 
 }  // namespace wmg

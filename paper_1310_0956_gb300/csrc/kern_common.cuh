@@ -32,6 +32,17 @@ __device__ __forceinline__ float fma_t(float a, float b, float c) { return __fma
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 __device__ __forceinline__ float ldg_t(const float *p) { return __ldg(p); }
+
+// Operator-storage loads and stores of the FP32 kernels: float, or bfloat16
+// (plans with BF16 operator storage) widened to / rounded from float.
+__device__ __forceinline__ float ld_op(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float ld_op(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+__device__ __forceinline__ double ld_op(const double *p) { return __ldg(p); }
+__device__ __forceinline__ void st_op(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st_op(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void st_op(float *p, double v) { *p = (float)v; }
+__device__ __forceinline__ void st_op(__nv_bfloat16 *p, double v) { *p = __double2bfloat16(v); }
+__device__ __forceinline__ void st_op(double *p, double v) { *p = v; }
 __device__ __forceinline__ double ldg_t(const double *p) { return __ldg(p); }
 
 // Distance t - tau between a line p.(c, s) = t and a pixel centre (x, y),

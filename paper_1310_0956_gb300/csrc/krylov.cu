@@ -62,8 +62,13 @@ k_img(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P, const int4 *
                 } else if (OP == IMG_DOT_SZ) {      // part = s.z
                     part += a.s[j] * a.z[j];
                 }
-                cp = (T)v;
-                if (a.copy_op) static_cast<T *>(a.copy_op)[j] = cp;
+                // bfloat16 copies: one rounding from FP64; the tile keeps
+                // the rounded value exactly for the transposed copy
+                cp = a.bf16 ? (T)__bfloat162float(__double2bfloat16(v)) : (T)v;
+                if (a.copy_op) {
+                    if (a.bf16) static_cast<__nv_bfloat16 *>(a.copy_op)[j] = __float2bfloat16_rn((float)cp);
+                    else static_cast<T *>(a.copy_op)[j] = cp;
+                }
             }
             tr[ty + 8 * r][tx] = cp;
         }
@@ -72,8 +77,11 @@ k_img(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P, const int4 *
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const int ox = tl.z + ty + 8 * r, oy = tl.y + tx;
-                if (ox < n && oy < n)
-                    static_cast<T *>(a.copyT_op)[pd.img + (int64_t)ox * n + oy] = tr[tx][ty + 8 * r];
+                if (ox < n && oy < n) {
+                    const int64_t o = pd.img + (int64_t)ox * n + oy;
+                    if (a.bf16) static_cast<__nv_bfloat16 *>(a.copyT_op)[o] = __float2bfloat16_rn((float)tr[tx][ty + 8 * r]);
+                    else static_cast<T *>(a.copyT_op)[o] = tr[tx][ty + 8 * r];
+                }
             }
         }
         if (a.part) {

@@ -25,6 +25,7 @@ struct ImgArgs {
     void *copy_op, *copyT_op;
     double *part;
     const double *S;
+    int bf16;                // copy_op / copyT_op stored as bfloat16 (FP32 plans with BF16 storage)
 };
 
 enum VecOp : int {

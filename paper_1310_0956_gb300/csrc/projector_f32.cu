@@ -44,7 +44,7 @@ __device__ __forceinline__ float chord_n(float wa, float wb, float d)
 // order whatever the tile holds, so a problem gets the same bits alone and
 // grouped with others.
 // ---------------------------------------------------------------------------
-template <int NW, int IB>
+template <int NW, int IB, class TS>
 __global__ void __launch_bounds__(32 * NW, 2)
 k_project_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
               const int4 *__restrict__ tiles, int ntiles, PjArgs a)
@@ -60,8 +60,8 @@ k_project_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
         const AngleF A = g.angf[ang];
         const int flags = __float_as_int(A.flags);
         const bool steep = flags & 1;
-        const float *__restrict__ base = static_cast<const float *>(steep ? a.img : a.imgT);
-        const float *src[IB];
+        const TS *__restrict__ base = static_cast<const TS *>(steep ? a.img : a.imgT);
+        const TS *src[IB];
         bool act[IB];
         bool any = false;
 #pragma unroll
@@ -143,8 +143,8 @@ k_project_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
                     float v0[R], v1[R];
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
-                        v0[r] = ok0[r] ? __ldg(src[b] + idx[r]) : 0.f;
-                        v1[r] = ok1[r] ? __ldg(src[b] + idx[r] + 1) : 0.f;
+                        v0[r] = ok0[r] ? ld_op(src[b] + idx[r]) : 0.f;
+                        v1[r] = ok1[r] ? ld_op(src[b] + idx[r] + 1) : 0.f;
                     }
                     // one product chain over the step's rows in row order,
                     // then one compensated (Kahan) step
@@ -180,7 +180,7 @@ k_project_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
             }
             const ProbDev pb = P[tl.x + b];
             const float v = (S - Cc) * (A.lmax * g.hf);
-            if (valid) static_cast<float *>(a.sino)[pb.sino + (int64_t)ang * D + k] = v;
+            if (valid) st_op(static_cast<TS *>(a.sino) + pb.sino + (int64_t)ang * D + k, v);
             if (a.part) {
                 double q2 = valid ? (double)v * (double)v : 0.0;
                 q2 = warp_sum_fixed(q2);
@@ -200,8 +200,15 @@ void launch_project_f32(const GeomDev *G, const ProbDev *P, const int4 *tiles, i
     count_launches(1);
     constexpr int NW = 8;
     const int grid = min(ntiles, num_sms() * (a.ctas_per_sm > 0 ? a.ctas_per_sm : 8));
-    if (a.group == kProjGroup) k_project_f32<NW, kProjGroup><<<grid, 32 * NW, 0, st>>>(G, P, tiles, ntiles, a);
-    else k_project_f32<NW, 1><<<grid, 32 * NW, 0, st>>>(G, P, tiles, ntiles, a);
+    if (a.bf16) {
+        if (a.group == kProjGroup)
+            k_project_f32<NW, kProjGroup, __nv_bfloat16><<<grid, 32 * NW, 0, st>>>(G, P, tiles, ntiles, a);
+        else k_project_f32<NW, 1, __nv_bfloat16><<<grid, 32 * NW, 0, st>>>(G, P, tiles, ntiles, a);
+    } else if (a.group == kProjGroup) {
+        k_project_f32<NW, kProjGroup, float><<<grid, 32 * NW, 0, st>>>(G, P, tiles, ntiles, a);
+    } else {
+        k_project_f32<NW, 1, float><<<grid, 32 * NW, 0, st>>>(G, P, tiles, ntiles, a);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -232,8 +239,8 @@ constexpr int kBpWarps = 32 / kBpRows;
 // before the sum, so both parities cost the same; t - tau is exact up to the
 // one rounding of the tail pc (split trigonometry).
 // COVERED: both candidates always lie on the detector (GeomDev::unit == 2).
-template <bool COVERED, bool QPAIR>
-__device__ __forceinline__ void bp_unit_sums(const GeomDev &g, const float *__restrict__ sg, float xo, float yo0,
+template <bool COVERED, bool QPAIR, class TS>
+__device__ __forceinline__ void bp_unit_sums(const GeomDev &g, const TS *__restrict__ sg, float xo, float yo0,
                                              float (&s)[kBpRows], float (&cmp)[kBpRows])
 {
     constexpr float kRound = 12582912.f;   // 1.5 * 2^23
@@ -263,8 +270,8 @@ __device__ __forceinline__ void bp_unit_sums(const GeomDev &g, const float *__re
         }
         const float l0 = c0.z, l1 = two ? c1.z : 0.f;   // a missing second angle weighs 0
         // the second angle's row: its own, or (no second angle) the first's
-        const float *row0 = sg + ((int64_t)a0 * D + kofs - kRoundBits);
-        const float *row1 = sg + ((int64_t)a1 * D + kofs - kRoundBits);
+        const TS *row0 = sg + ((int64_t)a0 * D + kofs - kRoundBits);
+        const TS *row1 = sg + ((int64_t)a1 * D + kofs - kRoundBits);
         float ph0 = __fmaf_rn(xo, t0.x, yo0 * t0.z) - e, pc0 = __fmaf_rn(xo, t0.y, yo0 * t0.w);
         float ph1 = __fmaf_rn(xo, t1.x, yo0 * t1.z) - e, pc1 = __fmaf_rn(xo, t1.y, yo0 * t1.w);
         const float dph0 = dy * t0.z, dpc0 = dy * t0.w, dph1 = dy * t1.z, dpc1 = dy * t1.w;
@@ -283,8 +290,8 @@ __device__ __forceinline__ void bp_unit_sums(const GeomDev &g, const float *__re
                 o00 = (unsigned)k0 < (unsigned)D; o01 = (unsigned)(k0 + 1) < (unsigned)D;
                 o10 = (unsigned)k1 < (unsigned)D; o11 = (unsigned)(k1 + 1) < (unsigned)D;
             }
-            const float u0 = o00 ? __ldg(row0 + b0) : 0.f, u1 = o01 ? __ldg(row0 + b0 + 1) : 0.f;
-            const float v0 = o10 ? __ldg(row1 + b1) : 0.f, v1 = o11 ? __ldg(row1 + b1 + 1) : 0.f;
+            const float u0 = o00 ? ld_op(row0 + b0) : 0.f, u1 = o01 ? ld_op(row0 + b0 + 1) : 0.f;
+            const float v0 = o10 ? ld_op(row1 + b1) : 0.f, v1 = o11 ? ld_op(row1 + b1 + 1) : 0.f;
             // explicit rounding: no contraction into the Kahan step
             float rs;
             if (QPAIR) {
@@ -309,8 +316,8 @@ __device__ __forceinline__ void bp_unit_sums(const GeomDev &g, const float *__re
 // FP32 instructions (two IEEE single-precision operations, each rounded to
 // nearest, per instruction): every value is the one bp_unit_sums<COVERED,
 // true> computes, in fewer instructions.
-template <bool COVERED>
-__device__ __forceinline__ void bp_unit_sums_qpair(const GeomDev &g, const float *__restrict__ sg, float xo,
+template <bool COVERED, class TS>
+__device__ __forceinline__ void bp_unit_sums_qpair(const GeomDev &g, const TS *__restrict__ sg, float xo,
                                                    float yo0, float (&s)[kBpRows], float (&cmp)[kBpRows])
 {
     constexpr float kRound = 12582912.f;   // 1.5 * 2^23
@@ -334,8 +341,8 @@ __device__ __forceinline__ void bp_unit_sums_qpair(const GeomDev &g, const float
         const float4 t0 = __ldg(q0), c0 = __ldg(q0 + 1);
         const float4 t1 = make_float4(-t0.z, -t0.w, t0.x, t0.y);
         const float l0 = c0.z;
-        const float *row0 = sg + ((int64_t)a0 * D + kofs - kRoundBits);
-        const float *row1 = sg + ((int64_t)a1 * D + kofs - kRoundBits);
+        const TS *row0 = sg + ((int64_t)a0 * D + kofs - kRoundBits);
+        const TS *row1 = sg + ((int64_t)a1 * D + kofs - kRoundBits);
         float2 ph = make_float2(__fmaf_rn(xo, t0.x, yo0 * t0.z) - e, __fmaf_rn(xo, t1.x, yo0 * t1.z) - e);
         float2 pc = make_float2(__fmaf_rn(xo, t0.y, yo0 * t0.w), __fmaf_rn(xo, t1.y, yo0 * t1.w));
         const float2 dph = make_float2(dy * t0.z, dy * t1.z), dpc = make_float2(dy * t0.w, dy * t1.w);
@@ -358,8 +365,8 @@ __device__ __forceinline__ void bp_unit_sums_qpair(const GeomDev &g, const float
                     o00 = (unsigned)k0 < (unsigned)D; o01 = (unsigned)(k0 + 1) < (unsigned)D;
                     o10 = (unsigned)k1 < (unsigned)D; o11 = (unsigned)(k1 + 1) < (unsigned)D;
                 }
-                const float u0 = o00 ? __ldg(row0 + b0) : 0.f, u1 = o01 ? __ldg(row0 + b0 + 1) : 0.f;
-                const float v0 = o10 ? __ldg(row1 + b1) : 0.f, v1 = o11 ? __ldg(row1 + b1 + 1) : 0.f;
+                const float u0 = o00 ? ld_op(row0 + b0) : 0.f, u1 = o01 ? ld_op(row0 + b0 + 1) : 0.f;
+                const float v0 = o10 ? ld_op(row1 + b1) : 0.f, v1 = o11 ? ld_op(row1 + b1 + 1) : 0.f;
                 const float x0 = __fmaf_rn(wa0, u0, __fmul_rn(wb0, u1));
                 rs[h] = __fmul_rn(__fmaf_rn(wa1, v0, __fmaf_rn(wb1, v1, x0)), l0);
                 ph = __fadd2_rn(ph, dph);
@@ -379,7 +386,7 @@ __device__ __forceinline__ void bp_unit_sums_qpair(const GeomDev &g, const float
     }
 }
 
-template <int EPI, bool ALL_UNIT>
+template <int EPI, bool ALL_UNIT, class TS>
 __global__ void __launch_bounds__(32 * kBpWarps, 4)
 k_backproject_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
                   const int4 *__restrict__ tiles, int ntiles, BpArgs a)
@@ -390,7 +397,7 @@ k_backproject_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
         const int4 tl = tiles[t];
         const ProbDev pb = P[tl.x];
         if (!slot_active(a.S, pb.slot)) continue;                  // CTA-uniform
-        const float *sg = static_cast<const float *>(a.sino) + pb.sino;
+        const TS *sg = static_cast<const TS *>(a.sino) + pb.sino;
         const GeomDev &g = G[pb.geom];
         const int n = g.n, m = g.m, D = g.D;
         const int ix = tl.z + tx;
@@ -404,11 +411,11 @@ k_backproject_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
         if (unit) {
             const bool qp = g.qpair;
             if (g.unit == 2) {
-                if (qp) bp_unit_sums_qpair<true>(g, sg, xo, yo0, s, cmp);
-                else bp_unit_sums<true, false>(g, sg, xo, yo0, s, cmp);
+                if (qp) bp_unit_sums_qpair<true, TS>(g, sg, xo, yo0, s, cmp);
+                else bp_unit_sums<true, false, TS>(g, sg, xo, yo0, s, cmp);
             } else {
-                if (qp) bp_unit_sums_qpair<false>(g, sg, xo, yo0, s, cmp);
-                else bp_unit_sums<false, false>(g, sg, xo, yo0, s, cmp);
+                if (qp) bp_unit_sums_qpair<false, TS>(g, sg, xo, yo0, s, cmp);
+                else bp_unit_sums<false, false, TS>(g, sg, xo, yo0, s, cmp);
             }
         } else {
             const float hD = g.hDf, dt = g.dtf, t0 = g.t0f, inv_dt = 1.f / g.dtf;
@@ -431,7 +438,7 @@ k_backproject_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
                         if ((unsigned)kk < (unsigned)D) {
                             const float tkk = __fmaf_rn((float)kk - hD, dt, t0);
                             const float wq = chord_f(A, axis, fabsf((tkk - ph) - pc));
-                            rs = __fmaf_rn(wq, __ldg(sg + roff + kk), rs);
+                            rs = __fmaf_rn(wq, ld_op(sg + roff + kk), rs);
                         }
                     }
                     const float y = rs - cmp[r];
@@ -449,7 +456,7 @@ k_backproject_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
             for (int r = 0; r < kBpRows; ++r) {
                 const int iy = tl.y + ty + kBpWarps * r;
                 if (iy < n)
-                    part += bp_epilogue<float, EPI>(g, pb, a, ix, iy, ((double)s[r] - (double)cmp[r]) * g.h);
+                    part += bp_epilogue<float, EPI, TS>(g, pb, a, ix, iy, ((double)s[r] - (double)cmp[r]) * g.h);
             }
         }
         if (a.part) {
@@ -474,10 +481,16 @@ void launch_backproject_f32(const GeomDev *G, const ProbDev *P, const int4 *tile
     if (ntiles <= 0) return;
     count_launches(1);
     const int grid = min(ntiles, num_sms() * 2 * (a.ctas_per_sm > 0 ? a.ctas_per_sm : 8));
-#define WMG_BPF(E)                                                                                  \
-    case E:                                                                                         \
-        if (unit) k_backproject_f32<E, true><<<grid, 32 * kBpWarps, 0, st>>>(G, P, tiles, ntiles, a);  \
-        else k_backproject_f32<E, false><<<grid, 32 * kBpWarps, 0, st>>>(G, P, tiles, ntiles, a);      \
+#define WMG_BPF(E)                                                                                        \
+    case E:                                                                                               \
+        if (a.bf16) {                                                                                     \
+            if (unit) k_backproject_f32<E, true, __nv_bfloat16><<<grid, 32 * kBpWarps, 0, st>>>(G, P, tiles, ntiles, a); \
+            else k_backproject_f32<E, false, __nv_bfloat16><<<grid, 32 * kBpWarps, 0, st>>>(G, P, tiles, ntiles, a);    \
+        } else if (unit) {                                                                                \
+            k_backproject_f32<E, true, float><<<grid, 32 * kBpWarps, 0, st>>>(G, P, tiles, ntiles, a);   \
+        } else {                                                                                          \
+            k_backproject_f32<E, false, float><<<grid, 32 * kBpWarps, 0, st>>>(G, P, tiles, ntiles, a);  \
+        }                                                                                                 \
         break;
     switch (a.epi) {
         WMG_BPF(BP_STORE) WMG_BPF(BP_CGLS_S) WMG_BPF(BP_RESID) WMG_BPF(BP_POST)

@@ -158,6 +158,7 @@ struct BpArgs {
     const double *S;         // per-problem scalars
     double *out64;           // FP64 output (BP_GMRES_W, BP_ATB, BP_APPLY_A in FP64 mode)
     const int *part_base;    // FP32 kernels: problem p's first partial index (its one-image tile list)
+    int bf16;                // FP32 kernels: sinogram input and T image copies / outputs stored as bfloat16
 };
 
 struct PjArgs {
@@ -169,6 +170,7 @@ struct PjArgs {
     const double *S;         // scalars (active flags), or NULL = all active
     const int *part_base;    // FP32 kernel: problem p's first partial index (its one-image tile list)
     int group;               // FP32 kernel: images per tile of the tile list (1 or kProjGroup)
+    int bf16;                // FP32 kernels: image input and sinogram output stored as bfloat16
 };
 
 // Images per group tile of the FP32 projector (consecutive problems of one

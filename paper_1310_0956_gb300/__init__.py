@@ -28,7 +28,7 @@ WMG_NOT_CONVERGED = 1
 STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA_ERROR",
                 -4: "LEAF_NOT_SPD", -5: "BREAKDOWN", -6: "TIMEOUT", -7: "NAN", -8: "REJECTED"}
 
-PREC_F64, PREC_F32 = 0, 1
+PREC_F64, PREC_F32, PREC_F32_BF16STORE = 0, 1, 2
 CYCLE_ADDITIVE, CYCLE_HYBRID, CYCLE_SYMMETRIC, CYCLE_MULTIPLICATIVE = 0, 1, 2, 3
 SOLVER_SIRT, SOLVER_CGLS, SOLVER_GMRES, SOLVER_BICGSTAB = 0, 1, 2, 3
 KERNEL_STRIP, KERNEL_JOSEPH = 0, 1          # W: exact intersection lengths, or Joseph's kernel
@@ -164,7 +164,14 @@ def last_error() -> str:
     return buf.value.decode(errors="replace")
 
 
-def _check(rc: int, allow_not_converged: bool = False) -> int:
+# per-problem outcomes a solve reports in its info entries (the problem
+# ended, its last iterate in x), as opposed to errors of the call itself
+PROBLEM_STATUSES = (WMG_ERR_BREAKDOWN, WMG_ERR_NAN)
+
+
+def _check(rc: int, allow_not_converged: bool = False, allow=()) -> int:
+    if rc in allow:
+        return rc
     if rc < 0 or (rc == WMG_NOT_CONVERGED and not allow_not_converged):
         raise WmgError(rc, last_error())
     return rc
@@ -212,15 +219,15 @@ def wmg_leaf_inverse(plan, k, out, stream=None):
 
 
 def wmg_solve(plan, solver, preconditioned, count, b, x, max_iter, rtol, restart, info, res_hist,
-              stream=None) -> int:
+              stream=None, allow=()) -> int:
     return _check(lib().wmg_solve(plan, solver, preconditioned, count, b, x, max_iter, rtol, restart,
-                                  info, res_hist, stream), allow_not_converged=True)
+                                  info, res_hist, stream), allow_not_converged=True, allow=allow)
 
 
 def wmg_solve_x0(plan, solver, preconditioned, count, b, x0, x, max_iter, rtol, restart, info, res_hist,
-                 stream=None) -> int:
+                 stream=None, allow=()) -> int:
     return _check(lib().wmg_solve_x0(plan, solver, preconditioned, count, b, x0, x, max_iter, rtol, restart,
-                                     info, res_hist, stream), allow_not_converged=True)
+                                     info, res_hist, stream), allow_not_converged=True, allow=allow)
 
 
 def wmg_state_bytes(plan) -> int:
@@ -237,9 +244,9 @@ def wmg_state_import(plan, host, nbytes, stream=None) -> None:
     _check(lib().wmg_state_import(plan, host, nbytes, stream))
 
 
-def wmg_solve_resume(plan, count, b, x, max_iter, rtol, info, res_hist, stream=None) -> int:
+def wmg_solve_resume(plan, count, b, x, max_iter, rtol, info, res_hist, stream=None, allow=()) -> int:
     return _check(lib().wmg_solve_resume(plan, count, b, x, max_iter, rtol, info, res_hist, stream),
-                  allow_not_converged=True)
+                  allow_not_converged=True, allow=allow)
 
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -569,9 +576,12 @@ class Plan:
         return res
 
     def solve(self, b, solver=SOLVER_CGLS, preconditioned=True, max_iter=100, rtol=1e-4, restart=20,
-              out=None, history=False, x0=None):
-        """Returns (x, info list, residual histories or None). x0: initial
-        guess (wmg_solve_x0), default 0."""
+              out=None, history=False, x0=None, problem_errors=True):
+        """Returns (x, info list, residual histories or None, status). x0:
+        initial guess (wmg_solve_x0), default 0. problem_errors=False
+        returns a problem's breakdown or non-finite data as its info status
+        (x holds its last iterate) instead of raising WmgError."""
+        allow = () if problem_errors else PROBLEM_STATUSES
         bp, cnt = self._arg(b, self.M)
         out = out if out is not None else self._torch.empty(cnt * self.N, dtype=self.dtype, device=b.device)
         info = (wmg_solve_info * cnt)()
@@ -579,13 +589,13 @@ class Plan:
         xp = self._out(out, self.N, cnt)
         if x0 is None:
             rc = wmg_solve(self.handle, solver, 1 if preconditioned else 0, cnt, bp, xp, max_iter, rtol, restart,
-                           info, hist, self._stream())
+                           info, hist, self._stream(), allow=allow)
         else:
             x0p, c0 = self._arg(x0, self.N)
             if c0 != cnt:
                 raise ValueError("x0 must hold as many images as b has sinograms")
             rc = wmg_solve_x0(self.handle, solver, 1 if preconditioned else 0, cnt, bp, x0p, xp, max_iter, rtol,
-                              restart, info, hist, self._stream())
+                              restart, info, hist, self._stream(), allow=allow)
         return (out,) + self._results(cnt, max_iter, info, hist) + (rc,)
 
     def _results(self, cnt, max_iter, info, hist):
@@ -610,15 +620,16 @@ class Plan:
         buf = C.create_string_buffer(bytes(state), len(state))
         wmg_state_import(self.handle, buf, len(state), self._stream())
 
-    def resume(self, b, max_iter, rtol=1e-4, out=None, history=False):
+    def resume(self, b, max_iter, rtol=1e-4, out=None, history=False, problem_errors=True):
         """Continues the plan's solver state to max_iter iterations in total
         (wmg_solve_resume); returns as solve."""
+        allow = () if problem_errors else PROBLEM_STATUSES
         bp, cnt = self._arg(b, self.M)
         out = out if out is not None else self._torch.empty(cnt * self.N, dtype=self.dtype, device=b.device)
         info = (wmg_solve_info * cnt)()
         hist = (C.c_double * (cnt * (max_iter + 1)))() if history else None
         xp = self._out(out, self.N, cnt)
-        rc = wmg_solve_resume(self.handle, cnt, bp, xp, max_iter, rtol, info, hist, self._stream())
+        rc = wmg_solve_resume(self.handle, cnt, bp, xp, max_iter, rtol, info, hist, self._stream(), allow=allow)
         return (out,) + self._results(cnt, max_iter, info, hist) + (rc,)
 
 

@@ -29,7 +29,7 @@ def plan(monkeypatch):
 def test_resume_passes_the_problem_count(plan, monkeypatch):
     calls = []
 
-    def rec(handle, count, b, x, max_iter, rtol, info, hist, stream):
+    def rec(handle, count, b, x, max_iter, rtol, info, hist, stream, allow=()):
         calls.append((count, b, x, max_iter, rtol))
         for i in range(count):
             info[i].iters, info[i].status = max_iter, 1
@@ -45,7 +45,7 @@ def test_resume_passes_the_problem_count(plan, monkeypatch):
 
 
 def test_outputs_of_the_wrong_size_are_refused(plan, monkeypatch):
-    def never(*a):
+    def never(*a, **kw):
         raise AssertionError("the library was called")
     for name in ("wmg_solve", "wmg_solve_x0", "wmg_project", "wmg_backproject", "wmg_precond_apply",
                  "wmg_haar_analysis", "wmg_haar_synthesis"):
@@ -69,7 +69,7 @@ def test_outputs_of_the_wrong_size_are_refused(plan, monkeypatch):
 def test_solve_from_x0_marshals_both_buffers(plan, monkeypatch):
     calls = []
 
-    def rec(handle, solver, pre, count, b, x0, x, max_iter, rtol, restart, info, hist, stream):
+    def rec(handle, solver, pre, count, b, x0, x, max_iter, rtol, restart, info, hist, stream, allow=()):
         calls.append((solver, pre, count, b, x0, x, max_iter, restart))
         return 0
     monkeypatch.setattr(wmg, "wmg_solve_x0", rec)
@@ -110,3 +110,19 @@ def test_noalloc_projection_checks_its_buffers(monkeypatch):
         wmg.wmg_project_noalloc(n, m, D, x, b)                  # host tensors
     with pytest.raises(TypeError):
         wmg.wmg_project_noalloc(n, m, D, x.data_ptr(), b)       # a raw pointer
+
+
+def test_problem_statuses_are_returned_only_when_asked(plan, monkeypatch):
+    # a breakdown ends its problem with the last iterate in x: solve raises
+    # by default, and returns the status (with x and info) when asked
+    def rec(handle, solver, pre, count, b, x, max_iter, rtol, restart, info, hist, stream, allow=()):
+        info[0].iters, info[0].status = 3, wmg.WMG_ERR_BREAKDOWN
+        return wmg._check(wmg.WMG_ERR_BREAKDOWN, True, allow)
+    monkeypatch.setattr(wmg, "wmg_solve", rec)
+    b = torch.zeros(6, dtype=torch.float64)
+    with pytest.raises(wmg.WmgError):
+        plan.solve(b, wmg.SOLVER_BICGSTAB, False, 9, 0.0)
+    x, infos, _, rc = plan.solve(b, wmg.SOLVER_BICGSTAB, False, 9, 0.0, problem_errors=False)
+    assert rc == wmg.WMG_ERR_BREAKDOWN and infos[0][:2] == (3, wmg.WMG_ERR_BREAKDOWN) and x.numel() == 4
+    with pytest.raises(wmg.WmgError):                  # errors of the call itself still raise
+        wmg._check(wmg.WMG_ERR_INVALID_ARG, True, wmg.PROBLEM_STATUSES)

@@ -15,12 +15,12 @@ class StandInPlan:
     def _out(self, k):
         return torch.full((4,), float(k)), [(k, 1, 0.0)], None, 1
 
-    def solve(self, b, solver, preconditioned, k, rtol, restart):
+    def solve(self, b, solver, preconditioned, k, rtol, restart, problem_errors=True):
         assert rtol == 0.0
         self.calls.append(("solve", k))
         return self._out(k)
 
-    def resume(self, b, k, rtol):
+    def resume(self, b, k, rtol, problem_errors=True):
         assert rtol == 0.0
         self.calls.append(("resume", k))
         return self._out(k)

@@ -501,6 +501,9 @@ def run_ours(args, rank, world, local):
         prof["fp32_fma_tflops_measured"] = max(peaks["fp32_fma"], peaks["fp32_fma_paired"])
         roofline = roofline_entry(prof, P0, B)
         roofline["measured_peaks_tflops"] = peaks
+        roofline["operator_launches"] = {k: {"launches": prof[k]["launches"], "mean_ms": prof[k]["mean_ms"],
+                                             "images_per_launch": prof[k]["images_per_launch"]}
+                                         for k in ("project", "backproject")}
     comparator = None
     if not args.no_comparator and rank == 0:
         try:

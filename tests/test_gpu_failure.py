@@ -12,7 +12,10 @@ by plan creation, and the projector's bounded waits running out.
   kernel aborts its CTA and raises the library's error flag, the solve
   returns WMG_ERR_TIMEOUT, and the next solve on the same plan is correct:
   the context stays usable. No wait in that path is unbounded and no copy is
-  in flight when the kernel ends."""
+  in flight when the kernel ends.
+* A Krylov breakdown from host data alone: WMG-BiCGStab in an FP32 plan run
+  past convergence until its search vectors underflow the FP32 copies; the
+  problem ends with WMG_ERR_BREAKDOWN and its last (converged) iterate."""
 import os
 
 import numpy as np
@@ -62,3 +65,42 @@ def test_staged_copy_wait_runs_out_and_the_plan_stays_usable(monkeypatch):
     assert np.array_equal(x.cpu().numpy(), x_ok)
     plan.close()
     assert os.environ.get("WMG_TEST_STALL_STAGED_COPIES") is None
+
+
+def test_krylov_breakdown_ends_the_problem_with_its_last_iterate():
+    # Run past convergence (rtol 0), the recursive residual of WMG-BiCGStab
+    # shrinks geometrically; in an FP32 plan the operator's FP32 copies of
+    # the search vectors underflow (below 1e-45) before the FP64 residual is
+    # exactly zero, so <r^, v> is exactly 0: a breakdown. Geometry and data
+    # of the semi-convergence study (160^2, 400 angles x 160 bins, Joseph's
+    # kernel, 1 % uniform noise), lambda = 0.1 m / n.
+    n, m, D, levels = 160, 400, 160, 5
+    x = S.phantom(n, 12, S.seed_for(6, 0))
+    xd = torch.tensor(x.reshape(-1), dtype=torch.float32, device="cuda")
+    p64 = wmg.Plan(n, m, D, levels=0, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F64,
+                   kernel=wmg.KERNEL_JOSEPH)
+    b = p64.project(xd.double())
+    b = b + 0.01 * b.abs().max() * torch.tensor(S.uniform_noise_draws(m * D, S.seed_for(6, 0)),
+                                                dtype=torch.float64, device="cuda")
+    p64.close()
+    lam = 0.1 * m / n
+    plans = {prec: wmg.Plan(n, m, D, levels=levels, nu1=0, nu2=0, lam=lam, hybrid_depth=levels - 1,
+                            cycle=wmg.CYCLE_HYBRID, precision=prec, kernel=wmg.KERNEL_JOSEPH)
+             for prec in (wmg.PREC_F32, wmg.PREC_F64)}
+    b32 = b.float().contiguous()
+    pl = plans[wmg.PREC_F32]
+    with pytest.raises(wmg.WmgError) as e:
+        pl.solve(b32, wmg.SOLVER_BICGSTAB, True, 100, 0.0)
+    assert e.value.code == wmg.WMG_ERR_BREAKDOWN
+    x, info, _, rc = pl.solve(b32, wmg.SOLVER_BICGSTAB, True, 100, 0.0, problem_errors=False)
+    assert rc == wmg.WMG_ERR_BREAKDOWN and info[0][1] == wmg.WMG_ERR_BREAKDOWN and info[0][0] < 100
+    # the last iterate is the converged regularised solution (FP32 operator)
+    x64, info64, _, _ = plans[wmg.PREC_F64].solve(b32.double(), wmg.SOLVER_BICGSTAB, True, 200, 1e-12)
+    assert info64[0][1] == 0
+    x, x64 = x.double(), x64
+    assert float((x - x64).norm() / x64.norm()) < 1e-5
+    # and the plan goes on solving
+    _, info, _, rc = pl.solve(b32, wmg.SOLVER_BICGSTAB, True, 100, 1e-4)
+    assert rc == 0 and info[0][1] == 0
+    for p in plans.values():
+        p.close()

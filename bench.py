@@ -1033,8 +1033,8 @@ def load_peaks():
 # profiles/dram_traffic_k_project_backproject_256x256.md), per image; each
 # valid while its kernel's source is the one measured (hash), else null.
 KERNEL_TRAFFIC = {
-    "project": {"source": "paper_1310_0956_gb300/csrc/projector_tma.cu", "sha256_16": "6115a9f383afc7ae",
-                "bytes_per_image": (8497664 + 8498432) / 2 / 16.0},
+    "project": {"source": "paper_1310_0956_gb300/csrc/projector_tma.cu", "sha256_16": "f9582b6dbc04d33f",
+                "bytes_per_image": (8525056 + 8501248) / 2 / 16.0},
     "backproject": {"source": "paper_1310_0956_gb300/csrc/projector_f32.cu", "sha256_16": "f970788f2cb7205d",
                     "bytes_per_image": (4068608 + 4069632) / 2 / 16.0},
 }

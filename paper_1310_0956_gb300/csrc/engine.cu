@@ -526,7 +526,10 @@ static ProbSet *band_set(wmg_plan *pl, int d, const std::vector<int> &nodes, con
     return raw;
 }
 
-// Leaf-solve tiles: {first slot of a run of same-geometry slots, leaf, run length}.
+// Leaf-solve tiles: {first slot of a run of same-geometry slots, leaf, run
+// length, 0}. FP32 plans (tensor-core leaf solves): one work item per leaf,
+// chunk of at most kLeafTcProblems slots of a run and block of kLeafTcRows
+// rows of the inverse, {first slot, leaf, chunk length, row block}.
 static TileList *leaf_tiles(wmg_plan *pl, int d, const std::vector<int> &nodes, const std::vector<int> &slots,
                             cudaStream_t st)
 {
@@ -534,14 +537,23 @@ static TileList *leaf_tiles(wmg_plan *pl, int d, const std::vector<int> &nodes, 
     auto it = pl->leafsets.find(key);
     if (it != pl->leafsets.end()) return it->second.get();
     auto tl = std::make_unique<TileList>();
+    const bool tc = pl->prec != WMG_PREC_F64;
     size_t i = 0;
     while (i < slots.size()) {
         size_t j = i + 1;
         while (j < slots.size() && slots[j] == slots[j - 1] + 1 && pl->pgeo[slots[j]] == pl->pgeo[slots[i]]) ++j;
-        const int L = pl->geo(slots[i]).g.L;
+        const GeomDev &g = pl->geo(slots[i]).g;
+        const int run = (int)(j - i);
         for (int q : nodes)
-            for (int k = node_lo(L, d, q); k < node_hi(L, d, q); ++k)
-                tl->h.push_back(make_int4(slots[i], k, (int)(j - i), 0));
+            for (int k = node_lo(g.L, d, q); k < node_hi(g.L, d, q); ++k) {
+                if (!tc) {
+                    tl->h.push_back(make_int4(slots[i], k, run, 0));
+                    continue;
+                }
+                for (int c0 = 0; c0 < run; c0 += kLeafTcProblems)
+                    for (int mb = 0; mb * kLeafTcRows < g.P; ++mb)
+                        tl->h.push_back(make_int4(slots[i] + c0, k, std::min(kLeafTcProblems, run - c0), mb));
+            }
         i = j;
     }
     if (!tl->upload(pl->cap, st)) return nullptr;
@@ -1359,6 +1371,7 @@ static int32_t collect(wmg_plan *pl, int max_iter, wmg_solve_info *info, double 
     if (const int e = tma_error_take())
         return e == 1 ? fail(WMG_ERR_TIMEOUT, "projector: a wait for staged pixels timed out")
                       : fail(WMG_ERR_CUDA, "projector: a candidate pixel fell outside its staged box");
+    if (tc_error_take()) return fail(WMG_ERR_TIMEOUT, "leaf solves: a wait for the tensor-core products timed out");
     int32_t rc = WMG_OK;
     for (int i = 0; i < count; ++i) {
         const int q = pl->batch ? pl->order[i] : i;

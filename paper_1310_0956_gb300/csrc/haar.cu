@@ -13,9 +13,11 @@
 // FP64 iterate and write the operator-precision copies (row-major and
 // transposed) that the next projection reads.
 //
-// Leaf solves: e_k = D_k^-1 c_k with the stored symmetric inverse; one CTA per
-// leaf streams D_k^-1 once for every problem of a same-geometry group, thread
-// i forming e_i = sum_j D^-1[j][i] c_j (rows read coalesced, symmetry).
+// Leaf solves: e_k = D_k^-1 c_k with the stored symmetric inverse. FP64 plans
+// here: one CTA per leaf streams D_k^-1 once for every problem of a
+// same-geometry group, thread i forming e_i = sum_j D^-1[j][i] c_j (rows read
+// coalesced, symmetry). FP32 plans: a tensor-core matrix product per leaf
+// and group of problems (leaf_tc.cu).
 #include "kern_common.cuh"
 
 namespace wmg {
@@ -319,82 +321,14 @@ k_leaf_apply(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
     }
 }
 
-// FP32 leaf solves (F32 plans). Work item = (tile, group of NPB problems of
-// its run): blockIdx.y selects the group, so the problems of a long run are
-// spread over CTAs; thread i forms row i of D_k^{-1} [c_1 .. c_NPB] reading
-// column i of the symmetric inverse (consecutive threads, consecutive
-// addresses), the coefficients broadcast from shared memory, FP32 sums of the
-// P products, results added to / stored in FP64.
-template <int NPB>
-__global__ void __launch_bounds__(256)
-k_leaf_apply32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
-               const int4 *__restrict__ tiles, int ntiles, const double *__restrict__ C,
-               double *__restrict__ E, int accumulate, const double *__restrict__ S)
-{
-    // coefficient j of the group's problems side by side (row pitch NPB + 4:
-    // 16-byte rows for vector loads, fewer bank conflicts when filling)
-    constexpr int kPitch = NPB + 4;
-    __shared__ __align__(16) float cb[256][kPitch];
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int4 tl = tiles[t];
-        const GeomDev &g = G[P[tl.x].geom];
-        const int Pn = g.P, k = tl.y;
-        const float *__restrict__ Dk = static_cast<const float *>(g.leafinv) + (int64_t)k * Pn * Pn;
-      for (int pb = blockIdx.y * NPB; pb < tl.z; pb += gridDim.y * NPB) {   // CTA-uniform bounds
-        const int np = min(NPB, tl.z - pb);
-        for (int q = threadIdx.x; q < NPB * Pn; q += blockDim.x) {
-            const int pi = q / Pn, j = q - pi * Pn;
-            float v = 0.f;
-            if (pi < np) {
-                const ProbDev pd = P[tl.x + pb + pi];
-                if (slot_active(S, pd.slot)) v = (float)C[pd.coef + (int64_t)k * Pn + j];
-            }
-            cb[j][pi] = v;
-        }
-        __syncthreads();
-        const int i = threadIdx.x;
-        if (i < Pn) {
-            float acc[NPB];
-#pragma unroll
-            for (int u = 0; u < NPB; ++u) acc[u] = 0.f;
-#pragma unroll 4
-            for (int j = 0; j < Pn; ++j) {
-                const float d = __ldg(Dk + (int64_t)j * Pn + i);
-                const float4 *cj = reinterpret_cast<const float4 *>(cb[j]);
-#pragma unroll
-                for (int u4 = 0; u4 < NPB / 4; ++u4) {
-                    const float4 c = cj[u4];
-                    acc[4 * u4 + 0] = __fmaf_rn(d, c.x, acc[4 * u4 + 0]);
-                    acc[4 * u4 + 1] = __fmaf_rn(d, c.y, acc[4 * u4 + 1]);
-                    acc[4 * u4 + 2] = __fmaf_rn(d, c.z, acc[4 * u4 + 2]);
-                    acc[4 * u4 + 3] = __fmaf_rn(d, c.w, acc[4 * u4 + 3]);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < NPB; ++u) {
-                if (u < np) {
-                    const ProbDev pd = P[tl.x + pb + u];
-                    if (!slot_active(S, pd.slot)) continue;
-                    double *e = E + pd.coef + (int64_t)k * Pn + i;
-                    *e = accumulate ? *e + (double)acc[u] : (double)acc[u];
-                }
-            }
-        }
-        __syncthreads();
-      }
-    }
-}
-
 void launch_leaf_apply(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
                        const double *C, double *E, int accumulate, const double *S, bool fp32,
                        cudaStream_t st)
 {
     if (ntiles <= 0) return;
     count_launches(1);
-    if (fp32) {
-        // 4 CTAs share each tile's run of problems (groups of 16 strided by 64)
-        const dim3 grid(min(ntiles, num_sms() * 8), 4);
-        k_leaf_apply32<16><<<grid, 256, 0, st>>>(G, P, tiles, ntiles, C, E, accumulate, S);
+    if (fp32) {                       // F32 plans: tensor cores (leaf_tc.cu)
+        launch_leaf_apply_tc(G, P, tiles, ntiles, C, E, accumulate, S, st);
         return;
     }
     const int grid = min(ntiles, num_sms() * 8);

@@ -234,11 +234,24 @@ void launch_haar_synthesis(const GeomDev *G, const ProbDev *P, const int4 *tiles
                            int smem_elems, const HaarArgs &a, cudaStream_t st);
 
 // Leaf solves E[k] = Dinv_k C[k] for the problems of a group (haar.cu):
-// FP64 inverses and arithmetic (fp32 = false) or FP32 inverses and
-// arithmetic (F32 plans); C and E are FP64 in both. accumulate = 1 adds into E.
+// FP64 inverses and arithmetic (fp32 = false) or FP32 inverses on the tensor
+// cores (F32 plans, launch_leaf_apply_tc); C and E are FP64 in both.
+// accumulate = 1 adds into E.
 void launch_leaf_apply(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
                        const double *C, double *E, int accumulate, const double *S, bool fp32,
                        cudaStream_t st);
+
+// The FP32 form on the tensor cores (leaf_tc.cu): tcgen05 TF32 products of
+// split operands, FP32 accumulation in tensor memory, leaves of P <= 256.
+// Its tiles are work items {first problem, leaf k, count <= kLeafTcProblems
+// (consecutive same-geometry problems), row block of kLeafTcRows rows}.
+constexpr int kLeafTcProblems = 64;
+constexpr int kLeafTcRows = 128;
+void launch_leaf_apply_tc(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles, const double *C,
+                          double *E, int accumulate, const double *S, cudaStream_t st);
+// Error flag of the tensor-core leaf solves since the last call (0: none; 1:
+// a wait for the products timed out), cleared. Synchronising.
+int tc_error_take();
 
 // Setup (setup.cu).
 // fp32: profiles and pair sums in FP32 (FP64 accumulation over angles).

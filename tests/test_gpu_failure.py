@@ -1,5 +1,6 @@
 """Failure detection on the GPU without a GPU fault: a singular leaf reported
-by plan creation, and the projector's bounded waits running out.
+by plan creation, the projector's and the leaf solves' bounded waits running
+out, and a Krylov breakdown.
 
 * One angle and a 4-bin detector leave the leaf Galerkin blocks off the
   detector's band with exactly zero rows (the oracle pins this case), so
@@ -13,6 +14,11 @@ by plan creation, and the projector's bounded waits running out.
   returns WMG_ERR_TIMEOUT, and the next solve on the same plan is correct:
   the context stays usable. No wait in that path is unbounded and no copy is
   in flight when the kernel ends.
+* The tensor-core leaf solves wait, with a bound, for the products one of
+  their threads issues. The test hook WMG_TEST_STALL_TENSOR_PRODUCTS=1 makes
+  that thread issue none, so the waits run out after a short limit; every
+  CTA frees its tensor memory and returns, the solve returns
+  WMG_ERR_TIMEOUT, and the next solve on the same plan is correct.
 * A Krylov breakdown from host data alone: WMG-BiCGStab in an FP32 plan run
   past convergence until its search vectors underflow the FP32 copies; the
   problem ends with WMG_ERR_BREAKDOWN and its last (converged) iterate."""
@@ -65,6 +71,25 @@ def test_staged_copy_wait_runs_out_and_the_plan_stays_usable(monkeypatch):
     assert np.array_equal(x.cpu().numpy(), x_ok)
     plan.close()
     assert os.environ.get("WMG_TEST_STALL_STAGED_COPIES") is None
+
+
+def test_tensor_product_wait_runs_out_and_the_plan_stays_usable(monkeypatch):
+    P = S.workload_small().problems[0]
+    op = oracle.Op(P.n, P.m, P.D)
+    bs = torch.tensor(np.tile(op.project(P.image()), 3), dtype=torch.float32, device="cuda")
+    plan = wmg.Plan(P.n, P.m, P.D, levels=P.levels, nu1=0, nu2=0, hybrid_depth=1, cycle=wmg.CYCLE_HYBRID,
+                    precision=wmg.PREC_F32)
+    x_ok, info_ok, _, _ = plan.solve(bs, wmg.SOLVER_GMRES, True, max_iter=4, rtol=0.0)
+    x_ok = x_ok.cpu().numpy()
+    monkeypatch.setenv("WMG_TEST_STALL_TENSOR_PRODUCTS", "1")
+    with pytest.raises(wmg.WmgError) as e:
+        plan.solve(bs, wmg.SOLVER_GMRES, True, max_iter=4, rtol=0.0)
+    assert e.value.code == wmg.WMG_ERR_TIMEOUT
+    monkeypatch.delenv("WMG_TEST_STALL_TENSOR_PRODUCTS")
+    x, info, _, _ = plan.solve(bs, wmg.SOLVER_GMRES, True, max_iter=4, rtol=0.0)
+    assert info == info_ok
+    assert np.array_equal(x.cpu().numpy(), x_ok)
+    plan.close()
 
 
 def test_krylov_breakdown_ends_the_problem_with_its_last_iterate():

@@ -163,7 +163,7 @@ void build_tiles(const wmg_plan *pl, ProbSet &ps)
     for (int q = 0; q < ps.nprob;) {
         if (ps.h[q].geom < 0) { ++q; continue; }
         int e = q + 1;
-        while (e < ps.nprob && ps.h[e].geom == ps.h[q].geom) ++e;
+        while (e < ps.nprob && ps.h[e].geom == ps.h[q].geom && !(e < (int)ps.brk.size() && ps.brk[e])) ++e;
         const GeomDev &g = pl->geos[ps.h[q].geom]->g;
         int f = q;
         for (; f + kProjGroup <= e; f += kProjGroup)
@@ -1299,16 +1299,6 @@ extern "C" int32_t wmg_precond_apply(wmg_plan *pl, int32_t count, const void *s,
 // ---------------------------------------------------------------------------
 // Solvers (every slot of the plan's table; b and x in slot layout)
 // ---------------------------------------------------------------------------
-static int32_t any_active(wmg_plan *pl, cudaStream_t st, bool *any)
-{
-    std::vector<double> S((size_t)pl->cap * NSCAL);
-    WMG_CUDA(cudaMemcpyAsync(S.data(), pl->S.p, S.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-    WMG_CUDA(cudaStreamSynchronize(st));
-    *any = false;
-    for (int q = 0; q < pl->cap; ++q)
-        if (S[(size_t)q * NSCAL + SC_ACTIVE] != 0.0) *any = true;
-    return WMG_OK;
-}
 
 // Capture `body(stream)` (a fixed sequence of launches) into g on the plan's
 // private stream. Returns false (and leaves g empty) when graphs are off or
@@ -1354,6 +1344,183 @@ static int32_t replay(const Graph &g, cudaStream_t st)
     WMG_CUDA(cudaGraphLaunch(g.exec, st));
     return WMG_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Work lists of the problems still iterating. A batched solve runs until its
+// slowest problem has converged; the problems that have stopped are skipped
+// by every kernel (inactive flag), but their tiles are still scheduled, and
+// the FP32 projector's group tiles, the leaf solves' work items and the
+// band-update sets keep costing for every problem they cover. Once few
+// problems are left, the solver swaps in a set whose stopped slots have no
+// tiles at all -- the form a server's empty slots take -- and the slot list
+// the WMG cycle walks is cut to the same problems. Every problem keeps its
+// slot, offsets and arithmetic, and tiles never mix problems' sums, so the
+// bits of each problem are those of the full set.
+// ---------------------------------------------------------------------------
+static void swap_buf(DevBuf &a, DevBuf &b)
+{
+    std::swap(a.p, b.p);
+    std::swap(a.bytes, b.bytes);
+    std::swap(a.persistent, b.persistent);
+    std::swap(a.ast, b.ast);
+    std::swap(a.owner, b.owner);
+    std::swap(a.owner_stream, b.owner_stream);
+}
+static void swap_list(TileList &a, TileList &b)
+{
+    swap_buf(a.tiles, b.tiles);
+    swap_buf(a.tb, b.tb);
+    swap_buf(a.te, b.te);
+    std::swap(a.n, b.n);
+    std::swap(a.h, b.h);
+}
+static void swap_set(ProbSet &a, ProbSet &b)
+{
+    std::swap(a.nprob, b.nprob);
+    std::swap(a.h, b.h);
+    swap_buf(a.d, b.d);
+    swap_list(a.proj, b.proj); swap_list(a.bp, b.bp); swap_list(a.haar, b.haar);
+    swap_list(a.vimg, b.vimg); swap_list(a.vsino, b.vsino);
+    swap_list(a.projg, b.projg); swap_list(a.proj1, b.proj1);
+    std::swap(a.tma_n, b.tma_n);
+    std::swap(a.tma_count, b.tma_count);
+    std::swap(a.brk, b.brk);
+    std::swap(a.haar_smem, b.haar_smem);
+    std::swap(a.pj_ctas, b.pj_ctas);
+    std::swap(a.bp_ctas, b.bp_ctas);
+}
+
+// A restriction pays once the live slots have fallen to this fraction; a
+// projector group stays whole while this many of its problems are going.
+constexpr double kRestrictFraction = 0.75;
+constexpr int kGroupKeep = 3;
+
+// Restriction of a plan's work lists to the slots still iterating, for the
+// duration of one solve: restrict_to() swaps the restricted set into
+// pl->real and pl->live; the destructor swaps the plan's own set back and
+// drops the work-list caches built for restricted slot lists.
+class ActiveSet {
+  public:
+    explicit ActiveSet(wmg_plan *p) : pl_(p) {}
+    ActiveSet(const ActiveSet &) = delete;
+    ActiveSet &operator=(const ActiveSet &) = delete;
+    ~ActiveSet() { restore(); }
+    int size() const { return (int)pl_->live.size(); }
+    // The plan's own live slots whose active flag is set in the scalar table.
+    std::vector<int> active(const std::vector<double> &S) const
+    {
+        std::vector<int> a;
+        for (int q : on_ ? full_live_ : pl_->live)
+            if (S[(size_t)q * NSCAL + SC_ACTIVE] != 0.0) a.push_back(q);
+        return a;
+    }
+    bool on() const { return on_; }
+    const std::vector<int> &live() const { return pl_->live; }
+    // Restricts to the problems `going` (ascending, of the plan's own live
+    // slots). FP32 plans keep a projector group of the plan's own set whole
+    // while at least kGroupKeep of its problems are going (its other members
+    // are masked in the kernels, as in the full set); a sparser group is
+    // dropped and its going problems run one-image tiles. The slot list the
+    // WMG cycle walks is every present problem whose active flag is set.
+    // *changed: whether the work lists changed (they stay when the same
+    // problems would be present with the same active ones).
+    int32_t restrict_to(const std::vector<int> &going, const std::vector<double> &S, cudaStream_t st,
+                        bool *changed)
+    {
+        *changed = false;
+        if (!on_) {
+            for (auto &kv : pl_->bands) kb_.push_back(kv.first);
+            for (auto &kv : pl_->leafsets) kl_.push_back(kv.first);
+            for (auto &kv : pl_->segsets) ks_.push_back(kv.first);
+            full_live_ = pl_->live;
+        }
+        ProbSet &cur = pl_->real;
+        const ProbSet &own = on_ ? *full_ : cur;
+        const int np = own.nprob;
+        std::vector<char> go(np, 0), present(np, 0), brk(np, 0);
+        for (int q : going) go[q] = 1;
+        const bool groups = pl_->prec != WMG_PREC_F64;
+        // every kept group and every single problem is a run of its own
+        for (int q = 0; q < np;) {                   // the own set's runs and groups (build_tiles)
+            if (own.h[q].geom < 0) { ++q; continue; }
+            int e = q + 1;
+            while (e < np && own.h[e].geom == own.h[q].geom) ++e;
+            int f = q;
+            for (; groups && f + kProjGroup <= e; f += kProjGroup) {
+                int k = 0;
+                for (int b = 0; b < kProjGroup; ++b) k += go[f + b];
+                if (k >= kGroupKeep) {
+                    for (int b = 0; b < kProjGroup; ++b) present[f + b] = 1;
+                    brk[f] = 1;
+                } else {
+                    for (int b = 0; b < kProjGroup; ++b)
+                        if (go[f + b]) present[f + b] = brk[f + b] = 1;
+                }
+            }
+            for (; f < e; ++f)
+                if (go[f]) present[f] = brk[f] = 1;
+            q = e;
+        }
+        std::vector<int> live;
+        for (int q = 0; q < np; ++q)
+            if (present[q] && S[(size_t)q * NSCAL + SC_ACTIVE] != 0.0) live.push_back(q);
+        if (on_ && live == pl_->live) {
+            bool same = true;
+            for (int q = 0; q < np && same; ++q) same = (cur.h[q].geom >= 0) == (present[q] != 0);
+            if (same) return WMG_OK;
+        }
+        auto rs = std::make_unique<ProbSet>();
+        rs->nprob = np;
+        rs->h = own.h;
+        rs->brk = brk;
+        for (int q = 0; q < np; ++q)
+            if (!present[q]) rs->h[q].geom = -1;
+        build_tiles(pl_, *rs);
+        if (!upload_set(*rs, st)) return fail(WMG_ERR_OOM, "work-list allocation failed");
+        rs->pj_ctas = cur.pj_ctas;
+        rs->bp_ctas = cur.bp_ctas;
+        // the plan's own set is kept aside (first restriction) or the previous
+        // restricted set is held (later ones)
+        if (!on_) {
+            full_ = std::make_unique<ProbSet>();
+            swap_set(*full_, cur);
+        }
+        swap_set(cur, *rs);                  // rs now holds the previous restricted set (or nothing)
+        held_.push_back(std::move(rs));      // freed at restore (graphs may still name it)
+        pl_->live = live;
+        on_ = true;
+        *changed = true;
+        return WMG_OK;
+    }
+
+    // The plan's own set and slot list back (before the results are stored).
+    void restore()
+    {
+        if (!on_) return;
+        swap_set(pl_->real, *full_);
+        pl_->live = full_live_;
+        drop_new(pl_->bands, kb_);
+        drop_new(pl_->leafsets, kl_);
+        drop_new(pl_->segsets, ks_);
+        on_ = false;
+    }
+
+  private:
+    template <class M>
+    static void drop_new(M &m, const std::vector<std::vector<int>> &keep)
+    {
+        for (auto it = m.begin(); it != m.end();) {
+            if (std::find(keep.begin(), keep.end(), it->first) == keep.end()) it = m.erase(it);
+            else ++it;
+        }
+    }
+    wmg_plan *pl_;
+    bool on_ = false;
+    std::unique_ptr<ProbSet> full_;
+    std::vector<std::unique_ptr<ProbSet>> held_;
+    std::vector<int> full_live_;
+    std::vector<std::vector<int>> kb_, kl_, ks_;
+};
 
 // Per-slot results; `order` (optional) maps the caller's problem i to its slot.
 static int32_t collect(wmg_plan *pl, int max_iter, wmg_solve_info *info, double *res_hist, cudaStream_t st)
@@ -1577,21 +1744,34 @@ static int32_t solve_cgls(wmg_plan *pl, bool pre, const void *b, const void *x0,
         return step_end(s);
     };
     const int chunk = 4;
+    // once few problems are left, the iterations run on their work lists only
+    // (ActiveSet), eagerly, with the flags tested after every iteration
+    ActiveSet act(pl);
     Graph graph;
     bool graphed = false;
+    std::vector<double> Sh((size_t)pl->cap * NSCAL);
     for (int it = start; it < max_iter; ++it) {
         // the first iteration runs eagerly (it fills the work-list caches),
         // the others replay its captured graph
-        if (it == start + 1) graphed = capture(pl, graph, iteration);
+        if (it == start + 1 && !act.on()) graphed = capture(pl, graph, iteration);
         int32_t rc = graphed ? replay(graph, st) : iteration(st);
         if (rc) return rc;
-        if ((it + 1) % chunk == 0 || it + 1 == max_iter) {
-            bool any = false;
-            int32_t rc = any_active(pl, st, &any);
-            if (rc) return rc;
-            if (!any) break;
+        if ((it + 1) % (act.on() ? 1 : chunk) == 0 || it + 1 == max_iter) {
+            WMG_CUDA(cudaMemcpyAsync(Sh.data(), pl->S.p, Sh.size() * 8, cudaMemcpyDeviceToHost, st));
+            WMG_CUDA(cudaStreamSynchronize(st));
+            const std::vector<int> left = act.active(Sh);
+            if (left.empty()) break;
+            if (left.size() <= kRestrictFraction * act.size() && it + 1 < max_iter) {
+                bool changed = false;
+                if ((rc = act.restrict_to(left, Sh, st, &changed))) return rc;
+                if (changed) {
+                    graph.reset();
+                    graphed = false;
+                }
+            }
         }
     }
+    act.restore();
     ImgArgs io{};
     io.z = pl->x.as<double>(); io.out_op = xout;
     img_op<T>(pl, IMG_STORE_OUT, io, st);
@@ -1691,9 +1871,10 @@ static int32_t solve_gmres(wmg_plan *pl, bool pre, const void *b, const void *x0
     ga.sn = pl->gsn.as<double>(); ga.g = pl->gg.as<double>(); ga.y = pl->gy.as<double>();
     ga.h1 = pl->h1.as<double>(); ga.h2 = pl->h2.as<double>(); ga.jn = pl->jn.as<int>();
     ga.done = pl->done.as<int>(); ga.skip = pl->reo.as<int>(); ga.hist = hist; ga.hist_ld = hld;
+    // the work lists in use (the plan's own, or those of the problems left)
     const ProbDev *P = ps.d.as<ProbDev>();
     const int4 *vt = ps.vimg.tiles.as<int4>();
-    const int nv = ps.vimg.n;
+    int nv = ps.vimg.n;
     if (start == 0) {
         cudaMemsetAsync(pl->H.p, 0, (size_t)count * ldp * restart * 8, st);
         // f = W^T b ; r0 = f - A x0 ; V_0 = r0 / |r0|
@@ -1805,31 +1986,64 @@ static int32_t solve_gmres(wmg_plan *pl, bool pre, const void *b, const void *x0
         launch_gm_setv(P, vt, nv, V, vstride, ldp, 0, V, S, s);
         return WMG_OK;
     };
+    ActiveSet act(pl);                        // declared before the graphs that may name its lists
     Graph g_step, g_end;
     bool step_graphed = false, end_graphed = false, step_tried = false, end_tried = false;
-    int done_iters = start;
+    int done_iters = start, eager_steps = 0;
+    // Restriction to the problems left (ActiveSet): the Arnoldi steps run on
+    // the problems still iterating in the cycle (active, not done), the cycle
+    // end on every active problem (those done in the cycle update x and
+    // restart or stop there). Once restricted, the loop tests the flags after
+    // every step, and the launches stay eager (the lists change too often for
+    // graphs to pay).
+    std::vector<double> Sh((size_t)count * NSCAL);
+    std::vector<int> dn(count);
+    auto use = [&](const std::vector<int> &slots) -> int32_t {
+        bool changed = false;
+        int32_t rc = act.restrict_to(slots, Sh, st, &changed);
+        if (rc || !changed) return rc;
+        P = ps.d.as<ProbDev>();
+        vt = ps.vimg.tiles.as<int4>();
+        nv = ps.vimg.n;
+        g_step.reset(); g_end.reset();
+        step_graphed = end_graphed = false;
+        step_tried = end_tried = true;                 // no further captures
+        return WMG_OK;
+    };
+    auto read_flags = [&]() -> int32_t {
+        WMG_CUDA(cudaMemcpyAsync(dn.data(), pl->done.p, count * 4, cudaMemcpyDeviceToHost, st));
+        WMG_CUDA(cudaMemcpyAsync(Sh.data(), pl->S.p, Sh.size() * 8, cudaMemcpyDeviceToHost, st));
+        WMG_CUDA(cudaStreamSynchronize(st));
+        return WMG_OK;
+    };
     while (true) {
         cudaMemsetAsync(pl->done.p, 0, (size_t)count * 4, st);
         int j = 0;
         for (; j < restart && done_iters < max_iter; ++j, ++done_iters) {
-            // first step eager (fills the work-list caches), then the graph
-            if (!step_tried && done_iters == start + 1) {
+            // first step on a work list eager (fills the work-list caches), then the graph
+            if (!step_tried && eager_steps >= 1) {
                 step_tried = true;
                 step_graphed = capture(pl, g_step, arnoldi);
             }
+            if (!step_tried) ++eager_steps;
             int32_t rc = step_graphed ? replay(g_step, st) : arnoldi(st);
             if (rc) return rc;
-            if ((j + 1) % 4 == 0) {
-                std::vector<int> dn(count);
-                WMG_CUDA(cudaMemcpyAsync(dn.data(), pl->done.p, count * 4, cudaMemcpyDeviceToHost, st));
-                std::vector<double> Sh((size_t)count * NSCAL);
-                WMG_CUDA(cudaMemcpyAsync(Sh.data(), pl->S.p, Sh.size() * 8, cudaMemcpyDeviceToHost, st));
-                WMG_CUDA(cudaStreamSynchronize(st));
-                bool all = true;
-                for (int q = 0; q < count; ++q)
-                    if (Sh[(size_t)q * NSCAL + SC_ACTIVE] != 0.0 && !dn[q]) all = false;
-                if (all) { ++j; ++done_iters; break; }
+            if ((j + 1) % (act.on() ? 1 : 4) == 0) {
+                if ((rc = read_flags())) return rc;
+                std::vector<int> going;
+                for (int q : act.live())
+                    if (Sh[(size_t)q * NSCAL + SC_ACTIVE] != 0.0 && !dn[q]) going.push_back(q);
+                if (going.empty()) { ++j; ++done_iters; break; }
+                if (going.size() <= kRestrictFraction * act.size() && j + 1 < restart && done_iters + 1 < max_iter)
+                    if ((rc = use(going))) return rc;
             }
+        }
+        if (act.on()) {
+            // the cycle end takes every active problem, done ones included
+            int32_t rc = read_flags();
+            if (rc) return rc;
+            const std::vector<int> ending = act.active(Sh);
+            if (ending != act.live() && (rc = use(ending))) return rc;
         }
         if (end_tried && !end_graphed) {
             int32_t rc = cycle_end(st);
@@ -1843,11 +2057,13 @@ static int32_t solve_gmres(wmg_plan *pl, bool pre, const void *b, const void *x0
             end_tried = true;
             end_graphed = capture(pl, g_end, cycle_end);
         }
-        bool any = false;
-        int32_t rc = any_active(pl, st, &any);
+        int32_t rc = read_flags();
         if (rc) return rc;
-        if (!any || done_iters >= max_iter) break;
+        const std::vector<int> left = act.active(Sh);
+        if (left.empty() || done_iters >= max_iter) break;
+        if (left.size() <= kRestrictFraction * act.size() && (rc = use(left))) return rc;
     }
+    act.restore();
     ImgArgs io{};
     io.z = pl->x.as<double>(); io.out_op = xout;
     img_op<T>(pl, IMG_STORE_OUT, io, st);
@@ -1868,9 +2084,10 @@ static int32_t solve_bicgstab(wmg_plan *pl, bool pre, const void *b, const void 
     int32_t rc0 = solver_pools(pl, WMG_SOLVER_BICGSTAB, pre, 0);
     if (rc0) return rc0;
     const ProbSet &ps = pl->real;
+    // the work lists in use (the plan's own, or those of the problems left)
     const ProbDev *P = ps.d.as<ProbDev>();
     const int4 *vt = ps.vimg.tiles.as<int4>();
-    const int nv = ps.vimg.n;
+    int nv = ps.vimg.n;
     const double *S = pl->S.as<double>();
     double *hist = pl->hist.as<double>();
     const int hld = max_iter + 1;
@@ -1936,18 +2153,35 @@ static int32_t solve_bicgstab(wmg_plan *pl, bool pre, const void *b, const void 
         finalize(pl, FIN_BI_RES, ps.vimg, pa, 1, &ps.vimg, pb, 0, hist, hld, s);
         return WMG_OK;
     };
+    // once few problems are left, the iterations run on their work lists only
+    // (ActiveSet), eagerly, with the flags tested after every iteration
+    ActiveSet act(pl);
     Graph graph;
     bool graphed = false;
+    std::vector<double> Sh((size_t)pl->cap * NSCAL);
     for (int it = start; it < max_iter; ++it) {
-        if (it == start + 1) graphed = capture(pl, graph, iteration);
+        if (it == start + 1 && !act.on()) graphed = capture(pl, graph, iteration);
         int32_t rc = graphed ? replay(graph, st) : iteration(st);
         if (rc) return rc;
-        if ((it + 1) % 4 == 0 || it + 1 == max_iter) {
-            bool any = false;
-            if ((rc = any_active(pl, st, &any))) return rc;
-            if (!any) break;
+        if ((it + 1) % (act.on() ? 1 : 4) == 0 || it + 1 == max_iter) {
+            WMG_CUDA(cudaMemcpyAsync(Sh.data(), pl->S.p, Sh.size() * 8, cudaMemcpyDeviceToHost, st));
+            WMG_CUDA(cudaStreamSynchronize(st));
+            const std::vector<int> left = act.active(Sh);
+            if (left.empty()) break;
+            if (left.size() <= kRestrictFraction * act.size() && it + 1 < max_iter) {
+                bool changed = false;
+                if ((rc = act.restrict_to(left, Sh, st, &changed))) return rc;
+                if (changed) {
+                    P = ps.d.as<ProbDev>();
+                    vt = ps.vimg.tiles.as<int4>();
+                    nv = ps.vimg.n;
+                    graph.reset();
+                    graphed = false;
+                }
+            }
         }
     }
+    act.restore();
     ImgArgs io{};
     io.z = pl->x.as<double>(); io.out_op = xout;
     img_op<T>(pl, IMG_STORE_OUT, io, st);

@@ -144,6 +144,9 @@ struct ProbSet {
     // tma_count images, and each group's images are consecutive there
     int tma_n = 0;
     int64_t tma_count = 0;
+    // brk[q] != 0: a run of same-geometry problems (for the projector's
+    // groups) starts at q even if q - 1 has the same geometry (empty: none)
+    std::vector<char> brk;
     int haar_smem = 0;
     // launch shapes of the projector / backprojector over this set's tiles
     // (CTAs per SM; 0 = 8), chosen by autotune(); they do not change results
@@ -251,9 +254,12 @@ struct Graph {
     Graph() = default;
     Graph(const Graph &) = delete;
     Graph &operator=(const Graph &) = delete;
-    ~Graph()
+    ~Graph() { reset(); }
+    void reset()
     {
         if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        launches = 0;
     }
 };
 

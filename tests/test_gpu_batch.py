@@ -145,3 +145,54 @@ def test_grouped_projection_equals_single(geom):
     assert np.abs(got - ref).max() <= 3e-6 * max(np.abs(ref).max(), 1e-300)
     plan.close()
     single.close()
+
+
+@pytest.mark.parametrize("prec,solver,cycle", [
+    (wmg.PREC_F64, wmg.SOLVER_GMRES, wmg.CYCLE_HYBRID),
+    (wmg.PREC_F32, wmg.SOLVER_GMRES, wmg.CYCLE_HYBRID),
+    (wmg.PREC_F32, wmg.SOLVER_CGLS, wmg.CYCLE_ADDITIVE),
+    (wmg.PREC_F64, wmg.SOLVER_BICGSTAB, wmg.CYCLE_HYBRID),
+])
+def test_solvers_on_the_problems_left_equal_alone(prec, solver, cycle):
+    """Batched solves whose problems stop at different iterations: once few
+    are left, the solver runs the remaining problems' work lists only (the
+    stopped slots get no tiles, the WMG cycle walks the remaining slots; for
+    GMRES also without the problems whose cycle has ended, until the cycle
+    end). Every problem keeps the bits it gets alone: iterate, iteration
+    count, status and residual. Four zero sinograms stop before the first
+    iteration; noiseless and noisy phantoms, at 1e-4 (GMRES restarted every 5
+    iterations), stop at different iterations (GMRES: 14 .. 23 in the
+    oracle)."""
+    dt = torch.float64 if prec == wmg.PREC_F64 else torch.float32
+    n, m, D = 64, 90, 91
+    op = oracle.Op(n, m, D)
+    bs = []
+    for i in range(12):
+        if i % 3 == 1:
+            bs.append(np.zeros(op.M))
+            continue
+        b = op.project(S.phantom(n, 3 + i, S.seed_for(8, i)))
+        noise = 0.0 if i % 3 == 0 else 0.002 * i
+        bs.append(b + noise * np.abs(b).max() * S.noise_draws(op.M, S.seed_for(8, i)))
+    hd = 0 if cycle == wmg.CYCLE_ADDITIVE else 1
+    plan = wmg.Plan(n, m, D, levels=3, nu1=0, nu2=0, hybrid_depth=hd, cycle=cycle, precision=prec)
+    bt = torch.tensor(np.concatenate(bs), dtype=dt, device="cuda")
+    x, info, _, _ = plan.solve(bt, solver, True, max_iter=80, rtol=1e-4, restart=5)
+    torch.cuda.synchronize()
+    iters = [i[0] for i in info]
+    assert all(i[1] == 0 for i in info), info
+    if solver == wmg.SOLVER_GMRES:
+        assert len({(k - 1) // 5 for k in iters if k > 0}) >= 2, iters   # stopped in different cycles
+    else:
+        assert len({k for k in iters if k > 0}) >= 3, iters
+    for i in range(12):
+        xa, ia, _, _ = plan.solve(torch.tensor(bs[i], dtype=dt, device="cuda"), solver, True,
+                                  max_iter=80, rtol=1e-4, restart=5)
+        torch.cuda.synchronize()
+        assert ia[0] == info[i], i
+        assert torch.equal(xa, x[i * n * n:(i + 1) * n * n]), i
+    # and the batch again (the plan's own work lists were restored)
+    x2, info2, _, _ = plan.solve(bt, solver, True, max_iter=80, rtol=1e-4, restart=5)
+    torch.cuda.synchronize()
+    assert info2 == info and torch.equal(x2, x)
+    plan.close()

@@ -155,7 +155,8 @@ static int haar_width(const GeomDev &g)
 void build_tiles(const wmg_plan *pl, ProbSet &ps)
 {
     ps.proj.h.clear(); ps.bp.h.clear(); ps.haar.h.clear(); ps.vimg.h.clear(); ps.vsino.h.clear();
-    ps.projg.h.clear(); ps.proj1.h.clear();
+    ps.projg.h.clear(); ps.proj1.h.clear(); ps.bpg.h.clear(); ps.bp1.h.clear();
+    std::vector<char> in_bpg(ps.nprob, 0);
     ps.haar_smem = 0;
     // FP32 projector tiles: runs of consecutive problems of one geometry cut
     // into full groups of kProjGroup images (one tile per group, angle and
@@ -166,9 +167,16 @@ void build_tiles(const wmg_plan *pl, ProbSet &ps)
         while (e < ps.nprob && ps.h[e].geom == ps.h[q].geom && !(e < (int)ps.brk.size() && ps.brk[e])) ++e;
         const GeomDev &g = pl->geos[ps.h[q].geom]->g;
         int f = q;
-        for (; f + kProjGroup <= e; f += kProjGroup)
+        const bool bpg = pl->prec != WMG_PREC_F64 && g.unit == 2 && g.qpair;
+        for (; f + kProjGroup <= e; f += kProjGroup) {
             for (int a = 0; a < g.m; ++a)
                 for (int k0 = 0; k0 < g.D; k0 += 32) ps.projg.h.push_back(make_int4(f, a, k0, kProjGroup));
+            if (!bpg) continue;
+            for (int iy = 0; iy < g.n; iy += 32)
+                for (int ix = 0; ix < g.n; ix += 32)
+                    for (int b = 0; b < kProjGroup; b += kBpGroup) ps.bpg.h.push_back(make_int4(f + b, iy, ix, kBpGroup));
+            for (int b = 0; b < kProjGroup; ++b) in_bpg[f + b] = 1;
+        }
         for (; f < e; ++f)
             for (int a = 0; a < g.m; ++a)
                 for (int k0 = 0; k0 < g.D; k0 += 32) ps.proj1.h.push_back(make_int4(f, a, k0, 1));
@@ -208,7 +216,10 @@ void build_tiles(const wmg_plan *pl, ProbSet &ps)
         for (int a = 0; a < g.m; ++a)
             for (int k0 = 0; k0 < g.D; k0 += 32) ps.proj.h.push_back(make_int4(q, a, k0, 0));
         for (int iy = 0; iy < g.n; iy += 32)
-            for (int ix = 0; ix < g.n; ix += 32) ps.bp.h.push_back(make_int4(q, iy, ix, 0));
+            for (int ix = 0; ix < g.n; ix += 32) {
+                ps.bp.h.push_back(make_int4(q, iy, ix, 0));
+                if (!in_bpg[q]) ps.bp1.h.push_back(make_int4(q, iy, ix, 0));
+            }
         for (int cy = 0; cy < g.nc; ++cy)
             for (int x0 = 0; x0 < g.n; x0 += W) ps.haar.h.push_back(make_int4(q, cy * g.B, x0, W));
         for (int64_t s0 = 0; s0 < G.N; s0 += 8192)
@@ -224,6 +235,7 @@ bool upload_set(ProbSet &ps, cudaStream_t st)
     cudaMemcpyAsync(ps.d.p, ps.h.data(), ps.h.size() * sizeof(ProbDev), cudaMemcpyHostToDevice, st);
     return ps.proj.upload(ps.nprob, st) && ps.bp.upload(ps.nprob, st) && ps.haar.upload(ps.nprob, st) &&
            ps.projg.upload(ps.nprob, st) && ps.proj1.upload(ps.nprob, st) &&
+           ps.bpg.upload(ps.nprob, st) && ps.bp1.upload(ps.nprob, st) &&
            ps.vimg.upload(ps.nprob, st) && ps.vsino.upload(ps.nprob, st);
 }
 
@@ -342,7 +354,15 @@ void backproject(wmg_plan *pl, const ProbSet &ps, BpArgs a, cudaStream_t st)
     a.ctas_per_sm = ps.bp_ctas;
     a.part_base = ps.bp.tb.as<int>();
     if (pl->profiling) prof_begin(pl, 1, ps.nprob, st);
-    launch_backproject<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.bp.tiles.as<int4>(), ps.bp.n, a, st);
+    // FP32 storage: the group tiles (shared bins and weights, staged
+    // sinograms) and the other problems' one-image tiles; the same bits
+    if (sizeof(T) == 4 && ps.bpg.n > 0 &&
+        launch_backproject_f32_group(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.bpg.tiles.as<int4>(),
+                                     ps.bpg.n, a, st))
+        launch_backproject<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.bp1.tiles.as<int4>(), ps.bp1.n, a,
+                              st);
+    else
+        launch_backproject<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.bp.tiles.as<int4>(), ps.bp.n, a, st);
     if (pl->profiling) prof_end(pl, st);
 }
 
@@ -1382,6 +1402,7 @@ static void swap_set(ProbSet &a, ProbSet &b)
     swap_list(a.proj, b.proj); swap_list(a.bp, b.bp); swap_list(a.haar, b.haar);
     swap_list(a.vimg, b.vimg); swap_list(a.vsino, b.vsino);
     swap_list(a.projg, b.projg); swap_list(a.proj1, b.proj1);
+    swap_list(a.bpg, b.bpg); swap_list(a.bp1, b.bp1);
     std::swap(a.tma_n, b.tma_n);
     std::swap(a.tma_count, b.tma_count);
     std::swap(a.brk, b.brk);
@@ -1539,6 +1560,7 @@ static int32_t collect(wmg_plan *pl, int max_iter, wmg_solve_info *info, double 
         return e == 1 ? fail(WMG_ERR_TIMEOUT, "projector: a wait for staged pixels timed out")
                       : fail(WMG_ERR_CUDA, "projector: a candidate pixel fell outside its staged box");
     if (tc_error_take()) return fail(WMG_ERR_TIMEOUT, "leaf solves: a wait for the tensor-core products timed out");
+    if (bpg_error_take()) return fail(WMG_ERR_CUDA, "backprojector: a candidate bin fell outside its staged window");
     int32_t rc = WMG_OK;
     for (int i = 0; i < count; ++i) {
         const int q = pl->batch ? pl->order[i] : i;

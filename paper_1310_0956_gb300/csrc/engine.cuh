@@ -138,6 +138,11 @@ struct ProbSet {
     // groups of kProjGroup consecutive same-geometry problems, and one-image
     // tiles for the problems left over
     TileList projg, proj1;
+    // FP32 backprojector tiles: group tiles ({first problem, iy0, ix0,
+    // kBpGroup}) of the projector's groups whose geometry has unit bins
+    // covering every tile and quarter-turn pairs, and one-image tiles of the
+    // other problems
+    TileList bpg, bp1;
     // the group tiles read their pixels through TMA boxes (projector_tma.cu)
     // when every problem has image side tma_n (> 0; a multiple of 4) and bins
     // no wider than a pixel, its image is image number img / n^2 of a pool of

@@ -17,6 +17,7 @@
 // Deterministic: no atomics, fixed combination orders.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "bp_epilogue.cuh"
 #include "kern_common.cuh"
@@ -473,6 +474,262 @@ k_backproject_f32(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
             __syncthreads();
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Backward, group tiles: tile = {first problem, iy0, ix0, kBpGroup} of the
+// same 32 x 32 pixels of kBpGroup consecutive problems of one geometry with
+// unit bins covering every tile (GeomDev::unit == 2) and quarter-turn angle
+// pairs (GeomDev::qpair). Thread = one column and kBpRows rows 4 apart, as in
+// the one-image tile; every image gets exactly the arithmetic of
+// bp_unit_sums_qpair<true> (same candidates, weights, products, compensated
+// steps and epilogue order), so a problem's bits do not depend on its tile.
+// What the group shares is each pixel's candidate bins and weights, computed
+// once for the group's images, and the sinogram values come from shared
+// memory: per stage, kBgPairs angle pairs, the window of kBgW bins of each
+// angle that the tile's pixels can reach (from the tile's corners), for
+// every image, copied in by cp.async (zero fill off the detector), the
+// values of an image pair interleaved so that one 64-bit read gives both;
+// two stages, the copies of the next in flight while the current is summed.
+// Within a warp the 32 columns' bins at one angle span fewer than 32 bins,
+// so the reads are free of bank conflicts.
+// ---------------------------------------------------------------------------
+constexpr int kBgPairs = 8;                       // angle pairs per stage
+constexpr int kBgW = 56;                          // window width (bins); the tile's reach is < 51
+constexpr int kBgStageFloats = kBgPairs * 2 * kBpGroup * kBgW;
+constexpr size_t kBgSmem = 2 * (size_t)kBgStageFloats * sizeof(float);
+
+// 0 = fine; 1 = a candidate bin fell outside its staged window (a bound of
+// the window width did not hold; the read was clamped into the window)
+__device__ int g_bpg_error;
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// First bin of the window of angle a for the tile whose pixel centres span
+// x in [xa, xa + 31], y in [ya, ya + 31] (pixel widths from the image centre):
+// every candidate bin k = m0 + kofs, k + 1 of those pixels (m0 within one of
+// floor(tau)) lies in [floor(tau_min) + kofs - 2, floor(tau_max) + kofs + 3].
+__device__ __forceinline__ int bpg_window(const AngleF &A, float xa, float ya, int kofs)
+{
+    const float c = A.chi + A.clo, s = A.shi + A.slo;
+    const float t00 = __fmaf_rn(xa, c, ya * s), t10 = __fmaf_rn(xa + 31.f, c, ya * s);
+    const float t01 = __fmaf_rn(xa, c, (ya + 31.f) * s), t11 = __fmaf_rn(xa + 31.f, c, (ya + 31.f) * s);
+    const float tmin = fminf(fminf(t00, t10), fminf(t01, t11));
+    return (int)floorf(tmin) + kofs - 2;
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(32 * kBpWarps, kBpGroup == 8 ? 2 : 3)
+k_backproject_f32_group(const GeomDev *__restrict__ G, const ProbDev *__restrict__ P,
+                        const int4 *__restrict__ tiles, int ntiles, BpArgs a)
+{
+    constexpr int NI = kBpGroup;
+    constexpr float kRound = 12582912.f;   // 1.5 * 2^23
+    constexpr int kRoundBits = 0x4B400000;
+    extern __shared__ __align__(16) float win[];           // [stage][pair][angle][image pair][bin][2]
+    __shared__ int kwin[2][2 * kBgPairs];
+    __shared__ double red[NI][kBpWarps];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    bool bad = false;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 tl = tiles[t];
+        unsigned actm = 0;                                      // active images (bit b)
+#pragma unroll
+        for (int b = 0; b < NI; ++b) actm |= slot_active(a.S, P[tl.x + b].slot) ? 1u << b : 0u;
+        if (!actm) continue;                                    // CTA-uniform
+        const GeomDev &g = G[P[tl.x].geom];
+        const int n = g.n, m = g.m, D = g.D;
+        const int ix = tl.z + tx;
+        const float half_n = 0.5f * (float)n;
+        const float xo = (float)ix + 0.5f - half_n;
+        const float yo0 = (float)(tl.y + ty) + 0.5f - half_n;
+        const float xa = (float)tl.z + 0.5f - half_n, ya = (float)tl.y + 0.5f - half_n;
+        const bool odd = D & 1;
+        const float e = odd ? 0.5f : 0.f;
+        const int kofs = odd ? (D - 1) / 2 : D / 2 - 1;
+        const int npair = m / 2;
+        const int nstage = (npair + kBgPairs - 1) / kBgPairs;
+        // stage copies: warp ty takes the angles ty, ty + 4, ... of the stage
+        // (one window each), all images, lanes the bins (coalesced); inactive
+        // images are zero-filled
+        int64_t sino_of[NI];
+#pragma unroll
+        for (int b = 0; b < NI; ++b) sino_of[b] = P[tl.x + b].sino;
+        auto stage_copy = [&](int sidx, int buf) {
+            float *dst = win + (size_t)buf * kBgStageFloats;
+            const int pr0 = sidx * kBgPairs;
+            for (int slot = ty; slot < 2 * kBgPairs; slot += kBpWarps) {     // slot = 2 * pair + angle of pair
+                const int pr = pr0 + (slot >> 1);
+                const bool have = pr < npair;
+                const int ang = have ? ((slot & 1) ? pr + m / 2 : pr) : 0;
+                const int k0 = have ? bpg_window(g.angf[ang], xa, ya, kofs) : 0;
+                if (tx == 0) kwin[buf][slot] = k0;
+#pragma unroll
+                for (int b = 0; b < NI; ++b) {
+                    const float *src = static_cast<const float *>(a.sino) + sino_of[b] + (int64_t)ang * D;
+                    const bool on = have && ((actm >> b) & 1u);
+                    // image b's values of this angle: bins at stride 2 in its pair's row
+                    float *drow = dst + ((size_t)slot * (NI / 2) + (b >> 1)) * (2 * kBgW) + (b & 1);
+                    for (int q = tx; q < kBgW; q += 32) {
+                        const int k = k0 + q;
+                        const bool valid = on && (unsigned)k < (unsigned)D;
+                        cp_async4(drow + 2 * q, valid ? src + k : src, valid);
+                    }
+                }
+            }
+            cp_async_commit();
+        };
+        // sums and compensations of images 2 pr, 2 pr + 1 (x, y) and row r
+        float2 s2[NI / 2][kBpRows], c2[NI / 2][kBpRows];
+#pragma unroll
+        for (int pr = 0; pr < NI / 2; ++pr)
+#pragma unroll
+            for (int r = 0; r < kBpRows; ++r) { s2[pr][r] = make_float2(0.f, 0.f); c2[pr][r] = s2[pr][r]; }
+        const float dy = (float)kBpWarps;
+        const float2 kr2 = make_float2(kRound, kRound), nkr2 = make_float2(-kRound, -kRound);
+        const float2 m1 = make_float2(-1.f, -1.f), mh = make_float2(-0.5f, -0.5f), one = make_float2(1.f, 1.f);
+        stage_copy(0, 0);
+        for (int si = 0; si < nstage; ++si) {
+            const int buf = si & 1;
+            cp_async_wait_all();
+            __syncthreads();                                    // stage si in place; stage si - 1 read by all
+            if (si + 1 < nstage) stage_copy(si + 1, buf ^ 1);
+            const float *wst = win + (size_t)buf * kBgStageFloats;
+            const int np = min(kBgPairs, npair - si * kBgPairs);
+            for (int pl = 0; pl < np; ++pl) {
+                const int a0 = si * kBgPairs + pl;
+                const float4 *q0 = reinterpret_cast<const float4 *>(g.angf + a0);
+                const float4 t0 = __ldg(q0), c0 = __ldg(q0 + 1);
+                const float4 t1 = make_float4(-t0.z, -t0.w, t0.x, t0.y);
+                const float l0 = c0.z;
+                const int kb0 = kofs - kRoundBits - kwin[buf][2 * pl];
+                const int kb1 = kofs - kRoundBits - kwin[buf][2 * pl + 1];
+                // the pair's two angles: rows of image pairs, (value of image 2 q, of 2 q + 1) per bin
+                const float2 *w0p = reinterpret_cast<const float2 *>(wst + (size_t)(2 * pl) * NI * kBgW);
+                const float2 *w1p = w0p + (NI / 2) * kBgW;
+                float2 ph = make_float2(__fmaf_rn(xo, t0.x, yo0 * t0.z) - e, __fmaf_rn(xo, t1.x, yo0 * t1.z) - e);
+                float2 pc = make_float2(__fmaf_rn(xo, t0.y, yo0 * t0.w), __fmaf_rn(xo, t1.y, yo0 * t1.w));
+                const float2 dph = make_float2(dy * t0.z, dy * t1.z), dpc = make_float2(dy * t0.w, dy * t1.w);
+#pragma unroll
+                for (int r2 = 0; r2 < kBpRows / 2; ++r2) {
+                    int i0[2], i1[2];
+                    float wa0[2], wb0[2], wa1[2], wb1[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const float2 y = __fadd2_rn(__fadd2_rn(ph, pc), kr2);
+                        int l = __float_as_int(y.x) + kb0, l1 = __float_as_int(y.y) + kb1;
+                        bad |= (unsigned)l > (unsigned)(kBgW - 2) || (unsigned)l1 > (unsigned)(kBgW - 2);
+                        i0[h] = min(max(l, 0), kBgW - 2);
+                        i1[h] = min(max(l1, 0), kBgW - 2);
+                        float2 d = __ffma2_rn(ph, m1, __fadd2_rn(y, nkr2));
+                        d = __ffma2_rn(pc, m1, __fadd2_rn(d, mh));
+                        const float2 d1 = __fadd2_rn(d, one);
+                        wa0[h] = chord_n(c0.x, c0.y, fabsf(d.x));
+                        wb0[h] = chord_n(c0.x, c0.y, fabsf(d1.x));
+                        wa1[h] = chord_n(c0.x, c0.y, fabsf(d.y));
+                        wb1[h] = chord_n(c0.x, c0.y, fabsf(d1.y));
+                        ph = __fadd2_rn(ph, dph);
+                        pc = __fadd2_rn(pc, dpc);
+                    }
+                    // each image's products and compensated step are those of
+                    // the one-image tile (rows paired there, images here: the
+                    // same IEEE operations, each rounded to nearest)
+                    const float2 l02 = make_float2(l0, l0);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const float2 a0 = make_float2(wa0[h], wa0[h]), b0 = make_float2(wb0[h], wb0[h]);
+                        const float2 a1 = make_float2(wa1[h], wa1[h]), b1 = make_float2(wb1[h], wb1[h]);
+                        const int r = 2 * r2 + h;
+#pragma unroll
+                        for (int q = 0; q < NI / 2; ++q) {
+                            const float2 *u = w0p + q * kBgW, *v = w1p + q * kBgW;
+                            const float2 x0 = __ffma2_rn(a0, u[i0[h]], __fmul2_rn(b0, u[i0[h] + 1]));
+                            const float2 rs = __fmul2_rn(__ffma2_rn(a1, v[i1[h]], __ffma2_rn(b1, v[i1[h] + 1], x0)), l02);
+                            const float2 yk = __ffma2_rn(c2[q][r], m1, rs);
+                            const float2 tt = __fadd2_rn(s2[q][r], yk);
+                            c2[q][r] = __ffma2_rn(yk, m1, __ffma2_rn(s2[q][r], m1, tt));
+                            s2[q][r] = tt;
+                        }
+                    }
+                }
+            }
+        }
+        // epilogues, image by image, in the one-image tile's order
+#pragma unroll
+        for (int b = 0; b < NI; ++b) {
+            const ProbDev pb = P[tl.x + b];
+            double part = 0.0;
+            if (((actm >> b) & 1u) && ix < n) {
+#pragma unroll
+                for (int r = 0; r < kBpRows; ++r) {
+                    const int iy = tl.y + ty + kBpWarps * r;
+                    const float sv = (b & 1) ? s2[b >> 1][r].y : s2[b >> 1][r].x;
+                    const float cv = (b & 1) ? c2[b >> 1][r].y : c2[b >> 1][r].x;
+                    if (iy < n) part += bp_epilogue<float, EPI, float>(g, pb, a, ix, iy, ((double)sv - (double)cv) * g.h);
+                }
+            }
+            if (a.part) {
+                part = warp_sum_fixed(part);
+                if (tx == 0) red[b][ty] = part;
+            }
+        }
+        if (a.part) {
+            __syncthreads();
+            if (threadIdx.x < NI && ((actm >> threadIdx.x) & 1u)) {
+                const int b = threadIdx.x;
+                double v = 0.0;
+                for (int i = 0; i < kBpWarps; ++i) v += red[b][i];
+                const int ntx = (n + 31) / 32;
+                a.part[a.part_base[tl.x + b] + (tl.y / 32) * ntx + tl.z / 32] = v;
+            }
+        }
+        __syncthreads();                                        // window and red reused by the next tile
+    }
+    if (__any_sync(0xffffffffu, bad) && tx == 0) atomicExch(&g_bpg_error, 1);
+}
+
+bool launch_backproject_f32_group(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
+                                  const BpArgs &a, cudaStream_t st)
+{
+    if (ntiles <= 0) return true;
+    if (a.bf16) return false;
+    count_launches(1);
+    const int grid = min(ntiles, num_sms() * 2);
+#define WMG_BPG(E)                                                                                          \
+    case E: {                                                                                               \
+        static std::once_flag once_##E;                                                                     \
+        std::call_once(once_##E, [] {                                                                       \
+            cudaFuncSetAttribute(k_backproject_f32_group<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                 (int)kBgSmem);                                                             \
+        });                                                                                                 \
+        k_backproject_f32_group<E><<<grid, 32 * kBpWarps, kBgSmem, st>>>(G, P, tiles, ntiles, a);           \
+        break;                                                                                              \
+    }
+    switch (a.epi) {
+        WMG_BPG(BP_STORE) WMG_BPG(BP_CGLS_S) WMG_BPG(BP_RESID) WMG_BPG(BP_POST)
+        WMG_BPG(BP_APPLY_A) WMG_BPG(BP_SIRT) WMG_BPG(BP_GMRES_W) WMG_BPG(BP_ATB)
+        default: break;
+    }
+#undef WMG_BPG
+    return true;
+}
+
+int bpg_error_take()
+{
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_bpg_error, sizeof(int)) != cudaSuccess) return -1;
+    if (v) {
+        const int z = 0;
+        cudaMemcpyToSymbol(g_bpg_error, &z, sizeof(int));
+    }
+    return v;
 }
 
 void launch_backproject_f32(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,

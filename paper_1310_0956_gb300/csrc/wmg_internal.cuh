@@ -177,6 +177,10 @@ struct PjArgs {
 // geometry share the weight computation). The backprojector keeps one image
 // per tile: grouping cost it more occupancy than it saved (measured).
 constexpr int kProjGroup = 8;
+// Images per group tile of the FP32 backprojector (a divisor of kProjGroup:
+// each projector group's problems form kProjGroup / kBpGroup such tiles;
+// 4 measured 14 % slower than 8 on the 256-image batch).
+constexpr int kBpGroup = 8;
 
 template <class T>
 void launch_project(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
@@ -202,6 +206,14 @@ bool launch_project_f32_tma(const GeomDev *G, const ProbDev *P, const int4 *tile
 // copy wait timed out; 2: a candidate pixel outside its box), cleared.
 // Synchronising.
 int tma_error_take();
+// Group tiles {first problem, iy0, ix0, kBpGroup} of the FP32 backprojector
+// (projector_f32.cu): geometries with unit == 2 and quarter-turn pairs, FP32
+// storage; false: not launched (bfloat16 storage): use the one-image tiles.
+bool launch_backproject_f32_group(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
+                                  const BpArgs &a, cudaStream_t st);
+// Error flag of the group backprojector since the last call (0: none; 1: a
+// candidate bin outside its staged window), cleared. Synchronising.
+int bpg_error_take();
 template <class T>
 void launch_transpose(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
                       const void *src, void *dst, cudaStream_t st);

@@ -196,3 +196,37 @@ def test_solvers_on_the_problems_left_equal_alone(prec, solver, cycle):
     torch.cuda.synchronize()
     assert info2 == info and torch.equal(x2, x)
     plan.close()
+
+
+@pytest.mark.parametrize("n,m,D,levels", [(32, 24, 48, 2), (64, 36, 92, 3)])
+def test_backprojection_group_tiles_equal_one_image_tiles(n, m, D, levels):
+    """FP32 backprojection of 11 problems of one geometry whose bins cover
+    every pixel tile and whose angles come in quarter-turn pairs: the first 8
+    run the group tiles (shared bins and weights, staged sinogram windows),
+    the other 3 one-image tiles. Every problem equals its backprojection
+    alone bit for bit, and the FP64 oracle's W^T to FP32 rounding; the same
+    for the fused epilogue of a CGLS solve."""
+    op = oracle.Op(n, m, D)
+    plan = wmg.Plan(n, m, D, levels=levels, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F32)
+    rng = np.random.default_rng(n + m)
+    ys = rng.random((11, op.M))
+    yt = torch.tensor(ys.reshape(-1), dtype=torch.float32, device="cuda")
+    batch = plan.backproject(yt)
+    torch.cuda.synchronize()
+    batch_h = batch.double().cpu().numpy().reshape(11, -1)
+    for i in range(11):
+        alone = plan.backproject(yt[i * op.M:(i + 1) * op.M].contiguous())
+        torch.cuda.synchronize()
+        assert torch.equal(alone, batch[i * op.N:(i + 1) * op.N]), i
+        ref = op.backproject(ys[i].astype(np.float32).astype(np.float64))
+        assert np.abs(batch_h[i] - ref).max() <= 2e-6 * np.abs(ref).max(), i
+    bs = [op.project(S.phantom(n, 4, S.seed_for(9, i))) for i in range(11)]
+    bt = torch.tensor(np.concatenate(bs), dtype=torch.float32, device="cuda")
+    x, info, _, _ = plan.solve(bt, wmg.SOLVER_CGLS, True, max_iter=6, rtol=0.0)
+    torch.cuda.synchronize()
+    for i in (0, 7, 10):
+        xa, ia, _, _ = plan.solve(bt[i * op.M:(i + 1) * op.M].contiguous(), wmg.SOLVER_CGLS, True, max_iter=6,
+                                  rtol=0.0)
+        torch.cuda.synchronize()
+        assert ia[0] == info[i] and torch.equal(xa, x[i * op.N:(i + 1) * op.N]), i
+    plan.close()

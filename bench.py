@@ -107,8 +107,10 @@ def parse():
                          "uneven-batch rule, hybrid depth 1), print its setup time and exit: the case for "
                          "ncu launch lists of the leaf setup")
     ap.add_argument("--kernel-case", action="store_true",
-                    help="run 3 projector and 3 backprojector launches on a batch of 16 images of the "
-                         "workload geometry (FP32) and exit: the small case for ncu captures")
+                    help="run 3 projector and 3 backprojector launches on a batch of --kernel-images images "
+                         "of the workload geometry (FP32) and exit: the small case for ncu captures")
+    ap.add_argument("--kernel-images", type=int, default=16,
+                    help="images of the --kernel-case batch (16: 2 group tiles per angle and ray block)")
     return ap.parse_args()
 
 
@@ -1028,15 +1030,15 @@ def load_peaks():
 
 
 # DRAM traffic of the FP32 projector (8-image TMA group tiles) and
-# backprojector measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum,
-# 16-image launches of the workload geometry;
+# backprojector (8-image group tiles) measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum, 16- and 64-image launches of the workload geometry;
 # profiles/dram_traffic_k_project_backproject_256x256.md), per image; each
 # valid while its kernel's source is the one measured (hash), else null.
 KERNEL_TRAFFIC = {
     "project": {"source": "paper_1310_0956_gb300/csrc/projector_tma.cu", "sha256_16": "f9582b6dbc04d33f",
                 "bytes_per_image": (8525056 + 8501248) / 2 / 16.0},
-    "backproject": {"source": "paper_1310_0956_gb300/csrc/projector_f32.cu", "sha256_16": "f970788f2cb7205d",
-                    "bytes_per_image": (4068608 + 4069632) / 2 / 16.0},
+    "backproject": {"source": "paper_1310_0956_gb300/csrc/projector_f32.cu", "sha256_16": "1d3603b8486cb0f1",
+                    "bytes_per_image": (16431360 + 16428800 + 16427776) / 3 / 64.0},
 }
 
 
@@ -1115,14 +1117,14 @@ def solve_case(batch: int):
     print(json.dumps({"solve_case": "ok", "iters_mean": its}))
 
 
-def kernel_case():
+def kernel_case(images: int = 16):
     import torch
     import paper_1310_0956_gb300 as wmg
     P0 = workload_problems(1, 0)[0]
     plan = wmg.Plan(P0.n, P0.m, P0.D, levels=0, nu1=0, nu2=0, cycle=wmg.CYCLE_ADDITIVE,
                     precision=wmg.PREC_F32)
-    x = torch.rand(16 * P0.N, dtype=torch.float32, device="cuda")
-    b = torch.empty(16 * P0.M, dtype=torch.float32, device="cuda")
+    x = torch.rand(images * P0.N, dtype=torch.float32, device="cuda")
+    b = torch.empty(images * P0.M, dtype=torch.float32, device="cuda")
     y = torch.empty_like(x)
     for _ in range(3):
         plan.project(x, out=b)
@@ -1172,7 +1174,7 @@ def main():
         setup_case(args.setup_case)
         return
     if args.kernel_case:
-        kernel_case()
+        kernel_case(args.kernel_images)
         return
     if args.solve_case:
         solve_case(args.batch)

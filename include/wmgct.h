@@ -252,7 +252,9 @@ int32_t wmg_solve_x0(wmg_plan *plan, int32_t solver, int32_t preconditioned, int
 
 /* ---- checkpoint / resume ----------------------------------------------------
  * A plan (wmg_plan_create) keeps the state of its last wmg_solve or
- * wmg_solve_x0 that returned WMG_OK or WMG_NOT_CONVERGED: the FP64 iterate,
+ * wmg_solve_x0 that ran to its end: returned WMG_OK or WMG_NOT_CONVERGED, or
+ * the status of a problem that stopped on its own (WMG_ERR_BREAKDOWN,
+ * WMG_ERR_NAN; such a problem keeps its result when resumed): the FP64 iterate,
  * the solver's other vectors (CGLS: r, p, s; GMRES at its last restart:
  * W^T b, the true residual, rotation data; BiCGStab: r, the shadow
  * residual, p, v; operator-precision copies included) and per-problem

@@ -2236,6 +2236,10 @@ static int32_t check_solve_args(wmg_plan *pl, int32_t solver, int32_t preconditi
     return WMG_OK;
 }
 
+// Statuses a solve reports for single problems (the others ran on): the
+// solve's state stays a valid continuation point.
+static bool problem_status(int32_t rc) { return rc == WMG_ERR_BREAKDOWN || rc == WMG_ERR_NAN; }
+
 static int32_t run_solve(wmg_plan *pl, int32_t solver, int32_t preconditioned, const void *b, const void *x0,
                          void *x, int32_t max_iter, double rtol, int32_t restart, wmg_solve_info *info,
                          double *res_hist, cudaStream_t st)
@@ -2248,7 +2252,7 @@ static int32_t run_solve(wmg_plan *pl, int32_t solver, int32_t preconditioned, c
     int32_t rc = WMG_DISPATCH(pl, do_solve, pl, solver, preconditioned != 0, b, x0, x, max_iter, restart, 0, st);
     if (rc) return rc;
     rc = collect(pl, max_iter, info, res_hist, st);
-    if (rc >= 0 && !pl->batch) {
+    if ((rc >= 0 || problem_status(rc)) && !pl->batch) {
         SolveState &s = pl->state;
         s.valid = true;
         s.solver = solver; s.pre = preconditioned != 0; s.restart = solver == WMG_SOLVER_GMRES ? restart : 0;
@@ -2452,7 +2456,7 @@ extern "C" int32_t wmg_solve_resume(wmg_plan *pl, int32_t count, const void *b, 
         if (rc) return rc;
     }
     rc = collect(pl, max_iter, info, res_hist, st);
-    if (rc < 0) pl->state.valid = false;
+    if (rc < 0 && !problem_status(rc)) pl->state.valid = false;
     return rc;
 }
 

@@ -124,6 +124,16 @@ def test_krylov_breakdown_ends_the_problem_with_its_last_iterate():
     assert info64[0][1] == 0
     x, x64 = x.double(), x64
     assert float((x - x64).norm() / x64.norm()) < 1e-5
+    # a broken-down solve stays a continuation point: the semi-convergence
+    # curve runs on through it (Section 4.2), every k past the breakdown
+    # reporting the iterate and iteration count the breakdown left
+    k_bd = info[0][0]
+    state = pl.state_export()
+    assert len(state) > 0
+    from paper_1310_0956_gb300 import study
+    curve = study.error_curve(pl, b32, xd, wmg.SOLVER_BICGSTAB, True, [4, k_bd + 1, 100])
+    assert curve[0][1] == 4 and curve[1][1] == k_bd and curve[2][1] == k_bd
+    assert curve[1][2] == curve[2][2]
     # and the plan goes on solving
     _, info, _, rc = pl.solve(b32, wmg.SOLVER_BICGSTAB, True, 100, 1e-4)
     assert rc == 0 and info[0][1] == 0

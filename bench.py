@@ -1031,14 +1031,14 @@ def load_peaks():
 
 # DRAM traffic of the FP32 projector (8-image TMA group tiles) and
 # backprojector (8-image group tiles) measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum, 16- and 64-image launches of the workload geometry;
+# dram__bytes_write.sum, 64-image launches of the workload geometry;
 # profiles/dram_traffic_k_project_backproject_256x256.md), per image; each
 # valid while its kernel's source is the one measured (hash), else null.
 KERNEL_TRAFFIC = {
-    "project": {"source": "paper_1310_0956_gb300/csrc/projector_tma.cu", "sha256_16": "f9582b6dbc04d33f",
-                "bytes_per_image": (8525056 + 8501248) / 2 / 16.0},
-    "backproject": {"source": "paper_1310_0956_gb300/csrc/projector_f32.cu", "sha256_16": "1d3603b8486cb0f1",
-                    "bytes_per_image": (16431360 + 16428800 + 16427776) / 3 / 64.0},
+    "project": {"source": "paper_1310_0956_gb300/csrc/projector_tma.cu", "sha256_16": "ae0bdc1d96090fc7",
+                "bytes_per_image": (33875712 + 11776 + 33876992 + 33878272) / 3 / 64.0},
+    "backproject": {"source": "paper_1310_0956_gb300/csrc/projector_f32.cu", "sha256_16": "944267f066ebc531",
+                    "bytes_per_image": (16432384 + 16489984 + 16479232) / 3 / 64.0},
 }
 
 

@@ -10,6 +10,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -61,6 +62,16 @@ static bool proj_tma_default()
 
 static std::atomic<long long> g_launches{0};
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+void ensure_dyn_smem(const void *fn, int bytes)
+{
+    static std::mutex mu;
+    static std::set<std::pair<int, const void *>> done;
+    int d = 0;
+    cudaGetDevice(&d);
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.insert({d, fn}).second) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
 
 int num_sms()
 {

@@ -38,7 +38,6 @@
 // problem gets the same bits alone and in any batch.
 #include <cstdint>
 #include <cstdlib>
-#include <mutex>
 
 #include "kern_common.cuh"
 
@@ -361,10 +360,7 @@ void launch_leaf_apply_tc(const GeomDev *G, const ProbDev *P, const int4 *tiles,
                           double *E, int accumulate, const double *S, cudaStream_t st)
 {
     if (ntiles <= 0) return;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        cudaFuncSetAttribute(k_leaf_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-    });
+    ensure_dyn_smem((const void *)k_leaf_apply_tc, (int)kSmem);
     count_launches(1);
     const int grid = min(ntiles, 2 * num_sms());                 // two CTAs per SM (shared memory)
     const bool stall = tc_stall_requested();

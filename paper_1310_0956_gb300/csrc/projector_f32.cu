@@ -17,7 +17,6 @@
 // Deterministic: no atomics, fixed combination orders.
 #include <cmath>
 #include <cstring>
-#include <mutex>
 
 #include "bp_epilogue.cuh"
 #include "kern_common.cuh"
@@ -703,15 +702,10 @@ bool launch_backproject_f32_group(const GeomDev *G, const ProbDev *P, const int4
     count_launches(1);
     const int grid = min(ntiles, num_sms() * 2);
 #define WMG_BPG(E)                                                                                          \
-    case E: {                                                                                               \
-        static std::once_flag once_##E;                                                                     \
-        std::call_once(once_##E, [] {                                                                       \
-            cudaFuncSetAttribute(k_backproject_f32_group<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                 (int)kBgSmem);                                                             \
-        });                                                                                                 \
+    case E:                                                                                                 \
+        ensure_dyn_smem((const void *)k_backproject_f32_group<E>, (int)kBgSmem);                            \
         k_backproject_f32_group<E><<<grid, 32 * kBpWarps, kBgSmem, st>>>(G, P, tiles, ntiles, a);           \
-        break;                                                                                              \
-    }
+        break;
     switch (a.epi) {
         WMG_BPG(BP_STORE) WMG_BPG(BP_CGLS_S) WMG_BPG(BP_RESID) WMG_BPG(BP_POST)
         WMG_BPG(BP_APPLY_A) WMG_BPG(BP_SIRT) WMG_BPG(BP_GMRES_W) WMG_BPG(BP_ATB)

@@ -435,10 +435,7 @@ bool launch_project_f32_tma(const GeomDev *G, const ProbDev *P, const int4 *tile
         return false;
     CUtensorMap mi, mt;
     if (!encode_pool_map(&mi, a.img, n, count) || !encode_pool_map(&mt, a.imgT, n, count)) return false;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        cudaFuncSetAttribute(k_project_f32_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-    });
+    ensure_dyn_smem((const void *)k_project_f32_tma, (int)kSmemBytes);
     count_launches(1);
     const int grid = min(ntiles, 2 * num_sms());               // two CTAs per SM
     const bool stall = stall_requested();

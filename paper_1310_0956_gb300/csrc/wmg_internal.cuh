@@ -245,6 +245,10 @@ template <class TIn, class TOut>
 void launch_haar_synthesis(const GeomDev *G, const ProbDev *P, const int4 *tiles, int ntiles,
                            int smem_elems, const HaarArgs &a, cudaStream_t st);
 
+// Lets kernel `fn` take `bytes` of dynamic shared memory on the current
+// device (once per device and kernel; thread-safe).
+void ensure_dyn_smem(const void *fn, int bytes);
+
 // Leaf solves E[k] = Dinv_k C[k] for the problems of a group (haar.cu):
 // FP64 inverses and arithmetic (fp32 = false) or FP32 inverses on the tensor
 // cores (F32 plans, launch_leaf_apply_tc); C and E are FP64 in both.

@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "active_groups.h"
 #include "engine.cuh"
 
 namespace wmg {
@@ -1469,30 +1470,11 @@ class ActiveSet {
         ProbSet &cur = pl_->real;
         const ProbSet &own = on_ ? *full_ : cur;
         const int np = own.nprob;
-        std::vector<char> go(np, 0), present(np, 0), brk(np, 0);
+        std::vector<int> geom(np);
+        std::vector<char> go(np, 0), present, brk;
+        for (int q = 0; q < np; ++q) geom[q] = own.h[q].geom;
         for (int q : going) go[q] = 1;
-        const bool groups = pl_->prec != WMG_PREC_F64;
-        // every kept group and every single problem is a run of its own
-        for (int q = 0; q < np;) {                   // the own set's runs and groups (build_tiles)
-            if (own.h[q].geom < 0) { ++q; continue; }
-            int e = q + 1;
-            while (e < np && own.h[e].geom == own.h[q].geom) ++e;
-            int f = q;
-            for (; groups && f + kProjGroup <= e; f += kProjGroup) {
-                int k = 0;
-                for (int b = 0; b < kProjGroup; ++b) k += go[f + b];
-                if (k >= kGroupKeep) {
-                    for (int b = 0; b < kProjGroup; ++b) present[f + b] = 1;
-                    brk[f] = 1;
-                } else {
-                    for (int b = 0; b < kProjGroup; ++b)
-                        if (go[f + b]) present[f + b] = brk[f + b] = 1;
-                }
-            }
-            for (; f < e; ++f)
-                if (go[f]) present[f] = brk[f] = 1;
-            q = e;
-        }
+        active_groups(geom, go, pl_->prec != WMG_PREC_F64, kProjGroup, kGroupKeep, present, brk);
         std::vector<int> live;
         for (int q = 0; q < np; ++q)
             if (present[q] && S[(size_t)q * NSCAL + SC_ACTIVE] != 0.0) live.push_back(q);

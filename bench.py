@@ -106,6 +106,8 @@ def parse():
                     help="create one FP32 plan of an N x N image and M angles (detectors and levels by the "
                          "uneven-batch rule, hybrid depth 1), print its setup time and exit: the case for "
                          "ncu launch lists of the leaf setup")
+    ap.add_argument("--batched-case", action="store_true",
+                    help="solve the uneven batch four times (one warm-up) and exit: the case for ncu launch lists")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run 3 projector and 3 backprojector launches on a batch of --kernel-images images "
                          "of the workload geometry (FP32) and exit: the small case for ncu captures")
@@ -829,7 +831,9 @@ def fp64_single_leg(geoms, bs64, solver, hybrid_depth, cycle, x_mixed, dev) -> d
             "timing": "host clock around each synchronising one-problem solve, setup excluded"}
 
 
-def batched_leg(args, dev) -> dict:
+def batched_inputs(dev):
+    """The uneven batch of 64 problems and their noisy FP32 sinograms
+    (projected by FP64 plans)."""
     import torch
     import paper_1310_0956_gb300 as wmg
 
@@ -842,9 +846,22 @@ def batched_leg(args, dev) -> dict:
         bs.append(b64.to(torch.float32).contiguous())
         op.close()
     torch.cuda.synchronize()
+    return probs, bs
+
+
+def batched_plans(probs):
+    import paper_1310_0956_gb300 as wmg
+    return wmg.Batch([dict(n=p.n, m=p.m, D=p.D, levels=p.levels, lam=SERVING_EPS * p.m / p.n) for p in probs],
+                     nu1=NU1, nu2=NU2, hybrid_depth=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F32)
+
+
+def batched_leg(args, dev) -> dict:
+    import torch
+    import paper_1310_0956_gb300 as wmg
+
+    probs, bs = batched_inputs(dev)
     t0 = time.perf_counter()
-    bt = wmg.Batch([dict(n=p.n, m=p.m, D=p.D, levels=p.levels, lam=SERVING_EPS * p.m / p.n) for p in probs],
-                   nu1=NU1, nu2=NU2, hybrid_depth=0, cycle=wmg.CYCLE_ADDITIVE, precision=wmg.PREC_F32)
+    bt = batched_plans(probs)
     torch.cuda.synchronize()
     setup = time.perf_counter() - t0
     outs = [torch.empty(p.N, dtype=torch.float32, device=dev) for p in probs]
@@ -1117,6 +1134,24 @@ def solve_case(batch: int):
     print(json.dumps({"solve_case": "ok", "iters_mean": its}))
 
 
+def batched_case():
+    """Three solves of the uneven batch (the batched leg's inputs and solver)
+    after one warm-up, and exit: the case for ncu launch lists of that leg."""
+    import torch
+    import paper_1310_0956_gb300 as wmg
+    dev = torch.device("cuda", 0)
+    probs, bs = batched_inputs(dev)
+    bt = batched_plans(probs)
+    outs = [torch.empty(p.N, dtype=torch.float32, device=dev) for p in probs]
+    its = []
+    for _ in range(4):
+        _, infos, _ = bt.solve(bs, wmg.SOLVER_CGLS, True, MAX_ITER, RTOL, outs=outs)
+        its.append(float(np.mean([i[0] for i in infos])))
+    torch.cuda.synchronize()
+    bt.close()
+    print(json.dumps({"batched_case": "ok", "iters_mean": its}))
+
+
 def kernel_case(images: int = 16):
     import torch
     import paper_1310_0956_gb300 as wmg
@@ -1178,6 +1213,9 @@ def main():
         return
     if args.solve_case:
         solve_case(args.batch)
+        return
+    if args.batched_case:
+        batched_case()
         return
     if args.impl == "reference":
         run_reference(args, rank, world)

@@ -507,7 +507,7 @@ def run_ours(args, rank, world, local):
         roofline["measured_peaks_tflops"] = peaks
         roofline["operator_launches"] = {k: {"launches": prof[k]["launches"], "mean_ms": prof[k]["mean_ms"],
                                              "images_per_launch": prof[k]["images_per_launch"]}
-                                         for k in ("project", "backproject")}
+                                         for k in ("project", "backproject", "project_2h")}
     comparator = None
     if not args.no_comparator and rank == 0:
         try:

@@ -473,7 +473,9 @@ int64_t wmg_launch_count(int32_t reset);
  * between wmg_profile_begin and wmg_profile_end every such launch is
  * bracketed by CUDA events recorded on its stream (adds a few microseconds
  * per launch; for measurement runs only). wmg_profile_end synchronises the
- * stream and fills *out. */
+ * stream and fills *out. Projections on the 2h grid (the hybrid cycle's band
+ * updates whose input lies in the first split's LL band: n/2 x n/2 images,
+ * about half the nonzeros of W) are counted apart from those of W. */
 typedef struct wmg_profile_stats {
     int32_t project_launches;
     double project_ms;            /* summed device time */
@@ -482,6 +484,9 @@ typedef struct wmg_profile_stats {
     double backproject_ms;
     double backproject_images;
     double nnz_per_image;         /* nonzeros of W */
+    int32_t project_2h_launches;  /* projections on the 2h grid */
+    double project_2h_ms;
+    double project_2h_images;
 } wmg_profile_stats;
 int32_t wmg_profile_begin(wmg_plan *plan);
 int32_t wmg_profile_end(wmg_plan *plan, wmg_profile_stats *out, void *stream);

@@ -60,7 +60,8 @@ class wmg_profile_stats(C.Structure):
     _fields_ = [("project_launches", C.c_int32), ("project_ms", C.c_double),
                 ("project_images", C.c_double), ("backproject_launches", C.c_int32),
                 ("backproject_ms", C.c_double), ("backproject_images", C.c_double),
-                ("nnz_per_image", C.c_double)]
+                ("nnz_per_image", C.c_double), ("project_2h_launches", C.c_int32),
+                ("project_2h_ms", C.c_double), ("project_2h_images", C.c_double)]
 
 
 class wmg_server_config(C.Structure):
@@ -567,7 +568,7 @@ class Plan:
         self.solve(b, solver, preconditioned, max_iter, rtol, restart, out=out)
         st = wmg_profile_end(self.handle, self._stream())
         res = {"nnz_per_image": st.nnz_per_image}
-        for k in ("project", "backproject"):
+        for k in ("project", "backproject", "project_2h"):
             n = getattr(st, k + "_launches")
             ms = getattr(st, k + "_ms")
             imgs = getattr(st, k + "_images")

@@ -164,6 +164,14 @@ static int haar_width(const GeomDev &g)
     return wb * g.B;
 }
 
+// The geometry a set's tiles and launches use for geometry gi: its own, or
+// its 2h grid (sets on the 2h grid).
+static const GeomDev &set_geom(const wmg_plan *pl, const ProbSet &ps, int gi)
+{
+    const Geo &G = *pl->geos[gi];
+    return ps.on_2h ? G.gc : G.g;
+}
+
 void build_tiles(const wmg_plan *pl, ProbSet &ps)
 {
     ps.proj.h.clear(); ps.bp.h.clear(); ps.haar.h.clear(); ps.vimg.h.clear(); ps.vsino.h.clear();
@@ -177,7 +185,7 @@ void build_tiles(const wmg_plan *pl, ProbSet &ps)
         if (ps.h[q].geom < 0) { ++q; continue; }
         int e = q + 1;
         while (e < ps.nprob && ps.h[e].geom == ps.h[q].geom && !(e < (int)ps.brk.size() && ps.brk[e])) ++e;
-        const GeomDev &g = pl->geos[ps.h[q].geom]->g;
+        const GeomDev &g = set_geom(pl, ps, ps.h[q].geom);
         int f = q;
         const bool bpg = pl->prec != WMG_PREC_F64 && g.unit == 2 && g.qpair;
         for (; f + kProjGroup <= e; f += kProjGroup) {
@@ -202,7 +210,7 @@ void build_tiles(const wmg_plan *pl, ProbSet &ps)
         int64_t count = 0;
         for (int q = 0; q < ps.nprob && ok; ++q) {
             if (ps.h[q].geom < 0) continue;
-            const GeomDev &g = pl->geos[ps.h[q].geom]->g;
+            const GeomDev &g = set_geom(pl, ps, ps.h[q].geom);
             if (n0 < 0) n0 = g.n;
             const int64_t N = (int64_t)g.n * g.n;
             ok = g.n == n0 && g.n % 4 == 0 && g.dt <= 1.0 && ps.h[q].img % N == 0;
@@ -222,8 +230,9 @@ void build_tiles(const wmg_plan *pl, ProbSet &ps)
     for (int q = 0; q < ps.nprob; ++q) {
         if (ps.h[q].geom < 0) continue;          // an empty server slot: no tiles
         const Geo &G = *pl->geos[ps.h[q].geom];
-        const GeomDev &g = G.g;
-        const int W = G.haar_W;
+        const GeomDev &g = set_geom(pl, ps, ps.h[q].geom);
+        const int W = ps.on_2h ? G.haar_Wc : G.haar_W;
+        const int64_t Nq = ps.on_2h ? G.Nc : G.N;
         ps.haar_smem = std::max(ps.haar_smem, g.B * (W + W / g.B + 1));
         for (int a = 0; a < g.m; ++a)
             for (int k0 = 0; k0 < g.D; k0 += 32) ps.proj.h.push_back(make_int4(q, a, k0, 0));
@@ -234,8 +243,8 @@ void build_tiles(const wmg_plan *pl, ProbSet &ps)
             }
         for (int cy = 0; cy < g.nc; ++cy)
             for (int x0 = 0; x0 < g.n; x0 += W) ps.haar.h.push_back(make_int4(q, cy * g.B, x0, W));
-        for (int64_t s0 = 0; s0 < G.N; s0 += 8192)
-            ps.vimg.h.push_back(make_int4(q, (int)s0, (int)std::min<int64_t>(8192, G.N - s0), 0));
+        for (int64_t s0 = 0; s0 < Nq; s0 += 8192)
+            ps.vimg.h.push_back(make_int4(q, (int)s0, (int)std::min<int64_t>(8192, Nq - s0), 0));
         for (int64_t s0 = 0; s0 < G.M; s0 += 8192)
             ps.vsino.h.push_back(make_int4(q, (int)s0, (int)std::min<int64_t>(8192, G.M - s0), 0));
     }
@@ -338,22 +347,20 @@ void project(wmg_plan *pl, const ProbSet &ps, const void *img, const void *imgT,
 {
     PjArgs a{ps.pj_ctas, img, imgT, sino, part, S, ps.proj.tb.as<int>(), 1};
     a.bf16 = pl->bf16_now ? 1 : 0;
-    if (pl->profiling) prof_begin(pl, 0, ps.nprob, st);
+    const GeomDev *G = (ps.on_2h ? pl->d_geom_2h : pl->d_geom).as<GeomDev>();
+    if (pl->profiling) prof_begin(pl, ps.on_2h ? 2 : 0, ps.nprob, st);
     if (sizeof(T) == 4) {
         // FP32: groups of kProjGroup images share the weights; the rest run
         // one image per tile (the same per-image arithmetic in both). The
         // staged-pixel kernel reads FP32 pools only.
         a.group = kProjGroup;
-        if (!(ps.tma_n > 0 && !a.bf16 && launch_project_f32_tma(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(),
-                                                      ps.projg.tiles.as<int4>(), ps.projg.n, a, ps.tma_n,
-                                                      ps.tma_count, st)))
-            launch_project<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.projg.tiles.as<int4>(), ps.projg.n,
-                              a, st);
+        if (!(ps.tma_n > 0 && !a.bf16 && launch_project_f32_tma(G, ps.d.as<ProbDev>(), ps.projg.tiles.as<int4>(),
+                                                                ps.projg.n, a, ps.tma_n, ps.tma_count, st)))
+            launch_project<T>(G, ps.d.as<ProbDev>(), ps.projg.tiles.as<int4>(), ps.projg.n, a, st);
         a.group = 1;
-        launch_project<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.proj1.tiles.as<int4>(), ps.proj1.n, a,
-                          st);
+        launch_project<T>(G, ps.d.as<ProbDev>(), ps.proj1.tiles.as<int4>(), ps.proj1.n, a, st);
     } else {
-        launch_project<T>(pl->d_geom.as<GeomDev>(), ps.d.as<ProbDev>(), ps.proj.tiles.as<int4>(), ps.proj.n, a, st);
+        launch_project<T>(G, ps.d.as<ProbDev>(), ps.proj.tiles.as<int4>(), ps.proj.n, a, st);
     }
     if (pl->profiling) prof_end(pl, st);
 }
@@ -553,6 +560,45 @@ static ProbSet *band_set(wmg_plan *pl, int d, const std::vector<int> &nodes, con
     if (!upload_set(*ps, st)) return nullptr;
     ps->pj_ctas = pl->real.pj_ctas;
     ps->bp_ctas = pl->real.bp_ctas;
+    // Entries whose input lies inside the first split's LL band (leaves
+    // below K/4) of a geometry with a 2h grid, and whose outputs lie on other
+    // leaves: their synthesis and projection run on the 2h grid, on n/2 x n/2
+    // images (the same leaf values, one level fewer), and their lambda term,
+    // Q_out^T Q_in = 0, drops. Decided per entry, so that a problem takes the
+    // same path alone and in any batch.
+    std::vector<char> e2h(ps->nprob, 0);
+    int n2h = 0;
+    for (int q = 0; q < ps->nprob; ++q) {
+        const ProbDev &pd = ps->h[q];
+        const Geo &G = *pl->geos[pd.geom];
+        e2h[q] = G.has_2h && pd.kin1 <= G.g.K / 4 && (pd.kout0 >= pd.kin1 || pd.kout1 <= pd.kin0);
+        n2h += e2h[q];
+    }
+    auto subset = [&](bool want, bool grid) -> std::unique_ptr<ProbSet> {
+        auto cs = std::make_unique<ProbSet>();
+        cs->on_2h = grid;
+        int64_t oc = 0;
+        for (int q = 0; q < ps->nprob; ++q) {
+            if ((e2h[q] != 0) != want) continue;
+            ProbDev pd = ps->h[q];
+            if (grid) {                      // n/2 x n/2 images, back to back
+                pd.img = oc;
+                oc += pl->geos[pd.geom]->Nc;
+            }
+            cs->h.push_back(pd);
+        }
+        cs->nprob = (int)cs->h.size();
+        build_tiles(pl, *cs);
+        if (!upload_set(*cs, st)) return nullptr;
+        cs->pj_ctas = pl->real.pj_ctas;
+        cs->bp_ctas = pl->real.bp_ctas;
+        return cs;
+    };
+    if (n2h > 0) {
+        if (!(ps->grid2h = subset(true, true))) return nullptr;
+        if (n2h < ps->nprob && (!(ps->bp2h = subset(true, false)) || !(ps->rest = subset(false, false))))
+            return nullptr;
+    }
     ProbSet *raw = ps.get();
     pl->bands[key] = std::move(ps);
     return raw;
@@ -637,13 +683,35 @@ static int32_t band_update(wmg_plan *pl, int d, const std::vector<int> &nodes, c
     hs.outT = pl->band_imgT.p;
     hs.S = S;
     hs.fp32 = pl->prec == WMG_PREC_F32;
-    syn_op<T>(pl, G, bs->d.as<ProbDev>(), bs->haar.tiles.as<int4>(), bs->haar.n,
-                                     bs->haar_smem, hs, st);
-    project<T>(pl, *bs, pl->band_img.p, pl->band_imgT.p, pl->band_sino.p, nullptr, S, st);
-    BpArgs a = bp_args(BP_APPLY_A, pl->band_sino.p, S);
-    a.v_op = pl->band_img.p;
-    a.out64 = pl->band_img2.as<double>();
-    backproject<T>(pl, *bs, a, st);
+    if (const ProbSet *cs = bs->grid2h.get()) {
+        // inputs in the LL band of the first split: Q_in E = I_{2h}^h c with
+        // c the n/2 x n/2 synthesis of the same leaves, and W I_{2h}^h c the
+        // 2h grid's projection (half the rows); lambda Q_out^T Q_in E = 0 (the
+        // leaf ranges are disjoint), so the backprojection is W^T u alone
+        syn_op<T>(pl, pl->d_geom_2h.as<GeomDev>(), cs->d.as<ProbDev>(), cs->haar.tiles.as<int4>(), cs->haar.n,
+                  cs->haar_smem, hs, st);
+        project<T>(pl, *cs, pl->band_img.p, pl->band_imgT.p, pl->band_sino.p, nullptr, S, st);
+        BpArgs a = bp_args(BP_ATB, pl->band_sino.p, S);
+        a.out64 = pl->band_img2.as<double>();
+        backproject<T>(pl, bs->bp2h ? *bs->bp2h : *bs, a, st);
+        if (const ProbSet *rs = bs->rest.get()) {
+            // the other entries on W's grid (their images overwrite the 2h
+            // ones in the pool only after the 2h projection, in stream order)
+            syn_op<T>(pl, G, rs->d.as<ProbDev>(), rs->haar.tiles.as<int4>(), rs->haar.n, rs->haar_smem, hs, st);
+            project<T>(pl, *rs, pl->band_img.p, pl->band_imgT.p, pl->band_sino.p, nullptr, S, st);
+            BpArgs r = bp_args(BP_APPLY_A, pl->band_sino.p, S);
+            r.v_op = pl->band_img.p;
+            r.out64 = pl->band_img2.as<double>();
+            backproject<T>(pl, *rs, r, st);
+        }
+    } else {
+        syn_op<T>(pl, G, bs->d.as<ProbDev>(), bs->haar.tiles.as<int4>(), bs->haar.n, bs->haar_smem, hs, st);
+        project<T>(pl, *bs, pl->band_img.p, pl->band_imgT.p, pl->band_sino.p, nullptr, S, st);
+        BpArgs a = bp_args(BP_APPLY_A, pl->band_sino.p, S);
+        a.v_op = pl->band_img.p;
+        a.out64 = pl->band_img2.as<double>();
+        backproject<T>(pl, *bs, a, st);
+    }
     HaarArgs ha{};
     ha.mode = HA_SUB_MASKED;
     ha.in = pl->band_img2.p;
@@ -904,21 +972,39 @@ int32_t make_geo(const wmg_geom *g, const wmg_opts *o, Geo &G, cudaStream_t st)
     gd.angf = G.angf.as<AngleF>();
     geometry_scalars(gd, angf.data());
     G.unit_bins = gd.unit != 0;
+    // The 2h grid (Section 2.3): pixels of 2 x 2 blocks, L - 1 levels over
+    // the same leaves, detector in 2h pixel widths; h stays the fine pixel
+    // width (the halving of W^{2h} c / 2 = W I_{2h}^h c)
+    G.has_2h = G.has_wmg && L >= 2 && gd.kernel == WMG_KERNEL_STRIP;
+    if (G.has_2h) {
+        GeomDev &gc = G.gc;
+        gc = gd;
+        gc.n = gd.n / 2; gc.L = L - 1; gc.K = gd.K / 4; gc.B = gd.B / 2;
+        gc.t0 = 0.5 * gd.t0;
+        gc.dt = 0.5 * gd.dt;
+        gc.dinv = gc.leafinv = gc.sirtR = gc.sirtC = nullptr;
+        geometry_scalars(gc, angf.data());
+        G.Nc = (int64_t)gc.n * gc.n;
+        G.haar_Wc = haar_width(gc);
+    }
     return WMG_OK;
 }
 
 int32_t upload_geoms(wmg_plan *pl, cudaStream_t st)
 {
-    std::vector<GeomDev> h;
+    std::vector<GeomDev> h, h2;
     bool unit = true;
     for (auto &g : pl->geos) {
-        if (!g) { h.push_back(GeomDev{}); continue; }   // an evicted server geometry
+        if (!g) { h.push_back(GeomDev{}); h2.push_back(GeomDev{}); continue; }   // an evicted server geometry
         h.push_back(g->g);
+        h2.push_back(g->has_2h ? g->gc : GeomDev{});
         unit = unit && g->unit_bins;
     }
     pl->unit_bins = unit;
-    if (!pl->d_geom.ensure(h.size() * sizeof(GeomDev))) return fail(WMG_ERR_OOM, "geometry table");
+    if (!pl->d_geom.ensure(h.size() * sizeof(GeomDev)) || !pl->d_geom_2h.ensure(h2.size() * sizeof(GeomDev)))
+        return fail(WMG_ERR_OOM, "geometry table");
     WMG_CUDA(cudaMemcpyAsync(pl->d_geom.p, h.data(), h.size() * sizeof(GeomDev), cudaMemcpyHostToDevice, st));
+    WMG_CUDA(cudaMemcpyAsync(pl->d_geom_2h.p, h2.data(), h2.size() * sizeof(GeomDev), cudaMemcpyHostToDevice, st));
     WMG_CUDA(cudaStreamSynchronize(st));
     return WMG_OK;
 }
@@ -1152,7 +1238,11 @@ extern "C" int32_t wmg_profile_end(wmg_plan *plan, wmg_profile_stats *out, void 
         float ms = 0.f;
         cudaEventElapsedTime(&ms, r.e0, r.e1);
         if (r.kind == 0) { out->project_launches++; out->project_ms += ms; out->project_images += r.images; }
-        else { out->backproject_launches++; out->backproject_ms += ms; out->backproject_images += r.images; }
+        else if (r.kind == 2) {
+            out->project_2h_launches++;
+            out->project_2h_ms += ms;
+            out->project_2h_images += r.images;
+        } else { out->backproject_launches++; out->backproject_ms += ms; out->backproject_images += r.images; }
         cudaEventDestroy(r.e0);
         cudaEventDestroy(r.e1);
     }
@@ -1421,6 +1511,10 @@ static void swap_set(ProbSet &a, ProbSet &b)
     std::swap(a.haar_smem, b.haar_smem);
     std::swap(a.pj_ctas, b.pj_ctas);
     std::swap(a.bp_ctas, b.bp_ctas);
+    std::swap(a.on_2h, b.on_2h);
+    std::swap(a.grid2h, b.grid2h);
+    std::swap(a.bp2h, b.bp2h);
+    std::swap(a.rest, b.rest);
 }
 
 // A restriction pays once the live slots have fallen to this fraction; a

@@ -156,6 +156,15 @@ struct ProbSet {
     // launch shapes of the projector / backprojector over this set's tiles
     // (CTAs per SM; 0 = 8), chosen by autotune(); they do not change results
     int pj_ctas = 0, bp_ctas = 0;
+    // on_2h: the set's tiles and launches use its geometries' 2h grids
+    // (Geo::gc, the plan's d_geom_2h table) and its images are n/2 x n/2
+    bool on_2h = false;
+    // Band sets, split by entry (an entry's path never depends on the other
+    // entries): grid2h = the entries whose input lies in the first split's LL
+    // band, on the 2h grid, for their synthesis and projection; bp2h = the
+    // same entries on W's grid, for their backprojection (null: all entries);
+    // rest = the other entries (null: none)
+    std::unique_ptr<ProbSet> grid2h, bp2h, rest;
 };
 
 // One geometry of a plan with its device tables.
@@ -165,6 +174,16 @@ struct Geo {
     bool has_wmg = true, unit_bins = true;
     int hd = 0;                 // hybrid depth in use: min(hybrid_depth, L), 0 for additive
     int haar_W = 1;             // Haar strip width (pixels)
+    // The same scan on the 2h grid of 2 x 2 pixel blocks (Section 2.3),
+    // exact-length kernel and L >= 2 only: side n/2, L - 1 levels, the same
+    // leaves (nc, P), detector offset and spacing in 2h pixel widths, and h
+    // kept at the fine pixel width, so that projecting an n/2 x n/2 image c
+    // gives W^{2h} c / 2 = W I_{2h}^h c (eq. intops; chords add over the
+    // four pixels of a block). Tables shared with g; no smoother or leaf data.
+    bool has_2h = false;
+    GeomDev gc{};
+    int64_t Nc = 0;             // (n/2)^2
+    int haar_Wc = 1;            // Haar strip width of the 2h grid
     DevBuf cs64{true}, cs32{true}, csx{true}, angf{true}, dinv{true}, leafinv{true}, sirtR{true}, sirtC{true};
 };
 
@@ -199,6 +218,7 @@ struct wmg_plan {
     wmg_opts opts{};
     std::vector<std::unique_ptr<wmg::Geo>> geos;
     wmg::DevBuf d_geom;         // GeomDev array, one per geometry
+    wmg::DevBuf d_geom_2h;      // their 2h grids (Geo::gc; zeros where there is none)
     bool unit_bins = true;      // every geometry has unit bins, zero offset
     bool batch = false;         // fixed problem list
     int cap = 0;                // problem slots

@@ -35,14 +35,18 @@ def solve_metrics(n: int, m: int, D: int, precision: int, solver: int, precondit
     """The record of one solve call. infos: (iterations, status, rel_res)
     per problem; hists: residual histories or None; prof: the library's
     launch profile of the call (wmg_profile_stats fields). Every A-pair
-    projects each problem once, so A-pairs per problem = projected images /
-    problems. Operator bytes are algorithmic: the projector reads an image
-    and its transposed copy and writes a sinogram, the backprojector reads a
-    sinogram and writes an image."""
+    projects each problem once, on W's grid or, in the hybrid cycle's band
+    updates whose input lies in the first split's LL band, on the 2h grid;
+    so A-pairs per problem = projected images of both kinds / problems.
+    Intersections and operator bytes count the launches on W's grid alone
+    (their time only). Operator bytes are algorithmic: the projector reads
+    an image and its transposed copy and writes a sinogram, the
+    backprojector reads a sinogram and writes an image."""
     cnt = len(infos)
     N, M = n * n, m * D
     esz = 8 if precision == PREC_F64 else 4
     pj_img, bp_img = prof["project_images"], prof["backproject_images"]
+    pj2_img = prof.get("project_2h_images", 0.0)
     op_s = (prof["project_ms"] + prof["backproject_ms"]) / 1e3
     inter = prof["nnz_per_image"] * (pj_img + bp_img)
     nbytes = (pj_img * (2 * N + M) + bp_img * (M + N)) * esz
@@ -52,10 +56,12 @@ def solve_metrics(n: int, m: int, D: int, precision: int, solver: int, precondit
         "iterations": [int(i[0]) for i in infos],
         "status": [STATUS_NAMES.get(int(i[1]), str(i[1])) for i in infos],
         "rel_res": [float(i[2]) for i in infos],
-        "a_pairs_per_problem": pj_img / cnt if cnt else 0.0,
+        "a_pairs_per_problem": (pj_img + pj2_img) / cnt if cnt else 0.0,
         "setup_s": setup_s, "solve_s": solve_s,
         "project": {"launches": prof["project_launches"], "ms": prof["project_ms"], "images": pj_img},
         "backproject": {"launches": prof["backproject_launches"], "ms": prof["backproject_ms"], "images": bp_img},
+        "project_2h": {"launches": prof.get("project_2h_launches", 0), "ms": prof.get("project_2h_ms", 0.0),
+                       "images": pj2_img},
         "intersections_per_s": inter / op_s if op_s > 0 else None,
         "operator_gb_per_s": nbytes / op_s / 1e9 if op_s > 0 else None,
     }
@@ -82,7 +88,8 @@ def profiled_solve(plan: Plan, b, solver: int, preconditioned: bool = True, max_
         st = wmg_profile_end(plan.handle, plan._stream())
     torch.cuda.synchronize()
     prof = {k: getattr(st, k) for k in ("project_launches", "project_ms", "project_images", "backproject_launches",
-                                        "backproject_ms", "backproject_images", "nnz_per_image")}
+                                        "backproject_ms", "backproject_images", "nnz_per_image",
+                                        "project_2h_launches", "project_2h_ms", "project_2h_images")}
     rec = solve_metrics(plan.n, plan.m, plan.D, plan.opts.precision, solver, preconditioned, infos, hists, prof,
                         e0.elapsed_time(e1) / 1e3, getattr(plan, "setup_s", None))
     if log is not None:

@@ -151,3 +151,43 @@ def test_launch_shapes_do_not_change_results(prec):
     for o in outs[1:]:
         for a_, b_ in zip(outs[0], o):
             assert torch.equal(a_, b_)
+
+
+TWO_H = [  # n, m, D, dt, t0, levels, cycle, hybrid depth, kernel, band updates on the 2h grid
+    (64, 36, 91, 1.0, 0.0, 4, wmg.CYCLE_HYBRID, 1, wmg.KERNEL_STRIP, True),
+    (64, 30, 110, 0.8, 0.3, 4, wmg.CYCLE_HYBRID, 1, wmg.KERNEL_STRIP, True),
+    (64, 36, 91, 1.0, 0.0, 3, wmg.CYCLE_MULTIPLICATIVE, 2, wmg.KERNEL_STRIP, True),
+    (32, 36, 46, 1.0, 0.0, 2, wmg.CYCLE_HYBRID, 1, wmg.KERNEL_STRIP, False),    # L = 1: no 2h grid
+    (64, 36, 91, 1.0, 0.0, 4, wmg.CYCLE_HYBRID, 1, wmg.KERNEL_JOSEPH, False),   # weights do not add over blocks
+]
+
+
+@pytest.mark.parametrize("n,m,D,dt,t0,levels,cycle,hd,kernel,on2h", TWO_H)
+def test_band_updates_on_the_2h_grid(n, m, D, dt, t0, levels, cycle, hd, kernel, on2h):
+    """Band updates whose input lies in the first split's LL band project an
+    n/2 x n/2 image on the 2h grid (Section 2.3; W I_{2h}^h c = W^{2h} c / 2
+    for exact intersection lengths, L >= 2), the others on W's grid. The
+    cycle matches the oracle's (FP64 plan at 1e-10, FP32 plan at 1e-4 on 11
+    problems: groups of 8 staged by TMA and one-image tiles on the 2h grid),
+    and a problem alone gets the bits it gets in the batch."""
+    okernel = oracle.KERNEL_JOSEPH if kernel == wmg.KERNEL_JOSEPH else oracle.KERNEL_STRIP
+    op = oracle.Op(n, m, D, dt=dt, t0=t0, kernel=okernel)
+    ref = oracle.Wmg(op, levels, 0, 0, 1.0, 0.0, cycle, hd)
+    rng = np.random.default_rng(n + m + levels)
+    s = rng.standard_normal((11, op.N))
+    for prec, tol in ((wmg.PREC_F64, 1e-10), (wmg.PREC_F32, 1e-4)):
+        dtype = torch.float64 if prec == wmg.PREC_F64 else torch.float32
+        plan = wmg.Plan(n, m, D, levels=levels, nu1=0, nu2=0, hybrid_depth=hd, cycle=cycle, precision=prec,
+                        det_spacing=dt, det_offset=t0, kernel=kernel)
+        z = host(plan.precond(dev(s.reshape(-1), dtype))).reshape(11, -1)
+        for i in (0, 5, 10):
+            assert relmax(z[i], ref.apply(s[i])) < tol, (prec, i)
+        for i in (0, 10):
+            alone = host(plan.precond(dev(s[i], dtype)))
+            assert np.array_equal(alone, z[i]), (prec, i)
+        b = plan.project(dev(s.reshape(-1), dtype))
+        x = torch.empty_like(dev(s.reshape(-1), dtype))
+        prof = plan.profile_step(b, x, 3, 0.0, 20)
+        assert (prof["project_2h"]["launches"] > 0) == on2h, prof
+        assert prof["project"]["launches"] > 0
+        plan.close()

@@ -27,6 +27,14 @@ def test_solve_record_arithmetic():
     assert rec["solver"] == "GMRES" and rec["precision"] == "f32" and rec["problems"] == 2
     assert rec["residual_history"] == [[1.0, 0.5], [1.0]]
     json.dumps(rec)                                      # serialisable as it stands
+    # 4 more images projected on the 2h grid in 1 ms: A-pairs count them, the
+    # intersections and bytes of W's grid do not change
+    rec2 = metrics.solve_metrics(4, 3, 5, wmg.PREC_F32, wmg.SOLVER_GMRES, True, infos, None,
+                                 dict(prof, project_2h_launches=2, project_2h_ms=1.0, project_2h_images=4.0),
+                                 0.01)
+    assert rec2["a_pairs_per_problem"] == 7.0
+    assert rec2["intersections_per_s"] == rec["intersections_per_s"]
+    assert rec2["project_2h"] == {"launches": 2, "ms": 1.0, "images": 4.0}
 
 
 def test_percentiles_match_numpy():
@@ -67,6 +75,7 @@ class _Stats:
     project_launches, project_ms, project_images = 3, 1.0, 6.0
     backproject_launches, backproject_ms, backproject_images = 3, 1.0, 6.0
     nnz_per_image = 10.0
+    project_2h_launches, project_2h_ms, project_2h_images = 0, 0.0, 0.0
 
 
 class _StandInPlan:

@@ -33,6 +33,19 @@ def test_roofline_uses_the_measured_peak_when_given():
     assert "peak measured" in r["note"]
 
 
+def test_roofline_counts_the_2h_projections_in_the_choice_not_the_rate():
+    base = {"nnz_per_image": 15149028.0,
+            "project": {"launches": 28, "total_ms": 45.0, "mean_ms": 1.6, "images_per_launch": 256.0},
+            "backproject": {"launches": 57, "total_ms": 55.0, "mean_ms": 0.96, "images_per_launch": 230.0}}
+    r = bench.roofline_entry(base, P0, 256)
+    assert r["kernel"] == "k_backproject"
+    prof = dict(base, project_2h={"launches": 28, "total_ms": 24.0, "mean_ms": 0.86, "images_per_launch": 203.0})
+    r = bench.roofline_entry(prof, P0, 256)
+    assert r["kernel"] == "k_project"
+    assert abs(r["achieved"] - 2 * 15149028.0 * 256 / 1.6e-3 / 1e12) < 1e-9      # W's grid launches only
+    assert "28 launches on the 2h grid" in r["note"]
+
+
 def test_whole_job_value():
     assert bench.whole_job_value(256, 2, 5, 2.0) == 256 * 2 * 5 / 2.0
 

@@ -79,7 +79,14 @@ extern "C" {
 
 #define WMG_CYCLE_ADDITIVE   0  /* all leaf corrections from one residual */
 #define WMG_CYCLE_HYBRID     1  /* Section 3.1.2: residual recomputed after the
-                                   LL band at every node above hybrid_depth */
+                                   LL band at every node above hybrid_depth.
+                                   A residual update whose correction lies in
+                                   the LL band of the first split projects it
+                                   on the 2h grid (Section 2.3: pixels of 2 x 2
+                                   blocks): with exact intersection lengths
+                                   the same product up to rounding, at half
+                                   the cost; Joseph's kernel and levels < 3
+                                   keep the full grid (all cycles) */
 #define WMG_CYCLE_SYMMETRIC  2  /* hybrid followed by a second LL correction
                                    (LL, rest, LL): symmetric, for CGLS */
 #define WMG_CYCLE_MULTIPLICATIVE 3  /* Section 3.1.2, eq. wmg: the fully

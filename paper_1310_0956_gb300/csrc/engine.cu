@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "active_groups.h"
+#include "band_grid.h"
 #include "engine.cuh"
 
 namespace wmg {
@@ -504,12 +505,8 @@ void finalize(wmg_plan *pl, int op, const TileList &ta, const double *pa, int ns
 
 // ---------------------------------------------------------------------------
 // WMG coarse correction (Section 3.1.2 recursion) on the packet coefficients.
-// A tree node at depth d is named by its path prefix q in [0, 4^d); for a
-// slot with L levels it owns the leaves [q 4^(L-d), (q+1) 4^(L-d)). The LL
-// child of q is 4q, the other children 4q+1 .. 4q+3.
+// Tree nodes, their leaf ranges and the band updates' ranges: band_grid.h.
 // ---------------------------------------------------------------------------
-static inline int node_lo(int L, int d, int q) { return q << (2 * (L - d)); }
-static inline int node_hi(int L, int d, int q) { return (q + 1) << (2 * (L - d)); }
 
 static std::vector<int> make_key(int tag, int d, const std::vector<int> &nodes, const std::vector<int> &slots)
 {
@@ -545,16 +542,7 @@ static ProbSet *band_set(wmg_plan *pl, int d, const std::vector<int> &nodes, con
             pd.geom = pl->pgeo[slot]; pd.slot = slot;
             pd.img = oi; pd.sino = os; pd.coef = pl->img_off[slot];
             oi += G.N; os += G.M;
-            const int lo = node_lo(L, d, q), hi = node_hi(L, d, q);
-            const int ll_hi = node_hi(L, d + 1, 4 * q);
-            if (mode == 1) {        // symmetric closing step: the whole node in, its LL child out
-                pd.kin0 = lo; pd.kin1 = hi; pd.kout0 = lo; pd.kout1 = ll_hi;
-            } else if (mode == 0) { // hybrid step: the LL child in, the three other children out
-                pd.kin0 = lo; pd.kin1 = ll_hi; pd.kout0 = ll_hi; pd.kout1 = hi;
-            } else {                // child mode - 1 in, the children after it out
-                pd.kin0 = node_lo(L, d + 1, 4 * q + mode - 1); pd.kin1 = node_hi(L, d + 1, 4 * q + mode - 1);
-                pd.kout0 = pd.kin1; pd.kout1 = hi;
-            }
+            band_leaf_ranges(L, d, q, mode, pd.kin0, pd.kin1, pd.kout0, pd.kout1);
         }
     build_tiles(pl, *ps);
     if (!upload_set(*ps, st)) return nullptr;
@@ -571,7 +559,7 @@ static ProbSet *band_set(wmg_plan *pl, int d, const std::vector<int> &nodes, con
     for (int q = 0; q < ps->nprob; ++q) {
         const ProbDev &pd = ps->h[q];
         const Geo &G = *pl->geos[pd.geom];
-        e2h[q] = G.has_2h && pd.kin1 <= G.g.K / 4 && (pd.kout0 >= pd.kin1 || pd.kout1 <= pd.kin0);
+        e2h[q] = band_on_2h(G.has_2h, G.g.K, pd.kin0, pd.kin1, pd.kout0, pd.kout1);
         n2h += e2h[q];
     }
     auto subset = [&](bool want, bool grid) -> std::unique_ptr<ProbSet> {

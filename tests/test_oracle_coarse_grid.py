@@ -66,3 +66,24 @@ def test_joseph_weights_do_not_add_over_blocks():
     y = fine.project(prolong(c, n // 2))
     yc = 0.5 * coarse.project(c)
     assert np.abs(y - yc).max() > 1e-3 * np.abs(y).max()
+
+
+@pytest.mark.parametrize("n,m,D,L,lam", [(32, 24, 46, 2, 0.0), (32, 30, 47, 3, 0.7), (64, 36, 92, 4, 0.05)])
+def test_band_update_in_its_2h_form(n, m, D, L, lam):
+    """The hybrid step's band update at the root (Section 3.1.2): the
+    residual of the three children after the LL correction loses
+    Q_rest^T (W^T W + lambda) Q_LL E_LL. Its 2h form: synthesise c from the
+    LL leaves through L - 1 levels, project on the 2h grid and halve,
+    backproject on W's grid, analyse into the other leaves; no lambda term
+    (Q_rest^T Q_LL = 0)."""
+    rng = np.random.default_rng(n + L)
+    N = n * n
+    E = np.zeros(N)
+    E[:N // 4] = rng.standard_normal(N // 4)
+    fine = oracle.Op(n, m, D)
+    coarse = oracle.Op(n // 2, m, D, dt=0.5)
+    x = oracle.packet_synthesis(E, n, L)
+    ref = oracle.packet_analysis(fine.backproject(fine.project(x)) + lam * x, n, L)[N // 4:]
+    c = oracle.packet_synthesis(E[:N // 4], n // 2, L - 1)
+    got = oracle.packet_analysis(fine.backproject(0.5 * coarse.project(c)), n, L)[N // 4:]
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
